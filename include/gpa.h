@@ -1,0 +1,316 @@
+/*
+ * gpa.h — C ABI of libgpa: contention-aware GPU-partition schedulability
+ * (Zahaf, Sañudo Olmedo, Singh, Capodieci, Faucou, "Contention-Aware GPU
+ * Partitioning and Task-to-Partition Allocation for Real-Time Workloads",
+ * arXiv 2105.10312).
+ *
+ * The library evaluates the paper's per-partition schedulability test over
+ * candidate splits of M SMs into partitions and task-to-partition maps, for
+ * large batches of task sets.  All time quantities are integer ticks; the
+ * interference factors are integer per-mille rationals; every result is
+ * exact (bit-identical to a plain CPU evaluation of the same definitions).
+ *
+ * Conventions (all entry points)
+ *  - Return value: int32_t status, GPA_OK (0) or a negative GPA_ERR_*.
+ *    No C++ exception crosses the ABI.  gpa_last_error() returns the message
+ *    of the last failing call on this thread.
+ *  - Ownership: the caller owns every array it passes (host or device).  The
+ *    library owns only the gpa_ctx (its stream binding, autotune cache,
+ *    cached CUDA graphs and device scratch) and the serving state.
+ *  - Memory tag: structs carrying arrays have a `mem` field, GPA_HOST or
+ *    GPA_DEVICE, that applies to every array of that struct.  Host inputs
+ *    are validated on the host before any launch (GPA_ERR_RANGE, nothing
+ *    launched) and the call is synchronous.  Device inputs are validated by
+ *    the kernels: an invalid set gets reason GPA_REASON_INVALID, its other
+ *    outputs are zero, and the context's sticky error word is set; the call
+ *    itself is asynchronous on the context stream and gpa_ctx_sync() reports
+ *    GPA_ERR_RANGE afterwards.
+ *  - Streams are passed as void* (a cudaStream_t); NULL is the legacy stream.
+ *
+ * Task model (paper §4.2, §7.1)
+ *  A task set is a slice [set_off[s], set_off[s+1]) of structure-of-arrays
+ *  task columns.  Task i has period T_i, relative deadline D_i (D_i <= T_i),
+ *  WCET parameters A_i, B_i, type (0 = compute-intensive, 1 = memory-
+ *  intensive; Def. 1) and utilisation u_ppm_i (parts per million, used for
+ *  ordering and for the inflated workload W).  Its WCET on a partition of
+ *  m SMs with interference factor k (per mille) is the scaling function of
+ *  §7.1, C = k (a/m + b), in integer form:
+ *
+ *      C_i^k(m) = ceil( k * (A_i + B_i * m) / (10^6 * m) )
+ *
+ *  with k = 1000 when the task is not in conflict (C^n of §3.3) and
+ *  k = k_c_pm (compute) or k_m_pm (memory) when it is (C^c of §3.3).  A task
+ *  is in conflict when at least one other task of its own type shares its
+ *  partition (§4.2).
+ *
+ * Per-partition test (§5.6 leaves the policy open): a partition of m SMs is
+ * one processor running its tasks under deadline-monotonic fixed priorities
+ * (priority order: D ascending, then T ascending, then task index); each
+ * task's response time is the least fixed point of
+ *      R_i = C_i + sum_{j in hp(i)} ceil(R_i / T_j) * C_j
+ * started from R_i^0 = C_i + sum_{hp(i)} C_j.  A task meets its deadline iff
+ * that fixed point is <= D_i; otherwise its reported R is -1.
+ *
+ * Validation bounds (GPA_ERR_RANGE): 0 <= n <= 128 tasks per set,
+ * 1 <= D <= T <= 2^31 - 1, A >= 0, B >= 0, 1 <= A + B <= 2^36,
+ * 0 <= u_ppm <= 2^32, type in {0, 1}; model: 1 <= g, g | M, 1 <= M <= 1024,
+ * 1000 <= k_c_pm, k_m_pm <= 16000.  These keep every WCET below 2^31 and
+ * every intermediate product inside 64 bits.
+ */
+#ifndef GPA_H_
+#define GPA_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GPA_ABI_VERSION 1
+#define GPA_NMAX 128          /* tasks per set */
+#define GPA_MMAX 1024         /* SMs on the modelled GPU */
+#define GPA_SEARCH_NMAX 14    /* tasks per set in gpa_search_best */
+#define GPA_SEARCH_KMAX 8     /* partitions per candidate in gpa_search_best */
+
+enum {
+  GPA_OK = 0,
+  GPA_ERR_ARG = -1,      /* NULL where an array is required, bad enum, bad size */
+  GPA_ERR_RANGE = -2,    /* input outside the validation bounds above */
+  GPA_ERR_NOMEM = -3,    /* device or host allocation failed */
+  GPA_ERR_CUDA = -4,     /* a CUDA runtime call failed */
+  GPA_ERR_TIMEOUT = -5,  /* a bounded wait expired */
+  GPA_ERR_BUSY = -6,     /* serving: the host queue is full */
+  GPA_ERR_NOTFOUND = -7  /* serving: unknown request id / tenant */
+};
+
+enum { GPA_HOST = 0, GPA_DEVICE = 1 };
+
+/* Task types (Def. 1). */
+enum { GPA_COMPUTE = 0, GPA_MEMORY = 1 };
+
+/* Per-set outcome of gpa_allocate. */
+enum {
+  GPA_REASON_OK = 0,        /* schedulable allocation found (Lemma 3) */
+  GPA_REASON_LEMMA1 = 1,    /* rejected by the necessary utilisation test (Lemma 1) */
+  GPA_REASON_LEMMA2 = 2,    /* a task meets its deadline on no size <= M (Lemma 2) */
+  GPA_REASON_NO_MERGE = 3,  /* Alg. 3 found no eligible merge while Pi > M */
+  GPA_REASON_TEST = 4,      /* 1G baseline: the single partition fails the test */
+  GPA_REASON_INVALID = 5    /* device-side validation rejected the set */
+};
+
+/* Allocation policies (§7.2). */
+enum {
+  GPA_POLICY_SMS = 0,       /* order >> of Def. 3: smallest merged size first */
+  GPA_POLICY_BF = 1,        /* order > of Def. 4: smallest merged workload first */
+  GPA_POLICY_ONE_GPU = 2    /* 1G baseline: all tasks in one partition of M SMs */
+};
+
+/* ---------------------------------------------------------------- context */
+
+typedef struct gpa_ctx gpa_ctx;
+
+/* Create a context bound to CUDA device `device` and stream `stream`
+ * (cudaStream_t, may be NULL).  *out receives the context.
+ * Errors: GPA_ERR_ARG (out NULL, bad device), GPA_ERR_CUDA. */
+int32_t gpa_ctx_create(int32_t device, void* stream, gpa_ctx** out);
+/* Destroy a context; frees its scratch, graphs and serving state. NULL is a no-op. */
+int32_t gpa_ctx_destroy(gpa_ctx* ctx);
+/* Rebind the context to another stream of the same device. */
+int32_t gpa_ctx_set_stream(gpa_ctx* ctx, void* stream);
+/* Wait for the context stream; return GPA_ERR_RANGE if any kernel since the
+ * last call flagged an invalid device-resident set (and clear the flag),
+ * GPA_ERR_CUDA on an asynchronous CUDA error, else GPA_OK. */
+int32_t gpa_ctx_sync(gpa_ctx* ctx);
+/* Copy the last error message of this thread into buf (NUL-terminated). */
+int32_t gpa_last_error(char* buf, int32_t len);
+/* Number of GPU kernel launches the context has issued since creation. */
+int32_t gpa_ctx_launch_count(gpa_ctx* ctx, int64_t* out);
+
+/* Context options (gpa_ctx_set_option).  None changes any result. */
+enum {
+  GPA_OPT_AUTOTUNE = 1,       /* 1: time the fast allocate kernel's launch shapes on the first call of each
+                                 batch signature and keep the fastest (default 0) */
+  GPA_OPT_GRAPH = 2,          /* 1: capture gpa_allocate's launches in a CUDA graph per argument set and
+                                 replay it (default 0); not allowed while the stream is being captured */
+  GPA_OPT_FAST_WARPS = 3,     /* force warps per CTA of the fast allocate kernel (0 = tuned/default) */
+  GPA_OPT_FAST_CHUNK = 4,     /* force task sets per work-queue ticket (0 = tuned/default) */
+  GPA_OPT_FAST_BLOCKS = 5,    /* force CTAs of the persistent grid (0 = tuned/default) */
+  GPA_OPT_PER_SET_LAUNCH = 6  /* 1: the plain form, one launch sequence per task set (comparison only) */
+};
+int32_t gpa_ctx_set_option(gpa_ctx* ctx, int32_t option, int64_t value);
+
+/* --------------------------------------------------------------- task sets */
+
+typedef struct {
+  int64_t nsets;
+  int32_t mem;              /* GPA_HOST or GPA_DEVICE for every array below */
+  int32_t n_max;            /* upper bound on tasks per set (<= GPA_NMAX) */
+  const int64_t* set_off;   /* [nsets + 1], set_off[0] = 0, non-decreasing */
+  const int64_t* T;         /* [ntasks] period */
+  const int64_t* D;         /* [ntasks] relative deadline */
+  const int64_t* A;         /* [ntasks] WCET parameter a (per-mille scaled) */
+  const int64_t* B;         /* [ntasks] WCET parameter b (per-mille scaled) */
+  const int64_t* u_ppm;     /* [ntasks] utilisation, parts per million */
+  const uint8_t* type;      /* [ntasks] GPA_COMPUTE / GPA_MEMORY */
+} gpa_tasksets;
+
+typedef struct {
+  int32_t M;       /* SMs of the modelled GPU (§4.1) */
+  int32_t g;       /* partition granularity in SMs (1 = SM, 2 = TPC); sizes are multiples of g */
+  int32_t k_c_pm;  /* conflict factor of compute-intensive tasks, per mille (§7.1: 1200) */
+  int32_t k_m_pm;  /* conflict factor of memory-intensive tasks, per mille (§7.1: 2300) */
+} gpa_model;
+
+/* Host-side validation of a task batch and model against the bounds above
+ * (host arrays only; no GPU needed).  *bad_set receives the first invalid
+ * set index or -1.  Returns GPA_OK or GPA_ERR_RANGE / GPA_ERR_ARG. */
+int32_t gpa_validate(const gpa_tasksets* sets, const gpa_model* model, int64_t* bad_set);
+
+/* --------------------------------------------------------------- generator */
+
+enum { GPA_DIST_UNIFORM = 0, GPA_DIST_LOGUNIFORM = 1, GPA_DIST_LIST = 2, GPA_DIST_BETA25 = 3 };
+enum { GPA_GEN_ALPHA = 0, GPA_GEN_PAPER = 1 };
+
+typedef struct {
+  uint64_t seed;
+  int64_t nsets;
+  int32_t n_min, n_max;        /* tasks per set */
+  int32_t n_dist;              /* UNIFORM or LOGUNIFORM over [n_min, n_max] */
+  int32_t U_steps;             /* 0: U ~ U[U_lo, U_hi]; > 0: U = U_lo + (s mod U_steps) * (U_hi - U_lo) / (U_steps - 1) */
+  int64_t U_lo_ppm, U_hi_ppm;  /* total utilisation per set, ppm */
+  int64_t T_lo, T_hi;          /* period range, ticks */
+  int32_t T_dist;              /* LOGUNIFORM over [T_lo, T_hi], or LIST = divisors of T_hi in [T_lo, T_hi] */
+  int32_t deadline_pm;         /* D = max(1, floor(T * deadline_pm / 1000)) */
+  int32_t alpha_lo_pm, alpha_hi_pm; /* ALPHA mode: serial fraction alpha ~ U{lo..hi} per mille */
+  int32_t mu_dist;             /* memory intensity: UNIFORM or BETA25 (Beta(2,5)), per mille */
+  int32_t prm_pm;              /* type = MEMORY iff mu_pm >= prm_pm */
+  int32_t mode;                /* GPA_GEN_ALPHA: A = C1 (1000 - alpha), B = C1 alpha
+                                  GPA_GEN_PAPER:    A = 1000 C1, B = beta C1 (beta by type) */
+  int32_t beta_c_pm, beta_m_pm;/* PAPER mode serial parts (§7.1: 20 and 100 per mille) */
+  int64_t u_max_ppm;           /* discard and redraw a set whose largest task utilisation exceeds this (0 = never) */
+  int32_t max_tries;           /* redraw limit per set (the last draw is kept, flagged) */
+  int32_t nthreads;            /* host threads (<= 0: 1) */
+} gpa_gen_params;
+
+typedef struct {
+  int64_t* set_off;    /* [nsets + 1] */
+  int64_t* T;          /* [ntasks] */
+  int64_t* D;
+  int64_t* A;
+  int64_t* B;
+  int64_t* u_ppm;      /* floor(10^6 C1 / T) after rounding C1 */
+  uint8_t* type;
+  int64_t* C1;         /* baseline single-SM execution time (ticks) */
+  int16_t* alpha_pm;
+  int16_t* mu_pm;
+  uint8_t* flags;      /* [nsets] bit 0: discard limit reached */
+} gpa_gen_out;
+
+/* Seeded, counter-based synthetic task-set generator (§7.1; utilisations are
+ * drawn uniformly on the simplex sum u_i = U).  Host memory only.
+ * Call with out == NULL to get the total task count in *ntasks; then call
+ * again with every array of *out allocated to that size. */
+int32_t gpa_gen_tasksets(const gpa_gen_params* params, gpa_gen_out* out, int64_t* ntasks);
+
+/* ------------------------------------------------------------- WCET tables */
+
+/* a2: Cn and Cc tables, layout [set][m-index][task]: for set s with n_s tasks
+ * at offset o_s, the entry of task t at size m = g (mi + 1), mi < M/g, is at
+ * o_s * (M/g) + mi * n_s + t.  Cn uses k = 1000; Cc uses k_c_pm or k_m_pm by
+ * type (§3.3, §7.1).  Both arrays hold ntasks * (M/g) int64 and live in the
+ * memory named by sets->mem. */
+int32_t gpa_build_wcet_tables(gpa_ctx* ctx, const gpa_tasksets* sets, const gpa_model* model,
+                              int64_t* Cn, int64_t* Cc);
+
+/* ---------------------------------------------------- partition enumeration */
+
+/* Number of compositions of Mu = M/g units into k parts, summed over
+ * k in [kmin, kmax] (candidate SM splits, §4.1). */
+int32_t gpa_enumerate_partitions(int32_t Mu, int32_t kmin, int32_t kmax, uint64_t* count);
+/* The composition of Mu into k positive parts of rank `rank` in
+ * lexicographic order of (parts[0], ..., parts[k-1]). */
+int32_t gpa_unrank_composition(int32_t Mu, int32_t k, uint64_t rank, int32_t* parts);
+/* Number of set partitions of n tasks into at most kmax blocks. */
+int32_t gpa_count_rgs(int32_t n, int32_t kmax, uint64_t* count);
+/* The restricted-growth string of rank `rank` (lexicographic order) among
+ * set partitions of n tasks into at most kmax blocks. */
+int32_t gpa_unrank_rgs(int32_t n, int32_t kmax, uint64_t rank, uint8_t* rgs);
+
+/* ------------------------------------------------------- explicit candidates */
+
+typedef struct {
+  int64_t ncands;
+  int32_t mem;
+  int32_t map_stride;       /* bytes per candidate in part_of_task (>= tasks of its set) */
+  int32_t kparts;           /* parts per candidate = entries per candidate in size_of_part */
+  int32_t pad_;
+  const int64_t* set;       /* [ncands] task-set index */
+  const uint8_t* part_of_task; /* [ncands * map_stride] part of each task (< kparts) */
+  const int32_t* size_of_part; /* [ncands * kparts] SMs of each part: 0 or a multiple of g in [g, M] */
+} gpa_candidates;
+
+/* a4 over a flat batch: candidate c is schedulable iff sum of its part sizes
+ * <= M and every non-empty part meets the per-partition test at its size (a
+ * non-empty part of size 0 fails).  verdict[c] in {0,1}; R (nullable) gets
+ * each task's response time at R[c * map_stride + t], -1 for a miss.
+ * Arrays live in cands->mem (which must equal sets->mem). */
+int32_t gpa_test_schedulable(gpa_ctx* ctx, const gpa_tasksets* sets, const gpa_model* model,
+                             const gpa_candidates* cands, uint8_t* verdict, int64_t* R);
+
+/* ------------------------------------------------------------- heuristic */
+
+typedef struct {
+  int32_t policy;       /* GPA_POLICY_SMS / BF / ONE_GPU */
+  int32_t act;          /* 1: fill the forbidden list with failing task pairs first (ACT); 0: INA */
+  int32_t linear_merge; /* 1: Alg. 2 linear scan; 0: binary search (same result) */
+  int32_t pad_;
+} gpa_params;
+
+typedef struct {
+  int32_t mem;
+  int32_t pad_;
+  uint8_t* verdict;       /* [nsets] 1 iff a schedulable allocation was found */
+  uint8_t* reason;        /* [nsets] GPA_REASON_* */
+  int32_t* n_parts;       /* [nsets] partitions in the final list */
+  int32_t* Pi;            /* [nsets] sum of partition sizes (SMs) */
+  int64_t* W;             /* [nsets] inflated workload sum_P sum_{i in P} k_i(P) u_ppm_i */
+  int32_t* n_tests;       /* [nsets] merge candidates evaluated (nullable) */
+  uint8_t* part_of_task;  /* [ntasks] partition of each task, 255 when none */
+  int16_t* size_of_part;  /* [ntasks] size of partition p of set s at set_off[s] + p (p < n_parts), else 0 */
+} gpa_alloc_result;
+
+/* a7/a9: the paper's partition-and-allocate heuristic (Alg. 1-3 with
+ * Lemmas 1-3, SMS/BF x ACT/INA) or the 1G baseline, for every set of the
+ * batch.  Partitions are numbered by their lowest task index.  result->mem
+ * must equal sets->mem. */
+int32_t gpa_allocate(gpa_ctx* ctx, const gpa_tasksets* sets, const gpa_model* model,
+                     const gpa_params* params, gpa_alloc_result* result);
+
+/* ------------------------------------------------------ exhaustive optimum */
+
+typedef struct {
+  int32_t mem;
+  int32_t pad_;
+  uint8_t* feasible;      /* [nsets] */
+  int64_t* W;             /* [nsets] inflated workload of the optimum */
+  int32_t* sum_minm;      /* [nsets] sum over blocks of the block's minimum size */
+  int32_t* n_blocks;      /* [nsets] */
+  int32_t* spare;         /* [nsets] M - sum_minm - max(0, kmin - n_blocks) * g */
+  uint8_t* rgs;           /* [ntasks] block of each task (restricted growth string) */
+  int16_t* minm_block;    /* [nsets * kmax] minimum size of each block, 0 past n_blocks */
+} gpa_best_result;
+
+/* a6/a8: exact optimum over every split of M into k in [kmin, kmax]
+ * partitions (multiples of g) and every task-to-partition map, for sets of
+ * at most GPA_SEARCH_NMAX tasks.  Key (lexicographic, minimised): W, then
+ * sum_minm, then the restricted-growth string of the induced set partition.
+ * A set partition with b blocks is realisable iff b <= kmax, every block
+ * has a minimum size, and sum_minm + max(0, kmin - b) g <= M. */
+int32_t gpa_search_best(gpa_ctx* ctx, const gpa_tasksets* sets, const gpa_model* model,
+                        int32_t kmin, int32_t kmax, gpa_best_result* result);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPA_H_ */

@@ -1,0 +1,191 @@
+"""Independent CPU references used to pin the oracle (test-only).
+
+Each function restates a fact the paper or textbook scheduling theory fixes,
+by a different route from the oracle's code:
+
+* ``wcet_alpha`` / ``wcet_paper``: the execution-time model of §3.3 in the
+  scaling-function form of §7.1, C = k (a/m + b), evaluated with exact
+  rationals from the serial-fraction parameters (alpha) or the paper's b = beta a.
+* ``simulate_fp``: a unit-step discrete-time simulation of a fixed-priority
+  uniprocessor schedule with synchronous release (the partition of §5.6 run
+  as one processor) -- response times by brute force, not by analysis.
+* ``heuristic``: Alg. 1-3 restated over Python frozensets (different data
+  structures and loop order from the oracle), using a supplied per-partition
+  test.
+* ``exhaustive_bruteforce``: every composition of M/g into k parts times every
+  task-to-part map, evaluated directly.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+from fractions import Fraction
+
+
+def wcet_alpha(C1, alpha_pm, k_pm, m):
+    """ceil(k C1 (alpha + (1 - alpha) / m)) with alpha = alpha_pm / 1000 (exact)."""
+    C1, alpha_pm, k_pm, m = int(C1), int(alpha_pm), int(k_pm), int(m)
+    a = Fraction(alpha_pm, 1000)
+    v = Fraction(k_pm, 1000) * C1 * (a + (1 - a) / m)
+    return math.ceil(v)
+
+
+def wcet_paper(a, beta_pm, k_pm, m):
+    """ceil(k (a / m + b)) with b = beta a (exact), the §7.1 scaling function."""
+    a, beta_pm, k_pm, m = int(a), int(beta_pm), int(k_pm), int(m)
+    v = Fraction(k_pm, 1000) * (Fraction(a, m) + Fraction(beta_pm, 1000) * a)
+    return math.ceil(v)
+
+
+def simulate_fp(tasks, horizon):
+    """tasks: list of (T, D, C) in priority order (index 0 highest).  Synchronous
+    release at t = 0, unit time steps, work-conserving.  Returns (first, worst):
+    the first job's response time of each task (None if not finished by
+    ``horizon``) and the largest response time over jobs released before
+    ``horizon`` that finished by ``horizon``."""
+    n = len(tasks)
+    pending = [[] for _ in range(n)]  # [release, remaining]
+    first = [None] * n
+    worst = [0] * n
+    jobno = [0] * n
+    for t in range(horizon):
+        for i, (T, D, C) in enumerate(tasks):
+            if t % T == 0:
+                pending[i].append([t, C, jobno[i]])
+                jobno[i] += 1
+        for i in range(n):
+            if pending[i]:
+                job = pending[i][0]
+                job[1] -= 1
+                if job[1] == 0:
+                    resp = t + 1 - job[0]
+                    if job[2] == 0:
+                        first[i] = resp
+                    worst[i] = max(worst[i], resp)
+                    pending[i].pop(0)
+                break
+    return first, worst
+
+
+def dm_order(T, D, idx):
+    return sorted(idx, key=lambda i: (D[i], T[i], i))
+
+
+def conflict_k(types, S, i, kc, km):
+    same = sum(1 for j in S if types[j] == types[i])
+    if same >= 2:
+        return km if types[i] == 1 else kc
+    return 1000
+
+
+def heuristic(n, u, M, g, single_size, test_min, policy="SMS", act=False, W=None):
+    """Alg. 1-3 over frozensets.  single_size(i) -> Lemma 2 size or 0;
+    test_min(S, lo, hi) -> smallest passing size in [lo, hi] or 0;
+    W(S) -> inflated workload (Def. 4 reading).  Returns (ok, parts, tests)
+    with parts a dict frozenset -> size; Lemma 1 is left to the caller."""
+    parts = {}
+    for i in range(n):
+        z = single_size(i)
+        if z == 0:
+            return "LEMMA2", {}, 0
+        parts[frozenset([i])] = z
+    tests = 0
+    act_pairs = set()
+    if act and sum(parts.values()) > M:
+        for i, j in itertools.combinations(range(n), 2):
+            a, b = parts[frozenset([i])], parts[frozenset([j])]
+            tests += 1
+            if test_min(frozenset([i, j]), max(a, b), a + b - g) == 0:
+                act_pairs.add(frozenset([i, j]))
+    failed = set()  # frozenset({P, Q})
+
+    def forbidden(P, Q):
+        if frozenset([P, Q]) in failed:
+            return True
+        return any(frozenset([i, j]) in act_pairs for i in P for j in Q)
+
+    while sum(parts.values()) > M:
+        order = sorted(parts, key=lambda P: (-sum(u[i] for i in P), min(P)))
+        chosen = None
+        for P in order:
+            elig = [Q for Q in order if Q != P and not forbidden(P, Q)]
+            if elig:
+                chosen = (P, elig)
+                break
+        if chosen is None:
+            return "NO_MERGE", parts, tests
+        P, elig = chosen
+        if policy == "SMS":
+            results = []
+            for pos, Q in enumerate(elig):
+                tests += 1
+                m3 = test_min(P | Q, max(parts[P], parts[Q]), parts[P] + parts[Q] - g)
+                if m3:
+                    results.append((m3, pos, Q))
+            if results:
+                m3, _, Q = min(results, key=lambda r: (r[0], r[1]))
+                del parts[P], parts[Q]
+                parts[P | Q] = m3
+            else:
+                for Q in elig:
+                    failed.add(frozenset([P, Q]))
+        else:
+            ranked = sorted(enumerate(elig), key=lambda pq: (W(P | pq[1]), pq[0]))
+            for _, Q in ranked:
+                tests += 1
+                m3 = test_min(P | Q, max(parts[P], parts[Q]), parts[P] + parts[Q] - g)
+                if m3:
+                    del parts[P], parts[Q]
+                    parts[P | Q] = m3
+                    break
+                failed.add(frozenset([P, Q]))
+    return "OK", parts, tests
+
+
+def compositions(total, k):
+    """All compositions of total into k positive parts, lexicographic."""
+    if k == 1:
+        yield (total,)
+        return
+    for first in range(1, total - k + 2):
+        for rest in compositions(total - first, k - 1):
+            yield (first,) + rest
+
+
+def rgs_of(labels):
+    seen = {}
+    out = []
+    for lab in labels:
+        if lab not in seen:
+            seen[lab] = len(seen)
+        out.append(seen[lab])
+    return tuple(out)
+
+
+def exhaustive_bruteforce(n, M, g, kmin, kmax, passes, minsize, W):
+    """passes(S, m) -> bool; minsize(S) -> minimal size in [g, M] or 0;
+    W(S) -> workload.  Returns None or (W, sum_minm, rgs)."""
+    best = None
+    Mu = M // g
+    for k in range(kmin, kmax + 1):
+        if k > Mu:
+            break
+        for comp in compositions(Mu, k):
+            for labels in itertools.product(range(k), repeat=n):
+                ok = True
+                for p in range(k):
+                    S = frozenset(i for i in range(n) if labels[i] == p)
+                    if S and not passes(S, comp[p] * g):
+                        ok = False
+                        break
+                if not ok:
+                    continue
+                rgs = rgs_of(labels)
+                blocks = {}
+                for i, b in enumerate(rgs):
+                    blocks.setdefault(b, set()).add(i)
+                key = (sum(W(frozenset(B)) for B in blocks.values()),
+                       sum(minsize(frozenset(B)) for B in blocks.values()), rgs)
+                if best is None or key < best:
+                    best = key
+    return best

@@ -1,0 +1,476 @@
+"""Pins of the CPU oracle against facts fixed outside it (no GPU).
+
+Each test checks the oracle against the paper (worked example, constants),
+closed forms, textbook scheduling results, brute force on tiny inputs, or an
+independent restatement in ``refs.py`` -- never against the oracle itself.
+"""
+import itertools
+import json
+import math
+import os
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+import refs
+from paper_2105_10312_gb300 import gen_tasksets, workloads
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+KC, KM = 1200, 2300
+
+
+def golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+# ------------------------------------------------------------ conflict rule
+
+def test_conflict_worked_example():
+    """§4.2: 9 compute + 1 memory kernel in one partition -> the memory kernel
+    is not in conflict, the 9 compute kernels are (observed through W and R)."""
+    g = golden("conflict_example.json")
+    types = np.array(g["types"], np.uint8)
+    n = len(types)
+    for i in range(n):
+        u = np.zeros(n, np.int64)
+        u[i] = 1
+        w = oracle.workload(u, types, np.ones(n, np.uint8), KC, KM)
+        k_expected = (KM if types[i] == 1 else KC) if g["in_conflict"][i] else 1000
+        assert w == k_expected, (i, w)
+    # through the test: the memory kernel at top priority responds in C^n
+    T = np.full(n, 10**6, np.int64)
+    D = T.copy()
+    D[9] = 1000  # highest priority under DM
+    A = np.full(n, 7 * 1000, np.int64)
+    B = np.zeros(n, np.int64)
+    _, R = oracle.rta(T, D, A, B, types, np.ones(n, np.uint8), 1, KC, KM)
+    assert R[9] == 7  # k = 1: not inflated
+    # a compute kernel sees its own inflated WCET: 7 * 1.2 -> ceil 9 (8.4)
+    _, R1 = oracle.rta(T, D, A, B, types, np.array([1, 0, 0, 0, 0, 0, 0, 0, 1, 0], np.uint8), 1, KC, KM)
+    assert R1[0] == 9 and R1[8] == 18
+
+
+def test_conflict_needs_same_type_partner():
+    """A lone task of each type is never in conflict (k = 1 for both)."""
+    types = np.array([0, 1], np.uint8)
+    for i in range(2):
+        u = np.zeros(2, np.int64)
+        u[i] = 5
+        assert oracle.workload(u, types, np.ones(2, np.uint8), KC, KM) == 5000
+
+
+# ---------------------------------------------------------------- WCET model
+
+def test_model_constants_golden():
+    g = golden("model_constants.json")
+    p = workloads.gen_params("paper50")
+    assert p["beta_c_pm"] == g["beta_compute_pm"] and p["beta_m_pm"] == g["beta_memory_pm"]
+    assert workloads.K_C == g["k_compute_pm"] and workloads.K_M == g["k_memory_pm"]
+    assert p["deadline_pm"] == g["deadline_pm"] and p["prm_pm"] == g["prm_pm"]
+    assert (p["T_lo"], p["T_hi"]) == (g["period_lo"], g["period_hi"])
+    assert workloads.model("paper50")["M"] == g["M"]
+
+
+def test_wcet_alpha_form_matches_rational_closed_form():
+    rng = random.Random(1)
+    for _ in range(3000):
+        C1 = rng.choice([1, 2, 3, 999, 1000, 12345, rng.randrange(1, 1 << 26)])
+        alpha = rng.randrange(0, 1001)
+        k = rng.choice([1000, 1200, 2300, rng.randrange(1000, 16001)])
+        m = rng.randrange(1, 1025)
+        A, B = C1 * (1000 - alpha), C1 * alpha
+        assert oracle.wcet(A, B, k, m) == refs.wcet_alpha(C1, alpha, k, m)
+
+
+def test_wcet_paper_form_matches_rational_closed_form():
+    rng = random.Random(2)
+    for _ in range(3000):
+        a = rng.randrange(1, 1 << 25)
+        beta = rng.choice([20, 100])
+        k = rng.choice([1000, 1200, 2300])
+        m = rng.randrange(1, 69)
+        assert oracle.wcet(1000 * a, beta * a, k, m) == refs.wcet_paper(a, beta, k, m)
+
+
+def test_wcet_properties():
+    """No timing anomaly (§4.1): non-increasing in m; m C^n(m) >= C^n(1)
+    (Lemma 1's basis); inflation never shrinks the WCET; C(1) = C1 in the
+    serial-fraction form."""
+    rng = random.Random(3)
+    for _ in range(300):
+        C1 = rng.randrange(1, 1 << 22)
+        alpha = rng.randrange(0, 1001)
+        A, B = C1 * (1000 - alpha), C1 * alpha
+        prev = None
+        c1 = oracle.wcet(A, B, 1000, 1)
+        assert c1 == C1
+        for m in range(1, 150, 7):
+            c = oracle.wcet(A, B, 1000, m)
+            assert m * c >= c1
+            assert oracle.wcet(A, B, 2300, m) >= oracle.wcet(A, B, 1200, m) >= c
+            if prev is not None:
+                assert c <= prev
+            prev = c
+
+
+def test_wcet_tables_layout():
+    s = gen_tasksets(seed=11, nsets=5, n_min=0, n_max=7)
+    Cn, Cc = oracle.wcet_tables(s, 12, 3, KC, KM)
+    off = s["set_off"]
+    Mu = 4
+    for si in range(5):
+        o, n = off[si], off[si + 1] - off[si]
+        for mi in range(Mu):
+            for t in range(n):
+                m = 3 * (mi + 1)
+                k = KM if s["type"][o + t] else KC
+                assert Cn[o * Mu + mi * n + t] == refs.wcet_alpha(s["C1"][o + t], s["alpha_pm"][o + t], 1000, m)
+                assert Cc[o * Mu + mi * n + t] == refs.wcet_alpha(s["C1"][o + t], s["alpha_pm"][o + t], k, m)
+
+
+# ------------------------------------------------- per-partition test (§5.6)
+
+def _no_inflation_set(rng, n, periods):
+    T = np.array([rng.choice(periods) for _ in range(n)], np.int64)
+    D = np.array([rng.randrange(max(1, t // 2), t + 1) for t in T], np.int64)
+    C = np.array([rng.randrange(1, max(2, t // 3)) for t in T], np.int64)
+    return T, D, C
+
+
+def test_rta_matches_fixed_priority_simulation():
+    """Response times equal the first job's completion in a unit-step FP
+    schedule with synchronous release; misses match; for tasks that meet
+    their deadline every job in the hyperperiod responds within R."""
+    rng = random.Random(4)
+    periods = [4, 5, 6, 8, 10, 12, 15, 20, 24, 30]
+    checked_miss = checked_ok = 0
+    for trial in range(400):
+        n = rng.randrange(1, 6)
+        T, D, C = _no_inflation_set(rng, n, periods)
+        # A = 1000 C, B = 0 -> C^n(1) = C; k = 1000 everywhere: no inflation
+        A, B = 1000 * C, np.zeros(n, np.int64)
+        typ = np.array([i % 2 for i in range(n)], np.uint8)
+        v, R = oracle.rta(T, D, A, B, typ, np.ones(n, np.uint8), 1, 1000, 1000)
+        order = refs.dm_order(T, D, range(n))
+        H = 1
+        for t in T:
+            H = H * int(t) // math.gcd(H, int(t))
+        first, worst = refs.simulate_fp([(int(T[i]), int(D[i]), int(C[i])) for i in order], H + int(D.max()) + 1)
+        for rank, i in enumerate(order):
+            if R[i] >= 0:
+                checked_ok += 1
+                assert first[rank] == R[i], (trial, i)
+                assert worst[rank] <= R[i]
+                assert R[i] <= D[i]
+            else:
+                checked_miss += 1
+                assert first[rank] is None or first[rank] > D[i], (trial, i)
+        assert v == int((R >= 0).all())
+    assert checked_ok > 200 and checked_miss > 50
+
+
+def test_rta_harmonic_rm_utilisation_bound():
+    """Harmonic periods, implicit deadlines (RM = DM): schedulable iff U <= 1."""
+    rng = random.Random(5)
+    for trial in range(300):
+        n = rng.randrange(1, 7)
+        base = rng.choice([1, 2, 3, 5])
+        T = np.array([base * 2 ** rng.randrange(0, 6) for _ in range(n)], np.int64)
+        C = np.array([rng.randrange(1, int(t) + 1) for t in T], np.int64)
+        U = sum(__import__("fractions").Fraction(int(c), int(t)) for c, t in zip(C, T))
+        v, _ = oracle.rta(T, T.copy(), 1000 * C, np.zeros(n, np.int64), np.zeros(n, np.uint8),
+                          np.ones(n, np.uint8), 1, 1000, 1000)
+        assert v == int(U <= 1), (trial, U)
+
+
+def test_rta_single_task_is_its_wcet():
+    rng = random.Random(6)
+    for _ in range(200):
+        C1 = rng.randrange(1, 10**6)
+        alpha = rng.randrange(0, 1001)
+        T = rng.randrange(1, 2**31 - 1)
+        m = rng.randrange(1, 200)
+        c = refs.wcet_alpha(C1, alpha, 1000, m)
+        v, R = oracle.rta(np.array([T]), np.array([T]), np.array([C1 * (1000 - alpha)]), np.array([C1 * alpha]),
+                          np.zeros(1, np.uint8), np.ones(1, np.uint8), m, KC, KM)
+        assert (R[0] == c) if c <= T else (R[0] == -1)
+        assert v == int(c <= T)
+
+
+def test_rta_monotone_in_m_and_in_tasks():
+    """No timing anomalies: passing at m implies passing at every m' > m;
+    removing a task never breaks a passing partition."""
+    s = gen_tasksets(seed=7, nsets=60, n_min=2, n_max=7, U_lo_ppm=300000, U_hi_ppm=3000000, deadline_pm=750)
+    off = s["set_off"]
+    for si in range(60):
+        o, e = off[si], off[si + 1]
+        args = [s[k][o:e] for k in ("T", "D", "A", "B", "type")]
+        n = e - o
+        allin = np.ones(n, np.uint8)
+        res = [oracle.rta(*args, allin, m, KC, KM)[0] for m in range(1, 40)]
+        assert all(res[j] <= res[j + 1] for j in range(len(res) - 1))
+        for m in (1, 4, 16, 39):
+            if oracle.rta(*args, allin, m, KC, KM)[0]:
+                for drop in range(n):
+                    sub = allin.copy()
+                    sub[drop] = 0
+                    assert oracle.rta(*args, sub, m, KC, KM)[0] == 1
+
+
+# ------------------------------------------------------------------- Lemmas
+
+def test_lemma2_singleton_size_closed_form():
+    """Lemma 2: smallest m with C^n(m) <= D; checked against the algebraic
+    form A <= m (1000 D - B) rounded up to the unit g."""
+    rng = random.Random(8)
+    for _ in range(1500):
+        C1 = rng.randrange(1, 10**6)
+        alpha = rng.randrange(0, 1001)
+        T = rng.randrange(1, 10**6)
+        D = rng.randrange(1, T + 1)
+        g = rng.choice([1, 2, 4])
+        M = g * rng.randrange(1, 100)
+        A, B = C1 * (1000 - alpha), C1 * alpha
+        den = 1000 * D - B
+        if den < 0 or (den == 0 and A > 0):
+            expect = 0
+        else:
+            m1 = 1 if A == 0 else max(1, -(-A // den))
+            mg = -(-m1 // g) * g
+            expect = mg if mg <= M else 0
+        got = oracle.minm([T], [D], [A], [B], [0], [1], g, M, g, KC, KM, linear=True)
+        assert got == expect
+
+
+def test_merge_search_linear_equals_binary():
+    """Alg. 2's linear scan and the §5.3 binary search give the same size."""
+    s = gen_tasksets(seed=9, nsets=80, n_min=2, n_max=8, U_lo_ppm=500000, U_hi_ppm=6000000, deadline_pm=750)
+    off = s["set_off"]
+    rng = random.Random(9)
+    for si in range(80):
+        o, e = off[si], off[si + 1]
+        n = e - o
+        args = [s[k][o:e] for k in ("T", "D", "A", "B", "type")]
+        for _ in range(5):
+            mask = np.array([rng.random() < 0.6 for _ in range(n)], np.uint8)
+            if not mask.any():
+                continue
+            g = rng.choice([1, 2])
+            lo = g * rng.randrange(1, 10)
+            hi = lo + g * rng.randrange(0, 30)
+            a = oracle.minm(*args, mask, lo, hi, g, KC, KM, linear=True)
+            b = oracle.minm(*args, mask, lo, hi, g, KC, KM, linear=False)
+            assert a == b
+            if a:
+                assert oracle.rta(*args, mask, a, KC, KM)[0] == 1
+                if a > lo:
+                    assert oracle.rta(*args, mask, a - g, KC, KM)[0] == 0
+
+
+def test_lemma1_utilisation_bound():
+    rng = random.Random(10)
+    for _ in range(500):
+        n = rng.randrange(1, 6)
+        T = [rng.randrange(10, 1000) for _ in range(n)]
+        C1 = [rng.randrange(1, 3000) for _ in range(n)]
+        M = rng.randrange(1, 8)
+        A = [1000 * c for c in C1]
+        B = [0] * n
+        expect = sum(10**6 * c // t for c, t in zip(C1, T)) > 10**6 * M
+        assert oracle.lemma1_rejects(T, A, B, M) == expect
+
+
+# ------------------------------------------------------ heuristic (Alg. 1-3)
+
+def _set_view(s, si):
+    o, e = s["set_off"][si], s["set_off"][si + 1]
+    return {k: s[k][o:e] for k in ("T", "D", "A", "B", "u_ppm", "type")}, o, e - o
+
+
+def _partitions_from(r, si, o, n):
+    parts = {}
+    for t in range(n):
+        parts.setdefault(int(r["part_of_task"][o + t]), set()).add(t)
+    sizes = [int(r["size_of_part"][o + p]) for p in range(r["n_parts"][si])]
+    return parts, sizes
+
+
+@pytest.mark.parametrize("policy,act", [("SMS", False), ("SMS", True), ("BF", False), ("BF", True)])
+def test_heuristic_matches_independent_restatement(policy, act):
+    """Alg. 1-3 restated over Python sets reaches the same final partitions,
+    the same verdict and the same number of merge evaluations."""
+    M, g = 12, 1
+    s = gen_tasksets(seed=12, nsets=50, n_min=3, n_max=9, U_lo_ppm=1000000, U_hi_ppm=12000000, deadline_pm=750,
+                     T_lo=50, T_hi=4000, T_dist="LIST", mode="PAPER")
+    r = oracle.allocate(s, M, g, KC, KM, policy=policy, act=act)
+    seen_merges = 0
+    for si in range(50):
+        v, o, n = _set_view(s, si)
+        if oracle.lemma1_rejects(v["T"], v["A"], v["B"], M):
+            assert r["reason"][si] == oracle.REASON["LEMMA1"]
+            continue
+
+        def single(i):
+            return oracle.minm(v["T"], v["D"], v["A"], v["B"], v["type"], np.eye(n, dtype=np.uint8)[i], g, M, g,
+                               KC, KM)
+
+        def test_min(S, lo, hi):
+            mask = np.array([i in S for i in range(n)], np.uint8)
+            return oracle.minm(v["T"], v["D"], v["A"], v["B"], v["type"], mask, lo, hi, g, KC, KM)
+
+        def W(S):
+            return sum(refs.conflict_k(v["type"], S, i, KC, KM) * int(v["u_ppm"][i]) for i in S)
+
+        status, parts, tests = refs.heuristic(n, [int(x) for x in v["u_ppm"]], M, g, single, test_min,
+                                              policy=policy, act=act, W=W)
+        assert oracle.REASON[status] == r["reason"][si], si
+        assert tests == r["n_tests"][si], si
+        if status == "LEMMA2":
+            continue
+        seen_merges += tests
+        got, sizes = _partitions_from(r, si, o, n)
+        want = sorted((sorted(P), z) for P, z in parts.items())
+        have = sorted((sorted(got[p]), sizes[p]) for p in got)
+        assert want == have, si
+        assert r["Pi"][si] == sum(parts.values())
+        assert r["W"][si] == sum(W(P) for P in parts)
+    assert seen_merges > 50
+
+
+def test_heuristic_invariants_paper_workload():
+    """On the paper's setting: success => Lemma 3 (Pi <= M), every partition
+    passes at its size, that size is its minimum (a merge never lands above
+    the smallest passing size), partitions cover every task exactly once,
+    and Lemma 1 passes."""
+    p = workloads.gen_params("paper50", nsets=68)
+    s = gen_tasksets(**p)
+    md = workloads.model("paper50")
+    r = oracle.allocate(s, md["M"], md["g"], KC, KM, policy="SMS", act=False, nthreads=4)
+    n_ok = 0
+    for si in range(68):
+        v, o, n = _set_view(s, si)
+        if r["reason"][si] in (oracle.REASON["LEMMA1"], oracle.REASON["LEMMA2"]):
+            continue
+        parts, sizes = _partitions_from(r, si, o, n)
+        assert sorted(t for P in parts.values() for t in P) == list(range(n))
+        assert sum(sizes) == r["Pi"][si]
+        for p_, P in parts.items():
+            mask = np.array([i in P for i in range(n)], np.uint8)
+            z = sizes[p_]
+            assert z >= 1 and oracle.rta(v["T"], v["D"], v["A"], v["B"], v["type"], mask, z, KC, KM)[0] == 1
+            assert oracle.minm(v["T"], v["D"], v["A"], v["B"], v["type"], mask, 1, md["M"], 1, KC, KM) == z
+        if r["verdict"][si]:
+            n_ok += 1
+            assert r["Pi"][si] <= md["M"]
+            assert not oracle.lemma1_rejects(v["T"], v["A"], v["B"], md["M"])
+        else:
+            assert r["Pi"][si] > md["M"]
+    assert n_ok > 10
+
+
+def test_one_gpu_is_the_whole_set_at_M():
+    s = gen_tasksets(seed=13, nsets=40, n_min=1, n_max=20, U_lo_ppm=100000, U_hi_ppm=6000000, deadline_pm=750,
+                     mu_dist="BETA25")
+    M = 148
+    r = oracle.allocate(s, M, 1, KC, KM, policy="ONE_GPU")
+    for si in range(40):
+        v, o, n = _set_view(s, si)
+        ok, _ = oracle.rta(v["T"], v["D"], v["A"], v["B"], v["type"], np.ones(n, np.uint8), M, KC, KM)
+        assert r["verdict"][si] == ok
+        assert r["n_parts"][si] == 1 and r["Pi"][si] == M
+
+
+# ------------------------------------------------------- exhaustive optimum
+
+def test_exhaustive_explicit_equals_subset_form_and_bruteforce():
+    rng = random.Random(14)
+    for trial in range(25):
+        n = rng.randrange(1, 6)
+        g = rng.choice([1, 2])
+        M = g * rng.randrange(2, 5)
+        kmin = rng.randrange(1, 3)
+        kmax = rng.randrange(kmin, 4)
+        s = gen_tasksets(seed=100 + trial, nsets=1, n_min=n, n_max=n, U_lo_ppm=300000, U_hi_ppm=2500000,
+                         deadline_pm=750, T_lo=1000, T_hi=100000)
+        a = oracle.search_best(s, M, g, KC, KM, kmin, kmax, explicit=False)
+        b = oracle.search_best(s, M, g, KC, KM, kmin, kmax, explicit=True)
+        for k in ("feasible", "W", "sum_minm", "n_blocks", "spare", "rgs", "minm_block"):
+            assert np.array_equal(a[k], b[k]), (trial, k)
+        v, o, _ = _set_view(s, 0)
+
+        def passes(S, m):
+            mask = np.array([i in S for i in range(n)], np.uint8)
+            return oracle.rta(v["T"], v["D"], v["A"], v["B"], v["type"], mask, m, KC, KM)[0] == 1
+
+        def minsize(S):
+            for m in range(g, M + 1, g):
+                if passes(S, m):
+                    return m
+            return 0
+
+        def W(S):
+            return sum(refs.conflict_k(v["type"], S, i, KC, KM) * int(v["u_ppm"][i]) for i in S)
+
+        best = refs.exhaustive_bruteforce(n, M, g, kmin, kmax, passes, minsize, W)
+        assert bool(a["feasible"][0]) == (best is not None)
+        if best is not None:
+            assert (a["W"][0], a["sum_minm"][0], tuple(a["rgs"][:n])) == best
+
+
+def test_explicit_candidate_count_single_workload():
+    """7 SM splits x 2^8 maps = 1 792 explicit candidates for one 8-task set on
+    8 SMs in exactly 2 partitions."""
+    s = gen_tasksets(**workloads.gen_params("single"))
+    r = oracle.search_best(s, 8, 1, KC, KM, 2, 2, explicit=True)
+    assert r["candidates"] == math.comb(7, 1) * 2**8 == 1792
+
+
+def test_exhaustive_removal_never_breaks_feasibility():
+    s = gen_tasksets(seed=15, nsets=30, n_min=2, n_max=7, U_lo_ppm=500000, U_hi_ppm=4000000, deadline_pm=750,
+                     T_lo=1000, T_hi=100000)
+    M, g, kmin, kmax = 12, 2, 1, 3
+    full = oracle.search_best(s, M, g, KC, KM, kmin, kmax)
+    off = s["set_off"]
+    for si in range(30):
+        if not full["feasible"][si]:
+            continue
+        o, e = off[si], off[si + 1]
+        for drop in range(e - o):
+            keep = [t for t in range(o, e) if t != o + drop]
+            sub = {k: s[k][keep] for k in ("T", "D", "A", "B", "u_ppm", "type")}
+            sub["set_off"] = np.array([0, len(keep)], np.int64)
+            r = oracle.search_best(sub, M, g, KC, KM, kmin, kmax)
+            assert r["feasible"][0] == 1
+
+
+def test_heuristic_success_implies_exhaustive_feasible_and_not_better():
+    s = gen_tasksets(seed=16, nsets=60, n_min=2, n_max=8, U_lo_ppm=500000, U_hi_ppm=5000000, deadline_pm=750,
+                     T_lo=1000, T_hi=100000)
+    M, g = 16, 2
+    h = oracle.allocate(s, M, g, KC, KM, policy="SMS")
+    e = oracle.search_best(s, M, g, KC, KM, 1, 8)
+    checked = 0
+    for si in range(60):
+        if h["verdict"][si]:
+            assert e["feasible"][si] == 1
+            assert e["W"][si] <= h["W"][si]
+            checked += 1
+    assert checked > 20
+
+
+def test_rgs_and_composition_counts():
+    """Stirling numbers of the second kind (recurrence) and binomials."""
+    def stirling(n, k):
+        S = [[0] * (k + 1) for _ in range(n + 1)]
+        S[0][0] = 1
+        for i in range(1, n + 1):
+            for j in range(1, k + 1):
+                S[i][j] = j * S[i - 1][j] + S[i - 1][j - 1]
+        return S[n][k]
+    assert sum(stirling(12, k) for k in range(1, 5)) == 700075
+    total = sum(math.comb(19, k - 1) * k**12 for k in range(1, 5))
+    assert total == 16348076540  # explicit (split x map) candidates per 12-task set on 20 units
+    assert [len(list(refs.compositions(8, 2)))] == [7]
