@@ -1,0 +1,330 @@
+"""GB300-native contention-aware GPU-partition schedulability (arXiv 2105.10312).
+
+A thin ctypes binding over ``libgpa.so`` (the C ABI declared in ``include/gpa.h``).
+Every step of the computation runs in the library's CUDA kernels; this module
+only marshals arguments: torch CUDA tensors go in as device pointers (GPA_DEVICE),
+numpy arrays as host pointers (GPA_HOST, validated on the host, synchronous).
+
+The first call into the library raises ImportError if ``libgpa.so`` has not
+been built (``python -c "import __graft_entry__ as g; g.build()"``): there is
+no CPU fallback.  The generator (``gen``) and the workload presets need no GPU.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import gen as _gen
+from .gen import gen_tasksets  # noqa: F401  (re-export)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgpa.so")
+
+# --- constants mirrored from gpa.h -------------------------------------------
+OK, ERR_ARG, ERR_RANGE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_NOTFOUND = 0, -1, -2, -3, -4, -5, -6, -7
+HOST, DEVICE = 0, 1
+POLICY = {"SMS": 0, "BF": 1, "ONE_GPU": 2}
+REASON = {"OK": 0, "LEMMA1": 1, "LEMMA2": 2, "NO_MERGE": 3, "TEST": 4, "INVALID": 5}
+OPT = {"AUTOTUNE": 1, "GRAPH": 2, "FAST_WARPS": 3, "FAST_CHUNK": 4, "FAST_BLOCKS": 5, "PER_SET_LAUNCH": 6}
+NMAX, MMAX, SEARCH_NMAX, SEARCH_KMAX = 128, 1024, 14, 8
+
+_vp = ctypes.c_void_p
+
+
+class GpaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"gpa error {code}: {msg}")
+        self.code = code
+
+
+def _check(code):
+    if code != OK:
+        buf = ctypes.create_string_buffer(512)
+        lib().gpa_last_error(buf, 512)
+        raise GpaError(code, buf.value.decode(errors="replace"))
+
+
+class Tasksets(ctypes.Structure):
+    _fields_ = [("nsets", ctypes.c_int64), ("mem", ctypes.c_int32), ("n_max", ctypes.c_int32),
+                ("set_off", _vp), ("T", _vp), ("D", _vp), ("A", _vp), ("B", _vp), ("u_ppm", _vp), ("type", _vp)]
+
+
+class Model(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int32), ("g", ctypes.c_int32), ("k_c_pm", ctypes.c_int32), ("k_m_pm", ctypes.c_int32)]
+
+
+class Candidates(ctypes.Structure):
+    _fields_ = [("ncands", ctypes.c_int64), ("mem", ctypes.c_int32), ("map_stride", ctypes.c_int32),
+                ("kparts", ctypes.c_int32), ("pad_", ctypes.c_int32), ("set", _vp), ("part_of_task", _vp),
+                ("size_of_part", _vp)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("policy", ctypes.c_int32), ("act", ctypes.c_int32), ("linear_merge", ctypes.c_int32),
+                ("pad_", ctypes.c_int32)]
+
+
+class AllocResult(ctypes.Structure):
+    _fields_ = [("mem", ctypes.c_int32), ("pad_", ctypes.c_int32), ("verdict", _vp), ("reason", _vp),
+                ("n_parts", _vp), ("Pi", _vp), ("W", _vp), ("n_tests", _vp), ("part_of_task", _vp),
+                ("size_of_part", _vp)]
+
+
+class BestResult(ctypes.Structure):
+    _fields_ = [("mem", ctypes.c_int32), ("pad_", ctypes.c_int32), ("feasible", _vp), ("W", _vp),
+                ("sum_minm", _vp), ("n_blocks", _vp), ("spare", _vp), ("rgs", _vp), ("minm_block", _vp)]
+
+
+_lib = None
+
+
+def _set_signatures(L):
+    L.gpa_ctx_create.argtypes = [ctypes.c_int32, _vp, ctypes.POINTER(_vp)]
+    L.gpa_ctx_destroy.argtypes = [_vp]
+    L.gpa_ctx_set_stream.argtypes = [_vp, _vp]
+    L.gpa_ctx_sync.argtypes = [_vp]
+    L.gpa_ctx_launch_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
+    L.gpa_ctx_set_option.argtypes = [_vp, ctypes.c_int32, ctypes.c_int64]
+    L.gpa_last_error.argtypes = [ctypes.c_char_p, ctypes.c_int32]
+    L.gpa_validate.argtypes = [ctypes.POINTER(Tasksets), ctypes.POINTER(Model), ctypes.POINTER(ctypes.c_int64)]
+    L.gpa_build_wcet_tables.argtypes = [_vp, ctypes.POINTER(Tasksets), ctypes.POINTER(Model), _vp, _vp]
+    L.gpa_test_schedulable.argtypes = [_vp, ctypes.POINTER(Tasksets), ctypes.POINTER(Model),
+                                          ctypes.POINTER(Candidates), _vp, _vp]
+    L.gpa_allocate.argtypes = [_vp, ctypes.POINTER(Tasksets), ctypes.POINTER(Model), ctypes.POINTER(Params),
+                                  ctypes.POINTER(AllocResult)]
+    L.gpa_search_best.argtypes = [_vp, ctypes.POINTER(Tasksets), ctypes.POINTER(Model), ctypes.c_int32,
+                                     ctypes.c_int32, ctypes.POINTER(BestResult)]
+    L.gpa_enumerate_partitions.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_uint64)]
+    L.gpa_unrank_composition.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _vp]
+    L.gpa_count_rgs.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64)]
+    L.gpa_unrank_rgs.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _vp]
+
+
+def lib():
+    """The loaded libgpa.so; raises ImportError if the CUDA extension was not built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                f"{LIB_PATH} is missing: build the CUDA extension first "
+                "(python -c 'import __graft_entry__ as g; g.build()'); there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        _set_signatures(L)
+        _lib = L
+    return _lib
+
+
+# --- array helpers --------------------------------------------------------------
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _mem_of(x):
+    if _is_torch(x):
+        return DEVICE if x.is_cuda else HOST
+    return HOST
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_torch(x):
+        assert x.is_contiguous(), "tensors must be contiguous"
+        return x.data_ptr()
+    assert isinstance(x, np.ndarray) and x.flags["C_CONTIGUOUS"], "numpy arrays must be C-contiguous"
+    return x.ctypes.data
+
+
+def _empty_like_mem(mem, n, np_dtype, device=None):
+    if mem == DEVICE:
+        import torch
+        tdt = {np.uint8: torch.uint8, np.int16: torch.int16, np.int32: torch.int32, np.int64: torch.int64}[np_dtype]
+        return torch.empty(max(n, 0), dtype=tdt, device=device)
+    return np.zeros(max(n, 0), dtype=np_dtype)
+
+
+def _len(x):
+    return int(x.numel()) if _is_torch(x) else int(x.size)
+
+
+def make_tasksets(sets, n_max=None):
+    """Build the gpa_tasksets view over a dict of arrays (all numpy or all CUDA tensors)."""
+    mem = _mem_of(sets["set_off"])
+    nsets = _len(sets["set_off"]) - 1
+    if n_max is None:
+        n_max = int(sets.get("n_max", NMAX))
+    ts = Tasksets(nsets, mem, int(n_max), _ptr(sets["set_off"]), _ptr(sets["T"]), _ptr(sets["D"]),
+                  _ptr(sets["A"]), _ptr(sets["B"]), _ptr(sets.get("u_ppm")), _ptr(sets["type"]))
+    return ts, mem
+
+
+def validate(sets, M=None, g=1, k_c_pm=1200, k_m_pm=2300):
+    ts, mem = make_tasksets(sets)
+    md = Model(M, g, k_c_pm, k_m_pm) if M is not None else None
+    bad = ctypes.c_int64(-1)
+    code = lib().gpa_validate(ctypes.byref(ts), ctypes.byref(md) if md is not None else None, ctypes.byref(bad))
+    return code, bad.value
+
+
+def enumerate_partitions(Mu, kmin, kmax):
+    out = ctypes.c_uint64()
+    _check(lib().gpa_enumerate_partitions(Mu, kmin, kmax, ctypes.byref(out)))
+    return out.value
+
+
+def unrank_composition(Mu, k, rank):
+    parts = np.zeros(k, dtype=np.int32)
+    _check(lib().gpa_unrank_composition(Mu, k, ctypes.c_uint64(rank), parts.ctypes.data))
+    return parts
+
+
+def count_rgs(n, kmax):
+    out = ctypes.c_uint64()
+    _check(lib().gpa_count_rgs(n, kmax, ctypes.byref(out)))
+    return out.value
+
+
+def unrank_rgs(n, kmax, rank):
+    rgs = np.zeros(max(n, 1), dtype=np.uint8)
+    _check(lib().gpa_unrank_rgs(n, kmax, ctypes.c_uint64(rank), rgs.ctypes.data))
+    return rgs[:n]
+
+
+class Context:
+    """A gpa_ctx bound to one CUDA device and stream (default: torch's current stream)."""
+
+    def __init__(self, device=0, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self._stream = stream
+        h = _vp()
+        _check(lib().gpa_ctx_create(device, _vp(stream.cuda_stream), ctypes.byref(h)))
+        self._h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gpa_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self._stream = stream
+        _check(lib().gpa_ctx_set_stream(self._h, _vp(stream.cuda_stream)))
+
+    def set_option(self, name, value):
+        _check(lib().gpa_ctx_set_option(self._h, OPT[name], int(value)))
+
+    def sync(self):
+        _check(lib().gpa_ctx_sync(self._h))
+
+    def launch_count(self):
+        out = ctypes.c_int64()
+        _check(lib().gpa_ctx_launch_count(self._h, ctypes.byref(out)))
+        return out.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    # --- entry points ----------------------------------------------------------
+
+    def build_wcet_tables(self, sets, M, g=1, k_c_pm=1200, k_m_pm=2300, out=None):
+        ts, mem = make_tasksets(sets)
+        md = Model(M, g, k_c_pm, k_m_pm)
+        ntasks = int(sets["set_off"][-1])
+        size = ntasks * (M // g)
+        dev = sets["T"].device if mem == DEVICE else None
+        Cn = out[0] if out else _empty_like_mem(mem, size, np.int64, dev)
+        Cc = out[1] if out else _empty_like_mem(mem, size, np.int64, dev)
+        _check(lib().gpa_build_wcet_tables(self._h, ctypes.byref(ts), ctypes.byref(md), _ptr(Cn), _ptr(Cc)))
+        return Cn, Cc
+
+    def test_schedulable(self, sets, M, cand_set, part_of_task, size_of_part, map_stride, kparts, g=1,
+                         k_c_pm=1200, k_m_pm=2300, with_R=True):
+        ts, mem = make_tasksets(sets)
+        md = Model(M, g, k_c_pm, k_m_pm)
+        nc = _len(cand_set)
+        cands = Candidates(nc, mem, int(map_stride), int(kparts), 0, _ptr(cand_set), _ptr(part_of_task),
+                           _ptr(size_of_part))
+        dev = sets["T"].device if mem == DEVICE else None
+        verdict = _empty_like_mem(mem, nc, np.uint8, dev)
+        R = _empty_like_mem(mem, nc * map_stride, np.int64, dev) if with_R else None
+        _check(lib().gpa_test_schedulable(self._h, ctypes.byref(ts), ctypes.byref(md), ctypes.byref(cands),
+                                         _ptr(verdict), _ptr(R)))
+        return verdict, R
+
+    def alloc_result(self, sets, with_tests=True):
+        mem = _mem_of(sets["set_off"])
+        nsets = _len(sets["set_off"]) - 1
+        ntasks = int(sets["set_off"][-1])
+        dev = sets["T"].device if mem == DEVICE else None
+        return {
+            "verdict": _empty_like_mem(mem, nsets, np.uint8, dev),
+            "reason": _empty_like_mem(mem, nsets, np.uint8, dev),
+            "n_parts": _empty_like_mem(mem, nsets, np.int32, dev),
+            "Pi": _empty_like_mem(mem, nsets, np.int32, dev),
+            "W": _empty_like_mem(mem, nsets, np.int64, dev),
+            "n_tests": _empty_like_mem(mem, nsets, np.int32, dev) if with_tests else None,
+            "part_of_task": _empty_like_mem(mem, ntasks, np.uint8, dev),
+            "size_of_part": _empty_like_mem(mem, ntasks, np.int16, dev),
+        }
+
+    def allocate(self, sets, M, g=1, k_c_pm=1200, k_m_pm=2300, policy="SMS", act=False, linear=True, out=None):
+        ts, mem = make_tasksets(sets)
+        md = Model(M, g, k_c_pm, k_m_pm)
+        pr = Params(POLICY[policy], 1 if act else 0, 1 if linear else 0, 0)
+        if out is None:
+            out = self.alloc_result(sets)
+        res = AllocResult(mem, 0, _ptr(out["verdict"]), _ptr(out["reason"]), _ptr(out["n_parts"]),
+                          _ptr(out["Pi"]), _ptr(out["W"]), _ptr(out.get("n_tests")), _ptr(out["part_of_task"]),
+                          _ptr(out["size_of_part"]))
+        _check(lib().gpa_allocate(self._h, ctypes.byref(ts), ctypes.byref(md), ctypes.byref(pr), ctypes.byref(res)))
+        return out
+
+    def best_result(self, sets, kmax):
+        mem = _mem_of(sets["set_off"])
+        nsets = _len(sets["set_off"]) - 1
+        ntasks = int(sets["set_off"][-1])
+        dev = sets["T"].device if mem == DEVICE else None
+        return {
+            "feasible": _empty_like_mem(mem, nsets, np.uint8, dev),
+            "W": _empty_like_mem(mem, nsets, np.int64, dev),
+            "sum_minm": _empty_like_mem(mem, nsets, np.int32, dev),
+            "n_blocks": _empty_like_mem(mem, nsets, np.int32, dev),
+            "spare": _empty_like_mem(mem, nsets, np.int32, dev),
+            "rgs": _empty_like_mem(mem, ntasks, np.uint8, dev),
+            "minm_block": _empty_like_mem(mem, nsets * kmax, np.int16, dev),
+        }
+
+    def search_best(self, sets, M, g=1, k_c_pm=1200, k_m_pm=2300, kmin=1, kmax=4, out=None):
+        ts, mem = make_tasksets(sets)
+        md = Model(M, g, k_c_pm, k_m_pm)
+        if out is None:
+            out = self.best_result(sets, kmax)
+        res = BestResult(mem, 0, _ptr(out["feasible"]), _ptr(out["W"]), _ptr(out["sum_minm"]),
+                         _ptr(out["n_blocks"]), _ptr(out["spare"]), _ptr(out["rgs"]), _ptr(out["minm_block"]))
+        _check(lib().gpa_search_best(self._h, ctypes.byref(ts), ctypes.byref(md), kmin, kmax, ctypes.byref(res)))
+        return out
+
+
+def to_device(sets, device="cuda"):
+    """Copy a numpy task batch to CUDA tensors (plumbing for callers and tests)."""
+    import torch
+    out = {}
+    for k, v in sets.items():
+        if isinstance(v, np.ndarray):
+            out[k] = torch.from_numpy(np.ascontiguousarray(v)).to(device)
+        else:
+            out[k] = v
+    return out

@@ -1,0 +1,51 @@
+// gpa_ctx.h — the library-owned context behind gpa_ctx* (host side only).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "gpa.h"
+#include "gpa_internal.h"
+
+struct CtxBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+struct CachedGraph {
+  cudaGraphExec_t exec;
+  long long kernels;  // kernel nodes in the graph
+};
+
+struct ServeState;
+
+struct gpa_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int sm_count = 0;
+  gpa::MagicDivHost* d_mdiv = nullptr;      // [GPA_MMAX + 1] reciprocals of 10^6 m
+  unsigned long long* d_counters = nullptr; // [8] work-queue tickets
+  unsigned int* d_err = nullptr;            // sticky error word
+  long long* d_slow = nullptr;              // deferred-set queue of the allocate kernels
+  long long slow_cap = 0;
+  std::vector<CtxBuf> bufs;                 // host-path staging, by slot
+  long long launches = 0;                   // kernels launched through this context
+  bool autotune = false;
+  bool use_graph = false;
+  bool per_set_launch = false;
+  bool graphs_dirty = false;
+  gpa::LaunchShape force_fast{0, 0, 0};
+  std::map<std::string, gpa::LaunchShape> tuned;
+  std::map<std::string, CachedGraph> graphs;
+  ServeState* serve = nullptr;
+};
+
+int32_t gpa_fail(int32_t code, const char* fmt, ...);
+int32_t gpa_cuda_fail(cudaError_t e, const char* what);
+void* ctx_buffer(gpa_ctx* c, int slot, size_t bytes);
+std::string tune_key(const gpa::DevSets& ds, const gpa::DevModel& md, const gpa_params& p);
+void gpa_serve_teardown(gpa_ctx* c);

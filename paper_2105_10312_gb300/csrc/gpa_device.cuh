@@ -1,0 +1,344 @@
+// gpa_device.cuh — device building blocks shared by the libgpa kernels.
+//
+//  * exact integer division by invariant divisors (Granlund & Montgomery,
+//    "Division by invariant integers using multiplication", PLDI 1994,
+//    Theorem 4.2), used for ceil(R / T_j) in the response-time iteration and
+//    for the WCET's division by 10^6 m;
+//  * staging of one task set from the caller's int64 structure-of-arrays
+//    into shared memory in deadline-monotonic order;
+//  * the WCET of §3.3/§7.1, C = ceil(k (A + B m) / (10^6 m)), with
+//    the conflict rule of §4.2;
+//  * the warp-cooperative per-partition response-time test of §5.6
+//    and the minimum-size search of Alg. 2.
+#pragma once
+
+#include <cstdint>
+
+#include "gpa.h"
+
+namespace gpa {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kNmax = GPA_NMAX;
+constexpr int kWords = kNmax / 32;        // 32-bit words of a task mask
+constexpr int kIterCap = 1 << 20;         // response-time iterations per task before GPA_ERR_TIMEOUT
+
+// error bits of the context's sticky error word
+constexpr unsigned kErrRange = 1u;        // a set failed device-side validation
+constexpr unsigned kErrIter = 2u;         // a response-time iteration hit kIterCap
+
+// floor(x / d) for 0 <= x < 2^60 and d = 10^6 m (m <= GPA_MMAX):
+// magic = ceil(2^(60+l) / d) with l = ceil(log2 d), then
+// floor(x / d) = floor(x * magic / 2^(60+l)) = umulhi64(x, magic) >> (l - 4).
+struct MagicDiv {
+  unsigned long long magic;
+  unsigned int shift;  // l - 4
+  unsigned int pad;
+};
+
+__device__ __forceinline__ unsigned long long div_by_1e6m(unsigned long long x, const MagicDiv& md) {
+  return __umul64hi(x, md.magic) >> md.shift;
+}
+
+// 32-bit divisor T (1 <= T < 2^31), dividend n < 2^31:
+// magic = ceil(2^(31+l) / T) < 2^32 with l = ceil(log2 T);
+// floor(n / T) = (n * magic) >> (31 + l).
+__device__ __forceinline__ void magic_for_period(unsigned int T, unsigned int* magic, unsigned int* shift) {
+  unsigned int l = (T <= 1u) ? 0u : 32u - __clz(T - 1u);
+  unsigned long long num = (1ull << (31 + l)) + T - 1;
+  *magic = (unsigned int)(num / T);
+  *shift = 31u + l;
+}
+
+// ceil(R / T) for 1 <= R < 2^31 as floor((R - 1) / T) + 1.
+__device__ __forceinline__ unsigned int ceil_div_T(unsigned int R, unsigned int magic, unsigned int shift) {
+  return (unsigned int)(((unsigned long long)(R - 1u) * magic) >> shift) + 1u;
+}
+
+// WCET at m SMs with factor k per mille: ceil(k (A + B m) / (10^6 m)).
+__device__ __forceinline__ unsigned int wcet(unsigned long long A, unsigned long long B, unsigned int k, unsigned int m,
+                                             const MagicDiv& md) {
+  unsigned long long x = (unsigned long long)k * (A + B * m);
+  return (unsigned int)(div_by_1e6m(x - 1ull, md) + 1ull);
+}
+
+// Validation bounds of gpa.h for one task.
+__device__ __forceinline__ bool task_valid(long long T, long long D, long long A, long long B, long long u,
+                                           unsigned int type) {
+  return D >= 1 && D <= T && T <= 2147483647LL && A >= 0 && B >= 0 && A + B >= 1 && A + B <= (1LL << 36) &&
+         u >= 0 && u <= 4294967295LL && type <= 1u;
+}
+
+// Lemma 2 in closed form: smallest multiple of g in [g, M] with
+// C^n(m) <= D, i.e. 1000 (A + B m) <= 10^6 D m  <=>  A <= m (1000 D - B).
+// Returns 0 when no size <= M qualifies.
+__device__ __forceinline__ unsigned int lemma2_size(unsigned long long A, unsigned long long B, unsigned long long D,
+                                                    unsigned int M, unsigned int g) {
+  long long den = (long long)(1000ull * D) - (long long)B;
+  if (den < 0) return 0u;
+  unsigned long long m1;
+  if (A == 0ull) m1 = 1ull;
+  else if (den == 0) return 0u;
+  else m1 = (A + (unsigned long long)den - 1ull) / (unsigned long long)den;
+  if (m1 < 1ull) m1 = 1ull;
+  unsigned long long mg = (m1 + g - 1ull) / g * g;
+  return mg <= M ? (unsigned int)mg : 0u;
+}
+
+// One task set staged in shared memory, rows in deadline-monotonic order
+// (D ascending, then T, then original index).
+struct SetSmem {
+  unsigned int T[kNmax];
+  unsigned int D[kNmax];
+  unsigned int mT[kNmax];    // Granlund-Montgomery magic of T
+  unsigned char shT[kNmax];  // its shift
+  unsigned char orig[kNmax]; // original index of the row's task
+  unsigned long long A[kNmax];
+  unsigned long long B[kNmax];
+  unsigned int u[kNmax];
+  unsigned int memmask[kWords];  // rows holding memory-intensive tasks
+  int n;
+};
+
+// Per-warp scratch of the response-time test: the partition's tasks,
+// compacted in priority order.
+struct RtaScratch {
+  unsigned int C[kNmax];
+  unsigned int T[kNmax];
+  unsigned int mT[kNmax];
+  unsigned int D[kNmax];
+  unsigned char sh[kNmax];
+  unsigned char pos[kNmax];
+};
+
+// Stage set [o, o + n) into st (warp-cooperative).  Returns false (on all
+// lanes) if any task violates the validation bounds.
+__device__ __forceinline__ bool stage_set(SetSmem& st, long long o, int n, const long long* __restrict__ T,
+                                          const long long* __restrict__ D, const long long* __restrict__ A,
+                                          const long long* __restrict__ B, const long long* __restrict__ u,
+                                          const unsigned char* __restrict__ type) {
+  const int lane = threadIdx.x & 31;
+  long long Tv[kWords], Dv[kWords];
+  unsigned int ty[kWords];
+  bool ok = true;
+  // first pass: load and validate; keep (D, T) for ranking
+  for (int c = 0; c < kWords; c++) {
+    int t = c * 32 + lane;
+    Tv[c] = 0;
+    Dv[c] = 0;
+    ty[c] = 0;
+    if (t < n) {
+      long long Tt = __ldg(T + o + t), Dt = __ldg(D + o + t), At = __ldg(A + o + t), Bt = __ldg(B + o + t);
+      long long ut = u ? __ldg(u + o + t) : 0;
+      unsigned int yt = __ldg(type + o + t);
+      ok = ok && task_valid(Tt, Dt, At, Bt, ut, yt);
+      Tv[c] = Tt;
+      Dv[c] = Dt;
+      ty[c] = yt;
+      // temporary: stash original-order values in the A/B/u rows of the
+      // original index; they are permuted below
+      st.A[t] = (unsigned long long)At;
+      st.B[t] = (unsigned long long)Bt;
+      st.u[t] = (unsigned int)ut;
+      st.T[t] = (unsigned int)Tt;
+      st.D[t] = (unsigned int)Dt;
+    }
+  }
+  ok = __all_sync(kFull, ok);
+  if (!ok) return false;
+  __syncwarp();
+  // DM rank of each task by counting (n <= 128)
+  int rank[kWords];
+  for (int c = 0; c < kWords; c++) {
+    int t = c * 32 + lane;
+    int r = 0;
+    if (t < n) {
+      unsigned long long key = ((unsigned long long)Dv[c] << 31) | (unsigned long long)Tv[c];
+      for (int j = 0; j < n; j++) {
+        unsigned long long kj = ((unsigned long long)st.D[j] << 31) | (unsigned long long)st.T[j];
+        r += (kj < key) || (kj == key && j < t);
+      }
+    }
+    rank[c] = r;
+  }
+  // gather original-order values into registers, then scatter by rank
+  unsigned long long Av[kWords], Bv[kWords];
+  unsigned int uv[kWords];
+  for (int c = 0; c < kWords; c++) {
+    int t = c * 32 + lane;
+    if (t < n) {
+      Av[c] = st.A[t];
+      Bv[c] = st.B[t];
+      uv[c] = st.u[t];
+    }
+  }
+  __syncwarp();
+  for (int w = 0; w < kWords; w++) st.memmask[w] = 0u;  // lanes write the same value
+  __syncwarp();
+  for (int c = 0; c < kWords; c++) {
+    int t = c * 32 + lane;
+    if (t < n) {
+      int r = rank[c];
+      st.T[r] = (unsigned int)Tv[c];
+      st.D[r] = (unsigned int)Dv[c];
+      unsigned int mg, sh;
+      magic_for_period((unsigned int)Tv[c], &mg, &sh);
+      st.mT[r] = mg;
+      st.shT[r] = (unsigned char)sh;
+      st.orig[r] = (unsigned char)t;
+      st.A[r] = Av[c];
+      st.B[r] = Bv[c];
+      st.u[r] = uv[c];
+    }
+  }
+  // memory mask by rank
+  for (int c = 0; c < kWords; c++) {
+    int t = c * 32 + lane;
+    bool mem = (t < n) && ty[c] == 1u;
+    int r = rank[c];
+    // each lane sets its bit with an atomic on shared memory
+    if (mem) atomicOr(&st.memmask[r >> 5], 1u << (r & 31));
+  }
+  if (lane == 0) st.n = n;
+  __syncwarp();
+  return true;
+}
+
+__device__ __forceinline__ int mask_popc(const unsigned int* S) {
+  int c = 0;
+#pragma unroll
+  for (int w = 0; w < kWords; w++) c += __popc(S[w]);
+  return c;
+}
+
+// Inflated workload W(S) = sum_{i in S} k_i(S) u_i from the per-type sums.
+__device__ __forceinline__ unsigned long long workload_from_sums(unsigned long long Uc, unsigned long long Um, int nc,
+                                                                 int nm, unsigned int kc, unsigned int km) {
+  return (unsigned long long)(nc >= 2 ? kc : 1000u) * Uc + (unsigned long long)(nm >= 2 ? km : 1000u) * Um;
+}
+
+// §5.6 per-partition test, warp-cooperative: the tasks of S (rows of st, a
+// mask in priority order) on one processor of m SMs.  Lane l owns the l-th,
+// (l+32)-th, ... task of S; its fixed point reads the higher-priority tasks
+// from the compacted scratch (broadcast shared-memory reads).
+// If R_row != nullptr, R_row[row] receives the response time or -1.
+// With early_exit the test stops at the first deadline miss (verdict only).
+// Returns the verdict on every lane.  *err |= kErrIter if the iteration cap
+// was reached (the verdict is then 0).
+static __device__ __noinline__ bool warp_rta(const SetSmem& st, const unsigned int* S, unsigned int m, unsigned int kc,
+                                      unsigned int km, const MagicDiv* __restrict__ mdiv, RtaScratch& sc,
+                                      long long* R_row, bool early_exit, unsigned int* err) {
+  const int lane = threadIdx.x & 31;
+  const MagicDiv md = mdiv[m];
+  int nm = 0, ns = 0;
+#pragma unroll
+  for (int w = 0; w < kWords; w++) {
+    nm += __popc(S[w] & st.memmask[w]);
+    ns += __popc(S[w]);
+  }
+  const unsigned int kmem = nm >= 2 ? km : 1000u;
+  const unsigned int kcmp = (ns - nm) >= 2 ? kc : 1000u;
+  // compaction of S's rows in priority order
+  int base = 0;
+  for (int w = 0; w < kWords && w * 32 < st.n; w++) {
+    unsigned int word = S[w];
+    if (word) {
+      int row = w * 32 + lane;
+      if ((word >> lane) & 1u) {
+        int idx = base + __popc(word & ((1u << lane) - 1u));
+        bool mem = (st.memmask[w] >> lane) & 1u;
+        sc.C[idx] = wcet(st.A[row], st.B[row], mem ? kmem : kcmp, m, md);
+        sc.T[idx] = st.T[row];
+        sc.mT[idx] = st.mT[row];
+        sc.sh[idx] = st.shT[row];
+        sc.D[idx] = st.D[row];
+        sc.pos[idx] = (unsigned char)row;
+      }
+      base += __popc(word);
+    }
+  }
+  __syncwarp();
+  const int s = base;
+  bool all_ok = true;
+  unsigned int errbits = 0u;
+  for (int c0 = 0; c0 < s; c0 += 32) {
+    const int i = c0 + lane;
+    const bool active = i < s;
+    unsigned int Ci = 0, Di = 0;
+    unsigned long long R = 0ull;
+    if (active) {
+      Ci = sc.C[i];
+      Di = sc.D[i];
+      R = Ci;
+      for (int j = 0; j < i; j++) R += sc.C[j];
+    }
+    bool done = !active, ok = true;
+    int iter = 0;
+    while (__any_sync(kFull, !done)) {
+      if (!done) {
+        if (R > Di) {
+          ok = false;
+          done = true;
+        } else {
+          const unsigned int Rc = (unsigned int)R;
+          const unsigned long long cap = (unsigned long long)Di + 1ull;
+          unsigned long long next = Ci;
+          for (int j = 0; j < i; j++) {
+            unsigned int q = ceil_div_T(Rc, sc.mT[j], sc.sh[j]);
+            unsigned long long t = (unsigned long long)q * sc.C[j];
+            next += t < cap ? t : cap;
+          }
+          if (next == R) done = true;
+          else R = next;
+          if (++iter > kIterCap) {
+            ok = false;
+            done = true;
+            errbits |= kErrIter;
+          }
+        }
+      }
+      if (early_exit && __any_sync(kFull, !ok)) break;
+    }
+    if (R_row && active) R_row[sc.pos[i]] = ok ? (long long)R : -1LL;
+    all_ok = __all_sync(kFull, ok) && all_ok;
+    if (early_exit && !all_ok) break;
+  }
+  errbits = __reduce_or_sync(kFull, errbits);
+  if (errbits && lane == 0) atomicOr(err, errbits);
+  __syncwarp();
+  return all_ok;
+}
+
+// Alg. 2: smallest multiple of g in [lo, hi] at which S passes; 0 if none.
+// The binary form (§5.3) returns the same size because the test is monotone
+// in m (no timing anomalies, §4.1).
+__device__ __forceinline__ unsigned int warp_minm(const SetSmem& st, const unsigned int* S, unsigned int lo,
+                                                  unsigned int hi, unsigned int g, bool linear, unsigned int kc,
+                                                  unsigned int km, const MagicDiv* __restrict__ mdiv, RtaScratch& sc,
+                                                  unsigned int* err) {
+  if (lo > hi) return 0u;
+  if (linear) {
+    for (unsigned int m = lo; m <= hi; m += g)
+      if (warp_rta(st, S, m, kc, km, mdiv, sc, nullptr, true, err)) return m;
+    return 0u;
+  }
+  if (!warp_rta(st, S, hi, kc, km, mdiv, sc, nullptr, true, err)) return 0u;
+  unsigned int a = lo / g, b = hi / g;
+  while (a < b) {
+    unsigned int mid = a + (b - a) / 2u;
+    if (warp_rta(st, S, mid * g, kc, km, mdiv, sc, nullptr, true, err)) b = mid;
+    else a = mid + 1u;
+  }
+  return a * g;
+}
+
+// Warp-wide sums.
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+__device__ __forceinline__ int warp_sum_i32(int v) { return __reduce_add_sync(kFull, (unsigned int)v); }
+
+}  // namespace gpa

@@ -1,0 +1,103 @@
+// gpa_internal.h — host-side interface between the C ABI (host.cpp) and the
+// kernel launchers (*.cu).  Not installed; not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "gpa.h"
+
+namespace gpa {
+
+// Granlund-Montgomery reciprocal of 10^6 m, one per m in [0, GPA_MMAX]
+// (layout identical to MagicDiv in gpa_device.cuh).
+struct MagicDivHost {
+  unsigned long long magic;
+  unsigned int shift;
+  unsigned int pad;
+};
+
+struct DevSets {
+  long long nsets;
+  int n_max;
+  const long long* set_off;
+  const long long* T;
+  const long long* D;
+  const long long* A;
+  const long long* B;
+  const long long* u;
+  const unsigned char* type;
+};
+
+struct DevModel {
+  int M, g, kc, km;
+};
+
+struct AllocOut {
+  unsigned char* verdict;
+  unsigned char* reason;
+  int* n_parts;
+  int* Pi;
+  long long* W;
+  int* n_tests;
+  unsigned char* part_of_task;
+  short* size_of_part;
+};
+
+// Work-queue state of the persistent allocate kernels.
+struct AllocQueue {
+  unsigned long long* counters;  // [4]: fast ticket, slow count, slow ticket, 1G ticket
+  long long* slow_sets;          // [nsets] sets deferred to the merge kernel
+  unsigned int* err;             // sticky error word
+};
+
+struct LaunchShape {
+  int warps_per_block;  // warps per CTA
+  int chunk;            // sets per ticket (fast kernel)
+  int blocks;           // CTAs of the persistent grid
+};
+
+struct BestOut {
+  unsigned char* feasible;
+  long long* W;
+  int* sum_minm;
+  int* n_blocks;
+  int* spare;
+  unsigned char* rgs;
+  short* minm_block;
+};
+
+struct Cands {
+  long long ncands;
+  int map_stride;
+  int kparts;
+  const long long* set;
+  const unsigned char* part_of_task;
+  const int* size_of_part;
+};
+
+// Kernel launchers; each returns the CUDA error of its launches and adds the
+// number of kernels it launched to *launches.
+cudaError_t launch_allocate(const DevSets& s, const DevModel& md, const gpa_params& p, const AllocOut& out,
+                            const AllocQueue& q, const MagicDivHost* mdiv, const LaunchShape& fast,
+                            const LaunchShape& slow, cudaStream_t st, long long* launches);
+cudaError_t launch_one_gpu(const DevSets& s, const DevModel& md, const AllocOut& out, const AllocQueue& q,
+                           const MagicDivHost* mdiv, const LaunchShape& shape, cudaStream_t st, long long* launches);
+// Per-process kernel attribute set-up (dynamic shared memory opt-in).
+cudaError_t alloc_kernels_init();
+cudaError_t search_kernels_init();
+cudaError_t launch_wcet_tables(const DevSets& s, const DevModel& md, long long* Cn, long long* Cc, unsigned int* err,
+                               const MagicDivHost* mdiv, int sm_count, cudaStream_t st, long long* launches);
+cudaError_t launch_test_schedulable(const DevSets& s, const DevModel& md, const Cands& c, unsigned char* verdict,
+                                    long long* R, unsigned int* err, const MagicDivHost* mdiv, int sm_count,
+                                    cudaStream_t st, long long* launches);
+cudaError_t launch_search_best(const DevSets& s, const DevModel& md, int kmin, int kmax, const BestOut& out,
+                               const AllocQueue& q, const MagicDivHost* mdiv, int sm_count, cudaStream_t st,
+                               long long* launches);
+
+// Largest dynamic shared memory (bytes) the allocate merge kernel needs per CTA.
+size_t slow_smem_bytes(int warps_per_block);
+size_t one_gpu_smem_bytes(int warps_per_block);
+
+}  // namespace gpa

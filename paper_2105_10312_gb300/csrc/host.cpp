@@ -1,0 +1,742 @@
+// host.cpp — the C ABI of libgpa (gpa.h): context, validation, the
+// host-memory path (stage in, run, copy back), the launch shapes of the
+// persistent kernels with their autotuner and CUDA-graph cache, and the
+// combinatorial helpers (ranking of SM splits and of set partitions).
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gpa.h"
+#include "gpa_internal.h"
+#include "gpa_ctx.h"
+
+using namespace gpa;
+
+// ------------------------------------------------------------------ errors
+
+static thread_local std::string g_last_error;
+
+int32_t gpa_fail(int32_t code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int32_t gpa_cuda_fail(cudaError_t e, const char* what) {
+  return gpa_fail(GPA_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+extern "C" int32_t gpa_last_error(char* buf, int32_t len) {
+  if (!buf || len <= 0) return GPA_ERR_ARG;
+  std::snprintf(buf, (size_t)len, "%s", g_last_error.c_str());
+  return GPA_OK;
+}
+
+// ------------------------------------------------------------- validation
+
+static bool model_valid(const gpa_model* m) {
+  return m && m->g >= 1 && m->M >= 1 && m->M <= GPA_MMAX && m->M % m->g == 0 && m->k_c_pm >= 1000 &&
+         m->k_c_pm <= 16000 && m->k_m_pm >= 1000 && m->k_m_pm <= 16000;
+}
+
+static bool host_task_valid(int64_t T, int64_t D, int64_t A, int64_t B, int64_t u, uint8_t type) {
+  return D >= 1 && D <= T && T <= 2147483647LL && A >= 0 && B >= 0 && A + B >= 1 && A + B <= (1LL << 36) &&
+         u >= 0 && u <= 4294967295LL && type <= 1;
+}
+
+extern "C" int32_t gpa_validate(const gpa_tasksets* sets, const gpa_model* model, int64_t* bad_set) {
+  if (bad_set) *bad_set = -1;
+  if (!sets || !sets->set_off) return gpa_fail(GPA_ERR_ARG, "gpa_validate: NULL task sets");
+  if (sets->mem != GPA_HOST) return gpa_fail(GPA_ERR_ARG, "gpa_validate: host arrays only");
+  if (model && !model_valid(model)) return gpa_fail(GPA_ERR_RANGE, "gpa_validate: model out of range");
+  if (sets->nsets < 0 || sets->n_max < 0 || sets->n_max > GPA_NMAX)
+    return gpa_fail(GPA_ERR_RANGE, "gpa_validate: nsets/n_max out of range");
+  if (sets->set_off[0] != 0) return gpa_fail(GPA_ERR_RANGE, "gpa_validate: set_off[0] != 0");
+  for (int64_t s = 0; s < sets->nsets; s++) {
+    int64_t o = sets->set_off[s], n = sets->set_off[s + 1] - o;
+    bool ok = n >= 0 && n <= sets->n_max;
+    if (ok && n > 0 && (!sets->T || !sets->D || !sets->A || !sets->B || !sets->type))
+      return gpa_fail(GPA_ERR_ARG, "gpa_validate: NULL task column");
+    for (int64_t t = 0; ok && t < n; t++)
+      ok = host_task_valid(sets->T[o + t], sets->D[o + t], sets->A[o + t], sets->B[o + t],
+                           sets->u_ppm ? sets->u_ppm[o + t] : 0, sets->type[o + t]);
+    if (!ok) {
+      if (bad_set) *bad_set = s;
+      return gpa_fail(GPA_ERR_RANGE, "gpa_validate: set %lld violates the bounds", (long long)s);
+    }
+  }
+  return GPA_OK;
+}
+
+// ----------------------------------------------------------------- context
+
+static void build_mdiv(std::vector<MagicDivHost>& t) {
+  t.assign(GPA_MMAX + 1, MagicDivHost{0, 0, 0});
+  for (int m = 1; m <= GPA_MMAX; m++) {
+    unsigned long long d = 1000000ull * (unsigned long long)m;
+    unsigned int l = 0;
+    while ((1ull << l) < d) l++;
+    unsigned __int128 num = ((unsigned __int128)1 << (60 + l)) + d - 1;
+    t[m].magic = (unsigned long long)(num / d);
+    t[m].shift = l - 4;
+  }
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+extern "C" int32_t gpa_ctx_create(int32_t device, void* stream, gpa_ctx** out) {
+  if (!out) return gpa_fail(GPA_ERR_ARG, "gpa_ctx_create: out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return gpa_cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= ndev) return gpa_fail(GPA_ERR_ARG, "gpa_ctx_create: no CUDA device %d", device);
+  DeviceGuard guard(device);
+  gpa_ctx* c = new gpa_ctx();
+  c->device = device;
+  c->stream = (cudaStream_t)stream;
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, device);
+  if (e != cudaSuccess) { delete c; return gpa_cuda_fail(e, "cudaGetDeviceProperties"); }
+  c->sm_count = prop.multiProcessorCount;
+  std::vector<MagicDivHost> t;
+  build_mdiv(t);
+  if ((e = cudaMalloc(&c->d_mdiv, sizeof(MagicDivHost) * t.size())) != cudaSuccess ||
+      (e = cudaMemcpy(c->d_mdiv, t.data(), sizeof(MagicDivHost) * t.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMalloc(&c->d_counters, 8 * sizeof(unsigned long long))) != cudaSuccess ||
+      (e = cudaMemset(c->d_counters, 0, 8 * sizeof(unsigned long long))) != cudaSuccess ||
+      (e = cudaMalloc(&c->d_err, sizeof(unsigned int))) != cudaSuccess ||
+      (e = cudaMemset(c->d_err, 0, sizeof(unsigned int))) != cudaSuccess) {
+    gpa_ctx_destroy(c);
+    return gpa_cuda_fail(e, "gpa_ctx_create: device allocation");
+  }
+  static std::once_flag once;
+  static cudaError_t init_err = cudaSuccess;
+  std::call_once(once, [] {
+    init_err = alloc_kernels_init();
+    if (init_err == cudaSuccess) init_err = search_kernels_init();
+  });
+  if (init_err != cudaSuccess) {
+    gpa_ctx_destroy(c);
+    return gpa_cuda_fail(init_err, "kernel attribute set-up");
+  }
+  *out = c;
+  return GPA_OK;
+}
+
+extern "C" int32_t gpa_ctx_destroy(gpa_ctx* c) {
+  if (!c) return GPA_OK;
+  DeviceGuard guard(c->device);
+  gpa_serve_teardown(c);
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+  for (auto& b : c->bufs) cudaFree(b.ptr);
+  cudaFree(c->d_mdiv);
+  cudaFree(c->d_counters);
+  cudaFree(c->d_err);
+  cudaFree(c->d_slow);
+  delete c;
+  return GPA_OK;
+}
+
+extern "C" int32_t gpa_ctx_set_stream(gpa_ctx* c, void* stream) {
+  if (!c) return gpa_fail(GPA_ERR_ARG, "gpa_ctx_set_stream: NULL context");
+  c->stream = (cudaStream_t)stream;
+  return GPA_OK;
+}
+
+extern "C" int32_t gpa_ctx_launch_count(gpa_ctx* c, int64_t* out) {
+  if (!c || !out) return gpa_fail(GPA_ERR_ARG, "gpa_ctx_launch_count: NULL argument");
+  *out = c->launches;
+  return GPA_OK;
+}
+
+extern "C" int32_t gpa_ctx_set_option(gpa_ctx* c, int32_t opt, int64_t value) {
+  if (!c) return gpa_fail(GPA_ERR_ARG, "gpa_ctx_set_option: NULL context");
+  switch (opt) {
+    case GPA_OPT_AUTOTUNE: c->autotune = value != 0; break;
+    case GPA_OPT_GRAPH: c->use_graph = value != 0; break;
+    case GPA_OPT_FAST_WARPS:
+      if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8) return gpa_fail(GPA_ERR_RANGE, "warps");
+      c->force_fast.warps_per_block = (int)value;
+      break;
+    case GPA_OPT_FAST_CHUNK:
+      if (value < 0 || value > 64) return gpa_fail(GPA_ERR_RANGE, "chunk");
+      c->force_fast.chunk = (int)value;
+      break;
+    case GPA_OPT_FAST_BLOCKS:
+      if (value < 0 || value > (1 << 20)) return gpa_fail(GPA_ERR_RANGE, "blocks");
+      c->force_fast.blocks = (int)value;
+      break;
+    case GPA_OPT_PER_SET_LAUNCH: c->per_set_launch = value != 0; break;
+    default: return gpa_fail(GPA_ERR_ARG, "gpa_ctx_set_option: unknown option %d", opt);
+  }
+  return GPA_OK;
+}
+
+extern "C" int32_t gpa_ctx_sync(gpa_ctx* c) {
+  if (!c) return gpa_fail(GPA_ERR_ARG, "gpa_ctx_sync: NULL context");
+  DeviceGuard guard(c->device);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return gpa_cuda_fail(e, "cudaStreamSynchronize");
+  unsigned int err = 0;
+  e = cudaMemcpy(&err, c->d_err, sizeof err, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return gpa_cuda_fail(e, "read error word");
+  if (err) {
+    cudaMemset(c->d_err, 0, sizeof(unsigned int));
+    if (err & 2u) return gpa_fail(GPA_ERR_TIMEOUT, "a response-time iteration exceeded its step limit");
+    return gpa_fail(GPA_ERR_RANGE, "a device-resident set failed validation");
+  }
+  return GPA_OK;
+}
+
+// --------------------------------------------------------- scratch buffers
+
+void* ctx_buffer(gpa_ctx* c, int slot, size_t bytes) {
+  if (slot >= (int)c->bufs.size()) c->bufs.resize((size_t)slot + 1);
+  CtxBuf& b = c->bufs[(size_t)slot];
+  if (b.bytes < bytes) {
+    if (b.ptr) cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+    size_t want = bytes < 256 ? 256 : bytes;
+    if (cudaMalloc(&b.ptr, want) != cudaSuccess) return nullptr;
+    b.bytes = want;
+    c->graphs_dirty = true;  // cached graphs may hold the old pointer
+  }
+  return b.ptr;
+}
+
+static int32_t ensure_slow(gpa_ctx* c, long long nsets) {
+  if (c->slow_cap >= nsets && c->d_slow) return GPA_OK;
+  if (c->d_slow) cudaFree(c->d_slow);
+  c->d_slow = nullptr;
+  long long cap = nsets < 1024 ? 1024 : nsets;
+  cudaError_t e = cudaMalloc(&c->d_slow, sizeof(long long) * (size_t)cap);
+  if (e != cudaSuccess) {
+    c->slow_cap = 0;
+    return gpa_fail(GPA_ERR_NOMEM, "slow-queue allocation of %lld sets failed", cap);
+  }
+  c->slow_cap = cap;
+  c->graphs_dirty = true;
+  return GPA_OK;
+}
+
+// --------------------------------------------------- host <-> device staging
+
+struct HostStage {
+  DevSets ds{};
+  long long ntasks = 0;
+};
+
+// Copy a host batch into context buffers (slots 0..6).
+static int32_t stage_in(gpa_ctx* c, const gpa_tasksets* sets, HostStage* hs) {
+  const long long ns = sets->nsets;
+  const long long nt = sets->set_off[ns];
+  hs->ntasks = nt;
+  const size_t b8 = sizeof(long long) * (size_t)(nt > 0 ? nt : 1);
+  long long* off = (long long*)ctx_buffer(c, 0, sizeof(long long) * (size_t)(ns + 1));
+  long long* T = (long long*)ctx_buffer(c, 1, b8);
+  long long* D = (long long*)ctx_buffer(c, 2, b8);
+  long long* A = (long long*)ctx_buffer(c, 3, b8);
+  long long* B = (long long*)ctx_buffer(c, 4, b8);
+  long long* u = (long long*)ctx_buffer(c, 5, b8);
+  unsigned char* ty = (unsigned char*)ctx_buffer(c, 6, (size_t)(nt > 0 ? nt : 1));
+  if (!off || !T || !D || !A || !B || !u || !ty) return gpa_fail(GPA_ERR_NOMEM, "staging allocation failed");
+  cudaStream_t st = c->stream;
+  cudaError_t e = cudaMemcpyAsync(off, sets->set_off, sizeof(long long) * (size_t)(ns + 1), cudaMemcpyHostToDevice, st);
+  if (nt > 0) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(T, sets->T, b8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(D, sets->D, b8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(A, sets->A, b8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(B, sets->B, b8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && sets->u_ppm) e = cudaMemcpyAsync(u, sets->u_ppm, b8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !sets->u_ppm) e = cudaMemsetAsync(u, 0, b8, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ty, sets->type, (size_t)nt, cudaMemcpyHostToDevice, st);
+  }
+  if (e != cudaSuccess) return gpa_cuda_fail(e, "host-to-device copy of task sets");
+  hs->ds = DevSets{ns, sets->n_max, off, T, D, A, B, u, ty};
+  return GPA_OK;
+}
+
+static DevSets dev_sets(const gpa_tasksets* s) {
+  return DevSets{s->nsets, s->n_max, (const long long*)s->set_off, (const long long*)s->T, (const long long*)s->D,
+                 (const long long*)s->A, (const long long*)s->B, (const long long*)s->u_ppm,
+                 (const unsigned char*)s->type};
+}
+
+static int32_t finish_host_call(gpa_ctx* c) { return gpa_ctx_sync(c); }
+
+static int32_t common_checks(gpa_ctx* c, const gpa_tasksets* sets, const gpa_model* model, const char* who) {
+  if (!c) return gpa_fail(GPA_ERR_ARG, "%s: NULL context", who);
+  if (!sets || !sets->set_off) return gpa_fail(GPA_ERR_ARG, "%s: NULL task sets", who);
+  if (sets->mem != GPA_HOST && sets->mem != GPA_DEVICE) return gpa_fail(GPA_ERR_ARG, "%s: bad mem tag", who);
+  if (!model_valid(model)) return gpa_fail(GPA_ERR_RANGE, "%s: model out of range", who);
+  if (sets->nsets < 0 || sets->n_max < 0 || sets->n_max > GPA_NMAX)
+    return gpa_fail(GPA_ERR_RANGE, "%s: nsets/n_max out of range", who);
+  if (sets->mem == GPA_HOST) {
+    int64_t bad;
+    int32_t st = gpa_validate(sets, model, &bad);
+    if (st != GPA_OK) return st;
+  }
+  return GPA_OK;
+}
+
+// -------------------------------------------------------------- WCET tables
+
+extern "C" int32_t gpa_build_wcet_tables(gpa_ctx* c, const gpa_tasksets* sets, const gpa_model* model, int64_t* Cn,
+                                         int64_t* Cc) {
+  int32_t st = common_checks(c, sets, model, "gpa_build_wcet_tables");
+  if (st != GPA_OK) return st;
+  if (sets->nsets == 0) return GPA_OK;
+  if (!Cn || !Cc) return gpa_fail(GPA_ERR_ARG, "gpa_build_wcet_tables: NULL output");
+  DeviceGuard guard(c->device);
+  DevModel md{model->M, model->g, model->k_c_pm, model->k_m_pm};
+  const long long Mu = model->M / model->g;
+  if (sets->mem == GPA_DEVICE) {
+    cudaError_t e = launch_wcet_tables(dev_sets(sets), md, (long long*)Cn, (long long*)Cc, c->d_err, c->d_mdiv,
+                                       c->sm_count, c->stream, &c->launches);
+    return e == cudaSuccess ? GPA_OK : gpa_cuda_fail(e, "wcet_tables launch");
+  }
+  HostStage hs;
+  if ((st = stage_in(c, sets, &hs)) != GPA_OK) return st;
+  const size_t bytes = sizeof(long long) * (size_t)(hs.ntasks * Mu > 0 ? hs.ntasks * Mu : 1);
+  long long* dCn = (long long*)ctx_buffer(c, 7, bytes);
+  long long* dCc = (long long*)ctx_buffer(c, 8, bytes);
+  if (!dCn || !dCc) return gpa_fail(GPA_ERR_NOMEM, "table allocation failed");
+  cudaError_t e = launch_wcet_tables(hs.ds, md, dCn, dCc, c->d_err, c->d_mdiv, c->sm_count, c->stream, &c->launches);
+  if (e == cudaSuccess && hs.ntasks * Mu > 0) {
+    e = cudaMemcpyAsync(Cn, dCn, sizeof(long long) * (size_t)(hs.ntasks * Mu), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(Cc, dCc, sizeof(long long) * (size_t)(hs.ntasks * Mu), cudaMemcpyDeviceToHost, c->stream);
+  }
+  if (e != cudaSuccess) return gpa_cuda_fail(e, "wcet_tables");
+  return finish_host_call(c);
+}
+
+// ------------------------------------------------------- explicit candidates
+
+extern "C" int32_t gpa_test_schedulable(gpa_ctx* c, const gpa_tasksets* sets, const gpa_model* model,
+                                        const gpa_candidates* cands, uint8_t* verdict, int64_t* R) {
+  int32_t st = common_checks(c, sets, model, "gpa_test_schedulable");
+  if (st != GPA_OK) return st;
+  if (!cands) return gpa_fail(GPA_ERR_ARG, "gpa_test_schedulable: NULL candidates");
+  if (cands->mem != sets->mem) return gpa_fail(GPA_ERR_ARG, "gpa_test_schedulable: candidates and sets differ in mem");
+  if (cands->ncands < 0 || cands->kparts < 1 || cands->kparts > 255 || cands->map_stride < 1 ||
+      cands->map_stride > 65536)
+    return gpa_fail(GPA_ERR_RANGE, "gpa_test_schedulable: candidate shape out of range");
+  if (cands->ncands == 0) return GPA_OK;
+  if (!verdict || !cands->set || !cands->part_of_task || !cands->size_of_part)
+    return gpa_fail(GPA_ERR_ARG, "gpa_test_schedulable: NULL array");
+  DeviceGuard guard(c->device);
+  DevModel md{model->M, model->g, model->k_c_pm, model->k_m_pm};
+  const long long nc = cands->ncands;
+  if (sets->mem == GPA_DEVICE) {
+    Cands cc{nc, cands->map_stride, cands->kparts, (const long long*)cands->set, cands->part_of_task,
+             cands->size_of_part};
+    cudaError_t e = launch_test_schedulable(dev_sets(sets), md, cc, verdict, (long long*)R, c->d_err, c->d_mdiv,
+                                            c->sm_count, c->stream, &c->launches);
+    return e == cudaSuccess ? GPA_OK : gpa_cuda_fail(e, "test_schedulable launch");
+  }
+  // host path: validate candidates on the host too
+  for (long long i = 0; i < nc; i++) {
+    long long s = cands->set[i];
+    if (s < 0 || s >= sets->nsets) return gpa_fail(GPA_ERR_RANGE, "candidate %lld: bad set index", i);
+    long long n = sets->set_off[s + 1] - sets->set_off[s];
+    if (n > cands->map_stride) return gpa_fail(GPA_ERR_RANGE, "candidate %lld: map_stride < tasks", i);
+    for (long long t = 0; t < n; t++)
+      if (cands->part_of_task[i * cands->map_stride + t] >= cands->kparts)
+        return gpa_fail(GPA_ERR_RANGE, "candidate %lld: part index out of range", i);
+    for (int p = 0; p < cands->kparts; p++) {
+      int z = cands->size_of_part[i * cands->kparts + p];
+      if (z < 0 || z > model->M || z % model->g != 0)
+        return gpa_fail(GPA_ERR_RANGE, "candidate %lld: part size out of range", i);
+    }
+  }
+  HostStage hs;
+  if ((st = stage_in(c, sets, &hs)) != GPA_OK) return st;
+  long long* dset = (long long*)ctx_buffer(c, 9, sizeof(long long) * (size_t)nc);
+  unsigned char* dmap = (unsigned char*)ctx_buffer(c, 10, (size_t)(nc * cands->map_stride));
+  int* dsize = (int*)ctx_buffer(c, 11, sizeof(int) * (size_t)(nc * cands->kparts));
+  unsigned char* dver = (unsigned char*)ctx_buffer(c, 12, (size_t)nc);
+  long long* dR = R ? (long long*)ctx_buffer(c, 13, sizeof(long long) * (size_t)(nc * cands->map_stride)) : nullptr;
+  if (!dset || !dmap || !dsize || !dver || (R && !dR)) return gpa_fail(GPA_ERR_NOMEM, "candidate staging failed");
+  cudaStream_t s = c->stream;
+  cudaError_t e = cudaMemcpyAsync(dset, cands->set, sizeof(long long) * (size_t)nc, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dmap, cands->part_of_task, (size_t)(nc * cands->map_stride), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dsize, cands->size_of_part, sizeof(int) * (size_t)(nc * cands->kparts),
+                        cudaMemcpyHostToDevice, s);
+  Cands cc{nc, cands->map_stride, cands->kparts, dset, dmap, dsize};
+  if (e == cudaSuccess)
+    e = launch_test_schedulable(hs.ds, md, cc, dver, dR, c->d_err, c->d_mdiv, c->sm_count, s, &c->launches);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(verdict, dver, (size_t)nc, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && R)
+    e = cudaMemcpyAsync(R, dR, sizeof(long long) * (size_t)(nc * cands->map_stride), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return gpa_cuda_fail(e, "test_schedulable");
+  return finish_host_call(c);
+}
+
+// --------------------------------------------------------------- allocate
+
+static LaunchShape default_fast(const gpa_ctx* c) { return LaunchShape{8, 2, c->sm_count * 8}; }
+static LaunchShape default_slow(const gpa_ctx* c) { return LaunchShape{4, 1, c->sm_count * 2}; }
+
+static LaunchShape fast_shape(gpa_ctx* c, const DevSets& ds, const DevModel& md, const gpa_params& p) {
+  LaunchShape sh = default_fast(c);
+  auto it = c->tuned.find(tune_key(ds, md, p));
+  if (it != c->tuned.end()) sh = it->second;
+  if (c->force_fast.warps_per_block) sh.warps_per_block = c->force_fast.warps_per_block;
+  if (c->force_fast.chunk) sh.chunk = c->force_fast.chunk;
+  if (c->force_fast.blocks) sh.blocks = c->force_fast.blocks;
+  return sh;
+}
+
+std::string tune_key(const DevSets& ds, const DevModel& md, const gpa_params& p) {
+  char buf[160];
+  std::snprintf(buf, sizeof buf, "alloc:%lld:%d:%d:%d:%d:%d:%d", ds.nsets, ds.n_max, md.M, md.g, p.policy, p.act,
+                (int)0);
+  return buf;
+}
+
+static cudaError_t run_allocate(gpa_ctx* c, const DevSets& ds, const DevModel& md, const gpa_params& p,
+                                const AllocOut& out, const LaunchShape& fast) {
+  AllocQueue q{c->d_counters, c->d_slow, c->d_err};
+  if (p.policy == GPA_POLICY_ONE_GPU) {
+    LaunchShape sh{8, 1, c->sm_count * 4};
+    return launch_one_gpu(ds, md, out, q, c->d_mdiv, sh, c->stream, &c->launches);
+  }
+  return launch_allocate(ds, md, p, out, q, c->d_mdiv, fast, default_slow(c), c->stream, &c->launches);
+}
+
+// Autotuner: time the candidate shapes of the fast kernel on this batch
+// (every shape computes the same result) and keep the fastest.
+static void autotune_allocate(gpa_ctx* c, const DevSets& ds, const DevModel& md, const gpa_params& p,
+                              const AllocOut& out) {
+  const std::string key = tune_key(ds, md, p);
+  if (c->tuned.count(key)) return;
+  static const int warps_opts[] = {4, 8};
+  static const int chunk_opts[] = {1, 2, 4, 8};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best_ms = 1e30f;
+  LaunchShape best = default_fast(c);
+  for (int w : warps_opts)
+    for (int ch : chunk_opts) {
+      LaunchShape sh{w, ch, c->sm_count * (2048 / (w * 32))};
+      float tot = 0.f;
+      for (int rep = 0; rep < 3; rep++) {
+        cudaEventRecord(e0, c->stream);
+        run_allocate(c, ds, md, p, out, sh);
+        cudaEventRecord(e1, c->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) tot += ms;
+      }
+      if (tot < best_ms) {
+        best_ms = tot;
+        best = sh;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->tuned[key] = best;
+}
+
+static std::string graph_key(const DevSets& ds, const DevModel& md, const gpa_params& p, const AllocOut& o,
+                             const LaunchShape& sh) {
+  char buf[512];
+  std::snprintf(buf, sizeof buf, "%lld|%d|%p|%p|%p|%p|%p|%p|%p|%d|%d|%d|%d|%d|%d|%d|%p|%p|%p|%p|%p|%p|%p|%p|%d|%d|%d",
+                ds.nsets, ds.n_max, (const void*)ds.set_off, (const void*)ds.T, (const void*)ds.D,
+                (const void*)ds.A, (const void*)ds.B, (const void*)ds.u, (const void*)ds.type, md.M, md.g, md.kc,
+                md.km, p.policy, p.act, p.linear_merge, (void*)o.verdict, (void*)o.reason, (void*)o.n_parts,
+                (void*)o.Pi, (void*)o.W, (void*)o.n_tests, (void*)o.part_of_task, (void*)o.size_of_part,
+                sh.warps_per_block, sh.chunk, sh.blocks);
+  return buf;
+}
+
+static int32_t allocate_device(gpa_ctx* c, const DevSets& ds, const DevModel& md, const gpa_params& p,
+                               const AllocOut& out) {
+  int32_t st = ensure_slow(c, ds.nsets);
+  if (st != GPA_OK) return st;
+  if (c->per_set_launch && p.policy != GPA_POLICY_ONE_GPU) {
+    // the plain form: one launch sequence per task set
+    for (long long s = 0; s < ds.nsets; s++) {
+      DevSets one = ds;
+      one.nsets = 1;
+      one.set_off = ds.set_off + s;
+      AllocOut o1 = out;
+      o1.verdict += s;
+      o1.reason += s;
+      o1.n_parts += s;
+      o1.Pi += s;
+      o1.W += s;
+      if (o1.n_tests) o1.n_tests += s;
+      LaunchShape one_shape{1, 1, 1};
+      AllocQueue q{c->d_counters, c->d_slow, c->d_err};
+      LaunchShape slow1{1, 1, 1};
+      cudaError_t e = launch_allocate(one, md, p, o1, q, c->d_mdiv, one_shape, slow1, c->stream, &c->launches);
+      if (e != cudaSuccess) return gpa_cuda_fail(e, "per-set allocate launch");
+    }
+    return GPA_OK;
+  }
+  if (c->autotune && p.policy != GPA_POLICY_ONE_GPU) autotune_allocate(c, ds, md, p, out);
+  const LaunchShape fast = fast_shape(c, ds, md, p);
+  if (c->use_graph) {
+    if (c->graphs_dirty) {
+      for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+      c->graphs.clear();
+      c->graphs_dirty = false;
+    }
+    const std::string key = graph_key(ds, md, p, out, fast);
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return gpa_cuda_fail(e, "cudaStreamBeginCapture");
+      long long before = c->launches;
+      cudaError_t le = run_allocate(c, ds, md, p, out, fast);
+      long long kernels = c->launches - before;
+      c->launches = before;
+      e = cudaStreamEndCapture(c->stream, &g);
+      if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return gpa_cuda_fail(le, "allocate capture");
+      }
+      if (e != cudaSuccess) return gpa_cuda_fail(e, "cudaStreamEndCapture");
+      cudaGraphExec_t exec = nullptr;
+      e = cudaGraphInstantiate(&exec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return gpa_cuda_fail(e, "cudaGraphInstantiate");
+      it = c->graphs.emplace(key, CachedGraph{exec, kernels}).first;
+    }
+    cudaError_t e = cudaGraphLaunch(it->second.exec, c->stream);
+    if (e != cudaSuccess) return gpa_cuda_fail(e, "cudaGraphLaunch");
+    c->launches += it->second.kernels;
+    return GPA_OK;
+  }
+  cudaError_t e = run_allocate(c, ds, md, p, out, fast);
+  return e == cudaSuccess ? GPA_OK : gpa_cuda_fail(e, "allocate launch");
+}
+
+extern "C" int32_t gpa_allocate(gpa_ctx* c, const gpa_tasksets* sets, const gpa_model* model,
+                                const gpa_params* params, gpa_alloc_result* r) {
+  int32_t st = common_checks(c, sets, model, "gpa_allocate");
+  if (st != GPA_OK) return st;
+  if (!params || !r) return gpa_fail(GPA_ERR_ARG, "gpa_allocate: NULL params/result");
+  if (params->policy < GPA_POLICY_SMS || params->policy > GPA_POLICY_ONE_GPU)
+    return gpa_fail(GPA_ERR_ARG, "gpa_allocate: unknown policy %d", params->policy);
+  if (r->mem != sets->mem) return gpa_fail(GPA_ERR_ARG, "gpa_allocate: result and sets differ in mem");
+  if (sets->nsets == 0) return GPA_OK;
+  if (!r->verdict || !r->reason || !r->n_parts || !r->Pi || !r->W || !r->part_of_task || !r->size_of_part)
+    return gpa_fail(GPA_ERR_ARG, "gpa_allocate: NULL result array");
+  if (!sets->u_ppm) return gpa_fail(GPA_ERR_ARG, "gpa_allocate: u_ppm is required");
+  DeviceGuard guard(c->device);
+  DevModel md{model->M, model->g, model->k_c_pm, model->k_m_pm};
+  if (sets->mem == GPA_DEVICE) {
+    AllocOut out{r->verdict, r->reason, r->n_parts, r->Pi, (long long*)r->W, r->n_tests, r->part_of_task,
+                 r->size_of_part};
+    return allocate_device(c, dev_sets(sets), md, *params, out);
+  }
+  HostStage hs;
+  if ((st = stage_in(c, sets, &hs)) != GPA_OK) return st;
+  const long long ns = sets->nsets, nt = hs.ntasks > 0 ? hs.ntasks : 1;
+  AllocOut out{(unsigned char*)ctx_buffer(c, 14, (size_t)ns), (unsigned char*)ctx_buffer(c, 15, (size_t)ns),
+               (int*)ctx_buffer(c, 16, sizeof(int) * (size_t)ns), (int*)ctx_buffer(c, 17, sizeof(int) * (size_t)ns),
+               (long long*)ctx_buffer(c, 18, sizeof(long long) * (size_t)ns),
+               r->n_tests ? (int*)ctx_buffer(c, 19, sizeof(int) * (size_t)ns) : nullptr,
+               (unsigned char*)ctx_buffer(c, 20, (size_t)nt), (short*)ctx_buffer(c, 21, sizeof(short) * (size_t)nt)};
+  if (!out.verdict || !out.reason || !out.n_parts || !out.Pi || !out.W || (r->n_tests && !out.n_tests) ||
+      !out.part_of_task || !out.size_of_part)
+    return gpa_fail(GPA_ERR_NOMEM, "result staging failed");
+  if ((st = allocate_device(c, hs.ds, md, *params, out)) != GPA_OK) return st;
+  cudaStream_t s = c->stream;
+  cudaError_t e = cudaMemcpyAsync(r->verdict, out.verdict, (size_t)ns, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(r->reason, out.reason, (size_t)ns, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(r->n_parts, out.n_parts, sizeof(int) * (size_t)ns, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(r->Pi, out.Pi, sizeof(int) * (size_t)ns, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(r->W, out.W, sizeof(long long) * (size_t)ns, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && r->n_tests)
+    e = cudaMemcpyAsync(r->n_tests, out.n_tests, sizeof(int) * (size_t)ns, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && hs.ntasks > 0)
+    e = cudaMemcpyAsync(r->part_of_task, out.part_of_task, (size_t)hs.ntasks, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && hs.ntasks > 0)
+    e = cudaMemcpyAsync(r->size_of_part, out.size_of_part, sizeof(short) * (size_t)hs.ntasks, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return gpa_cuda_fail(e, "allocate result copy");
+  return finish_host_call(c);
+}
+
+// ------------------------------------------------------- exhaustive optimum
+
+extern "C" int32_t gpa_search_best(gpa_ctx* c, const gpa_tasksets* sets, const gpa_model* model, int32_t kmin,
+                                   int32_t kmax, gpa_best_result* r) {
+  int32_t st = common_checks(c, sets, model, "gpa_search_best");
+  if (st != GPA_OK) return st;
+  if (!r) return gpa_fail(GPA_ERR_ARG, "gpa_search_best: NULL result");
+  if (kmin < 1 || kmax < kmin || kmax > GPA_SEARCH_KMAX)
+    return gpa_fail(GPA_ERR_RANGE, "gpa_search_best: need 1 <= kmin <= kmax <= %d", GPA_SEARCH_KMAX);
+  if (sets->n_max > GPA_SEARCH_NMAX)
+    return gpa_fail(GPA_ERR_RANGE, "gpa_search_best: n_max %d exceeds %d", sets->n_max, GPA_SEARCH_NMAX);
+  if (r->mem != sets->mem) return gpa_fail(GPA_ERR_ARG, "gpa_search_best: result and sets differ in mem");
+  if (sets->nsets == 0) return GPA_OK;
+  if (!sets->u_ppm) return gpa_fail(GPA_ERR_ARG, "gpa_search_best: u_ppm is required");
+  if (!r->feasible || !r->W || !r->sum_minm || !r->n_blocks || !r->spare || !r->rgs || !r->minm_block)
+    return gpa_fail(GPA_ERR_ARG, "gpa_search_best: NULL result array");
+  DeviceGuard guard(c->device);
+  DevModel md{model->M, model->g, model->k_c_pm, model->k_m_pm};
+  AllocQueue q{c->d_counters, c->d_slow, c->d_err};
+  if (sets->mem == GPA_DEVICE) {
+    BestOut out{r->feasible, (long long*)r->W, r->sum_minm, r->n_blocks, r->spare, r->rgs, r->minm_block};
+    cudaError_t e = launch_search_best(dev_sets(sets), md, kmin, kmax, out, q, c->d_mdiv, c->sm_count, c->stream,
+                                       &c->launches);
+    return e == cudaSuccess ? GPA_OK : gpa_cuda_fail(e, "search_best launch");
+  }
+  HostStage hs;
+  if ((st = stage_in(c, sets, &hs)) != GPA_OK) return st;
+  const long long ns = sets->nsets, nt = hs.ntasks > 0 ? hs.ntasks : 1;
+  BestOut out{(unsigned char*)ctx_buffer(c, 22, (size_t)ns), (long long*)ctx_buffer(c, 23, 8 * (size_t)ns),
+              (int*)ctx_buffer(c, 24, 4 * (size_t)ns), (int*)ctx_buffer(c, 25, 4 * (size_t)ns),
+              (int*)ctx_buffer(c, 26, 4 * (size_t)ns), (unsigned char*)ctx_buffer(c, 27, (size_t)nt),
+              (short*)ctx_buffer(c, 28, 2 * (size_t)(ns * kmax))};
+  if (!out.feasible || !out.W || !out.sum_minm || !out.n_blocks || !out.spare || !out.rgs || !out.minm_block)
+    return gpa_fail(GPA_ERR_NOMEM, "result staging failed");
+  cudaStream_t s = c->stream;
+  cudaError_t e = launch_search_best(hs.ds, md, kmin, kmax, out, q, c->d_mdiv, c->sm_count, s, &c->launches);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(r->feasible, out.feasible, (size_t)ns, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(r->W, out.W, 8 * (size_t)ns, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(r->sum_minm, out.sum_minm, 4 * (size_t)ns, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(r->n_blocks, out.n_blocks, 4 * (size_t)ns, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(r->spare, out.spare, 4 * (size_t)ns, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && hs.ntasks > 0)
+    e = cudaMemcpyAsync(r->rgs, out.rgs, (size_t)hs.ntasks, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(r->minm_block, out.minm_block, 2 * (size_t)(ns * kmax), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return gpa_cuda_fail(e, "search_best");
+  return finish_host_call(c);
+}
+
+// --------------------------------------------- compositions and set partitions
+
+static unsigned __int128 binom128(long long n, long long k) {
+  if (k < 0 || n < 0 || k > n) return 0;
+  if (k > n - k) k = n - k;
+  unsigned __int128 r = 1;
+  for (long long i = 1; i <= k; i++) {
+    r = r * (unsigned __int128)(n - k + i) / (unsigned __int128)i;
+    if (r > (((unsigned __int128)1) << 100)) return r;  // saturates; callers check against 2^64
+  }
+  return r;
+}
+
+extern "C" int32_t gpa_enumerate_partitions(int32_t Mu, int32_t kmin, int32_t kmax, uint64_t* count) {
+  if (!count) return gpa_fail(GPA_ERR_ARG, "gpa_enumerate_partitions: NULL count");
+  if (Mu < 1 || Mu > GPA_MMAX || kmin < 1 || kmax < kmin) return gpa_fail(GPA_ERR_RANGE, "bad Mu/kmin/kmax");
+  unsigned __int128 total = 0;
+  for (int k = kmin; k <= kmax && k <= Mu; k++) total += binom128(Mu - 1, k - 1);
+  if (total >> 64) return gpa_fail(GPA_ERR_RANGE, "count exceeds 2^64");
+  *count = (uint64_t)total;
+  return GPA_OK;
+}
+
+extern "C" int32_t gpa_unrank_composition(int32_t Mu, int32_t k, uint64_t rank, int32_t* parts) {
+  if (!parts) return gpa_fail(GPA_ERR_ARG, "NULL parts");
+  if (Mu < 1 || Mu > GPA_MMAX || k < 1 || k > Mu) return gpa_fail(GPA_ERR_RANGE, "bad Mu/k");
+  unsigned __int128 total = binom128(Mu - 1, k - 1);
+  if ((unsigned __int128)rank >= total) return gpa_fail(GPA_ERR_RANGE, "rank out of range");
+  unsigned __int128 r = rank;
+  int left = Mu;
+  for (int i = 0; i < k; i++) {
+    const int rest = k - i - 1;  // parts after this one
+    if (rest == 0) {
+      parts[i] = left;
+      break;
+    }
+    for (int p = 1; p <= left - rest; p++) {
+      // completions with parts[i] = p: compositions of left - p into rest parts
+      unsigned __int128 c = binom128(left - p - 1, rest - 1);
+      if (r < c) {
+        parts[i] = p;
+        left -= p;
+        break;
+      }
+      r -= c;
+    }
+  }
+  return GPA_OK;
+}
+
+// completions[i][j]: ways to label positions i..n-1 given j open blocks
+static void rgs_counts(int n, int kmax, std::vector<std::vector<unsigned __int128>>& cnt) {
+  cnt.assign((size_t)n + 1, std::vector<unsigned __int128>((size_t)kmax + 2, 0));
+  for (int j = 0; j <= kmax + 1; j++) cnt[(size_t)n][(size_t)j] = 1;
+  for (int i = n - 1; i >= 0; i--)
+    for (int j = 0; j <= kmax; j++) {
+      unsigned __int128 c = (unsigned __int128)j * cnt[(size_t)i + 1][(size_t)j];
+      if (j < kmax) c += cnt[(size_t)i + 1][(size_t)j + 1];
+      cnt[(size_t)i][(size_t)j] = c;
+    }
+}
+
+extern "C" int32_t gpa_count_rgs(int32_t n, int32_t kmax, uint64_t* count) {
+  if (!count) return gpa_fail(GPA_ERR_ARG, "NULL count");
+  if (n < 0 || n > GPA_NMAX || kmax < 1 || kmax > GPA_NMAX) return gpa_fail(GPA_ERR_RANGE, "bad n/kmax");
+  if (n == 0) {
+    *count = 1;
+    return GPA_OK;
+  }
+  std::vector<std::vector<unsigned __int128>> cnt;
+  rgs_counts(n, kmax, cnt);
+  unsigned __int128 t = cnt[1][1];
+  if (t >> 64) return gpa_fail(GPA_ERR_RANGE, "count exceeds 2^64");
+  *count = (uint64_t)t;
+  return GPA_OK;
+}
+
+extern "C" int32_t gpa_unrank_rgs(int32_t n, int32_t kmax, uint64_t rank, uint8_t* rgs) {
+  if (!rgs && n > 0) return gpa_fail(GPA_ERR_ARG, "NULL rgs");
+  if (n < 0 || n > GPA_NMAX || kmax < 1 || kmax > GPA_NMAX) return gpa_fail(GPA_ERR_RANGE, "bad n/kmax");
+  if (n == 0) return rank == 0 ? GPA_OK : gpa_fail(GPA_ERR_RANGE, "rank out of range");
+  std::vector<std::vector<unsigned __int128>> cnt;
+  rgs_counts(n, kmax, cnt);
+  if ((unsigned __int128)rank >= cnt[1][1]) return gpa_fail(GPA_ERR_RANGE, "rank out of range");
+  unsigned __int128 r = rank;
+  rgs[0] = 0;
+  int used = 1;
+  for (int i = 1; i < n; i++) {
+    const int top = used < kmax ? used : kmax - 1;
+    for (int b = 0; b <= top; b++) {
+      const int nu = b + 1 > used ? b + 1 : used;
+      unsigned __int128 c = cnt[(size_t)i + 1][(size_t)nu];
+      if (r < c) {
+        rgs[i] = (uint8_t)b;
+        used = nu;
+        break;
+      }
+      r -= c;
+    }
+  }
+  return GPA_OK;
+}

@@ -1,0 +1,124 @@
+"""The C ABI on the host (no GPU): exported symbols, validation, enumeration."""
+import ctypes
+import itertools
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2105_10312_gb300 as gpa
+import refs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            names += re.findall(r"^\s*int32_t\s+(gpa_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_entry_point():
+    names = _declared_functions()
+    assert len(names) >= 15
+    lib = ctypes.CDLL(gpa.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_header_documents_every_entry_point():
+    text = open(os.path.join(ROOT, "include", "gpa.h")).read()
+    for n in _declared_functions():
+        i = re.search(r"^\s*int32_t\s+" + n + r"\s*\(", text, flags=re.M).start()
+        before = text[max(0, i - 400):i]
+        assert "/*" in before or "*/" in before, n
+
+
+def test_ctx_create_without_gpu_fails_cleanly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    code = gpa.lib().gpa_ctx_create(0, None, ctypes.byref(h))
+    assert code in (gpa.ERR_CUDA, gpa.ERR_ARG)
+    buf = ctypes.create_string_buffer(256)
+    assert gpa.lib().gpa_last_error(buf, 256) == 0 and buf.value
+
+
+def test_host_validation_bounds():
+    s = gpa.gen_tasksets(seed=1, nsets=20, n_min=0, n_max=12)
+    assert gpa.validate(s, M=80)[0] == gpa.OK
+    for col, idx, val in (("D", 3, 0), ("T", 5, 2**31), ("A", 2, -1), ("B", 4, 2**36 + 1), ("type", 1, 2)):
+        bad = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in s.items()}
+        if col == "D":
+            bad["D"][idx] = val
+        elif col == "T":
+            bad["T"][idx] = val
+            bad["D"][idx] = 1
+        else:
+            bad[col][idx] = val
+        code, bad_set = gpa.validate(bad, M=80)
+        assert code == gpa.ERR_RANGE
+        assert bad["set_off"][bad_set] <= idx < bad["set_off"][bad_set + 1]
+    # D > T
+    bad = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in s.items()}
+    bad["D"][0] = bad["T"][0] + 1
+    assert gpa.validate(bad, M=80)[0] == gpa.ERR_RANGE
+    # model bounds: k < 1000 (an inflation factor below 1), g not dividing M, M too large
+    assert gpa.validate(s, M=80, k_c_pm=999)[0] == gpa.ERR_RANGE
+    assert gpa.validate(s, M=81, g=2)[0] == gpa.ERR_RANGE
+    assert gpa.validate(s, M=1025)[0] == gpa.ERR_RANGE
+
+
+def test_composition_count_and_unrank_lexicographic():
+    assert gpa.enumerate_partitions(8, 2, 2) == 7
+    assert gpa.enumerate_partitions(20, 1, 4) == sum(math.comb(19, k - 1) for k in range(1, 5))
+    for Mu, k in ((8, 2), (7, 3), (10, 4), (6, 6), (5, 1)):
+        want = list(refs.compositions(Mu, k))
+        got = [tuple(gpa.unrank_composition(Mu, k, r)) for r in range(len(want))]
+        assert got == want
+        with pytest.raises(gpa.GpaError):
+            gpa.unrank_composition(Mu, k, len(want))
+
+
+def test_rgs_count_and_unrank_lexicographic():
+    def all_rgs(n, kmax):
+        out = []
+        for labels in itertools.product(range(kmax), repeat=n):
+            r = refs.rgs_of(labels)
+            if tuple(labels) == r:
+                out.append(r)
+        return sorted(out)
+    assert gpa.count_rgs(12, 4) == 700075
+    for n, kmax in ((1, 1), (4, 2), (5, 3), (6, 4), (7, 7)):
+        want = all_rgs(n, kmax)
+        assert gpa.count_rgs(n, kmax) == len(want)
+        got = [tuple(int(x) for x in gpa.unrank_rgs(n, kmax, r)) for r in range(len(want))]
+        assert got == want
+
+
+def test_generator_is_deterministic_and_shaped():
+    a = gpa.gen_tasksets(seed=7, nsets=300, n_min=4, n_max=64, U_steps=60, U_lo_ppm=100000, U_hi_ppm=6000000,
+                         mu_dist="BETA25", deadline_pm=750, nthreads=1)
+    b = gpa.gen_tasksets(seed=7, nsets=300, n_min=4, n_max=64, U_steps=60, U_lo_ppm=100000, U_hi_ppm=6000000,
+                         mu_dist="BETA25", deadline_pm=750, nthreads=5)
+    for k in ("set_off", "T", "D", "A", "B", "u_ppm", "type", "C1"):
+        assert np.array_equal(a[k], b[k]), k
+    n = np.diff(a["set_off"])
+    assert n.min() >= 4 and n.max() <= 64
+    assert (a["D"] == a["T"] * 750 // 1000).all()
+    assert (a["T"] >= 10000).all() and (a["T"] <= 1000000).all()
+    # Beta(2,5) intensity with prm = 0.5: P(memory) = 7/64
+    frac = a["type"].mean()
+    assert 0.07 < frac < 0.15
+    # stepped total utilisation: U = 0.1 (s mod 60 + 1)
+    C1, T = a["C1"], a["T"]
+    for s in range(0, 300, 37):
+        o, e = a["set_off"][s], a["set_off"][s + 1]
+        U = (C1[o:e] / T[o:e]).sum()
+        assert abs(U - 0.1 * (s % 60 + 1)) < 0.02 * (e - o) / 10 + 0.01
