@@ -1,0 +1,424 @@
+#!/usr/bin/env python
+"""Benchmark of the contention-aware partition/allocation path on GB300.
+
+Default workload (the batching configuration): 100 000 synthetic task sets of
+16..32 tasks (uniform) on an 80-SM GPU, U ~ U[0.5, 3.0], D = 0.75 T; one step
+is one gpa_allocate pass (the paper's partition-and-allocate heuristic, SMS
+order, no ACT pre-pass) over the whole batch: the persistent fast kernel plus
+the merge kernel, replayed from a CUDA graph.  Metric: task sets decided per
+second (whole job, all ranks); candidate merges evaluated per second is
+reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload batch|sweep|exhaustive|single|paper50]
+
+Under torchrun each rank decides its own batch (seed offset by rank: weak
+scaling, no data-path collective); the timed region is bracketed by a barrier
+and a device synchronize, and the step time is the max over ranks.  The L2
+(129 MB) is flushed between timed steps by writing a 512 MB buffer and then
+reading a second 256 MB one (so the L2 holds clean lines, none of the inputs).
+``--impl reference`` times the CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2105_10312_gb300 import shard  # noqa: E402
+from paper_2105_10312_gb300 import workloads as W  # noqa: E402
+
+METRIC = "candidate allocations tested/sec, tasksets decided/sec (1 GB300); serve p50/p99 ms"
+
+DESCR = {
+    "batch": "batching: 100000 task sets x U{16..32} tasks, 80 SMs, U~U[0.5,3.0], D=0.75T; heuristic SMS/INA per set",
+    "sweep": "sweep: 1000000 task sets x U{4..64} tasks, 148 SMs, U=0.1..6.0 step 0.1, Beta(2,5) intensity; heuristic",
+    "sweep1g": "sweep: 1000000 task sets x U{4..64} tasks, 148 SMs, U=0.1..6.0 step 0.1, Beta(2,5) intensity; 1G baseline",
+    "exhaustive": "exhaustive: 20000 task sets x 12 tasks, 20 TPC units, 1..4 partitions; exact optimum per set",
+    "paper50": "paper setting: 3400 task sets x 50 tasks, 68 SMs, U=2..68 step 2, D=0.75T; heuristic SMS/INA",
+}
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("k_alloc.cu", "gpa_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2105_10312_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", f"alloc_fast_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.]+)", text)
+    h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    if not m or not h or h.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+def gpu_id_for_smi(local):
+    """nvidia-smi id of the CUDA device `local` (UUID when torch exposes it)."""
+    try:
+        import torch
+        u = str(torch.cuda.get_device_properties(local).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        if vis:
+            ids = [x.strip() for x in vis.split(",") if x.strip()]
+            if local < len(ids):
+                return ids[local]
+        return str(local)
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline_oracle(sets, md, policy, act, target_wall=2.0, max_wall=20.0):
+    """The CPU oracle as it stands, on the host cores, over repeated full
+    passes of the same workload (bounded)."""
+    import oracle
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    passes = 0
+    nsets = len(sets["set_off"]) - 1
+    while True:
+        oracle.allocate(sets, md["M"], md["g"], md["k_c_pm"], md["k_m_pm"], policy=policy, act=act,
+                        nthreads=threads)
+        passes += 1
+        el = time.perf_counter() - t0
+        if el >= target_wall or el >= max_wall:
+            break
+    return {"value": passes * nsets / el, "unit": "tasksets/s", "cores": threads, "kind": "oracle",
+            "sample": f"{passes} full pass(es) over the {nsets}-set batch, {threads} threads, {el:.2f} s wall"}
+
+
+def build_workload(name, rank, nsets_override=None):
+    import paper_2105_10312_gb300 as gpa
+    base = "sweep" if name == "sweep1g" else name
+    p = W.gen_params(base)
+    p["seed"] = shard.rank_seed(p["seed"], rank)
+    if nsets_override:
+        p["nsets"] = nsets_override
+    s = gpa.gen_tasksets(**p)
+    return s, W.model(base)
+
+
+def policy_of(name):
+    if name == "sweep1g":
+        return "ONE_GPU", False
+    return "SMS", False
+
+
+def run_reference(args):
+    rank, world, _ = shard.dist_env()
+    if rank != 0:
+        return 0
+    sets, md = build_workload(args.workload, 0, args.nsets)
+    policy, act = policy_of(args.workload)
+    import oracle
+    threads = os.cpu_count() or 1
+    nsets = len(sets["set_off"]) - 1
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle.allocate(sets, md["M"], md["g"], md["k_c_pm"], md["k_m_pm"], policy=policy, act=act, nthreads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.allocate(sets, md["M"], md["g"], md["k_c_pm"], md["k_m_pm"], policy=policy, act=act, nthreads=threads)
+    el = time.perf_counter() - t0
+    v = args.steps * nsets / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "tasksets/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": DESCR.get(args.workload, args.workload), "nsets": nsets, "M": md["M"],
+                   "policy": policy, "act": act},
+        "cpu_baseline": {"value": v, "unit": "tasksets/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{args.steps} full pass(es) over the {nsets}-set batch"},
+        "e2e": {"value": v, "unit": "tasksets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+
+    import paper_2105_10312_gb300 as gpa
+
+    rank, world, local = shard.dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    sets, md = build_workload(args.workload, rank, args.nsets)
+    policy, act = policy_of(args.workload)
+    nsets = len(sets["set_off"]) - 1
+    ntasks = int(sets["set_off"][-1])
+    d = gpa.to_device(sets, dev)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.synchronize(dev)
+    ctx = gpa.Context(local, stream=stream)
+    ctx.set_option("AUTOTUNE", 0 if args.no_autotune else 1)
+    ctx.set_option("GRAPH", 1)
+    ctx.set_option("PROFILE", 1)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+    flush_rd = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+
+    def flush_l2(i):
+        flush.fill_(i)
+        return flush_rd.sum()
+    kc, km = md["k_c_pm"], md["k_m_pm"]
+
+    if args.workload == "exhaustive":
+        wp = W.WORKLOADS["exhaustive"]
+        out = ctx.best_result(d, wp["kmax"])
+
+        def step():
+            ctx.search_best(d, **md, kmin=wp["kmin"], kmax=wp["kmax"], out=out)
+    else:
+        out = ctx.alloc_result(d)
+
+        def step():
+            ctx.allocate(d, **md, policy=policy, act=act, out=out)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 0)):
+            step()
+        torch.cuda.synchronize(dev)
+        ctx.sync()
+
+        shard.barrier()
+        torch.cuda.synchronize(dev)
+        sampler = ClockSampler(gpu_id_for_smi(local))
+        sampler.start()
+        launches0 = ctx.launch_count()
+        step_ms, kern_ms, kern2_ms = [], [], []
+        t_wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush_l2(i)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            t = ctx.last_timing()
+            if t:
+                kern_ms.append(t[0])
+                if len(t) > 1:
+                    kern2_ms.append(t[1])
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t_wall0
+        launches = ctx.launch_count() - launches0
+        clocks = sampler.stop()
+        ctx.sync()
+    shard.barrier()
+
+    mean_ms = float(np.mean(step_ms))
+    max_ms = shard.max_over_ranks(mean_ms)
+    total_sets = shard.sum_over_ranks(nsets)
+    if args.workload == "exhaustive":
+        cand = 4095 + 700075  # subset size searches + RGS keys per set
+        cand_total = shard.sum_over_ranks(cand * nsets)
+    else:
+        cand_total = shard.sum_over_ranks(float(out["n_tests"].sum().item()) if out.get("n_tests") is not None else 0)
+    value = total_sets / (max_ms / 1000.0)
+
+    # roofline of the dominant kernel (the fast allocate kernel for the heuristic workloads)
+    hbm_peak, peak_src = read_peaks()
+    roof = None
+    if kern_ms and args.workload != "exhaustive":
+        k_ms = float(np.mean(kern_ms))
+        if policy == "ONE_GPU":
+            alg_bytes = 41 * ntasks + 8 * (nsets + 1) + 23 * nsets + 2 * ntasks + ntasks
+        else:
+            # per task: T, D, A, B, u (5 x 8 B) + type (1 B) read; part (1 B) + size (2 B) written;
+            # per set: offset (8 B) read; verdict, reason, n_parts, Pi, W, n_tests (22 B) written
+            alg_bytes = 44 * ntasks + 30 * nsets
+        achieved = alg_bytes / (k_ms / 1000.0) / 1e9
+        traffic = recorded_traffic(args.workload) if policy != "ONE_GPU" else None
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": traffic, "kernel": "alloc_fast" if policy != "ONE_GPU" else "one_gpu",
+                "kernel_ms": k_ms, "algorithmic_bytes": alg_bytes, "peak_source": peak_src + " hbm_gbs"}
+    elif kern_ms:
+        roof = {"bound": "alu", "kernel": "search_sets", "kernel_ms": float(np.mean(kern_ms)), "achieved": None,
+                "peak": None, "unit": None, "frac": None, "traffic": None}
+
+    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    e2e = None
+    if args.e2e_steps > 0 and args.workload != "exhaustive":
+        hs = {}
+        for k in ("set_off", "T", "D", "A", "B", "u_ppm", "type"):
+            t = torch.from_numpy(np.ascontiguousarray(sets[k])).pin_memory()
+            hs[k] = t.numpy()
+        hs["n_max"] = sets["n_max"]
+        hout = {}
+        for k, v in ctx.alloc_result(sets).items():
+            hout[k] = torch.from_numpy(v).pin_memory().numpy() if v is not None else None
+        ctx_h = gpa.Context(local, stream=stream)
+        ctx_h.set_option("GRAPH", 1)
+        with torch.cuda.stream(stream):
+            ctx_h.allocate(hs, **md, policy=policy, act=act, out=hout)
+            times = []
+            for i in range(args.e2e_steps):
+                flush_l2(i)
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                ctx_h.allocate(hs, **md, policy=policy, act=act, out=hout)  # synchronous: H2D, kernels, D2H
+                times.append(time.perf_counter() - t0)
+        ctx_h.close()
+        e2e_t = shard.max_over_ranks(float(np.mean(times)))
+        h2d = 8 * (nsets + 1) + 41 * ntasks
+        d2h = 22 * nsets + 3 * ntasks
+        e2e = {"value": total_sets / e2e_t, "unit": "tasksets/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    # the plain form: one launch sequence per task set, on a sample
+    plain = None
+    if args.plain_sample > 0 and args.workload not in ("exhaustive",) and policy != "ONE_GPU":
+        import paper_2105_10312_gb300.gen as G
+        sub = G.subset(sets, np.arange(min(args.plain_sample, nsets)))
+        ds = gpa.to_device(sub, dev)
+        c2 = gpa.Context(local, stream=stream)
+        c2.set_option("PER_SET_LAUNCH", 1)
+        with torch.cuda.stream(stream):
+            o2 = c2.alloc_result(ds)
+            c2.allocate(ds, **md, policy=policy, act=act, out=o2)
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c2.allocate(ds, **md, policy=policy, act=act, out=o2)
+            e1.record(stream)
+            e1.synchronize()
+        c2.close()
+        nsub = len(sub["set_off"]) - 1
+        plain = {"tasksets_per_s": nsub / (e0.elapsed_time(e1) / 1000.0), "sample_sets": nsub,
+                 "launches_per_set": 2}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload != "exhaustive":
+        cpu = cpu_baseline_oracle(sets, md, policy, act)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "tasksets/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": DESCR.get(args.workload, args.workload), "nsets_per_gpu": nsets,
+                       "tasks_per_gpu": ntasks, "M": md["M"], "g": md["g"], "policy": policy, "act": act,
+                       "l2": "flushed between timed steps (512 MB write, then 256 MB read); inputs 109 MB < 129 MB L2",
+                       "parallelism": f"{world} independent shard(s)", "launch": "persistent + CUDA graph"},
+            "candidates_tested_per_s": cand_total / (max_ms / 1000.0),
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clocks, "per_set_launch": plain, "wall_s_timed": wall,
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gpa", "reference"], default="gpa")
+    ap.add_argument("--workload", choices=sorted(DESCR), default="batch")
+    ap.add_argument("--nsets", type=int, default=0, help="override the workload's set count (profiling)")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--plain-sample", type=int, default=2000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

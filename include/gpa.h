@@ -135,9 +135,17 @@ enum {
   GPA_OPT_FAST_WARPS = 3,     /* force warps per CTA of the fast allocate kernel (0 = tuned/default) */
   GPA_OPT_FAST_CHUNK = 4,     /* force task sets per work-queue ticket (0 = tuned/default) */
   GPA_OPT_FAST_BLOCKS = 5,    /* force CTAs of the persistent grid (0 = tuned/default) */
-  GPA_OPT_PER_SET_LAUNCH = 6  /* 1: the plain form, one launch sequence per task set (comparison only) */
+  GPA_OPT_PER_SET_LAUNCH = 6, /* 1: the plain form, one launch sequence per task set (comparison only) */
+  GPA_OPT_PROFILE = 7         /* 1: record CUDA events around each kernel of every call (also inside
+                                 captured graphs) so that gpa_ctx_last_timing can report them */
 };
 int32_t gpa_ctx_set_option(gpa_ctx* ctx, int32_t option, int64_t value);
+
+/* Device time (ms) of each kernel of the last call made with GPA_OPT_PROFILE
+ * on, in launch order (gpa_allocate: the fast kernel, then the merge kernel;
+ * every other entry point: its one kernel).  Waits for that call's work.
+ * ms[0 .. *count) are written, at most n of them. */
+int32_t gpa_ctx_last_timing(gpa_ctx* ctx, float* ms, int32_t n, int32_t* count);
 
 /* --------------------------------------------------------------- task sets */
 

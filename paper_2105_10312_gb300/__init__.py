@@ -27,7 +27,8 @@ OK, ERR_ARG, ERR_RANGE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_NOTFOUND
 HOST, DEVICE = 0, 1
 POLICY = {"SMS": 0, "BF": 1, "ONE_GPU": 2}
 REASON = {"OK": 0, "LEMMA1": 1, "LEMMA2": 2, "NO_MERGE": 3, "TEST": 4, "INVALID": 5}
-OPT = {"AUTOTUNE": 1, "GRAPH": 2, "FAST_WARPS": 3, "FAST_CHUNK": 4, "FAST_BLOCKS": 5, "PER_SET_LAUNCH": 6}
+OPT = {"AUTOTUNE": 1, "GRAPH": 2, "FAST_WARPS": 3, "FAST_CHUNK": 4, "FAST_BLOCKS": 5, "PER_SET_LAUNCH": 6,
+       "PROFILE": 7}
 NMAX, MMAX, SEARCH_NMAX, SEARCH_KMAX = 128, 1024, 14, 8
 
 _vp = ctypes.c_void_p
@@ -87,6 +88,8 @@ def _set_signatures(L):
     L.gpa_ctx_sync.argtypes = [_vp]
     L.gpa_ctx_launch_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
     L.gpa_ctx_set_option.argtypes = [_vp, ctypes.c_int32, ctypes.c_int64]
+    L.gpa_ctx_last_timing.argtypes = [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
+                                      ctypes.POINTER(ctypes.c_int32)]
     L.gpa_last_error.argtypes = [ctypes.c_char_p, ctypes.c_int32]
     L.gpa_validate.argtypes = [ctypes.POINTER(Tasksets), ctypes.POINTER(Model), ctypes.POINTER(ctypes.c_int64)]
     L.gpa_build_wcet_tables.argtypes = [_vp, ctypes.POINTER(Tasksets), ctypes.POINTER(Model), _vp, _vp]
@@ -232,6 +235,13 @@ class Context:
         out = ctypes.c_int64()
         _check(lib().gpa_ctx_launch_count(self._h, ctypes.byref(out)))
         return out.value
+
+    def last_timing(self):
+        """Kernel times (ms) of the last call made with the PROFILE option on."""
+        ms = (ctypes.c_float * 4)()
+        cnt = ctypes.c_int32()
+        _check(lib().gpa_ctx_last_timing(self._h, ms, 4, ctypes.byref(cnt)))
+        return [ms[i] for i in range(cnt.value)]
 
     @property
     def handle(self):

@@ -19,6 +19,7 @@ struct CtxBuf {
 struct CachedGraph {
   cudaGraphExec_t exec;
   long long kernels;  // kernel nodes in the graph
+  gpa::Prof prof;     // timing events captured as graph nodes (prof.used == 0 without profiling)
 };
 
 struct ServeState;
@@ -38,6 +39,9 @@ struct gpa_ctx {
   bool use_graph = false;
   bool per_set_launch = false;
   bool graphs_dirty = false;
+  bool profile = false;
+  gpa::Prof prof{};                          // timing events of direct (non-graph) calls
+  const gpa::Prof* last_prof = nullptr;      // events of the last profiled call
   gpa::LaunchShape force_fast{0, 0, 0};
   std::map<std::string, gpa::LaunchShape> tuned;
   std::map<std::string, CachedGraph> graphs;

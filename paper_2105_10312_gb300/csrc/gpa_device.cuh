@@ -62,11 +62,16 @@ __device__ __forceinline__ unsigned int wcet(unsigned long long A, unsigned long
   return (unsigned int)(div_by_1e6m(x - 1ull, md) + 1ull);
 }
 
-// Validation bounds of gpa.h for one task.
+// Validation bounds of gpa.h for one task: 1 <= D <= T <= 2^31 - 1,
+// A, B >= 0, 1 <= A + B <= 2^36, 0 <= u < 2^32, type in {0, 1}.  Written
+// with unsigned ranges (a negative value wraps to a huge one), so each bound
+// is one 64-bit compare.
 __device__ __forceinline__ bool task_valid(long long T, long long D, long long A, long long B, long long u,
                                            unsigned int type) {
-  return D >= 1 && D <= T && T <= 2147483647LL && A >= 0 && B >= 0 && A + B >= 1 && A + B <= (1LL << 36) &&
-         u >= 0 && u <= 4294967295LL && type <= 1u;
+  const unsigned long long uT = (unsigned long long)T, uD = (unsigned long long)D;
+  const unsigned long long uA = (unsigned long long)A, uB = (unsigned long long)B;
+  return (uT >> 31) == 0ull && uD - 1ull < uT && uA <= (1ull << 36) && uB <= (1ull << 36) &&
+         uA + uB - 1ull < (1ull << 36) && ((unsigned long long)u >> 32) == 0ull && type <= 1u;
 }
 
 // Lemma 2 in closed form: smallest multiple of g in [g, M] with
@@ -83,6 +88,28 @@ __device__ __forceinline__ unsigned int lemma2_size(unsigned long long A, unsign
   if (m1 < 1ull) m1 = 1ull;
   unsigned long long mg = (m1 + g - 1ull) / g * g;
   return mg <= M ? (unsigned int)mg : 0u;
+}
+
+// The same size without 64-bit division: if A <= M (1000 D - B), the
+// quotient q = ceil(A / den) is at most M <= 1024, so a float estimate is
+// within one of it and two exact integer checks settle it.
+__device__ __forceinline__ unsigned int lemma2_size_fast(unsigned long long A, unsigned long long B,
+                                                         unsigned long long D, unsigned int M, unsigned int g) {
+  const long long den = (long long)(1000ull * D) - (long long)B;
+  if (den < 0) return 0u;
+  if (A == 0ull) return g <= M ? g : 0u;
+  if (den == 0) return 0u;
+  const unsigned long long ud = (unsigned long long)den;
+  if (A <= ud) return g <= M ? g : 0u;  // one SM already meets the deadline (the common case)
+  if (A > ud * M) return 0u;
+  unsigned int q = (unsigned int)__fdividef((float)A, (float)ud);
+  q = min(max(q, 1u), M);
+  if ((unsigned long long)q * ud < A) q++;                        // estimate too small by one
+  if ((unsigned long long)q * ud < A) q++;
+  if (q > 1u && (unsigned long long)(q - 1u) * ud >= A) q--;      // estimate too large by one
+  if (q > 1u && (unsigned long long)(q - 1u) * ud >= A) q--;
+  const unsigned int mg = (g == 1u) ? q : (q + g - 1u) / g * g;
+  return mg <= M ? mg : 0u;
 }
 
 // One task set staged in shared memory, rows in deadline-monotonic order

@@ -52,6 +52,15 @@ struct AllocQueue {
   unsigned int* err;             // sticky error word
 };
 
+// Optional timing events recorded around kernels (see GPA_OPT_PROFILE).
+struct Prof {
+  cudaEvent_t ev[4];
+  int used;       // events recorded by the last call
+  bool capture;   // recording into a stream capture (graph node)
+};
+
+void prof_mark(Prof* p, cudaStream_t st);
+
 struct LaunchShape {
   int warps_per_block;  // warps per CTA
   int chunk;            // sets per ticket (fast kernel)
@@ -81,20 +90,22 @@ struct Cands {
 // number of kernels it launched to *launches.
 cudaError_t launch_allocate(const DevSets& s, const DevModel& md, const gpa_params& p, const AllocOut& out,
                             const AllocQueue& q, const MagicDivHost* mdiv, const LaunchShape& fast,
-                            const LaunchShape& slow, cudaStream_t st, long long* launches);
+                            const LaunchShape& slow, cudaStream_t st, long long* launches, Prof* prof);
 cudaError_t launch_one_gpu(const DevSets& s, const DevModel& md, const AllocOut& out, const AllocQueue& q,
-                           const MagicDivHost* mdiv, const LaunchShape& shape, cudaStream_t st, long long* launches);
+                           const MagicDivHost* mdiv, const LaunchShape& shape, cudaStream_t st, long long* launches,
+                           Prof* prof);
 // Per-process kernel attribute set-up (dynamic shared memory opt-in).
 cudaError_t alloc_kernels_init();
 cudaError_t search_kernels_init();
 cudaError_t launch_wcet_tables(const DevSets& s, const DevModel& md, long long* Cn, long long* Cc, unsigned int* err,
-                               const MagicDivHost* mdiv, int sm_count, cudaStream_t st, long long* launches);
+                               const MagicDivHost* mdiv, int sm_count, cudaStream_t st, long long* launches,
+                               Prof* prof);
 cudaError_t launch_test_schedulable(const DevSets& s, const DevModel& md, const Cands& c, unsigned char* verdict,
                                     long long* R, unsigned int* err, const MagicDivHost* mdiv, int sm_count,
-                                    cudaStream_t st, long long* launches);
+                                    cudaStream_t st, long long* launches, Prof* prof);
 cudaError_t launch_search_best(const DevSets& s, const DevModel& md, int kmin, int kmax, const BestOut& out,
                                const AllocQueue& q, const MagicDivHost* mdiv, int sm_count, cudaStream_t st,
-                               long long* launches);
+                               long long* launches, Prof* prof);
 
 // Largest dynamic shared memory (bytes) the allocate merge kernel needs per CTA.
 size_t slow_smem_bytes(int warps_per_block);

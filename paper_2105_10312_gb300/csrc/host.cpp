@@ -131,6 +131,11 @@ extern "C" int32_t gpa_ctx_create(int32_t device, void* stream, gpa_ctx** out) {
     gpa_ctx_destroy(c);
     return gpa_cuda_fail(e, "gpa_ctx_create: device allocation");
   }
+  for (int i = 0; i < 4 && e == cudaSuccess; i++) e = cudaEventCreate(&c->prof.ev[i]);
+  if (e != cudaSuccess) {
+    gpa_ctx_destroy(c);
+    return gpa_cuda_fail(e, "gpa_ctx_create: events");
+  }
   static std::once_flag once;
   static cudaError_t init_err = cudaSuccess;
   std::call_once(once, [] {
@@ -145,11 +150,45 @@ extern "C" int32_t gpa_ctx_create(int32_t device, void* stream, gpa_ctx** out) {
   return GPA_OK;
 }
 
+static void destroy_graph(CachedGraph& g) {
+  cudaGraphExecDestroy(g.exec);
+  for (int i = 0; i < 4; i++)
+    if (g.prof.ev[i]) cudaEventDestroy(g.prof.ev[i]);
+}
+
+// The timing events for the next call (nullptr when profiling is off).
+static Prof* begin_prof(gpa_ctx* c) {
+  if (!c->profile) return nullptr;
+  c->prof.used = 0;
+  c->prof.capture = false;
+  c->last_prof = &c->prof;
+  return &c->prof;
+}
+
+extern "C" int32_t gpa_ctx_last_timing(gpa_ctx* c, float* ms, int32_t n, int32_t* count) {
+  if (!c || !count || (n > 0 && !ms)) return gpa_fail(GPA_ERR_ARG, "gpa_ctx_last_timing: NULL argument");
+  *count = 0;
+  const Prof* p = c->last_prof;
+  if (!p || p->used < 2) return GPA_OK;
+  DeviceGuard guard(c->device);
+  cudaError_t e = cudaEventSynchronize(p->ev[p->used - 1]);
+  if (e != cudaSuccess) return gpa_cuda_fail(e, "cudaEventSynchronize");
+  int k = 0;
+  for (int i = 0; i + 1 < p->used && k < n; i++, k++) {
+    e = cudaEventElapsedTime(&ms[k], p->ev[i], p->ev[i + 1]);
+    if (e != cudaSuccess) return gpa_cuda_fail(e, "cudaEventElapsedTime");
+  }
+  *count = k;
+  return GPA_OK;
+}
+
 extern "C" int32_t gpa_ctx_destroy(gpa_ctx* c) {
   if (!c) return GPA_OK;
   DeviceGuard guard(c->device);
   gpa_serve_teardown(c);
-  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+  for (auto& kv : c->graphs) destroy_graph(kv.second);
+  for (int i = 0; i < 4; i++)
+    if (c->prof.ev[i]) cudaEventDestroy(c->prof.ev[i]);
   for (auto& b : c->bufs) cudaFree(b.ptr);
   cudaFree(c->d_mdiv);
   cudaFree(c->d_counters);
@@ -181,7 +220,7 @@ extern "C" int32_t gpa_ctx_set_option(gpa_ctx* c, int32_t opt, int64_t value) {
       c->force_fast.warps_per_block = (int)value;
       break;
     case GPA_OPT_FAST_CHUNK:
-      if (value < 0 || value > 64) return gpa_fail(GPA_ERR_RANGE, "chunk");
+      if (value < 0 || value > 64) return gpa_fail(GPA_ERR_RANGE, "chunk (task sets per tile, <= 64)");
       c->force_fast.chunk = (int)value;
       break;
     case GPA_OPT_FAST_BLOCKS:
@@ -189,6 +228,10 @@ extern "C" int32_t gpa_ctx_set_option(gpa_ctx* c, int32_t opt, int64_t value) {
       c->force_fast.blocks = (int)value;
       break;
     case GPA_OPT_PER_SET_LAUNCH: c->per_set_launch = value != 0; break;
+    case GPA_OPT_PROFILE:
+      c->profile = value != 0;
+      if (!c->profile) c->last_prof = nullptr;
+      break;
     default: return gpa_fail(GPA_ERR_ARG, "gpa_ctx_set_option: unknown option %d", opt);
   }
   return GPA_OK;
@@ -315,7 +358,7 @@ extern "C" int32_t gpa_build_wcet_tables(gpa_ctx* c, const gpa_tasksets* sets, c
   const long long Mu = model->M / model->g;
   if (sets->mem == GPA_DEVICE) {
     cudaError_t e = launch_wcet_tables(dev_sets(sets), md, (long long*)Cn, (long long*)Cc, c->d_err, c->d_mdiv,
-                                       c->sm_count, c->stream, &c->launches);
+                                       c->sm_count, c->stream, &c->launches, begin_prof(c));
     return e == cudaSuccess ? GPA_OK : gpa_cuda_fail(e, "wcet_tables launch");
   }
   HostStage hs;
@@ -324,7 +367,8 @@ extern "C" int32_t gpa_build_wcet_tables(gpa_ctx* c, const gpa_tasksets* sets, c
   long long* dCn = (long long*)ctx_buffer(c, 7, bytes);
   long long* dCc = (long long*)ctx_buffer(c, 8, bytes);
   if (!dCn || !dCc) return gpa_fail(GPA_ERR_NOMEM, "table allocation failed");
-  cudaError_t e = launch_wcet_tables(hs.ds, md, dCn, dCc, c->d_err, c->d_mdiv, c->sm_count, c->stream, &c->launches);
+  cudaError_t e = launch_wcet_tables(hs.ds, md, dCn, dCc, c->d_err, c->d_mdiv, c->sm_count, c->stream, &c->launches,
+                                     begin_prof(c));
   if (e == cudaSuccess && hs.ntasks * Mu > 0) {
     e = cudaMemcpyAsync(Cn, dCn, sizeof(long long) * (size_t)(hs.ntasks * Mu), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess)
@@ -355,7 +399,7 @@ extern "C" int32_t gpa_test_schedulable(gpa_ctx* c, const gpa_tasksets* sets, co
     Cands cc{nc, cands->map_stride, cands->kparts, (const long long*)cands->set, cands->part_of_task,
              cands->size_of_part};
     cudaError_t e = launch_test_schedulable(dev_sets(sets), md, cc, verdict, (long long*)R, c->d_err, c->d_mdiv,
-                                            c->sm_count, c->stream, &c->launches);
+                                            c->sm_count, c->stream, &c->launches, begin_prof(c));
     return e == cudaSuccess ? GPA_OK : gpa_cuda_fail(e, "test_schedulable launch");
   }
   // host path: validate candidates on the host too
@@ -390,7 +434,8 @@ extern "C" int32_t gpa_test_schedulable(gpa_ctx* c, const gpa_tasksets* sets, co
                         cudaMemcpyHostToDevice, s);
   Cands cc{nc, cands->map_stride, cands->kparts, dset, dmap, dsize};
   if (e == cudaSuccess)
-    e = launch_test_schedulable(hs.ds, md, cc, dver, dR, c->d_err, c->d_mdiv, c->sm_count, s, &c->launches);
+    e = launch_test_schedulable(hs.ds, md, cc, dver, dR, c->d_err, c->d_mdiv, c->sm_count, s, &c->launches,
+                                begin_prof(c));
   if (e == cudaSuccess) e = cudaMemcpyAsync(verdict, dver, (size_t)nc, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && R)
     e = cudaMemcpyAsync(R, dR, sizeof(long long) * (size_t)(nc * cands->map_stride), cudaMemcpyDeviceToHost, s);
@@ -400,7 +445,11 @@ extern "C" int32_t gpa_test_schedulable(gpa_ctx* c, const gpa_tasksets* sets, co
 
 // --------------------------------------------------------------- allocate
 
-static LaunchShape default_fast(const gpa_ctx* c) { return LaunchShape{8, 2, c->sm_count * 8}; }
+// blocks = 0: the launcher sizes the grid to the kernel's occupancy x SMs
+static LaunchShape default_fast(const gpa_ctx* c) {
+  (void)c;
+  return LaunchShape{8, 2, 0};
+}
 static LaunchShape default_slow(const gpa_ctx* c) { return LaunchShape{4, 1, c->sm_count * 2}; }
 
 static LaunchShape fast_shape(gpa_ctx* c, const DevSets& ds, const DevModel& md, const gpa_params& p) {
@@ -421,13 +470,13 @@ std::string tune_key(const DevSets& ds, const DevModel& md, const gpa_params& p)
 }
 
 static cudaError_t run_allocate(gpa_ctx* c, const DevSets& ds, const DevModel& md, const gpa_params& p,
-                                const AllocOut& out, const LaunchShape& fast) {
+                                const AllocOut& out, const LaunchShape& fast, Prof* prof) {
   AllocQueue q{c->d_counters, c->d_slow, c->d_err};
   if (p.policy == GPA_POLICY_ONE_GPU) {
     LaunchShape sh{8, 1, c->sm_count * 4};
-    return launch_one_gpu(ds, md, out, q, c->d_mdiv, sh, c->stream, &c->launches);
+    return launch_one_gpu(ds, md, out, q, c->d_mdiv, sh, c->stream, &c->launches, prof);
   }
-  return launch_allocate(ds, md, p, out, q, c->d_mdiv, fast, default_slow(c), c->stream, &c->launches);
+  return launch_allocate(ds, md, p, out, q, c->d_mdiv, fast, default_slow(c), c->stream, &c->launches, prof);
 }
 
 // Autotuner: time the candidate shapes of the fast kernel on this batch
@@ -437,7 +486,7 @@ static void autotune_allocate(gpa_ctx* c, const DevSets& ds, const DevModel& md,
   const std::string key = tune_key(ds, md, p);
   if (c->tuned.count(key)) return;
   static const int warps_opts[] = {4, 8};
-  static const int chunk_opts[] = {1, 2, 4, 8};
+  static const int chunk_opts[] = {1, 2, 3, 4, 8};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -445,11 +494,11 @@ static void autotune_allocate(gpa_ctx* c, const DevSets& ds, const DevModel& md,
   LaunchShape best = default_fast(c);
   for (int w : warps_opts)
     for (int ch : chunk_opts) {
-      LaunchShape sh{w, ch, c->sm_count * (2048 / (w * 32))};
+      LaunchShape sh{w, ch, 0};
       float tot = 0.f;
       for (int rep = 0; rep < 3; rep++) {
         cudaEventRecord(e0, c->stream);
-        run_allocate(c, ds, md, p, out, sh);
+        run_allocate(c, ds, md, p, out, sh, nullptr);
         cudaEventRecord(e1, c->stream);
         cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -498,7 +547,8 @@ static int32_t allocate_device(gpa_ctx* c, const DevSets& ds, const DevModel& md
       LaunchShape one_shape{1, 1, 1};
       AllocQueue q{c->d_counters, c->d_slow, c->d_err};
       LaunchShape slow1{1, 1, 1};
-      cudaError_t e = launch_allocate(one, md, p, o1, q, c->d_mdiv, one_shape, slow1, c->stream, &c->launches);
+      cudaError_t e =
+          launch_allocate(one, md, p, o1, q, c->d_mdiv, one_shape, slow1, c->stream, &c->launches, nullptr);
       if (e != cudaSuccess) return gpa_cuda_fail(e, "per-set allocate launch");
     }
     return GPA_OK;
@@ -507,18 +557,26 @@ static int32_t allocate_device(gpa_ctx* c, const DevSets& ds, const DevModel& md
   const LaunchShape fast = fast_shape(c, ds, md, p);
   if (c->use_graph) {
     if (c->graphs_dirty) {
-      for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+      for (auto& kv : c->graphs) destroy_graph(kv.second);
       c->graphs.clear();
+      c->last_prof = nullptr;
       c->graphs_dirty = false;
     }
-    const std::string key = graph_key(ds, md, p, out, fast);
+    const std::string key = graph_key(ds, md, p, out, fast) + (c->profile ? "|prof" : "");
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
+      Prof gp{};
+      gp.capture = true;
+      if (c->profile)
+        for (int i = 0; i < 4; i++) {
+          cudaError_t ee = cudaEventCreate(&gp.ev[i]);
+          if (ee != cudaSuccess) return gpa_cuda_fail(ee, "graph timing events");
+        }
       cudaGraph_t g = nullptr;
       cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
-      if (e != cudaSuccess) return gpa_cuda_fail(e, "cudaStreamBeginCapture");
+      if (e != cudaSuccess) return gpa_cuda_fail(e, "cudaStreamBeginCapture (graphs need a non-default stream)");
       long long before = c->launches;
-      cudaError_t le = run_allocate(c, ds, md, p, out, fast);
+      cudaError_t le = run_allocate(c, ds, md, p, out, fast, c->profile ? &gp : nullptr);
       long long kernels = c->launches - before;
       c->launches = before;
       e = cudaStreamEndCapture(c->stream, &g);
@@ -531,14 +589,15 @@ static int32_t allocate_device(gpa_ctx* c, const DevSets& ds, const DevModel& md
       e = cudaGraphInstantiate(&exec, g, 0);
       cudaGraphDestroy(g);
       if (e != cudaSuccess) return gpa_cuda_fail(e, "cudaGraphInstantiate");
-      it = c->graphs.emplace(key, CachedGraph{exec, kernels}).first;
+      it = c->graphs.emplace(key, CachedGraph{exec, kernels, gp}).first;
     }
     cudaError_t e = cudaGraphLaunch(it->second.exec, c->stream);
     if (e != cudaSuccess) return gpa_cuda_fail(e, "cudaGraphLaunch");
     c->launches += it->second.kernels;
+    c->last_prof = it->second.prof.used ? &it->second.prof : nullptr;
     return GPA_OK;
   }
-  cudaError_t e = run_allocate(c, ds, md, p, out, fast);
+  cudaError_t e = run_allocate(c, ds, md, p, out, fast, begin_prof(c));
   return e == cudaSuccess ? GPA_OK : gpa_cuda_fail(e, "allocate launch");
 }
 
@@ -611,7 +670,7 @@ extern "C" int32_t gpa_search_best(gpa_ctx* c, const gpa_tasksets* sets, const g
   if (sets->mem == GPA_DEVICE) {
     BestOut out{r->feasible, (long long*)r->W, r->sum_minm, r->n_blocks, r->spare, r->rgs, r->minm_block};
     cudaError_t e = launch_search_best(dev_sets(sets), md, kmin, kmax, out, q, c->d_mdiv, c->sm_count, c->stream,
-                                       &c->launches);
+                                       &c->launches, begin_prof(c));
     return e == cudaSuccess ? GPA_OK : gpa_cuda_fail(e, "search_best launch");
   }
   HostStage hs;
@@ -624,7 +683,8 @@ extern "C" int32_t gpa_search_best(gpa_ctx* c, const gpa_tasksets* sets, const g
   if (!out.feasible || !out.W || !out.sum_minm || !out.n_blocks || !out.spare || !out.rgs || !out.minm_block)
     return gpa_fail(GPA_ERR_NOMEM, "result staging failed");
   cudaStream_t s = c->stream;
-  cudaError_t e = launch_search_best(hs.ds, md, kmin, kmax, out, q, c->d_mdiv, c->sm_count, s, &c->launches);
+  cudaError_t e =
+      launch_search_best(hs.ds, md, kmin, kmax, out, q, c->d_mdiv, c->sm_count, s, &c->launches, begin_prof(c));
   if (e == cudaSuccess) e = cudaMemcpyAsync(r->feasible, out.feasible, (size_t)ns, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(r->W, out.W, 8 * (size_t)ns, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(r->sum_minm, out.sum_minm, 4 * (size_t)ns, cudaMemcpyDeviceToHost, s);

@@ -2,9 +2,9 @@
 // baseline, and the persistent work queue that batches them.
 //
 // Two persistent kernels run back to back on the context stream:
-//  * alloc_fast: one warp per task set, tasks in lanes, registers only.  It
-//    validates the set, sizes every singleton partition by Lemma 2 in closed
-//    form and sums Pi.  When Pi <= M the heuristic ends at its first exit
+//  * alloc_fast: a warp streams a few consecutive task sets at a time,
+//    registers only.  It validates each set, sizes every singleton partition
+//    by Lemma 2 in closed form and sums Pi.  When Pi <= M the heuristic ends at its first exit
 //    test (Lemma 3) with the singleton partitions, so the set is decided
 //    here (Lemma 1 cannot reject then: m C^n(m) >= C^n(1) and C^n(m) <= T
 //    give sum C^n(1)/T <= Pi).  Otherwise the set index is appended to a
@@ -58,74 +58,127 @@ __device__ __forceinline__ void write_empty(long long s, long long o, int n, uns
 }
 
 // ------------------------------------------------------------- fast kernel
+//
+// Each warp takes K consecutive task sets at a time (grid-stride over chunks
+// of K sets); their tasks are one contiguous range, which the lanes stream in
+// coalesced 32-task slices, U slices (6 columns each) in flight together.
+// Every task gets its Lemma 2 size in registers; a lane finds the set of its
+// task with K-1 compares against the chunk's offsets and adds its values to
+// per-set partial sums held in registers; K full-warp reductions finish the
+// chunk.  Sets whose singleton partitions already fit (Pi <= M) are decided
+// here; the others are appended to the merge kernel's queue, which rewrites
+// their per-task outputs.
 
-__global__ void __launch_bounds__(256) alloc_fast(DevSets S, DevModel md, AllocOut out, AllocQueue q, int chunk) {
+template <int K, int U>
+__global__ void __launch_bounds__(256) alloc_fast(DevSets S, DevModel md, AllocOut out, AllocQueue q) {
   const int lane = threadIdx.x & 31;
-  for (;;) {
-    long long s0 = 0;
-    if (lane == 0) s0 = (long long)atomicAdd(q.counters + 0, (unsigned long long)chunk);
-    s0 = __shfl_sync(kFull, s0, 0);
-    if (s0 >= S.nsets) break;
-    const long long s1 = min(s0 + (long long)chunk, S.nsets);
-    for (long long s = s0; s < s1; s++) {
-      const long long o = __ldg(S.set_off + s);
-      const long long n = __ldg(S.set_off + s + 1) - o;
-      if (n < 0 || n > S.n_max || n > kNmax) {
-        write_invalid(s, o, n < 0 ? 0 : n, out, q.err);
-        continue;
-      }
-      bool ok = true;
-      unsigned int mm[kWords];
-      unsigned long long usum = 0;
-      int pi = 0;
-      bool none = false;
+  const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const unsigned M = (unsigned)md.M, g = (unsigned)md.g;
+  // the offsets of the next chunk are loaded one iteration ahead
+  long long offv_next = 0;
+  {
+    const long long b0 = warp0 * K;
+    if (b0 < S.nsets && lane <= (int)min((long long)K, S.nsets - b0)) offv_next = __ldg(S.set_off + b0 + lane);
+  }
+  for (long long base = warp0 * K; base < S.nsets; base += nwarps * K) {
+    const int ns = (int)min((long long)K, S.nsets - base);
+    const long long offv = offv_next;
+    {
+      const long long bn = base + nwarps * K;
+      if (bn < S.nsets && lane <= (int)min((long long)K, S.nsets - bn)) offv_next = __ldg(S.set_off + bn + lane);
+    }
+    long long o[K + 1];
 #pragma unroll
-      for (int c = 0; c < kWords; c++) {
-        const int t = c * 32 + lane;
-        mm[c] = 0;
-        if (t < n) {
-          long long Tt = __ldg(S.T + o + t), Dt = __ldg(S.D + o + t), At = __ldg(S.A + o + t),
-                    Bt = __ldg(S.B + o + t), ut = __ldg(S.u + o + t);
-          unsigned int yt = __ldg(S.type + o + t);
-          ok = ok && task_valid(Tt, Dt, At, Bt, ut, yt);
-          mm[c] = lemma2_size((unsigned long long)At, (unsigned long long)Bt, (unsigned long long)Dt,
-                              (unsigned)md.M, (unsigned)md.g);
-          none = none || mm[c] == 0u;
-          pi += (int)mm[c];
-          usum += (unsigned long long)ut;
+    for (int k = 0; k <= K; k++) o[k] = __shfl_sync(kFull, offv, k <= ns ? k : ns);
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      const long long n = o[k + 1] - o[k];
+      bad = bad || n < 0 || n > S.n_max || n > kNmax;
+    }
+    if (bad) {
+      // a malformed size: the merge kernel validates these sets one by one
+      if (lane < ns) {
+        const unsigned long long idx = atomicAdd(q.counters + 1, 1ull);
+        q.slow_sets[idx] = base + lane;
+      }
+      continue;
+    }
+    const long long o0 = o[0];
+    const int nt = (int)(o[K] - o0);
+    unsigned int pi[K], lo[K], hi[K], fl[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) pi[k] = lo[k] = hi[k] = fl[k] = 0u;
+    for (int c0 = 0; c0 < nt; c0 += 32 * U) {
+      long long Tt[U], Dt[U], At[U], Bt[U], ut[U];
+      unsigned int yt[U];
+#pragma unroll
+      for (int uu = 0; uu < U; uu++) {
+        const int i = c0 + uu * 32 + lane;
+        if (i < nt) {
+          const long long t = o0 + i;
+          Tt[uu] = __ldg(S.T + t);
+          Dt[uu] = __ldg(S.D + t);
+          At[uu] = __ldg(S.A + t);
+          Bt[uu] = __ldg(S.B + t);
+          ut[uu] = __ldg(S.u + t);
+          yt[uu] = __ldg(S.type + t);
         }
       }
-      if (!__all_sync(kFull, ok)) {
-        write_invalid(s, o, n, out, q.err);
-        continue;
+#pragma unroll
+      for (int uu = 0; uu < U; uu++) {
+        const int i = c0 + uu * 32 + lane;
+        if (i < nt) {
+          const long long t = o0 + i;
+          int ks = 0;
+#pragma unroll
+          for (int k = 1; k < K; k++) ks += (t >= o[k]) ? 1 : 0;
+          unsigned int mm = 0u, f = 0u, ulo = 0u, uhi = 0u;
+          if (!task_valid(Tt[uu], Dt[uu], At[uu], Bt[uu], ut[uu], yt[uu])) {
+            f = 1u;
+          } else {
+            mm = lemma2_size_fast((unsigned long long)At[uu], (unsigned long long)Bt[uu],
+                                  (unsigned long long)Dt[uu], M, g);
+            f = mm == 0u ? 2u : 0u;
+            ulo = (unsigned int)ut[uu] & 0xffffu;
+            uhi = (unsigned int)((unsigned long long)ut[uu] >> 16);
+          }
+          long long ok_ = o0;
+#pragma unroll
+          for (int k = 0; k < K; k++) {
+            const bool mine = ks == k;
+            pi[k] += mine ? mm : 0u;
+            lo[k] += mine ? ulo : 0u;
+            hi[k] += mine ? uhi : 0u;
+            fl[k] |= mine ? f : 0u;
+            ok_ = mine ? o[k] : ok_;
+          }
+          out.part_of_task[t] = (unsigned char)(t - ok_);
+          out.size_of_part[t] = (short)mm;
+        }
       }
-      none = __any_sync(kFull, none);
-      pi = warp_sum_i32(pi);
-      if (none || pi > md.M) {
-        if (lane == 0) {
-          unsigned long long idx = atomicAdd(q.counters + 1, 1ull);
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      const unsigned int pk = __reduce_add_sync(kFull, pi[k]);
+      const unsigned int lk = __reduce_add_sync(kFull, lo[k]);
+      const unsigned int hk = __reduce_add_sync(kFull, hi[k]);
+      const unsigned int fk = __reduce_or_sync(kFull, fl[k]);
+      if (lane == k && k < ns) {
+        const long long s = base + k;
+        if (fk != 0u || pk > M) {
+          const unsigned long long idx = atomicAdd(q.counters + 1, 1ull);
           q.slow_sets[idx] = s;
+        } else {
+          // Lemma 3 holds for the singleton partitions (numbered by their task)
+          out.verdict[s] = 1;
+          out.reason[s] = GPA_REASON_OK;
+          out.n_parts[s] = (int)(o[k + 1] - o[k]);
+          out.Pi[s] = (int)pk;
+          out.W[s] = (long long)(1000ull * (((unsigned long long)hk << 16) + lk));
+          if (out.n_tests) out.n_tests[s] = 0;
         }
-        continue;
-      }
-      usum = warp_sum_u64(usum);
-      // Lemma 3 holds for the singleton partitions: write them, numbered by
-      // their (only) task index.
-#pragma unroll
-      for (int c = 0; c < kWords; c++) {
-        const int t = c * 32 + lane;
-        if (t < n) {
-          out.part_of_task[o + t] = (unsigned char)t;
-          out.size_of_part[o + t] = (short)mm[c];
-        }
-      }
-      if (lane == 0) {
-        out.verdict[s] = 1;
-        out.reason[s] = GPA_REASON_OK;
-        out.n_parts[s] = (int)n;
-        out.Pi[s] = pi;
-        out.W[s] = (long long)(1000ull * usum);
-        if (out.n_tests) out.n_tests[s] = 0;
       }
     }
   }
@@ -446,7 +499,12 @@ __global__ void __launch_bounds__(128) alloc_merge(DevSets S, DevModel md, gpa_p
     if (i >= nslow) break;
     const long long s = q.slow_sets[i];
     const long long o = S.set_off[s];
-    const int n = (int)(S.set_off[s + 1] - o);
+    const long long nl = S.set_off[s + 1] - o;
+    if (nl < 0 || nl > S.n_max || nl > kNmax) {
+      write_invalid(s, o, nl < 0 ? 0 : nl, out, q.err);
+      continue;
+    }
+    const int n = (int)nl;
     if (!stage_set(sm.st, o, n, S.T, S.D, S.A, S.B, S.u, S.type)) {
       write_invalid(s, o, n, out, q.err);
       continue;
@@ -523,30 +581,64 @@ size_t one_gpu_smem_bytes(int warps_per_block) { return sizeof(OneGpuSmem) * (si
 
 cudaError_t launch_allocate(const DevSets& s, const DevModel& md, const gpa_params& p, const AllocOut& out,
                             const AllocQueue& q, const MagicDivHost* mdiv, const LaunchShape& fast,
-                            const LaunchShape& slow, cudaStream_t st, long long* launches) {
+                            const LaunchShape& slow, cudaStream_t st, long long* launches, Prof* prof) {
   cudaError_t e = cudaMemsetAsync(q.counters, 0, 4 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
-  alloc_fast<<<fast.blocks, fast.warps_per_block * 32, 0, st>>>(s, md, out, q, fast.chunk);
+  prof_mark(prof, st);
+  const int threads = fast.warps_per_block * 32;
+  // grid: the requested CTAs, or (0) as many as fit on every SM at once
+  auto grid = [&](const void* fn) {
+    if (fast.blocks > 0) return fast.blocks;
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0);
+    return (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  };
+  if (fast.chunk >= 8) {
+    alloc_fast<8, 2><<<grid((const void*)alloc_fast<8, 2>), threads, 0, st>>>(s, md, out, q);
+  } else if (fast.chunk >= 4) {
+    alloc_fast<4, 3><<<grid((const void*)alloc_fast<4, 3>), threads, 0, st>>>(s, md, out, q);
+  } else if (fast.chunk == 3) {
+    alloc_fast<2, 3><<<grid((const void*)alloc_fast<2, 3>), threads, 0, st>>>(s, md, out, q);
+  } else if (fast.chunk >= 2) {
+    alloc_fast<2, 2><<<grid((const void*)alloc_fast<2, 2>), threads, 0, st>>>(s, md, out, q);
+  } else {
+    alloc_fast<1, 1><<<grid((const void*)alloc_fast<1, 1>), threads, 0, st>>>(s, md, out, q);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  prof_mark(prof, st);
   const size_t smem = slow_smem_bytes(slow.warps_per_block);
   alloc_merge<<<slow.blocks, slow.warps_per_block * 32, smem, st>>>(s, md, p, out, q,
                                                                      reinterpret_cast<const MagicDiv*>(mdiv));
   e = cudaGetLastError();
+  prof_mark(prof, st);
   *launches += 2;
   return e;
 }
 
 cudaError_t launch_one_gpu(const DevSets& s, const DevModel& md, const AllocOut& out, const AllocQueue& q,
-                           const MagicDivHost* mdiv, const LaunchShape& shape, cudaStream_t st, long long* launches) {
+                           const MagicDivHost* mdiv, const LaunchShape& shape, cudaStream_t st, long long* launches,
+                           Prof* prof) {
   unsigned long long* ticket = q.counters + 3;
   unsigned int* err = q.err;
   cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
+  prof_mark(prof, st);
   one_gpu<<<shape.blocks, shape.warps_per_block * 32, one_gpu_smem_bytes(shape.warps_per_block), st>>>(
       s, md, out, err, reinterpret_cast<const MagicDiv*>(mdiv), ticket);
+  e = cudaGetLastError();
+  prof_mark(prof, st);
   *launches += 1;
-  return cudaGetLastError();
+  return e;
+}
+
+// Record the next timing event of a profiled call (no-op when prof is null).
+void prof_mark(Prof* p, cudaStream_t st) {
+  if (!p || p->used >= 4) return;
+  cudaEventRecordWithFlags(p->ev[p->used], st, p->capture ? cudaEventRecordExternal : cudaEventRecordDefault);
+  p->used++;
 }
 
 // Opt in to the dynamic shared memory the kernels need (once per process).

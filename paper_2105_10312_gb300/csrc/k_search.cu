@@ -363,7 +363,7 @@ cudaError_t search_kernels_init() {
 
 cudaError_t launch_search_best(const DevSets& s, const DevModel& md, int kmin, int kmax, const BestOut& out,
                                const AllocQueue& q, const MagicDivHost* mdiv, int sm_count, cudaStream_t st,
-                               long long* launches) {
+                               long long* launches, Prof* prof) {
   int nmax = s.n_max < 0 ? 0 : (s.n_max > kSN ? kSN : s.n_max);
   const int nsub_max = 1 << nmax;
   const size_t smem = search_smem_bytes(nsub_max);
@@ -374,10 +374,13 @@ cudaError_t launch_search_best(const DevSets& s, const DevModel& md, int kmin, i
   unsigned int* err = q.err;
   cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
+  prof_mark(prof, st);
   search_sets<<<(int)blocks, kSThreads, smem, st>>>(s, md, kmin, kmax, out, err,
                                                      reinterpret_cast<const MagicDiv*>(mdiv), ticket, nsub_max);
+  e = cudaGetLastError();
+  prof_mark(prof, st);
   *launches += 1;
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace gpa

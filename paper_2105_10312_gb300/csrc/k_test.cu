@@ -159,29 +159,36 @@ __global__ void __launch_bounds__(256) test_candidates(DevSets S, DevModel md, C
 }  // namespace
 
 cudaError_t launch_wcet_tables(const DevSets& s, const DevModel& md, long long* Cn, long long* Cc, unsigned int* err,
-                               const MagicDivHost* mdiv, int sm_count, cudaStream_t st, long long* launches) {
+                               const MagicDivHost* mdiv, int sm_count, cudaStream_t st, long long* launches,
+                               Prof* prof) {
   const int warps = 8;
   long long need = (s.nsets + warps - 1) / warps;
   int blocks = (int)(need < (long long)sm_count * 8 ? need : (long long)sm_count * 8);
   if (blocks < 1) blocks = 1;
+  prof_mark(prof, st);
   wcet_tables<<<blocks, warps * 32, 0, st>>>(s, md, Cn, Cc, err, reinterpret_cast<const MagicDiv*>(mdiv));
+  cudaError_t e = cudaGetLastError();
+  prof_mark(prof, st);
   *launches += 1;
-  return cudaGetLastError();
+  return e;
 }
 
 static size_t test_smem_bytes(int warps) { return sizeof(TestSmem) * (size_t)warps; }
 
 cudaError_t launch_test_schedulable(const DevSets& s, const DevModel& md, const Cands& c, unsigned char* verdict,
                                     long long* R, unsigned int* err, const MagicDivHost* mdiv, int sm_count,
-                                    cudaStream_t st, long long* launches) {
+                                    cudaStream_t st, long long* launches, Prof* prof) {
   const int warps = 4;  // 4 x sizeof(TestSmem) stays below the 48 KB default
   long long need = (c.ncands + warps - 1) / warps;
   int blocks = (int)(need < (long long)sm_count * 4 ? need : (long long)sm_count * 4);
   if (blocks < 1) blocks = 1;
+  prof_mark(prof, st);
   test_candidates<<<blocks, warps * 32, test_smem_bytes(warps), st>>>(s, md, c, verdict, R, err,
                                                                       reinterpret_cast<const MagicDiv*>(mdiv));
+  cudaError_t e = cudaGetLastError();
+  prof_mark(prof, st);
   *launches += 1;
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace gpa

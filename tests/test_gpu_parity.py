@@ -214,7 +214,9 @@ def test_allocate_launch_shapes_graph_and_per_set(ctx):
     ref = oracle.allocate(s, md["M"], md["g"], KC, KM, nthreads=8)
     refp = oracle.allocate(p, 68, 1, KC, KM, nthreads=8)
     d, dp = gpa.to_device(s), gpa.to_device(p)
-    c2 = gpa.Context(0)
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()  # graph capture needs a non-default stream
+    c2 = gpa.Context(0, stream=stream)
     try:
         for warps in (1, 2, 4, 8):
             for chunk in (1, 3, 8):
