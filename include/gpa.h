@@ -43,7 +43,7 @@
  *  is in conflict when at least one other task of its own type shares its
  *  partition (§4.2).
  *
- * Per-partition test (§5.6 leaves the policy open): a partition of m SMs is
+ * Per-partition test (§5.5 leaves the policy open): a partition of m SMs is
  * one processor running its tasks under deadline-monotonic fixed priorities
  * (priority order: D ascending, then T ascending, then task index); each
  * task's response time is the least fixed point of

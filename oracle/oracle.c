@@ -17,14 +17,14 @@
  *                   C = k (a/m + b): ceil(k (A + B m) / (10^6 m))
  *   in_conflict()   §4.2 conflict rule (another task of the same type in
  *                   the partition)
- *   rta()           §5.6 per-partition test; policy = deadline-monotonic
+ *   rta()           §5.5 per-partition test; policy = deadline-monotonic
  *                   fixed priority, classic response-time iteration
  *   minm_linear()   Alg. 2 (merge): first size in [lo, hi] that passes
- *   minm_binary()   the binary-search variant the text of §5.3 mentions
+ *   minm_binary()   the binary-search variant the text of §5.2 mentions
  *   lemma1()        Lemma 1 (necessary utilisation test)
  *   allocate_one()  Alg. 1 with Lemma 2 (init), Lemma 3 (exit), Alg. 3
  *                   (select_partitions), Def. 2 (valid merge), Def. 3 (SMS
- *                   order), Def. 4 (BF order), forbidden list (§5.5, ACT/INA)
+ *                   order), Def. 4 (BF order), forbidden list (§5.3, ACT/INA)
  *   one_gpu()       the 1G baseline of §7.2 (all tasks, one partition of M)
  *   search_rgs()    exhaustive optimum over set partitions (subset form)
  *   search_explicit() the same optimum by brute force over every split of M
@@ -116,7 +116,7 @@ static int64_t workload(const oset* s, const omodel* md, const unsigned char* in
   return w;
 }
 
-/* §5.6: the partition `in` of m SMs, run as one processor under DM fixed
+/* §5.5: the partition `in` of m SMs, run as one processor under DM fixed
  * priorities with interference folded into the WCETs.  R[i] receives the
  * least fixed point of R = C_i + sum_{hp} ceil(R/T_j) C_j when it is <= D_i,
  * else -1.  Returns 1 iff every task of the partition meets its deadline. */
@@ -153,7 +153,7 @@ static int64_t minm_linear(const oset* s, const omodel* md, const unsigned char*
   return 0;
 }
 
-/* §5.3: the same answer by binary search (valid because the test is
+/* §5.2: the same answer by binary search (valid because the test is
  * monotone in m under the no-timing-anomaly hypothesis of §4.1). */
 static int64_t minm_binary(const oset* s, const omodel* md, const unsigned char* in, int64_t lo, int64_t hi) {
   if (lo > hi) return 0;
@@ -245,7 +245,7 @@ static int pairlist_add(pairlist* pl, const unsigned char* a, const unsigned cha
   return 1;
 }
 
-/* §5.5 and Alg. 3: is the merge of P and Q forbidden? */
+/* §5.3 and Alg. 3: is the merge of P and Q forbidden? */
 static int forbidden(const oset* s, const pairlist* pl, unsigned char act_pair[ONMAX][ONMAX], const opart* P,
                      const opart* Q) {
   for (int k = 0; k < pl->len; k++) {

@@ -8,7 +8,7 @@
 //    into shared memory in deadline-monotonic order;
 //  * the WCET of §3.3/§7.1, C = ceil(k (A + B m) / (10^6 m)), with
 //    the conflict rule of §4.2;
-//  * the warp-cooperative per-partition response-time test of §5.6
+//  * the warp-cooperative per-partition response-time test of §5.5
 //    and the minimum-size search of Alg. 2.
 #pragma once
 
@@ -244,7 +244,7 @@ __device__ __forceinline__ unsigned long long workload_from_sums(unsigned long l
   return (unsigned long long)(nc >= 2 ? kc : 1000u) * Uc + (unsigned long long)(nm >= 2 ? km : 1000u) * Um;
 }
 
-// §5.6 per-partition test, warp-cooperative: the tasks of S (rows of st, a
+// §5.5 per-partition test, warp-cooperative: the tasks of S (rows of st, a
 // mask in priority order) on one processor of m SMs.  Lane l owns the l-th,
 // (l+32)-th, ... task of S; its fixed point reads the higher-priority tasks
 // from the compacted scratch (broadcast shared-memory reads).
@@ -337,7 +337,7 @@ static __device__ __noinline__ bool warp_rta(const SetSmem& st, const unsigned i
 }
 
 // Alg. 2: smallest multiple of g in [lo, hi] at which S passes; 0 if none.
-// The binary form (§5.3) returns the same size because the test is monotone
+// The binary form (§5.2) returns the same size because the test is monotone
 // in m (no timing anomalies, §4.1).
 __device__ __forceinline__ unsigned int warp_minm(const SetSmem& st, const unsigned int* S, unsigned int lo,
                                                   unsigned int hi, unsigned int g, bool linear, unsigned int kc,

@@ -329,7 +329,7 @@ __device__ void merge_set(MergeSmem& sm, long long s, long long o, int n, const 
   }
   int tests = 0;
   // ACT: every task pair is tried as a merge of two singletons; pairs that
-  // fail are forbidden for the rest of the run (§5.5).
+  // fail are forbidden for the rest of the run (§5.3).
   if (p.act && pi > (int)M) {
     for (int a = 0; a < n; a++)
       for (int b = a + 1; b < n; b++) {

@@ -1,6 +1,6 @@
 // k_test.cu — WCET tables (§3.3 two-curve model in the §7.1 integer form)
 // and the per-partition test over a flat batch of explicit candidates
-// (a split of the SMs into parts plus a task-to-part map, §4.1-§4.2, §5.6).
+// (a split of the SMs into parts plus a task-to-part map, §4.1-§4.2, §5.5).
 #include <cuda_runtime.h>
 
 #include "gpa_device.cuh"

@@ -7,7 +7,7 @@ by a different route from the oracle's code:
   scaling-function form of §7.1, C = k (a/m + b), evaluated with exact
   rationals from the serial-fraction parameters (alpha) or the paper's b = beta a.
 * ``simulate_fp``: a unit-step discrete-time simulation of a fixed-priority
-  uniprocessor schedule with synchronous release (the partition of §5.6 run
+  uniprocessor schedule with synchronous release (the partition of §5.5 run
   as one processor) -- response times by brute force, not by analysis.
 * ``heuristic``: Alg. 1-3 restated over Python frozensets (different data
   structures and loop order from the oracle), using a supplied per-partition

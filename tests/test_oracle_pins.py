@@ -131,7 +131,7 @@ def test_wcet_tables_layout():
                 assert Cc[o * Mu + mi * n + t] == refs.wcet_alpha(s["C1"][o + t], s["alpha_pm"][o + t], k, m)
 
 
-# ------------------------------------------------- per-partition test (§5.6)
+# ------------------------------------------------- per-partition test (§5.5)
 
 def _no_inflation_set(rng, n, periods):
     T = np.array([rng.choice(periods) for _ in range(n)], np.int64)
@@ -246,7 +246,7 @@ def test_lemma2_singleton_size_closed_form():
 
 
 def test_merge_search_linear_equals_binary():
-    """Alg. 2's linear scan and the §5.3 binary search give the same size."""
+    """Alg. 2's linear scan and the §5.2 binary search give the same size."""
     s = gen_tasksets(seed=9, nsets=80, n_min=2, n_max=8, U_lo_ppm=500000, U_hi_ppm=6000000, deadline_pm=750)
     off = s["set_off"]
     rng = random.Random(9)
