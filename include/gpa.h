@@ -294,6 +294,34 @@ typedef struct {
 int32_t gpa_allocate(gpa_ctx* ctx, const gpa_tasksets* sets, const gpa_model* model,
                      const gpa_params* params, gpa_alloc_result* result);
 
+/* Task sets per call of gpa_allocate_noalloc. */
+#define GPA_NOALLOC_MAX_SETS 262144
+
+/* gpa_allocate for callers that cannot allocate device memory (the paper has
+ * no counterpart: this is a deployment variant).  Some callers may not call
+ * cudaMalloc: a host application or plug-in whose device memory belongs to
+ * someone else's pool or a fixed budget, or a real-time process that must not
+ * allocate once it runs.  This call takes no context and allocates nothing
+ * (no cudaMalloc, cudaFree or allocating library routine); its scratch -- the
+ * work-queue counters, a queue of up to GPA_NOALLOC_MAX_SETS deferred sets
+ * and the reciprocal table, about 2 MB -- is a static device array of the
+ * library, held by every GPU that loads it until the process exits.
+ *  - Same computation and outputs as gpa_allocate with GPA_POLICY_SMS or
+ *    GPA_POLICY_BF (GPA_ERR_ARG otherwise); device arrays only (both `mem`
+ *    fields GPA_DEVICE); work is enqueued on `stream` (a cudaStream_t).
+ *  - More than GPA_NOALLOC_MAX_SETS sets: GPA_ERR_RANGE, nothing launched.
+ *  - The first call on a device (the current device) sets that device up
+ *    synchronously (uploads the reciprocal table, looks up the scratch
+ *    address); make it before any stream capture.
+ *  - Every call shares the one scratch array, which keeps the previous
+ *    call's contents; each call clears the counters it needs zeroed.  Calls
+ *    whose GPU work overlaps (other streams, other threads) race on it: the
+ *    caller must serialise them.
+ *  - Device-side validation marks invalid sets with GPA_REASON_INVALID as
+ *    gpa_allocate does; there is no context to report it to beyond that. */
+int32_t gpa_allocate_noalloc(void* stream, const gpa_tasksets* sets, const gpa_model* model,
+                             const gpa_params* params, gpa_alloc_result* result);
+
 /* ------------------------------------------------------ exhaustive optimum */
 
 typedef struct {

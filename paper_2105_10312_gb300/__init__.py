@@ -104,6 +104,8 @@ def _set_signatures(L):
     L.gpa_unrank_composition.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _vp]
     L.gpa_count_rgs.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64)]
     L.gpa_unrank_rgs.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _vp]
+    L.gpa_allocate_noalloc.argtypes = [_vp, ctypes.POINTER(Tasksets), ctypes.POINTER(Model), ctypes.POINTER(Params),
+                                       ctypes.POINTER(AllocResult)]
 
 
 def lib():
@@ -326,6 +328,28 @@ class Context:
                          _ptr(out["n_blocks"]), _ptr(out["spare"]), _ptr(out["rgs"]), _ptr(out["minm_block"]))
         _check(lib().gpa_search_best(self._h, ctypes.byref(ts), ctypes.byref(md), kmin, kmax, ctypes.byref(res)))
         return out
+
+
+NOALLOC_MAX_SETS = 262144
+
+
+def allocate_noalloc(sets, out, M, g=1, k_c_pm=1200, k_m_pm=2300, policy="SMS", act=False, linear=True,
+                     stream=None):
+    """gpa_allocate_noalloc: the heuristic for callers that may not allocate device
+    memory.  No context; the library's static device scratch is used, so calls
+    must not overlap on the GPU.  ``sets`` and ``out`` are CUDA tensors the caller
+    allocated; work is enqueued on ``stream`` (default: torch's current stream)."""
+    import torch
+    ts, mem = make_tasksets(sets)
+    md = Model(M, g, k_c_pm, k_m_pm)
+    pr = Params(POLICY[policy], 1 if act else 0, 1 if linear else 0, 0)
+    res = AllocResult(mem, 0, _ptr(out["verdict"]), _ptr(out["reason"]), _ptr(out["n_parts"]), _ptr(out["Pi"]),
+                      _ptr(out["W"]), _ptr(out.get("n_tests")), _ptr(out["part_of_task"]), _ptr(out["size_of_part"]))
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(lib().gpa_allocate_noalloc(_vp(stream.cuda_stream), ctypes.byref(ts), ctypes.byref(md), ctypes.byref(pr),
+                                      ctypes.byref(res)))
+    return out
 
 
 def to_device(sets, device="cuda"):
