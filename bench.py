@@ -170,6 +170,100 @@ def cpu_baseline_oracle(sets, md, policy, act, target_wall=2.0, max_wall=20.0):
             "sample": f"{passes} full pass(es) over the {nsets}-set batch, {threads} threads, {el:.2f} s wall"}
 
 
+def serve_bench(local, rates=(2000, 5000, 10000, 20000, 50000), duration=0.5, plain=False, population=512,
+                seed=5):
+    """Open-loop Poisson stream of admission queries (10 % ADMIT of a new
+    tenant, 45 % ADD of one task, 45 % REMOVE) against a live population;
+    latency = submit to completion.  plain=True: one request per launch, one
+    stream (the per-request form)."""
+    import ctypes
+
+    import paper_2105_10312_gb300 as gpa
+    rng = np.random.default_rng(seed)
+    ctx = gpa.Context(local)
+    srv = gpa.Server(ctx, M=148, max_batch=1 if plain else 512, nstreams=1 if plain else 4,
+                     max_tenants=1 << 16, slots_per_chunk=1024)
+    L = gpa.lib()
+    nmax_new = 200000
+    sets = gpa.gen_tasksets(**W.gen_params("serve", nsets=population + nmax_new // 10 + 10, seed=seed))
+    pool = gpa.gen_tasksets(**W.gen_params("serve", nsets=nmax_new, seed=seed + 1, n_min=1, n_max=1,
+                                           U_lo_ppm=20000, U_hi_ppm=1000000))
+    keep = []
+
+    def req_for(op, tenant, k=None, j=None, index=0):
+        if op == "ADMIT":
+            o, e = sets["set_off"][k], sets["set_off"][k + 1]
+            cols = [np.ascontiguousarray(sets[c][o:e]) for c in ("T", "D", "A", "B", "u_ppm", "type")]
+            n = e - o
+        elif op == "ADD":
+            cols = [np.ascontiguousarray(pool[c][j:j + 1]) for c in ("T", "D", "A", "B", "u_ppm", "type")]
+            n = 1
+        else:
+            cols, n = [None] * 6, 0
+        keep.append(cols)
+        ptrs = [c.ctypes.data if c is not None else None for c in cols]
+        return gpa.Request(gpa.SERVE_OP[op], int(n), int(tenant), int(index), 0, *ptrs)
+
+    # population (not timed)
+    ids = [srv.submit("ADMIT", t, tasks={c: sets[c][sets["set_off"][t]:sets["set_off"][t + 1]]
+                                         for c in ("T", "D", "A", "B", "u_ppm", "type")}) for t in range(population)]
+    live = [t for t, i in zip(range(population), ids) if srv.poll(i)["verdict"]]
+    sizes = {t: int(sets["set_off"][t + 1] - sets["set_off"][t]) for t in live}
+    next_tenant, next_set, next_task = population, population, 0
+    out = {}
+    rid = ctypes.c_uint64()
+    for rate in rates:
+        nreq = int(rate * duration)
+        gaps = rng.exponential(1.0 / rate, nreq)
+        arrivals = np.cumsum(gaps)
+        reqs = []
+        for _ in range(nreq):
+            x = rng.random()
+            if x < 0.10 or not live:
+                reqs.append(req_for("ADMIT", next_tenant, k=next_set))
+                live.append(next_tenant)
+                sizes[next_tenant] = int(sets["set_off"][next_set + 1] - sets["set_off"][next_set])
+                next_tenant += 1
+                next_set += 1
+            else:
+                t = live[int(rng.integers(len(live)))]
+                if x < 0.55 and sizes[t] < 128:
+                    reqs.append(req_for("ADD", t, j=next_task))
+                    next_task += 1
+                    sizes[t] += 1
+                elif sizes[t] > 1:
+                    reqs.append(req_for("REMOVE", t, index=0))
+                    sizes[t] -= 1
+                else:
+                    reqs.append(req_for("ADD", t, j=next_task))
+                    next_task += 1
+                    sizes[t] += 1
+        sent = []
+        t0 = time.perf_counter()
+        for k in range(nreq):
+            while time.perf_counter() - t0 < arrivals[k]:
+                pass
+            L.gpa_serve_submit(ctx.handle, ctypes.byref(reqs[k]), ctypes.byref(rid))
+            sent.append(rid.value)
+        t_sub = time.perf_counter() - t0
+        lat = []
+        errors = 0
+        for i in sent:
+            r = srv.poll(i)
+            lat.append(r["latency_us"])
+            errors += r["status"] != 0
+        t_all = time.perf_counter() - t0
+        lat = np.array(lat)
+        out[str(rate)] = {"p50_ms": float(np.percentile(lat, 50)) / 1000, "p99_ms": float(np.percentile(lat, 99)) / 1000,
+                          "offered_req_s": nreq / max(t_sub, 1e-9), "completed_req_s": nreq / t_all,
+                          "requests": nreq, "errors": int(errors)}
+    st = srv.stats()
+    srv.stop()
+    ctx.close()
+    return {"rates": out, "batches": st["batches"], "max_batch": st["max_batch"], "overlapped_batches": st["overlapped"],
+            "form": "one request per launch, 1 stream" if plain else "continuous batching, up to 512 per batch, 4 streams"}
+
+
 def build_workload(name, rank, nsets_override=None):
     import paper_2105_10312_gb300 as gpa
     base = "sweep" if name == "sweep1g" else name
@@ -381,6 +475,11 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload != "exhaustive":
         cpu = cpu_baseline_oracle(sets, md, policy, act)
 
+    serve = None
+    if args.serve_duration > 0 and rank == 0:
+        serve = {"continuous": serve_bench(local, duration=args.serve_duration),
+                 "per_request": serve_bench(local, duration=args.serve_duration, plain=True)}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "tasksets/s", "n_gpus": world, "steps": args.steps,
@@ -392,7 +491,7 @@ def run_gpu(args):
                        "parallelism": f"{world} independent shard(s)", "launch": "persistent + CUDA graph"},
             "candidates_tested_per_s": cand_total / (max_ms / 1000.0),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clocks, "per_set_launch": plain, "wall_s_timed": wall,
+            "clocks": clocks, "per_set_launch": plain, "wall_s_timed": wall, "serve": serve,
         }
         print(json.dumps(line))
     ctx.close()
@@ -414,6 +513,8 @@ def main():
     ap.add_argument("--plain-sample", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--serve-duration", type=float, default=0.5,
+                    help="seconds of Poisson arrivals per offered rate in the serving measurement (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -345,6 +345,93 @@ typedef struct {
 int32_t gpa_search_best(gpa_ctx* ctx, const gpa_tasksets* sets, const gpa_model* model,
                         int32_t kmin, int32_t kmax, gpa_best_result* result);
 
+/* ----------------------------------------------------------------- serving */
+
+/* Admission control as a service: tenants (task sets of up to GPA_NMAX
+ * tasks) and their current allocation live in device memory; requests are
+ * queued, packed into micro-batches (at most one request per tenant per
+ * batch, each tenant's requests in submission order) and run one warp per
+ * request on one of several streams, so a batch starts while earlier ones are
+ * still on the GPU.  A tenant's state is always an allocation that passes
+ * (Lemma 3).  Every request's result depends only on its tenant's earlier
+ * requests, never on what else shares its batch.
+ *
+ * Operations:
+ *  GPA_SERVE_ADMIT  create tenant `tenant` from n tasks: Alg. 1 (the
+ *                   configured policy); admitted iff it succeeds.  Waits in
+ *                   the queue while no tenant slot is free and the device
+ *                   has no memory left to add slots (cudaMemGetInfo).
+ *  GPA_SERVE_ADD    append one task (index n): first partition (in order of
+ *                   lowest task index) that still passes at its size with the
+ *                   task; else the first that passes after growing into the
+ *                   spare SMs (Alg. 2 search from its size + g up to its size
+ *                   + spare); else a new partition of the task's Lemma 2 size
+ *                   if it fits in the spare SMs; else Alg. 1 on all tasks.  If
+ *                   all fail the task is rejected and the state is unchanged.
+ *  GPA_SERVE_REMOVE remove task `index` (later tasks shift down by one); its
+ *                   partition shrinks to its new minimum size (or disappears).
+ *  GPA_SERVE_EVICT  delete the tenant and free its slot. */
+enum { GPA_SERVE_ADMIT = 0, GPA_SERVE_ADD = 1, GPA_SERVE_REMOVE = 2, GPA_SERVE_EVICT = 3 };
+/* How an ADD was placed. */
+enum { GPA_PATH_NONE = 0, GPA_PATH_FIT = 1, GPA_PATH_GROW = 2, GPA_PATH_NEW = 3, GPA_PATH_REALLOC = 4 };
+
+typedef struct {
+  int32_t M, g, k_c_pm, k_m_pm;  /* the GPU model of every tenant */
+  int32_t policy;                /* GPA_POLICY_SMS or GPA_POLICY_BF for ADMIT and ADD's re-allocation */
+  int32_t act;
+  int32_t max_batch;             /* requests per micro-batch (<= 4096) */
+  int32_t nstreams;              /* concurrent micro-batches (1..8) */
+  int32_t queue_cap;             /* pending requests before GPA_ERR_BUSY */
+  int32_t slots_per_chunk;       /* tenant slots added per device allocation */
+  int64_t max_tenants;           /* upper bound on live tenants */
+  int64_t reserve_bytes;         /* device memory left free when adding slots */
+} gpa_serve_cfg;
+
+typedef struct {
+  int32_t op;                    /* GPA_SERVE_* */
+  int32_t n;                     /* ADMIT: tasks; ADD: 1 */
+  int64_t tenant;                /* caller's tenant id (>= 0) */
+  int32_t index;                 /* REMOVE: task index */
+  int32_t pad_;
+  const int64_t* T;              /* ADMIT/ADD host arrays of n tasks, copied at submit */
+  const int64_t* D;
+  const int64_t* A;
+  const int64_t* B;
+  const int64_t* u_ppm;
+  const uint8_t* type;
+} gpa_request;
+
+typedef struct {
+  uint64_t req_id;
+  int32_t status;                /* GPA_OK, or the request's error (GPA_ERR_RANGE / ARG / NOTFOUND) */
+  uint8_t verdict;               /* ADMIT/ADD: 1 if accepted; REMOVE/EVICT: 1 */
+  uint8_t reason;                /* GPA_REASON_* of the Alg. 1 run (ADMIT, ADD re-allocation) */
+  uint8_t path;                  /* GPA_PATH_* (ADD) */
+  uint8_t pad_;
+  int32_t n_tasks, n_parts, Pi;  /* the tenant's state after the request */
+  int64_t W;
+  uint8_t part_of_task[GPA_NMAX];
+  int16_t size_of_part[GPA_NMAX];
+  double latency_us;             /* submit to completion, host clock */
+} gpa_response;
+
+/* Start the server on the context's device (one server per context). */
+int32_t gpa_serve_start(gpa_ctx* ctx, const gpa_serve_cfg* cfg);
+/* Queue a request; *req_id identifies it.  GPA_ERR_BUSY only when the host
+ * queue is full; malformed requests are answered with an error status. */
+int32_t gpa_serve_submit(gpa_ctx* ctx, const gpa_request* req, uint64_t* req_id);
+/* Wait up to timeout_us (0: do not wait) for request req_id and move its
+ * response into *out.  GPA_ERR_TIMEOUT if not done in time (ask again later),
+ * GPA_ERR_NOTFOUND for an unknown or already collected id.  Never blocks
+ * beyond timeout_us. */
+int32_t gpa_serve_poll(gpa_ctx* ctx, uint64_t req_id, gpa_response* out, int64_t timeout_us);
+/* Finish the queued requests, stop the server and free its device state. */
+int32_t gpa_serve_stop(gpa_ctx* ctx);
+/* Counters: requests completed, micro-batches launched, largest batch,
+ * batches that overlapped another on the GPU, tenant slots allocated. */
+int32_t gpa_serve_stats(gpa_ctx* ctx, int64_t* completed, int64_t* batches, int64_t* max_batch,
+                        int64_t* overlapped, int64_t* slots);
+
 #ifdef __cplusplus
 }
 #endif

@@ -186,3 +186,92 @@ def search_best(sets, M, g, kc, km, kmin, kmax, explicit=False, nthreads=1):
     else:
         _check(lib().orc_search_best(*args), "search_best")
     return out
+
+
+class Tenant:
+    """One tenant of the serving loop, replayed on the CPU (ADMIT / ADD / REMOVE)."""
+
+    COLS = ("T", "D", "A", "B", "u_ppm", "type")
+
+    def __init__(self, M, g, kc, km, policy="SMS", act=False):
+        self.M, self.g, self.kc, self.km = M, g, kc, km
+        self.policy, self.act = POLICY[policy], 1 if act else 0
+        self.tasks = {k: np.zeros(0, np.uint8 if k == "type" else np.int64) for k in self.COLS}
+        self.part = np.zeros(0, np.uint8)
+        self.size = np.zeros(0, np.int16)
+        self.n_parts = 0
+        self.Pi = 0
+        self.W = 0
+        self.alive = False
+
+    @property
+    def n(self):
+        return len(self.tasks["T"])
+
+    def _res(self, verdict, reason, path):
+        return {"verdict": int(verdict), "reason": int(reason), "path": int(path), "n_tasks": self.n,
+                "n_parts": self.n_parts, "Pi": self.Pi, "W": self.W, "part_of_task": self.part.copy(),
+                "size_of_part": self.size[:self.n_parts].copy()}
+
+    def admit(self, tasks):
+        _fresh()
+        n = len(tasks["T"])
+        cols = {k: (_u8(tasks[k]) if k == "type" else _i64(tasks[k])) for k in self.COLS}
+        v, r = ctypes.c_uint8(), ctypes.c_uint8()
+        npart, Pi, W = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        part = np.zeros(max(n, 1), np.uint8)
+        size = np.zeros(max(n, 1), np.int16)
+        _check(lib().orc_serve_admit(ctypes.c_int(n), *[_p(cols[k]) for k in self.COLS], ctypes.c_int64(self.M),
+                                     ctypes.c_int64(self.g), ctypes.c_int64(self.kc), ctypes.c_int64(self.km),
+                                     ctypes.c_int(self.policy), ctypes.c_int(self.act), ctypes.byref(v),
+                                     ctypes.byref(r), _p(part), _p(size), ctypes.byref(npart), ctypes.byref(Pi),
+                                     ctypes.byref(W)), "serve_admit")
+        if v.value:
+            self.tasks = {k: cols[k].copy() for k in self.COLS}
+            self.part, self.size = part[:n].copy(), size.copy()
+            self.n_parts, self.Pi, self.W = npart.value, Pi.value, W.value
+            self.alive = True
+        return {"verdict": v.value, "reason": r.value, "path": 0, "n_tasks": n if v.value else 0,
+                "n_parts": npart.value if v.value else 0, "Pi": Pi.value if v.value else 0,
+                "W": W.value if v.value else 0, "part_of_task": part[:n].copy() if v.value else np.zeros(0, np.uint8),
+                "size_of_part": size[:npart.value].copy() if v.value else np.zeros(0, np.int16)}
+
+    def add(self, task):
+        _fresh()
+        n = self.n
+        cols = {k: np.concatenate([self.tasks[k], np.asarray([task[k]], self.tasks[k].dtype)]) for k in self.COLS}
+        v, r, path = ctypes.c_uint8(), ctypes.c_uint8(), ctypes.c_uint8()
+        npart, Pi, W = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        part_in = np.ascontiguousarray(self.part, np.uint8) if n else np.zeros(1, np.uint8)
+        size_in = np.ascontiguousarray(self.size, np.int16) if len(self.size) else np.zeros(1, np.int16)
+        part = np.zeros(n + 1, np.uint8)
+        size = np.zeros(n + 1, np.int16)
+        _check(lib().orc_serve_add(ctypes.c_int(n), *[_p(cols[k]) for k in self.COLS], _p(part_in), _p(size_in),
+                                   ctypes.c_int(self.n_parts), ctypes.c_int64(self.M), ctypes.c_int64(self.g),
+                                   ctypes.c_int64(self.kc), ctypes.c_int64(self.km), ctypes.c_int(self.policy),
+                                   ctypes.c_int(self.act), ctypes.byref(v), ctypes.byref(r), ctypes.byref(path),
+                                   _p(part), _p(size), ctypes.byref(npart), ctypes.byref(Pi), ctypes.byref(W)),
+               "serve_add")
+        if v.value:
+            self.tasks = cols
+            self.part, self.size = part.copy(), size.copy()
+            self.n_parts, self.Pi, self.W = npart.value, Pi.value, W.value
+        return self._res(v.value, r.value, path.value)
+
+    def remove(self, index):
+        _fresh()
+        n = self.n
+        outs = {k: np.zeros(max(n - 1, 1), np.uint8 if k == "type" else np.int64) for k in self.COLS}
+        part = np.zeros(max(n - 1, 1), np.uint8)
+        size = np.zeros(max(n, 1), np.int16)
+        npart, Pi, W = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _check(lib().orc_serve_remove(ctypes.c_int(n), *[_p(self.tasks[k]) for k in self.COLS], _p(self.part),
+                                      _p(self.size), ctypes.c_int(self.n_parts), ctypes.c_int(index),
+                                      ctypes.c_int64(self.M), ctypes.c_int64(self.g), ctypes.c_int64(self.kc),
+                                      ctypes.c_int64(self.km), *[_p(outs[k]) for k in self.COLS], _p(part),
+                                      _p(size), ctypes.byref(npart), ctypes.byref(Pi), ctypes.byref(W)),
+               "serve_remove")
+        self.tasks = {k: outs[k][:n - 1].copy() for k in self.COLS}
+        self.part, self.size = part[:n - 1].copy(), size.copy()
+        self.n_parts, self.Pi, self.W = npart.value, Pi.value, W.value
+        return self._res(1, 0, 0)

@@ -941,3 +941,173 @@ int orc_search_explicit(int64_t nsets, const int64_t* set_off, const int64_t* T,
   return search_batch(1, nsets, set_off, T, D, A, B, u, type, M, g, kc, km, kmin, kmax, feasible, W, sum_minm,
                       n_blocks, spare, rgs, minm_block, nthreads, candidates);
 }
+
+/* ------------------------------------------------------- serving operations
+ *
+ * One tenant's state: n tasks and an allocation (partition of each task,
+ * size of each partition, partitions numbered by their lowest task index)
+ * that passes the test (Lemma 3).  These are the operations of the serving
+ * loop, defined on top of Alg. 1-3: ADD tries, in order, to fit the new task
+ * into an existing partition at its size (first fit by partition number),
+ * to grow a partition into the spare SMs (Alg. 2 from its size + g up to
+ * its size + spare), a new Lemma 2 partition in the spare SMs, and Alg. 1 on
+ * all tasks; REMOVE drops a task and shrinks its partition to its minimum. */
+
+enum { PATH_NONE = 0, PATH_FIT = 1, PATH_GROW = 2, PATH_NEW = 3, PATH_REALLOC = 4 };
+
+static void summarise(const oset* s, const omodel* md, const uint8_t* part, const int16_t* size, int np,
+                      int32_t* Pi, int64_t* W) {
+  int64_t pi = 0, w = 0;
+  unsigned char in[ONMAX];
+  for (int p = 0; p < np; p++) {
+    pi += size[p];
+    for (int i = 0; i < s->n; i++) in[i] = part[i] == p;
+    w += workload(s, md, in);
+  }
+  *Pi = (int32_t)pi;
+  *W = w;
+}
+
+/* renumber partitions by their lowest task index */
+static void canonical(int n, uint8_t* part, int16_t* size, int np) {
+  int lowest[ONMAX], order[ONMAX], newid[ONMAX];
+  for (int p = 0; p < np; p++) lowest[p] = n;
+  for (int i = n - 1; i >= 0; i--) lowest[part[i]] = i;
+  for (int p = 0; p < np; p++) order[p] = p;
+  for (int a = 1; a < np; a++) {
+    int x = order[a], b = a - 1;
+    while (b >= 0 && lowest[order[b]] > lowest[x]) { order[b + 1] = order[b]; b--; }
+    order[b + 1] = x;
+  }
+  int16_t sz[ONMAX];
+  for (int r = 0; r < np; r++) { newid[order[r]] = r; sz[r] = size[order[r]]; }
+  for (int r = 0; r < np; r++) size[r] = sz[r];
+  for (int i = 0; i < n; i++) part[i] = (uint8_t)newid[part[i]];
+}
+
+int orc_serve_admit(int n, const int64_t* T, const int64_t* D, const int64_t* A, const int64_t* B, const int64_t* u,
+                    const uint8_t* type, int64_t M, int64_t g, int64_t kc, int64_t km, int policy, int act,
+                    uint8_t* verdict, uint8_t* reason, uint8_t* part_out, int16_t* size_out, int32_t* n_parts,
+                    int32_t* Pi, int64_t* W) {
+  oset s = {n, T, D, A, B, u, type};
+  omodel md = {M, g, kc, km};
+  if (!valid_model(&md) || !valid_set(&s)) return O_ERR_RANGE;
+  ores r;
+  int st = allocate_one(&s, &md, policy, act, 1, &r, part_out, size_out);
+  *verdict = r.verdict;
+  *reason = r.reason;
+  *n_parts = r.n_parts;
+  *Pi = r.Pi;
+  *W = r.W;
+  return st;
+}
+
+/* tasks: n + 1 entries (the state's n tasks, then the new one) */
+int orc_serve_add(int n, const int64_t* T, const int64_t* D, const int64_t* A, const int64_t* B, const int64_t* u,
+                  const uint8_t* type, const uint8_t* part_in, const int16_t* size_in, int np_in, int64_t M,
+                  int64_t g, int64_t kc, int64_t km, int policy, int act, uint8_t* verdict, uint8_t* reason,
+                  uint8_t* path, uint8_t* part_out, int16_t* size_out, int32_t* n_parts, int32_t* Pi, int64_t* W) {
+  oset s = {n + 1, T, D, A, B, u, type};
+  omodel md = {M, g, kc, km};
+  if (n + 1 > ONMAX || !valid_model(&md) || !valid_set(&s)) return O_ERR_RANGE;
+  const int nw = n;  /* index of the new task */
+  int np = np_in;
+  for (int i = 0; i < n; i++) part_out[i] = part_in[i];
+  for (int p = 0; p < np; p++) size_out[p] = size_in[p];
+  int64_t pi = 0;
+  for (int p = 0; p < np; p++) pi += size_in[p];
+  const int64_t spare = M - pi;
+  unsigned char in[ONMAX];
+  *verdict = 0;
+  *reason = R_OK;
+  *path = PATH_NONE;
+  /* fit into an existing partition at its size */
+  for (int p = 0; p < np && *path == PATH_NONE; p++) {
+    for (int i = 0; i <= n; i++) in[i] = (i == nw) || (i < n && part_in[i] == p);
+    if (rta(&s, &md, in, size_in[p], NULL)) { part_out[nw] = (uint8_t)p; *path = PATH_FIT; }
+  }
+  /* grow a partition into the spare SMs */
+  for (int p = 0; p < np && *path == PATH_NONE && spare >= g; p++) {
+    for (int i = 0; i <= n; i++) in[i] = (i == nw) || (i < n && part_in[i] == p);
+    int64_t m = minm_linear(&s, &md, in, size_in[p] + g, size_in[p] + spare);
+    if (m) { part_out[nw] = (uint8_t)p; size_out[p] = (int16_t)m; *path = PATH_GROW; }
+  }
+  /* a new partition of the task's Lemma 2 size */
+  if (*path == PATH_NONE) {
+    for (int i = 0; i <= n; i++) in[i] = i == nw;
+    int64_t z = minm_linear(&s, &md, in, g, M);
+    if (z && z <= spare) { part_out[nw] = (uint8_t)np; size_out[np] = (int16_t)z; np++; *path = PATH_NEW; }
+  }
+  if (*path != PATH_NONE) {
+    *verdict = 1;
+    *n_parts = np;
+    summarise(&s, &md, part_out, size_out, np, Pi, W);
+    return O_OK;
+  }
+  /* Alg. 1 on every task */
+  ores r;
+  uint8_t pt[ONMAX];
+  int16_t sz[ONMAX];
+  int st = allocate_one(&s, &md, policy, act, 1, &r, pt, sz);
+  if (st != O_OK) return st;
+  *reason = r.reason;
+  if (r.verdict) {
+    *verdict = 1;
+    *path = PATH_REALLOC;
+    for (int i = 0; i <= n; i++) part_out[i] = pt[i];
+    for (int p = 0; p <= n; p++) size_out[p] = sz[p];
+    *n_parts = r.n_parts;
+    *Pi = r.Pi;
+    *W = r.W;
+    return O_OK;
+  }
+  /* rejected: the state is unchanged (n tasks) */
+  oset s0 = {n, T, D, A, B, u, type};
+  *n_parts = np_in;
+  summarise(&s0, &md, part_out, size_out, np_in, Pi, W);
+  return O_OK;
+}
+
+/* tasks: the state's n tasks; removes task `index` */
+int orc_serve_remove(int n, const int64_t* T, const int64_t* D, const int64_t* A, const int64_t* B,
+                     const int64_t* u, const uint8_t* type, const uint8_t* part_in, const int16_t* size_in,
+                     int np_in, int index, int64_t M, int64_t g, int64_t kc, int64_t km, int64_t* T_out,
+                     int64_t* D_out, int64_t* A_out, int64_t* B_out, int64_t* u_out, uint8_t* type_out,
+                     uint8_t* part_out, int16_t* size_out, int32_t* n_parts, int32_t* Pi, int64_t* W) {
+  omodel md = {M, g, kc, km};
+  if (index < 0 || index >= n || !valid_model(&md)) return O_ERR_RANGE;
+  int k = 0;
+  for (int i = 0; i < n; i++) {
+    if (i == index) continue;
+    T_out[k] = T[i];
+    D_out[k] = D[i];
+    A_out[k] = A[i];
+    B_out[k] = B[i];
+    u_out[k] = u[i];
+    type_out[k] = type[i];
+    part_out[k] = part_in[i];
+    k++;
+  }
+  const int n2 = n - 1;
+  oset s = {n2, T_out, D_out, A_out, B_out, u_out, type_out};
+  int np = np_in;
+  for (int p = 0; p < np; p++) size_out[p] = size_in[p];
+  const int pr = part_in[index];
+  int still = 0;
+  for (int i = 0; i < n2; i++) still |= part_out[i] == pr;
+  if (!still) {
+    /* the partition is gone: close the gap in the numbering */
+    for (int i = 0; i < n2; i++)
+      if (part_out[i] > pr) part_out[i]--;
+    for (int p = pr; p + 1 < np; p++) size_out[p] = size_out[p + 1];
+    np--;
+  } else {
+    unsigned char in[ONMAX];
+    for (int i = 0; i < n2; i++) in[i] = part_out[i] == pr;
+    size_out[pr] = (int16_t)minm_linear(&s, &md, in, g, size_in[pr]);
+  }
+  canonical(n2, part_out, size_out, np);
+  *n_parts = np;
+  summarise(&s, &md, part_out, size_out, np, Pi, W);
+  return O_OK;
+}

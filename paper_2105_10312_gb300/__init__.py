@@ -362,3 +362,89 @@ def to_device(sets, device="cuda"):
         else:
             out[k] = v
     return out
+
+
+# --- serving ------------------------------------------------------------------
+
+SERVE_OP = {"ADMIT": 0, "ADD": 1, "REMOVE": 2, "EVICT": 3}
+PATH = {"NONE": 0, "FIT": 1, "GROW": 2, "NEW": 3, "REALLOC": 4}
+
+
+class ServeCfg(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int32), ("g", ctypes.c_int32), ("k_c_pm", ctypes.c_int32), ("k_m_pm", ctypes.c_int32),
+                ("policy", ctypes.c_int32), ("act", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("nstreams", ctypes.c_int32), ("queue_cap", ctypes.c_int32), ("slots_per_chunk", ctypes.c_int32),
+                ("max_tenants", ctypes.c_int64), ("reserve_bytes", ctypes.c_int64)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("n", ctypes.c_int32), ("tenant", ctypes.c_int64), ("index", ctypes.c_int32),
+                ("pad_", ctypes.c_int32), ("T", _vp), ("D", _vp), ("A", _vp), ("B", _vp), ("u_ppm", _vp),
+                ("type", _vp)]
+
+
+class Response(ctypes.Structure):
+    _fields_ = [("req_id", ctypes.c_uint64), ("status", ctypes.c_int32), ("verdict", ctypes.c_uint8),
+                ("reason", ctypes.c_uint8), ("path", ctypes.c_uint8), ("pad_", ctypes.c_uint8),
+                ("n_tasks", ctypes.c_int32), ("n_parts", ctypes.c_int32), ("Pi", ctypes.c_int32),
+                ("W", ctypes.c_int64), ("part_of_task", ctypes.c_uint8 * NMAX), ("size_of_part", ctypes.c_int16 * NMAX),
+                ("latency_us", ctypes.c_double)]
+
+    def as_dict(self):
+        n, k = self.n_tasks, self.n_parts
+        return {"req_id": self.req_id, "status": self.status, "verdict": self.verdict, "reason": self.reason,
+                "path": self.path, "n_tasks": n, "n_parts": k, "Pi": self.Pi, "W": self.W,
+                "part_of_task": np.array(self.part_of_task[:n], np.uint8),
+                "size_of_part": np.array(self.size_of_part[:k], np.int16), "latency_us": self.latency_us}
+
+
+def _serve_sigs(L):
+    L.gpa_serve_start.argtypes = [_vp, ctypes.POINTER(ServeCfg)]
+    L.gpa_serve_submit.argtypes = [_vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+    L.gpa_serve_poll.argtypes = [_vp, ctypes.c_uint64, ctypes.POINTER(Response), ctypes.c_int64]
+    L.gpa_serve_stop.argtypes = [_vp]
+    L.gpa_serve_stats.argtypes = [_vp] + [ctypes.POINTER(ctypes.c_int64)] * 5
+
+
+class Server:
+    """The admission-control server of a Context (gpa_serve_*)."""
+
+    def __init__(self, ctx, M, g=1, k_c_pm=1200, k_m_pm=2300, policy="SMS", act=False, max_batch=1024, nstreams=3,
+                 queue_cap=1 << 20, slots_per_chunk=256, max_tenants=1 << 16, reserve_bytes=1 << 30):
+        _serve_sigs(lib())
+        self.ctx = ctx
+        cfg = ServeCfg(M, g, k_c_pm, k_m_pm, POLICY[policy], 1 if act else 0, max_batch, nstreams, queue_cap,
+                       slots_per_chunk, max_tenants, reserve_bytes)
+        _check(lib().gpa_serve_start(ctx.handle, ctypes.byref(cfg)))
+        self.running = True
+
+    def submit(self, op, tenant, tasks=None, index=0):
+        """tasks: dict of numpy columns (T, D, A, B, u_ppm, type) for ADMIT (n tasks) or ADD (1 task)."""
+        keep = []
+        cols = [None] * 6
+        n = 0
+        if tasks is not None:
+            for i, k in enumerate(("T", "D", "A", "B", "u_ppm", "type")):
+                a = np.ascontiguousarray(tasks[k], np.uint8 if k == "type" else np.int64)
+                keep.append(a)
+                cols[i] = a.ctypes.data
+            n = len(keep[0])
+        rq = Request(SERVE_OP[op], n, int(tenant), int(index), 0, *cols)
+        rid = ctypes.c_uint64()
+        _check(lib().gpa_serve_submit(self.ctx.handle, ctypes.byref(rq), ctypes.byref(rid)))
+        return rid.value
+
+    def poll(self, req_id, timeout_us=10_000_000):
+        r = Response()
+        _check(lib().gpa_serve_poll(self.ctx.handle, ctypes.c_uint64(req_id), ctypes.byref(r), int(timeout_us)))
+        return r.as_dict()
+
+    def stats(self):
+        v = [ctypes.c_int64() for _ in range(5)]
+        _check(lib().gpa_serve_stats(self.ctx.handle, *[ctypes.byref(x) for x in v]))
+        return dict(zip(("completed", "batches", "max_batch", "overlapped", "slots"), [x.value for x in v]))
+
+    def stop(self):
+        if self.running:
+            _check(lib().gpa_serve_stop(self.ctx.handle))
+            self.running = False

@@ -15,47 +15,13 @@
 //    or BF (Def. 4) order, exactly as the CPU reading does.
 #include <cuda_runtime.h>
 
+#include "alloc_dev.cuh"
 #include "gpa_device.cuh"
 #include "gpa_internal.h"
 
 namespace gpa {
 
 namespace {
-
-__device__ __forceinline__ void write_invalid(long long s, long long o, long long n, const AllocOut& out,
-                                              unsigned int* err) {
-  const int lane = threadIdx.x & 31;
-  if (lane == 0) {
-    out.verdict[s] = 0;
-    out.reason[s] = GPA_REASON_INVALID;
-    out.n_parts[s] = 0;
-    out.Pi[s] = 0;
-    out.W[s] = 0;
-    if (out.n_tests) out.n_tests[s] = 0;
-    atomicOr(err, kErrRange);
-  }
-  for (long long t = lane; t < n; t += 32) {
-    out.part_of_task[o + t] = 255;
-    out.size_of_part[o + t] = 0;
-  }
-}
-
-__device__ __forceinline__ void write_empty(long long s, long long o, int n, unsigned char reason, const AllocOut& out,
-                                            int tests) {
-  const int lane = threadIdx.x & 31;
-  if (lane == 0) {
-    out.verdict[s] = 0;
-    out.reason[s] = reason;
-    out.n_parts[s] = 0;
-    out.Pi[s] = 0;
-    out.W[s] = 0;
-    if (out.n_tests) out.n_tests[s] = tests;
-  }
-  for (int t = lane; t < n; t += 32) {
-    out.part_of_task[o + t] = 255;
-    out.size_of_part[o + t] = 0;
-  }
-}
 
 // ------------------------------------------------------------- fast kernel
 //
@@ -181,308 +147,6 @@ __global__ void __launch_bounds__(256) alloc_fast(DevSets S, DevModel md, AllocO
         }
       }
     }
-  }
-}
-
-// ------------------------------------------------------------ merge kernel
-
-struct MergeSmem {
-  SetSmem st;
-  RtaScratch sc;
-  unsigned int mask[kNmax][kWords];  // tasks (rows) of each partition slot
-  unsigned int actm[kNmax][kWords];  // rows forbidden to the slot by ACT pairs
-  unsigned int forb[kNmax][kWords];  // slots whose exact pair with this slot failed
-  unsigned int act[kNmax][kWords];   // ACT pair matrix over rows
-  unsigned long long Uc[kNmax];      // utilisation of the slot's compute tasks
-  unsigned long long Um[kNmax];      // utilisation of the slot's memory tasks
-  unsigned long long wkey[kNmax];    // BF: workload of each candidate merge
-  unsigned short m[kNmax];           // slot size (SMs)
-  unsigned char nc[kNmax], nm[kNmax];
-  unsigned char lowest[kNmax];       // lowest original task index in the slot
-  unsigned char alive[kNmax];
-  unsigned char order[kNmax];        // par_list: slots in order
-  unsigned char cand[kNmax];         // BF: eligible slots sorted by (W, position)
-  unsigned char slot_of[kNmax];      // slot of each row
-  unsigned char rank[kNmax];         // output numbering of each slot
-};
-
-__device__ __forceinline__ bool mask_meets(const unsigned int* a, const unsigned int* b) {
-  unsigned int x = 0;
-#pragma unroll
-  for (int w = 0; w < kWords; w++) x |= a[w] & b[w];
-  return x != 0u;
-}
-
-// par_list order (decreasing utilisation, ties to the lower lowest index).
-__device__ int sort_par_list(MergeSmem& sm, int nslots) {
-  const int lane = threadIdx.x & 31;
-  int alive_count = 0;
-  for (int x = lane; x < nslots; x += 32) alive_count += sm.alive[x];
-  alive_count = warp_sum_i32(alive_count);
-  for (int x = lane; x < nslots; x += 32) {
-    if (!sm.alive[x]) continue;
-    unsigned long long ux = sm.Uc[x] + sm.Um[x];
-    int r = 0;
-    for (int y = 0; y < nslots; y++) {
-      if (!sm.alive[y] || y == x) continue;
-      unsigned long long uy = sm.Uc[y] + sm.Um[y];
-      r += (uy > ux) || (uy == ux && sm.lowest[y] < sm.lowest[x]);
-    }
-    sm.order[r] = (unsigned char)x;
-  }
-  __syncwarp();
-  return alive_count;
-}
-
-// Eligibility of every slot for a merge with slot c (Alg. 3: partners in a forbidden pair are excluded).
-__device__ __forceinline__ void eligible_of(const MergeSmem& sm, int c, int nslots, unsigned int* elig) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int w = 0; w < kWords; w++) {
-    const int e = w * 32 + lane;
-    bool ok = e < nslots && sm.alive[e] && e != c && !((sm.forb[c][w] >> lane) & 1u) &&
-              !mask_meets(sm.mask[e], sm.actm[c]);
-    elig[w] = __ballot_sync(kFull, ok);
-  }
-}
-
-__device__ void apply_merge(MergeSmem& sm, int a, int b, unsigned int m3, int nslots) {
-  const int lane = threadIdx.x & 31;
-  __syncwarp();
-  if (lane < kWords) {
-    sm.mask[a][lane] |= sm.mask[b][lane];
-    sm.actm[a][lane] |= sm.actm[b][lane];
-    sm.forb[a][lane] = 0u;
-    sm.forb[b][lane] = 0u;
-  }
-  if (lane == 0) {
-    sm.m[a] = (unsigned short)m3;
-    sm.Uc[a] += sm.Uc[b];
-    sm.Um[a] += sm.Um[b];
-    sm.nc[a] = (unsigned char)(sm.nc[a] + sm.nc[b]);
-    sm.nm[a] = (unsigned char)(sm.nm[a] + sm.nm[b]);
-    sm.lowest[a] = min(sm.lowest[a], sm.lowest[b]);
-    sm.alive[b] = 0;
-  }
-  __syncwarp();
-  // the merged slot holds a task set never seen before: clear its column
-  for (int x = lane; x < nslots; x += 32) {
-    sm.forb[x][a >> 5] &= ~(1u << (a & 31));
-    sm.forb[x][b >> 5] &= ~(1u << (b & 31));
-    if (sm.slot_of[x] == b) sm.slot_of[x] = (unsigned char)a;
-  }
-  __syncwarp();
-}
-
-__device__ void merge_set(MergeSmem& sm, long long s, long long o, int n, const DevModel& md, const gpa_params& p,
-                          const AllocOut& out, const MagicDiv* mdiv, unsigned int* err) {
-  const int lane = threadIdx.x & 31;
-  const unsigned kc = (unsigned)md.kc, km = (unsigned)md.km, g = (unsigned)md.g, M = (unsigned)md.M;
-  const bool linear = p.linear_merge != 0;
-
-  // Lemma 1: sum_i floor(10^6 C^n_i(1) / T_i) > 10^6 M rejects the set.
-  unsigned long long l1 = 0;
-  for (int r = lane; r < n; r += 32) {
-    unsigned long long c1 = (sm.st.A[r] + sm.st.B[r] + 999ull) / 1000ull;  // C^n(1)
-    l1 += c1 * 1000000ull / sm.st.T[r];
-  }
-  l1 = warp_sum_u64(l1);
-  if (l1 > 1000000ull * M) {
-    write_empty(s, o, n, GPA_REASON_LEMMA1, out, 0);
-    return;
-  }
-  // init_partitions (Lemma 2): slot r = row r
-  bool none = false;
-  int pi = 0;
-  for (int r = lane; r < kNmax; r += 32) {
-    unsigned int mr = 0;
-    if (r < n) {
-      mr = lemma2_size(sm.st.A[r], sm.st.B[r], sm.st.D[r], M, g);
-      none = none || mr == 0u;
-      pi += (int)mr;
-      const bool mem = (sm.st.memmask[r >> 5] >> (r & 31)) & 1u;
-      sm.m[r] = (unsigned short)mr;
-      sm.Uc[r] = mem ? 0ull : sm.st.u[r];
-      sm.Um[r] = mem ? sm.st.u[r] : 0ull;
-      sm.nc[r] = mem ? 0 : 1;
-      sm.nm[r] = mem ? 1 : 0;
-      sm.lowest[r] = sm.st.orig[r];
-      sm.alive[r] = 1;
-      sm.slot_of[r] = (unsigned char)r;
-    } else {
-      sm.alive[r] = 0;
-    }
-#pragma unroll
-    for (int w = 0; w < kWords; w++) {
-      sm.mask[r][w] = (r < n && (r >> 5) == w) ? (1u << (r & 31)) : 0u;
-      sm.actm[r][w] = 0u;
-      sm.forb[r][w] = 0u;
-      sm.act[r][w] = 0u;
-    }
-  }
-  none = __any_sync(kFull, none);
-  pi = warp_sum_i32(pi);
-  __syncwarp();
-  if (none) {
-    write_empty(s, o, n, GPA_REASON_LEMMA2, out, 0);
-    return;
-  }
-  int tests = 0;
-  // ACT: every task pair is tried as a merge of two singletons; pairs that
-  // fail are forbidden for the rest of the run (§5.3).
-  if (p.act && pi > (int)M) {
-    for (int a = 0; a < n; a++)
-      for (int b = a + 1; b < n; b++) {
-        unsigned int S2[kWords];
-#pragma unroll
-        for (int w = 0; w < kWords; w++) S2[w] = 0u;
-        S2[a >> 5] |= 1u << (a & 31);
-        S2[b >> 5] |= 1u << (b & 31);
-        unsigned int lo = max(sm.m[a], sm.m[b]), hi = sm.m[a] + sm.m[b] - g;
-        unsigned int m3 = warp_minm(sm.st, S2, lo, hi, g, linear, kc, km, mdiv, sm.sc, err);
-        tests++;
-        if (m3 == 0u && lane == 0) {
-          sm.act[a][b >> 5] |= 1u << (b & 31);
-          sm.act[b][a >> 5] |= 1u << (a & 31);
-        }
-      }
-    __syncwarp();
-    for (int r = lane; r < n; r += 32)
-#pragma unroll
-      for (int w = 0; w < kWords; w++) sm.actm[r][w] = sm.act[r][w];
-    __syncwarp();
-  }
-
-  bool stuck = false;
-  while (pi > (int)M) {
-    const int nal = sort_par_list(sm, n);
-    // Alg. 3: the first partition in par_list order with an eligible partner
-    int p1 = -1;
-    unsigned int elig[kWords];
-    for (int r = 0; r < nal; r++) {
-      const int c = sm.order[r];
-      eligible_of(sm, c, n, elig);
-      unsigned int any = 0u;
-#pragma unroll
-      for (int w = 0; w < kWords; w++) any |= elig[w];
-      if (any) {
-        p1 = c;
-        break;
-      }
-    }
-    if (p1 < 0) {
-      stuck = true;
-      break;
-    }
-    unsigned int U[kWords];
-    if (p.policy == GPA_POLICY_SMS) {
-      // Def. 3: compute every candidate merge; smallest size wins, ties to
-      // the earlier par_list position.
-      int best = -1;
-      unsigned int best_m = 0u;
-      for (int r = 0; r < nal; r++) {
-        const int e = sm.order[r];
-        if (!((elig[e >> 5] >> (e & 31)) & 1u)) continue;
-#pragma unroll
-        for (int w = 0; w < kWords; w++) U[w] = sm.mask[p1][w] | sm.mask[e][w];
-        unsigned int lo = max(sm.m[p1], sm.m[e]), hi = sm.m[p1] + sm.m[e] - g;
-        unsigned int m3 = warp_minm(sm.st, U, lo, hi, g, linear, kc, km, mdiv, sm.sc, err);
-        tests++;
-        if (m3 != 0u && (best < 0 || m3 < best_m)) {
-          best = e;
-          best_m = m3;
-        }
-      }
-      if (best >= 0) {
-        pi -= (int)sm.m[p1] + (int)sm.m[best] - (int)best_m;
-        apply_merge(sm, p1, best, best_m, n);
-      } else {
-        __syncwarp();
-        for (int e = lane; e < n; e += 32)
-          if ((elig[e >> 5] >> (e & 31)) & 1u) {
-            atomicOr(&sm.forb[p1][e >> 5], 1u << (e & 31));
-            atomicOr(&sm.forb[e][p1 >> 5], 1u << (p1 & 31));
-          }
-        __syncwarp();
-      }
-    } else {
-      // Def. 4: eligible partners sorted by the workload of the merge, ties
-      // to the earlier par_list position; tried in that order.
-      int ne = 0;
-      for (int r = 0; r < nal; r++) {
-        const int e = sm.order[r];
-        if (!((elig[e >> 5] >> (e & 31)) & 1u)) continue;
-        if (lane == 0) {
-          sm.cand[ne] = (unsigned char)e;
-          sm.wkey[ne] = workload_from_sums(sm.Uc[p1] + sm.Uc[e], sm.Um[p1] + sm.Um[e], sm.nc[p1] + sm.nc[e],
-                                           sm.nm[p1] + sm.nm[e], kc, km);
-        }
-        ne++;
-      }
-      __syncwarp();
-      unsigned char sorted_e[kWords];
-      int sorted_r[kWords];
-      for (int c = 0; c < kWords; c++) {
-        const int x = c * 32 + lane;
-        sorted_r[c] = -1;
-        if (x < ne) {
-          int rr = 0;
-          for (int y = 0; y < ne; y++) rr += (sm.wkey[y] < sm.wkey[x]) || (sm.wkey[y] == sm.wkey[x] && y < x);
-          sorted_r[c] = rr;
-          sorted_e[c] = sm.cand[x];
-        }
-      }
-      __syncwarp();
-      for (int c = 0; c < kWords; c++)
-        if (sorted_r[c] >= 0) sm.cand[sorted_r[c]] = sorted_e[c];
-      __syncwarp();
-      for (int k = 0; k < ne; k++) {
-        const int e = sm.cand[k];
-#pragma unroll
-        for (int w = 0; w < kWords; w++) U[w] = sm.mask[p1][w] | sm.mask[e][w];
-        unsigned int lo = max(sm.m[p1], sm.m[e]), hi = sm.m[p1] + sm.m[e] - g;
-        unsigned int m3 = warp_minm(sm.st, U, lo, hi, g, linear, kc, km, mdiv, sm.sc, err);
-        tests++;
-        if (m3 != 0u) {
-          pi -= (int)sm.m[p1] + (int)sm.m[e] - (int)m3;
-          apply_merge(sm, p1, e, m3, n);
-          break;
-        }
-        if (lane == 0) {
-          sm.forb[p1][e >> 5] |= 1u << (e & 31);
-          sm.forb[e][p1 >> 5] |= 1u << (p1 & 31);
-        }
-        __syncwarp();
-      }
-    }
-  }
-  // report: partitions numbered by their lowest task index
-  int nal = 0;
-  unsigned long long W = 0;
-  for (int x = lane; x < n; x += 32) {
-    if (!sm.alive[x]) continue;
-    nal++;
-    W += workload_from_sums(sm.Uc[x], sm.Um[x], sm.nc[x], sm.nm[x], kc, km);
-    int r = 0;
-    for (int y = 0; y < n; y++) r += sm.alive[y] && sm.lowest[y] < sm.lowest[x];
-    sm.rank[x] = (unsigned char)r;
-  }
-  nal = warp_sum_i32(nal);
-  W = warp_sum_u64(W);
-  __syncwarp();
-  for (int r = lane; r < n; r += 32) out.size_of_part[o + r] = 0;
-  __syncwarp();
-  for (int x = lane; x < n; x += 32)
-    if (sm.alive[x]) out.size_of_part[o + sm.rank[x]] = (short)sm.m[x];
-  for (int r = lane; r < n; r += 32) out.part_of_task[o + sm.st.orig[r]] = sm.rank[sm.slot_of[r]];
-  if (lane == 0) {
-    const bool ok = !stuck && pi <= (int)M;
-    out.verdict[s] = ok ? 1 : 0;
-    out.reason[s] = ok ? GPA_REASON_OK : GPA_REASON_NO_MERGE;
-    out.n_parts[s] = nal;
-    out.Pi[s] = pi;
-    out.W[s] = (long long)W;
-    if (out.n_tests) out.n_tests[s] = tests;
   }
 }
 

@@ -474,3 +474,72 @@ def test_rgs_and_composition_counts():
     total = sum(math.comb(19, k - 1) * k**12 for k in range(1, 5))
     assert total == 16348076540  # explicit (split x map) candidates per 12-task set on 20 units
     assert [len(list(refs.compositions(8, 2)))] == [7]
+
+
+# ------------------------------------------------------------- serving ops
+
+def _check_state(t, M, g):
+    """The tenant's allocation passes (Lemma 3), every partition passes at its
+    size and that size is its minimum, Pi and W are consistent."""
+    n = t.n
+    if n == 0:
+        assert t.n_parts == 0 and t.Pi == 0
+        return
+    parts = {}
+    for i in range(n):
+        parts.setdefault(int(t.part[i]), []).append(i)
+    assert sorted(parts) == list(range(t.n_parts))
+    # numbered by lowest task index
+    assert [min(parts[p]) for p in range(t.n_parts)] == sorted(min(v) for v in parts.values())
+    total = 0
+    Wsum = 0
+    for p, rows in parts.items():
+        mask = np.zeros(n, np.uint8)
+        mask[rows] = 1
+        z = int(t.size[p])
+        total += z
+        args = [t.tasks[k] for k in ("T", "D", "A", "B", "type")]
+        assert oracle.rta(*args, mask, z, KC, KM)[0] == 1
+        assert oracle.minm(*args, mask, g, M, g, KC, KM) == z
+        Wsum += sum(refs.conflict_k(t.tasks["type"], set(rows), i, KC, KM) * int(t.tasks["u_ppm"][i]) for i in rows)
+    assert total == t.Pi <= M
+    assert Wsum == t.W
+
+
+def test_serving_operations_keep_minimal_passing_allocations():
+    import serve_seq
+    M, g = 148, 1
+    ops = serve_seq.make_ops(12, 25, seed=3)
+    paths = set()
+    for seq in ops:
+        t = oracle.Tenant(M, g, KC, KM)
+        r = t.admit(seq[0][1])
+        if not r["verdict"]:
+            continue
+        _check_state(t, M, g)
+        for op, arg in seq[1:]:
+            if op == "ADD" and t.n < 128:
+                n0 = t.n
+                r = t.add(arg)
+                paths.add(r["path"])
+                assert t.n == n0 + (1 if r["verdict"] else 0)
+            elif op == "REMOVE" and t.n > 0:
+                t.remove(int(arg * t.n))
+            _check_state(t, M, g)
+    assert {1, 3} <= paths  # fits and new partitions both occur
+
+
+def test_serving_add_into_empty_tenant_takes_lemma2_size():
+    t = oracle.Tenant(8, 1, KC, KM)
+    empty = {k: np.zeros(0, np.uint8 if k == "type" else np.int64) for k in oracle.Tenant.COLS}
+    assert t.admit(empty)["verdict"] == 1
+    # C1 = 250 on a 100-tick deadline: alpha = 0 -> C(m) = ceil(250/m) -> m = 3
+    r = t.add({"T": 100, "D": 100, "A": 250000, "B": 0, "u_ppm": 2500000, "type": 0})
+    assert r["verdict"] == 1 and r["path"] == 3 and list(r["size_of_part"]) == [3] and r["Pi"] == 3
+    # a second compute task: the fit at 3 SMs would put both in conflict (k = 1.2)
+    r = t.add({"T": 100, "D": 100, "A": 100000, "B": 0, "u_ppm": 1000000, "type": 0})
+    assert r["verdict"] == 1
+    _check_state(t, 8, 1)
+    r = t.remove(0)
+    assert r["n_tasks"] == 1 and r["n_parts"] == 1
+    _check_state(t, 8, 1)
