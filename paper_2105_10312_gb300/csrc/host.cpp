@@ -8,7 +8,9 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <algorithm>
 #include <mutex>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -62,19 +64,36 @@ extern "C" int32_t gpa_validate(const gpa_tasksets* sets, const gpa_model* model
   if (sets->nsets < 0 || sets->n_max < 0 || sets->n_max > GPA_NMAX)
     return gpa_fail(GPA_ERR_RANGE, "gpa_validate: nsets/n_max out of range");
   if (sets->set_off[0] != 0) return gpa_fail(GPA_ERR_RANGE, "gpa_validate: set_off[0] != 0");
-  for (int64_t s = 0; s < sets->nsets; s++) {
-    int64_t o = sets->set_off[s], n = sets->set_off[s + 1] - o;
-    bool ok = n >= 0 && n <= sets->n_max;
-    if (ok && n > 0 && (!sets->T || !sets->D || !sets->A || !sets->B || !sets->type))
-      return gpa_fail(GPA_ERR_ARG, "gpa_validate: NULL task column");
-    for (int64_t t = 0; ok && t < n; t++)
-      ok = host_task_valid(sets->T[o + t], sets->D[o + t], sets->A[o + t], sets->B[o + t],
-                           sets->u_ppm ? sets->u_ppm[o + t] : 0, sets->type[o + t]);
-    if (!ok) {
+  if (sets->nsets > 0 && sets->set_off[sets->nsets] > 0 &&
+      (!sets->T || !sets->D || !sets->A || !sets->B || !sets->type))
+    return gpa_fail(GPA_ERR_ARG, "gpa_validate: NULL task column");
+  // sets are checked in parallel ranges; the first invalid set wins
+  auto check = [sets](int64_t s0, int64_t s1) -> int64_t {
+    for (int64_t s = s0; s < s1; s++) {
+      const int64_t o = sets->set_off[s], n = sets->set_off[s + 1] - o;
+      bool ok = n >= 0 && n <= sets->n_max;
+      for (int64_t t = 0; ok && t < n; t++)
+        ok = host_task_valid(sets->T[o + t], sets->D[o + t], sets->A[o + t], sets->B[o + t],
+                             sets->u_ppm ? sets->u_ppm[o + t] : 0, sets->type[o + t]);
+      if (!ok) return s;
+    }
+    return -1;
+  };
+  const int64_t ns = sets->nsets;
+  const int64_t ntasks = ns > 0 ? sets->set_off[ns] : 0;
+  int nth = (int)std::min<int64_t>(std::max(1u, std::thread::hardware_concurrency()), 32);
+  if (ntasks < 200000) nth = 1;
+  std::vector<int64_t> first((size_t)nth, -1);
+  std::vector<std::thread> pool;
+  for (int k = 1; k < nth; k++)
+    pool.emplace_back([&, k] { first[(size_t)k] = check(ns * k / nth, ns * (k + 1) / nth); });
+  first[0] = check(0, ns / nth);
+  for (auto& th : pool) th.join();
+  for (int64_t s : first)
+    if (s >= 0) {
       if (bad_set) *bad_set = s;
       return gpa_fail(GPA_ERR_RANGE, "gpa_validate: set %lld violates the bounds", (long long)s);
     }
-  }
   return GPA_OK;
 }
 

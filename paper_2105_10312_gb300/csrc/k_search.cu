@@ -10,9 +10,15 @@
 // CTA per task set
 //   phase A: computes minm(S) and the inflated workload W(S) of every
 //            non-empty subset S (one thread per subset, serial test);
-//   phase B: sweeps every restricted-growth string (RGS) with at most kmax
-//            blocks (threads take contiguous rank ranges), keeps the
-//            smallest key (W, sum minm, RGS), and reduces it over the CTA.
+//   phase B: enumerates restricted-growth strings (RGS) with at most kmax
+//            blocks depth first.  A job is an RGS prefix (jobs in
+//            lexicographic order, spread over the threads); a thread extends
+//            it label by label with the block masks, sum minm and W updated
+//            in place.  A branch is cut when a block becomes infeasible, sum
+//            minm exceeds M, or W exceeds the CTA's best W so far: all three
+//            only grow as tasks are added, so no cut branch holds the
+//            optimum.  Leaves are compared by the key (W, sum minm, RGS) and a
+//            CTA-wide shuffle argmin finishes.
 #include <cuda_runtime.h>
 
 #include "gpa_device.cuh"
@@ -25,6 +31,8 @@ namespace {
 constexpr int kSN = GPA_SEARCH_NMAX;  // tasks per set
 constexpr int kSK = GPA_SEARCH_KMAX;  // blocks per set partition
 constexpr int kSThreads = 256;
+constexpr int kSuffix = 4;            // RGS positions enumerated below a job's prefix
+constexpr int kTableMax = 2048;       // WCET table entries per curve (sizes x kSN)
 
 struct SearchHead {
   unsigned int T[kSN], D[kSN], mT[kSN], sh[kSN];
@@ -33,26 +41,51 @@ struct SearchHead {
   unsigned int memmask;        // rows of memory tasks
   unsigned int rowbit[kSN];    // original task -> bit of its DM row
   unsigned int singleton[kSN]; // Lemma 2 size of each row
-  unsigned long long cnt[kSN + 1][kSK + 2];  // RGS completion counts
+  unsigned long long cnt[kSN + 1][kSK + 2];  // prefix-completion counts (positions i..L-1)
   unsigned long long bestK1[kSThreads / 32];
   unsigned long long bestK2[kSThreads / 32];
+  unsigned long long gbestW;   // best W found by any thread of the CTA (for cutting)
   int n;
   long long set;
 };
 
+// Per-thread working storage in shared memory, laid out [field][thread] so
+// that a warp's accesses to one field hit 32 different banks.
+struct SearchThreads {
+  unsigned int C[kSN][kSThreads];           // WCETs of the current test (phase A)
+  unsigned short msk[kSK][kSThreads];       // block masks (phase B)
+  unsigned char lab[kSN][kSThreads];        // labels of the current path
+  unsigned char used[kSN + 1][kSThreads];   // blocks open before each position
+};
+
+// WCETs of one set at every size, when they fit in shared memory:
+// tn[mi * kSN + row] = C^n, tc[...] = C^c at m = g (mi + 1).
+struct WcetTables {
+  const unsigned int* tn;
+  const unsigned int* tc;
+};
+
 // Serial per-partition test (one thread): rows of S in priority order at m.
-__device__ bool serial_rta(const SearchHead& h, unsigned int S, unsigned int m, unsigned int kc, unsigned int km,
-                           const MagicDiv& md) {
+__device__ bool serial_rta(const SearchHead& h, SearchThreads& w, unsigned int S, unsigned int m, unsigned int g,
+                           unsigned int kc, unsigned int km, const MagicDiv& md, const WcetTables& tb) {
+  const int tid = threadIdx.x;
   const int nm = __popc(S & h.memmask), ns = __popc(S);
-  const unsigned int kmem = nm >= 2 ? km : 1000u, kcmp = (ns - nm) >= 2 ? kc : 1000u;
-  unsigned int C[kSN];
-  unsigned long long prefix = 0;
+  const bool cm = nm >= 2, cc = (ns - nm) >= 2;
+  const unsigned int kmem = cm ? km : 1000u, kcmp = cc ? kc : 1000u;
+  const int mi = (int)(m / g) - 1;
+  // Tasks are visited in priority order, and every one before task i met its
+  // deadline (the test stops at the first miss), so R_i >= R_prev + C_i: the
+  // iteration starts there instead of at the sum of the WCETs (same least
+  // fixed point, fewer steps).
+  unsigned long long Rprev = 0;
   for (unsigned int rest = S; rest; rest &= rest - 1u) {
     const int i = __ffs(rest) - 1;
-    const unsigned int Ci = wcet(h.A[i], h.B[i], ((h.memmask >> i) & 1u) ? kmem : kcmp, m, md);
-    C[i] = Ci;
-    unsigned long long R = prefix + Ci;
-    prefix = R;
+    const bool mem = (h.memmask >> i) & 1u;
+    unsigned int Ci;
+    if (tb.tn) Ci = ((mem ? cm : cc) ? tb.tc : tb.tn)[mi * kSN + i];
+    else Ci = wcet(h.A[i], h.B[i], mem ? kmem : kcmp, m, md);
+    w.C[i][tid] = Ci;
+    unsigned long long R = Rprev + Ci;
     const unsigned int Di = h.D[i];
     const unsigned int hp = S & ((1u << i) - 1u);
     int iter = 0;
@@ -62,36 +95,32 @@ __device__ bool serial_rta(const SearchHead& h, unsigned int S, unsigned int m, 
       unsigned long long next = Ci;
       for (unsigned int r2 = hp; r2; r2 &= r2 - 1u) {
         const int j = __ffs(r2) - 1;
-        const unsigned long long t = (unsigned long long)ceil_div_T((unsigned int)R, h.mT[j], h.sh[j]) * C[j];
+        const unsigned long long t = (unsigned long long)ceil_div_T((unsigned int)R, h.mT[j], h.sh[j]) * w.C[j][tid];
         next += t < cap ? t : cap;
       }
       if (next == R) break;
       R = next;
       if (++iter > kIterCap) return false;
     }
+    Rprev = R;
   }
   return true;
 }
 
-// smallest multiple of g in [g, M] at which S passes (0 if none): binary
-// search between the largest singleton size of S and M.
-__device__ unsigned int serial_minm(const SearchHead& h, unsigned int S, const DevModel& md,
-                                    const MagicDiv* __restrict__ mdiv) {
-  unsigned int lo = md.g;
-  for (unsigned int r = S; r; r &= r - 1u) {
-    const unsigned int z = h.singleton[__ffs(r) - 1];
-    if (z == 0u) return 0u;
-    lo = max(lo, z);
-  }
+// Smallest multiple of g in [lo, M] at which S passes (0 if none), for a lo
+// known not to exceed the answer (the largest Lemma 2 size of S's tasks): a
+// binary search over lo .. M with M + g standing for "no size passes" (valid
+// because the test is monotone in m, §4.1).
+__device__ unsigned int serial_minm(const SearchHead& h, SearchThreads& w, unsigned int S, unsigned int lo,
+                                    const DevModel& md, const MagicDiv* __restrict__ mdiv, const WcetTables& tb) {
   const unsigned int g = md.g, M = md.M;
-  if (!serial_rta(h, S, M, md.kc, md.km, mdiv[M])) return 0u;
-  unsigned int a = lo / g, b = M / g;
+  unsigned int a = lo / g, b = M / g + 1u;
   while (a < b) {
     const unsigned int mid = a + (b - a) / 2u;
-    if (serial_rta(h, S, mid * g, md.kc, md.km, mdiv[mid * g])) b = mid;
+    if (serial_rta(h, w, S, mid * g, g, md.kc, md.km, mdiv[mid * g], tb)) b = mid;
     else a = mid + 1u;
   }
-  return a * g;
+  return a * g <= M ? a * g : 0u;
 }
 
 __device__ __forceinline__ bool key_less(unsigned long long a1, unsigned long long a2, unsigned long long b1,
@@ -101,11 +130,15 @@ __device__ __forceinline__ bool key_less(unsigned long long a1, unsigned long lo
 
 __global__ void __launch_bounds__(kSThreads) search_sets(DevSets S, DevModel md, int kmin, int kmax, BestOut out,
                                                          unsigned int* err, const MagicDiv* __restrict__ mdiv,
-                                                         unsigned long long* ticket, int nsub_max) {
+                                                         unsigned long long* ticket, int nsub_max, int tab_cap) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SearchHead& h = *reinterpret_cast<SearchHead*>(smem_raw);
-  unsigned long long* Wsub = reinterpret_cast<unsigned long long*>(smem_raw + sizeof(SearchHead));
+  SearchThreads& w = *reinterpret_cast<SearchThreads*>(smem_raw + sizeof(SearchHead));
+  unsigned long long* Wsub = reinterpret_cast<unsigned long long*>(smem_raw + sizeof(SearchHead) +
+                                                                   sizeof(SearchThreads));
   unsigned short* msub = reinterpret_cast<unsigned short*>(Wsub + nsub_max);
+  unsigned int* tabn = reinterpret_cast<unsigned int*>(msub + nsub_max + (nsub_max & 1));
+  unsigned int* tabc = tabn + tab_cap;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned long long kNoKey = ~0ull;
 
@@ -118,8 +151,9 @@ __global__ void __launch_bounds__(kSThreads) search_sets(DevSets S, DevModel md,
     const long long o = S.set_off[s];
     const long long nl = S.set_off[s + 1] - o;
     // ---- stage (warp 0): validate, DM order, Lemma 2 sizes
-    bool bad = nl < 0 || nl > kSN || (1ll << (nl < 0 ? 0 : nl)) > nsub_max;
+    const bool bad = nl < 0 || nl > kSN || (1ll << (nl < 0 ? 0 : nl)) > nsub_max;
     const int n = bad ? 0 : (int)nl;
+    const int L = n > kSuffix ? n - kSuffix : (n > 0 ? 1 : 0);  // job prefix length
     if (warp == 0) {
       bool ok = !bad;
       long long Tt = 0, Dt = 0, At = 0, Bt = 0, ut = 0;
@@ -156,7 +190,6 @@ __global__ void __launch_bounds__(kSThreads) search_sets(DevSets S, DevModel md,
                                      (unsigned)md.M, (unsigned)md.g);
       }
       const unsigned int mem = __ballot_sync(kFull, ok && lane < n && yt == 1u);
-      // memmask over rows: rebuild from the rank of each memory task
       unsigned int mm = 0u;
       for (int j = 0; j < kSN; j++) {
         const int rj = __shfl_sync(kFull, r, j);
@@ -165,12 +198,13 @@ __global__ void __launch_bounds__(kSThreads) search_sets(DevSets S, DevModel md,
       if (lane == 0) {
         h.memmask = mm;
         h.n = ok ? n : -1;
+        h.gbestW = kNoKey;
       }
-      // RGS completion counts: cnt[i][j] = ways to label positions i..n-1
+      // prefix-completion counts: cnt[i][j] = ways to label positions i..L-1
       // with j blocks already open and at most kmax blocks in total
       if (lane == 0 && ok) {
-        for (int j = 0; j <= kmax + 1; j++) h.cnt[n][j] = 1ull;
-        for (int i = n - 1; i >= 0; i--)
+        for (int j = 0; j <= kmax + 1; j++) h.cnt[L][j] = 1ull;
+        for (int i = L - 1; i >= 0; i--)
           for (int j = 0; j <= kmax; j++) {
             unsigned long long c = (unsigned long long)j * h.cnt[i + 1][j];
             if (j < kmax) c += h.cnt[i + 1][j + 1];
@@ -206,13 +240,34 @@ __global__ void __launch_bounds__(kSThreads) search_sets(DevSets S, DevModel md,
     }
     // ---- phase A: minm and W of every non-empty subset of rows
     const unsigned int nsub = 1u << n;
+    const int Mu = md.M / md.g;
+    WcetTables tb{nullptr, nullptr};
+    if (Mu * kSN <= tab_cap) {
+      for (int e = tid; e < Mu * n; e += kSThreads) {
+        const int mi = e / n, row = e % n;
+        const unsigned int m = (unsigned)md.g * (unsigned)(mi + 1);
+        const bool mem = (h.memmask >> row) & 1u;
+        tabn[mi * kSN + row] = wcet(h.A[row], h.B[row], 1000u, m, mdiv[m]);
+        tabc[mi * kSN + row] = wcet(h.A[row], h.B[row], mem ? (unsigned)md.km : (unsigned)md.kc, m, mdiv[m]);
+      }
+      tb = WcetTables{tabn, tabc};
+    }
+    __syncthreads();
     for (unsigned int S2 = tid; S2 < nsub; S2 += kSThreads) {
       if (S2 == 0u) {
         msub[0] = 0;
         Wsub[0] = 0;
         continue;
       }
-      msub[S2] = (unsigned short)serial_minm(h, S2, md, mdiv);
+      // lower bound: the largest Lemma 2 size of its tasks (0: some task alone is infeasible)
+      unsigned int lo = 0u;
+      bool dead = false;
+      for (unsigned int r = S2; r; r &= r - 1u) {
+        const unsigned int z = h.singleton[__ffs(r) - 1];
+        dead = dead || z == 0u;
+        lo = max(lo, z);
+      }
+      msub[S2] = (unsigned short)(dead ? 0u : (__popc(S2) == 1 ? lo : serial_minm(h, w, S2, lo, md, mdiv, tb)));
       const int nmS = __popc(S2 & h.memmask), ncS = __popc(S2) - nmS;
       unsigned long long Uc = 0, Um = 0;
       for (unsigned int r = S2; r; r &= r - 1u) {
@@ -222,72 +277,103 @@ __global__ void __launch_bounds__(kSThreads) search_sets(DevSets S, DevModel md,
       Wsub[S2] = workload_from_sums(Uc, Um, ncS, nmS, md.kc, md.km);
     }
     __syncthreads();
-    // ---- phase B: every RGS with <= kmax blocks, contiguous rank ranges
-    const unsigned long long total = h.cnt[1][1];
-    const unsigned long long per = (total + kSThreads - 1) / kSThreads;
-    const unsigned long long r0 = per * tid;
-    const unsigned long long r1 = min(total, r0 + per);
-    unsigned long long best1 = kNoKey, best2 = kNoKey;
-    if (r0 < r1) {
-      unsigned char a[kSN];
-      // unrank r0
-      a[0] = 0;
-      unsigned long long rank = r0;
-      int used = 1;
-      for (int i = 1; i < n; i++) {
-        const int top = used < kmax ? used : kmax - 1;
-        for (int b = 0; b <= top; b++) {
-          const int nu = b + 1 > used ? b + 1 : used;
-          const unsigned long long c = h.cnt[i + 1][nu];
-          if (rank < c) {
-            a[i] = (unsigned char)b;
-            used = nu;
-            break;
-          }
-          rank -= c;
-        }
-      }
-      for (unsigned long long r = r0; r < r1; r++) {
-        unsigned int mask[kSK];
-        int nb = 0;
+    // ---- phase B: depth-first over RGS, jobs = prefixes of length L
+    const unsigned long long njobs = h.cnt[1][1];
+    const unsigned int M = (unsigned)md.M;
+    unsigned long long best1 = kNoKey, best2 = kNoKey;  // (W << 11 | sum minm, packed RGS)
+    for (unsigned long long job = tid; job < njobs; job += kSThreads) {
 #pragma unroll
-        for (int b = 0; b < kSK; b++) mask[b] = 0u;
-        unsigned long long packed = 0ull;
-        for (int i = 0; i < n; i++) {
-          mask[a[i]] |= h.rowbit[i];
-          nb = max(nb, (int)a[i] + 1);
-          packed = (packed << 3) | a[i];
+      for (int b = 0; b < kSK; b++) w.msk[b][tid] = 0;
+      unsigned long long Wp = 0;
+      unsigned int Sp = 0;
+      bool dead = false;
+      // unrank the prefix; task 0 is in block 0
+      unsigned long long rank = job;
+      int used = 0;
+      for (int i = 0; i < L; i++) {
+        int b = 0;
+        if (i > 0) {
+          const int top = used < kmax ? used : kmax - 1;
+          for (b = 0; b <= top; b++) {
+            const int nu = b + 1 > used ? b + 1 : used;
+            const unsigned long long c = h.cnt[i + 1][nu];
+            if (rank < c) break;
+            rank -= c;
+          }
         }
-        unsigned int sm = 0u;
-        unsigned long long W = 0ull;
-        bool ok = true;
-        for (int b = 0; b < nb; b++) {
-          const unsigned int z = msub[mask[b]];
-          ok = ok && z != 0u;
-          sm += z;
-          W += Wsub[mask[b]];
-        }
+        w.lab[i][tid] = (unsigned char)b;
+        w.used[i][tid] = (unsigned char)used;
+        used = b + 1 > used ? b + 1 : used;
+        const unsigned int old = w.msk[b][tid], nw = old | h.rowbit[i];
+        w.msk[b][tid] = (unsigned short)nw;
+        Wp += Wsub[nw] - Wsub[old];
+        Sp += (unsigned)msub[nw] - (unsigned)msub[old];
+        dead = dead || msub[nw] == 0;
+      }
+      w.used[L][tid] = (unsigned char)used;
+      if (dead || Sp > M || Wp > *(volatile unsigned long long*)&h.gbestW) continue;
+      // depth-first over positions L..n-1; lab = 255 means "not placed yet"
+      int i = L;
+      if (i == n) {
+        // the whole RGS is the prefix
+        const int nb = used;
         const int empty = kmin > nb ? kmin - nb : 0;
-        if (ok && (long long)sm + (long long)empty * md.g <= md.M) {
-          const unsigned long long k1 = (W << 11) | sm;
+        if ((long long)Sp + (long long)empty * md.g <= md.M) {
+          unsigned long long packed = 0;
+          for (int k = 0; k < n; k++) packed = (packed << 3) | w.lab[k][tid];
+          const unsigned long long k1 = (Wp << 11) | Sp;
           if (key_less(k1, packed, best1, best2)) {
             best1 = k1;
             best2 = packed;
+            atomicMin(&h.gbestW, Wp);
           }
         }
-        // lexicographic successor: bump the last position that can grow
-        if (r + 1 < r1) {
-          unsigned char pm[kSN];
-          pm[0] = 0;
-          for (int i = 1; i < n; i++) pm[i] = max(pm[i - 1], (unsigned char)(a[i - 1]));
-          int i = n - 1;
-          for (; i >= 1; i--) {
-            const int lim = min((int)pm[i] + 1, kmax - 1);
-            if (a[i] < lim) break;
-          }
-          a[i]++;
-          for (int j = i + 1; j < n; j++) a[j] = 0;
+        continue;
+      }
+      w.lab[i][tid] = 255;
+      while (i >= L) {
+        unsigned int lb = w.lab[i][tid];
+        const unsigned int bit = h.rowbit[i];
+        if (lb != 255u) {  // take task i out of its current block
+          const unsigned int old = w.msk[lb][tid], nw = old & ~bit;
+          w.msk[lb][tid] = (unsigned short)nw;
+          Wp -= Wsub[old] - Wsub[nw];
+          Sp -= (unsigned)msub[old] - (unsigned)msub[nw];
         }
+        lb = lb == 255u ? 0u : lb + 1u;
+        const unsigned int u_i = w.used[i][tid];
+        const unsigned int top = u_i < (unsigned)kmax ? u_i : (unsigned)kmax - 1u;
+        if (lb > top) {  // labels exhausted: back up
+          w.lab[i][tid] = 255;
+          i--;
+          continue;
+        }
+        w.lab[i][tid] = (unsigned char)lb;
+        const unsigned int old = w.msk[lb][tid], nw = old | bit;
+        w.msk[lb][tid] = (unsigned short)nw;
+        Wp += Wsub[nw] - Wsub[old];
+        Sp += (unsigned)msub[nw] - (unsigned)msub[old];
+        if (msub[nw] == 0 || Sp > M || Wp > *(volatile unsigned long long*)&h.gbestW) continue;
+        const unsigned int u_next = lb + 1u > u_i ? lb + 1u : u_i;
+        if (i + 1 == n) {
+          const int empty = kmin > (int)u_next ? kmin - (int)u_next : 0;
+          if ((long long)Sp + (long long)empty * md.g <= md.M) {
+            const unsigned long long k1 = (Wp << 11) | Sp;
+            if (k1 <= best1) {
+              unsigned long long packed = 0;
+              for (int k = 0; k < n; k++) packed = (packed << 3) | w.lab[k][tid];
+              if (key_less(k1, packed, best1, best2)) {
+                best1 = k1;
+                best2 = packed;
+                atomicMin(&h.gbestW, Wp);
+              }
+            }
+          }
+          continue;
+        }
+        w.used[i + 1][tid] = (unsigned char)u_next;
+        i++;
+        w.lab[i][tid] = 255;
       }
     }
     // ---- CTA argmin of (k1, k2)
@@ -320,7 +406,6 @@ __global__ void __launch_bounds__(kSThreads) search_sets(DevSets S, DevModel md,
       int ai = 0;
       if (lane < n) ai = found ? (int)((best2 >> (3 * (n - 1 - lane))) & 7ull) : 255;
       if (lane < n) out.rgs[o + lane] = (unsigned char)ai;
-      // block masks of the winner
       int nb = 0;
       unsigned int bm[kSK];
       for (int b = 0; b < kSK; b++) bm[b] = 0u;
@@ -350,15 +435,17 @@ __global__ void __launch_bounds__(kSThreads) search_sets(DevSets S, DevModel md,
   }
 }
 
-size_t search_smem_bytes(int nsub_max) {
-  return sizeof(SearchHead) + (size_t)nsub_max * (sizeof(unsigned long long) + sizeof(unsigned short));
+size_t search_smem_bytes(int nsub_max, int tab_cap) {
+  return sizeof(SearchHead) + sizeof(SearchThreads) +
+         (size_t)nsub_max * (sizeof(unsigned long long) + sizeof(unsigned short)) + 4 +
+         2 * (size_t)tab_cap * sizeof(unsigned int);
 }
 
 }  // namespace
 
 cudaError_t search_kernels_init() {
   return cudaFuncSetAttribute(search_sets, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)search_smem_bytes(1 << kSN));
+                              (int)search_smem_bytes(1 << kSN, kTableMax));
 }
 
 cudaError_t launch_search_best(const DevSets& s, const DevModel& md, int kmin, int kmax, const BestOut& out,
@@ -366,8 +453,12 @@ cudaError_t launch_search_best(const DevSets& s, const DevModel& md, int kmin, i
                                long long* launches, Prof* prof) {
   int nmax = s.n_max < 0 ? 0 : (s.n_max > kSN ? kSN : s.n_max);
   const int nsub_max = 1 << nmax;
-  const size_t smem = search_smem_bytes(nsub_max);
-  const int per_sm = smem <= 56 * 1024 ? 4 : (smem <= 110 * 1024 ? 2 : 1);
+  const int Mu = md.M / md.g;
+  const int tab_cap = Mu * kSN <= kTableMax ? Mu * kSN : 0;  // WCET tables only when they are small
+  const size_t smem = search_smem_bytes(nsub_max, tab_cap);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_sets, kSThreads, smem);
+  if (per_sm < 1) per_sm = 1;
   long long blocks = (long long)sm_count * per_sm;
   if (blocks > s.nsets) blocks = s.nsets > 0 ? s.nsets : 1;
   unsigned long long* ticket = q.counters + 3;
@@ -376,7 +467,7 @@ cudaError_t launch_search_best(const DevSets& s, const DevModel& md, int kmin, i
   if (e != cudaSuccess) return e;
   prof_mark(prof, st);
   search_sets<<<(int)blocks, kSThreads, smem, st>>>(s, md, kmin, kmax, out, err,
-                                                     reinterpret_cast<const MagicDiv*>(mdiv), ticket, nsub_max);
+                                                     reinterpret_cast<const MagicDiv*>(mdiv), ticket, nsub_max, tab_cap);
   e = cudaGetLastError();
   prof_mark(prof, st);
   *launches += 1;
