@@ -50,9 +50,21 @@ __device__ __forceinline__ void write_empty(long long s, long long o, int n, uns
 
 // ------------------------------------------------------------ merge kernel
 
+constexpr int kLaneMax = 16;  // merged sets of up to this many tasks are tested by one lane
+
+// One lane's serial test of a candidate merge: WCETs and rows of the merged
+// set's tasks in priority order, [position][lane] (conflict-free banks).
+struct LaneScratch {
+  unsigned int C[kLaneMax][32];
+  unsigned char row[kLaneMax][32];
+  unsigned short res[kNmax];  // size found per candidate; 0 none; kLaneNone: not tried by a lane
+};
+constexpr unsigned short kLaneNone = 0xFFFFu;
+
 struct MergeSmem {
   SetSmem st;
   RtaScratch sc;
+  LaneScratch ls;
   unsigned int mask[kNmax][kWords];  // tasks (rows) of each partition slot
   unsigned int actm[kNmax][kWords];  // rows forbidden to the slot by ACT pairs
   unsigned int forb[kNmax][kWords];  // slots whose exact pair with this slot failed
@@ -69,6 +81,102 @@ struct MergeSmem {
   unsigned char slot_of[kNmax];      // slot of each row
   unsigned char rank[kNmax];         // output numbering of each slot
 };
+
+
+// §5.5 per-partition test of a merged set S (at most kLaneMax tasks) by one
+// lane, serially.  Tasks are visited in priority order and each earlier task
+// met its deadline, so R_i >= R_prev + C_i starts the iteration (same least
+// fixed point as starting from the sum of the WCETs).
+__device__ bool lane_rta(const SetSmem& st, const unsigned int* S, unsigned int m, unsigned int kc, unsigned int km,
+                         const MagicDiv& md, LaneScratch& ls, int lane, unsigned int* err) {
+  int nm = 0, ns = 0;
+#pragma unroll
+  for (int w = 0; w < kWords; w++) {
+    nm += __popc(S[w] & st.memmask[w]);
+    ns += __popc(S[w]);
+  }
+  const unsigned int kmem = nm >= 2 ? km : 1000u, kcmp = (ns - nm) >= 2 ? kc : 1000u;
+  unsigned long long Rprev = 0;
+  int pos = 0;
+  for (int w = 0; w < kWords; w++) {
+    for (unsigned int bits = S[w]; bits; bits &= bits - 1u) {
+      const int row = w * 32 + __ffs(bits) - 1;
+      const bool mem = (st.memmask[w] >> (row & 31)) & 1u;
+      const unsigned int Ci = wcet(st.A[row], st.B[row], mem ? kmem : kcmp, m, md);
+      ls.C[pos][lane] = Ci;
+      ls.row[pos][lane] = (unsigned char)row;
+      unsigned long long R = Rprev + Ci;
+      const unsigned int Di = st.D[row];
+      const unsigned long long cap = (unsigned long long)Di + 1ull;
+      int iter = 0;
+      for (;;) {
+        if (R > Di) return false;
+        unsigned long long next = Ci;
+        for (int q = 0; q < pos; q++) {
+          const int rq = ls.row[q][lane];
+          const unsigned long long t = (unsigned long long)ceil_div_T((unsigned int)R, st.mT[rq], st.shT[rq]) *
+                                       ls.C[q][lane];
+          next += t < cap ? t : cap;
+        }
+        if (next == R) break;
+        R = next;
+        if (++iter > kIterCap) {
+          atomicOr(err, kErrIter);
+          return false;
+        }
+      }
+      Rprev = R;
+      pos++;
+    }
+  }
+  return true;
+}
+
+// Alg. 2 by one lane: the first size in lo, lo + g, ..., hi that passes.
+__device__ unsigned int lane_minm(const SetSmem& st, const unsigned int* S, unsigned int lo, unsigned int hi,
+                                  unsigned int g, unsigned int kc, unsigned int km, const MagicDiv* __restrict__ mdiv,
+                                  LaneScratch& ls, int lane, unsigned int* err) {
+  for (unsigned int m = lo; m <= hi; m += g)
+    if (lane_rta(st, S, m, kc, km, mdiv[m], ls, lane, err)) return m;
+  return 0u;
+}
+
+// Sizes of the candidate merges of slot p1 with cand[c0 .. c1) into ls.res:
+// one lane per candidate when the merged set is small, then the warp for
+// the others.  Warp-uniform arguments.
+__device__ void size_candidates(MergeSmem& sm, int p1, int c0, int c1, unsigned int g, bool linear, unsigned int kc,
+                                unsigned int km, const MagicDiv* __restrict__ mdiv, unsigned int* err) {
+  const int lane = threadIdx.x & 31;
+  for (int b = c0; b < c1; b += 32) {
+    const int k = b + lane;
+    if (k < c1) {
+      const int e = sm.cand[k];
+      unsigned int U[kWords];
+      int cnt = 0;
+#pragma unroll
+      for (int w = 0; w < kWords; w++) {
+        U[w] = sm.mask[p1][w] | sm.mask[e][w];
+        cnt += __popc(U[w]);
+      }
+      const unsigned int lo = max(sm.m[p1], sm.m[e]), hi = sm.m[p1] + sm.m[e] - g;
+      sm.ls.res[k] = cnt <= kLaneMax ? (unsigned short)lane_minm(sm.st, U, lo, hi, g, kc, km, mdiv, sm.ls, lane, err)
+                                     : kLaneNone;
+    }
+  }
+  __syncwarp();
+  for (int k = c0; k < c1; k++) {
+    if (sm.ls.res[k] != kLaneNone) continue;
+    const int e = sm.cand[k];
+    unsigned int U[kWords];
+#pragma unroll
+    for (int w = 0; w < kWords; w++) U[w] = sm.mask[p1][w] | sm.mask[e][w];
+    const unsigned int lo = max(sm.m[p1], sm.m[e]), hi = sm.m[p1] + sm.m[e] - g;
+    const unsigned int m3 = warp_minm(sm.st, U, lo, hi, g, linear, kc, km, mdiv, sm.sc, err);
+    __syncwarp();
+    if (lane == 0) sm.ls.res[k] = (unsigned short)m3;
+    __syncwarp();
+  }
+}
 
 __device__ __forceinline__ bool mask_meets(const unsigned int* a, const unsigned int* b) {
   unsigned int x = 0;
@@ -195,21 +303,24 @@ __device__ void merge_set(MergeSmem& sm, long long s, long long o, int n, const 
   // ACT: every task pair is tried as a merge of two singletons; pairs that
   // fail are forbidden for the rest of the run (§5.3).
   if (p.act && pi > (int)M) {
+    // one lane per pair (a, b), b > a
     for (int a = 0; a < n; a++)
-      for (int b = a + 1; b < n; b++) {
-        unsigned int S2[kWords];
+      for (int b0 = a + 1; b0 < n; b0 += 32) {
+        const int b = b0 + lane;
+        if (b < n) {
+          unsigned int S2[kWords];
 #pragma unroll
-        for (int w = 0; w < kWords; w++) S2[w] = 0u;
-        S2[a >> 5] |= 1u << (a & 31);
-        S2[b >> 5] |= 1u << (b & 31);
-        unsigned int lo = max(sm.m[a], sm.m[b]), hi = sm.m[a] + sm.m[b] - g;
-        unsigned int m3 = warp_minm(sm.st, S2, lo, hi, g, linear, kc, km, mdiv, sm.sc, err);
-        tests++;
-        if (m3 == 0u && lane == 0) {
-          sm.act[a][b >> 5] |= 1u << (b & 31);
-          sm.act[b][a >> 5] |= 1u << (a & 31);
+          for (int w = 0; w < kWords; w++) S2[w] = 0u;
+          S2[a >> 5] |= 1u << (a & 31);
+          S2[b >> 5] |= 1u << (b & 31);
+          const unsigned int lo = max(sm.m[a], sm.m[b]), hi = sm.m[a] + sm.m[b] - g;
+          if (lane_minm(sm.st, S2, lo, hi, g, kc, km, mdiv, sm.ls, lane, err) == 0u) {
+            atomicOr(&sm.act[a][b >> 5], 1u << (b & 31));
+            atomicOr(&sm.act[b][a >> 5], 1u << (a & 31));
+          }
         }
       }
+    tests += n * (n - 1) / 2;
     __syncwarp();
     for (int r = lane; r < n; r += 32)
 #pragma unroll
@@ -238,25 +349,28 @@ __device__ void merge_set(MergeSmem& sm, long long s, long long o, int n, const 
       stuck = true;
       break;
     }
-    unsigned int U[kWords];
     if (p.policy == GPA_POLICY_SMS) {
       // Def. 3: compute every candidate merge; smallest size wins, ties to
       // the earlier par_list position.
-      int best = -1;
-      unsigned int best_m = 0u;
+      int ne = 0;
       for (int r = 0; r < nal; r++) {
         const int e = sm.order[r];
         if (!((elig[e >> 5] >> (e & 31)) & 1u)) continue;
-#pragma unroll
-        for (int w = 0; w < kWords; w++) U[w] = sm.mask[p1][w] | sm.mask[e][w];
-        unsigned int lo = max(sm.m[p1], sm.m[e]), hi = sm.m[p1] + sm.m[e] - g;
-        unsigned int m3 = warp_minm(sm.st, U, lo, hi, g, linear, kc, km, mdiv, sm.sc, err);
-        tests++;
-        if (m3 != 0u && (best < 0 || m3 < best_m)) {
-          best = e;
-          best_m = m3;
-        }
+        if (lane == 0) sm.cand[ne] = (unsigned char)e;
+        ne++;
       }
+      __syncwarp();
+      size_candidates(sm, p1, 0, ne, g, linear, kc, km, mdiv, err);
+      tests += ne;
+      // smallest size, then earliest position: key = size << 8 | position
+      unsigned int keyv = 0xFFFFFFFFu;
+      for (int k = lane; k < ne; k += 32) {
+        const unsigned int m3 = sm.ls.res[k];
+        if (m3 != 0u) keyv = min(keyv, (m3 << 8) | (unsigned int)k);
+      }
+      keyv = __reduce_min_sync(kFull, keyv);
+      const int best = keyv == 0xFFFFFFFFu ? -1 : (int)sm.cand[keyv & 0xFFu];
+      const unsigned int best_m = keyv >> 8;
       if (best >= 0) {
         pi -= (int)sm.m[p1] + (int)sm.m[best] - (int)best_m;
         apply_merge(sm, p1, best, best_m, n);
@@ -300,23 +414,29 @@ __device__ void merge_set(MergeSmem& sm, long long s, long long o, int n, const 
       for (int c = 0; c < kWords; c++)
         if (sorted_r[c] >= 0) sm.cand[sorted_r[c]] = sorted_e[c];
       __syncwarp();
-      for (int k = 0; k < ne; k++) {
-        const int e = sm.cand[k];
-#pragma unroll
-        for (int w = 0; w < kWords; w++) U[w] = sm.mask[p1][w] | sm.mask[e][w];
-        unsigned int lo = max(sm.m[p1], sm.m[e]), hi = sm.m[p1] + sm.m[e] - g;
-        unsigned int m3 = warp_minm(sm.st, U, lo, hi, g, linear, kc, km, mdiv, sm.sc, err);
-        tests++;
-        if (m3 != 0u) {
+      // tried in that order: chunks of 32 are sized together, the first
+      // success (in order) is applied, every earlier failure is forbidden
+      for (int c0 = 0; c0 < ne; c0 += 32) {
+        const int c1 = min(ne, c0 + 32);
+        size_candidates(sm, p1, c0, c1, g, linear, kc, km, mdiv, err);
+        const int k = c0 + lane;
+        const unsigned int okb = __ballot_sync(kFull, k < c1 && sm.ls.res[k] != 0u);
+        const int first = okb ? c0 + __ffs(okb) - 1 : c1;
+        if (k < first) {
+          const int e = sm.cand[k];
+          atomicOr(&sm.forb[p1][e >> 5], 1u << (e & 31));
+          atomicOr(&sm.forb[e][p1 >> 5], 1u << (p1 & 31));
+        }
+        __syncwarp();
+        if (okb) {
+          tests += first - c0 + 1;
+          const int e = sm.cand[first];
+          const unsigned int m3 = sm.ls.res[first];
           pi -= (int)sm.m[p1] + (int)sm.m[e] - (int)m3;
           apply_merge(sm, p1, e, m3, n);
           break;
         }
-        if (lane == 0) {
-          sm.forb[p1][e >> 5] |= 1u << (e & 31);
-          sm.forb[e][p1 >> 5] |= 1u << (p1 & 31);
-        }
-        __syncwarp();
+        tests += c1 - c0;
       }
     }
   }
