@@ -132,13 +132,25 @@ __device__ bool lane_rta(const SetSmem& st, const unsigned int* S, unsigned int 
   return true;
 }
 
-// Alg. 2 by one lane: the first size in lo, lo + g, ..., hi that passes.
+// Alg. 2 by one lane: the first size in lo, lo + g, ..., hi that passes.  A
+// range of up to three sizes is scanned; a longer one is bisected (§5.2),
+// which finds the same size because the test is monotone in m.
 __device__ unsigned int lane_minm(const SetSmem& st, const unsigned int* S, unsigned int lo, unsigned int hi,
                                   unsigned int g, unsigned int kc, unsigned int km, const MagicDiv* __restrict__ mdiv,
                                   LaneScratch& ls, int lane, unsigned int* err) {
-  for (unsigned int m = lo; m <= hi; m += g)
-    if (lane_rta(st, S, m, kc, km, mdiv[m], ls, lane, err)) return m;
-  return 0u;
+  if (lo > hi) return 0u;
+  if (hi - lo <= 2u * g) {
+    for (unsigned int m = lo; m <= hi; m += g)
+      if (lane_rta(st, S, m, kc, km, mdiv[m], ls, lane, err)) return m;
+    return 0u;
+  }
+  unsigned int a = lo / g, b = hi / g + 1u;  // b stands for "no size passes"
+  while (a < b) {
+    const unsigned int mid = a + (b - a) / 2u;
+    if (lane_rta(st, S, mid * g, kc, km, mdiv[mid * g], ls, lane, err)) b = mid;
+    else a = mid + 1u;
+  }
+  return a * g <= hi ? a * g : 0u;
 }
 
 // Sizes of the candidate merges of slot p1 with cand[c0 .. c1) into ls.res:

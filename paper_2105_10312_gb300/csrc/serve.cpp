@@ -60,6 +60,7 @@ struct StreamCtx {
   unsigned char* d_type = nullptr;
   std::vector<Pending> batch;
   std::vector<int> slot_of;  // slot per batch entry
+  int64_t pay_used = 0;
   bool busy = false;
   bool done = false;  // set by the completion callback
 };
@@ -104,22 +105,30 @@ void CUDART_CB on_batch_done(void* arg) {
   delete pr;
 }
 
-bool grow_slots(ServeState* S) {
+// Add one chunk of tenant slots if the device keeps reserve_bytes free.
+// Called by the batcher thread with the lock RELEASED (cudaMalloc may
+// synchronise with work whose completion callbacks need the lock); only
+// that thread changes the chunk list.
+bool grow_slots(ServeState* S, std::unique_lock<std::mutex>* lk) {
   const int per = kSlotsPerChunkMax;
-  if ((int)S->chunks.size() >= kMaxChunks) return false;
-  if ((int64_t)(S->chunks.size() + 1) * per > S->cfg.max_tenants + per) return false;
-  size_t free_b = 0, total_b = 0;
-  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return false;
-  const size_t bytes = sizeof(TenantSlot) * (size_t)per;
-  if (free_b < bytes + (size_t)S->cfg.reserve_bytes) return false;
-  TenantSlot* c = nullptr;
-  if (cudaMalloc(&c, bytes) != cudaSuccess) return false;
   const int idx = (int)S->chunks.size();
+  if (idx >= kMaxChunks) return false;
+  if ((int64_t)(idx + 1) * per > S->cfg.max_tenants + per) return false;
+  if (lk) lk->unlock();
+  bool ok = false;
+  TenantSlot* c = nullptr;
+  size_t free_b = 0, total_b = 0;
+  const size_t bytes = sizeof(TenantSlot) * (size_t)per;
+  if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && free_b >= bytes + (size_t)S->cfg.reserve_bytes &&
+      cudaMalloc(&c, bytes) == cudaSuccess) {
+    ok = cudaMemcpyAsync(S->d_chunks + idx, &c, sizeof(TenantSlot*), cudaMemcpyHostToDevice, S->setup_stream) ==
+             cudaSuccess &&
+         cudaStreamSynchronize(S->setup_stream) == cudaSuccess;
+    if (!ok) cudaFree(c);
+  }
+  if (lk) lk->lock();
+  if (!ok) return false;
   S->chunks.push_back(c);
-  if (cudaMemcpyAsync(S->d_chunks + idx, &S->chunks[idx], sizeof(TenantSlot*), cudaMemcpyHostToDevice,
-                      S->setup_stream) != cudaSuccess ||
-      cudaStreamSynchronize(S->setup_stream) != cudaSuccess)
-    return false;
   for (int k = per - 1; k >= 0; k--) S->free_slots.push_back(idx * per + k);
   return true;
 }
@@ -175,9 +184,10 @@ void harvest(ServeState* S, StreamCtx& sc) {
   sc.done = false;
 }
 
-// Pack and launch one micro-batch on sc (lock held).  Returns false if the
-// queue had nothing launchable.
-bool launch_batch(ServeState* S, StreamCtx& sc) {
+// Pack one micro-batch for sc into its pinned staging buffers (lock held;
+// no CUDA call).  Returns false if the queue had nothing launchable;
+// *need_slots is set when an ADMIT waits for a free tenant slot.
+bool form_batch(ServeState* S, StreamCtx& sc, bool* need_slots) {
   std::unordered_set<int64_t> blocked;
   int64_t pay_used = 0;
   const int cap = S->cfg.max_batch;
@@ -218,8 +228,9 @@ bool launch_batch(ServeState* S, StreamCtx& sc) {
     if (pay_used + p.n > S->pay_cap) break;
     int slot = -1;
     if (p.op == GPA_SERVE_ADMIT) {
-      if (S->free_slots.empty() && !grow_slots(S)) {
-        blocked.insert(p.tenant);  // waits for a slot or for memory
+      if (S->free_slots.empty()) {
+        *need_slots = true;
+        blocked.insert(p.tenant);  // waits for a slot (or for memory to add one)
         ++it;
         continue;
       }
@@ -252,7 +263,24 @@ bool launch_batch(ServeState* S, StreamCtx& sc) {
     it = S->queue.erase(it);
   }
   if (sc.batch.empty()) return false;
+  sc.pay_used = pay_used;
+  sc.busy = true;
+  sc.done = false;
+  S->n_batches++;
+  if ((int64_t)sc.batch.size() > S->max_batch_seen) S->max_batch_seen = (int64_t)sc.batch.size();
+  for (auto& o : S->streams)
+    if (&o != &sc && o.busy && !o.done) {
+      S->n_overlapped++;
+      break;
+    }
+  return true;
+}
+
+// Enqueue a formed batch (lock RELEASED: a launch may block until earlier
+// work, whose completion callback takes the lock, has drained).
+void issue_batch(ServeState* S, StreamCtx& sc) {
   const int nreq = (int)sc.batch.size();
+  const int64_t pay_used = sc.pay_used;
   cudaStream_t st = sc.stream;
   cudaMemcpyAsync(sc.d_req, sc.h_req, sizeof(ServeReq) * (size_t)nreq, cudaMemcpyHostToDevice, st);
   if (pay_used > 0) {
@@ -264,19 +292,8 @@ bool launch_batch(ServeState* S, StreamCtx& sc) {
   ServePayload pay{sc.d_pay, sc.d_pay + S->pay_cap, sc.d_pay + 2 * S->pay_cap, sc.d_pay + 3 * S->pay_cap,
                    sc.d_pay + 4 * S->pay_cap, sc.d_type};
   launch_serve_batch(sc.d_req, nreq, S->d_chunks, pay, sc.d_resp, S->md, S->prm, S->ctx->d_mdiv, S->d_err, st);
-  S->ctx->launches += 1;
   cudaMemcpyAsync(sc.h_resp, sc.d_resp, sizeof(ServeResp) * (size_t)nreq, cudaMemcpyDeviceToHost, st);
   cudaLaunchHostFunc(st, on_batch_done, new std::pair<ServeState*, StreamCtx*>(S, &sc));
-  sc.busy = true;
-  sc.done = false;
-  S->n_batches++;
-  if (nreq > S->max_batch_seen) S->max_batch_seen = nreq;
-  for (auto& o : S->streams)
-    if (&o != &sc && o.busy && !o.done) {
-      S->n_overlapped++;
-      break;
-    }
-  return true;
 }
 
 void worker_main(ServeState* S) {
@@ -289,13 +306,18 @@ void worker_main(ServeState* S) {
       any_busy = any_busy || sc.busy;
     }
     S->cv_done.notify_all();
-    bool launched = false;
+    bool launched = false, need_slots = false;
     if (!S->queue.empty())
       for (auto& sc : S->streams)
-        if (!sc.busy && launch_batch(S, sc)) {
+        if (!sc.busy && form_batch(S, sc, &need_slots)) {
+          lk.unlock();
+          issue_batch(S, sc);
+          lk.lock();
+          S->ctx->launches += 1;
           launched = true;
           any_busy = true;
         }
+    if (need_slots && grow_slots(S, &lk)) launched = true;  // retry the waiting ADMITs at once
     if (S->stop && S->queue.empty() && !any_busy) break;
     if (launched) continue;
     // sleep until a submission or a completion (bounded, so a queue blocked
@@ -371,7 +393,7 @@ extern "C" int32_t gpa_serve_start(gpa_ctx* c, const gpa_serve_cfg* cfg) {
   }
   if (ok) {
     const int want = cfg->slots_per_chunk > 0 ? cfg->slots_per_chunk : kSlotsPerChunkMax;
-    for (int got = 0; got < want && ok; got += kSlotsPerChunkMax) ok = grow_slots(S);
+    for (int got = 0; got < want && ok; got += kSlotsPerChunkMax) ok = grow_slots(S, nullptr);
   }
   if (!ok) {
     free_state(S);
