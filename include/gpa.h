@@ -24,7 +24,9 @@
  *    the kernels: an invalid set gets reason GPA_REASON_INVALID, its other
  *    outputs are zero, and the context's sticky error word is set; the call
  *    itself is asynchronous on the context stream and gpa_ctx_sync() reports
- *    GPA_ERR_RANGE afterwards.
+ *    GPA_ERR_RANGE afterwards.  The task columns of a device batch must hold
+ *    set_off[nsets] tasks; a set whose slice is not inside [0, set_off[nsets])
+ *    is invalid and its per-task outputs are left untouched.
  *  - Streams are passed as void* (a cudaStream_t); NULL is the legacy stream.
  *
  * Task model (paper §4.2, §7.1)
@@ -53,7 +55,7 @@
  *
  * Validation bounds (GPA_ERR_RANGE): 0 <= n <= 128 tasks per set,
  * 1 <= D <= T <= 2^31 - 1, A >= 0, B >= 0, 1 <= A + B <= 2^36,
- * 0 <= u_ppm <= 2^32, type in {0, 1}; model: 1 <= g, g | M, 1 <= M <= 1024,
+ * 0 <= u_ppm < 2^32, type in {0, 1}; model: 1 <= g, g | M, 1 <= M <= 1024,
  * 1000 <= k_c_pm, k_m_pm <= 16000.  These keep every WCET below 2^31 and
  * every intermediate product inside 64 bits.
  */
@@ -132,12 +134,17 @@ enum {
                                  batch signature and keep the fastest (default 0) */
   GPA_OPT_GRAPH = 2,          /* 1: capture gpa_allocate's launches in a CUDA graph per argument set and
                                  replay it (default 0); not allowed while the stream is being captured */
-  GPA_OPT_FAST_WARPS = 3,     /* force warps per CTA of the fast allocate kernel (0 = tuned/default) */
+  GPA_OPT_FAST_WARPS = 3,     /* force warps per CTA of the fast allocate kernel: 1, 2, 4 or 8 (the staged
+                                 form adds a copy warp) (0 = tuned/default) */
   GPA_OPT_FAST_CHUNK = 4,     /* force task sets per work-queue ticket (0 = tuned/default) */
   GPA_OPT_FAST_BLOCKS = 5,    /* force CTAs of the persistent grid (0 = tuned/default) */
   GPA_OPT_PER_SET_LAUNCH = 6, /* 1: the plain form, one launch sequence per task set (comparison only) */
-  GPA_OPT_PROFILE = 7         /* 1: record CUDA events around each kernel of every call (also inside
+  GPA_OPT_PROFILE = 7,        /* 1: record CUDA events around each kernel of every call (also inside
                                  captured graphs) so that gpa_ctx_last_timing can report them */
+  GPA_OPT_FAST_STAGES = 8     /* force how the fast allocate kernel reads the task columns: 1 = direct
+                                 loads; 2..5 = through that many shared-memory stages filled by bulk
+                                 copies, used only when every task column starts on a 16-byte
+                                 boundary (direct loads otherwise) (0 = tuned/default) */
 };
 int32_t gpa_ctx_set_option(gpa_ctx* ctx, int32_t option, int64_t value);
 

@@ -12,6 +12,12 @@ namespace gpa {
 
 namespace {
 
+// A set's task slice [o, o + n) lies inside the task columns, whose length
+// is set_off[nsets].
+__device__ __forceinline__ bool slice_inside(long long o, long long n, long long ntasks) {
+  return o >= 0 && n >= 0 && o <= ntasks - n;
+}
+
 __device__ __forceinline__ void write_invalid(long long s, long long o, long long n, const AllocOut& out,
                                               unsigned int* err) {
   const int lane = threadIdx.x & 31;

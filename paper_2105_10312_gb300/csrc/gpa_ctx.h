@@ -42,7 +42,7 @@ struct gpa_ctx {
   bool profile = false;
   gpa::Prof prof{};                          // timing events of direct (non-graph) calls
   const gpa::Prof* last_prof = nullptr;      // events of the last profiled call
-  gpa::LaunchShape force_fast{0, 0, 0};
+  gpa::LaunchShape force_fast{0, 0, 0, 0};
   std::map<std::string, gpa::LaunchShape> tuned;
   std::map<std::string, CachedGraph> graphs;
   ServeState* serve = nullptr;

@@ -26,6 +26,7 @@ constexpr int kIterCap = 1 << 20;         // response-time iterations per task b
 // error bits of the context's sticky error word
 constexpr unsigned kErrRange = 1u;        // a set failed device-side validation
 constexpr unsigned kErrIter = 2u;         // a response-time iteration hit kIterCap
+constexpr unsigned kErrWait = 4u;         // a pipeline barrier wait hit its time limit
 
 // floor(x / d) for 0 <= x < 2^60 and d = 10^6 m (m <= GPA_MMAX):
 // magic = ceil(2^(60+l) / d) with l = ceil(log2 d), then

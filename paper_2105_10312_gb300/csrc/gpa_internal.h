@@ -65,6 +65,7 @@ struct LaunchShape {
   int warps_per_block;  // warps per CTA
   int chunk;            // sets per ticket (fast kernel)
   int blocks;           // CTAs of the persistent grid
+  int stages;           // fast kernel: 1 = direct loads, 2..5 = shared-memory stages fed by bulk copies
 };
 
 struct BestOut {
@@ -109,6 +110,7 @@ cudaError_t launch_search_best(const DevSets& s, const DevModel& md, int kmin, i
 
 // Largest dynamic shared memory (bytes) the allocate merge kernel needs per CTA.
 size_t slow_smem_bytes(int warps_per_block);
+size_t staged_smem_bytes(int stages);
 size_t one_gpu_smem_bytes(int warps_per_block);
 
 }  // namespace gpa

@@ -246,6 +246,10 @@ extern "C" int32_t gpa_ctx_set_option(gpa_ctx* c, int32_t opt, int64_t value) {
       if (value < 0 || value > (1 << 20)) return gpa_fail(GPA_ERR_RANGE, "blocks");
       c->force_fast.blocks = (int)value;
       break;
+    case GPA_OPT_FAST_STAGES:
+      if (value < 0 || value > 5) return gpa_fail(GPA_ERR_RANGE, "stages (0 = tuned, 1 = direct loads, 2..5)");
+      c->force_fast.stages = (int)value;
+      break;
     case GPA_OPT_PER_SET_LAUNCH: c->per_set_launch = value != 0; break;
     case GPA_OPT_PROFILE:
       c->profile = value != 0;
@@ -267,6 +271,7 @@ extern "C" int32_t gpa_ctx_sync(gpa_ctx* c) {
   if (err) {
     cudaMemset(c->d_err, 0, sizeof(unsigned int));
     if (err & 2u) return gpa_fail(GPA_ERR_TIMEOUT, "a response-time iteration exceeded its step limit");
+    if (err & 4u) return gpa_fail(GPA_ERR_TIMEOUT, "a pipeline barrier wait exceeded its time limit");
     return gpa_fail(GPA_ERR_RANGE, "a device-resident set failed validation");
   }
   return GPA_OK;
@@ -467,9 +472,9 @@ extern "C" int32_t gpa_test_schedulable(gpa_ctx* c, const gpa_tasksets* sets, co
 // blocks = 0: the launcher sizes the grid to the kernel's occupancy x SMs
 static LaunchShape default_fast(const gpa_ctx* c) {
   (void)c;
-  return LaunchShape{8, 2, 0};
+  return LaunchShape{8, 2, 0, 1};
 }
-static LaunchShape default_slow(const gpa_ctx* c) { return LaunchShape{4, 1, c->sm_count * 2}; }
+static LaunchShape default_slow(const gpa_ctx* c) { return LaunchShape{4, 1, c->sm_count * 2, 1}; }
 
 static LaunchShape fast_shape(gpa_ctx* c, const DevSets& ds, const DevModel& md, const gpa_params& p) {
   LaunchShape sh = default_fast(c);
@@ -478,6 +483,7 @@ static LaunchShape fast_shape(gpa_ctx* c, const DevSets& ds, const DevModel& md,
   if (c->force_fast.warps_per_block) sh.warps_per_block = c->force_fast.warps_per_block;
   if (c->force_fast.chunk) sh.chunk = c->force_fast.chunk;
   if (c->force_fast.blocks) sh.blocks = c->force_fast.blocks;
+  if (c->force_fast.stages) sh.stages = c->force_fast.stages;
   return sh;
 }
 
@@ -492,7 +498,7 @@ static cudaError_t run_allocate(gpa_ctx* c, const DevSets& ds, const DevModel& m
                                 const AllocOut& out, const LaunchShape& fast, Prof* prof) {
   AllocQueue q{c->d_counters, c->d_slow, c->d_err};
   if (p.policy == GPA_POLICY_ONE_GPU) {
-    LaunchShape sh{8, 1, c->sm_count * 4};
+    LaunchShape sh{8, 1, c->sm_count * 4, 1};
     return launch_one_gpu(ds, md, out, q, c->d_mdiv, sh, c->stream, &c->launches, prof);
   }
   return launch_allocate(ds, md, p, out, q, c->d_mdiv, fast, default_slow(c), c->stream, &c->launches, prof);
@@ -506,29 +512,35 @@ static void autotune_allocate(gpa_ctx* c, const DevSets& ds, const DevModel& md,
   if (c->tuned.count(key)) return;
   static const int warps_opts[] = {4, 8};
   static const int chunk_opts[] = {1, 2, 3, 4, 8};
+  // direct loads: warps {4, 8} x chunks {1, 2, 3, 4, 8}; staged: compute
+  // warps {4, 8} x chunks {1, 2, 4} x stages {2, 3}
+  std::vector<LaunchShape> shapes;
+  for (int w : warps_opts)
+    for (int ch : chunk_opts) shapes.push_back(LaunchShape{w, ch, 0, 1});
+  for (int w : warps_opts)
+    for (int ch : {1, 2, 4})
+      for (int stg : {2, 3}) shapes.push_back(LaunchShape{w, ch, 0, stg});
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best_ms = 1e30f;
   LaunchShape best = default_fast(c);
-  for (int w : warps_opts)
-    for (int ch : chunk_opts) {
-      LaunchShape sh{w, ch, 0};
-      float tot = 0.f;
-      for (int rep = 0; rep < 3; rep++) {
-        cudaEventRecord(e0, c->stream);
-        run_allocate(c, ds, md, p, out, sh, nullptr);
-        cudaEventRecord(e1, c->stream);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (rep > 0) tot += ms;
-      }
-      if (tot < best_ms) {
-        best_ms = tot;
-        best = sh;
-      }
+  for (const LaunchShape& sh : shapes) {
+    float tot = 0.f;
+    for (int rep = 0; rep < 3; rep++) {
+      cudaEventRecord(e0, c->stream);
+      run_allocate(c, ds, md, p, out, sh, nullptr);
+      cudaEventRecord(e1, c->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) tot += ms;
     }
+    if (tot < best_ms) {
+      best_ms = tot;
+      best = sh;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   c->tuned[key] = best;
@@ -537,12 +549,12 @@ static void autotune_allocate(gpa_ctx* c, const DevSets& ds, const DevModel& md,
 static std::string graph_key(const DevSets& ds, const DevModel& md, const gpa_params& p, const AllocOut& o,
                              const LaunchShape& sh) {
   char buf[512];
-  std::snprintf(buf, sizeof buf, "%lld|%d|%p|%p|%p|%p|%p|%p|%p|%d|%d|%d|%d|%d|%d|%d|%p|%p|%p|%p|%p|%p|%p|%p|%d|%d|%d",
+  std::snprintf(buf, sizeof buf, "%lld|%d|%p|%p|%p|%p|%p|%p|%p|%d|%d|%d|%d|%d|%d|%d|%p|%p|%p|%p|%p|%p|%p|%p|%d|%d|%d|%d",
                 ds.nsets, ds.n_max, (const void*)ds.set_off, (const void*)ds.T, (const void*)ds.D,
                 (const void*)ds.A, (const void*)ds.B, (const void*)ds.u, (const void*)ds.type, md.M, md.g, md.kc,
                 md.km, p.policy, p.act, p.linear_merge, (void*)o.verdict, (void*)o.reason, (void*)o.n_parts,
                 (void*)o.Pi, (void*)o.W, (void*)o.n_tests, (void*)o.part_of_task, (void*)o.size_of_part,
-                sh.warps_per_block, sh.chunk, sh.blocks);
+                sh.warps_per_block, sh.chunk, sh.blocks, sh.stages);
   return buf;
 }
 
@@ -563,9 +575,9 @@ static int32_t allocate_device(gpa_ctx* c, const DevSets& ds, const DevModel& md
       o1.Pi += s;
       o1.W += s;
       if (o1.n_tests) o1.n_tests += s;
-      LaunchShape one_shape{1, 1, 1};
+      LaunchShape one_shape{1, 1, 1, 1};
       AllocQueue q{c->d_counters, c->d_slow, c->d_err};
-      LaunchShape slow1{1, 1, 1};
+      LaunchShape slow1{1, 1, 1, 1};
       cudaError_t e =
           launch_allocate(one, md, p, o1, q, c->d_mdiv, one_shape, slow1, c->stream, &c->launches, nullptr);
       if (e != cudaSuccess) return gpa_cuda_fail(e, "per-set allocate launch");

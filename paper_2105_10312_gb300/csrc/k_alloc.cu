@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include "alloc_dev.cuh"
+#include "bulk_pipe.cuh"
 #include "gpa_device.cuh"
 #include "gpa_internal.h"
 
@@ -35,13 +36,97 @@ namespace {
 // here; the others are appended to the merge kernel's queue, which rewrites
 // their per-task outputs.
 
+// Per-task step of the fast kernel for one task already loaded: validity
+// (the same conditions as task_valid, grouped so that the common checks are
+// a few 32-bit operations), the Lemma 2 size and the split utilisation.
+// For a valid task A + B <= 2^36 and 1000 D < 2^41, and A <= 1000 D - B, the
+// one-SM case, is A + B <= 1000 D, which also covers A = 0.
+__device__ __forceinline__ void fast_task(long long T, long long D, long long A, long long B, long long u,
+                                          unsigned int y, unsigned int M, unsigned int g, unsigned int m_one,
+                                          unsigned int* mm, unsigned int* f, unsigned int* ulo, unsigned int* uhi) {
+  const unsigned long long uT = (unsigned long long)T, uD = (unsigned long long)D;
+  const unsigned long long uA = (unsigned long long)A, uB = (unsigned long long)B, uu = (unsigned long long)u;
+  const unsigned long long high = ((uT | uD) >> 31) | (uu >> 32) | ((uA | uB) >> 37);
+  const unsigned long long sAB = uA + uB;
+  const unsigned int D32 = (unsigned int)uD;
+  const bool valid = high == 0ull && D32 - 1u < (unsigned int)uT && sAB - 1ull < (1ull << 36) && y <= 1u;
+  const unsigned long long w = 1000ull * D32;
+  unsigned int m = m_one;
+  if (sAB > w) m = uB >= w ? 0u : lemma2_size_fast(uA, uB, uD, M, g);
+  *mm = valid ? m : 0u;
+  *f = valid ? (m == 0u ? 2u : 0u) : 1u;
+  *ulo = valid ? ((unsigned int)uu & 0xffffu) : 0u;
+  *uhi = valid ? ((unsigned int)uu >> 16) : 0u;
+}
+
+constexpr unsigned kBadShift = 20;  // pi sums carry Pi + (invalid or unsizable tasks << kBadShift)
+
+// Adds one task's values to the partial sums of its set (ks of the chunk's
+// K) and returns the chunk-relative index of that set's first task.
+template <int K>
+__device__ __forceinline__ int accumulate(int ks, unsigned int mm, unsigned int f, unsigned int ulo, unsigned int uhi,
+                                          const int (&orel)[K + 1], unsigned int (&pi)[K], unsigned int (&lo)[K],
+                                          unsigned int (&hi)[K]) {
+  const unsigned int v = mm + ((f != 0u ? 1u : 0u) << kBadShift);
+  int first = 0;
+#pragma unroll
+  for (int k = 0; k < K; k++) {
+    const bool mine = ks == k;
+    pi[k] += mine ? v : 0u;
+    lo[k] += mine ? ulo : 0u;
+    hi[k] += mine ? uhi : 0u;
+    first = mine ? orel[k] : first;
+  }
+  return first;
+}
+
+// Warp-wide totals of a chunk's K sets, gathered so that lane k holds set
+// k's; lanes k < ns then write their set's result when its singleton
+// partitions fit (Lemma 3: Pi <= M), or queue it for the merge kernel.
+template <int K>
+__device__ __forceinline__ void finish_chunk(const unsigned int (&pi)[K], const unsigned int (&lo)[K],
+                                             const unsigned int (&hi)[K], const int (&orel)[K + 1], long long base,
+                                             int ns, unsigned int M, int lane, const AllocOut& out,
+                                             const AllocQueue& q) {
+  unsigned int pk = 0u, lk = 0u, hk = 0u;
+  int nk = 0;
+#pragma unroll
+  for (int k = 0; k < K; k++) {
+    const unsigned int tp = __reduce_add_sync(kFull, pi[k]);
+    const unsigned int tl = __reduce_add_sync(kFull, lo[k]);
+    const unsigned int th = __reduce_add_sync(kFull, hi[k]);
+    if (lane == k) {
+      pk = tp;
+      lk = tl;
+      hk = th;
+      nk = orel[k + 1] - orel[k];
+    }
+  }
+  if (lane < ns) {
+    const long long s = base + lane;
+    const unsigned int Pi = pk & ((1u << kBadShift) - 1u);
+    if ((pk >> kBadShift) != 0u || Pi > M) {
+      const unsigned long long idx = atomicAdd(q.counters + 1, 1ull);
+      q.slow_sets[idx] = s;
+    } else {
+      out.verdict[s] = 1;
+      out.reason[s] = GPA_REASON_OK;
+      out.n_parts[s] = nk;
+      out.Pi[s] = (int)Pi;
+      out.W[s] = (long long)(1000ull * (((unsigned long long)hk << 16) + lk));
+      if (out.n_tests) out.n_tests[s] = 0;
+    }
+  }
+}
+
 template <int K, int U>
 __global__ void __launch_bounds__(256) alloc_fast(DevSets S, DevModel md, AllocOut out, AllocQueue q) {
   const int lane = threadIdx.x & 31;
   const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   const unsigned M = (unsigned)md.M, g = (unsigned)md.g;
-  // the offsets of the next chunk are loaded one iteration ahead
+  const unsigned m_one = g <= M ? g : 0u;
+  const long long ntasks = __ldg(S.set_off + S.nsets);
   long long offv_next = 0;
   {
     const long long b0 = warp0 * K;
@@ -57,14 +142,13 @@ __global__ void __launch_bounds__(256) alloc_fast(DevSets S, DevModel md, AllocO
     long long o[K + 1];
 #pragma unroll
     for (int k = 0; k <= K; k++) o[k] = __shfl_sync(kFull, offv, k <= ns ? k : ns);
-    bool bad = false;
+    bool bad = o[0] < 0 || o[K] > ntasks;
 #pragma unroll
     for (int k = 0; k < K; k++) {
       const long long n = o[k + 1] - o[k];
       bad = bad || n < 0 || n > S.n_max || n > kNmax;
     }
     if (bad) {
-      // a malformed size: the merge kernel validates these sets one by one
       if (lane < ns) {
         const unsigned long long idx = atomicAdd(q.counters + 1, 1ull);
         q.slow_sets[idx] = base + lane;
@@ -72,10 +156,21 @@ __global__ void __launch_bounds__(256) alloc_fast(DevSets S, DevModel md, AllocO
       continue;
     }
     const long long o0 = o[0];
-    const int nt = (int)(o[K] - o0);
-    unsigned int pi[K], lo[K], hi[K], fl[K];
+    int orel[K + 1];
 #pragma unroll
-    for (int k = 0; k < K; k++) pi[k] = lo[k] = hi[k] = fl[k] = 0u;
+    for (int k = 0; k <= K; k++) orel[k] = (int)(o[k] - o0);
+    const int nt = orel[K];
+    const long long* Tc = S.T + o0;
+    const long long* Dc = S.D + o0;
+    const long long* Ac = S.A + o0;
+    const long long* Bc = S.B + o0;
+    const long long* uc = S.u + o0;
+    const unsigned char* yc = S.type + o0;
+    unsigned char* pot = out.part_of_task + o0;
+    short* sop = out.size_of_part + o0;
+    unsigned int pi[K], lo[K], hi[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) pi[k] = lo[k] = hi[k] = 0u;
     for (int c0 = 0; c0 < nt; c0 += 32 * U) {
       long long Tt[U], Dt[U], At[U], Bt[U], ut[U];
       unsigned int yt[U];
@@ -83,79 +178,240 @@ __global__ void __launch_bounds__(256) alloc_fast(DevSets S, DevModel md, AllocO
       for (int uu = 0; uu < U; uu++) {
         const int i = c0 + uu * 32 + lane;
         if (i < nt) {
-          const long long t = o0 + i;
-          Tt[uu] = __ldg(S.T + t);
-          Dt[uu] = __ldg(S.D + t);
-          At[uu] = __ldg(S.A + t);
-          Bt[uu] = __ldg(S.B + t);
-          ut[uu] = __ldg(S.u + t);
-          yt[uu] = __ldg(S.type + t);
+          Tt[uu] = __ldg(Tc + i);
+          Dt[uu] = __ldg(Dc + i);
+          At[uu] = __ldg(Ac + i);
+          Bt[uu] = __ldg(Bc + i);
+          ut[uu] = __ldg(uc + i);
+          yt[uu] = __ldg(yc + i);
         }
       }
 #pragma unroll
       for (int uu = 0; uu < U; uu++) {
         const int i = c0 + uu * 32 + lane;
         if (i < nt) {
-          const long long t = o0 + i;
           int ks = 0;
 #pragma unroll
-          for (int k = 1; k < K; k++) ks += (t >= o[k]) ? 1 : 0;
-          unsigned int mm = 0u, f = 0u, ulo = 0u, uhi = 0u;
-          if (!task_valid(Tt[uu], Dt[uu], At[uu], Bt[uu], ut[uu], yt[uu])) {
-            f = 1u;
-          } else {
-            mm = lemma2_size_fast((unsigned long long)At[uu], (unsigned long long)Bt[uu],
-                                  (unsigned long long)Dt[uu], M, g);
-            f = mm == 0u ? 2u : 0u;
-            ulo = (unsigned int)ut[uu] & 0xffffu;
-            uhi = (unsigned int)((unsigned long long)ut[uu] >> 16);
-          }
-          long long ok_ = o0;
-#pragma unroll
-          for (int k = 0; k < K; k++) {
-            const bool mine = ks == k;
-            pi[k] += mine ? mm : 0u;
-            lo[k] += mine ? ulo : 0u;
-            hi[k] += mine ? uhi : 0u;
-            fl[k] |= mine ? f : 0u;
-            ok_ = mine ? o[k] : ok_;
-          }
-          out.part_of_task[t] = (unsigned char)(t - ok_);
-          out.size_of_part[t] = (short)mm;
+          for (int k = 1; k < K; k++) ks += i >= orel[k] ? 1 : 0;
+          unsigned int mm, f, ulo, uhi;
+          fast_task(Tt[uu], Dt[uu], At[uu], Bt[uu], ut[uu], yt[uu], M, g, m_one, &mm, &f, &ulo, &uhi);
+          const int first = accumulate<K>(ks, mm, f, ulo, uhi, orel, pi, lo, hi);
+          pot[i] = (unsigned char)(i - first);
+          sop[i] = (short)mm;
         }
       }
     }
+    finish_chunk<K>(pi, lo, hi, orel, base, ns, M, lane, out, q);
+  }
+}
+
+// ------------------------------------------------- staged fast kernel
+//
+// The same per-task and per-set work with the task columns brought into
+// shared memory by bulk copies (the TMA engine), so that the HBM reads of
+// later tiles overlap the arithmetic on the current one.  A tile is
+// `tile_sets` consecutive sets (tile_sets * n_max <= kStageCap); CTAs take
+// tiles grid-stride.  One producer warp per CTA loads a tile's set offsets,
+// checks them (sizes in [0, n_max], inside the task columns), writes them into
+// a free stage and issues six bulk copies: the five 8-byte columns from the
+// even task at or below the tile's first task, the type column from the
+// multiple of 16 at or below it.  A copy never reads past the last task: the
+// unaligned end of the columns (at most one task, 15 type bytes) is copied by
+// the producer's lanes with plain loads.  A tile with a malformed offset is
+// not copied; its sets go to the merge kernel, which validates each one.  The
+// other warps each take chunks of K sets of the tile as alloc_fast does.  The
+// stages cycle through `full` (data landed) and `empty` (every compute warp
+// done with it) barriers.
+
+constexpr int kStageCap = 1024;      // task slots per stage
+constexpr int kTileSetsMax = 64;     // sets per tile
+constexpr int kStagesMax = 5;
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // a pipeline wait gives up after 1 s
+
+struct alignas(16) FastStage {
+  long long col[5][kStageCap + 2];   // T, D, A, B, u_ppm from task e8 on
+  unsigned char ty[kStageCap + 16];  // type from task e1 on
+  long long off[kTileSetsMax + 2];   // the tile's set offsets
+  long long e8, e1;
+  int bad;
+  int pad[3];
+};
+constexpr size_t kStageHeader = 128;  // the barriers: full[kStagesMax], empty[kStagesMax]
+static_assert(2 * kStagesMax * sizeof(unsigned long long) <= kStageHeader, "barrier header too small");
+static_assert(sizeof(FastStage) % 16 == 0, "stages must keep 16-byte alignment");
+
+template <int K>
+__global__ void __launch_bounds__(288, 2) alloc_fast_staged(DevSets S, DevModel md, AllocOut out, AllocQueue q,
+                                                            int tile_sets, int nstages) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(smem_raw);
+  unsigned long long* empty = full + kStagesMax;
+  FastStage* stages = reinterpret_cast<FastStage*>(smem_raw + kStageHeader);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ncw = (int)(blockDim.x >> 5) - 1;  // compute warps; the last warp is the producer
+  const long long ntiles = (S.nsets + tile_sets - 1) / tile_sets;
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < nstages; st++) {
+      mbar_init(&full[st], 1u);
+      mbar_init(&empty[st], (unsigned)ncw);
+    }
+    mbar_init_fence();
+  }
+  __syncthreads();
+
+  if (warp == ncw) {
+    // ---------------------------------------------------------- producer
+    const long long ntasks = __ldg(S.set_off + S.nsets);
+    int it = 0;
+    bool ok = true;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, it++) {
+      const int st = it % nstages;
+      const long long s0 = tile * tile_sets;
+      const int nst = (int)min((long long)tile_sets, S.nsets - s0);
+      long long ov[3];
+      bool sizes_ok = true;
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-      const unsigned int pk = __reduce_add_sync(kFull, pi[k]);
-      const unsigned int lk = __reduce_add_sync(kFull, lo[k]);
-      const unsigned int hk = __reduce_add_sync(kFull, hi[k]);
-      const unsigned int fk = __reduce_or_sync(kFull, fl[k]);
-      if (lane == k && k < ns) {
-        const long long s = base + k;
-        if (fk != 0u || pk > M) {
+      for (int r = 0; r < 3; r++) {
+        const int j = r * 32 + lane;
+        ov[r] = j <= nst ? __ldg(S.set_off + s0 + j) : 0ll;
+        if (j < nst) {
+          const long long n = __ldg(S.set_off + s0 + j + 1) - ov[r];
+          sizes_ok = sizes_ok && n >= 0 && n <= S.n_max && n <= kNmax;
+        }
+      }
+      sizes_ok = __all_sync(kFull, sizes_ok);
+      const long long o_first = __shfl_sync(kFull, ov[0], 0);
+      const int last_r = nst >> 5;
+      const long long o_last = __shfl_sync(kFull, last_r == 0 ? ov[0] : (last_r == 1 ? ov[1] : ov[2]), nst & 31);
+      if (it >= nstages && !mbar_wait(&empty[st], (unsigned)((it / nstages) - 1) & 1u, kWaitLimitNs)) {
+        ok = false;
+        break;
+      }
+      FastStage& sg = stages[st];
+#pragma unroll
+      for (int r = 0; r < 3; r++) {
+        const int j = r * 32 + lane;
+        if (j <= nst) sg.off[j] = ov[r];
+      }
+      const bool bad = !sizes_ok || o_first < 0 || o_last < o_first || o_last > ntasks ||
+                       o_last - o_first > kStageCap;
+      const long long e8 = o_first & ~1ll, e1 = o_first & ~15ll;
+      unsigned b8 = 0u, b1 = 0u;
+      if (!bad) {
+        const long long want8 = ((o_last - e8 + 1) & ~1ll) * 8, have8 = ((ntasks - e8) & ~1ll) * 8;
+        const long long want1 = (o_last - e1 + 15) & ~15ll, have1 = (ntasks - e1) & ~15ll;
+        b8 = (unsigned)min(want8, have8);
+        b1 = (unsigned)min(want1, have1);
+        // the unaligned end of the columns, by plain loads
+        const long long t8 = e8 + b8 / 8;
+        if (lane == 0 && t8 < o_last) {
+          const int r = (int)(t8 - e8);
+          sg.col[0][r] = __ldg(S.T + t8);
+          sg.col[1][r] = __ldg(S.D + t8);
+          sg.col[2][r] = __ldg(S.A + t8);
+          sg.col[3][r] = __ldg(S.B + t8);
+          sg.col[4][r] = __ldg(S.u + t8);
+        }
+        const long long t1 = e1 + b1 + lane;
+        if (t1 < o_last) sg.ty[b1 + lane] = __ldg(S.type + t1);
+      }
+      if (lane == 0) {
+        sg.e8 = e8;
+        sg.e1 = e1;
+        sg.bad = bad ? 1 : 0;
+      }
+      __threadfence_block();
+      __syncwarp();
+      if (lane == 0) {
+        // order this warp's plain shared-memory writes before the copies
+        // that may later overwrite the same bytes
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(&full[st], 5u * b8 + b1);
+        if (b8) {
+          bulk_copy_g2s(sg.col[0], S.T + e8, b8, &full[st]);
+          bulk_copy_g2s(sg.col[1], S.D + e8, b8, &full[st]);
+          bulk_copy_g2s(sg.col[2], S.A + e8, b8, &full[st]);
+          bulk_copy_g2s(sg.col[3], S.B + e8, b8, &full[st]);
+          bulk_copy_g2s(sg.col[4], S.u + e8, b8, &full[st]);
+        }
+        if (b1) bulk_copy_g2s(sg.ty, S.type + e1, b1, &full[st]);
+      }
+    }
+    if (!ok) {
+      if (lane == 0) atomicOr(q.err, kErrWait);
+      // let the copies already issued land before the CTA can exit
+      const int issued = it < nstages ? it : nstages;
+      for (int k = 1; k <= issued; k++) {
+        const int j = it - k;
+        (void)mbar_wait(&full[j % nstages], (unsigned)(j / nstages) & 1u, kWaitLimitNs);
+      }
+    }
+    return;
+  }
+
+  // ------------------------------------------------------------- compute
+  const unsigned M = (unsigned)md.M, g = (unsigned)md.g;
+  const unsigned m_one = g <= M ? g : 0u;
+  int it = 0;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, it++) {
+    const int st = it % nstages;
+    if (!mbar_wait(&full[st], (unsigned)(it / nstages) & 1u, kWaitLimitNs)) {
+      if (lane == 0) atomicOr(q.err, kErrWait);
+      return;
+    }
+    const FastStage& sg = stages[st];
+    const long long s0 = tile * tile_sets;
+    const int nst = (int)min((long long)tile_sets, S.nsets - s0);
+    const int nchunks = (nst + K - 1) / K;
+    const bool tile_bad = sg.bad != 0;
+    const long long e8 = sg.e8, e1 = sg.e1;
+    for (int c = warp; c < nchunks; c += ncw) {
+      const long long base = s0 + (long long)c * K;
+      const int ns = min(K, nst - c * K);
+      if (tile_bad) {
+        if (lane < ns) {
           const unsigned long long idx = atomicAdd(q.counters + 1, 1ull);
-          q.slow_sets[idx] = s;
-        } else {
-          // Lemma 3 holds for the singleton partitions (numbered by their task)
-          out.verdict[s] = 1;
-          out.reason[s] = GPA_REASON_OK;
-          out.n_parts[s] = (int)(o[k + 1] - o[k]);
-          out.Pi[s] = (int)pk;
-          out.W[s] = (long long)(1000ull * (((unsigned long long)hk << 16) + lk));
-          if (out.n_tests) out.n_tests[s] = 0;
+          q.slow_sets[idx] = base + lane;
         }
+        continue;
       }
+      // the producer checked every size of the tile: the chunk is well formed
+      int orel[K + 1];
+      const long long o0 = sg.off[c * K];
+#pragma unroll
+      for (int k = 0; k <= K; k++) orel[k] = (int)(sg.off[c * K + (k <= ns ? k : ns)] - o0);
+      const int nt = orel[K];
+      const int r8 = (int)(o0 - e8), r1 = (int)(o0 - e1);
+      unsigned char* pot = out.part_of_task + o0;
+      short* sop = out.size_of_part + o0;
+      unsigned int pi[K], lo[K], hi[K];
+#pragma unroll
+      for (int k = 0; k < K; k++) pi[k] = lo[k] = hi[k] = 0u;
+      for (int i = lane; i < nt; i += 32) {
+        int ks = 0;
+#pragma unroll
+        for (int k = 1; k < K; k++) ks += i >= orel[k] ? 1 : 0;
+        unsigned int mm, f, ulo, uhi;
+        fast_task(sg.col[0][r8 + i], sg.col[1][r8 + i], sg.col[2][r8 + i], sg.col[3][r8 + i], sg.col[4][r8 + i],
+                  sg.ty[r1 + i], M, g, m_one, &mm, &f, &ulo, &uhi);
+        const int first = accumulate<K>(ks, mm, f, ulo, uhi, orel, pi, lo, hi);
+        pot[i] = (unsigned char)(i - first);
+        sop[i] = (short)mm;
+      }
+      finish_chunk<K>(pi, lo, hi, orel, base, ns, M, lane, out, q);
     }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);
   }
 }
 
 __global__ void __launch_bounds__(128) alloc_merge(DevSets S, DevModel md, gpa_params p, AllocOut out, AllocQueue q,
                                                    const MagicDiv* __restrict__ mdiv) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   MergeSmem& sm = reinterpret_cast<MergeSmem*>(smem_raw)[warp];
   const unsigned long long nslow = *(volatile unsigned long long*)(q.counters + 1);
+  const long long ntasks = S.set_off[S.nsets];
   for (;;) {
     unsigned long long i = 0;
     if (lane == 0) i = atomicAdd(q.counters + 2, 1ull);
@@ -164,8 +420,8 @@ __global__ void __launch_bounds__(128) alloc_merge(DevSets S, DevModel md, gpa_p
     const long long s = q.slow_sets[i];
     const long long o = S.set_off[s];
     const long long nl = S.set_off[s + 1] - o;
-    if (nl < 0 || nl > S.n_max || nl > kNmax) {
-      write_invalid(s, o, nl < 0 ? 0 : nl, out, q.err);
+    if (nl < 0 || nl > S.n_max || nl > kNmax || !slice_inside(o, nl, ntasks)) {
+      write_invalid(s, o, slice_inside(o, nl, ntasks) ? nl : 0, out, q.err);
       continue;
     }
     const int n = (int)nl;
@@ -187,9 +443,10 @@ struct OneGpuSmem {
 
 __global__ void __launch_bounds__(256) one_gpu(DevSets S, DevModel md, AllocOut out, unsigned int* err,
                                                const MagicDiv* __restrict__ mdiv, unsigned long long* ticket) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   OneGpuSmem& sm = reinterpret_cast<OneGpuSmem*>(smem_raw)[warp];
+  const long long ntasks = S.set_off[S.nsets];
   for (;;) {
     unsigned long long s = 0;
     if (lane == 0) s = atomicAdd(ticket, 1ull);
@@ -197,8 +454,8 @@ __global__ void __launch_bounds__(256) one_gpu(DevSets S, DevModel md, AllocOut 
     if ((long long)s >= S.nsets) break;
     const long long o = S.set_off[s];
     const long long n = S.set_off[s + 1] - o;
-    if (n < 0 || n > S.n_max || n > kNmax) {
-      write_invalid((long long)s, o, n < 0 ? 0 : n, out, err);
+    if (n < 0 || n > S.n_max || n > kNmax || !slice_inside(o, n, ntasks)) {
+      write_invalid((long long)s, o, slice_inside(o, n, ntasks) ? n : 0, out, err);
       continue;
     }
     if (!stage_set(sm.st, o, (int)n, S.T, S.D, S.A, S.B, S.u, S.type)) {
@@ -240,6 +497,7 @@ __global__ void __launch_bounds__(256) one_gpu(DevSets S, DevModel md, AllocOut 
 
 }  // namespace
 
+size_t staged_smem_bytes(int stages) { return kStageHeader + sizeof(FastStage) * (size_t)stages; }
 size_t slow_smem_bytes(int warps_per_block) { return sizeof(MergeSmem) * (size_t)warps_per_block; }
 size_t one_gpu_smem_bytes(int warps_per_block) { return sizeof(OneGpuSmem) * (size_t)warps_per_block; }
 
@@ -249,7 +507,7 @@ cudaError_t launch_allocate(const DevSets& s, const DevModel& md, const gpa_para
   cudaError_t e = cudaMemsetAsync(q.counters, 0, 4 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
   prof_mark(prof, st);
-  const int threads = fast.warps_per_block * 32;
+  const int threads = min(fast.warps_per_block, 8) * 32;  // the direct kernel takes up to 8 warps
   // grid: the requested CTAs, or (0) as many as fit on every SM at once
   auto grid = [&](const void* fn) {
     if (fast.blocks > 0) return fast.blocks;
@@ -259,13 +517,47 @@ cudaError_t launch_allocate(const DevSets& s, const DevModel& md, const gpa_para
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0);
     return (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
   };
-  if (fast.chunk >= 8) {
+  // the staged kernel copies 16-byte aligned ranges: every column must start
+  // on a 16-byte boundary
+  const unsigned long long align = (unsigned long long)(size_t)s.T | (unsigned long long)(size_t)s.D |
+                                   (unsigned long long)(size_t)s.A | (unsigned long long)(size_t)s.B |
+                                   (unsigned long long)(size_t)s.u | (unsigned long long)(size_t)s.type;
+  const int chunk = fast.chunk;
+  if (fast.stages >= 2 && fast.stages <= kStagesMax && (align & 15ull) == 0 && s.nsets > 0) {
+    const int nmax = s.n_max > 0 ? s.n_max : 1;
+    const int tile_sets = min(kTileSetsMax, kStageCap / nmax);
+    const long long ntiles = (s.nsets + tile_sets - 1) / tile_sets;
+    const int cw = min(fast.warps_per_block, 8);  // compute warps (the kernel takes at most 9 warps)
+    const int sthreads = (cw + 1) * 32;
+    const size_t smem = staged_smem_bytes(fast.stages);
+    auto sgrid = [&](const void* fn) -> int {
+      long long b = fast.blocks;
+      if (b <= 0) {
+        int per_sm = 0, dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, sthreads, smem);
+        b = (long long)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+      }
+      return (int)min(b, ntiles);
+    };
+    if (chunk >= 4) {
+      alloc_fast_staged<4><<<sgrid((const void*)alloc_fast_staged<4>), sthreads, smem, st>>>(s, md, out, q, tile_sets,
+                                                                                           fast.stages);
+    } else if (chunk >= 2) {
+      alloc_fast_staged<2><<<sgrid((const void*)alloc_fast_staged<2>), sthreads, smem, st>>>(s, md, out, q, tile_sets,
+                                                                                           fast.stages);
+    } else {
+      alloc_fast_staged<1><<<sgrid((const void*)alloc_fast_staged<1>), sthreads, smem, st>>>(s, md, out, q, tile_sets,
+                                                                                           fast.stages);
+    }
+  } else if (chunk >= 8) {
     alloc_fast<8, 2><<<grid((const void*)alloc_fast<8, 2>), threads, 0, st>>>(s, md, out, q);
-  } else if (fast.chunk >= 4) {
+  } else if (chunk >= 4) {
     alloc_fast<4, 3><<<grid((const void*)alloc_fast<4, 3>), threads, 0, st>>>(s, md, out, q);
-  } else if (fast.chunk == 3) {
+  } else if (chunk == 3) {
     alloc_fast<2, 3><<<grid((const void*)alloc_fast<2, 3>), threads, 0, st>>>(s, md, out, q);
-  } else if (fast.chunk >= 2) {
+  } else if (chunk >= 2) {
     alloc_fast<2, 2><<<grid((const void*)alloc_fast<2, 2>), threads, 0, st>>>(s, md, out, q);
   } else {
     alloc_fast<1, 1><<<grid((const void*)alloc_fast<1, 1>), threads, 0, st>>>(s, md, out, q);
@@ -310,6 +602,14 @@ cudaError_t alloc_kernels_init() {
   cudaError_t e = cudaFuncSetAttribute(alloc_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)slow_smem_bytes(4));
   if (e != cudaSuccess) return e;
+  const int staged = (int)staged_smem_bytes(kStagesMax);
+  if ((e = cudaFuncSetAttribute(alloc_fast_staged<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, staged)) !=
+          cudaSuccess ||
+      (e = cudaFuncSetAttribute(alloc_fast_staged<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, staged)) !=
+          cudaSuccess ||
+      (e = cudaFuncSetAttribute(alloc_fast_staged<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, staged)) !=
+          cudaSuccess)
+    return e;
   return cudaFuncSetAttribute(one_gpu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)one_gpu_smem_bytes(8));
 }
 

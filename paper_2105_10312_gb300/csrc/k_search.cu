@@ -151,7 +151,8 @@ __global__ void __launch_bounds__(kSThreads) search_sets(DevSets S, DevModel md,
     const long long o = S.set_off[s];
     const long long nl = S.set_off[s + 1] - o;
     // ---- stage (warp 0): validate, DM order, Lemma 2 sizes
-    const bool bad = nl < 0 || nl > kSN || (1ll << (nl < 0 ? 0 : nl)) > nsub_max;
+    const bool bad = nl < 0 || nl > kSN || (1ll << (nl < 0 ? 0 : nl)) > nsub_max || o < 0 ||
+                     o > S.set_off[S.nsets] - nl;
     const int n = bad ? 0 : (int)nl;
     const int L = n > kSuffix ? n - kSuffix : (n > 0 ? 1 : 0);  // job prefix length
     if (warp == 0) {

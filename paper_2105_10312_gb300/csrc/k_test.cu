@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(256) wcet_tables(DevSets S, DevModel md, long 
   for (long long s = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < S.nsets; s += warps) {
     const long long o = S.set_off[s];
     const long long n = S.set_off[s + 1] - o;
-    if (n < 0 || n > kNmax) {
+    if (n < 0 || n > kNmax || o < 0 || o > S.set_off[S.nsets] - n) {
       if (lane == 0) atomicOr(err, kErrRange);
       continue;
     }
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(256) test_candidates(DevSets S, DevModel md, C
     if (!bad) {
       o = S.set_off[s];
       long long nn = S.set_off[s + 1] - o;
-      bad = nn < 0 || nn > kNmax || nn > C.map_stride;
+      bad = nn < 0 || nn > kNmax || nn > C.map_stride || o < 0 || o > S.set_off[S.nsets] - nn;
       n = bad ? 0 : (int)nn;
     }
     const unsigned char* map = C.part_of_task + c * C.map_stride;

@@ -218,15 +218,17 @@ def test_allocate_launch_shapes_graph_and_per_set(ctx):
     stream = torch.cuda.Stream()  # graph capture needs a non-default stream
     c2 = gpa.Context(0, stream=stream)
     try:
-        for warps in (1, 2, 4, 8):
-            for chunk in (1, 3, 8):
-                c2.set_option("FAST_WARPS", warps)
-                c2.set_option("FAST_CHUNK", chunk)
-                c2.set_option("FAST_BLOCKS", 7)
-                out = c2.allocate(d, **md)
-                c2.sync()
-                _assert_equal(out, ref, ALLOC_KEYS, f"shape {warps}x{chunk}")
-        for k in ("FAST_WARPS", "FAST_CHUNK", "FAST_BLOCKS"):
+        for stages in (1, 2, 3, 5):
+            for warps in (1, 2, 4, 8):
+                for chunk in (1, 2, 3, 4, 8):
+                    c2.set_option("FAST_STAGES", stages)
+                    c2.set_option("FAST_WARPS", warps)
+                    c2.set_option("FAST_CHUNK", chunk)
+                    c2.set_option("FAST_BLOCKS", 7)
+                    out = c2.allocate(d, **md)
+                    c2.sync()
+                    _assert_equal(out, ref, ALLOC_KEYS, f"shape {stages}x{warps}x{chunk}")
+        for k in ("FAST_WARPS", "FAST_CHUNK", "FAST_BLOCKS", "FAST_STAGES"):
             c2.set_option(k, 0)
         c2.set_option("GRAPH", 1)
         for _ in range(3):
@@ -243,6 +245,54 @@ def test_allocate_launch_shapes_graph_and_per_set(ctx):
         out = c2.allocate(dp, M=68, g=1, k_c_pm=KC, k_m_pm=KM)
         c2.sync()
         _assert_equal(out, refp, ALLOC_KEYS, "per-set")
+    finally:
+        c2.close()
+
+
+def _shifted(dev, k, shift):
+    """A copy of column k that starts `shift` elements into a fresh buffer
+    (so that its base address loses the 16-byte alignment)."""
+    v = dev[k]
+    buf = torch.empty(v.numel() + shift, dtype=v.dtype, device=v.device)
+    buf[shift:].copy_(v)
+    return buf[shift:]
+
+
+@pytest.mark.parametrize("stages", [1, 3])
+def test_allocate_odd_task_count_and_unaligned_columns(ctx, stages):
+    """Bulk-copied stages: sets that start on odd task indices, an odd task
+    count (the last task and the type bytes past the last 16-byte boundary
+    are not bulk-copied) and columns whose base addresses are not 16-byte
+    aligned (the launcher then reads directly) all match the oracle."""
+    s = gpa.gen_tasksets(seed=41, nsets=1501, n_min=1, n_max=33, U_lo_ppm=200000, U_hi_ppm=4000000,
+                         deadline_pm=750, T_lo=1000, T_hi=100000)
+    if int(s["set_off"][-1]) % 2 == 0:  # make the task count odd: drop the last task
+        s = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in s.items()}
+        n_last = int(s["set_off"][-1] - s["set_off"][-2])
+        assert n_last > 1
+        s["set_off"][-1] -= 1
+        for k in ("T", "D", "A", "B", "u_ppm", "type"):
+            s[k] = s[k][:-1].copy()
+    assert int(s["set_off"][-1]) % 2 == 1
+    md = dict(M=80, g=1, k_c_pm=KC, k_m_pm=KM)
+    ref = oracle.allocate(s, md["M"], md["g"], KC, KM, nthreads=8)
+    d = gpa.to_device(s)
+    stream = torch.cuda.Stream()
+    c2 = gpa.Context(0, stream=stream)
+    try:
+        c2.set_option("FAST_STAGES", stages)
+        for chunk in (1, 2, 4, 8):
+            c2.set_option("FAST_CHUNK", chunk)
+            out = c2.allocate(d, **md)
+            c2.sync()
+            _assert_equal(out, ref, ALLOC_KEYS, f"odd count chunk {chunk}")
+        for k, shift in (("T", 1), ("u_ppm", 1), ("type", 1), ("type", 2)):
+            d2 = dict(d)
+            d2[k] = _shifted(d, k, shift)
+            torch.cuda.synchronize()
+            out = c2.allocate(d2, **md)
+            c2.sync()
+            _assert_equal(out, ref, ALLOC_KEYS, f"column {k} shifted by {shift}")
     finally:
         c2.close()
 
