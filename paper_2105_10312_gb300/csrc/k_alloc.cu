@@ -121,6 +121,7 @@ __device__ __forceinline__ void finish_chunk(const unsigned int (&pi)[K], const 
 
 template <int K, int U>
 __global__ void __launch_bounds__(256) alloc_fast(DevSets S, DevModel md, AllocOut out, AllocQueue q) {
+  asm volatile("griddepcontrol.launch_dependents;");  // the merge grid may be scheduled as CTAs drain
   const int lane = threadIdx.x & 31;
   const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -250,6 +251,7 @@ __global__ void __launch_bounds__(288, 2) alloc_fast_staged(DevSets S, DevModel 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ncw = (int)(blockDim.x >> 5) - 1;  // compute warps; the last warp is the producer
   const long long ntiles = (S.nsets + tile_sets - 1) / tile_sets;
+  asm volatile("griddepcontrol.launch_dependents;");
   if (threadIdx.x == 0) {
     for (int st = 0; st < nstages; st++) {
       mbar_init(&full[st], 1u);
@@ -410,6 +412,7 @@ __global__ void __launch_bounds__(128) alloc_merge(DevSets S, DevModel md, gpa_p
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   MergeSmem& sm = reinterpret_cast<MergeSmem*>(smem_raw)[warp];
+  asm volatile("griddepcontrol.wait;" ::: "memory");  // the fast grid has finished and its writes are visible
   const unsigned long long nslow = *(volatile unsigned long long*)(q.counters + 1);
   const long long ntasks = S.set_off[S.nsets];
   for (;;) {
@@ -565,9 +568,21 @@ cudaError_t launch_allocate(const DevSets& s, const DevModel& md, const gpa_para
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   prof_mark(prof, st);
-  const size_t smem = slow_smem_bytes(slow.warps_per_block);
-  alloc_merge<<<slow.blocks, slow.warps_per_block * 32, smem, st>>>(s, md, p, out, q,
-                                                                     reinterpret_cast<const MagicDiv*>(mdiv));
+  // programmatic dependent launch: the merge grid may be scheduled while the
+  // fast grid drains; it waits (griddepcontrol.wait) for the fast grid's
+  // completion and memory before it reads the queue
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)slow.blocks);
+  cfg.blockDim = dim3((unsigned)(slow.warps_per_block * 32));
+  cfg.dynamicSmemBytes = slow_smem_bytes(slow.warps_per_block);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, alloc_merge, s, md, p, out, q, reinterpret_cast<const MagicDiv*>(mdiv));
+  if (e != cudaSuccess) return e;
   e = cudaGetLastError();
   prof_mark(prof, st);
   *launches += 2;
