@@ -18,6 +18,7 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 POLICY = {"SMS": 0, "BF": 1, "ONE_GPU": 2}
+SCHED = {"DM": 0, "EDF": 1}
 REASON = {"OK": 0, "LEMMA1": 1, "LEMMA2": 2, "NO_MERGE": 3, "TEST": 4, "INVALID": 5}
 
 _lib = None
@@ -101,13 +102,21 @@ def rta(T, D, A, B, typ, in_mask, m, kc, km):
     return int(v), R
 
 
-def minm(T, D, A, B, typ, in_mask, lo, hi, g, kc, km, linear=True):
+def edf(T, D, A, B, typ, in_mask, m, kc, km):
+    """EDF processor-demand test of the tasks selected by in_mask at m SMs -> verdict."""
+    _fresh()
+    return int(lib().orc_edf(ctypes.c_int(len(T)), _p(_i64(T)), _p(_i64(D)), _p(_i64(A)), _p(_i64(B)),
+                             _p(_u8(typ)), _p(_u8(in_mask)), ctypes.c_int64(m), ctypes.c_int64(kc),
+                             ctypes.c_int64(km)))
+
+
+def minm(T, D, A, B, typ, in_mask, lo, hi, g, kc, km, linear=True, sched="DM"):
     _fresh()
     out = ctypes.c_int64()
     _check(lib().orc_minm(ctypes.c_int(len(T)), _p(_i64(T)), _p(_i64(D)), _p(_i64(A)), _p(_i64(B)), _p(_u8(typ)),
                           _p(_u8(in_mask)), ctypes.c_int64(lo), ctypes.c_int64(hi), ctypes.c_int64(g),
-                          ctypes.c_int64(kc), ctypes.c_int64(km), ctypes.c_int(1 if linear else 0),
-                          ctypes.byref(out)), "minm")
+                          ctypes.c_int64(kc), ctypes.c_int64(km), ctypes.c_int64(SCHED[sched]),
+                          ctypes.c_int(1 if linear else 0), ctypes.byref(out)), "minm")
     return out.value
 
 
@@ -125,7 +134,8 @@ def lemma1_rejects(T, A, B, M):
                                          ctypes.c_int64(M)))
 
 
-def test_schedulable(sets, M, g, kc, km, cand_set, part_of_task, map_stride, kparts, size_of_part, with_R=True):
+def test_schedulable(sets, M, g, kc, km, cand_set, part_of_task, map_stride, kparts, size_of_part, with_R=True,
+                     sched="DM"):
     _fresh()
     off = _i64(sets["set_off"])
     cand_set = _i64(cand_set)
@@ -137,12 +147,13 @@ def test_schedulable(sets, M, g, kc, km, cand_set, part_of_task, map_stride, kpa
     _check(lib().orc_test_schedulable(
         ctypes.c_int64(len(off) - 1), _p(off), _p(_i64(sets["T"])), _p(_i64(sets["D"])), _p(_i64(sets["A"])),
         _p(_i64(sets["B"])), _p(_u8(sets["type"])), ctypes.c_int64(M), ctypes.c_int64(g), ctypes.c_int64(kc),
-        ctypes.c_int64(km), ctypes.c_int64(nc), _p(cand_set), _p(pot), ctypes.c_int64(map_stride),
+        ctypes.c_int64(km), ctypes.c_int64(SCHED[sched]), ctypes.c_int64(nc), _p(cand_set), _p(pot),
+        ctypes.c_int64(map_stride),
         ctypes.c_int64(kparts), _p(sop), _p(verdict), _p(R)), "test_schedulable")
     return verdict, R
 
 
-def allocate(sets, M, g, kc, km, policy="SMS", act=False, linear=True, nthreads=1):
+def allocate(sets, M, g, kc, km, policy="SMS", act=False, linear=True, nthreads=1, sched="DM"):
     _fresh()
     off = _i64(sets["set_off"])
     nsets = len(off) - 1
@@ -156,14 +167,15 @@ def allocate(sets, M, g, kc, km, policy="SMS", act=False, linear=True, nthreads=
     _check(lib().orc_allocate(
         ctypes.c_int64(nsets), _p(off), _p(_i64(sets["T"])), _p(_i64(sets["D"])), _p(_i64(sets["A"])),
         _p(_i64(sets["B"])), _p(_i64(sets["u_ppm"])), _p(_u8(sets["type"])), ctypes.c_int64(M), ctypes.c_int64(g),
-        ctypes.c_int64(kc), ctypes.c_int64(km), ctypes.c_int(POLICY[policy]), ctypes.c_int(1 if act else 0),
+        ctypes.c_int64(kc), ctypes.c_int64(km), ctypes.c_int64(SCHED[sched]), ctypes.c_int(POLICY[policy]),
+        ctypes.c_int(1 if act else 0),
         ctypes.c_int(1 if linear else 0), _p(out["verdict"]), _p(out["reason"]), _p(out["n_parts"]), _p(out["Pi"]),
         _p(out["W"]), _p(out["n_tests"]), _p(out["part_of_task"]), _p(out["size_of_part"]),
         ctypes.c_int(nthreads)), "allocate")
     return out
 
 
-def search_best(sets, M, g, kc, km, kmin, kmax, explicit=False, nthreads=1):
+def search_best(sets, M, g, kc, km, kmin, kmax, explicit=False, nthreads=1, sched="DM"):
     _fresh()
     off = _i64(sets["set_off"])
     nsets = len(off) - 1
@@ -176,7 +188,8 @@ def search_best(sets, M, g, kc, km, kmin, kmax, explicit=False, nthreads=1):
     }
     args = [ctypes.c_int64(nsets), _p(off), _p(_i64(sets["T"])), _p(_i64(sets["D"])), _p(_i64(sets["A"])),
             _p(_i64(sets["B"])), _p(_i64(sets["u_ppm"])), _p(_u8(sets["type"])), ctypes.c_int64(M),
-            ctypes.c_int64(g), ctypes.c_int64(kc), ctypes.c_int64(km), ctypes.c_int(kmin), ctypes.c_int(kmax),
+            ctypes.c_int64(g), ctypes.c_int64(kc), ctypes.c_int64(km), ctypes.c_int64(SCHED[sched]),
+            ctypes.c_int(kmin), ctypes.c_int(kmax),
             _p(out["feasible"]), _p(out["W"]), _p(out["sum_minm"]), _p(out["n_blocks"]), _p(out["spare"]),
             _p(out["rgs"]), _p(out["minm_block"]), ctypes.c_int(nthreads)]
     if explicit:

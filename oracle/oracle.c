@@ -19,6 +19,8 @@
  *                   the partition)
  *   rta()           §5.5 per-partition test; policy = deadline-monotonic
  *                   fixed priority, classic response-time iteration
+ *   edf()           the second policy (EDF), processor-demand criterion
+ *                   over the first synchronous busy period
  *   minm_linear()   Alg. 2 (merge): first size in [lo, hi] that passes
  *   minm_binary()   the binary-search variant the text of §5.2 mentions
  *   lemma1()        Lemma 1 (necessary utilisation test)
@@ -58,8 +60,11 @@ typedef struct {
   const uint8_t* type;
 } oset;
 
+enum { S_DM = 0, S_EDF = 1 };
+
 typedef struct {
   int64_t M, g, kc, km;
+  int64_t sched; /* per-partition policy: S_DM (the reading of §5.5) or S_EDF */
 } omodel;
 
 static oset view(int64_t s, const int64_t* set_off, const int64_t* T, const int64_t* D, const int64_t* A,
@@ -145,11 +150,69 @@ static int rta(const oset* s, const omodel* md, const unsigned char* in, int64_t
   return all;
 }
 
+/* Second per-partition policy (the paper leaves the policy of §5.5 open):
+ * preemptive EDF on the partition as one processor, synchronous periodic
+ * release, constrained deadlines.  Written as the processor-demand criterion
+ * (Baruah, Rosier & Howell, 1990): every deadline is met iff U <= 1 and
+ *     dbf(t) = sum_{D_i <= t} (floor((t - D_i) / T_i) + 1) C_i  <=  t
+ * at every absolute deadline t up to the end L of the first synchronous busy
+ * period (George, Rivierre & Spuri, 1996), the least fixed point of
+ * w = sum_i ceil(w / T_i) C_i from w = sum_i C_i.
+ * Readings: one task passes iff C <= D; with two or more tasks U is bounded
+ * by U_hi = sum_i ceil(2^32 C_i / T_i) / 2^32 and the test passes only if
+ * U_hi < 1 (a set whose U lies within n 2^-32 of 1 is reported as missing a
+ * deadline: conservative, and it keeps L finite). */
+static int edf(const oset* s, const omodel* md, const unsigned char* in, int64_t m) {
+  int64_t C[ONMAX];
+  int idx[ONMAX], k = 0;
+  for (int i = 0; i < s->n; i++)
+    if (in[i]) {
+      C[i] = wcet(s->A[i], s->B[i], kfactor(s, md, in, i), m);
+      idx[k++] = i;
+    }
+  if (k == 0) return 1;
+  if (k == 1) return C[idx[0]] <= s->D[idx[0]];
+  i128 uhi = 0;
+  for (int a = 0; a < k; a++) {
+    int i = idx[a];
+    uhi += (((i128)C[i] << 32) + s->T[i] - 1) / s->T[i];
+  }
+  if (uhi >= ((i128)1 << 32)) return 0;
+  i128 L = 0;
+  for (int a = 0; a < k; a++) L += C[idx[a]];
+  for (;;) {
+    i128 next = 0;
+    for (int a = 0; a < k; a++) {
+      int i = idx[a];
+      next += ((L + s->T[i] - 1) / s->T[i]) * (i128)C[i];
+    }
+    if (next == L) break;
+    L = next;
+  }
+  for (int a = 0; a < k; a++) {
+    int i = idx[a];
+    for (i128 t = s->D[i]; t <= L; t += s->T[i]) {
+      i128 dbf = 0;
+      for (int b = 0; b < k; b++) {
+        int j = idx[b];
+        if (s->D[j] <= t) dbf += ((t - s->D[j]) / s->T[j] + 1) * (i128)C[j];
+      }
+      if (dbf > t) return 0;
+    }
+  }
+  return 1;
+}
+
+/* The per-partition test of the model's policy (verdict only). */
+static int test(const oset* s, const omodel* md, const unsigned char* in, int64_t m) {
+  return md->sched == S_EDF ? edf(s, md, in, m) : rta(s, md, in, m, NULL);
+}
+
 /* Alg. 2: the first size m in lo, lo+g, ..., hi at which the merged task set
  * passes the test; 0 when none does. */
 static int64_t minm_linear(const oset* s, const omodel* md, const unsigned char* in, int64_t lo, int64_t hi) {
   for (int64_t m = lo; m <= hi; m += md->g)
-    if (rta(s, md, in, m, NULL)) return m;
+    if (test(s, md, in, m)) return m;
   return 0;
 }
 
@@ -157,11 +220,11 @@ static int64_t minm_linear(const oset* s, const omodel* md, const unsigned char*
  * monotone in m under the no-timing-anomaly hypothesis of §4.1). */
 static int64_t minm_binary(const oset* s, const omodel* md, const unsigned char* in, int64_t lo, int64_t hi) {
   if (lo > hi) return 0;
-  if (!rta(s, md, in, hi, NULL)) return 0;
+  if (!test(s, md, in, hi)) return 0;
   int64_t a = lo / md->g, b = hi / md->g;
   while (a < b) {
     int64_t mid = a + (b - a) / 2;
-    if (rta(s, md, in, mid * md->g, NULL)) b = mid;
+    if (test(s, md, in, mid * md->g)) b = mid;
     else a = mid + 1;
   }
   return a * md->g;
@@ -426,7 +489,7 @@ static void one_gpu(const oset* s, const omodel* md, ores* r, uint8_t* part_of_t
   for (int i = 0; i < s->n; i++) { in[i] = 1; part_of_task[i] = 0; size_of_part[i] = 0; }
   r->n_tests = 1;
   if (s->n == 0) { r->verdict = 1; r->reason = R_OK; return; }
-  int ok = rta(s, md, in, md->M, NULL);
+  int ok = test(s, md, in, md->M);
   r->verdict = (uint8_t)ok;
   r->reason = ok ? R_OK : R_TEST;
   r->n_parts = 1;
@@ -568,7 +631,7 @@ static void explicit_candidates(explicit_walk* w) {
     for (int p = 0; p < k && feasible; p++) {
       int any = 0;
       for (int i = 0; i < n; i++) { in[i] = map[i] == p; any |= in[i]; }
-      if (any && !rta(s, w->md, in, w->parts[p] * w->md->g, NULL)) feasible = 0;
+      if (any && !test(s, w->md, in, w->parts[p] * w->md->g)) feasible = 0;
     }
     if (!feasible) continue;
     /* induced set partition, blocks relabelled by first occurrence */
@@ -632,6 +695,7 @@ static int64_t search_explicit(const oset* s, const omodel* md, int kmin, int km
 
 static int valid_model(const omodel* md) {
   if (md->g < 1 || md->M < 1 || md->M > 1024 || md->M % md->g != 0) return 0;
+  if (md->sched != S_DM && md->sched != S_EDF) return 0;
   if (md->kc < 1000 || md->kc > 16000 || md->km < 1000 || md->km > 16000) return 0;
   return 1;
 }
@@ -682,17 +746,27 @@ int orc_wcet_tables(int64_t nsets, const int64_t* set_off, const int64_t* A, con
 int orc_rta(int n, const int64_t* T, const int64_t* D, const int64_t* A, const int64_t* B, const uint8_t* type,
             const uint8_t* in_mask, int64_t m, int64_t kc, int64_t km, int64_t* R) {
   oset s = {n, T, D, A, B, NULL, type};
-  omodel md = {1024, 1, kc, km};
+  omodel md = {1024, 1, kc, km, S_DM};
   unsigned char in[ONMAX];
   for (int i = 0; i < n; i++) in[i] = in_mask[i] ? 1 : 0;
   return rta(&s, &md, in, m, R);
 }
 
-int orc_minm(int n, const int64_t* T, const int64_t* D, const int64_t* A, const int64_t* B, const uint8_t* type,
-             const uint8_t* in_mask, int64_t lo, int64_t hi, int64_t g, int64_t kc, int64_t km, int linear,
-             int64_t* out) {
+/* One partition under EDF at m SMs: the verdict (0/1). */
+int orc_edf(int n, const int64_t* T, const int64_t* D, const int64_t* A, const int64_t* B, const uint8_t* type,
+            const uint8_t* in_mask, int64_t m, int64_t kc, int64_t km) {
   oset s = {n, T, D, A, B, NULL, type};
-  omodel md = {hi, g, kc, km};
+  omodel md = {1024, 1, kc, km, S_EDF};
+  unsigned char in[ONMAX];
+  for (int i = 0; i < n; i++) in[i] = in_mask[i] ? 1 : 0;
+  return edf(&s, &md, in, m);
+}
+
+int orc_minm(int n, const int64_t* T, const int64_t* D, const int64_t* A, const int64_t* B, const uint8_t* type,
+             const uint8_t* in_mask, int64_t lo, int64_t hi, int64_t g, int64_t kc, int64_t km, int64_t sched,
+             int linear, int64_t* out) {
+  oset s = {n, T, D, A, B, NULL, type};
+  omodel md = {hi, g, kc, km, sched};
   unsigned char in[ONMAX];
   for (int i = 0; i < n; i++) in[i] = in_mask[i] ? 1 : 0;
   *out = minm(&s, &md, in, lo, hi, linear);
@@ -703,7 +777,7 @@ int orc_workload(int n, const int64_t* u, const uint8_t* type, const uint8_t* in
                  int64_t* out) {
   int64_t zeros[ONMAX] = {0};
   oset s = {n, zeros, zeros, zeros, zeros, u, type};
-  omodel md = {1024, 1, kc, km};
+  omodel md = {1024, 1, kc, km, S_DM};
   unsigned char in[ONMAX];
   for (int i = 0; i < n; i++) in[i] = in_mask[i] ? 1 : 0;
   *out = workload(&s, &md, in);
@@ -712,15 +786,16 @@ int orc_workload(int n, const int64_t* u, const uint8_t* type, const uint8_t* in
 
 int orc_lemma1_rejects(int n, const int64_t* T, const int64_t* A, const int64_t* B, int64_t M) {
   oset s = {n, T, T, A, B, NULL, NULL};
-  omodel md = {M, 1, 1000, 1000};
+  omodel md = {M, 1, 1000, 1000, S_DM};
   return lemma1_rejects(&s, &md);
 }
 
 int orc_test_schedulable(int64_t nsets, const int64_t* set_off, const int64_t* T, const int64_t* D, const int64_t* A,
                          const int64_t* B, const uint8_t* type, int64_t M, int64_t g, int64_t kc, int64_t km,
-                         int64_t ncands, const int64_t* cand_set, const uint8_t* part_of_task, int64_t map_stride,
-                         int64_t kparts, const int32_t* size_of_part, uint8_t* verdict, int64_t* R) {
-  omodel md = {M, g, kc, km};
+                         int64_t sched, int64_t ncands, const int64_t* cand_set, const uint8_t* part_of_task,
+                         int64_t map_stride, int64_t kparts, const int32_t* size_of_part, uint8_t* verdict,
+                         int64_t* R) {
+  omodel md = {M, g, kc, km, sched};
   if (!valid_model(&md) || kparts < 1 || kparts > 255) return O_ERR_RANGE;
   for (int64_t c = 0; c < ncands; c++) {
     int64_t si = cand_set[c];
@@ -745,7 +820,15 @@ int orc_test_schedulable(int64_t nsets, const int64_t* set_off, const int64_t* T
       for (int i = 0; i < s.n; i++) { in[i] = map[i] == p; any |= in[i]; }
       if (!any) continue;
       if (size[p] == 0) { ok = 0; continue; }
-      if (!rta(&s, &md, in, size[p], Rt)) ok = 0;
+      if (md.sched == S_EDF) {
+        /* EDF gives no response times: 0 for the tasks of a passing part */
+        int pass = edf(&s, &md, in, size[p]);
+        for (int i = 0; i < s.n; i++)
+          if (in[i]) Rt[i] = pass ? 0 : -1;
+        if (!pass) ok = 0;
+      } else if (!rta(&s, &md, in, size[p], Rt)) {
+        ok = 0;
+      }
     }
     verdict[c] = (uint8_t)ok;
     if (R)
@@ -807,10 +890,10 @@ static int run_threads(void* (*fn)(void*), void* jobs, size_t job_size, int nth)
 
 int orc_allocate(int64_t nsets, const int64_t* set_off, const int64_t* T, const int64_t* D, const int64_t* A,
                  const int64_t* B, const int64_t* u, const uint8_t* type, int64_t M, int64_t g, int64_t kc,
-                 int64_t km, int policy, int act, int linear, uint8_t* verdict, uint8_t* reason, int32_t* n_parts,
-                 int32_t* Pi, int64_t* W, int32_t* n_tests, uint8_t* part_of_task, int16_t* size_of_part,
-                 int nthreads) {
-  omodel md = {M, g, kc, km};
+                 int64_t km, int64_t sched, int policy, int act, int linear, uint8_t* verdict, uint8_t* reason,
+                 int32_t* n_parts, int32_t* Pi, int64_t* W, int32_t* n_tests, uint8_t* part_of_task,
+                 int16_t* size_of_part, int nthreads) {
+  omodel md = {M, g, kc, km, sched};
   if (!valid_model(&md)) return O_ERR_RANGE;
   if (policy < P_SMS || policy > P_ONE_GPU) return O_ERR_ARG;
   int nth = nthreads < 1 ? 1 : (nthreads > 256 ? 256 : nthreads);
@@ -886,10 +969,10 @@ static void* best_worker(void* arg) {
 
 static int search_batch(int explicit_form, int64_t nsets, const int64_t* set_off, const int64_t* T, const int64_t* D,
                         const int64_t* A, const int64_t* B, const int64_t* u, const uint8_t* type, int64_t M,
-                        int64_t g, int64_t kc, int64_t km, int kmin, int kmax, uint8_t* feasible, int64_t* W,
-                        int32_t* sum_minm, int32_t* n_blocks, int32_t* spare, uint8_t* rgs, int16_t* minm_block,
-                        int nthreads, int64_t* candidates) {
-  omodel md = {M, g, kc, km};
+                        int64_t g, int64_t kc, int64_t km, int64_t sched, int kmin, int kmax, uint8_t* feasible,
+                        int64_t* W, int32_t* sum_minm, int32_t* n_blocks, int32_t* spare, uint8_t* rgs,
+                        int16_t* minm_block, int nthreads, int64_t* candidates) {
+  omodel md = {M, g, kc, km, sched};
   if (!valid_model(&md)) return O_ERR_RANGE;
   if (kmin < 1 || kmax < kmin || kmax > 8) return O_ERR_RANGE;
   int nth = nthreads < 1 ? 1 : (nthreads > 256 ? 256 : nthreads);
@@ -927,19 +1010,19 @@ static int search_batch(int explicit_form, int64_t nsets, const int64_t* set_off
 
 int orc_search_best(int64_t nsets, const int64_t* set_off, const int64_t* T, const int64_t* D, const int64_t* A,
                     const int64_t* B, const int64_t* u, const uint8_t* type, int64_t M, int64_t g, int64_t kc,
-                    int64_t km, int kmin, int kmax, uint8_t* feasible, int64_t* W, int32_t* sum_minm,
+                    int64_t km, int64_t sched, int kmin, int kmax, uint8_t* feasible, int64_t* W, int32_t* sum_minm,
                     int32_t* n_blocks, int32_t* spare, uint8_t* rgs, int16_t* minm_block, int nthreads) {
-  return search_batch(0, nsets, set_off, T, D, A, B, u, type, M, g, kc, km, kmin, kmax, feasible, W, sum_minm,
-                      n_blocks, spare, rgs, minm_block, nthreads, NULL);
+  return search_batch(0, nsets, set_off, T, D, A, B, u, type, M, g, kc, km, sched, kmin, kmax, feasible, W,
+                      sum_minm, n_blocks, spare, rgs, minm_block, nthreads, NULL);
 }
 
 int orc_search_explicit(int64_t nsets, const int64_t* set_off, const int64_t* T, const int64_t* D, const int64_t* A,
                         const int64_t* B, const int64_t* u, const uint8_t* type, int64_t M, int64_t g, int64_t kc,
-                        int64_t km, int kmin, int kmax, uint8_t* feasible, int64_t* W, int32_t* sum_minm,
-                        int32_t* n_blocks, int32_t* spare, uint8_t* rgs, int16_t* minm_block, int nthreads,
-                        int64_t* candidates) {
-  return search_batch(1, nsets, set_off, T, D, A, B, u, type, M, g, kc, km, kmin, kmax, feasible, W, sum_minm,
-                      n_blocks, spare, rgs, minm_block, nthreads, candidates);
+                        int64_t km, int64_t sched, int kmin, int kmax, uint8_t* feasible, int64_t* W,
+                        int32_t* sum_minm, int32_t* n_blocks, int32_t* spare, uint8_t* rgs, int16_t* minm_block,
+                        int nthreads, int64_t* candidates) {
+  return search_batch(1, nsets, set_off, T, D, A, B, u, type, M, g, kc, km, sched, kmin, kmax, feasible, W,
+                      sum_minm, n_blocks, spare, rgs, minm_block, nthreads, candidates);
 }
 
 /* ------------------------------------------------------- serving operations
@@ -990,7 +1073,7 @@ int orc_serve_admit(int n, const int64_t* T, const int64_t* D, const int64_t* A,
                     uint8_t* verdict, uint8_t* reason, uint8_t* part_out, int16_t* size_out, int32_t* n_parts,
                     int32_t* Pi, int64_t* W) {
   oset s = {n, T, D, A, B, u, type};
-  omodel md = {M, g, kc, km};
+  omodel md = {M, g, kc, km, S_DM};
   if (!valid_model(&md) || !valid_set(&s)) return O_ERR_RANGE;
   ores r;
   int st = allocate_one(&s, &md, policy, act, 1, &r, part_out, size_out);
@@ -1008,7 +1091,7 @@ int orc_serve_add(int n, const int64_t* T, const int64_t* D, const int64_t* A, c
                   int64_t g, int64_t kc, int64_t km, int policy, int act, uint8_t* verdict, uint8_t* reason,
                   uint8_t* path, uint8_t* part_out, int16_t* size_out, int32_t* n_parts, int32_t* Pi, int64_t* W) {
   oset s = {n + 1, T, D, A, B, u, type};
-  omodel md = {M, g, kc, km};
+  omodel md = {M, g, kc, km, S_DM};
   if (n + 1 > ONMAX || !valid_model(&md) || !valid_set(&s)) return O_ERR_RANGE;
   const int nw = n;  /* index of the new task */
   int np = np_in;
@@ -1074,7 +1157,7 @@ int orc_serve_remove(int n, const int64_t* T, const int64_t* D, const int64_t* A
                      int np_in, int index, int64_t M, int64_t g, int64_t kc, int64_t km, int64_t* T_out,
                      int64_t* D_out, int64_t* A_out, int64_t* B_out, int64_t* u_out, uint8_t* type_out,
                      uint8_t* part_out, int16_t* size_out, int32_t* n_parts, int32_t* Pi, int64_t* W) {
-  omodel md = {M, g, kc, km};
+  omodel md = {M, g, kc, km, S_DM};
   if (index < 0 || index >= n || !valid_model(&md)) return O_ERR_RANGE;
   int k = 0;
   for (int i = 0; i < n; i++) {

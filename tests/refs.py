@@ -9,6 +9,8 @@ by a different route from the oracle's code:
 * ``simulate_fp``: a unit-step discrete-time simulation of a fixed-priority
   uniprocessor schedule with synchronous release (the partition of §5.5 run
   as one processor) -- response times by brute force, not by analysis.
+* ``simulate_edf``: the same simulation under earliest-deadline-first
+  dispatching -- deadline misses by brute force, not by a demand bound.
 * ``heuristic``: Alg. 1-3 restated over Python frozensets (different data
   structures and loop order from the oracle), using a supplied per-partition
   test.
@@ -65,6 +67,26 @@ def simulate_fp(tasks, horizon):
                     pending[i].pop(0)
                 break
     return first, worst
+
+
+def simulate_edf(tasks, horizon):
+    """tasks: list of (T, D, C).  Synchronous periodic release at t = 0, unit
+    time steps, preemptive EDF (ties: lower task index).  Returns True iff no
+    job misses its absolute deadline before ``horizon``."""
+    jobs = []  # [absolute deadline, task index, remaining]
+    for t in range(horizon):
+        for i, (T, D, C) in enumerate(tasks):
+            if t % T == 0:
+                jobs.append([t + D, i, C])
+        if jobs:
+            jobs.sort(key=lambda j: (j[0], j[1]))
+            jobs[0][2] -= 1
+            if jobs[0][2] == 0:
+                jobs.pop(0)
+        for j in jobs:
+            if j[0] <= t + 1 and j[2] > 0:
+                return False
+    return True
 
 
 def dm_order(T, D, idx):

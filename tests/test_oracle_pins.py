@@ -220,6 +220,122 @@ def test_rta_monotone_in_m_and_in_tasks():
                     assert oracle.rta(*args, sub, m, KC, KM)[0] == 1
 
 
+# ------------------------------------------ EDF, the second per-partition policy
+
+def _edf_band(C, T):
+    """The oracle's reading: with two or more tasks U is bounded by
+    sum ceil(2^32 C / T) / 2^32, and the test needs that bound below 1."""
+    return sum(-(-(int(c) << 32) // int(t)) for c, t in zip(C, T)) >= (1 << 32)
+
+
+def test_edf_matches_edf_simulation():
+    """Processor-demand verdicts equal a unit-step EDF schedule simulated
+    over two hyperperiods (synchronous release, constrained deadlines); in
+    the band around U = 1 the test reports a miss (the conservative reading)."""
+    rng = random.Random(41)
+    periods = [3, 4, 5, 6, 8, 10, 12, 15, 20]
+    ok = miss = band = 0
+    for trial in range(600):
+        n = rng.randrange(1, 6)
+        T = np.array([rng.choice(periods) for _ in range(n)], np.int64)
+        D = np.array([rng.randrange(max(1, t // 3), t + 1) for t in T], np.int64)
+        C = np.array([rng.randrange(1, max(2, (2 * t) // n)) for t in T], np.int64)
+        v = oracle.edf(T, D, 1000 * C, np.zeros(n, np.int64), np.zeros(n, np.uint8), np.ones(n, np.uint8), 1,
+                       1000, 1000)
+        H = 1
+        for t in T:
+            H = H * int(t) // math.gcd(H, int(t))
+        sim = refs.simulate_edf([(int(T[i]), int(D[i]), int(C[i])) for i in range(n)], 2 * H + int(D.max()) + 1)
+        if n >= 2 and _edf_band(C, T):
+            band += 1
+            assert v == 0, trial
+            continue
+        assert v == int(sim), (trial, list(T), list(D), list(C))
+        ok += v
+        miss += 1 - v
+    assert ok > 150 and miss > 150 and band > 5
+
+
+def test_edf_implicit_deadlines_utilisation_bound():
+    """Liu & Layland: with D = T, EDF meets every deadline iff U <= 1 (sets
+    in the band around U = 1 excepted, where the reading reports a miss)."""
+    from fractions import Fraction
+    rng = random.Random(42)
+    seen = [0, 0]
+    for trial in range(400):
+        n = rng.randrange(2, 9)
+        T = np.array([rng.randrange(10, 100000) for _ in range(n)], np.int64)
+        C = np.array([rng.randrange(1, int(t) * 8 // (5 * n) + 1) for t in T], np.int64)
+        U = sum(Fraction(int(c), int(t)) for c, t in zip(C, T))
+        v = oracle.edf(T, T.copy(), 1000 * C, np.zeros(n, np.int64), np.zeros(n, np.uint8), np.ones(n, np.uint8),
+                       1, 1000, 1000)
+        if U > 1 or _edf_band(C, T):
+            assert v == 0, (trial, U)
+        else:
+            assert v == 1, (trial, U)
+        seen[int(U <= 1)] += 1
+    assert min(seen) > 50
+
+
+def test_edf_dominates_dm_and_is_monotone():
+    """EDF is optimal on one processor: a DM-schedulable partition passes the
+    EDF test (outside the band); the EDF test is monotone in m and in the
+    task set, like the DM test (no timing anomalies)."""
+    s = gen_tasksets(seed=43, nsets=80, n_min=2, n_max=8, U_lo_ppm=300000, U_hi_ppm=4000000, deadline_pm=750,
+                     T_lo=1000, T_hi=100000)
+    off = s["set_off"]
+    dm_ok = strict = 0
+    for si in range(80):
+        o, e = off[si], off[si + 1]
+        args = [s[k][o:e] for k in ("T", "D", "A", "B", "type")]
+        n = e - o
+        allin = np.ones(n, np.uint8)
+        ed = [oracle.edf(*args, allin, m, KC, KM) for m in range(1, 30)]
+        dm = [oracle.rta(*args, allin, m, KC, KM)[0] for m in range(1, 30)]
+        assert all(ed[j] <= ed[j + 1] for j in range(len(ed) - 1))
+        for a, b in zip(dm, ed):
+            if a:
+                dm_ok += 1
+                assert b == 1
+            strict += b and not a
+        for m in (2, 8, 29):
+            if oracle.edf(*args, allin, m, KC, KM):
+                for drop in range(n):
+                    sub = allin.copy()
+                    sub[drop] = 0
+                    assert oracle.edf(*args, sub, m, KC, KM) == 1
+    assert dm_ok > 200 and strict > 0
+
+
+def test_edf_single_task_and_minm():
+    """One task passes iff C <= D (the same as Lemma 2); the EDF minimum size
+    of a singleton is the Lemma 2 size, and of a set never above the DM one."""
+    rng = random.Random(44)
+    for _ in range(300):
+        C1 = rng.randrange(1, 10**6)
+        alpha = rng.randrange(0, 1001)
+        T = rng.randrange(1, 2**31 - 1)
+        D = rng.randrange(1, T + 1)
+        m = rng.randrange(1, 200)
+        c = refs.wcet_alpha(C1, alpha, 1000, m)
+        v = oracle.edf(np.array([T]), np.array([D]), np.array([C1 * (1000 - alpha)]), np.array([C1 * alpha]),
+                       np.zeros(1, np.uint8), np.ones(1, np.uint8), m, KC, KM)
+        assert v == int(c <= D)
+    s = gen_tasksets(seed=45, nsets=40, n_min=1, n_max=6, U_lo_ppm=300000, U_hi_ppm=5000000, deadline_pm=750,
+                     T_lo=1000, T_hi=100000)
+    for si in range(40):
+        v, o, n = _set_view(s, si)
+        mask = np.ones(n, np.uint8)
+        me = oracle.minm(v["T"], v["D"], v["A"], v["B"], v["type"], mask, 1, 64, 1, KC, KM, sched="EDF")
+        md = oracle.minm(v["T"], v["D"], v["A"], v["B"], v["type"], mask, 1, 64, 1, KC, KM)
+        assert me == oracle.minm(v["T"], v["D"], v["A"], v["B"], v["type"], mask, 1, 64, 1, KC, KM, linear=False,
+                                 sched="EDF")
+        if md:
+            assert 1 <= me <= md
+        if n == 1:
+            assert me == md
+
+
 # ------------------------------------------------------------------- Lemmas
 
 def test_lemma2_singleton_size_closed_form():
@@ -298,14 +414,16 @@ def _partitions_from(r, si, o, n):
     return parts, sizes
 
 
-@pytest.mark.parametrize("policy,act", [("SMS", False), ("SMS", True), ("BF", False), ("BF", True)])
-def test_heuristic_matches_independent_restatement(policy, act):
+@pytest.mark.parametrize("policy,act,sched", [("SMS", False, "DM"), ("SMS", True, "DM"), ("BF", False, "DM"),
+                                              ("BF", True, "DM"), ("SMS", False, "EDF"), ("BF", True, "EDF")])
+def test_heuristic_matches_independent_restatement(policy, act, sched):
     """Alg. 1-3 restated over Python sets reaches the same final partitions,
-    the same verdict and the same number of merge evaluations."""
+    the same verdict and the same number of merge evaluations (under either
+    per-partition policy)."""
     M, g = 12, 1
     s = gen_tasksets(seed=12, nsets=50, n_min=3, n_max=9, U_lo_ppm=1000000, U_hi_ppm=12000000, deadline_pm=750,
                      T_lo=50, T_hi=4000, T_dist="LIST", mode="PAPER")
-    r = oracle.allocate(s, M, g, KC, KM, policy=policy, act=act)
+    r = oracle.allocate(s, M, g, KC, KM, policy=policy, act=act, sched=sched)
     seen_merges = 0
     for si in range(50):
         v, o, n = _set_view(s, si)
@@ -315,11 +433,11 @@ def test_heuristic_matches_independent_restatement(policy, act):
 
         def single(i):
             return oracle.minm(v["T"], v["D"], v["A"], v["B"], v["type"], np.eye(n, dtype=np.uint8)[i], g, M, g,
-                               KC, KM)
+                               KC, KM, sched=sched)
 
         def test_min(S, lo, hi):
             mask = np.array([i in S for i in range(n)], np.uint8)
-            return oracle.minm(v["T"], v["D"], v["A"], v["B"], v["type"], mask, lo, hi, g, KC, KM)
+            return oracle.minm(v["T"], v["D"], v["A"], v["B"], v["type"], mask, lo, hi, g, KC, KM, sched=sched)
 
         def W(S):
             return sum(refs.conflict_k(v["type"], S, i, KC, KM) * int(v["u_ppm"][i]) for i in S)
@@ -385,7 +503,8 @@ def test_one_gpu_is_the_whole_set_at_M():
 
 # ------------------------------------------------------- exhaustive optimum
 
-def test_exhaustive_explicit_equals_subset_form_and_bruteforce():
+@pytest.mark.parametrize("sched", ["DM", "EDF"])
+def test_exhaustive_explicit_equals_subset_form_and_bruteforce(sched):
     rng = random.Random(14)
     for trial in range(25):
         n = rng.randrange(1, 6)
@@ -395,14 +514,16 @@ def test_exhaustive_explicit_equals_subset_form_and_bruteforce():
         kmax = rng.randrange(kmin, 4)
         s = gen_tasksets(seed=100 + trial, nsets=1, n_min=n, n_max=n, U_lo_ppm=300000, U_hi_ppm=2500000,
                          deadline_pm=750, T_lo=1000, T_hi=100000)
-        a = oracle.search_best(s, M, g, KC, KM, kmin, kmax, explicit=False)
-        b = oracle.search_best(s, M, g, KC, KM, kmin, kmax, explicit=True)
+        a = oracle.search_best(s, M, g, KC, KM, kmin, kmax, explicit=False, sched=sched)
+        b = oracle.search_best(s, M, g, KC, KM, kmin, kmax, explicit=True, sched=sched)
         for k in ("feasible", "W", "sum_minm", "n_blocks", "spare", "rgs", "minm_block"):
             assert np.array_equal(a[k], b[k]), (trial, k)
         v, o, _ = _set_view(s, 0)
 
         def passes(S, m):
             mask = np.array([i in S for i in range(n)], np.uint8)
+            if sched == "EDF":
+                return oracle.edf(v["T"], v["D"], v["A"], v["B"], v["type"], mask, m, KC, KM) == 1
             return oracle.rta(v["T"], v["D"], v["A"], v["B"], v["type"], mask, m, KC, KM)[0] == 1
 
         def minsize(S):
