@@ -52,6 +52,14 @@
  *      R_i = C_i + sum_{j in hp(i)} ceil(R_i / T_j) * C_j
  * started from R_i^0 = C_i + sum_{hp(i)} C_j.  A task meets its deadline iff
  * that fixed point is <= D_i; otherwise its reported R is -1.
+ * Second policy (GPA_SCHED_EDF, model->sched; not from the paper): preemptive
+ * EDF on the partition, synchronous periodic release.  Exact processor-demand
+ * test: dbf(t) = sum_{D_i <= t} (floor((t - D_i) / T_i) + 1) C_i <= t at every
+ * absolute deadline up to the first synchronous busy period (evaluated with
+ * QPA, Zhang & Burns 2009).  One task passes iff C <= D; with two or more
+ * tasks the test requires sum_i ceil(2^32 C_i / T_i) < 2^32, so a set whose
+ * utilisation lies within n 2^-32 of 1 is reported as failing (conservative).
+ * EDF gives no response times: R is 0 for the tasks of a passing part.
  *
  * Validation bounds (GPA_ERR_RANGE): 0 <= n <= 128 tasks per set,
  * 1 <= D <= T <= 2^31 - 1, A >= 0, B >= 0, 1 <= A + B <= 2^36,
@@ -68,7 +76,7 @@
 extern "C" {
 #endif
 
-#define GPA_ABI_VERSION 1
+#define GPA_ABI_VERSION 2
 #define GPA_NMAX 128          /* tasks per set */
 #define GPA_MMAX 1024         /* SMs on the modelled GPU */
 #define GPA_SEARCH_NMAX 14    /* tasks per set in gpa_search_best */
@@ -105,6 +113,12 @@ enum {
   GPA_POLICY_SMS = 0,       /* order >> of Def. 3: smallest merged size first */
   GPA_POLICY_BF = 1,        /* order > of Def. 4: smallest merged workload first */
   GPA_POLICY_ONE_GPU = 2    /* 1G baseline: all tasks in one partition of M SMs */
+};
+
+/* Per-partition scheduling policies (gpa_model.sched). */
+enum {
+  GPA_SCHED_DM = 0,   /* deadline-monotonic fixed priority, response-time analysis (§5.5 reading) */
+  GPA_SCHED_EDF = 1   /* preemptive EDF, processor-demand test */
 };
 
 /* ---------------------------------------------------------------- context */
@@ -174,6 +188,8 @@ typedef struct {
   int32_t g;       /* partition granularity in SMs (1 = SM, 2 = TPC); sizes are multiples of g */
   int32_t k_c_pm;  /* conflict factor of compute-intensive tasks, per mille (§7.1: 1200) */
   int32_t k_m_pm;  /* conflict factor of memory-intensive tasks, per mille (§7.1: 2300) */
+  int32_t sched;   /* per-partition policy: GPA_SCHED_DM or GPA_SCHED_EDF (not in serving: DM only) */
+  int32_t reserved_;  /* 0 */
 } gpa_model;
 
 /* Host-side validation of a task batch and model against the bounds above
@@ -267,7 +283,8 @@ typedef struct {
 /* a4 over a flat batch: candidate c is schedulable iff sum of its part sizes
  * <= M and every non-empty part meets the per-partition test at its size (a
  * non-empty part of size 0 fails).  verdict[c] in {0,1}; R (nullable) gets
- * each task's response time at R[c * map_stride + t], -1 for a miss.
+ * each task's response time at R[c * map_stride + t], -1 for a miss (under
+ * EDF: 0 for the tasks of a passing part, -1 otherwise).
  * Arrays live in cands->mem (which must equal sets->mem). */
 int32_t gpa_test_schedulable(gpa_ctx* ctx, const gpa_tasksets* sets, const gpa_model* model,
                              const gpa_candidates* cands, uint8_t* verdict, int64_t* R);

@@ -26,6 +26,7 @@ LIB_PATH = os.path.join(_HERE, "libgpa.so")
 OK, ERR_ARG, ERR_RANGE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_NOTFOUND = 0, -1, -2, -3, -4, -5, -6, -7
 HOST, DEVICE = 0, 1
 POLICY = {"SMS": 0, "BF": 1, "ONE_GPU": 2}
+SCHED = {"DM": 0, "EDF": 1}
 REASON = {"OK": 0, "LEMMA1": 1, "LEMMA2": 2, "NO_MERGE": 3, "TEST": 4, "INVALID": 5}
 OPT = {"AUTOTUNE": 1, "GRAPH": 2, "FAST_WARPS": 3, "FAST_CHUNK": 4, "FAST_BLOCKS": 5, "PER_SET_LAUNCH": 6,
        "PROFILE": 7, "FAST_STAGES": 8}
@@ -53,7 +54,8 @@ class Tasksets(ctypes.Structure):
 
 
 class Model(ctypes.Structure):
-    _fields_ = [("M", ctypes.c_int32), ("g", ctypes.c_int32), ("k_c_pm", ctypes.c_int32), ("k_m_pm", ctypes.c_int32)]
+    _fields_ = [("M", ctypes.c_int32), ("g", ctypes.c_int32), ("k_c_pm", ctypes.c_int32), ("k_m_pm", ctypes.c_int32),
+                ("sched", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
 
 
 class Candidates(ctypes.Structure):
@@ -263,9 +265,9 @@ class Context:
         return Cn, Cc
 
     def test_schedulable(self, sets, M, cand_set, part_of_task, size_of_part, map_stride, kparts, g=1,
-                         k_c_pm=1200, k_m_pm=2300, with_R=True):
+                         k_c_pm=1200, k_m_pm=2300, with_R=True, sched="DM"):
         ts, mem = make_tasksets(sets)
-        md = Model(M, g, k_c_pm, k_m_pm)
+        md = Model(M, g, k_c_pm, k_m_pm, SCHED[sched], 0)
         nc = _len(cand_set)
         cands = Candidates(nc, mem, int(map_stride), int(kparts), 0, _ptr(cand_set), _ptr(part_of_task),
                            _ptr(size_of_part))
@@ -292,9 +294,10 @@ class Context:
             "size_of_part": _empty_like_mem(mem, ntasks, np.int16, dev),
         }
 
-    def allocate(self, sets, M, g=1, k_c_pm=1200, k_m_pm=2300, policy="SMS", act=False, linear=True, out=None):
+    def allocate(self, sets, M, g=1, k_c_pm=1200, k_m_pm=2300, policy="SMS", act=False, linear=True, out=None,
+                 sched="DM"):
         ts, mem = make_tasksets(sets)
-        md = Model(M, g, k_c_pm, k_m_pm)
+        md = Model(M, g, k_c_pm, k_m_pm, SCHED[sched], 0)
         pr = Params(POLICY[policy], 1 if act else 0, 1 if linear else 0, 0)
         if out is None:
             out = self.alloc_result(sets)
@@ -319,9 +322,9 @@ class Context:
             "minm_block": _empty_like_mem(mem, nsets * kmax, np.int16, dev),
         }
 
-    def search_best(self, sets, M, g=1, k_c_pm=1200, k_m_pm=2300, kmin=1, kmax=4, out=None):
+    def search_best(self, sets, M, g=1, k_c_pm=1200, k_m_pm=2300, kmin=1, kmax=4, out=None, sched="DM"):
         ts, mem = make_tasksets(sets)
-        md = Model(M, g, k_c_pm, k_m_pm)
+        md = Model(M, g, k_c_pm, k_m_pm, SCHED[sched], 0)
         if out is None:
             out = self.best_result(sets, kmax)
         res = BestResult(mem, 0, _ptr(out["feasible"]), _ptr(out["W"]), _ptr(out["sum_minm"]),

@@ -138,22 +138,63 @@ __device__ bool lane_rta(const SetSmem& st, const unsigned int* S, unsigned int 
   return true;
 }
 
+// The EDF test of S (at most kLaneMax tasks) by one lane.
+__device__ bool lane_edf(const SetSmem& st, const unsigned int* S, unsigned int m, unsigned int kc, unsigned int km,
+                         const MagicDiv& md, LaneScratch& ls, int lane, unsigned int* err) {
+  int nm = 0, ns = 0;
+#pragma unroll
+  for (int w = 0; w < kWords; w++) {
+    nm += __popc(S[w] & st.memmask[w]);
+    ns += __popc(S[w]);
+  }
+  const unsigned int kmem = nm >= 2 ? km : 1000u, kcmp = (ns - nm) >= 2 ? kc : 1000u;
+  int pos = 0;
+  for (int w = 0; w < kWords; w++) {
+    for (unsigned int bits = S[w]; bits; bits &= bits - 1u) {
+      const int row = w * 32 + __ffs(bits) - 1;
+      const bool mem = (st.memmask[w] >> (row & 31)) & 1u;
+      ls.C[pos][lane] = wcet(st.A[row], st.B[row], mem ? kmem : kcmp, m, md);
+      ls.row[pos][lane] = (unsigned char)row;
+      pos++;
+    }
+  }
+  unsigned int eb = 0u;
+  const bool ok = serial_edf(
+      pos,
+      [&](int a, unsigned int& C, unsigned int& T, unsigned int& D) {
+        const int r = ls.row[a][lane];
+        C = ls.C[a][lane];
+        T = st.T[r];
+        D = st.D[r];
+      },
+      &eb);
+  if (eb) atomicOr(err, eb);
+  return ok;
+}
+
+__device__ __forceinline__ bool lane_test(const SetSmem& st, const unsigned int* S, unsigned int m, unsigned int kc,
+                                          unsigned int km, int sched, const MagicDiv& md, LaneScratch& ls, int lane,
+                                          unsigned int* err) {
+  return sched == GPA_SCHED_EDF ? lane_edf(st, S, m, kc, km, md, ls, lane, err)
+                                : lane_rta(st, S, m, kc, km, md, ls, lane, err);
+}
+
 // Alg. 2 by one lane: the first size in lo, lo + g, ..., hi that passes.  A
 // range of up to three sizes is scanned; a longer one is bisected (§5.2),
 // which finds the same size because the test is monotone in m.
 __device__ unsigned int lane_minm(const SetSmem& st, const unsigned int* S, unsigned int lo, unsigned int hi,
-                                  unsigned int g, unsigned int kc, unsigned int km, const MagicDiv* __restrict__ mdiv,
-                                  LaneScratch& ls, int lane, unsigned int* err) {
+                                  unsigned int g, unsigned int kc, unsigned int km, int sched,
+                                  const MagicDiv* __restrict__ mdiv, LaneScratch& ls, int lane, unsigned int* err) {
   if (lo > hi) return 0u;
   if (hi - lo <= 2u * g) {
     for (unsigned int m = lo; m <= hi; m += g)
-      if (lane_rta(st, S, m, kc, km, mdiv[m], ls, lane, err)) return m;
+      if (lane_test(st, S, m, kc, km, sched, mdiv[m], ls, lane, err)) return m;
     return 0u;
   }
   unsigned int a = lo / g, b = hi / g + 1u;  // b stands for "no size passes"
   while (a < b) {
     const unsigned int mid = a + (b - a) / 2u;
-    if (lane_rta(st, S, mid * g, kc, km, mdiv[mid * g], ls, lane, err)) b = mid;
+    if (lane_test(st, S, mid * g, kc, km, sched, mdiv[mid * g], ls, lane, err)) b = mid;
     else a = mid + 1u;
   }
   return a * g <= hi ? a * g : 0u;
@@ -163,7 +204,7 @@ __device__ unsigned int lane_minm(const SetSmem& st, const unsigned int* S, unsi
 // one lane per candidate when the merged set is small, then the warp for
 // the others.  Warp-uniform arguments.
 __device__ void size_candidates(MergeSmem& sm, int p1, int c0, int c1, unsigned int g, bool linear, unsigned int kc,
-                                unsigned int km, const MagicDiv* __restrict__ mdiv, unsigned int* err) {
+                                unsigned int km, int sched, const MagicDiv* __restrict__ mdiv, unsigned int* err) {
   const int lane = threadIdx.x & 31;
   for (int b = c0; b < c1; b += 32) {
     const int k = b + lane;
@@ -177,7 +218,7 @@ __device__ void size_candidates(MergeSmem& sm, int p1, int c0, int c1, unsigned 
         cnt += __popc(U[w]);
       }
       const unsigned int lo = max(sm.m[p1], sm.m[e]), hi = sm.m[p1] + sm.m[e] - g;
-      sm.ls.res[k] = cnt <= kLaneMax ? (unsigned short)lane_minm(sm.st, U, lo, hi, g, kc, km, mdiv, sm.ls, lane, err)
+      sm.ls.res[k] = cnt <= kLaneMax ? (unsigned short)lane_minm(sm.st, U, lo, hi, g, kc, km, sched, mdiv, sm.ls, lane, err)
                                      : kLaneNone;
     }
   }
@@ -189,7 +230,7 @@ __device__ void size_candidates(MergeSmem& sm, int p1, int c0, int c1, unsigned 
 #pragma unroll
     for (int w = 0; w < kWords; w++) U[w] = sm.mask[p1][w] | sm.mask[e][w];
     const unsigned int lo = max(sm.m[p1], sm.m[e]), hi = sm.m[p1] + sm.m[e] - g;
-    const unsigned int m3 = warp_minm(sm.st, U, lo, hi, g, linear, kc, km, mdiv, sm.sc, err);
+    const unsigned int m3 = warp_minm(sm.st, U, lo, hi, g, linear, kc, km, sched, mdiv, sm.sc, err);
     __syncwarp();
     if (lane == 0) sm.ls.res[k] = (unsigned short)m3;
     __syncwarp();
@@ -268,6 +309,7 @@ __device__ void merge_set(MergeSmem& sm, long long s, long long o, int n, const 
                           const AllocOut& out, const MagicDiv* mdiv, unsigned int* err) {
   const int lane = threadIdx.x & 31;
   const unsigned kc = (unsigned)md.kc, km = (unsigned)md.km, g = (unsigned)md.g, M = (unsigned)md.M;
+  const int sched = md.sched;
   const bool linear = p.linear_merge != 0;
 
   // Lemma 1: sum_i floor(10^6 C^n_i(1) / T_i) > 10^6 M rejects the set.
@@ -332,7 +374,7 @@ __device__ void merge_set(MergeSmem& sm, long long s, long long o, int n, const 
           S2[a >> 5] |= 1u << (a & 31);
           S2[b >> 5] |= 1u << (b & 31);
           const unsigned int lo = max(sm.m[a], sm.m[b]), hi = sm.m[a] + sm.m[b] - g;
-          if (lane_minm(sm.st, S2, lo, hi, g, kc, km, mdiv, sm.ls, lane, err) == 0u) {
+          if (lane_minm(sm.st, S2, lo, hi, g, kc, km, sched, mdiv, sm.ls, lane, err) == 0u) {
             atomicOr(&sm.act[a][b >> 5], 1u << (b & 31));
             atomicOr(&sm.act[b][a >> 5], 1u << (a & 31));
           }
@@ -378,7 +420,7 @@ __device__ void merge_set(MergeSmem& sm, long long s, long long o, int n, const 
         ne++;
       }
       __syncwarp();
-      size_candidates(sm, p1, 0, ne, g, linear, kc, km, mdiv, err);
+      size_candidates(sm, p1, 0, ne, g, linear, kc, km, sched, mdiv, err);
       tests += ne;
       // smallest size, then earliest position: key = size << 8 | position
       unsigned int keyv = 0xFFFFFFFFu;
@@ -436,7 +478,7 @@ __device__ void merge_set(MergeSmem& sm, long long s, long long o, int n, const 
       // success (in order) is applied, every earlier failure is forbidden
       for (int c0 = 0; c0 < ne; c0 += 32) {
         const int c1 = min(ne, c0 + 32);
-        size_candidates(sm, p1, c0, c1, g, linear, kc, km, mdiv, err);
+        size_candidates(sm, p1, c0, c1, g, linear, kc, km, sched, mdiv, err);
         const int k = c0 + lane;
         const unsigned int okb = __ballot_sync(kFull, k < c1 && sm.ls.res[k] != 0u);
         const int first = okb ? c0 + __ffs(okb) - 1 : c1;

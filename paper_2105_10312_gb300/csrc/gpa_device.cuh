@@ -253,11 +253,12 @@ __device__ __forceinline__ unsigned long long workload_from_sums(unsigned long l
 // With early_exit the test stops at the first deadline miss (verdict only).
 // Returns the verdict on every lane.  *err |= kErrIter if the iteration cap
 // was reached (the verdict is then 0).
-static __device__ __noinline__ bool warp_rta(const SetSmem& st, const unsigned int* S, unsigned int m, unsigned int kc,
-                                      unsigned int km, const MagicDiv* __restrict__ mdiv, RtaScratch& sc,
-                                      long long* R_row, bool early_exit, unsigned int* err) {
+// Compacts S's rows (priority order) into sc with their WCETs at m SMs
+// (conflict factors of §4.2); returns the number of tasks (every lane).
+__device__ __forceinline__ int compact_partition(const SetSmem& st, const unsigned int* S, unsigned int m,
+                                                 unsigned int kc, unsigned int km, const MagicDiv& md,
+                                                 RtaScratch& sc) {
   const int lane = threadIdx.x & 31;
-  const MagicDiv md = mdiv[m];
   int nm = 0, ns = 0;
 #pragma unroll
   for (int w = 0; w < kWords; w++) {
@@ -266,7 +267,6 @@ static __device__ __noinline__ bool warp_rta(const SetSmem& st, const unsigned i
   }
   const unsigned int kmem = nm >= 2 ? km : 1000u;
   const unsigned int kcmp = (ns - nm) >= 2 ? kc : 1000u;
-  // compaction of S's rows in priority order
   int base = 0;
   for (int w = 0; w < kWords && w * 32 < st.n; w++) {
     unsigned int word = S[w];
@@ -286,7 +286,14 @@ static __device__ __noinline__ bool warp_rta(const SetSmem& st, const unsigned i
     }
   }
   __syncwarp();
-  const int s = base;
+  return base;
+}
+
+static __device__ __noinline__ bool warp_rta(const SetSmem& st, const unsigned int* S, unsigned int m, unsigned int kc,
+                                      unsigned int km, const MagicDiv* __restrict__ mdiv, RtaScratch& sc,
+                                      long long* R_row, bool early_exit, unsigned int* err) {
+  const int lane = threadIdx.x & 31;
+  const int s = compact_partition(st, S, m, kc, km, mdiv[m], sc);
   bool all_ok = true;
   unsigned int errbits = 0u;
   for (int c0 = 0; c0 < s; c0 += 32) {
@@ -337,24 +344,264 @@ static __device__ __noinline__ bool warp_rta(const SetSmem& st, const unsigned i
   return all_ok;
 }
 
+// ------------------------------------------------------------------ EDF
+//
+// Second per-partition policy (the paper leaves §5.5's policy open):
+// preemptive EDF on the partition as one processor, synchronous periodic
+// release, constrained deadlines.  Exact processor-demand test by QPA (Zhang
+// & Burns, 2009): with dbf(t) = sum_{D_i <= t} (floor((t - D_i)/T_i) + 1) C_i,
+// start from the largest absolute deadline t < L and repeat
+//     h = dbf(t);  h > t: miss;  h <= d_min: schedulable;
+//     t = h if h < t, else the largest absolute deadline below t,
+// where L = min(L_a, L_b): L_a = max(D_max, sum (T_i - D_i) U_i / (1 - U))
+// (bounded from above in integers and floating point with a margin) and L_b
+// the synchronous busy period (least fixed point of sum ceil(w/T_i) C_i).
+// Same verdict as the plain criterion over every deadline up to the busy
+// period.  Readings (shared with the CPU reference): one task passes iff
+// C <= D; with two or more tasks the test needs
+// U_hi = sum ceil(2^32 C_i / T_i) < 2^32, i.e. it reports a miss whenever U
+// lies within n 2^-32 of 1.  A task with C > D misses at t = D.
+// Values stay below 2^63: C <= D <= T bounds each demand term by t + C.
+
+constexpr unsigned long long kEdfLmax = 1ull << 62;
+
+__device__ __forceinline__ unsigned long long edf_uterm(unsigned int C, unsigned int T) {
+  return (((unsigned long long)C << 32) + T - 1u) / T;
+}
+
+// Upper bound of L_a from the integer utilisation bound (floating point with
+// a relative margin far above its rounding error), capped at kEdfLmax.
+__device__ __forceinline__ unsigned long long edf_la_bound(double num, unsigned long long uhi, unsigned int dmax) {
+  const double den = (double)((1ull << 32) - uhi);
+  const double la = num / den * (1.0 + 0x1p-30) + 2.0;
+  const unsigned long long up = la >= (double)kEdfLmax ? kEdfLmax : (unsigned long long)la;
+  return up > dmax ? up : (unsigned long long)dmax;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(kFull, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64_edf(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// The largest absolute deadline k T + D (k >= 0) strictly below t, or 0.
+__device__ __forceinline__ unsigned long long edf_deadline_below(unsigned long long t, unsigned int T, unsigned int D) {
+  if (t <= D) return 0ull;
+  return (t - 1ull - D) / T * T + D;
+}
+
+// Warp-cooperative EDF test of S at m SMs; lane l holds the compacted tasks
+// l, l + 32, ...  Returns the verdict on every lane; *err |= kErrIter if an
+// iteration cap was reached (the verdict is then 0).
+static __device__ __noinline__ bool warp_edf(const SetSmem& st, const unsigned int* S, unsigned int m, unsigned int kc,
+                                      unsigned int km, const MagicDiv* __restrict__ mdiv, RtaScratch& sc,
+                                      unsigned int* err) {
+  const int lane = threadIdx.x & 31;
+  const int s = compact_partition(st, S, m, kc, km, mdiv[m], sc);
+  if (s == 0) return true;
+  if (s == 1) return sc.C[0] <= sc.D[0];
+  bool late = false;
+  unsigned long long uhi = 0, csum = 0;
+  double num = 0.0;
+  unsigned int dmin = 0xffffffffu, dmax = 0u;
+  for (int i = lane; i < s; i += 32) {
+    const unsigned int C = sc.C[i], T = sc.T[i], D = sc.D[i];
+    late = late || C > D;
+    const unsigned long long q = C <= D ? edf_uterm(C, T) : 0ull;
+    uhi += q;
+    csum += C;
+    num += (double)(T - D) * (double)q;
+    dmin = min(dmin, D);
+    dmax = max(dmax, D);
+  }
+  if (__any_sync(kFull, late)) return false;
+  uhi = warp_sum_u64_edf(uhi);
+  if (uhi >= (1ull << 32)) return false;
+  csum = warp_sum_u64_edf(csum);
+  num = warp_sum_f64(num);
+  dmin = __reduce_min_sync(kFull, dmin);
+  dmax = __reduce_max_sync(kFull, dmax);
+  const unsigned long long La = edf_la_bound(num, uhi, dmax);
+  // synchronous busy period, stopped at La
+  unsigned long long L = csum;
+  int iter = 0;
+  for (;;) {
+    unsigned long long part = 0;
+    for (int i = lane; i < s; i += 32) part += (L + sc.T[i] - 1ull) / sc.T[i] * sc.C[i];
+    const unsigned long long next = warp_sum_u64_edf(part);
+    if (next == L) break;
+    if (next >= La) {
+      L = La;
+      break;
+    }
+    L = next;
+    if (++iter > kIterCap) {
+      if (lane == 0) atomicOr(err, kErrIter);
+      return false;
+    }
+  }
+  // QPA
+  unsigned long long t = 0;
+  for (int i = lane; i < s; i += 32) {
+    const unsigned long long d = edf_deadline_below(L, sc.T[i], sc.D[i]);
+    t = d > t ? d : t;
+  }
+  t = warp_max_u64(t);
+  iter = 0;
+  while (t > 0ull) {
+    unsigned long long part = 0;
+    for (int i = lane; i < s; i += 32) {
+      const unsigned int D = sc.D[i];
+      if (D <= t) part += ((t - D) / sc.T[i] + 1ull) * sc.C[i];
+    }
+    const unsigned long long h = warp_sum_u64_edf(part);
+    if (h > t) return false;
+    if (h <= dmin) return true;
+    if (h < t) {
+      t = h;
+    } else {
+      unsigned long long d = 0;
+      for (int i = lane; i < s; i += 32) {
+        const unsigned long long e = edf_deadline_below(t, sc.T[i], sc.D[i]);
+        d = e > d ? e : d;
+      }
+      t = warp_max_u64(d);
+    }
+    if (++iter > kIterCap) {
+      if (lane == 0) atomicOr(err, kErrIter);
+      return false;
+    }
+  }
+  return true;
+}
+
+// The same EDF test by one thread over k tasks; get(a, C, T, D) yields the
+// a-th.  *errbits |= kErrIter if an iteration cap was reached.
+template <class Get>
+__device__ bool serial_edf(int k, Get get, unsigned int* errbits) {
+  unsigned int C, T, D;
+  if (k == 0) return true;
+  if (k == 1) {
+    get(0, C, T, D);
+    return C <= D;
+  }
+  unsigned long long uhi = 0, csum = 0;
+  double num = 0.0;
+  unsigned int dmin = 0xffffffffu, dmax = 0u;
+  for (int a = 0; a < k; a++) {
+    get(a, C, T, D);
+    if (C > D) return false;
+    const unsigned long long q = edf_uterm(C, T);
+    uhi += q;
+    csum += C;
+    num += (double)(T - D) * (double)q;
+    dmin = min(dmin, D);
+    dmax = max(dmax, D);
+  }
+  if (uhi >= (1ull << 32)) return false;
+  const unsigned long long La = edf_la_bound(num, uhi, dmax);
+  unsigned long long L = csum;
+  int iter = 0;
+  for (;;) {
+    unsigned long long next = 0;
+    for (int a = 0; a < k; a++) {
+      get(a, C, T, D);
+      next += (L + T - 1ull) / T * C;
+    }
+    if (next == L) break;
+    if (next >= La) {
+      L = La;
+      break;
+    }
+    L = next;
+    if (++iter > kIterCap) {
+      *errbits |= kErrIter;
+      return false;
+    }
+  }
+  unsigned long long t = 0;
+  for (int a = 0; a < k; a++) {
+    get(a, C, T, D);
+    const unsigned long long d = edf_deadline_below(L, T, D);
+    t = d > t ? d : t;
+  }
+  iter = 0;
+  while (t > 0ull) {
+    unsigned long long h = 0;
+    for (int a = 0; a < k; a++) {
+      get(a, C, T, D);
+      if (D <= t) h += ((t - D) / T + 1ull) * C;
+    }
+    if (h > t) return false;
+    if (h <= dmin) return true;
+    if (h < t) {
+      t = h;
+    } else {
+      unsigned long long d = 0;
+      for (int a = 0; a < k; a++) {
+        get(a, C, T, D);
+        const unsigned long long e = edf_deadline_below(t, T, D);
+        d = e > d ? e : d;
+      }
+      t = d;
+    }
+    if (++iter > kIterCap) {
+      *errbits |= kErrIter;
+      return false;
+    }
+  }
+  return true;
+}
+
+// The per-partition test of the model's policy.  Under EDF the test gives
+// no response times: R_row receives 0 for S's tasks when S passes, else -1.
+__device__ __forceinline__ bool warp_test(const SetSmem& st, const unsigned int* S, unsigned int m, unsigned int kc,
+                                          unsigned int km, int sched, const MagicDiv* __restrict__ mdiv,
+                                          RtaScratch& sc, long long* R_row, bool early_exit, unsigned int* err) {
+  if (sched != GPA_SCHED_EDF) return warp_rta(st, S, m, kc, km, mdiv, sc, R_row, early_exit, err);
+  const bool ok = warp_edf(st, S, m, kc, km, mdiv, sc, err);
+  if (R_row) {
+    const int lane = threadIdx.x & 31;
+    for (int w = 0; w < kWords; w++)
+      if ((S[w] >> lane) & 1u) R_row[w * 32 + lane] = ok ? 0ll : -1ll;
+  }
+  __syncwarp();
+  return ok;
+}
+
 // Alg. 2: smallest multiple of g in [lo, hi] at which S passes; 0 if none.
 // The binary form (§5.2) returns the same size because the test is monotone
 // in m (no timing anomalies, §4.1).
 __device__ __forceinline__ unsigned int warp_minm(const SetSmem& st, const unsigned int* S, unsigned int lo,
                                                   unsigned int hi, unsigned int g, bool linear, unsigned int kc,
-                                                  unsigned int km, const MagicDiv* __restrict__ mdiv, RtaScratch& sc,
-                                                  unsigned int* err) {
+                                                  unsigned int km, int sched, const MagicDiv* __restrict__ mdiv,
+                                                  RtaScratch& sc, unsigned int* err) {
   if (lo > hi) return 0u;
   if (linear) {
     for (unsigned int m = lo; m <= hi; m += g)
-      if (warp_rta(st, S, m, kc, km, mdiv, sc, nullptr, true, err)) return m;
+      if (warp_test(st, S, m, kc, km, sched, mdiv, sc, nullptr, true, err)) return m;
     return 0u;
   }
-  if (!warp_rta(st, S, hi, kc, km, mdiv, sc, nullptr, true, err)) return 0u;
+  if (!warp_test(st, S, hi, kc, km, sched, mdiv, sc, nullptr, true, err)) return 0u;
   unsigned int a = lo / g, b = hi / g;
   while (a < b) {
     unsigned int mid = a + (b - a) / 2u;
-    if (warp_rta(st, S, mid * g, kc, km, mdiv, sc, nullptr, true, err)) b = mid;
+    if (warp_test(st, S, mid * g, kc, km, sched, mdiv, sc, nullptr, true, err)) b = mid;
     else a = mid + 1u;
   }
   return a * g;

@@ -32,6 +32,7 @@ struct DevSets {
 
 struct DevModel {
   int M, g, kc, km;
+  int sched;  // GPA_SCHED_DM or GPA_SCHED_EDF
 };
 
 struct AllocOut {

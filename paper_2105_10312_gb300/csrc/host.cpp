@@ -48,7 +48,8 @@ extern "C" int32_t gpa_last_error(char* buf, int32_t len) {
 
 static bool model_valid(const gpa_model* m) {
   return m && m->g >= 1 && m->M >= 1 && m->M <= GPA_MMAX && m->M % m->g == 0 && m->k_c_pm >= 1000 &&
-         m->k_c_pm <= 16000 && m->k_m_pm >= 1000 && m->k_m_pm <= 16000;
+         m->k_c_pm <= 16000 && m->k_m_pm >= 1000 && m->k_m_pm <= 16000 &&
+         (m->sched == GPA_SCHED_DM || m->sched == GPA_SCHED_EDF);
 }
 
 static bool host_task_valid(int64_t T, int64_t D, int64_t A, int64_t B, int64_t u, uint8_t type) {
@@ -378,7 +379,7 @@ extern "C" int32_t gpa_build_wcet_tables(gpa_ctx* c, const gpa_tasksets* sets, c
   if (sets->nsets == 0) return GPA_OK;
   if (!Cn || !Cc) return gpa_fail(GPA_ERR_ARG, "gpa_build_wcet_tables: NULL output");
   DeviceGuard guard(c->device);
-  DevModel md{model->M, model->g, model->k_c_pm, model->k_m_pm};
+  DevModel md{model->M, model->g, model->k_c_pm, model->k_m_pm, model->sched};
   const long long Mu = model->M / model->g;
   if (sets->mem == GPA_DEVICE) {
     cudaError_t e = launch_wcet_tables(dev_sets(sets), md, (long long*)Cn, (long long*)Cc, c->d_err, c->d_mdiv,
@@ -417,7 +418,7 @@ extern "C" int32_t gpa_test_schedulable(gpa_ctx* c, const gpa_tasksets* sets, co
   if (!verdict || !cands->set || !cands->part_of_task || !cands->size_of_part)
     return gpa_fail(GPA_ERR_ARG, "gpa_test_schedulable: NULL array");
   DeviceGuard guard(c->device);
-  DevModel md{model->M, model->g, model->k_c_pm, model->k_m_pm};
+  DevModel md{model->M, model->g, model->k_c_pm, model->k_m_pm, model->sched};
   const long long nc = cands->ncands;
   if (sets->mem == GPA_DEVICE) {
     Cands cc{nc, cands->map_stride, cands->kparts, (const long long*)cands->set, cands->part_of_task,
@@ -490,7 +491,7 @@ static LaunchShape fast_shape(gpa_ctx* c, const DevSets& ds, const DevModel& md,
 std::string tune_key(const DevSets& ds, const DevModel& md, const gpa_params& p) {
   char buf[160];
   std::snprintf(buf, sizeof buf, "alloc:%lld:%d:%d:%d:%d:%d:%d", ds.nsets, ds.n_max, md.M, md.g, p.policy, p.act,
-                (int)0);
+                md.sched);
   return buf;
 }
 
@@ -549,10 +550,10 @@ static void autotune_allocate(gpa_ctx* c, const DevSets& ds, const DevModel& md,
 static std::string graph_key(const DevSets& ds, const DevModel& md, const gpa_params& p, const AllocOut& o,
                              const LaunchShape& sh) {
   char buf[512];
-  std::snprintf(buf, sizeof buf, "%lld|%d|%p|%p|%p|%p|%p|%p|%p|%d|%d|%d|%d|%d|%d|%d|%p|%p|%p|%p|%p|%p|%p|%p|%d|%d|%d|%d",
+  std::snprintf(buf, sizeof buf, "%lld|%d|%p|%p|%p|%p|%p|%p|%p|%d|%d|%d|%d|%d|%d|%d|%d|%p|%p|%p|%p|%p|%p|%p|%p|%d|%d|%d|%d",
                 ds.nsets, ds.n_max, (const void*)ds.set_off, (const void*)ds.T, (const void*)ds.D,
                 (const void*)ds.A, (const void*)ds.B, (const void*)ds.u, (const void*)ds.type, md.M, md.g, md.kc,
-                md.km, p.policy, p.act, p.linear_merge, (void*)o.verdict, (void*)o.reason, (void*)o.n_parts,
+                md.km, md.sched, p.policy, p.act, p.linear_merge, (void*)o.verdict, (void*)o.reason, (void*)o.n_parts,
                 (void*)o.Pi, (void*)o.W, (void*)o.n_tests, (void*)o.part_of_task, (void*)o.size_of_part,
                 sh.warps_per_block, sh.chunk, sh.blocks, sh.stages);
   return buf;
@@ -645,7 +646,7 @@ extern "C" int32_t gpa_allocate(gpa_ctx* c, const gpa_tasksets* sets, const gpa_
     return gpa_fail(GPA_ERR_ARG, "gpa_allocate: NULL result array");
   if (!sets->u_ppm) return gpa_fail(GPA_ERR_ARG, "gpa_allocate: u_ppm is required");
   DeviceGuard guard(c->device);
-  DevModel md{model->M, model->g, model->k_c_pm, model->k_m_pm};
+  DevModel md{model->M, model->g, model->k_c_pm, model->k_m_pm, model->sched};
   if (sets->mem == GPA_DEVICE) {
     AllocOut out{r->verdict, r->reason, r->n_parts, r->Pi, (long long*)r->W, r->n_tests, r->part_of_task,
                  r->size_of_part};
@@ -696,7 +697,7 @@ extern "C" int32_t gpa_search_best(gpa_ctx* c, const gpa_tasksets* sets, const g
   if (!r->feasible || !r->W || !r->sum_minm || !r->n_blocks || !r->spare || !r->rgs || !r->minm_block)
     return gpa_fail(GPA_ERR_ARG, "gpa_search_best: NULL result array");
   DeviceGuard guard(c->device);
-  DevModel md{model->M, model->g, model->k_c_pm, model->k_m_pm};
+  DevModel md{model->M, model->g, model->k_c_pm, model->k_m_pm, model->sched};
   AllocQueue q{c->d_counters, c->d_slow, c->d_err};
   if (sets->mem == GPA_DEVICE) {
     BestOut out{r->feasible, (long long*)r->W, r->sum_minm, r->n_blocks, r->spare, r->rgs, r->minm_block};

@@ -471,7 +471,8 @@ __global__ void __launch_bounds__(256) one_gpu(DevSets S, DevModel md, AllocOut 
       int lo = w * 32;
       all[w] = n >= lo + 32 ? kFull : (n > lo ? ((1u << (n - lo)) - 1u) : 0u);
     }
-    bool ok = n == 0 ? true : warp_rta(sm.st, all, (unsigned)md.M, md.kc, md.km, mdiv, sm.sc, nullptr, true, err);
+    bool ok = n == 0 ? true
+                     : warp_test(sm.st, all, (unsigned)md.M, md.kc, md.km, md.sched, mdiv, sm.sc, nullptr, true, err);
     unsigned long long Uc = 0, Um = 0;
     int nm = 0;
     for (int r = lane; r < n; r += 32) {

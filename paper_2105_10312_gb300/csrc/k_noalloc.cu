@@ -109,7 +109,8 @@ extern "C" int32_t gpa_allocate_noalloc(void* stream, const gpa_tasksets* sets, 
                     (long long)sets->nsets, kNoAllocMaxSets);
   if (sets->n_max < 0 || sets->n_max > GPA_NMAX) return gpa_fail(GPA_ERR_RANGE, "gpa_allocate_noalloc: n_max");
   if (model->g < 1 || model->M < 1 || model->M > GPA_MMAX || model->M % model->g != 0 || model->k_c_pm < 1000 ||
-      model->k_c_pm > 16000 || model->k_m_pm < 1000 || model->k_m_pm > 16000)
+      model->k_c_pm > 16000 || model->k_m_pm < 1000 || model->k_m_pm > 16000 ||
+      (model->sched != GPA_SCHED_DM && model->sched != GPA_SCHED_EDF))
     return gpa_fail(GPA_ERR_RANGE, "gpa_allocate_noalloc: model out of range");
   if (params->policy != GPA_POLICY_SMS && params->policy != GPA_POLICY_BF)
     return gpa_fail(GPA_ERR_ARG, "gpa_allocate_noalloc: policy must be GPA_POLICY_SMS or GPA_POLICY_BF");
@@ -129,7 +130,7 @@ extern "C" int32_t gpa_allocate_noalloc(void* stream, const gpa_tasksets* sets, 
                   (const long long*)sets->B,
                   (const long long*)sets->u_ppm,
                   (const unsigned char*)sets->type};
-  gpa::DevModel md{model->M, model->g, model->k_c_pm, model->k_m_pm};
+  gpa::DevModel md{model->M, model->g, model->k_c_pm, model->k_m_pm, model->sched};
   gpa::AllocOut out{r->verdict, r->reason, r->n_parts, r->Pi, (long long*)r->W, r->n_tests, r->part_of_task,
                     r->size_of_part};
   gpa::AllocQueue q{d->scratch->counters, d->scratch->slow_sets, &d->scratch->err};

@@ -107,6 +107,34 @@ __device__ bool serial_rta(const SearchHead& h, SearchThreads& w, unsigned int S
   return true;
 }
 
+// The model's per-partition test, serially: DM as above, or EDF (the
+// tasks' WCETs into w.C, then the processor-demand test).
+__device__ bool serial_test(const SearchHead& h, SearchThreads& w, unsigned int S, unsigned int m, unsigned int g,
+                            unsigned int kc, unsigned int km, int sched, const MagicDiv& md, const WcetTables& tb) {
+  if (sched != GPA_SCHED_EDF) return serial_rta(h, w, S, m, g, kc, km, md, tb);
+  const int tid = threadIdx.x;
+  const int nm = __popc(S & h.memmask), ns = __popc(S);
+  const bool cm = nm >= 2, cc = (ns - nm) >= 2;
+  const unsigned int kmem = cm ? km : 1000u, kcmp = cc ? kc : 1000u;
+  const int mi = (int)(m / g) - 1;
+  for (unsigned int rest = S; rest; rest &= rest - 1u) {
+    const int i = __ffs(rest) - 1;
+    const bool mem = (h.memmask >> i) & 1u;
+    w.C[i][tid] = tb.tn ? ((mem ? cm : cc) ? tb.tc : tb.tn)[mi * kSN + i]
+                        : wcet(h.A[i], h.B[i], mem ? kmem : kcmp, m, md);
+  }
+  unsigned int eb = 0u;
+  return serial_edf(
+      ns,
+      [&](int a, unsigned int& C, unsigned int& T, unsigned int& D) {
+        const int i = (int)__fns(S, 0u, a + 1);
+        C = w.C[i][tid];
+        T = h.T[i];
+        D = h.D[i];
+      },
+      &eb);
+}
+
 // Smallest multiple of g in [lo, M] at which S passes (0 if none), for a lo
 // known not to exceed the answer (the largest Lemma 2 size of S's tasks): a
 // binary search over lo .. M with M + g standing for "no size passes" (valid
@@ -117,7 +145,7 @@ __device__ unsigned int serial_minm(const SearchHead& h, SearchThreads& w, unsig
   unsigned int a = lo / g, b = M / g + 1u;
   while (a < b) {
     const unsigned int mid = a + (b - a) / 2u;
-    if (serial_rta(h, w, S, mid * g, g, md.kc, md.km, mdiv[mid * g], tb)) b = mid;
+    if (serial_test(h, w, S, mid * g, g, md.kc, md.km, md.sched, mdiv[mid * g], tb)) b = mid;
     else a = mid + 1u;
   }
   return a * g <= M ? a * g : 0u;

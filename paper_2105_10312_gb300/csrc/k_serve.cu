@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(128) serve_batch(const ServeReq* __restrict__ 
     for (int p = 0; p < np && path == GPA_PATH_NONE; p++) {
       rows_of(sm, n + 1, p, S);
       S[rnew >> 5] |= 1u << (rnew & 31);
-      if (warp_rta(sm.m.st, S, (unsigned)t->size[p], md.kc, md.km, mdiv, sm.m.sc, nullptr, true, err)) {
+      if (warp_test(sm.m.st, S, (unsigned)t->size[p], md.kc, md.km, md.sched, mdiv, sm.m.sc, nullptr, true, err)) {
         path = GPA_PATH_FIT;
         where = p;
         newsize = t->size[p];
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(128) serve_batch(const ServeReq* __restrict__ 
       rows_of(sm, n + 1, p, S);
       S[rnew >> 5] |= 1u << (rnew & 31);
       const unsigned m = warp_minm(sm.m.st, S, (unsigned)t->size[p] + g, (unsigned)t->size[p] + (unsigned)spare, g,
-                                   true, md.kc, md.km, mdiv, sm.m.sc, err);
+                                   true, md.kc, md.km, md.sched, mdiv, sm.m.sc, err);
       if (m) {
         path = GPA_PATH_GROW;
         where = p;
@@ -348,7 +348,8 @@ __global__ void __launch_bounds__(128) serve_batch(const ServeReq* __restrict__ 
       // its partition shrinks to its minimum size (the search of Alg. 2)
       unsigned int S[kWords];
       rows_of(sm, n2, pr, S);
-      const unsigned m = warp_minm(sm.m.st, S, g, (unsigned)t->size[pr], g, false, md.kc, md.km, mdiv, sm.m.sc, err);
+      const unsigned m =
+          warp_minm(sm.m.st, S, g, (unsigned)t->size[pr], g, false, md.kc, md.km, md.sched, mdiv, sm.m.sc, err);
       if (lane == 0) t->size[pr] = (short)m;
     }
     __syncwarp();

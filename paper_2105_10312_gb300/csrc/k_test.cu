@@ -141,8 +141,8 @@ __global__ void __launch_bounds__(256) test_candidates(DevSets S, DevModel md, C
         ok = false;
         continue;
       }
-      const bool pass = warp_rta(sm.st, Sp, (unsigned)z, (unsigned)md.kc, (unsigned)md.km, mdiv, sm.sc,
-                                 Rout ? sm.R : nullptr, Rout == nullptr, err);
+      const bool pass = warp_test(sm.st, Sp, (unsigned)z, (unsigned)md.kc, (unsigned)md.km, md.sched, mdiv, sm.sc,
+                                  Rout ? sm.R : nullptr, Rout == nullptr, err);
       ok = ok && pass;
       if (!ok && !Rout) break;
     }

@@ -369,7 +369,7 @@ extern "C" int32_t gpa_serve_start(gpa_ctx* c, const gpa_serve_cfg* cfg) {
   S->ctx = c;
   S->cfg = *cfg;
   S->device = c->device;
-  S->md = DevModel{cfg->M, cfg->g, cfg->k_c_pm, cfg->k_m_pm};
+  S->md = DevModel{cfg->M, cfg->g, cfg->k_c_pm, cfg->k_m_pm, GPA_SCHED_DM};
   S->prm = gpa_params{cfg->policy, cfg->act, 1, 0};
   S->pay_cap = (int64_t)cfg->max_batch * GPA_NMAX;
   bool ok = cudaStreamCreateWithFlags(&S->setup_stream, cudaStreamNonBlocking) == cudaSuccess &&

@@ -1,0 +1,111 @@
+"""GPU parity of the EDF per-partition policy (processor-demand test) against
+the CPU oracle: the candidate test, the heuristic, the 1G baseline and the
+exhaustive search, element by element on seeded inputs."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2105_10312_gb300 as gpa
+from paper_2105_10312_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+KC, KM = W.K_C, W.K_M
+ALLOC_KEYS = ("verdict", "reason", "n_parts", "Pi", "W", "n_tests", "part_of_task", "size_of_part")
+BEST_KEYS = ("feasible", "W", "sum_minm", "n_blocks", "spare", "rgs", "minm_block")
+
+
+def _np(x):
+    return x.cpu().numpy() if torch.is_tensor(x) else x
+
+
+def _assert_equal(got, ref, keys, what):
+    for k in keys:
+        g, r = _np(got[k]), ref[k]
+        if not np.array_equal(g, r):
+            bad = np.nonzero(g != r)[0]
+            raise AssertionError(f"{what}: {k} differs at {len(bad)} positions, first {bad[:8]}: "
+                                 f"gpu {g[bad[:8]]} oracle {r[bad[:8]]}")
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_edf_random_candidates(ctx, seed):
+    """Random splits and maps of 0..128-task sets: verdicts and the per-task
+    R convention (0 in a passing part, -1 otherwise) equal the oracle's; EDF
+    accepts every candidate DM accepts, and some that DM rejects."""
+    rng = np.random.default_rng(seed)
+    s = gpa.gen_tasksets(seed=60 + seed, nsets=64, n_min=0, n_max=128, U_lo_ppm=100000, U_hi_ppm=8000000,
+                         deadline_pm=750, mu_dist="BETA25", T_lo=1000, T_hi=100000)
+    M, g, k, stride = 96, 2, 5, 128
+    nc = 3000
+    cset = rng.integers(0, 64, nc).astype(np.int64)
+    cmap = rng.integers(0, k, nc * stride).astype(np.uint8)
+    csize = (g * rng.integers(0, M // g // 3 + 1, nc * k)).astype(np.int32)
+    d = gpa.to_device(s)
+    args = (torch.from_numpy(cset).cuda(), torch.from_numpy(cmap).cuda(), torch.from_numpy(csize).cuda(), stride, k)
+    for with_R in (True, False):
+        v, R = ctx.test_schedulable(d, M, *args, g=g, with_R=with_R, sched="EDF")
+        ctx.sync()
+        vr, Rr = oracle.test_schedulable(s, M, g, KC, KM, cset, cmap, stride, k, csize, with_R=with_R, sched="EDF")
+        assert np.array_equal(_np(v), vr)
+        if with_R:
+            assert np.array_equal(_np(R), Rr)
+    vd, _ = ctx.test_schedulable(d, M, *args, g=g, with_R=False)
+    ctx.sync()
+    vd = _np(vd)
+    assert (vr >= vd).all()
+    assert (vr > vd).sum() > 0 and 0 < vr.sum() < nc
+
+
+@pytest.mark.parametrize("policy,act", [("SMS", False), ("SMS", True), ("BF", False), ("BF", True)])
+def test_edf_allocate_paper_setting(ctx, policy, act):
+    """The §7 setting under EDF: the merge loop runs (one-lane candidate
+    sizing and the warp test both), results equal the oracle's."""
+    s = gpa.gen_tasksets(**W.gen_params("paper50", nsets=34 * 3))
+    md = W.model("paper50")
+    out = ctx.allocate(gpa.to_device(s), **md, policy=policy, act=act, sched="EDF")
+    ctx.sync()
+    ref = oracle.allocate(s, md["M"], md["g"], KC, KM, policy=policy, act=act, nthreads=8, sched="EDF")
+    _assert_equal(out, ref, ALLOC_KEYS, f"paper50 EDF {policy} act={act}")
+    assert ref["n_tests"].sum() > 1000
+
+
+def test_edf_allocate_binary_merge_tpc_and_batch(ctx):
+    s = gpa.gen_tasksets(seed=61, nsets=400, n_min=1, n_max=40, U_lo_ppm=500000, U_hi_ppm=20000000,
+                         deadline_pm=750, T_lo=1000, T_hi=100000)
+    for md in (dict(M=40, g=2, k_c_pm=KC, k_m_pm=KM), dict(M=16, g=4, k_c_pm=1500, k_m_pm=4000)):
+        for linear in (True, False):
+            out = ctx.allocate(gpa.to_device(s), **md, linear=linear, sched="EDF")
+            ctx.sync()
+            ref = oracle.allocate(s, md["M"], md["g"], md["k_c_pm"], md["k_m_pm"], linear=linear, nthreads=8,
+                                  sched="EDF")
+            _assert_equal(out, ref, ALLOC_KEYS, f"EDF M={md['M']} g={md['g']} linear={linear}")
+    b = gpa.gen_tasksets(**W.gen_params("batch", nsets=5000))
+    md = W.model("batch")
+    out = ctx.allocate(gpa.to_device(b), **md, sched="EDF")
+    ctx.sync()
+    ref = oracle.allocate(b, md["M"], md["g"], KC, KM, nthreads=8, sched="EDF")
+    _assert_equal(out, ref, ALLOC_KEYS, "EDF batch")
+
+
+def test_edf_one_gpu(ctx):
+    s = gpa.gen_tasksets(**W.gen_params("sweep", nsets=3000))
+    md = W.model("sweep")
+    out = ctx.allocate(gpa.to_device(s), **md, policy="ONE_GPU", sched="EDF")
+    ctx.sync()
+    ref = oracle.allocate(s, md["M"], md["g"], KC, KM, policy="ONE_GPU", nthreads=8, sched="EDF")
+    _assert_equal(out, ref, ALLOC_KEYS, "EDF 1G")
+    dm = oracle.allocate(s, md["M"], md["g"], KC, KM, policy="ONE_GPU", nthreads=8)
+    assert (ref["verdict"] >= dm["verdict"]).all() and 0 < ref["verdict"].sum() < 3000
+
+
+def test_edf_search_best(ctx):
+    s = gpa.gen_tasksets(seed=62, nsets=40, n_min=1, n_max=8, U_lo_ppm=500000, U_hi_ppm=3500000, deadline_pm=750,
+                         T_lo=1000, T_hi=100000)
+    M, g, kmin, kmax = 40, 2, 1, 4
+    out = ctx.search_best(gpa.to_device(s), M, g=g, k_c_pm=KC, k_m_pm=KM, kmin=kmin, kmax=kmax, sched="EDF")
+    ctx.sync()
+    ref = oracle.search_best(s, M, g, KC, KM, kmin, kmax, nthreads=8, sched="EDF")
+    _assert_equal(out, ref, BEST_KEYS, "EDF search")
+    assert ref["feasible"].sum() > 10
