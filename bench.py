@@ -168,10 +168,10 @@ def oracle_step(sets, md, workload, policy, act, threads):
     if workload == "exhaustive":
         wp = W.WORKLOADS["exhaustive"]
         oracle.search_best(sets, md["M"], md["g"], md["k_c_pm"], md["k_m_pm"], wp["kmin"], wp["kmax"],
-                           nthreads=threads)
+                           nthreads=threads, sched=md.get("sched", "DM"))
     else:
         oracle.allocate(sets, md["M"], md["g"], md["k_c_pm"], md["k_m_pm"], policy=policy, act=act,
-                        nthreads=threads)
+                        nthreads=threads, sched=md.get("sched", "DM"))
 
 
 def oracle_sample(sets, md, workload, policy, act, threads, target_s):
@@ -330,6 +330,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     sets, md = build_workload(args.workload, 0, args.nsets)
+    md["sched"] = args.sched.upper()
     policy, act = policy_of(args.workload)
     threads = os.cpu_count() or 1
     nsets_all = len(sets["set_off"]) - 1
@@ -348,7 +349,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": DESCR.get(args.workload, args.workload), "nsets": nsets, "M": md["M"],
-                   "policy": policy, "act": act},
+                   "policy": policy, "act": act, "sched": md["sched"]},
         "cpu_baseline": {"value": v, "unit": "tasksets/s", "cores": threads, "kind": "oracle",
                          "sample": f"{args.steps} pass(es) over the first {nsets} of the {nsets_all} sets"},
         "e2e": {"value": v, "unit": "tasksets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -371,6 +372,7 @@ def run_gpu(args):
     torch.cuda.set_device(dev)
 
     sets, md = build_workload(args.workload, rank, args.nsets)
+    md["sched"] = args.sched.upper()
     policy, act = policy_of(args.workload)
     nsets = len(sets["set_off"]) - 1
     ntasks = int(sets["set_off"][-1])
@@ -557,6 +559,7 @@ def run_gpu(args):
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": DESCR.get(args.workload, args.workload), "nsets_per_gpu": nsets,
                        "tasks_per_gpu": ntasks, "M": md["M"], "g": md["g"], "policy": policy, "act": act,
+                       "sched": md["sched"],
                        "l2": "flushed between timed steps (512 MB write, then 256 MB read); inputs 109 MB < 129 MB L2",
                        "parallelism": f"{world} independent shard(s)", "launch": "persistent + CUDA graph",
                        "launch_shape": "autotuned" if autotune else
@@ -583,6 +586,8 @@ def main():
     ap.add_argument("--impl", choices=["gpa", "reference"], default="gpa")
     ap.add_argument("--workload", choices=sorted(DESCR), default="batch")
     ap.add_argument("--nsets", type=int, default=0, help="override the workload's set count (profiling)")
+    ap.add_argument("--sched", choices=["dm", "edf"], default="dm",
+                    help="per-partition policy: deadline-monotonic response-time test (default) or EDF demand test")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--plain-sample", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")

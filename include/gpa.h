@@ -57,8 +57,9 @@
  * test: dbf(t) = sum_{D_i <= t} (floor((t - D_i) / T_i) + 1) C_i <= t at every
  * absolute deadline up to the first synchronous busy period (evaluated with
  * QPA, Zhang & Burns 2009).  One task passes iff C <= D; with two or more
- * tasks the test requires sum_i ceil(2^32 C_i / T_i) < 2^32, so a set whose
- * utilisation lies within n 2^-32 of 1 is reported as failing (conservative).
+ * tasks the test requires sum_i ceil(2^32 C_i / T_i) <= 2^32 - 2^22, i.e.
+ * U <= 1 - 2^-10: a set above that is reported as failing (conservative; it
+ * bounds the busy period, and so the analysis time, near U = 1).
  * EDF gives no response times: R is 0 for the tasks of a passing part.
  *
  * Validation bounds (GPA_ERR_RANGE): 0 <= n <= 128 tasks per set,

@@ -160,8 +160,9 @@ static int rta(const oset* s, const omodel* md, const unsigned char* in, int64_t
  * w = sum_i ceil(w / T_i) C_i from w = sum_i C_i.
  * Readings: one task passes iff C <= D; with two or more tasks U is bounded
  * by U_hi = sum_i ceil(2^32 C_i / T_i) / 2^32 and the test passes only if
- * U_hi < 1 (a set whose U lies within n 2^-32 of 1 is reported as missing a
- * deadline: conservative, and it keeps L finite). */
+ * U_hi <= 1 - 2^-10 (a set with U above that, or within n 2^-32 below it, is
+ * reported as missing a deadline: conservative; it keeps L within about
+ * 2^10 times the total WCET, so the analysis ends quickly). */
 static int edf(const oset* s, const omodel* md, const unsigned char* in, int64_t m) {
   int64_t C[ONMAX];
   int idx[ONMAX], k = 0;
@@ -177,7 +178,7 @@ static int edf(const oset* s, const omodel* md, const unsigned char* in, int64_t
     int i = idx[a];
     uhi += (((i128)C[i] << 32) + s->T[i] - 1) / s->T[i];
   }
-  if (uhi >= ((i128)1 << 32)) return 0;
+  if (uhi > ((i128)1 << 32) - ((i128)1 << 22)) return 0;
   i128 L = 0;
   for (int a = 0; a < k; a++) L += C[idx[a]];
   for (;;) {

@@ -359,11 +359,14 @@ static __device__ __noinline__ bool warp_rta(const SetSmem& st, const unsigned i
 // Same verdict as the plain criterion over every deadline up to the busy
 // period.  Readings (shared with the CPU reference): one task passes iff
 // C <= D; with two or more tasks the test needs
-// U_hi = sum ceil(2^32 C_i / T_i) < 2^32, i.e. it reports a miss whenever U
-// lies within n 2^-32 of 1.  A task with C > D misses at t = D.
+// U_hi = sum ceil(2^32 C_i / T_i) <= 2^32 - 2^22, i.e. U <= 1 - 2^-10 (a
+// miss is reported above that: conservative, and it bounds the busy period
+// by about 2^10 times the total WCET, so both iterations end quickly).  A
+// task with C > D misses at t = D.
 // Values stay below 2^63: C <= D <= T bounds each demand term by t + C.
 
 constexpr unsigned long long kEdfLmax = 1ull << 62;
+constexpr unsigned long long kEdfUmax = (1ull << 32) - (1ull << 22);  // the largest accepted U_hi (x 2^32)
 
 __device__ __forceinline__ unsigned long long edf_uterm(unsigned int C, unsigned int T) {
   return (((unsigned long long)C << 32) + T - 1u) / T;
@@ -431,7 +434,7 @@ static __device__ __noinline__ bool warp_edf(const SetSmem& st, const unsigned i
   }
   if (__any_sync(kFull, late)) return false;
   uhi = warp_sum_u64_edf(uhi);
-  if (uhi >= (1ull << 32)) return false;
+  if (uhi > kEdfUmax) return false;
   csum = warp_sum_u64_edf(csum);
   num = warp_sum_f64(num);
   dmin = __reduce_min_sync(kFull, dmin);
@@ -513,7 +516,7 @@ __device__ bool serial_edf(int k, Get get, unsigned int* errbits) {
     dmin = min(dmin, D);
     dmax = max(dmax, D);
   }
-  if (uhi >= (1ull << 32)) return false;
+  if (uhi > kEdfUmax) return false;
   const unsigned long long La = edf_la_bound(num, uhi, dmax);
   unsigned long long L = csum;
   int iter = 0;

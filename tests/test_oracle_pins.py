@@ -224,8 +224,8 @@ def test_rta_monotone_in_m_and_in_tasks():
 
 def _edf_band(C, T):
     """The oracle's reading: with two or more tasks U is bounded by
-    sum ceil(2^32 C / T) / 2^32, and the test needs that bound below 1."""
-    return sum(-(-(int(c) << 32) // int(t)) for c, t in zip(C, T)) >= (1 << 32)
+    sum ceil(2^32 C / T) / 2^32, and the test needs that bound <= 1 - 2^-10."""
+    return sum(-(-(int(c) << 32) // int(t)) for c, t in zip(C, T)) > (1 << 32) - (1 << 22)
 
 
 def test_edf_matches_edf_simulation():
