@@ -19,8 +19,10 @@
  *    cached CUDA graphs and device scratch) and the serving state.
  *  - Memory tag: structs carrying arrays have a `mem` field, GPA_HOST or
  *    GPA_DEVICE, that applies to every array of that struct.  Host inputs
- *    are validated on the host before any launch (GPA_ERR_RANGE, nothing
- *    launched) and the call is synchronous.  Device inputs are validated by
+ *    are copied into the context's device buffers and checked against the
+ *    bounds there before any computation (GPA_ERR_RANGE naming the first
+ *    offending set; nothing is computed and no output is written); the call
+ *    is synchronous.  Device inputs are validated by
  *    the kernels: an invalid set gets reason GPA_REASON_INVALID, its other
  *    outputs are zero, and the context's sticky error word is set; the call
  *    itself is asynchronous on the context stream and gpa_ctx_sync() reports

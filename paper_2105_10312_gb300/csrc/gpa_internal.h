@@ -99,6 +99,8 @@ cudaError_t launch_one_gpu(const DevSets& s, const DevModel& md, const AllocOut&
 // Per-process kernel attribute set-up (dynamic shared memory opt-in).
 cudaError_t alloc_kernels_init();
 cudaError_t search_kernels_init();
+cudaError_t launch_validate_batch(const DevSets& s, unsigned int* flag, int sm_count, cudaStream_t st,
+                                  long long* launches);
 cudaError_t launch_wcet_tables(const DevSets& s, const DevModel& md, long long* Cn, long long* Cc, unsigned int* err,
                                const MagicDivHost* mdiv, int sm_count, cudaStream_t st, long long* launches,
                                Prof* prof);

@@ -9,6 +9,9 @@
 #include <cstring>
 #include <map>
 #include <algorithm>
+#include <atomic>
+#include <condition_variable>
+#include <functional>
 #include <mutex>
 #include <thread>
 #include <string>
@@ -57,6 +60,74 @@ static bool host_task_valid(int64_t T, int64_t D, int64_t A, int64_t B, int64_t 
          u >= 0 && u <= 4294967295LL && type <= 1;
 }
 
+// The same bounds without branches (unsigned compares), so that a loop over
+// a column range vectorises.
+static inline bool task_in_bounds(int64_t T, int64_t D, int64_t A, int64_t B, int64_t u, uint8_t type) {
+  const uint64_t uT = (uint64_t)T, uD = (uint64_t)D, uA = (uint64_t)A, uB = (uint64_t)B, uu = (uint64_t)u;
+  return (uT <= 0x7fffffffull) & (uD - 1ull < uT) & (uA <= (1ull << 36)) & (uB <= (1ull << 36)) &
+         (uA + uB - 1ull < (1ull << 36)) & (uu <= 0xffffffffull) & (type <= 1);
+}
+
+// A fixed pool of host worker threads (created on first use, never torn
+// down; calls are serialised) for the batch validation of host inputs.
+namespace {
+class HostPool {
+ public:
+  static HostPool& get() {
+    static HostPool* pool = new HostPool();
+    return *pool;
+  }
+  int workers() const { return (int)threads_.size(); }
+  // fn(k) for k in [0, parts), on the workers and the calling thread.
+  void run(int parts, const std::function<void(int)>& fn) {
+    std::lock_guard<std::mutex> call(call_mu_);
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      fn_ = &fn;
+      parts_ = parts;
+      next_.store(0);
+      done_ = 0;
+      gen_++;
+    }
+    cv_.notify_all();
+    work();
+    std::unique_lock<std::mutex> lk(mu_);
+    done_cv_.wait(lk, [&] { return done_ == (int)threads_.size(); });
+    fn_ = nullptr;
+  }
+
+ private:
+  HostPool() {
+    int n = (int)std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()), 32u) - 1;
+    for (int i = 0; i < n; i++) threads_.emplace_back([this] { loop(); });
+    for (auto& t : threads_) t.detach();
+  }
+  void work() {
+    for (int k = next_.fetch_add(1); k < parts_; k = next_.fetch_add(1)) (*fn_)(k);
+  }
+  void loop() {
+    unsigned long long seen = 0;
+    for (;;) {
+      {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [&] { return gen_ != seen; });
+        seen = gen_;
+      }
+      work();
+      std::lock_guard<std::mutex> lk(mu_);
+      if (++done_ == (int)threads_.size()) done_cv_.notify_one();
+    }
+  }
+  std::vector<std::thread> threads_;
+  std::mutex call_mu_, mu_;
+  std::condition_variable cv_, done_cv_;
+  const std::function<void(int)>* fn_ = nullptr;
+  int parts_ = 0, done_ = 0;
+  std::atomic<int> next_{0};
+  unsigned long long gen_ = 0;
+};
+}  // namespace
+
 extern "C" int32_t gpa_validate(const gpa_tasksets* sets, const gpa_model* model, int64_t* bad_set) {
   if (bad_set) *bad_set = -1;
   if (!sets || !sets->set_off) return gpa_fail(GPA_ERR_ARG, "gpa_validate: NULL task sets");
@@ -68,33 +139,58 @@ extern "C" int32_t gpa_validate(const gpa_tasksets* sets, const gpa_model* model
   if (sets->nsets > 0 && sets->set_off[sets->nsets] > 0 &&
       (!sets->T || !sets->D || !sets->A || !sets->B || !sets->type))
     return gpa_fail(GPA_ERR_ARG, "gpa_validate: NULL task column");
-  // sets are checked in parallel ranges; the first invalid set wins
-  auto check = [sets](int64_t s0, int64_t s1) -> int64_t {
-    for (int64_t s = s0; s < s1; s++) {
-      const int64_t o = sets->set_off[s], n = sets->set_off[s + 1] - o;
-      bool ok = n >= 0 && n <= sets->n_max;
-      for (int64_t t = 0; ok && t < n; t++)
-        ok = host_task_valid(sets->T[o + t], sets->D[o + t], sets->A[o + t], sets->B[o + t],
-                             sets->u_ppm ? sets->u_ppm[o + t] : 0, sets->type[o + t]);
-      if (!ok) return s;
-    }
-    return -1;
-  };
   const int64_t ns = sets->nsets;
-  const int64_t ntasks = ns > 0 ? sets->set_off[ns] : 0;
-  int nth = (int)std::min<int64_t>(std::max(1u, std::thread::hardware_concurrency()), 32);
-  if (ntasks < 200000) nth = 1;
-  std::vector<int64_t> first((size_t)nth, -1);
-  std::vector<std::thread> pool;
-  for (int k = 1; k < nth; k++)
-    pool.emplace_back([&, k] { first[(size_t)k] = check(ns * k / nth, ns * (k + 1) / nth); });
-  first[0] = check(0, ns / nth);
-  for (auto& th : pool) th.join();
-  for (int64_t s : first)
-    if (s >= 0) {
+  const int64_t* off = sets->set_off;
+  // fast pass: every set size in [0, n_max], then (the offsets being
+  // monotone) every task in bounds, in parallel ranges of sets
+  const int64_t ntasks_hint = ns > 0 ? off[ns] : 0;
+  const int parts = ntasks_hint >= 200000 ? 64 : 1;
+  std::atomic<bool> bad{false};
+  auto sizes_ok = [&](int64_t s0, int64_t s1) {
+    bool ok = true;
+    for (int64_t s = s0; s < s1; s++) {
+      const int64_t n = off[s + 1] - off[s];
+      ok &= (n >= 0) & (n <= sets->n_max);
+    }
+    return ok;
+  };
+  auto tasks_ok = [&](int64_t t0, int64_t t1) {
+    bool ok = true;
+    const int64_t *T = sets->T, *D = sets->D, *A = sets->A, *B = sets->B, *u = sets->u_ppm;
+    const uint8_t* ty = sets->type;
+    if (u) {
+      for (int64_t t = t0; t < t1; t++) ok &= task_in_bounds(T[t], D[t], A[t], B[t], u[t], ty[t]);
+    } else {
+      for (int64_t t = t0; t < t1; t++) ok &= task_in_bounds(T[t], D[t], A[t], B[t], 0, ty[t]);
+    }
+    return ok;
+  };
+  std::function<void(int)> size_pass = [&](int k) {
+    if (!sizes_ok(ns * k / parts, ns * (k + 1) / parts)) bad.store(true);
+  };
+  std::function<void(int)> task_pass = [&](int k) {
+    const int64_t s0 = ns * k / parts, s1 = ns * (k + 1) / parts;
+    if (!tasks_ok(off[s0], off[s1])) bad.store(true);
+  };
+  if (parts > 1) HostPool::get().run(parts, size_pass);
+  else size_pass(0);
+  if (!bad.load()) {
+    if (parts > 1) HostPool::get().run(parts, task_pass);
+    else task_pass(0);
+  }
+  if (!bad.load()) return GPA_OK;
+  // slow path: the first invalid set
+  for (int64_t s = 0; s < ns; s++) {
+    const int64_t o = off[s], n = off[s + 1] - o;
+    bool ok = n >= 0 && n <= sets->n_max;
+    for (int64_t t = 0; ok && t < n; t++)
+      ok = host_task_valid(sets->T[o + t], sets->D[o + t], sets->A[o + t], sets->B[o + t],
+                           sets->u_ppm ? sets->u_ppm[o + t] : 0, sets->type[o + t]);
+    if (!ok) {
       if (bad_set) *bad_set = s;
       return gpa_fail(GPA_ERR_RANGE, "gpa_validate: set %lld violates the bounds", (long long)s);
     }
+  }
   return GPA_OK;
 }
 
@@ -363,9 +459,37 @@ static int32_t common_checks(gpa_ctx* c, const gpa_tasksets* sets, const gpa_mod
   if (sets->nsets < 0 || sets->n_max < 0 || sets->n_max > GPA_NMAX)
     return gpa_fail(GPA_ERR_RANGE, "%s: nsets/n_max out of range", who);
   if (sets->mem == GPA_HOST) {
-    int64_t bad;
-    int32_t st = gpa_validate(sets, model, &bad);
-    if (st != GPA_OK) return st;
+    // cheap structural checks here; the bounds of every task are checked by
+    // stage_in_validated while the copies run
+    if (sets->set_off[0] != 0) return gpa_fail(GPA_ERR_RANGE, "%s: set_off[0] != 0", who);
+    if (sets->nsets > 0 && sets->set_off[sets->nsets] < 0)
+      return gpa_fail(GPA_ERR_RANGE, "%s: negative task count", who);
+  }
+  return GPA_OK;
+}
+
+// Host inputs: copy the batch into context buffers, check its bounds there
+// with one grid-stride kernel, and launch no computation when they fail (the
+// host then names the first offending set with gpa_validate).  The copies
+// and the check are waited for before the call goes on, so no transfer reads
+// the caller's arrays after an early return.
+static int32_t stage_in_validated(gpa_ctx* c, const gpa_tasksets* sets, const gpa_model* model, HostStage* hs) {
+  int32_t st = GPA_OK;
+  if (sets->nsets > 0 && sets->set_off[sets->nsets] > 0 &&
+      (!sets->T || !sets->D || !sets->A || !sets->B || !sets->type))
+    return gpa_fail(GPA_ERR_ARG, "NULL task column");
+  if ((st = stage_in(c, sets, hs)) != GPA_OK) return st;
+  unsigned int* dflag = (unsigned int*)ctx_buffer(c, 29, sizeof(unsigned int));
+  if (!dflag) return gpa_fail(GPA_ERR_NOMEM, "validation flag allocation failed");
+  cudaError_t e = launch_validate_batch(hs->ds, dflag, c->sm_count, c->stream, &c->launches);
+  unsigned int flag = 0u;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, dflag, sizeof flag, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return gpa_cuda_fail(e, "batch validation");
+  if (flag) {
+    int64_t bad = -1;
+    st = gpa_validate(sets, model, &bad);
+    return st != GPA_OK ? st : gpa_fail(GPA_ERR_RANGE, "a set violates the bounds");
   }
   return GPA_OK;
 }
@@ -387,7 +511,7 @@ extern "C" int32_t gpa_build_wcet_tables(gpa_ctx* c, const gpa_tasksets* sets, c
     return e == cudaSuccess ? GPA_OK : gpa_cuda_fail(e, "wcet_tables launch");
   }
   HostStage hs;
-  if ((st = stage_in(c, sets, &hs)) != GPA_OK) return st;
+  if ((st = stage_in_validated(c, sets, model, &hs)) != GPA_OK) return st;
   const size_t bytes = sizeof(long long) * (size_t)(hs.ntasks * Mu > 0 ? hs.ntasks * Mu : 1);
   long long* dCn = (long long*)ctx_buffer(c, 7, bytes);
   long long* dCc = (long long*)ctx_buffer(c, 8, bytes);
@@ -443,7 +567,7 @@ extern "C" int32_t gpa_test_schedulable(gpa_ctx* c, const gpa_tasksets* sets, co
     }
   }
   HostStage hs;
-  if ((st = stage_in(c, sets, &hs)) != GPA_OK) return st;
+  if ((st = stage_in_validated(c, sets, model, &hs)) != GPA_OK) return st;
   long long* dset = (long long*)ctx_buffer(c, 9, sizeof(long long) * (size_t)nc);
   unsigned char* dmap = (unsigned char*)ctx_buffer(c, 10, (size_t)(nc * cands->map_stride));
   int* dsize = (int*)ctx_buffer(c, 11, sizeof(int) * (size_t)(nc * cands->kparts));
@@ -653,7 +777,7 @@ extern "C" int32_t gpa_allocate(gpa_ctx* c, const gpa_tasksets* sets, const gpa_
     return allocate_device(c, dev_sets(sets), md, *params, out);
   }
   HostStage hs;
-  if ((st = stage_in(c, sets, &hs)) != GPA_OK) return st;
+  if ((st = stage_in_validated(c, sets, model, &hs)) != GPA_OK) return st;
   const long long ns = sets->nsets, nt = hs.ntasks > 0 ? hs.ntasks : 1;
   AllocOut out{(unsigned char*)ctx_buffer(c, 14, (size_t)ns), (unsigned char*)ctx_buffer(c, 15, (size_t)ns),
                (int*)ctx_buffer(c, 16, sizeof(int) * (size_t)ns), (int*)ctx_buffer(c, 17, sizeof(int) * (size_t)ns),
@@ -706,7 +830,7 @@ extern "C" int32_t gpa_search_best(gpa_ctx* c, const gpa_tasksets* sets, const g
     return e == cudaSuccess ? GPA_OK : gpa_cuda_fail(e, "search_best launch");
   }
   HostStage hs;
-  if ((st = stage_in(c, sets, &hs)) != GPA_OK) return st;
+  if ((st = stage_in_validated(c, sets, model, &hs)) != GPA_OK) return st;
   const long long ns = sets->nsets, nt = hs.ntasks > 0 ? hs.ntasks : 1;
   BestOut out{(unsigned char*)ctx_buffer(c, 22, (size_t)ns), (long long*)ctx_buffer(c, 23, 8 * (size_t)ns),
               (int*)ctx_buffer(c, 24, 4 * (size_t)ns), (int*)ctx_buffer(c, 25, 4 * (size_t)ns),

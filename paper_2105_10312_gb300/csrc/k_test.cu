@@ -156,7 +156,35 @@ __global__ void __launch_bounds__(256) test_candidates(DevSets S, DevModel md, C
   }
 }
 
+// Bounds of a staged host batch (the same as task_valid and the set sizes
+// in [0, n_max]): *flag becomes nonzero if any set or task violates them.
+// Grid-stride and coalesced; the first offending set is looked up on the
+// host only when the flag is set.
+__global__ void __launch_bounds__(256) validate_batch(DevSets S, unsigned int* flag) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long ntasks = S.set_off[S.nsets];
+  bool bad = false;
+  for (long long s = tid; s < S.nsets; s += stride) {
+    const long long n = S.set_off[s + 1] - S.set_off[s];
+    bad = bad || n < 0 || n > S.n_max;
+  }
+  for (long long t = tid; t < ntasks; t += stride)
+    bad = bad || !task_valid(__ldg(S.T + t), __ldg(S.D + t), __ldg(S.A + t), __ldg(S.B + t),
+                             S.u ? __ldg(S.u + t) : 0ll, __ldg(S.type + t));
+  if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
 }  // namespace
+
+cudaError_t launch_validate_batch(const DevSets& s, unsigned int* flag, int sm_count, cudaStream_t st,
+                                  long long* launches) {
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) return e;
+  validate_batch<<<sm_count * 4, 256, 0, st>>>(s, flag);
+  *launches += 1;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_wcet_tables(const DevSets& s, const DevModel& md, long long* Cn, long long* Cc, unsigned int* err,
                                const MagicDivHost* mdiv, int sm_count, cudaStream_t st, long long* launches,

@@ -297,6 +297,28 @@ def test_allocate_odd_task_count_and_unaligned_columns(ctx, stages):
         c2.close()
 
 
+def test_host_input_out_of_bounds_computes_nothing(ctx):
+    """A host batch with one task out of bounds: GPA_ERR_RANGE naming that
+    set, no output written; the next valid call works."""
+    s = gpa.gen_tasksets(**W.gen_params("batch", nsets=2000))
+    bad = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in s.items()}
+    bad["D"][int(bad["set_off"][1234]) + 1] = 0
+    md = W.model("batch")
+    out = ctx.alloc_result(bad)
+    for v in out.values():
+        if v is not None:
+            v.fill(77)
+    with pytest.raises(gpa.GpaError) as ei:
+        ctx.allocate(bad, **md, out=out)
+    assert ei.value.code == gpa.ERR_RANGE and "1234" in str(ei.value)
+    for k, v in out.items():
+        if v is not None:
+            assert (v == 77).all(), k
+    good = ctx.allocate(s, **md)
+    ref = oracle.allocate(s, md["M"], md["g"], KC, KM, nthreads=8)
+    _assert_equal(good, ref, ALLOC_KEYS, "after a rejected call")
+
+
 def test_device_validation_flags_invalid_sets(ctx):
     s = _edge_batch()
     s["D"] = s["D"].copy()
