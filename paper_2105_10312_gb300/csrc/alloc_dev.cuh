@@ -161,11 +161,13 @@ __device__ bool lane_edf(const SetSmem& st, const unsigned int* S, unsigned int 
   unsigned int eb = 0u;
   const bool ok = serial_edf(
       pos,
-      [&](int a, unsigned int& C, unsigned int& T, unsigned int& D) {
+      [&](int a, unsigned int& C, unsigned int& T, unsigned int& D, unsigned int& mg, unsigned int& sh) {
         const int r = ls.row[a][lane];
         C = ls.C[a][lane];
         T = st.T[r];
         D = st.D[r];
+        mg = st.mT[r];
+        sh = st.shT[r];
       },
       &eb);
   if (eb) atomicOr(err, eb);

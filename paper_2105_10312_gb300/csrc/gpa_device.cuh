@@ -381,6 +381,26 @@ __device__ __forceinline__ unsigned long long edf_la_bound(double num, unsigned 
   return up > dmax ? up : (unsigned long long)dmax;
 }
 
+// The band rule decided cheaply first: uf = sum of float C_i / T_i is within
+// 2^-14 of U for n <= 128 (each term within 3 ulp, the float sum within
+// n ulp), and U <= U_hi / 2^32 <= U + n 2^-32.  So uf below kEdfPass means
+// U_hi <= kEdfUmax, above kEdfFail means U_hi > kEdfUmax; only in between
+// are the exact integer terms summed.  numf = sum (T_i - D_i) C_i / T_i in
+// the same precision gives L_a <= numf (1 + 2^-20) / (1 - uf - 2^-14).
+constexpr float kEdfPass = 1.0f - 0x1p-10f - 0x1p-13f;
+constexpr float kEdfFail = 1.0f - 0x1p-10f + 0x1p-13f;
+// Density: sum C_i / D_i <= 1 makes a constrained-deadline set EDF-feasible
+// (dbf(t) <= sum C_i (t / D_i) <= t); the float sum is within 2^-14 of the
+// exact one, so dens <= 1 - 2^-14 proves it.
+constexpr float kEdfDensity = 1.0f - 0x1p-14f;
+
+__device__ __forceinline__ unsigned long long edf_la_bound_f(double numf, float uf, unsigned int dmax) {
+  const double den = 1.0 - ((double)uf + 0x1p-14);
+  const double la = numf * (1.0 + 0x1p-20) / den * (1.0 + 0x1p-30) + 2.0;
+  const unsigned long long up = la >= (double)kEdfLmax ? kEdfLmax : (unsigned long long)la;
+  return up > dmax ? up : (unsigned long long)dmax;
+}
+
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -402,10 +422,24 @@ __device__ __forceinline__ unsigned long long warp_sum_u64_edf(unsigned long lon
   return v;
 }
 
+// floor(x / T) and ceil(x / T) for 64-bit x: the period's reciprocal while
+// x stays below 2^31 (the common case), a 64-bit division above.
+__device__ __forceinline__ unsigned long long floor_div_T64(unsigned long long x, unsigned int T, unsigned int mg,
+                                                            unsigned int sh) {
+  return x < 0x7fffffffull ? (unsigned long long)(ceil_div_T((unsigned int)x + 1u, mg, sh) - 1u) : x / T;
+}
+
+__device__ __forceinline__ unsigned long long ceil_div_T64(unsigned long long x, unsigned int T, unsigned int mg,
+                                                           unsigned int sh) {
+  if (x == 0ull) return 0ull;
+  return x < 0x80000000ull ? (unsigned long long)ceil_div_T((unsigned int)x, mg, sh) : (x + T - 1ull) / T;
+}
+
 // The largest absolute deadline k T + D (k >= 0) strictly below t, or 0.
-__device__ __forceinline__ unsigned long long edf_deadline_below(unsigned long long t, unsigned int T, unsigned int D) {
+__device__ __forceinline__ unsigned long long edf_deadline_below(unsigned long long t, unsigned int T, unsigned int D,
+                                                                 unsigned int mg, unsigned int sh) {
   if (t <= D) return 0ull;
-  return (t - 1ull - D) / T * T + D;
+  return floor_div_T64(t - 1ull - D, T, mg, sh) * T + D;
 }
 
 // Warp-cooperative EDF test of S at m SMs; lane l holds the compacted tasks
@@ -419,33 +453,52 @@ static __device__ __noinline__ bool warp_edf(const SetSmem& st, const unsigned i
   if (s == 0) return true;
   if (s == 1) return sc.C[0] <= sc.D[0];
   bool late = false;
-  unsigned long long uhi = 0, csum = 0;
-  double num = 0.0;
+  unsigned long long csum = 0;
+  float uf = 0.0f;
+  double numf = 0.0;
   unsigned int dmin = 0xffffffffu, dmax = 0u;
+  float dens = 0.0f;
   for (int i = lane; i < s; i += 32) {
     const unsigned int C = sc.C[i], T = sc.T[i], D = sc.D[i];
     late = late || C > D;
-    const unsigned long long q = C <= D ? edf_uterm(C, T) : 0ull;
-    uhi += q;
+    const float r = (float)C / (float)T;
+    uf += r;
+    dens += (float)C / (float)D;
+    numf += (double)(T - D) * (double)r;
     csum += C;
-    num += (double)(T - D) * (double)q;
     dmin = min(dmin, D);
     dmax = max(dmax, D);
   }
   if (__any_sync(kFull, late)) return false;
-  uhi = warp_sum_u64_edf(uhi);
-  if (uhi > kEdfUmax) return false;
+  uf = (float)warp_sum_f64((double)uf);  // the butterfly leaves the same sum on every lane
+  dens = (float)warp_sum_f64((double)dens);
   csum = warp_sum_u64_edf(csum);
-  num = warp_sum_f64(num);
   dmin = __reduce_min_sync(kFull, dmin);
   dmax = __reduce_max_sync(kFull, dmax);
-  const unsigned long long La = edf_la_bound(num, uhi, dmax);
+  if (uf > kEdfFail) return false;
+  // density sum C_i / D_i <= 1 is sufficient (within the band)
+  if (uf < kEdfPass && dens <= kEdfDensity) return true;
+  unsigned long long La;
+  if (uf < kEdfPass) {
+    La = edf_la_bound_f(warp_sum_f64(numf), uf, dmax);
+  } else {
+    unsigned long long uhi = 0;
+    double num = 0.0;
+    for (int i = lane; i < s; i += 32) {
+      const unsigned long long q = edf_uterm(sc.C[i], sc.T[i]);
+      uhi += q;
+      num += (double)(sc.T[i] - sc.D[i]) * (double)q;
+    }
+    uhi = warp_sum_u64_edf(uhi);
+    if (uhi > kEdfUmax) return false;
+    La = edf_la_bound(warp_sum_f64(num), uhi, dmax);
+  }
   // synchronous busy period, stopped at La
   unsigned long long L = csum;
   int iter = 0;
   for (;;) {
     unsigned long long part = 0;
-    for (int i = lane; i < s; i += 32) part += (L + sc.T[i] - 1ull) / sc.T[i] * sc.C[i];
+    for (int i = lane; i < s; i += 32) part += ceil_div_T64(L, sc.T[i], sc.mT[i], sc.sh[i]) * sc.C[i];
     const unsigned long long next = warp_sum_u64_edf(part);
     if (next == L) break;
     if (next >= La) {
@@ -461,7 +514,7 @@ static __device__ __noinline__ bool warp_edf(const SetSmem& st, const unsigned i
   // QPA
   unsigned long long t = 0;
   for (int i = lane; i < s; i += 32) {
-    const unsigned long long d = edf_deadline_below(L, sc.T[i], sc.D[i]);
+    const unsigned long long d = edf_deadline_below(L, sc.T[i], sc.D[i], sc.mT[i], sc.sh[i]);
     t = d > t ? d : t;
   }
   t = warp_max_u64(t);
@@ -470,7 +523,7 @@ static __device__ __noinline__ bool warp_edf(const SetSmem& st, const unsigned i
     unsigned long long part = 0;
     for (int i = lane; i < s; i += 32) {
       const unsigned int D = sc.D[i];
-      if (D <= t) part += ((t - D) / sc.T[i] + 1ull) * sc.C[i];
+      if (D <= t) part += (floor_div_T64(t - D, sc.T[i], sc.mT[i], sc.sh[i]) + 1ull) * sc.C[i];
     }
     const unsigned long long h = warp_sum_u64_edf(part);
     if (h > t) return false;
@@ -480,7 +533,7 @@ static __device__ __noinline__ bool warp_edf(const SetSmem& st, const unsigned i
     } else {
       unsigned long long d = 0;
       for (int i = lane; i < s; i += 32) {
-        const unsigned long long e = edf_deadline_below(t, sc.T[i], sc.D[i]);
+        const unsigned long long e = edf_deadline_below(t, sc.T[i], sc.D[i], sc.mT[i], sc.sh[i]);
         d = e > d ? e : d;
       }
       t = warp_max_u64(d);
@@ -493,38 +546,57 @@ static __device__ __noinline__ bool warp_edf(const SetSmem& st, const unsigned i
   return true;
 }
 
-// The same EDF test by one thread over k tasks; get(a, C, T, D) yields the
-// a-th.  *errbits |= kErrIter if an iteration cap was reached.
+// The same EDF test by one thread over k tasks; get(a, C, T, D, mg, sh)
+// yields the a-th with its period's reciprocal.  *errbits |= kErrIter if an
+// iteration cap was reached.
 template <class Get>
 __device__ bool serial_edf(int k, Get get, unsigned int* errbits) {
-  unsigned int C, T, D;
+  unsigned int C, T, D, mg, sh;
   if (k == 0) return true;
   if (k == 1) {
-    get(0, C, T, D);
+    get(0, C, T, D, mg, sh);
     return C <= D;
   }
-  unsigned long long uhi = 0, csum = 0;
-  double num = 0.0;
+  unsigned long long csum = 0;
+  float uf = 0.0f;
+  double numf = 0.0;
   unsigned int dmin = 0xffffffffu, dmax = 0u;
+  float dens = 0.0f;
   for (int a = 0; a < k; a++) {
-    get(a, C, T, D);
+    get(a, C, T, D, mg, sh);
     if (C > D) return false;
-    const unsigned long long q = edf_uterm(C, T);
-    uhi += q;
+    const float r = (float)C / (float)T;
+    uf += r;
+    dens += (float)C / (float)D;
+    numf += (double)(T - D) * (double)r;
     csum += C;
-    num += (double)(T - D) * (double)q;
     dmin = min(dmin, D);
     dmax = max(dmax, D);
   }
-  if (uhi > kEdfUmax) return false;
-  const unsigned long long La = edf_la_bound(num, uhi, dmax);
+  if (uf > kEdfFail) return false;
+  if (uf < kEdfPass && dens <= kEdfDensity) return true;  // density <= 1 suffices
+  unsigned long long La;
+  if (uf < kEdfPass) {
+    La = edf_la_bound_f(numf, uf, dmax);
+  } else {
+    unsigned long long uhi = 0;
+    double num = 0.0;
+    for (int a = 0; a < k; a++) {
+      get(a, C, T, D, mg, sh);
+      const unsigned long long q = edf_uterm(C, T);
+      uhi += q;
+      num += (double)(T - D) * (double)q;
+    }
+    if (uhi > kEdfUmax) return false;
+    La = edf_la_bound(num, uhi, dmax);
+  }
   unsigned long long L = csum;
   int iter = 0;
   for (;;) {
     unsigned long long next = 0;
     for (int a = 0; a < k; a++) {
-      get(a, C, T, D);
-      next += (L + T - 1ull) / T * C;
+      get(a, C, T, D, mg, sh);
+      next += ceil_div_T64(L, T, mg, sh) * C;
     }
     if (next == L) break;
     if (next >= La) {
@@ -539,16 +611,16 @@ __device__ bool serial_edf(int k, Get get, unsigned int* errbits) {
   }
   unsigned long long t = 0;
   for (int a = 0; a < k; a++) {
-    get(a, C, T, D);
-    const unsigned long long d = edf_deadline_below(L, T, D);
+    get(a, C, T, D, mg, sh);
+    const unsigned long long d = edf_deadline_below(L, T, D, mg, sh);
     t = d > t ? d : t;
   }
   iter = 0;
   while (t > 0ull) {
     unsigned long long h = 0;
     for (int a = 0; a < k; a++) {
-      get(a, C, T, D);
-      if (D <= t) h += ((t - D) / T + 1ull) * C;
+      get(a, C, T, D, mg, sh);
+      if (D <= t) h += (floor_div_T64(t - D, T, mg, sh) + 1ull) * C;
     }
     if (h > t) return false;
     if (h <= dmin) return true;
@@ -557,8 +629,8 @@ __device__ bool serial_edf(int k, Get get, unsigned int* errbits) {
     } else {
       unsigned long long d = 0;
       for (int a = 0; a < k; a++) {
-        get(a, C, T, D);
-        const unsigned long long e = edf_deadline_below(t, T, D);
+        get(a, C, T, D, mg, sh);
+        const unsigned long long e = edf_deadline_below(t, T, D, mg, sh);
         d = e > d ? e : d;
       }
       t = d;

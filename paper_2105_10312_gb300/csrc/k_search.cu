@@ -126,11 +126,13 @@ __device__ bool serial_test(const SearchHead& h, SearchThreads& w, unsigned int 
   unsigned int eb = 0u;
   return serial_edf(
       ns,
-      [&](int a, unsigned int& C, unsigned int& T, unsigned int& D) {
+      [&](int a, unsigned int& C, unsigned int& T, unsigned int& D, unsigned int& mg, unsigned int& sh) {
         const int i = (int)__fns(S, 0u, a + 1);
         C = w.C[i][tid];
         T = h.T[i];
         D = h.D[i];
+        mg = h.mT[i];
+        sh = h.sh[i];
       },
       &eb);
 }
