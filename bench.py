@@ -563,7 +563,7 @@ def run_gpu(args):
                        "l2": "flushed between timed steps (512 MB write, then 256 MB read); inputs 109 MB < 129 MB L2",
                        "parallelism": f"{world} independent shard(s)", "launch": "persistent + CUDA graph",
                        "launch_shape": "autotuned" if autotune else
-                       "library default (fast kernel: direct loads, 8 warps/CTA, 2 sets per chunk, grid = occupancy x SMs)"},
+                       "library default (fast kernel: direct loads, 4 warps/CTA, 2 sets per chunk, grid = occupancy x SMs)"},
             "candidates_tested_per_s": cand_total / (max_ms / 1000.0),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks, "per_set_launch": plain, "wall_s_timed": wall, "serve": serve,

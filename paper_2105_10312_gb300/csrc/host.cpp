@@ -597,7 +597,7 @@ extern "C" int32_t gpa_test_schedulable(gpa_ctx* c, const gpa_tasksets* sets, co
 // blocks = 0: the launcher sizes the grid to the kernel's occupancy x SMs
 static LaunchShape default_fast(const gpa_ctx* c) {
   (void)c;
-  return LaunchShape{8, 2, 0, 1};
+  return LaunchShape{4, 2, 0, 1};
 }
 static LaunchShape default_slow(const gpa_ctx* c) { return LaunchShape{4, 1, c->sm_count * 2, 1}; }
 
