@@ -109,3 +109,79 @@ def test_edf_search_best(ctx):
     ref = oracle.search_best(s, M, g, KC, KM, kmin, kmax, nthreads=8, sched="EDF")
     _assert_equal(out, ref, BEST_KEYS, "EDF search")
     assert ref["feasible"].sum() > 10
+
+
+def _crafted_batch(sets_tasks):
+    """Sets of (T, D, C) tasks alternating types (no conflict at k = 1000),
+    A = 1000 C and B = 0 so that C(1) = C."""
+    off, cols = [0], {k: [] for k in ("T", "D", "A", "B", "u_ppm", "type")}
+    for tasks in sets_tasks:
+        for j, (T, D, C) in enumerate(tasks):
+            cols["T"].append(T)
+            cols["D"].append(D)
+            cols["A"].append(1000 * C)
+            cols["B"].append(0)
+            cols["u_ppm"].append(10**6 * C // T)
+            cols["type"].append(j % 2)
+        off.append(off[-1] + len(tasks))
+    out = {k: np.array(v, np.uint8 if k == "type" else np.int64) for k, v in cols.items()}
+    out["set_off"] = np.array(off, np.int64)
+    out["n_max"] = max(len(t) for t in sets_tasks)
+    return out
+
+
+def _one_part_candidates(s, m):
+    nsets = len(s["set_off"]) - 1
+    stride = int(s["n_max"])
+    cset = np.arange(nsets, dtype=np.int64)
+    cmap = np.zeros(nsets * stride, np.uint8)
+    csize = np.full(nsets, m, np.int32)
+    return cset, cmap, csize, stride
+
+
+def _edf_candidate_parity(ctx, s, M=1, kc=1000, km=1000):
+    cset, cmap, csize, stride = _one_part_candidates(s, 1)
+    d = gpa.to_device(s)
+    v, R = ctx.test_schedulable(d, M, torch.from_numpy(cset).cuda(), torch.from_numpy(cmap).cuda(),
+                                torch.from_numpy(csize).cuda(), stride, 1, k_c_pm=kc, k_m_pm=km, sched="EDF")
+    ctx.sync()
+    vr, Rr = oracle.test_schedulable(s, M, 1, kc, km, cset, cmap, stride, 1, csize, sched="EDF")
+    assert np.array_equal(_np(v), vr) and np.array_equal(_np(R), Rr)
+    return vr
+
+
+def test_edf_utilisation_band_edges(ctx):
+    """Pairs of tasks whose U straddles the accepted bound 1 - 2^-10 by a few
+    WCET units, so the float pre-check defers to the exact integer terms;
+    constrained and implicit deadlines; verdicts equal the oracle's."""
+    sets = []
+    T1 = T2 = 1000000
+    for dc in range(-40, 41, 4):
+        C1 = 499000
+        C2 = 500023 + dc        # U = (C1 + C2) / 10^6 around 1 - 2^-10 = 0.9990234375
+        sets.append([(T1, T1, C1), (T2, T2, C2)])
+        sets.append([(T1, 999999, C1), (T2, T2, C2)])
+    for dc in range(-30, 31, 3):
+        sets.append([(3 * 1000003, 3 * 1000003, 1500000 + dc), (2000000, 1999000, 998000)])
+    v = _edf_candidate_parity(ctx, _crafted_batch(sets))
+    assert 0 < v.sum() < len(v)
+
+
+def test_edf_busy_period_beyond_31_bits(ctx):
+    """Many large tasks at U close to the bound: the busy period and the QPA
+    points pass 2^31, so the 64-bit division paths run; verdicts equal the
+    oracle's."""
+    rng = np.random.default_rng(7)
+    sets = []
+    for trial in range(24):
+        n = int(rng.integers(60, 128))
+        T = rng.integers(100_000_000, 400_000_000, n)
+        target = 0.95 + 0.049 * rng.random()   # total U in [0.95, 0.999)
+        w = rng.random(n)
+        C = np.maximum(1, (target * w / w.sum() * T).astype(np.int64))
+        C = np.minimum(C, 60_000_000)  # A = 1000 C stays within 2^36
+        D = np.maximum(C, (T * rng.uniform(0.15, 1.0, n)).astype(np.int64))
+        sets.append(list(zip(T.tolist(), D.tolist(), C.tolist())))
+    s = _crafted_batch(sets)
+    v = _edf_candidate_parity(ctx, s)
+    assert v.sum() > 0
