@@ -469,6 +469,44 @@ def run_gpu(args):
         cand_total = shard.sum_over_ranks(float(out["n_tests"].sum().item()) if out.get("n_tests") is not None else 0)
     value = total_sets / (max_ms / 1000.0)
 
+    # outcome summaries the configurations ask for (untimed): the optimum
+    # against the heuristic per set (exhaustive), and the schedulability
+    # ratio per utilisation step of the heuristic against 1G (sweep)
+    outcome = None
+    if args.workload == "exhaustive":
+        wp = W.WORKLOADS["exhaustive"]
+        with torch.cuda.stream(stream):
+            h = ctx.allocate(d, **md, policy="SMS", act=False)
+            ctx.sync()
+        fo = out["feasible"].cpu().numpy().astype(bool)
+        fh = h["verdict"].cpu().numpy().astype(bool)
+        wo, wh = out["W"].cpu().numpy(), h["W"].cpu().numpy()
+        nph = h["n_parts"].cpu().numpy()
+        # the optimum is over at most kmax partitions; the heuristic may end
+        # with more (down to one per task), so W is compared where it kept
+        # within kmax
+        comp = fo & fh & (nph >= wp["kmin"]) & (nph <= wp["kmax"])
+        outcome = {"optimum_feasible": float(fo.mean()), "heuristic_feasible": float(fh.mean()),
+                   "heuristic_partitions_mean": float(nph[fh].mean()) if fh.any() else None,
+                   "mean_W_heuristic_over_optimum": float((wh[fo & fh] / np.maximum(wo[fo & fh], 1)).mean())
+                   if (fo & fh).any() else None,
+                   "heuristic_within_kmax": float(comp.sum() / max(1, (fo & fh).sum())),
+                   "mean_W_heuristic_over_optimum_within_kmax":
+                       float((wh[comp] / np.maximum(wo[comp], 1)).mean()) if comp.any() else None,
+                   "heuristic_at_optimum_W_within_kmax": float((wh[comp] == wo[comp]).mean()) if comp.any() else None,
+                   "optimum_partitions": f"{wp['kmin']}..{wp['kmax']}"}
+    elif args.workload in ("sweep", "sweep1g"):
+        steps = W.WORKLOADS["sweep"]["gen"]["U_steps"]
+        with torch.cuda.stream(stream):
+            hh = ctx.allocate(d, **md, policy="SMS", act=False)
+            g1 = ctx.allocate(d, **md, policy="ONE_GPU", act=False)
+            ctx.sync()
+        vh, v1 = hh["verdict"].cpu().numpy(), g1["verdict"].cpu().numpy()
+        st = np.arange(nsets) % steps
+        outcome = {"U": [round(0.1 * (j + 1), 1) for j in range(steps)],
+                   "heuristic": [round(float(vh[st == j].mean()), 4) for j in range(steps)],
+                   "1G": [round(float(v1[st == j].mean()), 4) for j in range(steps)]}
+
     # roofline of the dominant kernel (the fast allocate kernel for the heuristic workloads)
     hbm_peak, peak_src = read_peaks()
     roof = None
@@ -567,6 +605,7 @@ def run_gpu(args):
             "candidates_tested_per_s": cand_total / (max_ms / 1000.0),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks, "per_set_launch": plain, "wall_s_timed": wall, "serve": serve,
+            "outcome": outcome,
         }
         print(json.dumps(line))
     ctx.close()
