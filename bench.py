@@ -401,7 +401,7 @@ def run_gpu(args):
         out = ctx.alloc_result(d)
 
         def step():
-            ctx.allocate(d, **md, policy=policy, act=act, out=out)
+            ctx.allocate(d, **md, policy=policy, act=act, linear=args.merge == "linear", out=out)
 
     with torch.cuda.stream(stream):
         for i in range(max(args.warmup, 0)):
@@ -597,7 +597,7 @@ def run_gpu(args):
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": DESCR.get(args.workload, args.workload), "nsets_per_gpu": nsets,
                        "tasks_per_gpu": ntasks, "M": md["M"], "g": md["g"], "policy": policy, "act": act,
-                       "sched": md["sched"],
+                       "sched": md["sched"], "merge_search": args.merge,
                        "l2": "flushed between timed steps (512 MB write, then 256 MB read); inputs 109 MB < 129 MB L2",
                        "parallelism": f"{world} independent shard(s)", "launch": "persistent + CUDA graph",
                        "launch_shape": "autotuned" if autotune else
@@ -625,6 +625,8 @@ def main():
     ap.add_argument("--impl", choices=["gpa", "reference"], default="gpa")
     ap.add_argument("--workload", choices=sorted(DESCR), default="batch")
     ap.add_argument("--nsets", type=int, default=0, help="override the workload's set count (profiling)")
+    ap.add_argument("--merge", choices=["linear", "binary"], default="linear",
+                    help="Alg. 2 size search of a merge: linear scan (default) or the binary search of §5.2")
     ap.add_argument("--sched", choices=["dm", "edf"], default="dm",
                     help="per-partition policy: deadline-monotonic response-time test (default) or EDF demand test")
     ap.add_argument("--e2e-steps", type=int, default=5)

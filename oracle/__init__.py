@@ -110,13 +110,22 @@ def edf(T, D, A, B, typ, in_mask, m, kc, km):
                              ctypes.c_int64(km)))
 
 
-def minm(T, D, A, B, typ, in_mask, lo, hi, g, kc, km, linear=True, sched="DM"):
+def _sizes(sizes):
+    """(pointer, count) of an admissible size list; (None, 0) for every multiple of g."""
+    if sizes is None or len(sizes) == 0:
+        return None, 0
+    arr = np.ascontiguousarray(sizes, dtype=np.int32)
+    return _p(arr), len(arr)
+
+
+def minm(T, D, A, B, typ, in_mask, lo, hi, g, kc, km, linear=True, sched="DM", sizes=None):
     _fresh()
     out = ctypes.c_int64()
+    zp, zn = _sizes(sizes)
     _check(lib().orc_minm(ctypes.c_int(len(T)), _p(_i64(T)), _p(_i64(D)), _p(_i64(A)), _p(_i64(B)), _p(_u8(typ)),
                           _p(_u8(in_mask)), ctypes.c_int64(lo), ctypes.c_int64(hi), ctypes.c_int64(g),
-                          ctypes.c_int64(kc), ctypes.c_int64(km), ctypes.c_int64(SCHED[sched]),
-                          ctypes.c_int(1 if linear else 0), ctypes.byref(out)), "minm")
+                          ctypes.c_int64(kc), ctypes.c_int64(km), ctypes.c_int64(SCHED[sched]), zp,
+                          ctypes.c_int64(zn), ctypes.c_int(1 if linear else 0), ctypes.byref(out)), "minm")
     return out.value
 
 
@@ -135,8 +144,9 @@ def lemma1_rejects(T, A, B, M):
 
 
 def test_schedulable(sets, M, g, kc, km, cand_set, part_of_task, map_stride, kparts, size_of_part, with_R=True,
-                     sched="DM"):
+                     sched="DM", sizes=None):
     _fresh()
+    zp, zn = _sizes(sizes)
     off = _i64(sets["set_off"])
     cand_set = _i64(cand_set)
     nc = len(cand_set)
@@ -147,14 +157,16 @@ def test_schedulable(sets, M, g, kc, km, cand_set, part_of_task, map_stride, kpa
     _check(lib().orc_test_schedulable(
         ctypes.c_int64(len(off) - 1), _p(off), _p(_i64(sets["T"])), _p(_i64(sets["D"])), _p(_i64(sets["A"])),
         _p(_i64(sets["B"])), _p(_u8(sets["type"])), ctypes.c_int64(M), ctypes.c_int64(g), ctypes.c_int64(kc),
-        ctypes.c_int64(km), ctypes.c_int64(SCHED[sched]), ctypes.c_int64(nc), _p(cand_set), _p(pot),
+        ctypes.c_int64(km), ctypes.c_int64(SCHED[sched]), zp, ctypes.c_int64(zn), ctypes.c_int64(nc), _p(cand_set),
+        _p(pot),
         ctypes.c_int64(map_stride),
         ctypes.c_int64(kparts), _p(sop), _p(verdict), _p(R)), "test_schedulable")
     return verdict, R
 
 
-def allocate(sets, M, g, kc, km, policy="SMS", act=False, linear=True, nthreads=1, sched="DM"):
+def allocate(sets, M, g, kc, km, policy="SMS", act=False, linear=True, nthreads=1, sched="DM", sizes=None):
     _fresh()
+    zp, zn = _sizes(sizes)
     off = _i64(sets["set_off"])
     nsets = len(off) - 1
     ntasks = int(off[-1])
@@ -167,7 +179,8 @@ def allocate(sets, M, g, kc, km, policy="SMS", act=False, linear=True, nthreads=
     _check(lib().orc_allocate(
         ctypes.c_int64(nsets), _p(off), _p(_i64(sets["T"])), _p(_i64(sets["D"])), _p(_i64(sets["A"])),
         _p(_i64(sets["B"])), _p(_i64(sets["u_ppm"])), _p(_u8(sets["type"])), ctypes.c_int64(M), ctypes.c_int64(g),
-        ctypes.c_int64(kc), ctypes.c_int64(km), ctypes.c_int64(SCHED[sched]), ctypes.c_int(POLICY[policy]),
+        ctypes.c_int64(kc), ctypes.c_int64(km), ctypes.c_int64(SCHED[sched]), zp, ctypes.c_int64(zn),
+        ctypes.c_int(POLICY[policy]),
         ctypes.c_int(1 if act else 0),
         ctypes.c_int(1 if linear else 0), _p(out["verdict"]), _p(out["reason"]), _p(out["n_parts"]), _p(out["Pi"]),
         _p(out["W"]), _p(out["n_tests"]), _p(out["part_of_task"]), _p(out["size_of_part"]),
@@ -175,8 +188,9 @@ def allocate(sets, M, g, kc, km, policy="SMS", act=False, linear=True, nthreads=
     return out
 
 
-def search_best(sets, M, g, kc, km, kmin, kmax, explicit=False, nthreads=1, sched="DM"):
+def search_best(sets, M, g, kc, km, kmin, kmax, explicit=False, nthreads=1, sched="DM", sizes=None):
     _fresh()
+    zp, zn = _sizes(sizes)
     off = _i64(sets["set_off"])
     nsets = len(off) - 1
     ntasks = int(off[-1])
@@ -188,8 +202,8 @@ def search_best(sets, M, g, kc, km, kmin, kmax, explicit=False, nthreads=1, sche
     }
     args = [ctypes.c_int64(nsets), _p(off), _p(_i64(sets["T"])), _p(_i64(sets["D"])), _p(_i64(sets["A"])),
             _p(_i64(sets["B"])), _p(_i64(sets["u_ppm"])), _p(_u8(sets["type"])), ctypes.c_int64(M),
-            ctypes.c_int64(g), ctypes.c_int64(kc), ctypes.c_int64(km), ctypes.c_int64(SCHED[sched]),
-            ctypes.c_int(kmin), ctypes.c_int(kmax),
+            ctypes.c_int64(g), ctypes.c_int64(kc), ctypes.c_int64(km), ctypes.c_int64(SCHED[sched]), zp,
+            ctypes.c_int64(zn), ctypes.c_int(kmin), ctypes.c_int(kmax),
             _p(out["feasible"]), _p(out["W"]), _p(out["sum_minm"]), _p(out["n_blocks"]), _p(out["spare"]),
             _p(out["rgs"]), _p(out["minm_block"]), ctypes.c_int(nthreads)]
     if explicit:

@@ -65,7 +65,25 @@ enum { S_DM = 0, S_EDF = 1 };
 typedef struct {
   int64_t M, g, kc, km;
   int64_t sched; /* per-partition policy: S_DM (the reading of §5.5) or S_EDF */
+  const int32_t* sizes; /* admissible partition sizes, increasing; NULL: every multiple of g */
+  int64_t nsizes;
 } omodel;
+
+/* Is m an admissible partition size of the model?  Without a size list,
+ * every multiple of g in [g, M] is (§4.1 with the unit g); with one, only
+ * its members are (partitions of whole GPCs / MIG slices, §2). */
+static int admissible(const omodel* md, int64_t m) {
+  if (m < md->g || m > md->M) return 0;
+  if (md->nsizes == 0) return m % md->g == 0;
+  for (int64_t k = 0; k < md->nsizes; k++)
+    if (md->sizes[k] == m) return 1;
+  return 0;
+}
+
+/* The smallest admissible size. */
+static int64_t smallest_size(const omodel* md) {
+  return md->nsizes == 0 ? md->g : md->sizes[0];
+}
 
 static oset view(int64_t s, const int64_t* set_off, const int64_t* T, const int64_t* D, const int64_t* A,
                  const int64_t* B, const int64_t* u, const uint8_t* type) {
@@ -209,26 +227,29 @@ static int test(const oset* s, const omodel* md, const unsigned char* in, int64_
   return md->sched == S_EDF ? edf(s, md, in, m) : rta(s, md, in, m, NULL);
 }
 
-/* Alg. 2: the first size m in lo, lo+g, ..., hi at which the merged task set
- * passes the test; 0 when none does. */
+/* Alg. 2: the first admissible size m in [lo, hi] at which the merged task
+ * set passes the test; 0 when none does. */
 static int64_t minm_linear(const oset* s, const omodel* md, const unsigned char* in, int64_t lo, int64_t hi) {
-  for (int64_t m = lo; m <= hi; m += md->g)
-    if (test(s, md, in, m)) return m;
+  for (int64_t m = lo; m <= hi; m++)
+    if (admissible(md, m) && test(s, md, in, m)) return m;
   return 0;
 }
 
 /* §5.2: the same answer by binary search (valid because the test is
  * monotone in m under the no-timing-anomaly hypothesis of §4.1). */
 static int64_t minm_binary(const oset* s, const omodel* md, const unsigned char* in, int64_t lo, int64_t hi) {
-  if (lo > hi) return 0;
-  if (!test(s, md, in, hi)) return 0;
-  int64_t a = lo / md->g, b = hi / md->g;
+  int64_t cand[1025];
+  int nc = 0;
+  for (int64_t m = lo; m <= hi && m <= 1024; m++)
+    if (admissible(md, m)) cand[nc++] = m;
+  if (nc == 0 || !test(s, md, in, cand[nc - 1])) return 0;
+  int a = 0, b = nc - 1;
   while (a < b) {
-    int64_t mid = a + (b - a) / 2;
-    if (test(s, md, in, mid * md->g)) b = mid;
+    int mid = a + (b - a) / 2;
+    if (test(s, md, in, cand[mid])) b = mid;
     else a = mid + 1;
   }
-  return a * md->g;
+  return cand[a];
 }
 
 static int64_t minm(const oset* s, const omodel* md, const unsigned char* in, int64_t lo, int64_t hi, int linear) {
@@ -400,7 +421,7 @@ static int allocate_one(const oset* s, const omodel* md, int policy, int act, in
         unsigned char in[ONMAX];
         union_of(&a, &b, in, n);
         int64_t lo = a.m > b.m ? a.m : b.m;
-        int64_t hi = a.m + b.m - md->g;
+        int64_t hi = a.m + b.m - 1;
         tests++;
         if (minm(s, md, in, lo, hi, linear) == 0) act_pair[i][j] = act_pair[j][i] = 1;
       }
@@ -430,7 +451,7 @@ static int allocate_one(const oset* s, const omodel* md, int policy, int act, in
         const opart* Q = &list[elig[k]];
         union_of(&list[p1], Q, in, n);
         int64_t lo = list[p1].m > Q->m ? list[p1].m : Q->m;
-        int64_t hi = list[p1].m + Q->m - md->g;
+        int64_t hi = list[p1].m + Q->m - 1;
         int64_t m3 = minm(s, md, in, lo, hi, linear);
         tests++;
         if (m3 > 0 && (best < 0 || m3 < best_m)) { best = elig[k]; best_m = m3; }
@@ -463,7 +484,7 @@ static int allocate_one(const oset* s, const omodel* md, int policy, int act, in
         const opart* Q = &list[elig[k]];
         union_of(&list[p1], Q, in, n);
         int64_t lo = list[p1].m > Q->m ? list[p1].m : Q->m;
-        int64_t hi = list[p1].m + Q->m - md->g;
+        int64_t hi = list[p1].m + Q->m - 1;
         int64_t m3 = minm(s, md, in, lo, hi, linear);
         tests++;
         if (m3 > 0) {
@@ -544,7 +565,7 @@ static void rgs_leaf(rgs_walk* w) {
     W += w->W_sub[mask[b]];
   }
   int64_t empty = w->kmin > nb ? (int64_t)(w->kmin - nb) : 0;
-  if (sm + empty * w->md->g > w->md->M) return;
+  if (sm + empty * smallest_size(w->md) > w->md->M) return;
   if (key_less(W, sm, w->rgs, w->best, n)) {
     w->best->found = 1;
     w->best->W = W;
@@ -577,7 +598,7 @@ static int search_rgs(const oset* s, const omodel* md, int kmin, int kmax, obest
   memset(best, 0, sizeof *best);
   if (n == 0) {
     /* no tasks: the empty partition, realisable iff kmin parts fit */
-    int64_t need = (int64_t)kmin * md->g;
+    int64_t need = (int64_t)kmin * smallest_size(md);
     if (need <= md->M) { best->found = 1; best->nb = 0; }
     return O_OK;
   }
@@ -607,8 +628,9 @@ static int search_rgs(const oset* s, const omodel* md, int kmin, int kmax, obest
 }
 
 /* Optimum by brute force: every composition of M/g into k parts (k in
- * [kmin, kmax]) times every map of tasks to parts; a candidate is feasible
- * iff every non-empty part passes the test at its size. */
+ * [kmin, kmax]; with a size list: every k admissible sizes of sum <= M)
+ * times every map of tasks to parts; a candidate is feasible iff every
+ * non-empty part passes the test at its size. */
 typedef struct {
   const oset* s;
   const omodel* md;
@@ -632,7 +654,7 @@ static void explicit_candidates(explicit_walk* w) {
     for (int p = 0; p < k && feasible; p++) {
       int any = 0;
       for (int i = 0; i < n; i++) { in[i] = map[i] == p; any |= in[i]; }
-      if (any && !test(s, w->md, in, w->parts[p] * w->md->g)) feasible = 0;
+      if (any && !test(s, w->md, in, w->parts[p])) feasible = 0;
     }
     if (!feasible) continue;
     /* induced set partition, blocks relabelled by first occurrence */
@@ -662,15 +684,29 @@ static void explicit_candidates(explicit_walk* w) {
   }
 }
 
+/* parts in SMs; `left` in units of g (exact sums) */
 static void compositions(explicit_walk* w, int part, int64_t left) {
   if (part == w->k - 1) {
-    w->parts[part] = left;
+    w->parts[part] = left * w->md->g;
     explicit_candidates(w);
     return;
   }
   for (int64_t v = 1; v <= left - (w->k - 1 - part); v++) {
-    w->parts[part] = v;
+    w->parts[part] = v * w->md->g;
     compositions(w, part + 1, left - v);
+  }
+}
+
+/* with a size list: every admissible size for each part, sum <= M (`left`
+ * in SMs) */
+static void admissible_splits(explicit_walk* w, int part, int64_t left) {
+  const int64_t zmin = smallest_size(w->md);
+  for (int64_t k = 0; k < w->md->nsizes; k++) {
+    const int64_t v = w->md->sizes[k];
+    if (v + (int64_t)(w->k - 1 - part) * zmin > left) break;
+    w->parts[part] = v;
+    if (part == w->k - 1) explicit_candidates(w);
+    else admissible_splits(w, part + 1, left - v);
   }
 }
 
@@ -687,7 +723,8 @@ static int64_t search_explicit(const oset* s, const omodel* md, int kmin, int km
   for (int k = kmin; k <= kmax; k++) {
     if (k > Mu) break;
     w.k = k;
-    compositions(&w, 0, Mu);
+    if (md->nsizes == 0) compositions(&w, 0, Mu);
+    else admissible_splits(&w, 0, md->M);
   }
   return w.candidates;
 }
@@ -697,6 +734,11 @@ static int64_t search_explicit(const oset* s, const omodel* md, int kmin, int km
 static int valid_model(const omodel* md) {
   if (md->g < 1 || md->M < 1 || md->M > 1024 || md->M % md->g != 0) return 0;
   if (md->sched != S_DM && md->sched != S_EDF) return 0;
+  if (md->nsizes < 0 || md->nsizes > 1024 || (md->nsizes > 0 && !md->sizes)) return 0;
+  for (int64_t k = 0; k < md->nsizes; k++) {
+    const int64_t z = md->sizes[k];
+    if (z < md->g || z > md->M || z % md->g != 0 || (k > 0 && z <= md->sizes[k - 1])) return 0;
+  }
   if (md->kc < 1000 || md->kc > 16000 || md->km < 1000 || md->km > 16000) return 0;
   return 1;
 }
@@ -747,7 +789,7 @@ int orc_wcet_tables(int64_t nsets, const int64_t* set_off, const int64_t* A, con
 int orc_rta(int n, const int64_t* T, const int64_t* D, const int64_t* A, const int64_t* B, const uint8_t* type,
             const uint8_t* in_mask, int64_t m, int64_t kc, int64_t km, int64_t* R) {
   oset s = {n, T, D, A, B, NULL, type};
-  omodel md = {1024, 1, kc, km, S_DM};
+  omodel md = {1024, 1, kc, km, S_DM, NULL, 0};
   unsigned char in[ONMAX];
   for (int i = 0; i < n; i++) in[i] = in_mask[i] ? 1 : 0;
   return rta(&s, &md, in, m, R);
@@ -757,7 +799,7 @@ int orc_rta(int n, const int64_t* T, const int64_t* D, const int64_t* A, const i
 int orc_edf(int n, const int64_t* T, const int64_t* D, const int64_t* A, const int64_t* B, const uint8_t* type,
             const uint8_t* in_mask, int64_t m, int64_t kc, int64_t km) {
   oset s = {n, T, D, A, B, NULL, type};
-  omodel md = {1024, 1, kc, km, S_EDF};
+  omodel md = {1024, 1, kc, km, S_EDF, NULL, 0};
   unsigned char in[ONMAX];
   for (int i = 0; i < n; i++) in[i] = in_mask[i] ? 1 : 0;
   return edf(&s, &md, in, m);
@@ -765,9 +807,9 @@ int orc_edf(int n, const int64_t* T, const int64_t* D, const int64_t* A, const i
 
 int orc_minm(int n, const int64_t* T, const int64_t* D, const int64_t* A, const int64_t* B, const uint8_t* type,
              const uint8_t* in_mask, int64_t lo, int64_t hi, int64_t g, int64_t kc, int64_t km, int64_t sched,
-             int linear, int64_t* out) {
+             const int32_t* sizes, int64_t nsizes, int linear, int64_t* out) {
   oset s = {n, T, D, A, B, NULL, type};
-  omodel md = {hi, g, kc, km, sched};
+  omodel md = {hi, g, kc, km, sched, sizes, nsizes};
   unsigned char in[ONMAX];
   for (int i = 0; i < n; i++) in[i] = in_mask[i] ? 1 : 0;
   *out = minm(&s, &md, in, lo, hi, linear);
@@ -778,7 +820,7 @@ int orc_workload(int n, const int64_t* u, const uint8_t* type, const uint8_t* in
                  int64_t* out) {
   int64_t zeros[ONMAX] = {0};
   oset s = {n, zeros, zeros, zeros, zeros, u, type};
-  omodel md = {1024, 1, kc, km, S_DM};
+  omodel md = {1024, 1, kc, km, S_DM, NULL, 0};
   unsigned char in[ONMAX];
   for (int i = 0; i < n; i++) in[i] = in_mask[i] ? 1 : 0;
   *out = workload(&s, &md, in);
@@ -787,16 +829,16 @@ int orc_workload(int n, const int64_t* u, const uint8_t* type, const uint8_t* in
 
 int orc_lemma1_rejects(int n, const int64_t* T, const int64_t* A, const int64_t* B, int64_t M) {
   oset s = {n, T, T, A, B, NULL, NULL};
-  omodel md = {M, 1, 1000, 1000, S_DM};
+  omodel md = {M, 1, 1000, 1000, S_DM, NULL, 0};
   return lemma1_rejects(&s, &md);
 }
 
 int orc_test_schedulable(int64_t nsets, const int64_t* set_off, const int64_t* T, const int64_t* D, const int64_t* A,
                          const int64_t* B, const uint8_t* type, int64_t M, int64_t g, int64_t kc, int64_t km,
-                         int64_t sched, int64_t ncands, const int64_t* cand_set, const uint8_t* part_of_task,
-                         int64_t map_stride, int64_t kparts, const int32_t* size_of_part, uint8_t* verdict,
-                         int64_t* R) {
-  omodel md = {M, g, kc, km, sched};
+                         int64_t sched, const int32_t* sizes, int64_t nsizes, int64_t ncands,
+                         const int64_t* cand_set, const uint8_t* part_of_task, int64_t map_stride, int64_t kparts,
+                         const int32_t* size_of_part, uint8_t* verdict, int64_t* R) {
+  omodel md = {M, g, kc, km, sched, sizes, nsizes};
   if (!valid_model(&md) || kparts < 1 || kparts > 255) return O_ERR_RANGE;
   for (int64_t c = 0; c < ncands; c++) {
     int64_t si = cand_set[c];
@@ -807,7 +849,7 @@ int orc_test_schedulable(int64_t nsets, const int64_t* set_off, const int64_t* T
     const int32_t* size = size_of_part + c * kparts;
     int64_t total = 0;
     for (int64_t p = 0; p < kparts; p++) {
-      if (size[p] < 0 || size[p] > M || size[p] % g != 0) return O_ERR_RANGE;
+      if (size[p] != 0 && !admissible(&md, size[p])) return O_ERR_RANGE;
       total += size[p];
     }
     for (int i = 0; i < s.n; i++)
@@ -891,10 +933,10 @@ static int run_threads(void* (*fn)(void*), void* jobs, size_t job_size, int nth)
 
 int orc_allocate(int64_t nsets, const int64_t* set_off, const int64_t* T, const int64_t* D, const int64_t* A,
                  const int64_t* B, const int64_t* u, const uint8_t* type, int64_t M, int64_t g, int64_t kc,
-                 int64_t km, int64_t sched, int policy, int act, int linear, uint8_t* verdict, uint8_t* reason,
-                 int32_t* n_parts, int32_t* Pi, int64_t* W, int32_t* n_tests, uint8_t* part_of_task,
-                 int16_t* size_of_part, int nthreads) {
-  omodel md = {M, g, kc, km, sched};
+                 int64_t km, int64_t sched, const int32_t* sizes, int64_t nsizes, int policy, int act, int linear,
+                 uint8_t* verdict, uint8_t* reason, int32_t* n_parts, int32_t* Pi, int64_t* W, int32_t* n_tests,
+                 uint8_t* part_of_task, int16_t* size_of_part, int nthreads) {
+  omodel md = {M, g, kc, km, sched, sizes, nsizes};
   if (!valid_model(&md)) return O_ERR_RANGE;
   if (policy < P_SMS || policy > P_ONE_GPU) return O_ERR_ARG;
   int nth = nthreads < 1 ? 1 : (nthreads > 256 ? 256 : nthreads);
@@ -960,7 +1002,7 @@ static void* best_worker(void* arg) {
     j->sum_minm[si] = best.found ? (int32_t)best.sum_minm : 0;
     j->n_blocks[si] = best.found ? best.nb : 0;
     int64_t empty = (best.found && j->kmin > best.nb) ? (int64_t)(j->kmin - best.nb) : 0;
-    j->spare[si] = best.found ? (int32_t)(j->md.M - best.sum_minm - empty * j->md.g) : 0;
+    j->spare[si] = best.found ? (int32_t)(j->md.M - best.sum_minm - empty * smallest_size(&j->md)) : 0;
     for (int i = 0; i < s.n && i < ONMAX; i++) j->rgs[o + i] = best.found ? best.rgs[i] : 255;
     for (int b = 0; b < j->kmax; b++)
       j->minm_block[si * j->kmax + b] = (int16_t)((best.found && b < best.nb) ? best.minm_block[b] : 0);
@@ -970,10 +1012,10 @@ static void* best_worker(void* arg) {
 
 static int search_batch(int explicit_form, int64_t nsets, const int64_t* set_off, const int64_t* T, const int64_t* D,
                         const int64_t* A, const int64_t* B, const int64_t* u, const uint8_t* type, int64_t M,
-                        int64_t g, int64_t kc, int64_t km, int64_t sched, int kmin, int kmax, uint8_t* feasible,
-                        int64_t* W, int32_t* sum_minm, int32_t* n_blocks, int32_t* spare, uint8_t* rgs,
-                        int16_t* minm_block, int nthreads, int64_t* candidates) {
-  omodel md = {M, g, kc, km, sched};
+                        int64_t g, int64_t kc, int64_t km, int64_t sched, const int32_t* sizes, int64_t nsizes,
+                        int kmin, int kmax, uint8_t* feasible, int64_t* W, int32_t* sum_minm, int32_t* n_blocks,
+                        int32_t* spare, uint8_t* rgs, int16_t* minm_block, int nthreads, int64_t* candidates) {
+  omodel md = {M, g, kc, km, sched, sizes, nsizes};
   if (!valid_model(&md)) return O_ERR_RANGE;
   if (kmin < 1 || kmax < kmin || kmax > 8) return O_ERR_RANGE;
   int nth = nthreads < 1 ? 1 : (nthreads > 256 ? 256 : nthreads);
@@ -1011,19 +1053,20 @@ static int search_batch(int explicit_form, int64_t nsets, const int64_t* set_off
 
 int orc_search_best(int64_t nsets, const int64_t* set_off, const int64_t* T, const int64_t* D, const int64_t* A,
                     const int64_t* B, const int64_t* u, const uint8_t* type, int64_t M, int64_t g, int64_t kc,
-                    int64_t km, int64_t sched, int kmin, int kmax, uint8_t* feasible, int64_t* W, int32_t* sum_minm,
-                    int32_t* n_blocks, int32_t* spare, uint8_t* rgs, int16_t* minm_block, int nthreads) {
-  return search_batch(0, nsets, set_off, T, D, A, B, u, type, M, g, kc, km, sched, kmin, kmax, feasible, W,
-                      sum_minm, n_blocks, spare, rgs, minm_block, nthreads, NULL);
+                    int64_t km, int64_t sched, const int32_t* sizes, int64_t nsizes, int kmin, int kmax,
+                    uint8_t* feasible, int64_t* W, int32_t* sum_minm, int32_t* n_blocks, int32_t* spare, uint8_t* rgs,
+                    int16_t* minm_block, int nthreads) {
+  return search_batch(0, nsets, set_off, T, D, A, B, u, type, M, g, kc, km, sched, sizes, nsizes, kmin, kmax,
+                      feasible, W, sum_minm, n_blocks, spare, rgs, minm_block, nthreads, NULL);
 }
 
 int orc_search_explicit(int64_t nsets, const int64_t* set_off, const int64_t* T, const int64_t* D, const int64_t* A,
                         const int64_t* B, const int64_t* u, const uint8_t* type, int64_t M, int64_t g, int64_t kc,
-                        int64_t km, int64_t sched, int kmin, int kmax, uint8_t* feasible, int64_t* W,
-                        int32_t* sum_minm, int32_t* n_blocks, int32_t* spare, uint8_t* rgs, int16_t* minm_block,
-                        int nthreads, int64_t* candidates) {
-  return search_batch(1, nsets, set_off, T, D, A, B, u, type, M, g, kc, km, sched, kmin, kmax, feasible, W,
-                      sum_minm, n_blocks, spare, rgs, minm_block, nthreads, candidates);
+                        int64_t km, int64_t sched, const int32_t* sizes, int64_t nsizes, int kmin, int kmax,
+                        uint8_t* feasible, int64_t* W, int32_t* sum_minm, int32_t* n_blocks, int32_t* spare,
+                        uint8_t* rgs, int16_t* minm_block, int nthreads, int64_t* candidates) {
+  return search_batch(1, nsets, set_off, T, D, A, B, u, type, M, g, kc, km, sched, sizes, nsizes, kmin, kmax,
+                      feasible, W, sum_minm, n_blocks, spare, rgs, minm_block, nthreads, candidates);
 }
 
 /* ------------------------------------------------------- serving operations
@@ -1074,7 +1117,7 @@ int orc_serve_admit(int n, const int64_t* T, const int64_t* D, const int64_t* A,
                     uint8_t* verdict, uint8_t* reason, uint8_t* part_out, int16_t* size_out, int32_t* n_parts,
                     int32_t* Pi, int64_t* W) {
   oset s = {n, T, D, A, B, u, type};
-  omodel md = {M, g, kc, km, S_DM};
+  omodel md = {M, g, kc, km, S_DM, NULL, 0};
   if (!valid_model(&md) || !valid_set(&s)) return O_ERR_RANGE;
   ores r;
   int st = allocate_one(&s, &md, policy, act, 1, &r, part_out, size_out);
@@ -1092,7 +1135,7 @@ int orc_serve_add(int n, const int64_t* T, const int64_t* D, const int64_t* A, c
                   int64_t g, int64_t kc, int64_t km, int policy, int act, uint8_t* verdict, uint8_t* reason,
                   uint8_t* path, uint8_t* part_out, int16_t* size_out, int32_t* n_parts, int32_t* Pi, int64_t* W) {
   oset s = {n + 1, T, D, A, B, u, type};
-  omodel md = {M, g, kc, km, S_DM};
+  omodel md = {M, g, kc, km, S_DM, NULL, 0};
   if (n + 1 > ONMAX || !valid_model(&md) || !valid_set(&s)) return O_ERR_RANGE;
   const int nw = n;  /* index of the new task */
   int np = np_in;
@@ -1113,7 +1156,7 @@ int orc_serve_add(int n, const int64_t* T, const int64_t* D, const int64_t* A, c
   /* grow a partition into the spare SMs */
   for (int p = 0; p < np && *path == PATH_NONE && spare >= g; p++) {
     for (int i = 0; i <= n; i++) in[i] = (i == nw) || (i < n && part_in[i] == p);
-    int64_t m = minm_linear(&s, &md, in, size_in[p] + g, size_in[p] + spare);
+    int64_t m = minm_linear(&s, &md, in, size_in[p] + 1, size_in[p] + spare);
     if (m) { part_out[nw] = (uint8_t)p; size_out[p] = (int16_t)m; *path = PATH_GROW; }
   }
   /* a new partition of the task's Lemma 2 size */
@@ -1158,7 +1201,7 @@ int orc_serve_remove(int n, const int64_t* T, const int64_t* D, const int64_t* A
                      int np_in, int index, int64_t M, int64_t g, int64_t kc, int64_t km, int64_t* T_out,
                      int64_t* D_out, int64_t* A_out, int64_t* B_out, int64_t* u_out, uint8_t* type_out,
                      uint8_t* part_out, int16_t* size_out, int32_t* n_parts, int32_t* Pi, int64_t* W) {
-  omodel md = {M, g, kc, km, S_DM};
+  omodel md = {M, g, kc, km, S_DM, NULL, 0};
   if (index < 0 || index >= n || !valid_model(&md)) return O_ERR_RANGE;
   int k = 0;
   for (int i = 0; i < n; i++) {

@@ -100,11 +100,14 @@ def conflict_k(types, S, i, kc, km):
     return 1000
 
 
-def heuristic(n, u, M, g, single_size, test_min, policy="SMS", act=False, W=None):
+def heuristic(n, u, M, g, single_size, test_min, policy="SMS", act=False, W=None, gap=None):
     """Alg. 1-3 over frozensets.  single_size(i) -> Lemma 2 size or 0;
     test_min(S, lo, hi) -> smallest passing size in [lo, hi] or 0;
-    W(S) -> inflated workload (Def. 4 reading).  Returns (ok, parts, tests)
-    with parts a dict frozenset -> size; Lemma 1 is left to the caller."""
+    W(S) -> inflated workload (Def. 4 reading).  A merge of sizes a and b is
+    sized in [max(a, b), a + b - gap] (gap = g by default).  Returns
+    (ok, parts, tests) with parts a dict frozenset -> size; Lemma 1 is left
+    to the caller."""
+    gap = g if gap is None else gap
     parts = {}
     for i in range(n):
         z = single_size(i)
@@ -117,7 +120,7 @@ def heuristic(n, u, M, g, single_size, test_min, policy="SMS", act=False, W=None
         for i, j in itertools.combinations(range(n), 2):
             a, b = parts[frozenset([i])], parts[frozenset([j])]
             tests += 1
-            if test_min(frozenset([i, j]), max(a, b), a + b - g) == 0:
+            if test_min(frozenset([i, j]), max(a, b), a + b - gap) == 0:
                 act_pairs.add(frozenset([i, j]))
     failed = set()  # frozenset({P, Q})
 
@@ -141,7 +144,7 @@ def heuristic(n, u, M, g, single_size, test_min, policy="SMS", act=False, W=None
             results = []
             for pos, Q in enumerate(elig):
                 tests += 1
-                m3 = test_min(P | Q, max(parts[P], parts[Q]), parts[P] + parts[Q] - g)
+                m3 = test_min(P | Q, max(parts[P], parts[Q]), parts[P] + parts[Q] - gap)
                 if m3:
                     results.append((m3, pos, Q))
             if results:
@@ -155,7 +158,7 @@ def heuristic(n, u, M, g, single_size, test_min, policy="SMS", act=False, W=None
             ranked = sorted(enumerate(elig), key=lambda pq: (W(P | pq[1]), pq[0]))
             for _, Q in ranked:
                 tests += 1
-                m3 = test_min(P | Q, max(parts[P], parts[Q]), parts[P] + parts[Q] - g)
+                m3 = test_min(P | Q, max(parts[P], parts[Q]), parts[P] + parts[Q] - gap)
                 if m3:
                     del parts[P], parts[Q]
                     parts[P | Q] = m3
@@ -184,20 +187,26 @@ def rgs_of(labels):
     return tuple(out)
 
 
-def exhaustive_bruteforce(n, M, g, kmin, kmax, passes, minsize, W):
+def exhaustive_bruteforce(n, M, g, kmin, kmax, passes, minsize, W, sizes=None):
     """passes(S, m) -> bool; minsize(S) -> minimal size in [g, M] or 0;
-    W(S) -> workload.  Returns None or (W, sum_minm, rgs)."""
+    W(S) -> workload.  Splits: compositions of M/g into k parts, or with an
+    admissible size list every k sizes from it of sum <= M.  Returns None
+    or (W, sum_minm, rgs)."""
     best = None
     Mu = M // g
     for k in range(kmin, kmax + 1):
         if k > Mu:
             break
-        for comp in compositions(Mu, k):
+        if sizes:
+            splits = [c for c in itertools.product(sizes, repeat=k) if sum(c) <= M]
+        else:
+            splits = [tuple(x * g for x in c) for c in compositions(Mu, k)]
+        for comp in splits:
             for labels in itertools.product(range(k), repeat=n):
                 ok = True
                 for p in range(k):
                     S = frozenset(i for i in range(n) if labels[i] == p)
-                    if S and not passes(S, comp[p] * g):
+                    if S and not passes(S, comp[p]):
                         ok = False
                         break
                 if not ok:

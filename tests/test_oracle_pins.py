@@ -582,6 +582,122 @@ def test_heuristic_success_implies_exhaustive_feasible_and_not_better():
     assert checked > 20
 
 
+# ------------------------------------------- admissible partition sizes (§2)
+
+def test_sizes_listing_every_multiple_of_g_changes_nothing():
+    s = gen_tasksets(seed=70, nsets=60, n_min=2, n_max=10, U_lo_ppm=500000, U_hi_ppm=6000000, deadline_pm=750,
+                     T_lo=1000, T_hi=100000)
+    M, g = 24, 2
+    every = list(range(g, M + 1, g))
+    for policy, act in (("SMS", False), ("BF", True)):
+        a = oracle.allocate(s, M, g, KC, KM, policy=policy, act=act)
+        b = oracle.allocate(s, M, g, KC, KM, policy=policy, act=act, sizes=every)
+        for k in a:
+            assert np.array_equal(a[k], b[k]), k
+    small = gen_tasksets(seed=71, nsets=20, n_min=1, n_max=6, U_lo_ppm=500000, U_hi_ppm=3000000, deadline_pm=750,
+                         T_lo=1000, T_hi=100000)
+    a = oracle.search_best(small, M, g, KC, KM, 1, 3)
+    b = oracle.search_best(small, M, g, KC, KM, 1, 3, sizes=every)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_sizes_singleton_is_next_admissible_lemma2_size():
+    rng = random.Random(72)
+    sizes = [3, 4, 7, 12, 20, 33]
+    for _ in range(400):
+        C1 = rng.randrange(1, 10**6)
+        alpha = rng.randrange(0, 1001)
+        T = rng.randrange(1000, 10**6)
+        D = rng.randrange(max(1, T // 2), T + 1)
+        A, B = C1 * (1000 - alpha), C1 * alpha
+        m = oracle.minm(np.array([T]), np.array([D]), np.array([A]), np.array([B]), np.zeros(1, np.uint8),
+                        np.ones(1, np.uint8), 1, 40, 1, KC, KM, sizes=sizes)
+        plain = next((z for z in range(1, 41) if refs.wcet_alpha(C1, alpha, 1000, z) <= D), 0)
+        want = next((z for z in sizes if z >= plain), 0) if plain else 0
+        assert m == want, (C1, alpha, T, D)
+
+
+@pytest.mark.parametrize("policy,act", [("SMS", False), ("BF", True)])
+def test_sizes_heuristic_matches_restatement(policy, act):
+    """Alg. 1-3 with partition sizes from a GPC-like list: the restatement
+    (merges sized in [max(a, b), a + b - 1] over the list) agrees."""
+    M, g, sizes = 16, 1, [2, 3, 5, 8, 11, 16]
+    s = gen_tasksets(seed=73, nsets=40, n_min=3, n_max=8, U_lo_ppm=1000000, U_hi_ppm=12000000, deadline_pm=750,
+                     T_lo=50, T_hi=4000, T_dist="LIST", mode="PAPER")
+    r = oracle.allocate(s, M, g, KC, KM, policy=policy, act=act, sizes=sizes)
+    merges = 0
+    for si in range(40):
+        v, o, n = _set_view(s, si)
+        if oracle.lemma1_rejects(v["T"], v["A"], v["B"], M):
+            assert r["reason"][si] == oracle.REASON["LEMMA1"]
+            continue
+
+        def test_min(S, lo, hi):
+            mask = np.array([i in S for i in range(n)], np.uint8)
+            return oracle.minm(v["T"], v["D"], v["A"], v["B"], v["type"], mask, lo, hi, g, KC, KM, sizes=sizes)
+
+        def single(i):
+            return test_min({i}, g, M)
+
+        def W(S):
+            return sum(refs.conflict_k(v["type"], S, i, KC, KM) * int(v["u_ppm"][i]) for i in S)
+
+        status, parts, tests = refs.heuristic(n, [int(x) for x in v["u_ppm"]], M, g, single, test_min,
+                                              policy=policy, act=act, W=W, gap=1)
+        assert oracle.REASON[status] == r["reason"][si], si
+        assert tests == r["n_tests"][si], si
+        if status == "LEMMA2":
+            continue
+        merges += tests
+        got, zs = _partitions_from(r, si, o, n)
+        assert sorted((sorted(P), z) for P, z in parts.items()) == sorted((sorted(got[p]), zs[p]) for p in got)
+        assert all(z in sizes for z in zs)
+    assert merges > 20
+
+
+def test_sizes_exhaustive_matches_bruteforce():
+    rng = random.Random(74)
+    for trial in range(20):
+        n = rng.randrange(1, 5)
+        M = rng.choice([6, 8, 10])
+        sizes = sorted(rng.sample(range(1, M + 1), rng.randrange(1, min(M, 4) + 1)))
+        kmin = rng.randrange(1, 3)
+        kmax = rng.randrange(kmin, 4)
+        s = gen_tasksets(seed=200 + trial, nsets=1, n_min=n, n_max=n, U_lo_ppm=300000, U_hi_ppm=2500000,
+                         deadline_pm=750, T_lo=1000, T_hi=100000)
+        a = oracle.search_best(s, M, 1, KC, KM, kmin, kmax, sizes=sizes)
+        b = oracle.search_best(s, M, 1, KC, KM, kmin, kmax, explicit=True, sizes=sizes)
+        for k in ("feasible", "W", "sum_minm", "n_blocks", "spare", "rgs", "minm_block"):
+            assert np.array_equal(a[k], b[k]), (trial, k)
+        v, o, _ = _set_view(s, 0)
+
+        def passes(S, m):
+            mask = np.array([i in S for i in range(n)], np.uint8)
+            return oracle.rta(v["T"], v["D"], v["A"], v["B"], v["type"], mask, m, KC, KM)[0] == 1
+
+        def minsize(S):
+            return next((z for z in sizes if passes(S, z)), 0)
+
+        def W(S):
+            return sum(refs.conflict_k(v["type"], S, i, KC, KM) * int(v["u_ppm"][i]) for i in S)
+
+        best = refs.exhaustive_bruteforce(n, M, 1, kmin, kmax, passes, minsize, W, sizes=sizes)
+        assert bool(a["feasible"][0]) == (best is not None), trial
+        if best is not None:
+            assert (a["W"][0], a["sum_minm"][0], tuple(a["rgs"][:n])) == best
+
+
+def test_sizes_candidate_part_must_be_admissible():
+    s = gen_tasksets(seed=75, nsets=2, n_min=3, n_max=3)
+    cset = np.array([0, 1], np.int64)
+    cmap = np.zeros(6, np.uint8)
+    v, _ = oracle.test_schedulable(s, 16, 1, KC, KM, cset, cmap, 3, 1, np.array([8, 8], np.int32), sizes=[4, 8, 16])
+    assert len(v) == 2
+    with pytest.raises(RuntimeError):
+        oracle.test_schedulable(s, 16, 1, KC, KM, cset, cmap, 3, 1, np.array([8, 6], np.int32), sizes=[4, 8, 16])
+
+
 def test_rgs_and_composition_counts():
     """Stirling numbers of the second kind (recurrence) and binomials."""
     def stirling(n, k):
