@@ -168,10 +168,10 @@ def oracle_step(sets, md, workload, policy, act, threads):
     if workload == "exhaustive":
         wp = W.WORKLOADS["exhaustive"]
         oracle.search_best(sets, md["M"], md["g"], md["k_c_pm"], md["k_m_pm"], wp["kmin"], wp["kmax"],
-                           nthreads=threads, sched=md.get("sched", "DM"))
+                           nthreads=threads, sched=md.get("sched", "DM"), sizes=md.get("sizes"))
     else:
         oracle.allocate(sets, md["M"], md["g"], md["k_c_pm"], md["k_m_pm"], policy=policy, act=act,
-                        nthreads=threads, sched=md.get("sched", "DM"))
+                        nthreads=threads, sched=md.get("sched", "DM"), sizes=md.get("sizes"))
 
 
 def oracle_sample(sets, md, workload, policy, act, threads, target_s):
@@ -331,6 +331,8 @@ def run_reference(args):
         return 0
     sets, md = build_workload(args.workload, 0, args.nsets)
     md["sched"] = args.sched.upper()
+    if args.sizes:
+        md["sizes"] = [int(x) for x in args.sizes.split(",")]
     policy, act = policy_of(args.workload)
     threads = os.cpu_count() or 1
     nsets_all = len(sets["set_off"]) - 1
@@ -373,6 +375,8 @@ def run_gpu(args):
 
     sets, md = build_workload(args.workload, rank, args.nsets)
     md["sched"] = args.sched.upper()
+    if args.sizes:
+        md["sizes"] = [int(x) for x in args.sizes.split(",")]
     policy, act = policy_of(args.workload)
     nsets = len(sets["set_off"]) - 1
     ntasks = int(sets["set_off"][-1])
@@ -597,7 +601,7 @@ def run_gpu(args):
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": DESCR.get(args.workload, args.workload), "nsets_per_gpu": nsets,
                        "tasks_per_gpu": ntasks, "M": md["M"], "g": md["g"], "policy": policy, "act": act,
-                       "sched": md["sched"], "merge_search": args.merge,
+                       "sched": md["sched"], "merge_search": args.merge, "sizes": md.get("sizes"),
                        "l2": "flushed between timed steps (512 MB write, then 256 MB read); inputs 109 MB < 129 MB L2",
                        "parallelism": f"{world} independent shard(s)", "launch": "persistent + CUDA graph",
                        "launch_shape": "autotuned" if autotune else
@@ -625,6 +629,8 @@ def main():
     ap.add_argument("--impl", choices=["gpa", "reference"], default="gpa")
     ap.add_argument("--workload", choices=sorted(DESCR), default="batch")
     ap.add_argument("--nsets", type=int, default=0, help="override the workload's set count (profiling)")
+    ap.add_argument("--sizes", default="",
+                    help="comma-separated admissible partition sizes (default: every multiple of g)")
     ap.add_argument("--merge", choices=["linear", "binary"], default="linear",
                     help="Alg. 2 size search of a merge: linear scan (default) or the binary search of §5.2")
     ap.add_argument("--sched", choices=["dm", "edf"], default="dm",

@@ -192,7 +192,14 @@ typedef struct {
   int32_t k_c_pm;  /* conflict factor of compute-intensive tasks, per mille (§7.1: 1200) */
   int32_t k_m_pm;  /* conflict factor of memory-intensive tasks, per mille (§7.1: 2300) */
   int32_t sched;   /* per-partition policy: GPA_SCHED_DM or GPA_SCHED_EDF (not in serving: DM only) */
-  int32_t reserved_;  /* 0 */
+  int32_t nsizes;  /* 0: every multiple of g in [g, M] is a partition size; else the length of `sizes` */
+  const int32_t* sizes; /* host array, strictly increasing multiples of g in [g, M]: the only admissible
+                           partition sizes (whole GPCs or MIG slices, §2).  Used by gpa_allocate
+                           (Lemma 2 sizes round up to the next listed size; a merge is sized over the
+                           listed sizes below the sum of the two), gpa_test_schedulable (a non-empty
+                           part's size must be listed) and gpa_search_best (blocks take listed sizes; an
+                           empty part counts the smallest).  1G uses M; serving and
+                           gpa_allocate_noalloc take no list (GPA_ERR_ARG). */
 } gpa_model;
 
 /* Host-side validation of a task batch and model against the bounds above

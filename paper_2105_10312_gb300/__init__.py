@@ -55,7 +55,18 @@ class Tasksets(ctypes.Structure):
 
 class Model(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int32), ("g", ctypes.c_int32), ("k_c_pm", ctypes.c_int32), ("k_m_pm", ctypes.c_int32),
-                ("sched", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
+                ("sched", ctypes.c_int32), ("nsizes", ctypes.c_int32), ("sizes", _vp)]
+
+
+def make_model(M, g, k_c_pm, k_m_pm, sched="DM", sizes=None):
+    """The gpa_model of the arguments; the size list (if any) is kept alive
+    on the returned structure."""
+    if sizes is None or len(sizes) == 0:
+        return Model(M, g, k_c_pm, k_m_pm, SCHED[sched], 0, None)
+    arr = np.ascontiguousarray(sizes, dtype=np.int32)
+    md = Model(M, g, k_c_pm, k_m_pm, SCHED[sched], len(arr), arr.ctypes.data)
+    md._keep = arr
+    return md
 
 
 class Candidates(ctypes.Structure):
@@ -265,9 +276,9 @@ class Context:
         return Cn, Cc
 
     def test_schedulable(self, sets, M, cand_set, part_of_task, size_of_part, map_stride, kparts, g=1,
-                         k_c_pm=1200, k_m_pm=2300, with_R=True, sched="DM"):
+                         k_c_pm=1200, k_m_pm=2300, with_R=True, sched="DM", sizes=None):
         ts, mem = make_tasksets(sets)
-        md = Model(M, g, k_c_pm, k_m_pm, SCHED[sched], 0)
+        md = make_model(M, g, k_c_pm, k_m_pm, sched, sizes)
         nc = _len(cand_set)
         cands = Candidates(nc, mem, int(map_stride), int(kparts), 0, _ptr(cand_set), _ptr(part_of_task),
                            _ptr(size_of_part))
@@ -295,9 +306,9 @@ class Context:
         }
 
     def allocate(self, sets, M, g=1, k_c_pm=1200, k_m_pm=2300, policy="SMS", act=False, linear=True, out=None,
-                 sched="DM"):
+                 sched="DM", sizes=None):
         ts, mem = make_tasksets(sets)
-        md = Model(M, g, k_c_pm, k_m_pm, SCHED[sched], 0)
+        md = make_model(M, g, k_c_pm, k_m_pm, sched, sizes)
         pr = Params(POLICY[policy], 1 if act else 0, 1 if linear else 0, 0)
         if out is None:
             out = self.alloc_result(sets)
@@ -322,9 +333,9 @@ class Context:
             "minm_block": _empty_like_mem(mem, nsets * kmax, np.int16, dev),
         }
 
-    def search_best(self, sets, M, g=1, k_c_pm=1200, k_m_pm=2300, kmin=1, kmax=4, out=None, sched="DM"):
+    def search_best(self, sets, M, g=1, k_c_pm=1200, k_m_pm=2300, kmin=1, kmax=4, out=None, sched="DM", sizes=None):
         ts, mem = make_tasksets(sets)
-        md = Model(M, g, k_c_pm, k_m_pm, SCHED[sched], 0)
+        md = make_model(M, g, k_c_pm, k_m_pm, sched, sizes)
         if out is None:
             out = self.best_result(sets, kmax)
         res = BestResult(mem, 0, _ptr(out["feasible"]), _ptr(out["W"]), _ptr(out["sum_minm"]),

@@ -181,31 +181,42 @@ __device__ __forceinline__ bool lane_test(const SetSmem& st, const unsigned int*
                                 : lane_rta(st, S, m, kc, km, md, ls, lane, err);
 }
 
-// Alg. 2 by one lane: the first size in lo, lo + g, ..., hi that passes.  A
+// The admissible sizes of the model.
+__device__ __forceinline__ Sizes sizes_of(const DevModel& md) {
+  return Sizes{(unsigned int)md.M, (unsigned int)md.g, md.zlist, md.zrank, md.nz};
+}
+
+// Alg. 2 by one lane: the first admissible size in [lo, hi] that passes.  A
 // range of up to three sizes is scanned; a longer one is bisected (§5.2),
 // which finds the same size because the test is monotone in m.
 __device__ unsigned int lane_minm(const SetSmem& st, const unsigned int* S, unsigned int lo, unsigned int hi,
-                                  unsigned int g, unsigned int kc, unsigned int km, int sched,
+                                  const Sizes& z, unsigned int kc, unsigned int km, int sched,
                                   const MagicDiv* __restrict__ mdiv, LaneScratch& ls, int lane, unsigned int* err) {
   if (lo > hi) return 0u;
-  if (hi - lo <= 2u * g) {
-    for (unsigned int m = lo; m <= hi; m += g)
+  hi = min(hi, z.M);
+  int a = z.below(lo);
+  const int e = z.below(hi + 1u);  // indices of the admissible sizes in [lo, hi]: a .. e - 1
+  if (e - a <= 3) {
+    for (int k = a; k < e; k++) {
+      const unsigned int m = z.at(k);
       if (lane_test(st, S, m, kc, km, sched, mdiv[m], ls, lane, err)) return m;
+    }
     return 0u;
   }
-  unsigned int a = lo / g, b = hi / g + 1u;  // b stands for "no size passes"
+  int b = e;  // e stands for "no size passes"
   while (a < b) {
-    const unsigned int mid = a + (b - a) / 2u;
-    if (lane_test(st, S, mid * g, kc, km, sched, mdiv[mid * g], ls, lane, err)) b = mid;
-    else a = mid + 1u;
+    const int mid = a + (b - a) / 2;
+    const unsigned int m = z.at(mid);
+    if (lane_test(st, S, m, kc, km, sched, mdiv[m], ls, lane, err)) b = mid;
+    else a = mid + 1;
   }
-  return a * g <= hi ? a * g : 0u;
+  return a < e ? z.at(a) : 0u;
 }
 
 // Sizes of the candidate merges of slot p1 with cand[c0 .. c1) into ls.res:
 // one lane per candidate when the merged set is small, then the warp for
 // the others.  Warp-uniform arguments.
-__device__ void size_candidates(MergeSmem& sm, int p1, int c0, int c1, unsigned int g, bool linear, unsigned int kc,
+__device__ void size_candidates(MergeSmem& sm, int p1, int c0, int c1, const Sizes& z, bool linear, unsigned int kc,
                                 unsigned int km, int sched, const MagicDiv* __restrict__ mdiv, unsigned int* err) {
   const int lane = threadIdx.x & 31;
   for (int b = c0; b < c1; b += 32) {
@@ -219,8 +230,9 @@ __device__ void size_candidates(MergeSmem& sm, int p1, int c0, int c1, unsigned 
         U[w] = sm.mask[p1][w] | sm.mask[e][w];
         cnt += __popc(U[w]);
       }
-      const unsigned int lo = max(sm.m[p1], sm.m[e]), hi = sm.m[p1] + sm.m[e] - g;
-      sm.ls.res[k] = cnt <= kLaneMax ? (unsigned short)lane_minm(sm.st, U, lo, hi, g, kc, km, sched, mdiv, sm.ls, lane, err)
+      // merged sizes: admissible, from the larger of the two up to below their sum
+      const unsigned int lo = max(sm.m[p1], sm.m[e]), hi = sm.m[p1] + sm.m[e] - 1u;
+      sm.ls.res[k] = cnt <= kLaneMax ? (unsigned short)lane_minm(sm.st, U, lo, hi, z, kc, km, sched, mdiv, sm.ls, lane, err)
                                      : kLaneNone;
     }
   }
@@ -231,8 +243,8 @@ __device__ void size_candidates(MergeSmem& sm, int p1, int c0, int c1, unsigned 
     unsigned int U[kWords];
 #pragma unroll
     for (int w = 0; w < kWords; w++) U[w] = sm.mask[p1][w] | sm.mask[e][w];
-    const unsigned int lo = max(sm.m[p1], sm.m[e]), hi = sm.m[p1] + sm.m[e] - g;
-    const unsigned int m3 = warp_minm(sm.st, U, lo, hi, g, linear, kc, km, sched, mdiv, sm.sc, err);
+    const unsigned int lo = max(sm.m[p1], sm.m[e]), hi = sm.m[p1] + sm.m[e] - 1u;
+    const unsigned int m3 = warp_minm(sm.st, U, lo, hi, z, linear, kc, km, sched, mdiv, sm.sc, err);
     __syncwarp();
     if (lane == 0) sm.ls.res[k] = (unsigned short)m3;
     __syncwarp();
@@ -310,8 +322,9 @@ __device__ void apply_merge(MergeSmem& sm, int a, int b, unsigned int m3, int ns
 __device__ void merge_set(MergeSmem& sm, long long s, long long o, int n, const DevModel& md, const gpa_params& p,
                           const AllocOut& out, const MagicDiv* mdiv, unsigned int* err) {
   const int lane = threadIdx.x & 31;
-  const unsigned kc = (unsigned)md.kc, km = (unsigned)md.km, g = (unsigned)md.g, M = (unsigned)md.M;
+  const unsigned kc = (unsigned)md.kc, km = (unsigned)md.km, M = (unsigned)md.M;
   const int sched = md.sched;
+  const Sizes z = sizes_of(md);
   const bool linear = p.linear_merge != 0;
 
   // Lemma 1: sum_i floor(10^6 C^n_i(1) / T_i) > 10^6 M rejects the set.
@@ -331,7 +344,7 @@ __device__ void merge_set(MergeSmem& sm, long long s, long long o, int n, const 
   for (int r = lane; r < kNmax; r += 32) {
     unsigned int mr = 0;
     if (r < n) {
-      mr = lemma2_size(sm.st.A[r], sm.st.B[r], sm.st.D[r], M, g);
+      mr = lemma2_size(sm.st.A[r], sm.st.B[r], sm.st.D[r], z);
       none = none || mr == 0u;
       pi += (int)mr;
       const bool mem = (sm.st.memmask[r >> 5] >> (r & 31)) & 1u;
@@ -375,8 +388,8 @@ __device__ void merge_set(MergeSmem& sm, long long s, long long o, int n, const 
           for (int w = 0; w < kWords; w++) S2[w] = 0u;
           S2[a >> 5] |= 1u << (a & 31);
           S2[b >> 5] |= 1u << (b & 31);
-          const unsigned int lo = max(sm.m[a], sm.m[b]), hi = sm.m[a] + sm.m[b] - g;
-          if (lane_minm(sm.st, S2, lo, hi, g, kc, km, sched, mdiv, sm.ls, lane, err) == 0u) {
+          const unsigned int lo = max(sm.m[a], sm.m[b]), hi = sm.m[a] + sm.m[b] - 1u;
+          if (lane_minm(sm.st, S2, lo, hi, z, kc, km, sched, mdiv, sm.ls, lane, err) == 0u) {
             atomicOr(&sm.act[a][b >> 5], 1u << (b & 31));
             atomicOr(&sm.act[b][a >> 5], 1u << (a & 31));
           }
@@ -422,7 +435,7 @@ __device__ void merge_set(MergeSmem& sm, long long s, long long o, int n, const 
         ne++;
       }
       __syncwarp();
-      size_candidates(sm, p1, 0, ne, g, linear, kc, km, sched, mdiv, err);
+      size_candidates(sm, p1, 0, ne, z, linear, kc, km, sched, mdiv, err);
       tests += ne;
       // smallest size, then earliest position: key = size << 8 | position
       unsigned int keyv = 0xFFFFFFFFu;
@@ -480,7 +493,7 @@ __device__ void merge_set(MergeSmem& sm, long long s, long long o, int n, const 
       // success (in order) is applied, every earlier failure is forbidden
       for (int c0 = 0; c0 < ne; c0 += 32) {
         const int c1 = min(ne, c0 + 32);
-        size_candidates(sm, p1, c0, c1, g, linear, kc, km, sched, mdiv, err);
+        size_candidates(sm, p1, c0, c1, z, linear, kc, km, sched, mdiv, err);
         const int k = c0 + lane;
         const unsigned int okb = __ballot_sync(kFull, k < c1 && sm.ls.res[k] != 0u);
         const int first = okb ? c0 + __ffs(okb) - 1 : c1;

@@ -43,6 +43,8 @@ struct gpa_ctx {
   gpa::Prof prof{};                          // timing events of direct (non-graph) calls
   const gpa::Prof* last_prof = nullptr;      // events of the last profiled call
   gpa::LaunchShape force_fast{0, 0, 0, 0};
+  std::vector<unsigned short> size_table;   // last admissible-size table copied to the device
+  void* size_table_ptr = nullptr;
   std::map<std::string, gpa::LaunchShape> tuned;
   std::map<std::string, CachedGraph> graphs;
   ServeState* serve = nullptr;

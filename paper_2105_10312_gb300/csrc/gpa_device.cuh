@@ -75,11 +75,37 @@ __device__ __forceinline__ bool task_valid(long long T, long long D, long long A
          uA + uB - 1ull < (1ull << 36) && ((unsigned long long)u >> 32) == 0ull && type <= 1u;
 }
 
-// Lemma 2 in closed form: smallest multiple of g in [g, M] with
-// C^n(m) <= D, i.e. 1000 (A + B m) <= 10^6 D m  <=>  A <= m (1000 D - B).
-// Returns 0 when no size <= M qualifies.
+// The admissible partition sizes of a model: every multiple of g in [g, M]
+// (list == nullptr), or a listed increasing subset of them (whole GPCs or
+// MIG slices, §2).  rank[m], m in [0, M + 1], counts the listed sizes < m.
+struct Sizes {
+  unsigned int M, g;
+  const unsigned short* list;
+  const unsigned short* rank;
+  int n;
+  // number of admissible sizes below m (m <= M + 1)
+  __device__ __forceinline__ int below(unsigned int m) const {
+    if (!list) return m == 0u ? 0 : (int)((m - 1u) / g);
+    return rank[m];
+  }
+  __device__ __forceinline__ int count() const { return list ? n : (int)(M / g); }
+  __device__ __forceinline__ unsigned int at(int k) const { return list ? (unsigned int)list[k] : (unsigned int)(k + 1) * g; }
+  // smallest admissible size >= m (1 <= m), 0 if none
+  __device__ __forceinline__ unsigned int next(unsigned int m) const {
+    if (m > M) return 0u;
+    const int k = below(m);
+    return k < count() ? at(k) : 0u;
+  }
+  __device__ __forceinline__ bool admissible(unsigned int m) const {
+    return m >= 1u && m <= M && below(m + 1u) - below(m) == 1 && (list || m % g == 0u);
+  }
+};
+
+// Lemma 2 in closed form: the smallest admissible size m with C^n(m) <= D,
+// i.e. 1000 (A + B m) <= 10^6 D m  <=>  A <= m (1000 D - B).  Returns 0 when
+// no admissible size qualifies.
 __device__ __forceinline__ unsigned int lemma2_size(unsigned long long A, unsigned long long B, unsigned long long D,
-                                                    unsigned int M, unsigned int g) {
+                                                    const Sizes& z) {
   long long den = (long long)(1000ull * D) - (long long)B;
   if (den < 0) return 0u;
   unsigned long long m1;
@@ -87,21 +113,22 @@ __device__ __forceinline__ unsigned int lemma2_size(unsigned long long A, unsign
   else if (den == 0) return 0u;
   else m1 = (A + (unsigned long long)den - 1ull) / (unsigned long long)den;
   if (m1 < 1ull) m1 = 1ull;
-  unsigned long long mg = (m1 + g - 1ull) / g * g;
-  return mg <= M ? (unsigned int)mg : 0u;
+  return m1 <= z.M ? z.next((unsigned int)m1) : 0u;
 }
 
 // The same size without 64-bit division: if A <= M (1000 D - B), the
 // quotient q = ceil(A / den) is at most M <= 1024, so a float estimate is
-// within one of it and two exact integer checks settle it.
+// within one of it and two exact integer checks settle it.  m_one is the
+// smallest admissible size.
 __device__ __forceinline__ unsigned int lemma2_size_fast(unsigned long long A, unsigned long long B,
-                                                         unsigned long long D, unsigned int M, unsigned int g) {
+                                                         unsigned long long D, const Sizes& z, unsigned int m_one) {
+  const unsigned int M = z.M;
   const long long den = (long long)(1000ull * D) - (long long)B;
   if (den < 0) return 0u;
-  if (A == 0ull) return g <= M ? g : 0u;
+  if (A == 0ull) return m_one;
   if (den == 0) return 0u;
   const unsigned long long ud = (unsigned long long)den;
-  if (A <= ud) return g <= M ? g : 0u;  // one SM already meets the deadline (the common case)
+  if (A <= ud) return m_one;  // one SM already meets the deadline (the common case)
   if (A > ud * M) return 0u;
   unsigned int q = (unsigned int)__fdividef((float)A, (float)ud);
   q = min(max(q, 1u), M);
@@ -109,8 +136,11 @@ __device__ __forceinline__ unsigned int lemma2_size_fast(unsigned long long A, u
   if ((unsigned long long)q * ud < A) q++;
   if (q > 1u && (unsigned long long)(q - 1u) * ud >= A) q--;      // estimate too large by one
   if (q > 1u && (unsigned long long)(q - 1u) * ud >= A) q--;
-  const unsigned int mg = (g == 1u) ? q : (q + g - 1u) / g * g;
-  return mg <= M ? mg : 0u;
+  if (!z.list) {
+    const unsigned int mg = (z.g == 1u) ? q : (q + z.g - 1u) / z.g * z.g;
+    return mg <= M ? mg : 0u;
+  }
+  return z.next(q);
 }
 
 // One task set staged in shared memory, rows in deadline-monotonic order
@@ -659,27 +689,31 @@ __device__ __forceinline__ bool warp_test(const SetSmem& st, const unsigned int*
   return ok;
 }
 
-// Alg. 2: smallest multiple of g in [lo, hi] at which S passes; 0 if none.
+// Alg. 2: smallest admissible size in [lo, hi] at which S passes; 0 if none.
 // The binary form (§5.2) returns the same size because the test is monotone
 // in m (no timing anomalies, §4.1).
 __device__ __forceinline__ unsigned int warp_minm(const SetSmem& st, const unsigned int* S, unsigned int lo,
-                                                  unsigned int hi, unsigned int g, bool linear, unsigned int kc,
+                                                  unsigned int hi, const Sizes& z, bool linear, unsigned int kc,
                                                   unsigned int km, int sched, const MagicDiv* __restrict__ mdiv,
                                                   RtaScratch& sc, unsigned int* err) {
   if (lo > hi) return 0u;
+  hi = min(hi, z.M);
+  int a = z.below(lo);
+  const int e = z.below(hi + 1u);  // admissible sizes in [lo, hi]: indices a .. e - 1
+  if (a >= e) return 0u;
   if (linear) {
-    for (unsigned int m = lo; m <= hi; m += g)
-      if (warp_test(st, S, m, kc, km, sched, mdiv, sc, nullptr, true, err)) return m;
+    for (int k = a; k < e; k++)
+      if (warp_test(st, S, z.at(k), kc, km, sched, mdiv, sc, nullptr, true, err)) return z.at(k);
     return 0u;
   }
-  if (!warp_test(st, S, hi, kc, km, sched, mdiv, sc, nullptr, true, err)) return 0u;
-  unsigned int a = lo / g, b = hi / g;
+  int b = e - 1;
+  if (!warp_test(st, S, z.at(b), kc, km, sched, mdiv, sc, nullptr, true, err)) return 0u;
   while (a < b) {
-    unsigned int mid = a + (b - a) / 2u;
-    if (warp_test(st, S, mid * g, kc, km, sched, mdiv, sc, nullptr, true, err)) b = mid;
-    else a = mid + 1u;
+    const int mid = a + (b - a) / 2;
+    if (warp_test(st, S, z.at(mid), kc, km, sched, mdiv, sc, nullptr, true, err)) b = mid;
+    else a = mid + 1;
   }
-  return a * g;
+  return z.at(a);
 }
 
 // Warp-wide sums.

@@ -33,6 +33,11 @@ struct DevSets {
 struct DevModel {
   int M, g, kc, km;
   int sched;  // GPA_SCHED_DM or GPA_SCHED_EDF
+  // admissible partition sizes (device arrays): zlist[k] the k-th, zrank[m]
+  // (m in [0, M + 1]) how many are < m; zlist == nullptr: every multiple of g
+  int nz;
+  const unsigned short* zlist;
+  const unsigned short* zrank;
 };
 
 struct AllocOut {

@@ -50,9 +50,46 @@ extern "C" int32_t gpa_last_error(char* buf, int32_t len) {
 // ------------------------------------------------------------- validation
 
 static bool model_valid(const gpa_model* m) {
-  return m && m->g >= 1 && m->M >= 1 && m->M <= GPA_MMAX && m->M % m->g == 0 && m->k_c_pm >= 1000 &&
-         m->k_c_pm <= 16000 && m->k_m_pm >= 1000 && m->k_m_pm <= 16000 &&
-         (m->sched == GPA_SCHED_DM || m->sched == GPA_SCHED_EDF);
+  if (!(m && m->g >= 1 && m->M >= 1 && m->M <= GPA_MMAX && m->M % m->g == 0 && m->k_c_pm >= 1000 &&
+        m->k_c_pm <= 16000 && m->k_m_pm >= 1000 && m->k_m_pm <= 16000 &&
+        (m->sched == GPA_SCHED_DM || m->sched == GPA_SCHED_EDF)))
+    return false;
+  if (m->nsizes < 0 || m->nsizes > GPA_MMAX || (m->nsizes > 0 && !m->sizes)) return false;
+  for (int k = 0; k < m->nsizes; k++) {
+    const int z = m->sizes[k];
+    if (z < m->g || z > m->M || z % m->g != 0 || (k > 0 && z <= m->sizes[k - 1])) return false;
+  }
+  return true;
+}
+
+// The model's admissible partition sizes on the device: nothing for the
+// default (every multiple of g), else the list and its rank table (how many
+// listed sizes lie below each m in [0, M + 1]) in context buffers, copied on
+// the context stream when they change.
+static int32_t device_model(gpa_ctx* c, const gpa_model* model, DevModel* md) {
+  *md = DevModel{model->M, model->g, model->k_c_pm, model->k_m_pm, model->sched, 0, nullptr, nullptr};
+  if (model->nsizes == 0) return GPA_OK;
+  const int M = model->M;
+  std::vector<unsigned short> host((size_t)model->nsizes + (size_t)M + 2);
+  for (int k = 0; k < model->nsizes; k++) host[(size_t)k] = (unsigned short)model->sizes[k];
+  int below = 0;
+  for (int m = 0; m <= M + 1; m++) {
+    host[(size_t)model->nsizes + (size_t)m] = (unsigned short)below;
+    if (below < model->nsizes && model->sizes[below] == m) below++;
+  }
+  unsigned short* dev = (unsigned short*)ctx_buffer(c, 30, sizeof(unsigned short) * host.size());
+  if (!dev) return gpa_fail(GPA_ERR_NOMEM, "size table allocation failed");
+  if (c->size_table != host || c->size_table_ptr != dev) {
+    cudaError_t e = cudaMemcpyAsync(dev, host.data(), sizeof(unsigned short) * host.size(), cudaMemcpyHostToDevice,
+                                    c->stream);
+    if (e != cudaSuccess) return gpa_cuda_fail(e, "size table copy");
+    c->size_table = host;
+    c->size_table_ptr = dev;
+  }
+  md->nz = model->nsizes;
+  md->zlist = dev;
+  md->zrank = dev + model->nsizes;
+  return GPA_OK;
 }
 
 static bool host_task_valid(int64_t T, int64_t D, int64_t A, int64_t B, int64_t u, uint8_t type) {
@@ -503,7 +540,8 @@ extern "C" int32_t gpa_build_wcet_tables(gpa_ctx* c, const gpa_tasksets* sets, c
   if (sets->nsets == 0) return GPA_OK;
   if (!Cn || !Cc) return gpa_fail(GPA_ERR_ARG, "gpa_build_wcet_tables: NULL output");
   DeviceGuard guard(c->device);
-  DevModel md{model->M, model->g, model->k_c_pm, model->k_m_pm, model->sched};
+  DevModel md;
+  if ((st = device_model(c, model, &md)) != GPA_OK) return st;
   const long long Mu = model->M / model->g;
   if (sets->mem == GPA_DEVICE) {
     cudaError_t e = launch_wcet_tables(dev_sets(sets), md, (long long*)Cn, (long long*)Cc, c->d_err, c->d_mdiv,
@@ -542,7 +580,8 @@ extern "C" int32_t gpa_test_schedulable(gpa_ctx* c, const gpa_tasksets* sets, co
   if (!verdict || !cands->set || !cands->part_of_task || !cands->size_of_part)
     return gpa_fail(GPA_ERR_ARG, "gpa_test_schedulable: NULL array");
   DeviceGuard guard(c->device);
-  DevModel md{model->M, model->g, model->k_c_pm, model->k_m_pm, model->sched};
+  DevModel md;
+  if ((st = device_model(c, model, &md)) != GPA_OK) return st;
   const long long nc = cands->ncands;
   if (sets->mem == GPA_DEVICE) {
     Cands cc{nc, cands->map_stride, cands->kparts, (const long long*)cands->set, cands->part_of_task,
@@ -562,8 +601,9 @@ extern "C" int32_t gpa_test_schedulable(gpa_ctx* c, const gpa_tasksets* sets, co
         return gpa_fail(GPA_ERR_RANGE, "candidate %lld: part index out of range", i);
     for (int p = 0; p < cands->kparts; p++) {
       int z = cands->size_of_part[i * cands->kparts + p];
-      if (z < 0 || z > model->M || z % model->g != 0)
-        return gpa_fail(GPA_ERR_RANGE, "candidate %lld: part size out of range", i);
+      bool ok = z == 0 || (z >= model->g && z <= model->M && z % model->g == 0);
+      if (ok && z != 0 && model->nsizes > 0) ok = std::binary_search(model->sizes, model->sizes + model->nsizes, z);
+      if (!ok) return gpa_fail(GPA_ERR_RANGE, "candidate %lld: part size not admissible", i);
     }
   }
   HostStage hs;
@@ -614,8 +654,8 @@ static LaunchShape fast_shape(gpa_ctx* c, const DevSets& ds, const DevModel& md,
 
 std::string tune_key(const DevSets& ds, const DevModel& md, const gpa_params& p) {
   char buf[160];
-  std::snprintf(buf, sizeof buf, "alloc:%lld:%d:%d:%d:%d:%d:%d", ds.nsets, ds.n_max, md.M, md.g, p.policy, p.act,
-                md.sched);
+  std::snprintf(buf, sizeof buf, "alloc:%lld:%d:%d:%d:%d:%d:%d:%d", ds.nsets, ds.n_max, md.M, md.g, p.policy, p.act,
+                md.sched, md.nz);
   return buf;
 }
 
@@ -674,10 +714,10 @@ static void autotune_allocate(gpa_ctx* c, const DevSets& ds, const DevModel& md,
 static std::string graph_key(const DevSets& ds, const DevModel& md, const gpa_params& p, const AllocOut& o,
                              const LaunchShape& sh) {
   char buf[512];
-  std::snprintf(buf, sizeof buf, "%lld|%d|%p|%p|%p|%p|%p|%p|%p|%d|%d|%d|%d|%d|%d|%d|%d|%p|%p|%p|%p|%p|%p|%p|%p|%d|%d|%d|%d",
+  std::snprintf(buf, sizeof buf, "%lld|%d|%p|%p|%p|%p|%p|%p|%p|%d|%d|%d|%d|%d|%d|%p|%d|%d|%d|%p|%p|%p|%p|%p|%p|%p|%p|%d|%d|%d|%d",
                 ds.nsets, ds.n_max, (const void*)ds.set_off, (const void*)ds.T, (const void*)ds.D,
                 (const void*)ds.A, (const void*)ds.B, (const void*)ds.u, (const void*)ds.type, md.M, md.g, md.kc,
-                md.km, md.sched, p.policy, p.act, p.linear_merge, (void*)o.verdict, (void*)o.reason, (void*)o.n_parts,
+                md.km, md.sched, md.nz, (const void*)md.zlist, p.policy, p.act, p.linear_merge, (void*)o.verdict, (void*)o.reason, (void*)o.n_parts,
                 (void*)o.Pi, (void*)o.W, (void*)o.n_tests, (void*)o.part_of_task, (void*)o.size_of_part,
                 sh.warps_per_block, sh.chunk, sh.blocks, sh.stages);
   return buf;
@@ -770,7 +810,8 @@ extern "C" int32_t gpa_allocate(gpa_ctx* c, const gpa_tasksets* sets, const gpa_
     return gpa_fail(GPA_ERR_ARG, "gpa_allocate: NULL result array");
   if (!sets->u_ppm) return gpa_fail(GPA_ERR_ARG, "gpa_allocate: u_ppm is required");
   DeviceGuard guard(c->device);
-  DevModel md{model->M, model->g, model->k_c_pm, model->k_m_pm, model->sched};
+  DevModel md;
+  if ((st = device_model(c, model, &md)) != GPA_OK) return st;
   if (sets->mem == GPA_DEVICE) {
     AllocOut out{r->verdict, r->reason, r->n_parts, r->Pi, (long long*)r->W, r->n_tests, r->part_of_task,
                  r->size_of_part};
@@ -821,7 +862,8 @@ extern "C" int32_t gpa_search_best(gpa_ctx* c, const gpa_tasksets* sets, const g
   if (!r->feasible || !r->W || !r->sum_minm || !r->n_blocks || !r->spare || !r->rgs || !r->minm_block)
     return gpa_fail(GPA_ERR_ARG, "gpa_search_best: NULL result array");
   DeviceGuard guard(c->device);
-  DevModel md{model->M, model->g, model->k_c_pm, model->k_m_pm, model->sched};
+  DevModel md;
+  if ((st = device_model(c, model, &md)) != GPA_OK) return st;
   AllocQueue q{c->d_counters, c->d_slow, c->d_err};
   if (sets->mem == GPA_DEVICE) {
     BestOut out{r->feasible, (long long*)r->W, r->sum_minm, r->n_blocks, r->spare, r->rgs, r->minm_block};

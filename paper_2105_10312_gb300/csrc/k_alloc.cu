@@ -42,7 +42,7 @@ namespace {
 // For a valid task A + B <= 2^36 and 1000 D < 2^41, and A <= 1000 D - B, the
 // one-SM case, is A + B <= 1000 D, which also covers A = 0.
 __device__ __forceinline__ void fast_task(long long T, long long D, long long A, long long B, long long u,
-                                          unsigned int y, unsigned int M, unsigned int g, unsigned int m_one,
+                                          unsigned int y, const Sizes& z, unsigned int m_one,
                                           unsigned int* mm, unsigned int* f, unsigned int* ulo, unsigned int* uhi) {
   const unsigned long long uT = (unsigned long long)T, uD = (unsigned long long)D;
   const unsigned long long uA = (unsigned long long)A, uB = (unsigned long long)B, uu = (unsigned long long)u;
@@ -52,7 +52,7 @@ __device__ __forceinline__ void fast_task(long long T, long long D, long long A,
   const bool valid = high == 0ull && D32 - 1u < (unsigned int)uT && sAB - 1ull < (1ull << 36) && y <= 1u;
   const unsigned long long w = 1000ull * D32;
   unsigned int m = m_one;
-  if (sAB > w) m = uB >= w ? 0u : lemma2_size_fast(uA, uB, uD, M, g);
+  if (sAB > w) m = uB >= w ? 0u : lemma2_size_fast(uA, uB, uD, z, m_one);
   *mm = valid ? m : 0u;
   *f = valid ? (m == 0u ? 2u : 0u) : 1u;
   *ulo = valid ? ((unsigned int)uu & 0xffffu) : 0u;
@@ -125,8 +125,9 @@ __global__ void __launch_bounds__(256) alloc_fast(DevSets S, DevModel md, AllocO
   const int lane = threadIdx.x & 31;
   const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  const unsigned M = (unsigned)md.M, g = (unsigned)md.g;
-  const unsigned m_one = g <= M ? g : 0u;
+  const unsigned M = (unsigned)md.M;
+  const Sizes z = sizes_of(md);
+  const unsigned m_one = z.next(1u);  // the smallest admissible size
   const long long ntasks = __ldg(S.set_off + S.nsets);
   long long offv_next = 0;
   {
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(256) alloc_fast(DevSets S, DevModel md, AllocO
 #pragma unroll
           for (int k = 1; k < K; k++) ks += i >= orel[k] ? 1 : 0;
           unsigned int mm, f, ulo, uhi;
-          fast_task(Tt[uu], Dt[uu], At[uu], Bt[uu], ut[uu], yt[uu], M, g, m_one, &mm, &f, &ulo, &uhi);
+          fast_task(Tt[uu], Dt[uu], At[uu], Bt[uu], ut[uu], yt[uu], z, m_one, &mm, &f, &ulo, &uhi);
           const int first = accumulate<K>(ks, mm, f, ulo, uhi, orel, pi, lo, hi);
           pot[i] = (unsigned char)(i - first);
           sop[i] = (short)mm;
@@ -352,8 +353,9 @@ __global__ void __launch_bounds__(288, 2) alloc_fast_staged(DevSets S, DevModel 
   }
 
   // ------------------------------------------------------------- compute
-  const unsigned M = (unsigned)md.M, g = (unsigned)md.g;
-  const unsigned m_one = g <= M ? g : 0u;
+  const unsigned M = (unsigned)md.M;
+  const Sizes z = sizes_of(md);
+  const unsigned m_one = z.next(1u);  // the smallest admissible size
   int it = 0;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, it++) {
     const int st = it % nstages;
@@ -395,7 +397,7 @@ __global__ void __launch_bounds__(288, 2) alloc_fast_staged(DevSets S, DevModel 
         for (int k = 1; k < K; k++) ks += i >= orel[k] ? 1 : 0;
         unsigned int mm, f, ulo, uhi;
         fast_task(sg.col[0][r8 + i], sg.col[1][r8 + i], sg.col[2][r8 + i], sg.col[3][r8 + i], sg.col[4][r8 + i],
-                  sg.ty[r1 + i], M, g, m_one, &mm, &f, &ulo, &uhi);
+                  sg.ty[r1 + i], z, m_one, &mm, &f, &ulo, &uhi);
         const int first = accumulate<K>(ks, mm, f, ulo, uhi, orel, pi, lo, hi);
         pot[i] = (unsigned char)(i - first);
         sop[i] = (short)mm;

@@ -112,6 +112,7 @@ extern "C" int32_t gpa_allocate_noalloc(void* stream, const gpa_tasksets* sets, 
       model->k_c_pm > 16000 || model->k_m_pm < 1000 || model->k_m_pm > 16000 ||
       (model->sched != GPA_SCHED_DM && model->sched != GPA_SCHED_EDF))
     return gpa_fail(GPA_ERR_RANGE, "gpa_allocate_noalloc: model out of range");
+  if (model->nsizes != 0) return gpa_fail(GPA_ERR_ARG, "gpa_allocate_noalloc: admissible size lists need a context");
   if (params->policy != GPA_POLICY_SMS && params->policy != GPA_POLICY_BF)
     return gpa_fail(GPA_ERR_ARG, "gpa_allocate_noalloc: policy must be GPA_POLICY_SMS or GPA_POLICY_BF");
   if (sets->nsets == 0) return GPA_OK;

@@ -137,20 +137,27 @@ __device__ bool serial_test(const SearchHead& h, SearchThreads& w, unsigned int 
       &eb);
 }
 
-// Smallest multiple of g in [lo, M] at which S passes (0 if none), for a lo
-// known not to exceed the answer (the largest Lemma 2 size of S's tasks): a
-// binary search over lo .. M with M + g standing for "no size passes" (valid
-// because the test is monotone in m, §4.1).
+__device__ __forceinline__ Sizes sizes_of(const DevModel& md) {
+  return Sizes{(unsigned int)md.M, (unsigned int)md.g, md.zlist, md.zrank, md.nz};
+}
+
+// Smallest admissible size in [lo, M] at which S passes (0 if none), for a
+// lo known not to exceed the answer (the largest Lemma 2 size of S's tasks):
+// a binary search over the admissible sizes from lo with one past the last
+// standing for "no size passes" (valid because the test is monotone in m,
+// §4.1).
 __device__ unsigned int serial_minm(const SearchHead& h, SearchThreads& w, unsigned int S, unsigned int lo,
-                                    const DevModel& md, const MagicDiv* __restrict__ mdiv, const WcetTables& tb) {
-  const unsigned int g = md.g, M = md.M;
-  unsigned int a = lo / g, b = M / g + 1u;
+                                    const DevModel& md, const Sizes& z, const MagicDiv* __restrict__ mdiv,
+                                    const WcetTables& tb) {
+  const int e = z.count();
+  int a = z.below(lo), b = e;
   while (a < b) {
-    const unsigned int mid = a + (b - a) / 2u;
-    if (serial_test(h, w, S, mid * g, g, md.kc, md.km, md.sched, mdiv[mid * g], tb)) b = mid;
-    else a = mid + 1u;
+    const int mid = a + (b - a) / 2;
+    const unsigned int m = z.at(mid);
+    if (serial_test(h, w, S, m, (unsigned)md.g, md.kc, md.km, md.sched, mdiv[m], tb)) b = mid;
+    else a = mid + 1;
   }
-  return a * g <= M ? a * g : 0u;
+  return a < e ? z.at(a) : 0u;
 }
 
 __device__ __forceinline__ bool key_less(unsigned long long a1, unsigned long long a2, unsigned long long b1,
@@ -171,6 +178,8 @@ __global__ void __launch_bounds__(kSThreads) search_sets(DevSets S, DevModel md,
   unsigned int* tabc = tabn + tab_cap;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned long long kNoKey = ~0ull;
+  const Sizes z = sizes_of(md);
+  const unsigned int zmin = z.count() > 0 ? z.at(0) : (unsigned)md.M + 1u;  // an empty part's size
 
   for (;;) {
     __syncthreads();
@@ -217,8 +226,7 @@ __global__ void __launch_bounds__(kSThreads) search_sets(DevSets S, DevModel md,
         h.B[r] = (unsigned long long)Bt;
         h.u[r] = (unsigned int)ut;
         h.rowbit[lane] = 1u << r;
-        h.singleton[r] = lemma2_size((unsigned long long)At, (unsigned long long)Bt, (unsigned long long)Dt,
-                                     (unsigned)md.M, (unsigned)md.g);
+        h.singleton[r] = lemma2_size((unsigned long long)At, (unsigned long long)Bt, (unsigned long long)Dt, z);
       }
       const unsigned int mem = __ballot_sync(kFull, ok && lane < n && yt == 1u);
       unsigned int mm = 0u;
@@ -259,12 +267,12 @@ __global__ void __launch_bounds__(kSThreads) search_sets(DevSets S, DevModel md,
     }
     if (n == 0) {
       if (tid == 0) {
-        const bool f = (long long)kmin * md.g <= md.M;
+        const bool f = z.count() > 0 && (long long)kmin * zmin <= md.M;
         out.feasible[s] = f ? 1 : 0;
         out.W[s] = 0;
         out.sum_minm[s] = 0;
         out.n_blocks[s] = 0;
-        out.spare[s] = f ? md.M - kmin * md.g : 0;
+        out.spare[s] = f ? md.M - kmin * (int)zmin : 0;
       }
       for (int b = tid; b < kmax; b += kSThreads) out.minm_block[s * kmax + b] = 0;
       continue;
@@ -298,7 +306,7 @@ __global__ void __launch_bounds__(kSThreads) search_sets(DevSets S, DevModel md,
         dead = dead || z == 0u;
         lo = max(lo, z);
       }
-      msub[S2] = (unsigned short)(dead ? 0u : (__popc(S2) == 1 ? lo : serial_minm(h, w, S2, lo, md, mdiv, tb)));
+      msub[S2] = (unsigned short)(dead ? 0u : (__popc(S2) == 1 ? lo : serial_minm(h, w, S2, lo, md, z, mdiv, tb)));
       const int nmS = __popc(S2 & h.memmask), ncS = __popc(S2) - nmS;
       unsigned long long Uc = 0, Um = 0;
       for (unsigned int r = S2; r; r &= r - 1u) {
@@ -349,7 +357,7 @@ __global__ void __launch_bounds__(kSThreads) search_sets(DevSets S, DevModel md,
         // the whole RGS is the prefix
         const int nb = used;
         const int empty = kmin > nb ? kmin - nb : 0;
-        if ((long long)Sp + (long long)empty * md.g <= md.M) {
+        if ((long long)Sp + (long long)empty * zmin <= md.M) {
           unsigned long long packed = 0;
           for (int k = 0; k < n; k++) packed = (packed << 3) | w.lab[k][tid];
           const unsigned long long k1 = (Wp << 11) | Sp;
@@ -388,7 +396,7 @@ __global__ void __launch_bounds__(kSThreads) search_sets(DevSets S, DevModel md,
         const unsigned int u_next = lb + 1u > u_i ? lb + 1u : u_i;
         if (i + 1 == n) {
           const int empty = kmin > (int)u_next ? kmin - (int)u_next : 0;
-          if ((long long)Sp + (long long)empty * md.g <= md.M) {
+          if ((long long)Sp + (long long)empty * zmin <= md.M) {
             const unsigned long long k1 = (Wp << 11) | Sp;
             if (k1 <= best1) {
               unsigned long long packed = 0;
@@ -460,7 +468,7 @@ __global__ void __launch_bounds__(kSThreads) search_sets(DevSets S, DevModel md,
         out.W[s] = found ? (long long)(best1 >> 11) : 0;
         out.sum_minm[s] = (int)sm;
         out.n_blocks[s] = found ? nb : 0;
-        out.spare[s] = found ? md.M - (int)sm - empty * md.g : 0;
+        out.spare[s] = found ? md.M - (int)sm - empty * (int)zmin : 0;
       }
     }
   }

@@ -140,7 +140,8 @@ __global__ void __launch_bounds__(128) serve_batch(const ServeReq* __restrict__ 
     return;
   }
   TenantSlot* t = slot_ptr(chunks, rq.slot);
-  const unsigned M = (unsigned)md.M, g = (unsigned)md.g;
+  const unsigned g = (unsigned)md.g;
+  const Sizes z = sizes_of(md);
 
   if (rq.op == GPA_SERVE_ADMIT) {
     const int n = rq.n;
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(128) serve_batch(const ServeReq* __restrict__ 
     for (int p = 0; p < np && path == GPA_PATH_NONE && spare >= md.g; p++) {
       rows_of(sm, n + 1, p, S);
       S[rnew >> 5] |= 1u << (rnew & 31);
-      const unsigned m = warp_minm(sm.m.st, S, (unsigned)t->size[p] + g, (unsigned)t->size[p] + (unsigned)spare, g,
+      const unsigned m = warp_minm(sm.m.st, S, (unsigned)t->size[p] + 1u, (unsigned)t->size[p] + (unsigned)spare, z,
                                    true, md.kc, md.km, md.sched, mdiv, sm.m.sc, err);
       if (m) {
         path = GPA_PATH_GROW;
@@ -231,11 +232,11 @@ __global__ void __launch_bounds__(128) serve_batch(const ServeReq* __restrict__ 
     }
     // a new partition of the task's Lemma 2 size
     if (path == GPA_PATH_NONE) {
-      const unsigned z = lemma2_size(sm.m.st.A[rnew], sm.m.st.B[rnew], sm.m.st.D[rnew], M, g);
-      if (z && (int)z <= spare) {
+      const unsigned z1 = lemma2_size(sm.m.st.A[rnew], sm.m.st.B[rnew], sm.m.st.D[rnew], z);
+      if (z1 && (int)z1 <= spare) {
         path = GPA_PATH_NEW;
         where = np;
-        newsize = (int)z;
+        newsize = (int)z1;
       }
     }
     if (path != GPA_PATH_NONE) {
@@ -349,7 +350,7 @@ __global__ void __launch_bounds__(128) serve_batch(const ServeReq* __restrict__ 
       unsigned int S[kWords];
       rows_of(sm, n2, pr, S);
       const unsigned m =
-          warp_minm(sm.m.st, S, g, (unsigned)t->size[pr], g, false, md.kc, md.km, md.sched, mdiv, sm.m.sc, err);
+          warp_minm(sm.m.st, S, g, (unsigned)t->size[pr], z, false, md.kc, md.km, md.sched, mdiv, sm.m.sc, err);
       if (lane == 0) t->size[pr] = (short)m;
     }
     __syncwarp();

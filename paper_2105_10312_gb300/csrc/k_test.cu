@@ -74,6 +74,7 @@ struct TestSmem {
 __global__ void __launch_bounds__(256) test_candidates(DevSets S, DevModel md, Cands C, unsigned char* verdict,
                                                        long long* Rout, unsigned int* err,
                                                        const MagicDiv* __restrict__ mdiv) {
+  const Sizes zs{(unsigned int)md.M, (unsigned int)md.g, md.zlist, md.zrank, md.nz};  // admissible part sizes
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   TestSmem& sm = reinterpret_cast<TestSmem*>(smem_raw)[warp];
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(256) test_candidates(DevSets S, DevModel md, C
     bool bad_size = false;
     for (int p = lane; p < C.kparts; p += 32) {
       int z = size[p];
-      bad_size = bad_size || z < 0 || z > md.M || (z % md.g) != 0;
+      bad_size = bad_size || (z != 0 && !zs.admissible((unsigned int)z)) || z < 0;
       total += z;
     }
     bad = __any_sync(kFull, bad || bad_size);
