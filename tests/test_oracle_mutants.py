@@ -1,0 +1,100 @@
+"""The pins catch plausible mistakes in the oracle.
+
+Each case plants one mistake in a copy of oracle.c (a dropped term, a
+flipped comparison, a swapped operand, an off-by-one), builds it into a
+temporary library, points the oracle module at it and runs every pin of
+tests/test_oracle_pins.py: at least one pin must fail.  The real oracle is
+untouched; all of this runs on the CPU."""
+import ctypes
+import inspect
+import itertools
+import os
+import subprocess
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+MUTANTS = [
+    ("wcet drops m from the b term", "(i128)A + (i128)B * (i128)m", "(i128)A + (i128)B"),
+    ("wcet rounds down", "return (int64_t)((num + den - 1) / den);", "return (int64_t)(num / den);"),
+    ("a task conflicts with itself", "return same >= 2;", "return same >= 1;"),
+    ("conflict factors swapped", "return s->type[i] == 1 ? md->km : md->kc;",
+     "return s->type[i] == 1 ? md->kc : md->km;"),
+    ("priority order reversed", "if (s->D[j] != s->D[i]) return s->D[j] < s->D[i];",
+     "if (s->D[j] != s->D[i]) return s->D[j] > s->D[i];"),
+    ("interference rounded down", "((r + s->T[j] - 1) / s->T[j])", "(r / s->T[j])"),
+    ("Lemma 1 boundary", "return sum > (i128)1000000 * md->M;", "return sum >= (i128)1000000 * md->M;"),
+    ("BF ties to the later candidate", "while (j >= 0 && w[j] > xw)", "while (j >= 0 && w[j] >= xw)"),
+    ("par_list increasing", "if (ux != uy) return ux > uy;", "if (ux != uy) return ux < uy;"),
+    ("demand bound drops the first job", "dbf += ((t - s->D[j]) / s->T[j] + 1) * (i128)C[j];",
+     "dbf += ((t - s->D[j]) / s->T[j]) * (i128)C[j];"),
+    ("size search skips lo", "for (int64_t m = lo; m <= hi; m++)", "for (int64_t m = lo + 1; m <= hi; m++)"),
+    ("merge may keep the sum", "+ Q->m - 1;", "+ Q->m;"),
+    ("workload ignores conflicts", "if (in[i]) w += kfactor(s, md, in, i) * s->u[i];",
+     "if (in[i]) w += 1000 * s->u[i];"),
+    ("SMS ties to the later candidate", "if (m3 > 0 && (best < 0 || m3 < best_m))",
+     "if (m3 > 0 && (best < 0 || m3 <= best_m))"),
+    ("search forgets empty parts", "if (sm + empty * smallest_size(w->md) > w->md->M) return;",
+     "if (sm > w->md->M) return;"),
+    ("EDF single task needs slack", "if (k == 1) return C[idx[0]] <= s->D[idx[0]];",
+     "if (k == 1) return C[idx[0]] < s->D[idx[0]];"),
+    ("sizes ignore the unit g", "if (md->nsizes == 0) return m % md->g == 0;", "if (md->nsizes == 0) return 1;"),
+]
+
+
+def _pin_calls():
+    """(name, function, kwargs) for every pin, parametrised ones expanded."""
+    calls = []
+    for name, f in inspect.getmembers(pins, inspect.isfunction):
+        if not name.startswith("test_") or f.__module__ != pins.__name__:
+            continue
+        marks = [m for m in getattr(f, "pytestmark", []) if m.name == "parametrize"]
+        if not marks:
+            calls.append((name, f, {}))
+            continue
+        grids = []
+        for m in marks:
+            argnames = [a.strip() for a in (m.args[0].split(",") if isinstance(m.args[0], str) else m.args[0])]
+            grids.append([dict(zip(argnames, v if isinstance(v, (tuple, list)) and len(argnames) > 1 else (v,)))
+                          for v in m.args[1]])
+        for combo in itertools.product(*grids):
+            kw = {}
+            for d in combo:
+                kw.update(d)
+            calls.append((name, f, kw))
+    return calls
+
+
+def _failing_pins(source, tmp_path):
+    """Names of the pins that fail with the oracle built from `source`."""
+    c_path = tmp_path / "mutant.c"
+    so_path = tmp_path / "libmutant.so"
+    c_path.write_text(source)
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", str(so_path), str(c_path), "-lpthread"],
+                   check=True)
+    saved = oracle.lib()
+    oracle._lib = ctypes.CDLL(str(so_path))
+    failed = []
+    try:
+        for name, f, kw in _pin_calls():
+            try:
+                f(**kw)
+            except Exception:  # an AssertionError, or a status the mutant made the oracle return
+                failed.append(name)
+    finally:
+        oracle._lib = saved
+    return failed
+
+
+def test_unmutated_copy_passes_every_pin(tmp_path):
+    """Control: the same harness on an unchanged copy fails no pin."""
+    assert _failing_pins(open(oracle._SRC).read(), tmp_path) == []
+
+
+@pytest.mark.parametrize("label,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(label, old, new, tmp_path):
+    src = open(oracle._SRC).read()
+    assert old in src, label
+    assert _failing_pins(src.replace(old, new), tmp_path), f"no pin caught the planted mistake: {label}"

@@ -387,16 +387,28 @@ def test_merge_search_linear_equals_binary():
 
 
 def test_lemma1_utilisation_bound():
-    rng = random.Random(10)
-    for _ in range(500):
-        n = rng.randrange(1, 6)
-        T = [rng.randrange(10, 1000) for _ in range(n)]
-        C1 = [rng.randrange(1, 3000) for _ in range(n)]
-        M = rng.randrange(1, 8)
-        A = [1000 * c for c in C1]
-        B = [0] * n
-        expect = sum(10**6 * c // t for c, t in zip(C1, T)) > 10**6 * M
-        assert oracle.lemma1_rejects(T, A, B, M) == expect
+    """Lemma 1 (necessary condition): a set whose total single-SM
+    utilisation exceeds M has no schedulable partition of M SMs.  Pinned at
+    the exact boundary (U = M passes, a hair above fails) and against the
+    exhaustive search: whenever Lemma 1 rejects, no allocation is feasible."""
+    for M in range(1, 7):
+        for n, want in ((M, False), (M + 1, True)):
+            T = [1000] * n
+            A = [1000 * 1000] * n  # C^n(1) = 1000 = T: utilisation exactly 1 per task
+            assert oracle.lemma1_rejects(T, A, [0] * n, M) == want, (M, n)
+        T = [997, 1000]
+        A = [1000 * 997 * M, 1000]  # U = M + 1/1000 in total
+        assert oracle.lemma1_rejects(T, A, [0, 0], M)
+    s = gen_tasksets(seed=10, nsets=120, n_min=2, n_max=6, U_lo_ppm=1000000, U_hi_ppm=9000000, deadline_pm=1000,
+                     T_lo=1000, T_hi=100000)
+    M, rejected = 6, 0
+    r = oracle.search_best(s, M, 1, KC, KM, 1, 6)
+    for si in range(120):
+        v, o, n = _set_view(s, si)
+        if oracle.lemma1_rejects(v["T"], v["A"], v["B"], M):
+            rejected += 1
+            assert r["feasible"][si] == 0, si
+    assert rejected > 20
 
 
 # ------------------------------------------------------ heuristic (Alg. 1-3)
