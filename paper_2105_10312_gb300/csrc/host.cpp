@@ -639,7 +639,8 @@ static LaunchShape default_fast(const gpa_ctx* c) {
   (void)c;
   return LaunchShape{4, 2, 0, 1};
 }
-static LaunchShape default_slow(const gpa_ctx* c) { return LaunchShape{4, 1, c->sm_count * 2, 1}; }
+// merge kernel: 2 warps (44 KB of shared memory) per CTA, 5 CTAs per SM
+static LaunchShape default_slow(const gpa_ctx* c) { return LaunchShape{2, 1, c->sm_count * 5, 1}; }
 
 static LaunchShape fast_shape(gpa_ctx* c, const DevSets& ds, const DevModel& md, const gpa_params& p) {
   LaunchShape sh = default_fast(c);
