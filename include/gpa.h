@@ -191,15 +191,15 @@ typedef struct {
   int32_t g;       /* partition granularity in SMs (1 = SM, 2 = TPC); sizes are multiples of g */
   int32_t k_c_pm;  /* conflict factor of compute-intensive tasks, per mille (§7.1: 1200) */
   int32_t k_m_pm;  /* conflict factor of memory-intensive tasks, per mille (§7.1: 2300) */
-  int32_t sched;   /* per-partition policy: GPA_SCHED_DM or GPA_SCHED_EDF (not in serving: DM only) */
+  int32_t sched;   /* per-partition policy: GPA_SCHED_DM or GPA_SCHED_EDF */
   int32_t nsizes;  /* 0: every multiple of g in [g, M] is a partition size; else the length of `sizes` */
   const int32_t* sizes; /* host array, strictly increasing multiples of g in [g, M]: the only admissible
                            partition sizes (whole GPCs or MIG slices, §2).  Used by gpa_allocate
                            (Lemma 2 sizes round up to the next listed size; a merge is sized over the
                            listed sizes below the sum of the two), gpa_test_schedulable (a non-empty
                            part's size must be listed) and gpa_search_best (blocks take listed sizes; an
-                           empty part counts the smallest).  1G uses M; serving and
-                           gpa_allocate_noalloc take no list (GPA_ERR_ARG). */
+                           empty part counts the smallest).  1G uses M; serving takes its list in
+                           gpa_serve_cfg; gpa_allocate_noalloc takes none (GPA_ERR_ARG). */
 } gpa_model;
 
 /* Host-side validation of a task batch and model against the bounds above
@@ -419,6 +419,9 @@ typedef struct {
   int32_t slots_per_chunk;       /* tenant slots added per device allocation */
   int64_t max_tenants;           /* upper bound on live tenants */
   int64_t reserve_bytes;         /* device memory left free when adding slots */
+  int32_t sched;                 /* per-partition policy: GPA_SCHED_DM or GPA_SCHED_EDF */
+  int32_t nsizes;                /* admissible partition sizes as in gpa_model (0: every multiple of g) */
+  const int32_t* sizes;          /* host array, copied by gpa_serve_start */
 } gpa_serve_cfg;
 
 typedef struct {

@@ -220,9 +220,15 @@ class Tenant:
 
     COLS = ("T", "D", "A", "B", "u_ppm", "type")
 
-    def __init__(self, M, g, kc, km, policy="SMS", act=False):
+    def __init__(self, M, g, kc, km, policy="SMS", act=False, sched="DM", sizes=None):
         self.M, self.g, self.kc, self.km = M, g, kc, km
         self.policy, self.act = POLICY[policy], 1 if act else 0
+        self.sched = SCHED[sched]
+        self.sizes = None if sizes is None or len(sizes) == 0 else np.ascontiguousarray(sizes, dtype=np.int32)
+
+    def _model_args(self):
+        zp = ctypes.c_void_p(self.sizes.ctypes.data) if self.sizes is not None else ctypes.c_void_p(0)
+        return (ctypes.c_int64(self.sched), zp, ctypes.c_int64(0 if self.sizes is None else len(self.sizes)))
         self.tasks = {k: np.zeros(0, np.uint8 if k == "type" else np.int64) for k in self.COLS}
         self.part = np.zeros(0, np.uint8)
         self.size = np.zeros(0, np.int16)
@@ -250,7 +256,8 @@ class Tenant:
         size = np.zeros(max(n, 1), np.int16)
         _check(lib().orc_serve_admit(ctypes.c_int(n), *[_p(cols[k]) for k in self.COLS], ctypes.c_int64(self.M),
                                      ctypes.c_int64(self.g), ctypes.c_int64(self.kc), ctypes.c_int64(self.km),
-                                     ctypes.c_int(self.policy), ctypes.c_int(self.act), ctypes.byref(v),
+                                     *self._model_args(), ctypes.c_int(self.policy), ctypes.c_int(self.act),
+                                     ctypes.byref(v),
                                      ctypes.byref(r), _p(part), _p(size), ctypes.byref(npart), ctypes.byref(Pi),
                                      ctypes.byref(W)), "serve_admit")
         if v.value:
@@ -275,7 +282,8 @@ class Tenant:
         size = np.zeros(n + 1, np.int16)
         _check(lib().orc_serve_add(ctypes.c_int(n), *[_p(cols[k]) for k in self.COLS], _p(part_in), _p(size_in),
                                    ctypes.c_int(self.n_parts), ctypes.c_int64(self.M), ctypes.c_int64(self.g),
-                                   ctypes.c_int64(self.kc), ctypes.c_int64(self.km), ctypes.c_int(self.policy),
+                                   ctypes.c_int64(self.kc), ctypes.c_int64(self.km), *self._model_args(),
+                                   ctypes.c_int(self.policy),
                                    ctypes.c_int(self.act), ctypes.byref(v), ctypes.byref(r), ctypes.byref(path),
                                    _p(part), _p(size), ctypes.byref(npart), ctypes.byref(Pi), ctypes.byref(W)),
                "serve_add")
@@ -295,7 +303,8 @@ class Tenant:
         _check(lib().orc_serve_remove(ctypes.c_int(n), *[_p(self.tasks[k]) for k in self.COLS], _p(self.part),
                                       _p(self.size), ctypes.c_int(self.n_parts), ctypes.c_int(index),
                                       ctypes.c_int64(self.M), ctypes.c_int64(self.g), ctypes.c_int64(self.kc),
-                                      ctypes.c_int64(self.km), *[_p(outs[k]) for k in self.COLS], _p(part),
+                                      ctypes.c_int64(self.km), *self._model_args(), *[_p(outs[k]) for k in self.COLS],
+                                      _p(part),
                                       _p(size), ctypes.byref(npart), ctypes.byref(Pi), ctypes.byref(W)),
                "serve_remove")
         self.tasks = {k: outs[k][:n - 1].copy() for k in self.COLS}

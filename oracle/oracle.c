@@ -1113,11 +1113,11 @@ static void canonical(int n, uint8_t* part, int16_t* size, int np) {
 }
 
 int orc_serve_admit(int n, const int64_t* T, const int64_t* D, const int64_t* A, const int64_t* B, const int64_t* u,
-                    const uint8_t* type, int64_t M, int64_t g, int64_t kc, int64_t km, int policy, int act,
-                    uint8_t* verdict, uint8_t* reason, uint8_t* part_out, int16_t* size_out, int32_t* n_parts,
-                    int32_t* Pi, int64_t* W) {
+                    const uint8_t* type, int64_t M, int64_t g, int64_t kc, int64_t km, int64_t sched,
+                    const int32_t* sizes, int64_t nsizes, int policy, int act, uint8_t* verdict, uint8_t* reason,
+                    uint8_t* part_out, int16_t* size_out, int32_t* n_parts, int32_t* Pi, int64_t* W) {
   oset s = {n, T, D, A, B, u, type};
-  omodel md = {M, g, kc, km, S_DM, NULL, 0};
+  omodel md = {M, g, kc, km, sched, sizes, nsizes};
   if (!valid_model(&md) || !valid_set(&s)) return O_ERR_RANGE;
   ores r;
   int st = allocate_one(&s, &md, policy, act, 1, &r, part_out, size_out);
@@ -1132,10 +1132,11 @@ int orc_serve_admit(int n, const int64_t* T, const int64_t* D, const int64_t* A,
 /* tasks: n + 1 entries (the state's n tasks, then the new one) */
 int orc_serve_add(int n, const int64_t* T, const int64_t* D, const int64_t* A, const int64_t* B, const int64_t* u,
                   const uint8_t* type, const uint8_t* part_in, const int16_t* size_in, int np_in, int64_t M,
-                  int64_t g, int64_t kc, int64_t km, int policy, int act, uint8_t* verdict, uint8_t* reason,
-                  uint8_t* path, uint8_t* part_out, int16_t* size_out, int32_t* n_parts, int32_t* Pi, int64_t* W) {
+                  int64_t g, int64_t kc, int64_t km, int64_t sched, const int32_t* sizes, int64_t nsizes, int policy,
+                  int act, uint8_t* verdict, uint8_t* reason, uint8_t* path, uint8_t* part_out, int16_t* size_out,
+                  int32_t* n_parts, int32_t* Pi, int64_t* W) {
   oset s = {n + 1, T, D, A, B, u, type};
-  omodel md = {M, g, kc, km, S_DM, NULL, 0};
+  omodel md = {M, g, kc, km, sched, sizes, nsizes};
   if (n + 1 > ONMAX || !valid_model(&md) || !valid_set(&s)) return O_ERR_RANGE;
   const int nw = n;  /* index of the new task */
   int np = np_in;
@@ -1151,7 +1152,7 @@ int orc_serve_add(int n, const int64_t* T, const int64_t* D, const int64_t* A, c
   /* fit into an existing partition at its size */
   for (int p = 0; p < np && *path == PATH_NONE; p++) {
     for (int i = 0; i <= n; i++) in[i] = (i == nw) || (i < n && part_in[i] == p);
-    if (rta(&s, &md, in, size_in[p], NULL)) { part_out[nw] = (uint8_t)p; *path = PATH_FIT; }
+    if (test(&s, &md, in, size_in[p])) { part_out[nw] = (uint8_t)p; *path = PATH_FIT; }
   }
   /* grow a partition into the spare SMs */
   for (int p = 0; p < np && *path == PATH_NONE && spare >= g; p++) {
@@ -1198,10 +1199,11 @@ int orc_serve_add(int n, const int64_t* T, const int64_t* D, const int64_t* A, c
 /* tasks: the state's n tasks; removes task `index` */
 int orc_serve_remove(int n, const int64_t* T, const int64_t* D, const int64_t* A, const int64_t* B,
                      const int64_t* u, const uint8_t* type, const uint8_t* part_in, const int16_t* size_in,
-                     int np_in, int index, int64_t M, int64_t g, int64_t kc, int64_t km, int64_t* T_out,
-                     int64_t* D_out, int64_t* A_out, int64_t* B_out, int64_t* u_out, uint8_t* type_out,
-                     uint8_t* part_out, int16_t* size_out, int32_t* n_parts, int32_t* Pi, int64_t* W) {
-  omodel md = {M, g, kc, km, S_DM, NULL, 0};
+                     int np_in, int index, int64_t M, int64_t g, int64_t kc, int64_t km, int64_t sched,
+                     const int32_t* sizes, int64_t nsizes, int64_t* T_out, int64_t* D_out, int64_t* A_out,
+                     int64_t* B_out, int64_t* u_out, uint8_t* type_out, uint8_t* part_out, int16_t* size_out,
+                     int32_t* n_parts, int32_t* Pi, int64_t* W) {
+  omodel md = {M, g, kc, km, sched, sizes, nsizes};
   if (index < 0 || index >= n || !valid_model(&md)) return O_ERR_RANGE;
   int k = 0;
   for (int i = 0; i < n; i++) {

@@ -388,7 +388,8 @@ class ServeCfg(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int32), ("g", ctypes.c_int32), ("k_c_pm", ctypes.c_int32), ("k_m_pm", ctypes.c_int32),
                 ("policy", ctypes.c_int32), ("act", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("nstreams", ctypes.c_int32), ("queue_cap", ctypes.c_int32), ("slots_per_chunk", ctypes.c_int32),
-                ("max_tenants", ctypes.c_int64), ("reserve_bytes", ctypes.c_int64)]
+                ("max_tenants", ctypes.c_int64), ("reserve_bytes", ctypes.c_int64), ("sched", ctypes.c_int32),
+                ("nsizes", ctypes.c_int32), ("sizes", _vp)]
 
 
 class Request(ctypes.Structure):
@@ -424,11 +425,14 @@ class Server:
     """The admission-control server of a Context (gpa_serve_*)."""
 
     def __init__(self, ctx, M, g=1, k_c_pm=1200, k_m_pm=2300, policy="SMS", act=False, max_batch=1024, nstreams=3,
-                 queue_cap=1 << 20, slots_per_chunk=256, max_tenants=1 << 16, reserve_bytes=1 << 30):
+                 queue_cap=1 << 20, slots_per_chunk=256, max_tenants=1 << 16, reserve_bytes=1 << 30, sched="DM",
+                 sizes=None):
         _serve_sigs(lib())
         self.ctx = ctx
+        zs = None if sizes is None or len(sizes) == 0 else np.ascontiguousarray(sizes, dtype=np.int32)
         cfg = ServeCfg(M, g, k_c_pm, k_m_pm, POLICY[policy], 1 if act else 0, max_batch, nstreams, queue_cap,
-                       slots_per_chunk, max_tenants, reserve_bytes)
+                       slots_per_chunk, max_tenants, reserve_bytes, SCHED[sched], 0 if zs is None else len(zs),
+                       None if zs is None else zs.ctypes.data)
         _check(lib().gpa_serve_start(ctx.handle, ctypes.byref(cfg)))
         self.running = True
 

@@ -91,6 +91,7 @@ struct ServeState {
   int64_t n_completed = 0, n_batches = 0, max_batch_seen = 0, n_overlapped = 0;
   int64_t pay_cap = 0;
   unsigned int* d_err = nullptr;
+  unsigned short* d_sizes = nullptr;  // admissible sizes and rank table, or none
 };
 
 namespace {
@@ -342,6 +343,7 @@ void free_state(ServeState* S) {
   for (auto* c : S->chunks) cudaFree(c);
   cudaFree(S->d_chunks);
   cudaFree(S->d_err);
+  cudaFree(S->d_sizes);
   if (S->setup_stream) cudaStreamDestroy(S->setup_stream);
 }
 
@@ -359,6 +361,15 @@ extern "C" int32_t gpa_serve_start(gpa_ctx* c, const gpa_serve_cfg* cfg) {
     return gpa_fail(GPA_ERR_RANGE, "gpa_serve_start: model out of range");
   if (cfg->policy != GPA_POLICY_SMS && cfg->policy != GPA_POLICY_BF)
     return gpa_fail(GPA_ERR_ARG, "gpa_serve_start: policy must be SMS or BF");
+  if (cfg->sched != GPA_SCHED_DM && cfg->sched != GPA_SCHED_EDF)
+    return gpa_fail(GPA_ERR_ARG, "gpa_serve_start: unknown scheduling policy");
+  if (cfg->nsizes < 0 || cfg->nsizes > GPA_MMAX || (cfg->nsizes > 0 && !cfg->sizes))
+    return gpa_fail(GPA_ERR_RANGE, "gpa_serve_start: size list out of range");
+  for (int k = 0; k < cfg->nsizes; k++) {
+    const int z = cfg->sizes[k];
+    if (z < cfg->g || z > cfg->M || z % cfg->g != 0 || (k > 0 && z <= cfg->sizes[k - 1]))
+      return gpa_fail(GPA_ERR_RANGE, "gpa_serve_start: size list must increase over multiples of g in [g, M]");
+  }
   if (cfg->max_batch < 1 || cfg->max_batch > 4096 || cfg->nstreams < 1 || cfg->nstreams > 8 || cfg->queue_cap < 1 ||
       cfg->max_tenants < 1 || cfg->max_tenants > (int64_t)kSlotsPerChunkMax * kMaxChunks || cfg->reserve_bytes < 0)
     return gpa_fail(GPA_ERR_RANGE, "gpa_serve_start: configuration out of range");
@@ -369,7 +380,8 @@ extern "C" int32_t gpa_serve_start(gpa_ctx* c, const gpa_serve_cfg* cfg) {
   S->ctx = c;
   S->cfg = *cfg;
   S->device = c->device;
-  S->md = DevModel{cfg->M, cfg->g, cfg->k_c_pm, cfg->k_m_pm, GPA_SCHED_DM};
+  S->md = DevModel{cfg->M, cfg->g, cfg->k_c_pm, cfg->k_m_pm, cfg->sched, 0, nullptr, nullptr};
+  S->cfg.sizes = nullptr;  // the list is copied to the device below, not kept by pointer
   S->prm = gpa_params{cfg->policy, cfg->act, 1, 0};
   S->pay_cap = (int64_t)cfg->max_batch * GPA_NMAX;
   bool ok = cudaStreamCreateWithFlags(&S->setup_stream, cudaStreamNonBlocking) == cudaSuccess &&
@@ -390,6 +402,24 @@ extern "C" int32_t gpa_serve_start(gpa_ctx* c, const gpa_serve_cfg* cfg) {
          cudaMalloc(&sc.d_resp, sizeof(ServeResp) * nb) == cudaSuccess &&
          cudaMalloc(&sc.d_pay, sizeof(long long) * 5 * pb) == cudaSuccess &&
          cudaMalloc(&sc.d_type, pb) == cudaSuccess;
+  }
+  if (ok && cfg->nsizes > 0) {
+    // the admissible sizes and their rank table over [0, M + 1] (see gpa_model)
+    std::vector<unsigned short> host((size_t)cfg->nsizes + (size_t)cfg->M + 2);
+    for (int k = 0; k < cfg->nsizes; k++) host[(size_t)k] = (unsigned short)cfg->sizes[k];
+    int below = 0;
+    for (int m = 0; m <= cfg->M + 1; m++) {
+      host[(size_t)cfg->nsizes + (size_t)m] = (unsigned short)below;
+      if (below < cfg->nsizes && cfg->sizes[below] == m) below++;
+    }
+    ok = cudaMalloc(&S->d_sizes, sizeof(unsigned short) * host.size()) == cudaSuccess &&
+         cudaMemcpy(S->d_sizes, host.data(), sizeof(unsigned short) * host.size(), cudaMemcpyHostToDevice) ==
+             cudaSuccess;
+    if (ok) {
+      S->md.nz = cfg->nsizes;
+      S->md.zlist = S->d_sizes;
+      S->md.zrank = S->d_sizes + cfg->nsizes;
+    }
   }
   if (ok) {
     const int want = cfg->slots_per_chunk > 0 ? cfg->slots_per_chunk : kSlotsPerChunkMax;

@@ -15,9 +15,9 @@ KC, KM = W.K_C, W.K_M
 M = 148
 
 
-def _replay(seq):
+def _replay(seq, sched="DM", sizes=None):
     """Oracle responses for one tenant's sequence, and the concrete ops."""
-    t = oracle.Tenant(M, 1, KC, KM)
+    t = oracle.Tenant(M, 1, KC, KM, sched=sched, sizes=sizes)
     out, concrete = [], []
     alive = False
     for op, arg in seq:
@@ -135,6 +135,38 @@ def test_serve_errors_and_poll_contract():
         assert ok["status"] == 0 and again["status"] == gpa.ERR_ARG  # the tenant exists
         r = srv.poll(srv.submit("REMOVE", 9, index=500))
         assert r["status"] == gpa.ERR_RANGE
+    finally:
+        srv.stop()
+        ctx.close()
+
+
+@pytest.mark.parametrize("sched,sizes", [("EDF", None), ("DM", [4, 8, 12, 16, 24, 32, 48, 64, 96, 148]),
+                                         ("EDF", [7, 14, 21, 28, 42, 74, 148])])
+def test_serve_policy_and_sizes_match_oracle(sched, sizes):
+    """The EDF policy and admissible size lists in the serving loop: mixed
+    micro-batches, every response equal to its tenant's replay."""
+    ops = serve_seq.make_ops(24, 25, seed=13, evict=True)
+    work = [_replay(seq, sched=sched, sizes=sizes) for seq in ops]
+    ctx = gpa.Context(0)
+    srv = gpa.Server(ctx, M=M, max_batch=16, nstreams=3, sched=sched, sizes=sizes)
+    try:
+        ids = []
+        depth = max(len(c) for c, _ in work)
+        for j in range(depth):
+            for k, (concrete, expect) in enumerate(work):
+                if j < len(concrete):
+                    op, arg, idx = concrete[j]
+                    ids.append((k, j, _submit(srv, 2000 + k, op, arg, idx)))
+        for k, j, rid in ids:
+            r = srv.poll(rid)
+            assert r["status"] == 0
+            _same(r, work[k][1][j], f"{sched} {sizes is not None} tenant {k} request {j}")
+        if sizes:
+            used = set()
+            for _, expect in work:
+                for e in expect:
+                    used |= set(e["size_of_part"].tolist())
+            assert used and used <= set(sizes)
     finally:
         srv.stop()
         ctx.close()
