@@ -546,6 +546,7 @@ def run_gpu(args):
             hout[k] = torch.from_numpy(v).pin_memory().numpy() if v is not None else None
         ctx_h = gpa.Context(local, stream=stream)
         ctx_h.set_option("GRAPH", 1)
+        ctx_h.set_option("HOST_SLICES", args.host_slices)
         with torch.cuda.stream(stream):
             ctx_h.allocate(hs, **md, policy=policy, act=act, out=hout)
             times = []
@@ -560,7 +561,11 @@ def run_gpu(args):
         h2d = 8 * (nsets + 1) + 41 * ntasks
         d2h = 22 * nsets + 3 * ntasks
         e2e = {"value": total_sets / e2e_t, "unit": "tasksets/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h}
+               "d2h_bytes_per_step": d2h, "ms_per_call": 1000.0 * e2e_t,
+               "path": "gpa_allocate on pinned host buffers, synchronous; host slices "
+                       + ("by size (batches over 48 MB split into slices of <= 64 MB whose copies in, kernels and copies "
+                          "out overlap; page-locked arrays moved by the staging kernel)"
+                          if args.host_slices == 0 else str(args.host_slices))}
 
     # the plain form: one launch sequence per task set, on a sample
     plain = None
@@ -636,6 +641,9 @@ def main():
     ap.add_argument("--sched", choices=["dm", "edf"], default="dm",
                     help="per-partition policy: deadline-monotonic response-time test (default) or EDF demand test")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--host-slices", type=int, default=0,
+                    help="host-buffer path: 0 = library default (split batches over 48 MB), 1 = whole batch checked "
+                         "before computing, n = n slices")
     ap.add_argument("--plain-sample", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true",

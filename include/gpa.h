@@ -22,7 +22,13 @@
  *    are copied into the context's device buffers and checked against the
  *    bounds there before any computation (GPA_ERR_RANGE naming the first
  *    offending set; nothing is computed and no output is written); the call
- *    is synchronous.  Device inputs are validated by
+ *    is synchronous.  gpa_allocate instead checks host sets in the kernels
+ *    that compute them and splits a large batch into slices whose copies
+ *    and kernels overlap (GPA_OPT_HOST_SLICES): a rejected batch returns
+ *    GPA_ERR_RANGE naming the first offending set, and its outputs are
+ *    unspecified (GPA_OPT_HOST_SLICES = 1 restores check-before-compute).
+ *    Page-locked host arrays are read and written by a staging kernel over
+ *    the host link, pageable ones by cudaMemcpyAsync (GPA_OPT_HOST_COPY).  Device inputs are validated by
  *    the kernels: an invalid set gets reason GPA_REASON_INVALID, its other
  *    outputs are zero, and the context's sticky error word is set; the call
  *    itself is asynchronous on the context stream and gpa_ctx_sync() reports
@@ -158,10 +164,22 @@ enum {
   GPA_OPT_PER_SET_LAUNCH = 6, /* 1: the plain form, one launch sequence per task set (comparison only) */
   GPA_OPT_PROFILE = 7,        /* 1: record CUDA events around each kernel of every call (also inside
                                  captured graphs) so that gpa_ctx_last_timing can report them */
-  GPA_OPT_FAST_STAGES = 8     /* force how the fast allocate kernel reads the task columns: 1 = direct
+  GPA_OPT_FAST_STAGES = 8,    /* force how the fast allocate kernel reads the task columns: 1 = direct
                                  loads; 2..5 = through that many shared-memory stages filled by bulk
                                  copies, used only when every task column starts on a 16-byte
                                  boundary (direct loads otherwise) (0 = tuned/default) */
+  GPA_OPT_HOST_SLICES = 9,    /* gpa_allocate on host buffers: 0 = sets checked by the computing
+                                 kernels, batches of more than 48 MB of task columns split into
+                                 max(2, ceil(MB / 64)) slices (at most 16) whose copies in, kernels and
+                                 copies out overlap; 1 = the whole batch checked before any computation (a
+                                 rejected batch leaves the outputs untouched); n in 2..64 = as 0 but
+                                 every batch split into n slices (fewer when it has fewer sets)
+                                 (default 0) */
+  GPA_OPT_HOST_COPY = 10      /* how host buffers move: 0 = arrays that are page-locked (cudaHostAlloc,
+                                 cudaHostRegister) are read and written by one staging kernel per
+                                 direction and slice, over the host link, with up to 16 CTAs per array;
+                                 other arrays by cudaMemcpyAsync; 1 = cudaMemcpyAsync for every array;
+                                 n in 2..256 = the staging kernel with n CTAs per array (default 0) */
 };
 int32_t gpa_ctx_set_option(gpa_ctx* ctx, int32_t option, int64_t value);
 

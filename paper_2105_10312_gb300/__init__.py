@@ -29,7 +29,8 @@ POLICY = {"SMS": 0, "BF": 1, "ONE_GPU": 2}
 SCHED = {"DM": 0, "EDF": 1}
 REASON = {"OK": 0, "LEMMA1": 1, "LEMMA2": 2, "NO_MERGE": 3, "TEST": 4, "INVALID": 5}
 OPT = {"AUTOTUNE": 1, "GRAPH": 2, "FAST_WARPS": 3, "FAST_CHUNK": 4, "FAST_BLOCKS": 5, "PER_SET_LAUNCH": 6,
-       "PROFILE": 7, "FAST_STAGES": 8}
+       "PROFILE": 7, "FAST_STAGES": 8, "HOST_SLICES": 9,
+       "HOST_COPY": 10}
 NMAX, MMAX, SEARCH_NMAX, SEARCH_KMAX = 128, 1024, 14, 8
 
 _vp = ctypes.c_void_p

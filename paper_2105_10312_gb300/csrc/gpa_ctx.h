@@ -43,6 +43,12 @@ struct gpa_ctx {
   gpa::Prof prof{};                          // timing events of direct (non-graph) calls
   const gpa::Prof* last_prof = nullptr;      // events of the last profiled call
   gpa::LaunchShape force_fast{0, 0, 0, 0};
+  int host_slices = 0;                       // GPA_OPT_HOST_SLICES
+  int host_copy = 0;                         // GPA_OPT_HOST_COPY
+  cudaStream_t copy_in = nullptr;            // sliced host path: host-to-device copies
+  cudaStream_t copy_out = nullptr;           // sliced host path: device-to-host copies
+  cudaEvent_t pipe_ev[3] = {nullptr, nullptr, nullptr};  // start, slice copied in, slice computed
+  unsigned int* h_err = nullptr;             // page-locked copy of the error word read at the end of a call
   std::vector<unsigned short> size_table;   // last admissible-size table copied to the device
   void* size_table_ptr = nullptr;
   std::map<std::string, gpa::LaunchShape> tuned;

@@ -51,6 +51,21 @@ struct AllocOut {
   short* size_of_part;
 };
 
+// Byte ranges copied by one launch of the staging kernel (k_stage.cu); one
+// side of each is page-locked host memory mapped into the device's address
+// space, the other a device buffer.
+constexpr int kStageRangesMax = 12;
+struct StageRange {
+  const void* src;
+  void* dst;
+  unsigned long long bytes;
+};
+struct StageList {
+  StageRange r[kStageRangesMax];
+  int n;
+};
+cudaError_t launch_stage_copy(const StageList& L, int blocks_per_range, cudaStream_t st, long long* launches);
+
 // Work-queue state of the persistent allocate kernels.
 struct AllocQueue {
   unsigned long long* counters;  // [4]: fast ticket, slow count, slow ticket, 1G ticket

@@ -343,6 +343,11 @@ extern "C" int32_t gpa_ctx_destroy(gpa_ctx* c) {
   for (int i = 0; i < 4; i++)
     if (c->prof.ev[i]) cudaEventDestroy(c->prof.ev[i]);
   for (auto& b : c->bufs) cudaFree(b.ptr);
+  for (cudaEvent_t ev : c->pipe_ev)
+    if (ev) cudaEventDestroy(ev);
+  if (c->h_err) cudaFreeHost(c->h_err);
+  if (c->copy_in) cudaStreamDestroy(c->copy_in);
+  if (c->copy_out) cudaStreamDestroy(c->copy_out);
   cudaFree(c->d_mdiv);
   cudaFree(c->d_counters);
   cudaFree(c->d_err);
@@ -384,6 +389,14 @@ extern "C" int32_t gpa_ctx_set_option(gpa_ctx* c, int32_t opt, int64_t value) {
       if (value < 0 || value > 5) return gpa_fail(GPA_ERR_RANGE, "stages (0 = tuned, 1 = direct loads, 2..5)");
       c->force_fast.stages = (int)value;
       break;
+    case GPA_OPT_HOST_SLICES:
+      if (value < 0 || value > 64) return gpa_fail(GPA_ERR_RANGE, "host slices (0 = by size, 1 = whole, <= 64)");
+      c->host_slices = (int)value;
+      break;
+    case GPA_OPT_HOST_COPY:
+      if (value < 0 || value > 256) return gpa_fail(GPA_ERR_RANGE, "host copy (0 = by kernel where page-locked, 1 = copies, <= 256)");
+      c->host_copy = (int)value;
+      break;
     case GPA_OPT_PER_SET_LAUNCH: c->per_set_launch = value != 0; break;
     case GPA_OPT_PROFILE:
       c->profile = value != 0;
@@ -394,6 +407,15 @@ extern "C" int32_t gpa_ctx_set_option(gpa_ctx* c, int32_t opt, int64_t value) {
   return GPA_OK;
 }
 
+// The status a nonzero error word stands for; clears the word on the device.
+static int32_t err_word_status(gpa_ctx* c, unsigned int err) {
+  if (!err) return GPA_OK;
+  cudaMemset(c->d_err, 0, sizeof(unsigned int));
+  if (err & 2u) return gpa_fail(GPA_ERR_TIMEOUT, "a response-time iteration exceeded its step limit");
+  if (err & 4u) return gpa_fail(GPA_ERR_TIMEOUT, "a pipeline barrier wait exceeded its time limit");
+  return gpa_fail(GPA_ERR_RANGE, "a device-resident set failed validation");
+}
+
 extern "C" int32_t gpa_ctx_sync(gpa_ctx* c) {
   if (!c) return gpa_fail(GPA_ERR_ARG, "gpa_ctx_sync: NULL context");
   DeviceGuard guard(c->device);
@@ -402,13 +424,7 @@ extern "C" int32_t gpa_ctx_sync(gpa_ctx* c) {
   unsigned int err = 0;
   e = cudaMemcpy(&err, c->d_err, sizeof err, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return gpa_cuda_fail(e, "read error word");
-  if (err) {
-    cudaMemset(c->d_err, 0, sizeof(unsigned int));
-    if (err & 2u) return gpa_fail(GPA_ERR_TIMEOUT, "a response-time iteration exceeded its step limit");
-    if (err & 4u) return gpa_fail(GPA_ERR_TIMEOUT, "a pipeline barrier wait exceeded its time limit");
-    return gpa_fail(GPA_ERR_RANGE, "a device-resident set failed validation");
-  }
-  return GPA_OK;
+  return err_word_status(c, err);
 }
 
 // --------------------------------------------------------- scratch buffers
@@ -445,6 +461,68 @@ static int32_t ensure_slow(gpa_ctx* c, long long nsets) {
 
 // --------------------------------------------------- host <-> device staging
 
+// The device address of host range [p, p + bytes) when both its first and its
+// last byte lie in page-locked memory mapped for the current device (then the
+// staging kernel may read or write it), else nullptr.  A caller's array is one
+// allocation, page-locked as a whole or not at all.
+static void* mapped_host(const void* p, size_t bytes) {
+  if (!p || bytes == 0) return nullptr;
+  cudaPointerAttributes a{}, b{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+  const char* last = static_cast<const char*>(p) + bytes - 1;
+  if (cudaPointerGetAttributes(&b, last) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (b.type != cudaMemoryTypeHost || static_cast<char*>(b.devicePointer) != static_cast<char*>(a.devicePointer) + (bytes - 1))
+    return nullptr;
+  return a.devicePointer;
+}
+
+// The copies of one direction on one stream: ranges whose host side is
+// page-locked are gathered into one launch of the staging kernel, the others
+// go to cudaMemcpyAsync (GPA_OPT_HOST_COPY = 1 sends every range there).
+struct Mover {
+  gpa_ctx* c;
+  cudaStream_t st;
+  bool to_device;
+  bool engine;  // copy engine only
+  StageList L{};
+  unsigned long long widest = 0;
+  cudaError_t e = cudaSuccess;
+
+  Mover(gpa_ctx* ctx, cudaStream_t s, bool in, bool engine_only = false)
+      : c(ctx), st(s), to_device(in), engine(engine_only || ctx->host_copy == 1) {}
+
+  void add(void* dst, const void* src, size_t bytes) {
+    if (e != cudaSuccess || bytes == 0) return;
+    void* mapped = engine ? nullptr : mapped_host(to_device ? src : dst, bytes);
+    if (mapped) {
+      if (L.n == kStageRangesMax) flush();
+      if (e != cudaSuccess) return;
+      L.r[L.n++] = to_device ? StageRange{mapped, dst, bytes} : StageRange{src, mapped, bytes};
+      if (bytes > widest) widest = bytes;
+      return;
+    }
+    e = cudaMemcpyAsync(dst, src, bytes, to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost, st);
+  }
+  // CTAs per range: one per 256 KB of the widest range, at most 16 (or the
+  // count GPA_OPT_HOST_COPY forces)
+  cudaError_t flush() {
+    if (e == cudaSuccess && L.n > 0) {
+      int blocks = c->host_copy >= 2 ? c->host_copy : (int)std::min<unsigned long long>(16, 1 + (widest >> 18));
+      e = launch_stage_copy(L, blocks, st, &c->launches);
+    }
+    L.n = 0;
+    widest = 0;
+    return e;
+  }
+};
+
 struct HostStage {
   DevSets ds{};
   long long ntasks = 0;
@@ -465,16 +543,18 @@ static int32_t stage_in(gpa_ctx* c, const gpa_tasksets* sets, HostStage* hs) {
   unsigned char* ty = (unsigned char*)ctx_buffer(c, 6, (size_t)(nt > 0 ? nt : 1));
   if (!off || !T || !D || !A || !B || !u || !ty) return gpa_fail(GPA_ERR_NOMEM, "staging allocation failed");
   cudaStream_t st = c->stream;
-  cudaError_t e = cudaMemcpyAsync(off, sets->set_off, sizeof(long long) * (size_t)(ns + 1), cudaMemcpyHostToDevice, st);
+  Mover mv(c, st, true);
+  mv.add(off, sets->set_off, sizeof(long long) * (size_t)(ns + 1));
   if (nt > 0) {
-    if (e == cudaSuccess) e = cudaMemcpyAsync(T, sets->T, b8, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(D, sets->D, b8, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(A, sets->A, b8, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(B, sets->B, b8, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && sets->u_ppm) e = cudaMemcpyAsync(u, sets->u_ppm, b8, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && !sets->u_ppm) e = cudaMemsetAsync(u, 0, b8, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ty, sets->type, (size_t)nt, cudaMemcpyHostToDevice, st);
+    mv.add(T, sets->T, b8);
+    mv.add(D, sets->D, b8);
+    mv.add(A, sets->A, b8);
+    mv.add(B, sets->B, b8);
+    if (sets->u_ppm) mv.add(u, sets->u_ppm, b8);
+    mv.add(ty, sets->type, (size_t)nt);
   }
+  cudaError_t e = mv.flush();
+  if (e == cudaSuccess && nt > 0 && !sets->u_ppm) e = cudaMemsetAsync(u, 0, b8, st);
   if (e != cudaSuccess) return gpa_cuda_fail(e, "host-to-device copy of task sets");
   hs->ds = DevSets{ns, sets->n_max, off, T, D, A, B, u, ty};
   return GPA_OK;
@@ -798,6 +878,168 @@ static int32_t allocate_device(gpa_ctx* c, const DevSets& ds, const DevModel& md
   return e == cudaSuccess ? GPA_OK : gpa_cuda_fail(e, "allocate launch");
 }
 
+// ------------------------------------------- allocate on host buffers, sliced
+
+// gpa_allocate on host buffers.  The batch's sets are checked by the kernels
+// that compute them (as for device inputs), so no pass over the batch
+// precedes the computation and the call waits for the GPU once, at its end.
+// A batch with more than 3/4 of kSliceBytes of task columns is split into
+// max(2, ceil(bytes / kSliceBytes)) slices (at most kAutoSlicesMax): slice j's
+// copy in, its kernels and its copy out run on three streams, so the host
+// link carries slice j + 1 in while slice j computes and slice j - 1 goes
+// out.  Each slice costs a few launches and waits, and the two directions of
+// the link share its bandwidth, so a few large slices do best.  GPA_OPT_HOST_SLICES = 1 selects the
+// whole-batch form instead: copy, check on the device, then compute only if
+// every set passed.
+static const long long kSliceBytes = 64ll << 20;
+static const int kAutoSlicesMax = 16;
+
+// Set boundaries 0 = b[0] < b[1] < ... < b[S] = nsets balancing the task
+// count (S = 1 for a batch that is not split); an empty vector selects the
+// whole-batch form.  set_off is not yet checked, so every boundary's task
+// offset is checked to lie in [0, ntasks] and not to decrease (a batch that
+// fails this takes the whole-batch form, whose check rejects it).
+static std::vector<long long> slice_bounds(const gpa_ctx* c, const gpa_tasksets* sets) {
+  const long long ns = sets->nsets, nt = sets->set_off[ns];
+  long long S = c->host_slices;
+  if (S == 1) return {};
+  if (S == 0) {
+    const long long bytes = 41 * nt + 8 * ns;
+    S = 4 * bytes <= 3 * kSliceBytes
+            ? 1
+            : std::min<long long>(std::max(2ll, (bytes + kSliceBytes - 1) / kSliceBytes), kAutoSlicesMax);
+  }
+  S = std::max(1ll, std::min(S, ns));
+  std::vector<long long> b{0};
+  for (long long j = 1; j < S; j++) {
+    const long long target = nt / S * j + nt % S * j / S;
+    long long lo = b.back() + 1, hi = ns - 1;  // first set index in [lo, hi] whose offset reaches target
+    if (lo > hi) break;
+    while (lo < hi) {
+      const long long mid = lo + (hi - lo) / 2;
+      if (sets->set_off[mid] < target) lo = mid + 1;
+      else hi = mid;
+    }
+    b.push_back(lo);
+  }
+  b.push_back(ns);
+  for (size_t j = 0; j + 1 < b.size(); j++) {
+    const long long t0 = sets->set_off[b[j]], t1 = sets->set_off[b[j + 1]];
+    if (b[j + 1] <= b[j] || t0 < 0 || t1 < t0 || t1 > nt) return {};
+  }
+  return b;
+}
+
+static int32_t ensure_pipe(gpa_ctx* c) {
+  cudaError_t e = cudaSuccess;
+  if (!c->copy_in) e = cudaStreamCreateWithFlags(&c->copy_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !c->copy_out) e = cudaStreamCreateWithFlags(&c->copy_out, cudaStreamNonBlocking);
+  for (int i = 0; i < 3 && e == cudaSuccess; i++)
+    if (!c->pipe_ev[i]) e = cudaEventCreateWithFlags(&c->pipe_ev[i], cudaEventDisableTiming);
+  if (e == cudaSuccess && !c->h_err) e = cudaHostAlloc((void**)&c->h_err, 64, cudaHostAllocDefault);
+  return e == cudaSuccess ? GPA_OK : gpa_cuda_fail(e, "copy streams");
+}
+
+static int32_t allocate_host_sliced(gpa_ctx* c, const gpa_tasksets* sets, const gpa_model* model,
+                                    const DevModel& md, const gpa_params& p, gpa_alloc_result* r,
+                                    const std::vector<long long>& b) {
+  const long long ns = sets->nsets, nt = sets->set_off[ns];
+  if (nt > 0 && (!sets->T || !sets->D || !sets->A || !sets->B || !sets->type))
+    return gpa_fail(GPA_ERR_ARG, "NULL task column");
+  int32_t st = ensure_pipe(c);
+  if (st != GPA_OK) return st;
+  if ((st = ensure_slow(c, ns)) != GPA_OK) return st;
+  const size_t b8 = sizeof(long long) * (size_t)(nt > 0 ? nt : 1);
+  long long* off = (long long*)ctx_buffer(c, 0, sizeof(long long) * (size_t)(ns + 1));
+  long long* T = (long long*)ctx_buffer(c, 1, b8);
+  long long* D = (long long*)ctx_buffer(c, 2, b8);
+  long long* A = (long long*)ctx_buffer(c, 3, b8);
+  long long* B = (long long*)ctx_buffer(c, 4, b8);
+  long long* u = (long long*)ctx_buffer(c, 5, b8);
+  unsigned char* ty = (unsigned char*)ctx_buffer(c, 6, (size_t)(nt > 0 ? nt : 1));
+  const size_t ntb = (size_t)(nt > 0 ? nt : 1);
+  AllocOut out{(unsigned char*)ctx_buffer(c, 14, (size_t)ns), (unsigned char*)ctx_buffer(c, 15, (size_t)ns),
+               (int*)ctx_buffer(c, 16, sizeof(int) * (size_t)ns), (int*)ctx_buffer(c, 17, sizeof(int) * (size_t)ns),
+               (long long*)ctx_buffer(c, 18, sizeof(long long) * (size_t)ns),
+               r->n_tests ? (int*)ctx_buffer(c, 19, sizeof(int) * (size_t)ns) : nullptr,
+               (unsigned char*)ctx_buffer(c, 20, ntb), (short*)ctx_buffer(c, 21, sizeof(short) * ntb)};
+  if (!off || !T || !D || !A || !B || !u || !ty || !out.verdict || !out.reason || !out.n_parts || !out.Pi ||
+      !out.W || (r->n_tests && !out.n_tests) || !out.part_of_task || !out.size_of_part)
+    return gpa_fail(GPA_ERR_NOMEM, "staging allocation failed");
+  cudaStream_t in = c->copy_in, cs = c->stream, ot = c->copy_out;
+  cudaEvent_t ev_start = c->pipe_ev[0], ev_in = c->pipe_ev[1], ev_done = c->pipe_ev[2];
+  // Every wait below is issued right after the record it waits for, so the
+  // three events serve all slices.
+  cudaError_t e = cudaEventRecord(ev_start, cs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(in, ev_start, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ot, ev_start, 0);
+  // The staging kernel needs SM slots while the previous slice computes; the
+  // 1G kernel holds every SM for its whole slice, so its slices move by copy
+  // engine (unless GPA_OPT_HOST_COPY forces the kernel).
+  const bool engine = p.policy == GPA_POLICY_ONE_GPU && c->host_copy < 2 && b.size() > 2;
+  Mover mi(c, in, true, engine), mo(c, ot, false, engine);
+  mi.add(off, sets->set_off, sizeof(long long) * (size_t)(ns + 1));
+  st = GPA_OK;
+  for (size_t j = 0; j + 1 < b.size() && e == cudaSuccess && st == GPA_OK; j++) {
+    const long long s0 = b[j], s1 = b[j + 1], t0 = sets->set_off[s0], t1 = sets->set_off[s1];
+    const size_t n = (size_t)(t1 - t0), n8 = sizeof(long long) * n;
+    mi.add(T + t0, sets->T + t0, n8);
+    mi.add(D + t0, sets->D + t0, n8);
+    mi.add(A + t0, sets->A + t0, n8);
+    mi.add(B + t0, sets->B + t0, n8);
+    mi.add(u + t0, sets->u_ppm + t0, n8);
+    mi.add(ty + t0, sets->type + t0, n);
+    if ((e = mi.flush()) != cudaSuccess) break;
+    e = cudaEventRecord(ev_in, in);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_in, 0);
+    if (e != cudaSuccess) break;
+    // the slice's sets index the full task columns (their offsets are absolute)
+    DevSets ds{s1 - s0, sets->n_max, off + s0, T, D, A, B, u, ty};
+    AllocOut o = out;
+    o.verdict += s0;
+    o.reason += s0;
+    o.n_parts += s0;
+    o.Pi += s0;
+    o.W += s0;
+    if (o.n_tests) o.n_tests += s0;
+    if ((st = allocate_device(c, ds, md, p, o)) != GPA_OK) break;
+    e = cudaEventRecord(ev_done, cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ot, ev_done, 0);
+    if (e != cudaSuccess) break;
+    const size_t m = (size_t)(s1 - s0);
+    mo.add(r->verdict + s0, o.verdict, m);
+    mo.add(r->reason + s0, o.reason, m);
+    mo.add(r->n_parts + s0, o.n_parts, sizeof(int) * m);
+    mo.add(r->Pi + s0, o.Pi, sizeof(int) * m);
+    mo.add(r->W + s0, o.W, sizeof(long long) * m);
+    if (r->n_tests) mo.add(r->n_tests + s0, o.n_tests, sizeof(int) * m);
+    mo.add(r->part_of_task + t0, out.part_of_task + t0, n);
+    mo.add(r->size_of_part + t0, out.size_of_part + t0, sizeof(short) * n);
+    // after the last slice, the error word comes out with the results
+    if (j + 2 == b.size()) mo.add(c->h_err, c->d_err, sizeof(unsigned int));
+    e = mo.flush();
+  }
+  if (st != GPA_OK || e != cudaSuccess) {
+    // No copy may touch the caller's arrays after the call returns: wait for
+    // all three streams whatever happened above.
+    cudaStreamSynchronize(in);
+    cudaStreamSynchronize(cs);
+    cudaStreamSynchronize(ot);
+    return st != GPA_OK ? st : gpa_cuda_fail(e, "allocate on host buffers");
+  }
+  // the copy-out stream's last work waited for the last slice's kernels,
+  // which waited for the last copy in: one wait covers all three streams
+  if ((e = cudaStreamSynchronize(ot)) != cudaSuccess) return gpa_cuda_fail(e, "allocate on host buffers");
+  st = err_word_status(c, *c->h_err);
+  if (st == GPA_ERR_RANGE) {
+    // the kernels flagged an invalid set: name the first one
+    int64_t bad = -1;
+    const int32_t vs = gpa_validate(sets, model, &bad);
+    if (vs != GPA_OK) return vs;
+  }
+  return st;
+}
+
 extern "C" int32_t gpa_allocate(gpa_ctx* c, const gpa_tasksets* sets, const gpa_model* model,
                                 const gpa_params* params, gpa_alloc_result* r) {
   int32_t st = common_checks(c, sets, model, "gpa_allocate");
@@ -818,6 +1060,8 @@ extern "C" int32_t gpa_allocate(gpa_ctx* c, const gpa_tasksets* sets, const gpa_
                  r->size_of_part};
     return allocate_device(c, dev_sets(sets), md, *params, out);
   }
+  const std::vector<long long> bounds = slice_bounds(c, sets);
+  if (!bounds.empty()) return allocate_host_sliced(c, sets, model, md, *params, r, bounds);
   HostStage hs;
   if ((st = stage_in_validated(c, sets, model, &hs)) != GPA_OK) return st;
   const long long ns = sets->nsets, nt = hs.ntasks > 0 ? hs.ntasks : 1;
@@ -830,18 +1074,18 @@ extern "C" int32_t gpa_allocate(gpa_ctx* c, const gpa_tasksets* sets, const gpa_
       !out.part_of_task || !out.size_of_part)
     return gpa_fail(GPA_ERR_NOMEM, "result staging failed");
   if ((st = allocate_device(c, hs.ds, md, *params, out)) != GPA_OK) return st;
-  cudaStream_t s = c->stream;
-  cudaError_t e = cudaMemcpyAsync(r->verdict, out.verdict, (size_t)ns, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(r->reason, out.reason, (size_t)ns, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(r->n_parts, out.n_parts, sizeof(int) * (size_t)ns, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(r->Pi, out.Pi, sizeof(int) * (size_t)ns, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(r->W, out.W, sizeof(long long) * (size_t)ns, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && r->n_tests)
-    e = cudaMemcpyAsync(r->n_tests, out.n_tests, sizeof(int) * (size_t)ns, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && hs.ntasks > 0)
-    e = cudaMemcpyAsync(r->part_of_task, out.part_of_task, (size_t)hs.ntasks, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && hs.ntasks > 0)
-    e = cudaMemcpyAsync(r->size_of_part, out.size_of_part, sizeof(short) * (size_t)hs.ntasks, cudaMemcpyDeviceToHost, s);
+  Mover mv(c, c->stream, false);
+  mv.add(r->verdict, out.verdict, (size_t)ns);
+  mv.add(r->reason, out.reason, (size_t)ns);
+  mv.add(r->n_parts, out.n_parts, sizeof(int) * (size_t)ns);
+  mv.add(r->Pi, out.Pi, sizeof(int) * (size_t)ns);
+  mv.add(r->W, out.W, sizeof(long long) * (size_t)ns);
+  if (r->n_tests) mv.add(r->n_tests, out.n_tests, sizeof(int) * (size_t)ns);
+  if (hs.ntasks > 0) {
+    mv.add(r->part_of_task, out.part_of_task, (size_t)hs.ntasks);
+    mv.add(r->size_of_part, out.size_of_part, sizeof(short) * (size_t)hs.ntasks);
+  }
+  cudaError_t e = mv.flush();
   if (e != cudaSuccess) return gpa_cuda_fail(e, "allocate result copy");
   return finish_host_call(c);
 }

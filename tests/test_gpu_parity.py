@@ -299,17 +299,25 @@ def test_allocate_odd_task_count_and_unaligned_columns(ctx, stages):
 
 def test_host_input_out_of_bounds_computes_nothing(ctx):
     """A host batch with one task out of bounds: GPA_ERR_RANGE naming that
-    set, no output written; the next valid call works."""
+    set, from the kernels by default and from the check before computation
+    with HOST_SLICES = 1, which writes no output; the next valid call works."""
     s = gpa.gen_tasksets(**W.gen_params("batch", nsets=2000))
     bad = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in s.items()}
     bad["D"][int(bad["set_off"][1234]) + 1] = 0
     md = W.model("batch")
+    with pytest.raises(gpa.GpaError) as ei:
+        ctx.allocate(bad, **md)
+    assert ei.value.code == gpa.ERR_RANGE and "1234" in str(ei.value)
     out = ctx.alloc_result(bad)
     for v in out.values():
         if v is not None:
             v.fill(77)
-    with pytest.raises(gpa.GpaError) as ei:
-        ctx.allocate(bad, **md, out=out)
+    ctx.set_option("HOST_SLICES", 1)
+    try:
+        with pytest.raises(gpa.GpaError) as ei:
+            ctx.allocate(bad, **md, out=out)
+    finally:
+        ctx.set_option("HOST_SLICES", 0)
     assert ei.value.code == gpa.ERR_RANGE and "1234" in str(ei.value)
     for k, v in out.items():
         if v is not None:
@@ -331,7 +339,7 @@ def test_device_validation_flags_invalid_sets(ctx):
     assert _np(out["reason"])[0] == gpa.REASON["OK"]
     ctx.sync()  # the flag is cleared
     with pytest.raises(gpa.GpaError) as ei:
-        ctx.allocate(s, M=68, g=1, k_c_pm=KC, k_m_pm=KM)  # host path: rejected before any launch
+        ctx.allocate(s, M=68, g=1, k_c_pm=KC, k_m_pm=KM)  # host path: rejected by the kernels
     assert ei.value.code == gpa.ERR_RANGE
 
 
