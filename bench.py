@@ -10,7 +10,7 @@ second (whole job, all ranks); candidate merges evaluated per second is
 reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload batch|sweep|exhaustive|single|paper50]
+                  [--workload batch|sweep|sweep1g|exhaustive|single|paper50|paper200]
 
 Under torchrun each rank decides its own batch (seed offset by rank: weak
 scaling, no data-path collective); the timed region is bracketed by a barrier
@@ -47,6 +47,7 @@ DESCR = {
     "sweep1g": "sweep: 1000000 task sets x U{4..64} tasks, 148 SMs, U=0.1..6.0 step 0.1, Beta(2,5) intensity; 1G baseline",
     "exhaustive": "exhaustive: 20000 task sets x 12 tasks, 20 TPC units, 1..4 partitions; exact optimum per set",
     "paper50": "paper setting: 3400 task sets x 50 tasks, 68 SMs, U=2..68 step 2, D=0.75T; heuristic SMS/INA",
+    "paper200": "paper setting: 3400 task sets x 200 tasks, 68 SMs, U=2..68 step 2, D=0.75T; heuristic SMS/INA",
 }
 
 
@@ -61,25 +62,42 @@ def read_peaks():
 
 
 def kernel_source_hash():
+    """Hash of every kernel source (the .cu files and device headers)."""
+    d = os.path.join(ROOT, "paper_2105_10312_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("k_alloc.cu", "gpa_device.cuh", "bulk_pipe.cuh"):
-        with open(os.path.join(ROOT, "paper_2105_10312_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")) or f == "gpa_ns.h":
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, if it was taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", f"alloc_fast_{workload}.md")
-    if not os.path.exists(path):
+# the committed ncu summary of each workload's dominant kernel
+PROFILES = {("alloc_fast", "batch"): "alloc_fast_batch.md", ("alloc_merge", "paper50"): "alloc_merge_paper50.md",
+            ("one_gpu", "sweep1g"): "one_gpu_sweep.md", ("search_sets", "exhaustive"): "search_sets_exhaustive.md"}
+
+
+def recorded_profile(kernel, workload):
+    """Figures of the committed ncu summary of `kernel` on `workload` (DRAM
+    bytes per launch, ALU pipe, issue and warps-active percentages), if it
+    was taken on the current kernel sources; else None."""
+    name = PROFILES.get((kernel, workload))
+    path = os.path.join(ROOT, "profiles", name) if name else None
+    if not path or not os.path.exists(path):
         return None
     text = open(path).read()
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.]+)", text)
     h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
-    if not m or not h or h.group(1) != kernel_source_hash():
+    if not h or h.group(1) != kernel_source_hash():
         return None
-    return float(m.group(1))
+    out = {"source": "profiles/" + name}
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.]+)", text)
+    out["traffic"] = float(m.group(1)) if m else None
+    for key, metric in (("alu_pipe_pct", "sm__pipe_alu_cycles_active.avg.pct_of_peak_sustained_active"),
+                        ("issue_active_pct", "smsp__issue_active.avg.pct_of_peak_sustained_active"),
+                        ("warps_active_pct", "sm__warps_active.avg.pct_of_peak_sustained_active")):
+        m = re.search(r"\| " + re.escape(metric) + r" \| ([0-9.]+)", text)
+        out[key] = float(m.group(1)) if m else None
+    return out
 
 
 def gpu_id_for_smi(local):
@@ -511,27 +529,35 @@ def run_gpu(args):
                    "heuristic": [round(float(vh[st == j].mean()), 4) for j in range(steps)],
                    "1G": [round(float(v1[st == j].mean()), 4) for j in range(steps)]}
 
-    # roofline of the dominant kernel (the fast allocate kernel for the heuristic workloads)
+    # roofline of the dominant kernel: the fast allocate kernel (HBM-bound)
+    # when it takes most of the step, else the merge, 1G or search kernel,
+    # which are bound by serial integer work (reported with the ALU pipe and
+    # issue figures of their committed ncu summary)
     hbm_peak, peak_src = read_peaks()
     roof = None
-    if kern_ms and args.workload != "exhaustive":
-        k_ms = float(np.mean(kern_ms))
-        if policy == "ONE_GPU":
-            alg_bytes = 41 * ntasks + 8 * (nsets + 1) + 23 * nsets + 2 * ntasks + ntasks
-        else:
-            # per task: T, D, A, B, u (5 x 8 B) + type (1 B) read; part (1 B) + size (2 B) written;
-            # per set: offset (8 B) read; verdict, reason, n_parts, Pi, W, n_tests (22 B) written
-            alg_bytes = 44 * ntasks + 30 * nsets
+    timing = ("CUDA events around the kernel on the context stream, a second pass of the same K flushed steps; "
+              "step time with those events %.4f ms" % float(np.mean(prof_step_ms))) if kern_ms else None
+    k_ms = float(np.mean(kern_ms)) if kern_ms else None
+    k2_ms = float(np.mean(kern2_ms)) if kern2_ms else 0.0
+    if kern_ms and args.workload != "exhaustive" and policy != "ONE_GPU" and k_ms >= k2_ms:
+        # per task: T, D, A, B, u (5 x 8 B) + type (1 B) read; part (1 B) + size (2 B) written;
+        # per set: offset (8 B) read; verdict, reason, n_parts, Pi, W, n_tests (22 B) written
+        alg_bytes = 44 * ntasks + 30 * nsets
         achieved = alg_bytes / (k_ms / 1000.0) / 1e9
-        traffic = recorded_traffic(args.workload) if policy != "ONE_GPU" else None
+        prof = recorded_profile("alloc_fast", args.workload)
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": traffic, "kernel": "alloc_fast" if policy != "ONE_GPU" else "one_gpu",
+                "traffic": prof["traffic"] if prof else None, "kernel": "alloc_fast",
                 "kernel_ms": k_ms, "algorithmic_bytes": alg_bytes, "peak_source": peak_src + " hbm_gbs",
-                "kernel_timing": "CUDA events around the kernel on the context stream, a second pass of the same "
-                                 "K flushed steps; step time with those events %.4f ms" % float(np.mean(prof_step_ms))}
+                "kernel_timing": timing}
     elif kern_ms:
-        roof = {"bound": "alu", "kernel": "search_sets", "kernel_ms": float(np.mean(kern_ms)), "achieved": None,
-                "peak": None, "unit": None, "frac": None, "traffic": None}
+        kernel, ms = ("search_sets", k_ms) if args.workload == "exhaustive" else \
+            ("one_gpu", k_ms) if policy == "ONE_GPU" else ("alloc_merge", k2_ms)
+        prof = recorded_profile(kernel, args.workload)
+        roof = {"bound": "alu", "kernel": kernel, "kernel_ms": ms, "achieved": None, "peak": None, "unit": None,
+                "frac": None, "traffic": prof["traffic"] if prof else None, "kernel_timing": timing,
+                "ncu": prof,
+                "note": "serial integer fixed-point chains (one warp or thread per set, subset or candidate); "
+                        "no live ALU-throughput figure: see the ncu ALU pipe and issue percentages"}
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     e2e = None
@@ -629,7 +655,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
                     help="timed steps (default: enough for about 0.2 s of steps and several clock samples; "
-                         "batch 1000, paper50 / sweep / sweep1g 100, exhaustive 10)")
+                         "batch 1000, paper50 / sweep / sweep1g 100, exhaustive 10, paper200 5)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gpa", "reference"], default="gpa")
     ap.add_argument("--workload", choices=sorted(DESCR), default="batch")
@@ -653,7 +679,7 @@ def main():
                     help="seconds of Poisson arrivals per offered rate in the serving measurement (0: skip)")
     args = ap.parse_args()
     if args.steps is None:
-        args.steps = {"batch": 1000, "exhaustive": 10}.get(args.workload, 100)
+        args.steps = {"batch": 1000, "exhaustive": 10, "paper200": 5}.get(args.workload, 100)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -70,7 +70,8 @@
  * bounds the busy period, and so the analysis time, near U = 1).
  * EDF gives no response times: R is 0 for the tasks of a passing part.
  *
- * Validation bounds (GPA_ERR_RANGE): 0 <= n <= 128 tasks per set,
+ * Validation bounds (GPA_ERR_RANGE): 0 <= n <= 256 tasks per set (128 for
+ * serving tenants and gpa_allocate_noalloc),
  * 1 <= D <= T <= 2^31 - 1, A >= 0, B >= 0, 1 <= A + B <= 2^36,
  * 0 <= u_ppm < 2^32, type in {0, 1}; model: 1 <= g, g | M, 1 <= M <= 1024,
  * 1000 <= k_c_pm, k_m_pm <= 16000.  These keep every WCET below 2^31 and
@@ -85,8 +86,9 @@
 extern "C" {
 #endif
 
-#define GPA_ABI_VERSION 2
-#define GPA_NMAX 128          /* tasks per set */
+#define GPA_ABI_VERSION 3
+#define GPA_NMAX 256          /* tasks per set */
+#define GPA_SERVE_NMAX 128    /* tasks per serving tenant and per set of gpa_allocate_noalloc */
 #define GPA_MMAX 1024         /* SMs on the modelled GPU */
 #define GPA_SEARCH_NMAX 14    /* tasks per set in gpa_search_best */
 #define GPA_SEARCH_KMAX 8     /* partitions per candidate in gpa_search_best */
@@ -399,8 +401,8 @@ int32_t gpa_search_best(gpa_ctx* ctx, const gpa_tasksets* sets, const gpa_model*
 
 /* ----------------------------------------------------------------- serving */
 
-/* Admission control as a service: tenants (task sets of up to GPA_NMAX
- * tasks) and their current allocation live in device memory; requests are
+/* Admission control as a service: tenants (task sets of up to
+ * GPA_SERVE_NMAX tasks) and their current allocation live in device memory; requests are
  * queued, packed into micro-batches (at most one request per tenant per
  * batch, each tenant's requests in submission order) and run one warp per
  * request on one of several streams, so a batch starts while earlier ones are
@@ -465,8 +467,8 @@ typedef struct {
   uint8_t pad_;
   int32_t n_tasks, n_parts, Pi;  /* the tenant's state after the request */
   int64_t W;
-  uint8_t part_of_task[GPA_NMAX];
-  int16_t size_of_part[GPA_NMAX];
+  uint8_t part_of_task[GPA_SERVE_NMAX];
+  int16_t size_of_part[GPA_SERVE_NMAX];
   double latency_us;             /* submit to completion, host clock */
 } gpa_response;
 

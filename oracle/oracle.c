@@ -48,7 +48,8 @@
 
 typedef __int128 i128;
 
-#define ONMAX 128
+#define ONMAX 256       /* tasks per set */
+#define OSERVE_NMAX 128 /* tasks per serving tenant */
 
 enum { O_OK = 0, O_ERR_ARG = -1, O_ERR_RANGE = -2, O_ERR_NOMEM = -3 };
 enum { R_OK = 0, R_LEMMA1 = 1, R_LEMMA2 = 2, R_NO_MERGE = 3, R_TEST = 4, R_INVALID = 5 };
@@ -1118,7 +1119,7 @@ int orc_serve_admit(int n, const int64_t* T, const int64_t* D, const int64_t* A,
                     uint8_t* part_out, int16_t* size_out, int32_t* n_parts, int32_t* Pi, int64_t* W) {
   oset s = {n, T, D, A, B, u, type};
   omodel md = {M, g, kc, km, sched, sizes, nsizes};
-  if (!valid_model(&md) || !valid_set(&s)) return O_ERR_RANGE;
+  if (n > OSERVE_NMAX || !valid_model(&md) || !valid_set(&s)) return O_ERR_RANGE;
   ores r;
   int st = allocate_one(&s, &md, policy, act, 1, &r, part_out, size_out);
   *verdict = r.verdict;
@@ -1137,7 +1138,7 @@ int orc_serve_add(int n, const int64_t* T, const int64_t* D, const int64_t* A, c
                   int32_t* n_parts, int32_t* Pi, int64_t* W) {
   oset s = {n + 1, T, D, A, B, u, type};
   omodel md = {M, g, kc, km, sched, sizes, nsizes};
-  if (n + 1 > ONMAX || !valid_model(&md) || !valid_set(&s)) return O_ERR_RANGE;
+  if (n + 1 > OSERVE_NMAX || !valid_model(&md) || !valid_set(&s)) return O_ERR_RANGE;
   const int nw = n;  /* index of the new task */
   int np = np_in;
   for (int i = 0; i < n; i++) part_out[i] = part_in[i];

@@ -31,7 +31,7 @@ REASON = {"OK": 0, "LEMMA1": 1, "LEMMA2": 2, "NO_MERGE": 3, "TEST": 4, "INVALID"
 OPT = {"AUTOTUNE": 1, "GRAPH": 2, "FAST_WARPS": 3, "FAST_CHUNK": 4, "FAST_BLOCKS": 5, "PER_SET_LAUNCH": 6,
        "PROFILE": 7, "FAST_STAGES": 8, "HOST_SLICES": 9,
        "HOST_COPY": 10}
-NMAX, MMAX, SEARCH_NMAX, SEARCH_KMAX = 128, 1024, 14, 8
+NMAX, SERVE_NMAX, MMAX, SEARCH_NMAX, SEARCH_KMAX = 256, 128, 1024, 14, 8
 
 _vp = ctypes.c_void_p
 
@@ -175,7 +175,13 @@ def make_tasksets(sets, n_max=None):
     mem = _mem_of(sets["set_off"])
     nsets = _len(sets["set_off"]) - 1
     if n_max is None:
-        n_max = int(sets.get("n_max", NMAX))
+        n_max = sets.get("n_max")
+    if n_max is None:
+        # the largest set of the batch (the kernels are chosen by it: up to 128
+        # tasks, or up to 256)
+        off = sets["set_off"]
+        n_max = int((off[1:] - off[:-1]).max()) if nsets > 0 else 0
+    n_max = int(n_max)
     ts = Tasksets(nsets, mem, int(n_max), _ptr(sets["set_off"]), _ptr(sets["T"]), _ptr(sets["D"]),
                   _ptr(sets["A"]), _ptr(sets["B"]), _ptr(sets.get("u_ppm")), _ptr(sets["type"]))
     return ts, mem
@@ -403,7 +409,8 @@ class Response(ctypes.Structure):
     _fields_ = [("req_id", ctypes.c_uint64), ("status", ctypes.c_int32), ("verdict", ctypes.c_uint8),
                 ("reason", ctypes.c_uint8), ("path", ctypes.c_uint8), ("pad_", ctypes.c_uint8),
                 ("n_tasks", ctypes.c_int32), ("n_parts", ctypes.c_int32), ("Pi", ctypes.c_int32),
-                ("W", ctypes.c_int64), ("part_of_task", ctypes.c_uint8 * NMAX), ("size_of_part", ctypes.c_int16 * NMAX),
+                ("W", ctypes.c_int64), ("part_of_task", ctypes.c_uint8 * SERVE_NMAX),
+                ("size_of_part", ctypes.c_int16 * SERVE_NMAX),
                 ("latency_us", ctypes.c_double)]
 
     def as_dict(self):

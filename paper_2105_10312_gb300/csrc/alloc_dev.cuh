@@ -8,7 +8,7 @@
 #include "gpa_device.cuh"
 #include "gpa_internal.h"
 
-namespace gpa {
+GPA_NS_BEGIN
 
 namespace {
 
@@ -548,4 +548,4 @@ __device__ void merge_set(MergeSmem& sm, long long s, long long o, int n, const 
 
 }  // namespace
 
-}  // namespace gpa
+GPA_NS_END

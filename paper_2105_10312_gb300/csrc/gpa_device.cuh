@@ -15,11 +15,12 @@
 #include <cstdint>
 
 #include "gpa.h"
+#include "gpa_ns.h"
 
-namespace gpa {
+GPA_NS_BEGIN
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kNmax = GPA_NMAX;
+constexpr int kNmax = GPA_KNMAX;
 constexpr int kWords = kNmax / 32;        // 32-bit words of a task mask
 constexpr int kIterCap = 1 << 20;         // response-time iterations per task before GPA_ERR_TIMEOUT
 
@@ -205,7 +206,7 @@ __device__ __forceinline__ bool stage_set(SetSmem& st, long long o, int n, const
   ok = __all_sync(kFull, ok);
   if (!ok) return false;
   __syncwarp();
-  // DM rank of each task by counting (n <= 128)
+  // DM rank of each task by counting
   int rank[kWords];
   for (int c = 0; c < kWords; c++) {
     int t = c * 32 + lane;
@@ -412,8 +413,8 @@ __device__ __forceinline__ unsigned long long edf_la_bound(double num, unsigned 
 }
 
 // The band rule decided cheaply first: uf = sum of float C_i / T_i is within
-// 2^-14 of U for n <= 128 (each term within 3 ulp, the float sum within
-// n ulp), and U <= U_hi / 2^32 <= U + n 2^-32.  So uf below kEdfPass means
+// 2^-14 of U for n <= 256 (each term within 3 ulp, the float sum within
+// n ulp: at most 258 ulp = 2^-16), and U <= U_hi / 2^32 <= U + n 2^-32.  So uf below kEdfPass means
 // U_hi <= kEdfUmax, above kEdfFail means U_hi > kEdfUmax; only in between
 // are the exact integer terms summed.  numf = sum (T_i - D_i) C_i / T_i in
 // the same precision gives L_a <= numf (1 + 2^-20) / (1 - uf - 2^-14).
@@ -725,4 +726,4 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 
 __device__ __forceinline__ int warp_sum_i32(int v) { return __reduce_add_sync(kFull, (unsigned int)v); }
 
-}  // namespace gpa
+GPA_NS_END

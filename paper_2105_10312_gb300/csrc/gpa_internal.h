@@ -136,4 +136,21 @@ size_t slow_smem_bytes(int warps_per_block);
 size_t staged_smem_bytes(int stages);
 size_t one_gpu_smem_bytes(int warps_per_block);
 
+// The same allocate and candidate-test kernels built for sets of up to 256
+// tasks (k_alloc_wide.cu, k_test_wide.cu); the host uses them when a batch's
+// n_max exceeds kNarrowNmax.
+constexpr int kNarrowNmax = 128;
+namespace wide {
+cudaError_t launch_allocate(const DevSets& s, const DevModel& md, const gpa_params& p, const AllocOut& out,
+                            const AllocQueue& q, const MagicDivHost* mdiv, const LaunchShape& fast,
+                            const LaunchShape& slow, cudaStream_t st, long long* launches, Prof* prof);
+cudaError_t launch_one_gpu(const DevSets& s, const DevModel& md, const AllocOut& out, const AllocQueue& q,
+                           const MagicDivHost* mdiv, const LaunchShape& shape, cudaStream_t st, long long* launches,
+                           Prof* prof);
+cudaError_t alloc_kernels_init();
+cudaError_t launch_test_schedulable(const DevSets& s, const DevModel& md, const Cands& c, unsigned char* verdict,
+                                    long long* R, unsigned int* err, const MagicDivHost* mdiv, int sm_count,
+                                    cudaStream_t st, long long* launches, Prof* prof);
+}  // namespace wide
+
 }  // namespace gpa

@@ -293,6 +293,7 @@ extern "C" int32_t gpa_ctx_create(int32_t device, void* stream, gpa_ctx** out) {
   static cudaError_t init_err = cudaSuccess;
   std::call_once(once, [] {
     init_err = alloc_kernels_init();
+    if (init_err == cudaSuccess) init_err = wide::alloc_kernels_init();
     if (init_err == cudaSuccess) init_err = search_kernels_init();
   });
   if (init_err != cudaSuccess) {
@@ -666,8 +667,9 @@ extern "C" int32_t gpa_test_schedulable(gpa_ctx* c, const gpa_tasksets* sets, co
   if (sets->mem == GPA_DEVICE) {
     Cands cc{nc, cands->map_stride, cands->kparts, (const long long*)cands->set, cands->part_of_task,
              cands->size_of_part};
-    cudaError_t e = launch_test_schedulable(dev_sets(sets), md, cc, verdict, (long long*)R, c->d_err, c->d_mdiv,
-                                            c->sm_count, c->stream, &c->launches, begin_prof(c));
+    cudaError_t e = (sets->n_max > kNarrowNmax ? wide::launch_test_schedulable : launch_test_schedulable)(
+        dev_sets(sets), md, cc, verdict, (long long*)R, c->d_err, c->d_mdiv, c->sm_count, c->stream, &c->launches,
+        begin_prof(c));
     return e == cudaSuccess ? GPA_OK : gpa_cuda_fail(e, "test_schedulable launch");
   }
   // host path: validate candidates on the host too
@@ -703,8 +705,8 @@ extern "C" int32_t gpa_test_schedulable(gpa_ctx* c, const gpa_tasksets* sets, co
                         cudaMemcpyHostToDevice, s);
   Cands cc{nc, cands->map_stride, cands->kparts, dset, dmap, dsize};
   if (e == cudaSuccess)
-    e = launch_test_schedulable(hs.ds, md, cc, dver, dR, c->d_err, c->d_mdiv, c->sm_count, s, &c->launches,
-                                begin_prof(c));
+    e = (hs.ds.n_max > kNarrowNmax ? wide::launch_test_schedulable : launch_test_schedulable)(
+        hs.ds, md, cc, dver, dR, c->d_err, c->d_mdiv, c->sm_count, s, &c->launches, begin_prof(c));
   if (e == cudaSuccess) e = cudaMemcpyAsync(verdict, dver, (size_t)nc, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && R)
     e = cudaMemcpyAsync(R, dR, sizeof(long long) * (size_t)(nc * cands->map_stride), cudaMemcpyDeviceToHost, s);
@@ -740,14 +742,22 @@ std::string tune_key(const DevSets& ds, const DevModel& md, const gpa_params& p)
   return buf;
 }
 
+// The kernels of the batch's task capacity: the 128-task build, or the
+// 256-task build when n_max exceeds 128.
 static cudaError_t run_allocate(gpa_ctx* c, const DevSets& ds, const DevModel& md, const gpa_params& p,
                                 const AllocOut& out, const LaunchShape& fast, Prof* prof) {
   AllocQueue q{c->d_counters, c->d_slow, c->d_err};
+  const bool wide_sets = ds.n_max > kNarrowNmax;
   if (p.policy == GPA_POLICY_ONE_GPU) {
     LaunchShape sh{8, 1, c->sm_count * 4, 1};
-    return launch_one_gpu(ds, md, out, q, c->d_mdiv, sh, c->stream, &c->launches, prof);
+    return (wide_sets ? wide::launch_one_gpu : launch_one_gpu)(ds, md, out, q, c->d_mdiv, sh, c->stream,
+                                                                &c->launches, prof);
   }
-  return launch_allocate(ds, md, p, out, q, c->d_mdiv, fast, default_slow(c), c->stream, &c->launches, prof);
+  // merge kernel of the 256-task build: 58 KB of shared memory per warp, so
+  // one warp per CTA and three CTAs per SM
+  const LaunchShape slow = wide_sets ? LaunchShape{1, 1, c->sm_count * 3, 1} : default_slow(c);
+  return (wide_sets ? wide::launch_allocate : launch_allocate)(ds, md, p, out, q, c->d_mdiv, fast, slow, c->stream,
+                                                                &c->launches, prof);
 }
 
 // Autotuner: time the candidate shapes of the fast kernel on this batch
@@ -824,8 +834,8 @@ static int32_t allocate_device(gpa_ctx* c, const DevSets& ds, const DevModel& md
       LaunchShape one_shape{1, 1, 1, 1};
       AllocQueue q{c->d_counters, c->d_slow, c->d_err};
       LaunchShape slow1{1, 1, 1, 1};
-      cudaError_t e =
-          launch_allocate(one, md, p, o1, q, c->d_mdiv, one_shape, slow1, c->stream, &c->launches, nullptr);
+      cudaError_t e = (one.n_max > kNarrowNmax ? wide::launch_allocate : launch_allocate)(
+          one, md, p, o1, q, c->d_mdiv, one_shape, slow1, c->stream, &c->launches, nullptr);
       if (e != cudaSuccess) return gpa_cuda_fail(e, "per-set allocate launch");
     }
     return GPA_OK;

@@ -20,7 +20,7 @@
 #include "gpa_device.cuh"
 #include "gpa_internal.h"
 
-namespace gpa {
+GPA_NS_BEGIN
 
 namespace {
 
@@ -445,6 +445,9 @@ struct OneGpuSmem {
   SetSmem st;
   RtaScratch sc;
 };
+// the dynamic shared memory opted in by alloc_kernels_init (227 KB per CTA at most)
+static_assert(4 * sizeof(MergeSmem) <= 232448, "merge kernel: four warps must fit 227 KB");
+static_assert(8 * sizeof(OneGpuSmem) <= 232448, "1G kernel: eight warps must fit 227 KB");
 
 __global__ void __launch_bounds__(256) one_gpu(DevSets S, DevModel md, AllocOut out, unsigned int* err,
                                                const MagicDiv* __restrict__ mdiv, unsigned long long* ticket) {
@@ -631,4 +634,4 @@ cudaError_t alloc_kernels_init() {
   return cudaFuncSetAttribute(one_gpu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)one_gpu_smem_bytes(8));
 }
 
-}  // namespace gpa
+GPA_NS_END

@@ -107,7 +107,8 @@ extern "C" int32_t gpa_allocate_noalloc(void* stream, const gpa_tasksets* sets, 
   if (sets->nsets < 0 || sets->nsets > kNoAllocMaxSets)
     return gpa_fail(GPA_ERR_RANGE, "gpa_allocate_noalloc: %lld task sets exceed the limit of %lld per call",
                     (long long)sets->nsets, kNoAllocMaxSets);
-  if (sets->n_max < 0 || sets->n_max > GPA_NMAX) return gpa_fail(GPA_ERR_RANGE, "gpa_allocate_noalloc: n_max");
+  if (sets->n_max < 0 || sets->n_max > GPA_SERVE_NMAX)
+    return gpa_fail(GPA_ERR_RANGE, "gpa_allocate_noalloc: n_max above %d", GPA_SERVE_NMAX);
   if (model->g < 1 || model->M < 1 || model->M > GPA_MMAX || model->M % model->g != 0 || model->k_c_pm < 1000 ||
       model->k_c_pm > 16000 || model->k_m_pm < 1000 || model->k_m_pm > 16000 ||
       (model->sched != GPA_SCHED_DM && model->sched != GPA_SCHED_EDF))

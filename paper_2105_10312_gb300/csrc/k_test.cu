@@ -6,7 +6,7 @@
 #include "gpa_device.cuh"
 #include "gpa_internal.h"
 
-namespace gpa {
+GPA_NS_BEGIN
 
 namespace {
 
@@ -207,7 +207,7 @@ static size_t test_smem_bytes(int warps) { return sizeof(TestSmem) * (size_t)war
 cudaError_t launch_test_schedulable(const DevSets& s, const DevModel& md, const Cands& c, unsigned char* verdict,
                                     long long* R, unsigned int* err, const MagicDivHost* mdiv, int sm_count,
                                     cudaStream_t st, long long* launches, Prof* prof) {
-  const int warps = 4;  // 4 x sizeof(TestSmem) stays below the 48 KB default
+  const int warps = kNmax > 128 ? 2 : 4;  // warps x sizeof(TestSmem) stays below the 48 KB default
   long long need = (c.ncands + warps - 1) / warps;
   int blocks = (int)(need < (long long)sm_count * 4 ? need : (long long)sm_count * 4);
   if (blocks < 1) blocks = 1;
@@ -220,4 +220,4 @@ cudaError_t launch_test_schedulable(const DevSets& s, const DevModel& md, const 
   return e;
 }
 
-}  // namespace gpa
+GPA_NS_END

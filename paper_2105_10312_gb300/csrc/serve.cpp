@@ -215,7 +215,7 @@ bool form_batch(ServeState* S, StreamCtx& sc, bool* need_slots) {
       blocked.insert(p.tenant);
       ++it;
       continue;
-    } else if (p.op == GPA_SERVE_ADD && ti->second.n >= GPA_NMAX) {
+    } else if (p.op == GPA_SERVE_ADD && ti->second.n >= GPA_SERVE_NMAX) {
       err = GPA_ERR_RANGE;
     } else if (p.op == GPA_SERVE_REMOVE && (p.index < 0 || p.index >= ti->second.n)) {
       err = GPA_ERR_RANGE;
@@ -383,7 +383,7 @@ extern "C" int32_t gpa_serve_start(gpa_ctx* c, const gpa_serve_cfg* cfg) {
   S->md = DevModel{cfg->M, cfg->g, cfg->k_c_pm, cfg->k_m_pm, cfg->sched, 0, nullptr, nullptr};
   S->cfg.sizes = nullptr;  // the list is copied to the device below, not kept by pointer
   S->prm = gpa_params{cfg->policy, cfg->act, 1, 0};
-  S->pay_cap = (int64_t)cfg->max_batch * GPA_NMAX;
+  S->pay_cap = (int64_t)cfg->max_batch * GPA_SERVE_NMAX;
   bool ok = cudaStreamCreateWithFlags(&S->setup_stream, cudaStreamNonBlocking) == cudaSuccess &&
             cudaMalloc(&S->d_chunks, sizeof(TenantSlot*) * kMaxChunks) == cudaSuccess &&
             cudaMemset(S->d_chunks, 0, sizeof(TenantSlot*) * kMaxChunks) == cudaSuccess &&
@@ -447,7 +447,7 @@ extern "C" int32_t gpa_serve_submit(gpa_ctx* c, const gpa_request* r, uint64_t* 
   p.n = 0;
   if (r->op == GPA_SERVE_ADMIT || r->op == GPA_SERVE_ADD) {
     const int n = r->op == GPA_SERVE_ADD ? 1 : r->n;
-    if (n < 0 || n > GPA_NMAX) return gpa_fail(GPA_ERR_RANGE, "gpa_serve_submit: %d tasks", n);
+    if (n < 0 || n > GPA_SERVE_NMAX) return gpa_fail(GPA_ERR_RANGE, "gpa_serve_submit: %d tasks", n);
     if (n > 0 && (!r->T || !r->D || !r->A || !r->B || !r->u_ppm || !r->type))
       return gpa_fail(GPA_ERR_ARG, "gpa_serve_submit: NULL task column");
     for (int i = 0; i < n; i++) {

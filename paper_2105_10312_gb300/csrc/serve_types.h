@@ -17,10 +17,10 @@ constexpr int kMaxChunks = 4096;        // chunk table entries
 // One tenant: its tasks (structure of arrays, original order) and its
 // allocation (partition of each task, size of each partition).
 struct TenantSlot {
-  long long T[GPA_NMAX], D[GPA_NMAX], A[GPA_NMAX], B[GPA_NMAX], u[GPA_NMAX];
-  unsigned char type[GPA_NMAX];
-  unsigned char part[GPA_NMAX];
-  short size[GPA_NMAX];
+  long long T[GPA_SERVE_NMAX], D[GPA_SERVE_NMAX], A[GPA_SERVE_NMAX], B[GPA_SERVE_NMAX], u[GPA_SERVE_NMAX];
+  unsigned char type[GPA_SERVE_NMAX];
+  unsigned char part[GPA_SERVE_NMAX];
+  short size[GPA_SERVE_NMAX];
   int n, n_parts, Pi, pad;
   long long W;
 };
@@ -48,8 +48,8 @@ struct ServeResp {
   int n_tasks, n_parts, Pi;
   long long W;
   int n_tests, pad;
-  unsigned char part[GPA_NMAX];
-  short size[GPA_NMAX];
+  unsigned char part[GPA_SERVE_NMAX];
+  short size[GPA_SERVE_NMAX];
 };
 
 size_t serve_smem_bytes(int warps);

@@ -1,20 +1,20 @@
-"""Data of the paper's §7 experiments on synthetic task sets (Figs. 4 and 5):
+"""Data of the paper's §7 experiments on synthetic task sets (Figs. 4-7):
 per total utilisation U, the schedulability rate, the number of partitions
 and the scheduled (inflated) workload against its bounds, for the 1G
 baseline and the four heuristic variants SMS/BF x ACT/INA, computed on the
 GPU through the library.
 
-    python -m paper_2105_10312_gb300.figures [--sets-per-step 100] [--sched dm|edf] [--out figs.json]
+    python -m paper_2105_10312_gb300.figures [--tasks 50|200] [--sets-per-step 100] [--sched dm|edf]
+                                             [--out figs.json]
 
-The setting is §7's: 68 SMs, 50 tasks per set, U = 2, 4, ..., 68, D = 0.75 T,
+The setting is §7's: 68 SMs, 50 tasks per set (Figs. 4 and 5) or 200 (Figs. 6
+and 7), U = 2, 4, ..., 68, D = 0.75 T,
 periods from the divisors of 4000 in [50, 4000], a 50 % memory-intensive
 ratio, b = 0.02 a (compute) / 0.1 a (memory).  The workload bounds of §7's
 efficiency figure are, per task set, Best = sum_i u_i (every task without
 interference) and Worst = sum_i k_i u_i with the conflict factor of its type
 (every task in conflict); a heuristic's scheduled load of a set it
-allocates is W / 1000 = sum over its partitions of sum_i k_i(P) u_i.  The
-paper's 200-task experiments (Figs. 6 and 7) exceed this library's
-128-task limit per set and are not produced.
+allocates is W / 1000 = sum over its partitions of sum_i k_i(P) u_i.
 """
 from __future__ import annotations
 
@@ -69,16 +69,18 @@ def aggregate(results, best, worst, steps):
     return out
 
 
-def run(sets_per_step=100, sched="DM", device=0):
-    """Allocate the §7 batch with every variant on the GPU; returns the
-    aggregate (see aggregate) plus the U of each step."""
+def run(sets_per_step=100, sched="DM", device=0, tasks=50):
+    """Allocate the §7 batch of `tasks` (50 or 200) tasks per set with every
+    variant on the GPU; returns the aggregate (see aggregate) plus the U of
+    each step."""
     import torch
 
     import paper_2105_10312_gb300 as gpa
     from paper_2105_10312_gb300 import workloads as W
-    p = W.gen_params("paper50", nsets=34 * sets_per_step)
+    name = {50: "paper50", 200: "paper200"}[tasks]
+    p = W.gen_params(name, nsets=34 * sets_per_step)
     s = gpa.gen_tasksets(**p)
-    md = W.model("paper50")
+    md = W.model(name)
     d = gpa.to_device(s, f"cuda:{device}")
     stream = torch.cuda.Stream(device)
     ctx = gpa.Context(device, stream=stream)
@@ -96,16 +98,18 @@ def run(sets_per_step=100, sched="DM", device=0):
                 for j in range(p["U_steps"])]
     agg["sets_per_step"] = sets_per_step
     agg["sched"] = sched
+    agg["tasks"] = tasks
     return agg
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--tasks", type=int, choices=[50, 200], default=50)
     ap.add_argument("--sets-per-step", type=int, default=100)
     ap.add_argument("--sched", choices=["dm", "edf"], default="dm")
     ap.add_argument("--out", default="")
     args = ap.parse_args(argv)
-    agg = run(args.sets_per_step, args.sched.upper())
+    agg = run(args.sets_per_step, args.sched.upper(), tasks=args.tasks)
     text = json.dumps(agg)
     if args.out:
         with open(args.out, "w") as f:

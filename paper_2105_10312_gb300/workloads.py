@@ -19,6 +19,7 @@ evaluation (§7) is synthetic too.
 * ``paper50``  the paper's §7 setting: 68 SMs, 50 tasks, U = 2..68 in steps of 2,
                100 sets per step, D = 0.75 T, periods from the divisors of 4000 in
                [50, 4000], a 50 % memory-kernel ratio, b = 0.02 a / 0.1 a.
+* ``paper200`` the same with 200 tasks per set (the paper's Figs. 6 and 7).
 """
 from __future__ import annotations
 
@@ -49,6 +50,11 @@ WORKLOADS = {
         model=dict(M=148, g=1, k_c_pm=K_C, k_m_pm=K_M)),
     "paper50": dict(
         gen=dict(seed=6, nsets=3400, n_min=50, n_max=50, U_steps=34, U_lo_ppm=2000000, U_hi_ppm=68000000,
+                 T_lo=50, T_hi=4000, T_dist="LIST", deadline_pm=750, mu_dist="UNIFORM", prm_pm=500,
+                 mode="PAPER", beta_c_pm=20, beta_m_pm=100, alpha_lo_pm=0, alpha_hi_pm=0),
+        model=dict(M=68, g=1, k_c_pm=K_C, k_m_pm=K_M)),
+    "paper200": dict(
+        gen=dict(seed=7, nsets=3400, n_min=200, n_max=200, U_steps=34, U_lo_ppm=2000000, U_hi_ppm=68000000,
                  T_lo=50, T_hi=4000, T_dist="LIST", deadline_pm=750, mu_dist="UNIFORM", prm_pm=500,
                  mode="PAPER", beta_c_pm=20, beta_m_pm=100, alpha_lo_pm=0, alpha_hi_pm=0),
         model=dict(M=68, g=1, k_c_pm=K_C, k_m_pm=K_M)),

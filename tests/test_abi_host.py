@@ -122,3 +122,16 @@ def test_generator_is_deterministic_and_shaped():
         o, e = a["set_off"][s], a["set_off"][s + 1]
         U = (C1[o:e] / T[o:e]).sum()
         assert abs(U - 0.1 * (s % 60 + 1)) < 0.02 * (e - o) / 10 + 0.01
+
+
+def test_task_limits():
+    """Sets of up to 256 tasks pass the host check and the generator; 257
+    do not (the serving tenants' 128-task limit is checked on the GPU)."""
+    t = gpa.gen_tasksets(seed=1, nsets=3, n_min=256, n_max=256)
+    assert np.array_equal(np.diff(t["set_off"]), [256, 256, 256])
+    assert gpa.validate(t, M=512) == (0, -1)
+    t["n_max"] = 257
+    assert gpa.validate(t, M=512)[0] == gpa.ERR_RANGE
+    with pytest.raises(ValueError):
+        gpa.gen_tasksets(seed=1, nsets=2, n_min=1, n_max=257)
+    assert gpa.NMAX == 256 and gpa.SERVE_NMAX == 128

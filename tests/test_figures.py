@@ -50,3 +50,18 @@ def test_figure_data_matches_oracle_aggregation():
         v = agg["variants"][name]
         assert all(a >= b for a, b in zip(v["rate"], agg["variants"]["1G"]["rate"]))
         assert all(r is None or -1e-9 <= r <= 1 + 1e-9 for r in v["load_in_bounds"])
+
+
+@pytest.mark.gpu
+def test_figure_data_200_tasks():
+    """Figs. 6 and 7's setting (200 tasks per set, 256-task build), one set per
+    U step: the rates are fractions, the heuristics schedule at least what 1G
+    does, and the scheduled load of each allocated set lies in its bounds."""
+    agg = figures.run(sets_per_step=1, tasks=200)
+    assert agg["tasks"] == 200 and len(agg["U"]) == 34
+    for name in ("SMS_ACT", "SMS_INA", "BF_ACT", "BF_INA"):
+        v = agg["variants"][name]
+        assert all(r is None or 0.0 <= r <= 1.0 for r in v["rate"])
+        assert all(a >= b for a, b in zip(v["rate"], agg["variants"]["1G"]["rate"]))
+        assert all(r is None or -1e-9 <= r <= 1 + 1e-9 for r in v["load_in_bounds"])
+    assert agg["variants"]["SMS_INA"]["rate"][0] == 1.0
