@@ -489,6 +489,55 @@ int32_t gpa_serve_stop(gpa_ctx* ctx);
 int32_t gpa_serve_stats(gpa_ctx* ctx, int64_t* completed, int64_t* batches, int64_t* max_batch,
                         int64_t* overlapped, int64_t* slots);
 
+/* ---------------------------------------------- measured WCET curves (§3)
+ *
+ * The execution time C(m) of a kernel on m SMs, measured as §3 describes for
+ * Fig. 1: a blocker kernel takes sm_count - m SMs (one CTA per SM, each
+ * holding the whole 227 KB of opt-in shared memory so that no other CTA fits
+ * beside it) for a fixed time window, and the kernel under test, launched on
+ * another stream, runs on the m SMs left.  With `interfere` set the blocker
+ * streams a 1 GB buffer from HBM meanwhile, the memory-intensive co-runner
+ * of §3.3, so that C_interfered(m) / C(m) estimates the interference factor
+ * k of the kernel's type.  Every CTA records its SM (%smid): a measurement
+ * counts only if the two kernels ran on disjoint SMs, the kernel under test
+ * on exactly m of them, and it finished inside the blocker's window; a
+ * repetition that fails this is retried (at most 3 times per repetition).
+ * No kernel waits on another: the blocker's window is a %globaltimer bound.
+ *
+ * Kernels under test, written from the published definitions of those §3
+ * used (vector add, transpose, hotspot-like stencil) plus an FMA loop:
+ * GPA_PROBE_VADD (n floats), GPA_PROBE_TRANSPOSE (n x n floats through 32 x
+ * 32 tiles), GPA_PROBE_STENCIL (one 5-point sweep of an n x n grid),
+ * GPA_PROBE_COMPUTE (64 dependent FMAs per each of n floats). */
+enum { GPA_PROBE_VADD = 0, GPA_PROBE_TRANSPOSE = 1, GPA_PROBE_STENCIL = 2, GPA_PROBE_COMPUTE = 3 };
+
+typedef struct {
+  int32_t kernel;     /* GPA_PROBE_* */
+  int32_t interfere;  /* 0: the blocked SMs idle; 1: they stream HBM */
+  int64_t n;          /* problem size: elements (VADD, COMPUTE) or matrix side (TRANSPOSE, STENCIL) */
+  int32_t reps;       /* timed repetitions per m (the median is reported), 1..100 */
+  int32_t ctas;       /* CTAs of the kernel under test (0: 4 per SM of the whole GPU) */
+} gpa_probe_cfg;
+
+/* For each m[i] (1 <= m[i] <= the device's SM count): ms[i] = median device
+ * time (CUDA events on the kernel's stream) of the kernel under test on
+ * m[i] SMs, sms_used[i] = the SMs it ran on (m[i]), or ms[i] = -1 and
+ * sms_used[i] = -1 when no repetition passed the placement check.  Device
+ * buffers (3 arrays of the problem, 1 GB with `interfere`) are allocated
+ * and freed by the call; it is synchronous and uses its own two streams.
+ * Errors: GPA_ERR_ARG (NULL, bad kernel or counts), GPA_ERR_RANGE (n, m or
+ * reps out of range: n in [1, 2^28] elements, side in [32, 16384]),
+ * GPA_ERR_NOMEM, GPA_ERR_CUDA. */
+int32_t gpa_measure_wcet(gpa_ctx* ctx, const gpa_probe_cfg* cfg, const int32_t* m, int32_t nm, double* ms,
+                         int32_t* sms_used);
+
+/* Least-squares fit of C(m) = a / m + b (§3.3's model without interference;
+ * in the task model of this header, with times in microseconds, A = 1000 a
+ * and B = 1000 b) to n points (m[i], ms[i]); points with ms[i] < 0 are
+ * skipped.  Errors: GPA_ERR_ARG (NULL, fewer than two usable points or all
+ * at one m). */
+int32_t gpa_fit_wcet(const int32_t* m, const double* ms, int32_t n, double* a, double* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -474,3 +474,43 @@ class Server:
         if self.running:
             _check(lib().gpa_serve_stop(self.ctx.handle))
             self.running = False
+
+
+# ------------------------------------------------- measured WCET curves (§3)
+
+PROBE = {"VADD": 0, "TRANSPOSE": 1, "STENCIL": 2, "COMPUTE": 3}
+
+
+class ProbeCfg(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("interfere", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("reps", ctypes.c_int32), ("ctas", ctypes.c_int32)]
+
+
+def _probe_sigs(L):
+    L.gpa_measure_wcet.argtypes = [_vp, ctypes.POINTER(ProbeCfg), _vp, ctypes.c_int32, _vp, _vp]
+    L.gpa_fit_wcet.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double)]
+
+
+def measure_wcet(ctx, kernel, m, n, reps=5, interfere=False, ctas=0):
+    """gpa_measure_wcet: median device time (ms) of probe `kernel` on each m
+    SMs (the rest held by the blocker, idle or streaming HBM), and the SMs it
+    ran on (-1 where no repetition passed the placement check)."""
+    _probe_sigs(lib())
+    mm = np.ascontiguousarray(m, dtype=np.int32)
+    ms = np.zeros(len(mm), np.float64)
+    used = np.zeros(len(mm), np.int32)
+    cfg = ProbeCfg(PROBE[kernel], 1 if interfere else 0, int(n), int(reps), int(ctas))
+    _check(lib().gpa_measure_wcet(ctx.handle, ctypes.byref(cfg), mm.ctypes.data, len(mm), ms.ctypes.data,
+                                  used.ctypes.data))
+    return ms, used
+
+
+def fit_wcet(m, ms):
+    """gpa_fit_wcet: least squares of ms = a / m + b; returns (a, b)."""
+    _probe_sigs(lib())
+    mm = np.ascontiguousarray(m, dtype=np.int32)
+    t = np.ascontiguousarray(ms, dtype=np.float64)
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().gpa_fit_wcet(mm.ctypes.data, t.ctypes.data, len(mm), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value

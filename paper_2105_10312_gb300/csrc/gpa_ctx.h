@@ -56,6 +56,20 @@ struct gpa_ctx {
   ServeState* serve = nullptr;
 };
 
+// Makes `dev` the current device for the scope, then restores the previous one.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
 int32_t gpa_fail(int32_t code, const char* fmt, ...);
 int32_t gpa_cuda_fail(cudaError_t e, const char* what);
 void* ctx_buffer(gpa_ctx* c, int slot, size_t bytes);

@@ -66,6 +66,20 @@ struct StageList {
 };
 cudaError_t launch_stage_copy(const StageList& L, int blocks_per_range, cudaStream_t st, long long* launches);
 
+// Measured WCET curves (k_probe.cu): the buffers of the kernel under test,
+// the blocker that holds sm_count - m SMs, and the kernels' launchers.
+struct ProbeBuffers {
+  float* a;
+  float* b;
+  float* c;
+};
+size_t probe_blocker_smem();
+cudaError_t probe_kernels_init();
+cudaError_t launch_probe_blocker(int ctas, unsigned long long window_ns, const void* buf, unsigned long long buf_bytes,
+                                 unsigned int* smid, unsigned long long* t_end, float* sink, cudaStream_t st);
+cudaError_t launch_probe_kernel(int kernel, int ctas, const ProbeBuffers& b, unsigned long long n,
+                                unsigned int* smid, unsigned long long* t_done, cudaStream_t st);
+
 // Work-queue state of the persistent allocate kernels.
 struct AllocQueue {
   unsigned long long* counters;  // [4]: fast ticket, slow count, slow ticket, 1G ticket

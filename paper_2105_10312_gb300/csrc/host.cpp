@@ -245,19 +245,6 @@ static void build_mdiv(std::vector<MagicDivHost>& t) {
   }
 }
 
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    cudaGetDevice(&prev);
-    if (prev != dev) cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    cudaGetDevice(&cur);
-    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-  }
-};
-
 extern "C" int32_t gpa_ctx_create(int32_t device, void* stream, gpa_ctx** out) {
   if (!out) return gpa_fail(GPA_ERR_ARG, "gpa_ctx_create: out is NULL");
   *out = nullptr;
