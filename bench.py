@@ -61,14 +61,20 @@ def read_peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash():
-    """Hash of every kernel source (the .cu files and device headers)."""
+# the sources each profiled kernel is compiled from
+KERNEL_SOURCES = {
+    "alloc": ("k_alloc.cu", "alloc_dev.cuh", "gpa_device.cuh", "bulk_pipe.cuh", "gpa_ns.h", "gpa_internal.h"),
+    "search": ("k_search.cu", "gpa_device.cuh", "gpa_ns.h", "gpa_internal.h"),
+}
+
+
+def kernel_source_hash(kernel="alloc_fast"):
+    """Hash of the sources `kernel` is compiled from."""
     d = os.path.join(ROOT, "paper_2105_10312_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")) or f == "gpa_ns.h":
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(fh.read())
+    for f in KERNEL_SOURCES["search" if kernel == "search_sets" else "alloc"]:
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -87,7 +93,7 @@ def recorded_profile(kernel, workload):
         return None
     text = open(path).read()
     h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
-    if not h or h.group(1) != kernel_source_hash():
+    if not h or h.group(1) != kernel_source_hash(kernel):
         return None
     out = {"source": "profiles/" + name}
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.]+)", text)
@@ -411,6 +417,31 @@ def run_gpu(args):
     def flush_l2(i):
         flush.fill_(i)
         return flush_rd.sum()
+
+    def read_floor(nbytes, kernel_ms, reps=20):
+        """The same-size reference for the roofline: one streaming read of
+        the kernel's read bytes (torch's int64 sum over a buffer of that
+        size, L2 flushed first, CUDA events on the same stream).  The peak
+        above is a large copy; a ~100 MB launch also pays the launch, the
+        ramp to full DRAM throughput and the tail."""
+        buf = torch.ones(max(1, nbytes // 8), dtype=torch.int64, device=dev)
+        ts = []
+        with torch.cuda.stream(stream):
+            for i in range(reps + 3):
+                flush_l2(i)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                buf.sum()
+                e1.record(stream)
+                e1.synchronize()
+                if i >= 3:
+                    ts.append(e0.elapsed_time(e1))
+        f = float(np.median(ts))
+        del buf
+        return {"what": "torch int64 sum over a buffer of the kernel's read bytes (one streaming read), "
+                        "L2 flushed first, CUDA events on the same stream; median of %d" % reps,
+                "bytes": nbytes, "ms": f, "gbs": nbytes / (f / 1000.0) / 1e9, "kernel_ms_over_floor_ms": kernel_ms / f}
     kc, km = md["k_c_pm"], md["k_m_pm"]
 
     if args.workload == "exhaustive":
@@ -548,7 +579,7 @@ def run_gpu(args):
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                 "traffic": prof["traffic"] if prof else None, "kernel": "alloc_fast",
                 "kernel_ms": k_ms, "algorithmic_bytes": alg_bytes, "peak_source": peak_src + " hbm_gbs",
-                "kernel_timing": timing}
+                "kernel_timing": timing, "size_floor": read_floor(44 * ntasks + 8 * nsets, k_ms)}
     elif kern_ms:
         kernel, ms = ("search_sets", k_ms) if args.workload == "exhaustive" else \
             ("one_gpu", k_ms) if policy == "ONE_GPU" else ("alloc_merge", k2_ms)
