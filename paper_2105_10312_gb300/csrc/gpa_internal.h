@@ -150,10 +150,21 @@ size_t slow_smem_bytes(int warps_per_block);
 size_t staged_smem_bytes(int stages);
 size_t one_gpu_smem_bytes(int warps_per_block);
 
-// The same allocate and candidate-test kernels built for sets of up to 256
-// tasks (k_alloc_wide.cu, k_test_wide.cu); the host uses them when a batch's
-// n_max exceeds kNarrowNmax.
+// The same allocate kernels built for sets of up to 64 tasks
+// (k_alloc_small.cu), used when a batch's n_max is at most kSmallNmax, and
+// the allocate and candidate-test kernels built for up to 256 tasks
+// (k_alloc_wide.cu, k_test_wide.cu), used when it exceeds kNarrowNmax.
+constexpr int kSmallNmax = 64;
 constexpr int kNarrowNmax = 128;
+namespace small {
+cudaError_t launch_allocate(const DevSets& s, const DevModel& md, const gpa_params& p, const AllocOut& out,
+                            const AllocQueue& q, const MagicDivHost* mdiv, const LaunchShape& fast,
+                            const LaunchShape& slow, cudaStream_t st, long long* launches, Prof* prof);
+cudaError_t launch_one_gpu(const DevSets& s, const DevModel& md, const AllocOut& out, const AllocQueue& q,
+                           const MagicDivHost* mdiv, const LaunchShape& shape, cudaStream_t st, long long* launches,
+                           Prof* prof);
+cudaError_t alloc_kernels_init();
+}  // namespace small
 namespace wide {
 cudaError_t launch_allocate(const DevSets& s, const DevModel& md, const gpa_params& p, const AllocOut& out,
                             const AllocQueue& q, const MagicDivHost* mdiv, const LaunchShape& fast,

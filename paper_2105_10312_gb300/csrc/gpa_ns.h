@@ -2,18 +2,29 @@
 //
 // The allocate and candidate-test kernels keep per-set state in shared memory
 // and per-lane task masks in registers, both sized by the task capacity.
-// They are compiled twice: for sets of up to 128 tasks in namespace gpa, and,
-// with GPA_WIDE defined (k_alloc_wide.cu, k_test_wide.cu), for up to
-// GPA_NMAX = 256 tasks in namespace gpa::wide.  The host picks the build by
-// the batch's n_max, so batches of at most 128 tasks keep the smaller
-// register and shared-memory budget.
+// They are compiled for sets of up to 128 tasks in namespace gpa; the
+// allocate kernels also, with GPA_SMALL defined (k_alloc_small.cu), for up to
+// 64 tasks in namespace gpa::small, and both, with GPA_WIDE defined
+// (k_alloc_wide.cu, k_test_wide.cu), for up to GPA_NMAX = 256 tasks in
+// namespace gpa::wide.  The host picks the build by the batch's n_max, so a
+// batch pays only for the capacity it uses: more merge warps fit on an SM
+// with the 64-task state, and batches of at most 128 tasks never carry the
+// 256-task state.
 #pragma once
 
-#ifdef GPA_WIDE
+#if defined(GPA_WIDE)
 #define GPA_KNMAX 256
 #define GPA_NS_BEGIN \
   namespace gpa {    \
   namespace wide {
+#define GPA_NS_END \
+  }                \
+  }
+#elif defined(GPA_SMALL)
+#define GPA_KNMAX 64
+#define GPA_NS_BEGIN \
+  namespace gpa {    \
+  namespace small {
 #define GPA_NS_END \
   }                \
   }

@@ -281,6 +281,7 @@ extern "C" int32_t gpa_ctx_create(int32_t device, void* stream, gpa_ctx** out) {
   std::call_once(once, [] {
     init_err = alloc_kernels_init();
     if (init_err == cudaSuccess) init_err = wide::alloc_kernels_init();
+    if (init_err == cudaSuccess) init_err = small::alloc_kernels_init();
     if (init_err == cudaSuccess) init_err = search_kernels_init();
   });
   if (init_err != cudaSuccess) {
@@ -729,22 +730,32 @@ std::string tune_key(const DevSets& ds, const DevModel& md, const gpa_params& p)
   return buf;
 }
 
-// The kernels of the batch's task capacity: the 128-task build, or the
-// 256-task build when n_max exceeds 128.
+// The launchers of the batch's task capacity: the 64-task build when n_max
+// is at most 64, the 256-task build when it exceeds 128, else the 128-task
+// build.
+using AllocLauncher = cudaError_t (*)(const DevSets&, const DevModel&, const gpa_params&, const AllocOut&,
+                                      const AllocQueue&, const MagicDivHost*, const LaunchShape&, const LaunchShape&,
+                                      cudaStream_t, long long*, Prof*);
+static AllocLauncher allocate_launcher(int n_max) {
+  return n_max > kNarrowNmax ? wide::launch_allocate : n_max <= kSmallNmax ? small::launch_allocate : launch_allocate;
+}
+
 static cudaError_t run_allocate(gpa_ctx* c, const DevSets& ds, const DevModel& md, const gpa_params& p,
                                 const AllocOut& out, const LaunchShape& fast, Prof* prof) {
   AllocQueue q{c->d_counters, c->d_slow, c->d_err};
-  const bool wide_sets = ds.n_max > kNarrowNmax;
+  const bool wide_sets = ds.n_max > kNarrowNmax, small_sets = ds.n_max <= kSmallNmax;
   if (p.policy == GPA_POLICY_ONE_GPU) {
     LaunchShape sh{8, 1, c->sm_count * 4, 1};
-    return (wide_sets ? wide::launch_one_gpu : launch_one_gpu)(ds, md, out, q, c->d_mdiv, sh, c->stream,
-                                                                &c->launches, prof);
+    return (wide_sets ? wide::launch_one_gpu : small_sets ? small::launch_one_gpu : launch_one_gpu)(
+        ds, md, out, q, c->d_mdiv, sh, c->stream, &c->launches, prof);
   }
-  // merge kernel of the 256-task build: 58 KB of shared memory per warp, so
-  // one warp per CTA and three CTAs per SM
-  const LaunchShape slow = wide_sets ? LaunchShape{1, 1, c->sm_count * 3, 1} : default_slow(c);
-  return (wide_sets ? wide::launch_allocate : launch_allocate)(ds, md, p, out, q, c->d_mdiv, fast, slow, c->stream,
-                                                                &c->launches, prof);
+  // merge kernel: the 256-task build keeps 58 KB of shared memory per warp
+  // (one warp per CTA, three CTAs per SM); the 64-task build 10 KB and 128
+  // registers per thread (two warps per CTA, eight CTAs per SM)
+  const LaunchShape slow = wide_sets    ? LaunchShape{1, 1, c->sm_count * 3, 1}
+                           : small_sets ? LaunchShape{2, 1, c->sm_count * 8, 1}
+                                        : default_slow(c);
+  return allocate_launcher(ds.n_max)(ds, md, p, out, q, c->d_mdiv, fast, slow, c->stream, &c->launches, prof);
 }
 
 // Autotuner: time the candidate shapes of the fast kernel on this batch
@@ -821,8 +832,8 @@ static int32_t allocate_device(gpa_ctx* c, const DevSets& ds, const DevModel& md
       LaunchShape one_shape{1, 1, 1, 1};
       AllocQueue q{c->d_counters, c->d_slow, c->d_err};
       LaunchShape slow1{1, 1, 1, 1};
-      cudaError_t e = (one.n_max > kNarrowNmax ? wide::launch_allocate : launch_allocate)(
-          one, md, p, o1, q, c->d_mdiv, one_shape, slow1, c->stream, &c->launches, nullptr);
+      cudaError_t e = allocate_launcher(one.n_max)(one, md, p, o1, q, c->d_mdiv, one_shape, slow1, c->stream,
+                                                   &c->launches, nullptr);
       if (e != cudaSuccess) return gpa_cuda_fail(e, "per-set allocate launch");
     }
     return GPA_OK;

@@ -93,20 +93,23 @@ def test_wide_candidates_match_oracle(ctx, sched):
     assert 0 < vr.sum() < nc
 
 
-def test_builds_agree_at_the_switch(ctx):
-    """Sets of at most 128 tasks declared with n_max 128 (the 128-task build)
-    and with n_max 129 and 256 (the 256-task build): identical results, equal
+@pytest.mark.parametrize("n_top,n_maxes,policy", [(128, (128, 129, 256), "SMS"), (64, (64, 65, 128, 256), "SMS"),
+                                                  (64, (64, 65, 256), "ONE_GPU")])
+def test_builds_agree_at_the_switch(ctx, n_top, n_maxes, policy):
+    """Sets of at most n_top tasks declared with every n_max that selects a
+    different build (64-task, 128-task, 256-task): identical results, equal
     to the oracle's."""
-    s = gpa.gen_tasksets(seed=98, nsets=600, n_min=0, n_max=128, U_lo_ppm=500000, U_hi_ppm=20000000,
+    s = gpa.gen_tasksets(seed=98, nsets=600, n_min=0, n_max=n_top, U_lo_ppm=500000, U_hi_ppm=20000000,
                          deadline_pm=750, mu_dist="BETA25", T_lo=1000, T_hi=100000)
     M, g = 96, 2
-    ref = oracle.allocate(s, M, g, KC, KM, policy="SMS", act=True, nthreads=8)
-    for n_max in (128, 129, 256):
+    act = policy != "ONE_GPU"
+    ref = oracle.allocate(s, M, g, KC, KM, policy=policy, act=act, nthreads=8)
+    for n_max in n_maxes:
         d = gpa.to_device(s)
         d["n_max"] = n_max
-        out = ctx.allocate(d, M, g=g, k_c_pm=KC, k_m_pm=KM, policy="SMS", act=True)
+        out = ctx.allocate(d, M, g=g, k_c_pm=KC, k_m_pm=KM, policy=policy, act=act)
         ctx.sync()
-        _assert_equal(out, ref, ALLOC_KEYS, f"n_max={n_max}")
+        _assert_equal(out, ref, ALLOC_KEYS, f"n_max={n_max} {policy}")
 
 
 def test_wide_limits(ctx):
