@@ -241,8 +241,15 @@ def cpu_baseline_oracle(sets, md, workload, policy, act, target_wall=2.0, max_wa
     if workload == "paper200":
         what = (f"{n} of the batch's U = 2 sets (the oracle's time per 200-task set grows to minutes at "
                 f"high U)")
+    # the same oracle on one thread, on a sample of about a second
+    sub1, n1 = oracle_sample(sets, md, workload, policy, act, 1, 1.0)
+    t1 = time.perf_counter()
+    oracle_step(sub1, md, workload, policy, act, 1)
+    el1 = time.perf_counter() - t1
     return {"value": passes * n / el, "unit": "tasksets/s", "cores": threads, "kind": "oracle",
-            "sample": f"{passes} pass(es) over {what}, {threads} threads, {el:.2f} s wall"}
+            "sample": f"{passes} pass(es) over {what}, {threads} threads, {el:.2f} s wall",
+            "single_thread": {"value": n1 / el1, "unit": "tasksets/s",
+                              "sample": f"one pass over {n1} sets, 1 thread, {el1:.2f} s wall"}}
 
 
 def serve_bench(local, rates=(2000, 5000, 10000, 20000, 50000), duration=0.5, plain=False, population=512,
