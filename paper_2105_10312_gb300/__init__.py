@@ -3,7 +3,8 @@
 A thin ctypes binding over ``libgpa.so`` (the C ABI declared in ``include/gpa.h``).
 Every step of the computation runs in the library's CUDA kernels; this module
 only marshals arguments: torch CUDA tensors go in as device pointers (GPA_DEVICE),
-numpy arrays as host pointers (GPA_HOST, validated on the host, synchronous).
+numpy arrays as host pointers (GPA_HOST: copied in and checked on the device,
+synchronous).
 
 The first call into the library raises ImportError if ``libgpa.so`` has not
 been built (``python -c "import __graft_entry__ as g; g.build()"``): there is
