@@ -604,11 +604,15 @@ def run_gpu(args):
         kernel, ms = ("search_sets", k_ms) if args.workload == "exhaustive" else \
             ("one_gpu", k_ms) if policy == "ONE_GPU" else ("alloc_merge", k2_ms)
         prof = recorded_profile(kernel, args.workload)
+        alu = prof.get("alu_pipe_pct") if prof else None
         roof = {"bound": "alu", "kernel": kernel, "kernel_ms": ms, "achieved": None, "peak": None, "unit": None,
-                "frac": None, "traffic": prof["traffic"] if prof else None, "kernel_timing": timing,
-                "ncu": prof,
+                "frac": alu / 100.0 if alu is not None else None,
+                "frac_source": "ncu sm__pipe_alu_cycles_active (fraction of the integer ALU pipe's peak) from the "
+                               "committed summary of this kernel, taken on the current sources" if alu is not None
+                               else None,
+                "traffic": prof["traffic"] if prof else None, "kernel_timing": timing, "ncu": prof,
                 "note": "serial integer fixed-point chains (one warp or thread per set, subset or candidate); "
-                        "no live ALU-throughput figure: see the ncu ALU pipe and issue percentages"}
+                        "no live ALU-throughput figure, so achieved and peak stay empty"}
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     e2e = None
