@@ -130,3 +130,21 @@ def test_wide_limits(ctx):
         ctx.sync()
     assert ei.value.code == gpa.ERR_RANGE
     assert _np(out["reason"])[int(np.argmax(n))] == gpa.REASON["INVALID"]
+
+
+@pytest.mark.parametrize("slices,copy", [(3, 0), (2, 1)])
+def test_wide_sets_through_sliced_host_buffers(ctx, slices, copy):
+    """120..256-task sets (the 256-task build) from page-locked host buffers
+    split into slices, by the staging kernel and by copies."""
+    s = _random_wide(95)
+    hs = {k: (torch.from_numpy(v).pin_memory().numpy() if isinstance(v, np.ndarray) else v) for k, v in s.items()}
+    M, g = 256, 2
+    ref = oracle.allocate(s, M, g, KC, KM, policy="SMS", act=True, nthreads=8)
+    ctx.set_option("HOST_SLICES", slices)
+    ctx.set_option("HOST_COPY", copy)
+    try:
+        out = ctx.allocate(hs, M, g=g, k_c_pm=KC, k_m_pm=KM, policy="SMS", act=True)
+    finally:
+        ctx.set_option("HOST_SLICES", 0)
+        ctx.set_option("HOST_COPY", 0)
+    _assert_equal(out, ref, ALLOC_KEYS, f"wide sliced={slices} copy={copy}")
