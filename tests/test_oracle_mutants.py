@@ -41,6 +41,14 @@ MUTANTS = [
     ("EDF single task needs slack", "if (k == 1) return C[idx[0]] <= s->D[idx[0]];",
      "if (k == 1) return C[idx[0]] < s->D[idx[0]];"),
     ("sizes ignore the unit g", "if (md->nsizes == 0) return m % md->g == 0;", "if (md->nsizes == 0) return 1;"),
+    ("EDF demand equal to t fails", "      if (dbf > t) return 0;", "      if (dbf >= t) return 0;"),
+    ("EDF demand counts tasks not yet due", "if (s->D[j] <= t) dbf +=", "if (1) dbf +="),
+    ("EDF utilisation band rounded down", "uhi += (((i128)C[i] << 32) + s->T[i] - 1) / s->T[i];",
+     "uhi += ((i128)C[i] << 32) / s->T[i];"),
+    ("EDF band at U < 1 - 2^-12", "if (uhi > ((i128)1 << 32) - ((i128)1 << 22)) return 0;",
+     "if (uhi > ((i128)1 << 32) - ((i128)1 << 20)) return 0;"),
+    ("EDF busy period by floor", "next += ((L + s->T[i] - 1) / s->T[i]) * (i128)C[i];",
+     "next += (L / s->T[i]) * (i128)C[i];"),
 ]
 
 

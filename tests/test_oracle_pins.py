@@ -256,6 +256,21 @@ def test_edf_matches_edf_simulation():
     assert ok > 150 and miss > 150 and band > 5
 
 
+def test_edf_band_rounds_each_term_up():
+    """The band sums ceil(2^32 C_i / T_i) (the reading), not floors: for this
+    pair the floored sum is 2^32 - 2^22 - 1 and the rounded-up sum one above
+    the bound, so the pair is reported as a miss; one unit of C less passes
+    (D = T and U < 1: the demand test itself passes)."""
+    T = np.array([1329, 1048573], np.int64)
+    for C2, want in ((523657, 0), (523656, 1)):
+        C = np.array([664, C2], np.int64)
+        floor_sum = sum((int(c) << 32) // int(t) for c, t in zip(C, T))
+        assert _edf_band(C, T) == (want == 0) and floor_sum <= (1 << 32) - (1 << 22)
+        v = oracle.edf(T, T.copy(), 1000 * C, np.zeros(2, np.int64), np.zeros(2, np.uint8), np.ones(2, np.uint8),
+                       1, 1000, 1000)
+        assert v == want, (C2, v)
+
+
 def test_edf_implicit_deadlines_utilisation_bound():
     """Liu & Layland: with D = T, EDF meets every deadline iff U <= 1 (sets
     in the band around U = 1 excepted, where the reading reports a miss)."""
