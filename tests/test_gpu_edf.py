@@ -163,8 +163,13 @@ def test_edf_utilisation_band_edges(ctx):
         sets.append([(T1, 999999, C1), (T2, T2, C2)])
     for dc in range(-30, 31, 3):
         sets.append([(3 * 1000003, 3 * 1000003, 1500000 + dc), (2000000, 1999000, 998000)])
+    # floored and rounded-up band sums straddling the bound by one unit: a miss,
+    # and one unit of C less passes
+    for c2 in (523657, 523656):
+        sets.append([(1329, 1329, 664), (1048573, 1048573, c2)])
     v = _edf_candidate_parity(ctx, _crafted_batch(sets))
     assert 0 < v.sum() < len(v)
+    assert list(v[-2:]) == [0, 1]
 
 
 def test_edf_busy_period_beyond_31_bits(ctx):
