@@ -23,6 +23,8 @@ import itertools
 import math
 from fractions import Fraction
 
+import numpy as np
+
 
 def wcet_alpha(C1, alpha_pm, k_pm, m):
     """ceil(k C1 (alpha + (1 - alpha) / m)) with alpha = alpha_pm / 1000 (exact)."""
@@ -220,3 +222,91 @@ def exhaustive_bruteforce(n, M, g, kmin, kmax, passes, minsize, W, sizes=None):
                 if best is None or key < best:
                     best = key
     return best
+
+
+# ------------------------------------------------------- serving, restated
+
+_SCOLS = ("T", "D", "A", "B", "u_ppm", "type")
+
+
+def _passes(cols, rows, m, kc, km):
+    import oracle
+    n = len(cols["T"])
+    mask = np.zeros(n, np.uint8)
+    mask[list(rows)] = 1
+    return oracle.rta(*[cols[k] for k in ("T", "D", "A", "B", "type")], mask, m, kc, km)[0] == 1
+
+
+def _smallest(cols, rows, lo, hi, g, kc, km):
+    """Smallest multiple of g in [lo, hi] at which the rows pass, else 0."""
+    m = -(-lo // g) * g
+    while m <= hi:
+        if _passes(cols, rows, m, kc, km):
+            return m
+        m += g
+    return 0
+
+
+def _canonical(part, size):
+    """Partitions renumbered in the order of their lowest task index."""
+    order = []
+    for p in part:
+        if p not in order:
+            order.append(int(p))
+    new = {p: k for k, p in enumerate(order)}
+    return [new[int(p)] for p in part], [size[p] for p in order]
+
+
+def serve_add(tasks, part, size, task, M, g, kc, km, policy="SMS", act=False):
+    """ADD of one task to a tenant's allocation, restated: the first
+    partition (in order) that still passes at its size takes it (FIT); else
+    the first that passes after growing into the spare SMs, at its smallest
+    such size (GROW); else a new partition of the task's Lemma 2 size if the
+    spare SMs hold it (NEW); else Alg. 1 on every task (REALLOC); else the
+    request is rejected and the state is unchanged.  Returns (path, tasks,
+    part, size) with path 1..4, or (0, ...) with the old state."""
+    import oracle
+    cols = {k: np.concatenate([tasks[k], np.asarray([task[k]], tasks[k].dtype)]) for k in _SCOLS}
+    n = len(tasks["T"])
+    part, size = [int(p) for p in part], [int(z) for z in size]
+    spare = M - sum(size)
+    members = [[i for i in range(n) if part[i] == p] + [n] for p in range(len(size))]
+    for p, rows in enumerate(members):
+        if _passes(cols, rows, size[p], kc, km):
+            return 1, cols, part + [p], size
+    if spare >= g:
+        for p, rows in enumerate(members):
+            m = _smallest(cols, rows, size[p] + 1, size[p] + spare, g, kc, km)
+            if m:
+                size2 = list(size)
+                size2[p] = m
+                return 2, cols, part + [p], size2
+    z = _smallest(cols, [n], g, M, g, kc, km)
+    if z and z <= spare:
+        return 3, cols, part + [len(size)], size + [z]
+    one = {k: cols[k] for k in _SCOLS}
+    one["set_off"] = np.array([0, n + 1], np.int64)
+    r = oracle.allocate(one, M, g, kc, km, policy=policy, act=act)
+    if r["verdict"][0]:
+        k = int(r["n_parts"][0])
+        return 4, cols, [int(p) for p in r["part_of_task"]], [int(z) for z in r["size_of_part"][:k]]
+    return 0, tasks, part, size
+
+
+def serve_remove(tasks, part, size, index, g, kc, km):
+    """REMOVE of task `index`, restated: its partition disappears if it was
+    the last task there, else shrinks to the smallest passing size at or
+    below its size; partitions are then renumbered by lowest task index."""
+    keep = [i for i in range(len(tasks["T"])) if i != index]
+    cols = {k: tasks[k][keep] for k in _SCOLS}
+    part2 = [int(part[i]) for i in keep]
+    size2 = [int(z) for z in size]
+    pr = int(part[index])
+    if pr in part2:
+        rows = [i for i, p in enumerate(part2) if p == pr]
+        size2[pr] = _smallest(cols, rows, g, size2[pr], g, kc, km)
+    else:
+        part2 = [p - 1 if p > pr else p for p in part2]
+        del size2[pr]
+    part2, size2 = _canonical(part2, size2)
+    return cols, part2, size2

@@ -49,6 +49,11 @@ MUTANTS = [
      "if (uhi > ((i128)1 << 32) - ((i128)1 << 20)) return 0;"),
     ("EDF busy period by floor", "next += ((L + s->T[i] - 1) / s->T[i]) * (i128)C[i];",
      "next += (L / s->T[i]) * (i128)C[i];"),
+    ("serving GROW leaves one spare SM unused", "size_in[p] + 1, size_in[p] + spare);",
+     "size_in[p] + 1, size_in[p] + spare - 1);"),
+    ("serving NEW ignores the spare SMs", "if (z && z <= spare) { part_out[nw]", "if (z) { part_out[nw]"),
+    ("serving REMOVE keeps the size", "size_out[pr] = (int16_t)minm_linear(&s, &md, in, g, size_in[pr]);",
+     "size_out[pr] = size_in[pr];"),
 ]
 
 

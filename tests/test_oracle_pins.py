@@ -807,3 +807,54 @@ def test_serving_add_into_empty_tenant_takes_lemma2_size():
     r = t.remove(0)
     assert r["n_tasks"] == 1 and r["n_parts"] == 1
     _check_state(t, 8, 1)
+
+
+def test_serving_paths_match_a_restatement():
+    """ADD and REMOVE of the oracle's tenant against refs.serve_add /
+    serve_remove (the FIT, GROW, NEW, REALLOC order and ranges restated over
+    the pinned per-partition test): same path, partitions and sizes after
+    every request of seeded sequences."""
+    import serve_seq
+    M, g = 148, 1
+    paths = set()
+    for seq in serve_seq.make_ops(12, 25, seed=3):
+        t = oracle.Tenant(M, g, KC, KM)
+        if not t.admit(seq[0][1])["verdict"]:
+            continue
+        for op, arg in seq[1:]:
+            if op == "ADD" and t.n < 128:
+                path, cols, part, size = refs.serve_add(t.tasks, t.part, t.size[:t.n_parts], arg, M, g, KC, KM)
+                r = t.add(arg)
+                paths.add(path)
+                assert r["path"] == path and bool(r["verdict"]) == (path != 0)
+            elif op == "REMOVE" and t.n > 0:
+                idx = int(arg * t.n)
+                cols, part, size = refs.serve_remove(t.tasks, t.part, t.size[:t.n_parts], idx, g, KC, KM)
+                t.remove(idx)
+            else:
+                continue
+            assert list(t.part) == list(part) and list(t.size[:t.n_parts]) == list(size)
+            for k in ("T", "D", "A", "B", "u_ppm", "type"):
+                assert np.array_equal(t.tasks[k], cols[k]), k
+    assert {1, 3} <= paths
+
+
+def test_serving_new_partition_must_fit_the_spare_sms():
+    """8 SMs held as 3 + 4 (a compute task of C1 = 250 and a memory task of
+    C1 = 350, both T = D = 100): one SM spare.  A compute task of C1 = 190
+    needs 2 SMs alone, fails in both partitions at their sizes (with the
+    other compute task: 100 + 76 > 100; beside the memory task: 88 + 48 > 100)
+    and after growing into the spare SM (75 + 57, 70 + 38 > 100), so it may
+    not open a new partition: the request reallocates within 8 SMs or is
+    rejected with the state unchanged, as the restatement says."""
+    def task(C1, typ):
+        return {"T": 100, "D": 100, "A": 1000 * C1, "B": 0, "u_ppm": C1 * 10000, "type": typ}
+    t = oracle.Tenant(8, 1, KC, KM)
+    cols = {k: np.array([task(250, 0)[k], task(350, 1)[k]], np.uint8 if k == "type" else np.int64)
+            for k in oracle.Tenant.COLS}
+    assert t.admit(cols)["verdict"] == 1
+    assert sorted(int(z) for z in t.size[:t.n_parts]) == [3, 4]
+    path, _, part, size = refs.serve_add(t.tasks, t.part, t.size[:t.n_parts], task(190, 0), 8, 1, KC, KM)
+    r = t.add(task(190, 0))
+    assert path in (0, 4) and r["path"] == path
+    assert r["Pi"] <= 8 and list(t.size[:t.n_parts]) == list(size)
