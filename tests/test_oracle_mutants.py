@@ -54,6 +54,10 @@ MUTANTS = [
     ("serving NEW ignores the spare SMs", "if (z && z <= spare) { part_out[nw]", "if (z) { part_out[nw]"),
     ("serving REMOVE keeps the size", "size_out[pr] = (int16_t)minm_linear(&s, &md, in, g, size_in[pr]);",
      "size_out[pr] = size_in[pr];"),
+    ("optimum ties to the larger size sum", "if (sm != b->sum_minm) return sm < b->sum_minm;",
+     "if (sm != b->sum_minm) return sm > b->sum_minm;"),
+    ("optimum ties to the later RGS", "if (rgs[i] != b->rgs[i]) return rgs[i] < b->rgs[i];",
+     "if (rgs[i] != b->rgs[i]) return rgs[i] > b->rgs[i];"),
 ]
 
 
