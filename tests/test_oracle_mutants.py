@@ -54,6 +54,9 @@ MUTANTS = [
     ("serving NEW ignores the spare SMs", "if (z && z <= spare) { part_out[nw]", "if (z) { part_out[nw]"),
     ("serving REMOVE keeps the size", "size_out[pr] = (int16_t)minm_linear(&s, &md, in, g, size_in[pr]);",
      "size_out[pr] = size_in[pr];"),
+    ("equal deadlines ordered by the longer period", "if (s->T[j] != s->T[i]) return s->T[j] < s->T[i];",
+     "if (s->T[j] != s->T[i]) return s->T[j] > s->T[i];"),
+    ("full ties ordered by the later index", "  return j < i;\n}", "  return j > i;\n}"),
     ("optimum ties to the larger size sum", "if (sm != b->sum_minm) return sm < b->sum_minm;",
      "if (sm != b->sum_minm) return sm > b->sum_minm;"),
     ("optimum ties to the later RGS", "if (rgs[i] != b->rgs[i]) return rgs[i] < b->rgs[i];",
