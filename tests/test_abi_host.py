@@ -135,3 +135,24 @@ def test_task_limits():
     with pytest.raises(ValueError):
         gpa.gen_tasksets(seed=1, nsets=2, n_min=1, n_max=257)
     assert gpa.NMAX == 256 and gpa.SERVE_NMAX == 128
+
+
+def test_binding_constants_match_the_header():
+    """Every enum value the binding mirrors equals the header's."""
+    text = open(os.path.join(ROOT, "include", "gpa.h")).read()
+    hdr = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(GPA_[A-Z0-9_]+)\s*=\s*(-?\d+)", text)}
+    defines = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(GPA_[A-Z0-9_]+)\s+(-?\d+)", text)}
+    from paper_2105_10312_gb300 import gen as G
+    serve = {k: v for k, v in hdr.items() if k.startswith("GPA_SERVE_") and k != "GPA_SERVE_NMAX"}
+    assert {k[len("GPA_SERVE_"):]: v for k, v in serve.items()} == gpa.SERVE_OP
+    for prefix, table in (("GPA_OPT_", gpa.OPT), ("GPA_POLICY_", gpa.POLICY), ("GPA_SCHED_", gpa.SCHED),
+                          ("GPA_REASON_", gpa.REASON), ("GPA_PROBE_", gpa.PROBE), ("GPA_PATH_", gpa.PATH),
+                          ("GPA_DIST_", G.DIST), ("GPA_GEN_", G.MODE)):
+        declared = {k[len(prefix):]: v for k, v in hdr.items() if k.startswith(prefix)}
+        assert declared == table, prefix
+    errs = {k: v for k, v in hdr.items() if k.startswith("GPA_ERR_") or k == "GPA_OK"}
+    assert errs == {"GPA_OK": gpa.OK, "GPA_ERR_ARG": gpa.ERR_ARG, "GPA_ERR_RANGE": gpa.ERR_RANGE,
+                    "GPA_ERR_NOMEM": gpa.ERR_NOMEM, "GPA_ERR_CUDA": gpa.ERR_CUDA, "GPA_ERR_TIMEOUT": gpa.ERR_TIMEOUT,
+                    "GPA_ERR_BUSY": gpa.ERR_BUSY, "GPA_ERR_NOTFOUND": gpa.ERR_NOTFOUND}
+    assert (defines["GPA_NMAX"], defines["GPA_SERVE_NMAX"], defines["GPA_MMAX"], defines["GPA_SEARCH_NMAX"],
+            defines["GPA_SEARCH_KMAX"]) == (gpa.NMAX, gpa.SERVE_NMAX, gpa.MMAX, gpa.SEARCH_NMAX, gpa.SEARCH_KMAX)
