@@ -4,6 +4,7 @@ import itertools
 import math
 import os
 import re
+import subprocess
 
 import numpy as np
 import pytest
@@ -156,3 +157,37 @@ def test_binding_constants_match_the_header():
                     "GPA_ERR_BUSY": gpa.ERR_BUSY, "GPA_ERR_NOTFOUND": gpa.ERR_NOTFOUND}
     assert (defines["GPA_NMAX"], defines["GPA_SERVE_NMAX"], defines["GPA_MMAX"], defines["GPA_SEARCH_NMAX"],
             defines["GPA_SEARCH_KMAX"]) == (gpa.NMAX, gpa.SERVE_NMAX, gpa.MMAX, gpa.SEARCH_NMAX, gpa.SEARCH_KMAX)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures have the size and field offsets of
+    the header's C structs (gcc compiles offsetof / sizeof of each)."""
+    import shutil
+    from paper_2105_10312_gb300 import gen as G
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    pairs = {"gpa_tasksets": gpa.Tasksets, "gpa_model": gpa.Model, "gpa_candidates": gpa.Candidates,
+             "gpa_params": gpa.Params, "gpa_alloc_result": gpa.AllocResult, "gpa_best_result": gpa.BestResult,
+             "gpa_serve_cfg": gpa.ServeCfg, "gpa_request": gpa.Request, "gpa_response": gpa.Response,
+             "gpa_probe_cfg": gpa.ProbeCfg, "gpa_gen_params": G.GenParams, "gpa_gen_out": G.GenOut}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "gpa.h"', "int main(void) {"]
+    for cname, cls in pairs.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            if fname.startswith("pad"):
+                continue
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        cname, field, value = ln.split()
+        got[(cname, field)] = int(value)
+    for cname, cls in pairs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            if not fname.startswith("pad"):
+                assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
