@@ -34,12 +34,38 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+class OracleRefused(RuntimeError):
+    """The oracle declined an analysis that would not end in reasonable time
+    (an EDF busy period beyond 2^100, or more than 2^34 demand terms)."""
+
+
+class _Checked:
+    """The loaded library, each of whose functions raises OracleRefused after
+    a call during which the oracle refused an analysis."""
+
+    def __init__(self, cdll):
+        self._cdll = cdll
+
+    def __getattr__(self, name):
+        f = getattr(self._cdll, name)
+        if name == "orc_take_refused":
+            return f
+        take = self._cdll.orc_take_refused
+
+        def call(*args):
+            r = f(*args)
+            if take():
+                raise OracleRefused(f"oracle {name}: an analysis was refused (too long to run)")
+            return r
+        return call
+
+
 def lib():
     global _lib
     if _lib is None:
         build()
         _lib = ctypes.CDLL(_LIB)
-    return _lib
+    return _Checked(_lib)
 
 
 # Arrays converted for a call are kept alive in _KEEP until the next call

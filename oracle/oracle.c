@@ -43,6 +43,7 @@
  */
 #include <pthread.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -169,6 +170,84 @@ static int rta(const oset* s, const omodel* md, const unsigned char* in, int64_t
   return all;
 }
 
+/* Set when an analysis was refused (see edf); read and cleared by
+ * orc_take_refused after each call. */
+static int g_refused;
+static void refuse(void) { __atomic_store_n(&g_refused, 1, __ATOMIC_RELAXED); }
+int orc_take_refused(void) { return __atomic_exchange_n(&g_refused, 0, __ATOMIC_RELAXED); }
+
+/* ------------------------------------------------ exact utilisation bound
+ *
+ * Multi-limb unsigned integers (little-endian 32-bit limbs), just enough to
+ * decide sum_i C_i / T_i <= 1 exactly: with T_i < 2^32 and at most ONMAX
+ * tasks the common denominator prod_i T_i has at most 32 ONMAX bits. */
+#define BIG_LIMBS (ONMAX + 4)
+typedef struct {
+  int n; /* limbs in use; the value is 0 when n == 0 */
+  uint32_t d[BIG_LIMBS];
+} bigu;
+
+static void big_set(bigu* a, uint32_t v) {
+  a->n = v ? 1 : 0;
+  a->d[0] = v;
+}
+
+/* out = a * x */
+static void big_mul(bigu* out, const bigu* a, uint32_t x) {
+  uint64_t carry = 0;
+  int i;
+  for (i = 0; i < a->n; i++) {
+    uint64_t v = (uint64_t)a->d[i] * x + carry;
+    out->d[i] = (uint32_t)v;
+    carry = v >> 32;
+  }
+  out->n = a->n;
+  if (carry) out->d[out->n++] = (uint32_t)carry;
+  while (out->n > 0 && out->d[out->n - 1] == 0) out->n--;
+}
+
+/* a += b */
+static void big_add(bigu* a, const bigu* b) {
+  uint64_t carry = 0;
+  int n = a->n > b->n ? a->n : b->n;
+  for (int i = 0; i < n; i++) {
+    uint64_t v = carry + (i < a->n ? a->d[i] : 0) + (i < b->n ? b->d[i] : 0);
+    a->d[i] = (uint32_t)v;
+    carry = v >> 32;
+  }
+  a->n = n;
+  if (carry) a->d[a->n++] = (uint32_t)carry;
+}
+
+static int big_cmp(const bigu* a, const bigu* b) {
+  if (a->n != b->n) return a->n < b->n ? -1 : 1;
+  for (int i = a->n - 1; i >= 0; i--)
+    if (a->d[i] != b->d[i]) return a->d[i] < b->d[i] ? -1 : 1;
+  return 0;
+}
+
+/* Sign of U - 1 for U = sum over the k tasks idx[] of C_i / T_i, exactly:
+ * the running fraction p / q takes each task as p <- p T_i + C_i q,
+ * q <- q T_i, and the end compares p with q. */
+static int utilisation_vs_one(const oset* s, const int64_t* C, const int* idx, int k) {
+  bigu p, q, t;
+  big_set(&p, 0);
+  big_set(&q, 1);
+  for (int a = 0; a < k; a++) {
+    const int i = idx[a];
+    if (s->T[i] < 1 || s->T[i] > (int64_t)UINT32_MAX || C[i] < 0 || C[i] > (int64_t)UINT32_MAX) {
+      fprintf(stderr, "oracle edf: a period or WCET beyond 2^32, refusing\n");
+      refuse();
+      return 1;
+    }
+    big_mul(&t, &q, (uint32_t)C[i]);
+    big_mul(&p, &p, (uint32_t)s->T[i]);
+    big_add(&p, &t);
+    big_mul(&q, &q, (uint32_t)s->T[i]);
+  }
+  return big_cmp(&p, &q);
+}
+
 /* Second per-partition policy (the paper leaves the policy of §5.5 open):
  * preemptive EDF on the partition as one processor, synchronous periodic
  * release, constrained deadlines.  Written as the processor-demand criterion
@@ -176,12 +255,15 @@ static int rta(const oset* s, const omodel* md, const unsigned char* in, int64_t
  *     dbf(t) = sum_{D_i <= t} (floor((t - D_i) / T_i) + 1) C_i  <=  t
  * at every absolute deadline t up to the end L of the first synchronous busy
  * period (George, Rivierre & Spuri, 1996), the least fixed point of
- * w = sum_i ceil(w / T_i) C_i from w = sum_i C_i.
- * Readings: one task passes iff C <= D; with two or more tasks U is bounded
- * by U_hi = sum_i ceil(2^32 C_i / T_i) / 2^32 and the test passes only if
- * U_hi <= 1 - 2^-10 (a set with U above that, or within n 2^-32 below it, is
- * reported as missing a deadline: conservative; it keeps L within about
- * 2^10 times the total WCET, so the analysis ends quickly). */
+ * w = sum_i ceil(w / T_i) C_i from w = sum_i C_i, which exists iff U <= 1
+ * (at U = 1 it is the first instant the processor idles, a multiple of the
+ * hyperperiod).  Every step is exact: U is compared with 1 as a fraction of
+ * multi-limb integers, and the deadlines are enumerated one by one.  A task
+ * with C > D misses at t = D (so one task passes iff C <= D).  The oracle
+ * refuses a partition whose busy period passes 2^100 or whose deadlines
+ * below it need more than 2^34 demand terms (its analysis would not end in
+ * reasonable time): it prints a message, sets the refusal flag that
+ * orc_take_refused() reports (the Python wrapper raises on it) and returns 0. */
 static int edf(const oset* s, const omodel* md, const unsigned char* in, int64_t m) {
   int64_t C[ONMAX];
   int idx[ONMAX], k = 0;
@@ -191,13 +273,10 @@ static int edf(const oset* s, const omodel* md, const unsigned char* in, int64_t
       idx[k++] = i;
     }
   if (k == 0) return 1;
-  if (k == 1) return C[idx[0]] <= s->D[idx[0]];
-  i128 uhi = 0;
-  for (int a = 0; a < k; a++) {
-    int i = idx[a];
-    uhi += (((i128)C[i] << 32) + s->T[i] - 1) / s->T[i];
-  }
-  if (uhi > ((i128)1 << 32) - ((i128)1 << 22)) return 0;
+  for (int a = 0; a < k; a++)
+    if (C[idx[a]] > s->D[idx[a]]) return 0;
+  if (utilisation_vs_one(s, C, idx, k) > 0) return 0;
+  const i128 Lmax = (i128)1 << 100;
   i128 L = 0;
   for (int a = 0; a < k; a++) L += C[idx[a]];
   for (;;) {
@@ -208,6 +287,18 @@ static int edf(const oset* s, const omodel* md, const unsigned char* in, int64_t
     }
     if (next == L) break;
     L = next;
+    if (L > Lmax) {
+      fprintf(stderr, "oracle edf: busy period beyond 2^100, refusing\n");
+      refuse();
+      return 0;
+    }
+  }
+  i128 checks = 0;
+  for (int a = 0; a < k; a++) checks += (L / s->T[idx[a]] + 1) * k;
+  if (checks > ((i128)1 << 34)) {
+    fprintf(stderr, "oracle edf: more than 2^34 demand terms below the busy period, refusing\n");
+    refuse();
+    return 0;
   }
   for (int a = 0; a < k; a++) {
     int i = idx[a];

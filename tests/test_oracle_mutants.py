@@ -38,15 +38,16 @@ MUTANTS = [
      "if (m3 > 0 && (best < 0 || m3 <= best_m))"),
     ("search forgets empty parts", "if (sm + empty * smallest_size(w->md) > w->md->M) return;",
      "if (sm > w->md->M) return;"),
-    ("EDF single task needs slack", "if (k == 1) return C[idx[0]] <= s->D[idx[0]];",
-     "if (k == 1) return C[idx[0]] < s->D[idx[0]];"),
+    ("EDF task needs slack", "if (C[idx[a]] > s->D[idx[a]]) return 0;", "if (C[idx[a]] >= s->D[idx[a]]) return 0;"),
     ("sizes ignore the unit g", "if (md->nsizes == 0) return m % md->g == 0;", "if (md->nsizes == 0) return 1;"),
     ("EDF demand equal to t fails", "      if (dbf > t) return 0;", "      if (dbf >= t) return 0;"),
     ("EDF demand counts tasks not yet due", "if (s->D[j] <= t) dbf +=", "if (1) dbf +="),
-    ("EDF utilisation band rounded down", "uhi += (((i128)C[i] << 32) + s->T[i] - 1) / s->T[i];",
-     "uhi += ((i128)C[i] << 32) / s->T[i];"),
-    ("EDF band at U < 1 - 2^-12", "if (uhi > ((i128)1 << 32) - ((i128)1 << 22)) return 0;",
-     "if (uhi > ((i128)1 << 32) - ((i128)1 << 20)) return 0;"),
+    ("EDF rejects U = 1", "if (utilisation_vs_one(s, C, idx, k) > 0) return 0;",
+     "if (utilisation_vs_one(s, C, idx, k) >= 0) return 0;"),
+    ("EDF utilisation test dropped", "if (utilisation_vs_one(s, C, idx, k) > 0) return 0;", ""),
+    ("EDF utilisation adds C unscaled", "big_mul(&t, &q, (uint32_t)C[i]);", "big_set(&t, (uint32_t)C[i]);"),
+    ("multi-limb product drops its top limb", "  out->n = a->n;\n  if (carry) out->d[out->n++] = (uint32_t)carry;",
+     "  out->n = a->n;"),
     ("EDF busy period by floor", "next += ((L + s->T[i] - 1) / s->T[i]) * (i128)C[i];",
      "next += (L / s->T[i]) * (i128)C[i];"),
     ("serving GROW leaves one spare SM unused", "size_in[p] + 1, size_in[p] + spare);",
@@ -94,7 +95,8 @@ def _failing_pins(source, tmp_path):
     c_path.write_text(source)
     subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", str(so_path), str(c_path), "-lpthread"],
                    check=True)
-    saved = oracle.lib()
+    oracle.lib()
+    saved = oracle._lib
     oracle._lib = ctypes.CDLL(str(so_path))
     failed = []
     try:

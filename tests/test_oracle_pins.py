@@ -222,58 +222,77 @@ def test_rta_monotone_in_m_and_in_tasks():
 
 # ------------------------------------------ EDF, the second per-partition policy
 
-def _edf_band(C, T):
-    """The oracle's reading: with two or more tasks U is bounded by
-    sum ceil(2^32 C / T) / 2^32, and the test needs that bound <= 1 - 2^-10."""
-    return sum(-(-(int(c) << 32) // int(t)) for c, t in zip(C, T)) > (1 << 32) - (1 << 22)
+def _edf(T, D, C):
+    """The oracle's EDF verdict for tasks with WCET C (k = 1, m = 1)."""
+    n = len(T)
+    return oracle.edf(np.asarray(T, np.int64), np.asarray(D, np.int64), 1000 * np.asarray(C, np.int64),
+                      np.zeros(n, np.int64), np.zeros(n, np.uint8), np.ones(n, np.uint8), 1, 1000, 1000)
+
+
+def _hyperperiod(T):
+    H = 1
+    for t in T:
+        H = H * int(t) // math.gcd(H, int(t))
+    return H
 
 
 def test_edf_matches_edf_simulation():
     """Processor-demand verdicts equal a unit-step EDF schedule simulated
-    over two hyperperiods (synchronous release, constrained deadlines); in
-    the band around U = 1 the test reports a miss (the conservative reading)."""
+    over two hyperperiods (synchronous release, constrained deadlines), over
+    the whole range of U, U = 1 included: random sets, and sets whose WCETs
+    are completed so that U is exactly 1."""
+    from fractions import Fraction
     rng = random.Random(41)
     periods = [3, 4, 5, 6, 8, 10, 12, 15, 20]
-    ok = miss = band = 0
-    for trial in range(600):
+    ok = miss = at_one = 0
+    for trial in range(900):
         n = rng.randrange(1, 6)
-        T = np.array([rng.choice(periods) for _ in range(n)], np.int64)
-        D = np.array([rng.randrange(max(1, t // 3), t + 1) for t in T], np.int64)
-        C = np.array([rng.randrange(1, max(2, (2 * t) // n)) for t in T], np.int64)
-        v = oracle.edf(T, D, 1000 * C, np.zeros(n, np.int64), np.zeros(n, np.uint8), np.ones(n, np.uint8), 1,
-                       1000, 1000)
-        H = 1
-        for t in T:
-            H = H * int(t) // math.gcd(H, int(t))
-        sim = refs.simulate_edf([(int(T[i]), int(D[i]), int(C[i])) for i in range(n)], 2 * H + int(D.max()) + 1)
-        if n >= 2 and _edf_band(C, T):
-            band += 1
-            assert v == 0, trial
-            continue
-        assert v == int(sim), (trial, list(T), list(D), list(C))
+        T = [rng.choice(periods) for _ in range(n)]
+        D = [rng.randrange(max(1, t // 3), t + 1) for t in T]
+        C = [rng.randrange(1, max(2, (2 * t) // n)) for t in T]
+        if trial % 3 == 0 and n >= 2:
+            # complete the last WCET so that U = 1 exactly, when that is possible
+            rest = 1 - sum(Fraction(c, t) for c, t in zip(C[:-1], T[:-1]))
+            last = rest * T[-1]
+            if rest > 0 and last.denominator == 1 and 1 <= last <= T[-1]:
+                C[-1] = int(last)
+        U = sum(Fraction(c, t) for c, t in zip(C, T))
+        v = _edf(T, D, C)
+        sim = refs.simulate_edf(list(zip(T, D, C)), 2 * _hyperperiod(T) + max(D) + 1)
+        assert v == int(sim), (trial, T, D, C)
         ok += v
         miss += 1 - v
-    assert ok > 150 and miss > 150 and band > 5
+        at_one += U == 1
+    assert ok > 150 and miss > 150 and at_one > 40
 
 
-def test_edf_band_rounds_each_term_up():
-    """The band sums ceil(2^32 C_i / T_i) (the reading), not floors: for this
-    pair the floored sum is 2^32 - 2^22 - 1 and the rounded-up sum one above
-    the bound, so the pair is reported as a miss; one unit of C less passes
-    (D = T and U < 1: the demand test itself passes)."""
-    T = np.array([1329, 1048573], np.int64)
-    for C2, want in ((523657, 0), (523656, 1)):
-        C = np.array([664, C2], np.int64)
-        floor_sum = sum((int(c) << 32) // int(t) for c, t in zip(C, T))
-        assert _edf_band(C, T) == (want == 0) and floor_sum <= (1 << 32) - (1 << 22)
-        v = oracle.edf(T, T.copy(), 1000 * C, np.zeros(2, np.int64), np.zeros(2, np.uint8), np.ones(2, np.uint8),
-                       1, 1000, 1000)
-        assert v == want, (C2, v)
+def test_edf_exact_at_utilisation_one():
+    """U is compared with 1 exactly: with D = T a set passes iff U <= 1, at
+    U = 1 exactly and one unit of C either side of it, for harmonic pairs,
+    for 1/3 + 2/3 (whose 2^64-scaled terms straddle 1), and for pairs of
+    large coprime periods, where U - 1 is a multiple of 1 / (T1 T2)."""
+    from fractions import Fraction
+    cases = [([3, 3], [1, 2]), ([1000003, 2000006], [600001, 800004]), ([7, 14, 28], [3, 4, 8])]
+    # large coprime periods: C2 chosen so that U straddles 1 by one unit
+    T1, T2 = 1329, 1048573
+    for C1 in (1, 664, 1328):
+        C2 = (T2 * (T1 - C1)) // T1  # U <= 1 with the largest such C2
+        cases.append(([T1, T2], [C1, C2]))
+        cases.append(([T1, T2], [C1, C2 + 1]))
+    seen = [0, 0, 0]  # below 1, at 1, above 1
+    for T, C in cases:
+        for dc in (-1, 0, 1):
+            CC = list(C[:-1]) + [C[-1] + dc]
+            if not 1 <= CC[-1] <= T[-1]:
+                continue
+            U = sum(Fraction(c, t) for c, t in zip(CC, T))
+            assert _edf(T, T, CC) == int(U <= 1), (T, CC, U)
+            seen[(U > 1) - (U < 1) + 1] += 1
+    assert min(seen) >= 3
 
 
 def test_edf_implicit_deadlines_utilisation_bound():
-    """Liu & Layland: with D = T, EDF meets every deadline iff U <= 1 (sets
-    in the band around U = 1 excepted, where the reading reports a miss)."""
+    """Liu & Layland: with D = T, EDF meets every deadline iff U <= 1."""
     from fractions import Fraction
     rng = random.Random(42)
     seen = [0, 0]
@@ -282,19 +301,15 @@ def test_edf_implicit_deadlines_utilisation_bound():
         T = np.array([rng.randrange(10, 100000) for _ in range(n)], np.int64)
         C = np.array([rng.randrange(1, int(t) * 8 // (5 * n) + 1) for t in T], np.int64)
         U = sum(Fraction(int(c), int(t)) for c, t in zip(C, T))
-        v = oracle.edf(T, T.copy(), 1000 * C, np.zeros(n, np.int64), np.zeros(n, np.uint8), np.ones(n, np.uint8),
-                       1, 1000, 1000)
-        if U > 1 or _edf_band(C, T):
-            assert v == 0, (trial, U)
-        else:
-            assert v == 1, (trial, U)
+        v = _edf(T, T, C)
+        assert v == int(U <= 1), (trial, U)
         seen[int(U <= 1)] += 1
     assert min(seen) > 50
 
 
 def test_edf_dominates_dm_and_is_monotone():
     """EDF is optimal on one processor: a DM-schedulable partition passes the
-    EDF test (outside the band); the EDF test is monotone in m and in the
+    EDF test; the EDF test is monotone in m and in the
     task set, like the DM test (no timing anomalies)."""
     s = gen_tasksets(seed=43, nsets=80, n_min=2, n_max=8, U_lo_ppm=300000, U_hi_ppm=4000000, deadline_pm=750,
                      T_lo=1000, T_hi=100000)
