@@ -62,13 +62,21 @@
  * that fixed point is <= D_i; otherwise its reported R is -1.
  * Second policy (GPA_SCHED_EDF, model->sched; not from the paper): preemptive
  * EDF on the partition, synchronous periodic release.  Exact processor-demand
- * test: dbf(t) = sum_{D_i <= t} (floor((t - D_i) / T_i) + 1) C_i <= t at every
- * absolute deadline up to the first synchronous busy period (evaluated with
- * QPA, Zhang & Burns 2009).  One task passes iff C <= D; with two or more
- * tasks the test requires sum_i ceil(2^32 C_i / T_i) <= 2^32 - 2^22, i.e.
- * U <= 1 - 2^-10: a set above that is reported as failing (conservative; it
- * bounds the busy period, and so the analysis time, near U = 1).
- * EDF gives no response times: R is 0 for the tasks of a passing part.
+ * test: U <= 1 (compared exactly) and dbf(t) = sum_{D_i <= t}
+ * (floor((t - D_i) / T_i) + 1) C_i <= t at every absolute deadline up to the
+ * first synchronous busy period (evaluated with QPA, Zhang & Burns 2009).
+ * One task passes iff C <= D.  EDF gives no response times: R is 0 for the
+ * tasks of a passing part.
+ *
+ * Undecided tests.  Every test is bounded: a DM fixed point stops after 2^20
+ * steps per task, an EDF analysis after 2^20 busy-period or QPA steps, or
+ * when its busy period would pass 2^62, or when U lies within n 2^-64 of 1
+ * and the periods' least common multiple exceeds 2^62.  Such a test is
+ * undecided, never reported as a miss: the set gets GPA_REASON_UNDECIDED
+ * (gpa_allocate), the candidate verdict 2 (gpa_test_schedulable), the
+ * optimum feasible = 2 (gpa_search_best), the serving request status
+ * GPA_ERR_TIMEOUT; and gpa_ctx_sync returns GPA_ERR_TIMEOUT.  Near U = 1 an
+ * EDF analysis takes about 1 / (1 - U) steps, so undecided tests are rare.
  *
  * Validation bounds (GPA_ERR_RANGE): 0 <= n <= 256 tasks per set (128 for
  * serving tenants and gpa_allocate_noalloc),
@@ -86,7 +94,7 @@
 extern "C" {
 #endif
 
-#define GPA_ABI_VERSION 3
+#define GPA_ABI_VERSION 4
 #define GPA_NMAX 256          /* tasks per set */
 #define GPA_SERVE_NMAX 128    /* tasks per serving tenant and per set of gpa_allocate_noalloc */
 #define GPA_MMAX 1024         /* SMs on the modelled GPU */
@@ -116,7 +124,9 @@ enum {
   GPA_REASON_LEMMA2 = 2,    /* a task meets its deadline on no size <= M (Lemma 2) */
   GPA_REASON_NO_MERGE = 3,  /* Alg. 3 found no eligible merge while Pi > M */
   GPA_REASON_TEST = 4,      /* 1G baseline: the single partition fails the test */
-  GPA_REASON_INVALID = 5    /* device-side validation rejected the set */
+  GPA_REASON_INVALID = 5,   /* device-side validation rejected the set */
+  GPA_REASON_UNDECIDED = 6  /* a per-partition test hit its step limit: the verdict is unknown (0 is
+                               written); the set's other outputs are unspecified */
 };
 
 /* Allocation policies (§7.2). */
@@ -144,9 +154,10 @@ int32_t gpa_ctx_create(int32_t device, void* stream, gpa_ctx** out);
 int32_t gpa_ctx_destroy(gpa_ctx* ctx);
 /* Rebind the context to another stream of the same device. */
 int32_t gpa_ctx_set_stream(gpa_ctx* ctx, void* stream);
-/* Wait for the context stream; return GPA_ERR_RANGE if any kernel since the
- * last call flagged an invalid device-resident set (and clear the flag),
- * GPA_ERR_CUDA on an asynchronous CUDA error, else GPA_OK. */
+/* Wait for the context stream; return GPA_ERR_TIMEOUT if any kernel since
+ * the last call left a test undecided (see "Undecided tests" above), else
+ * GPA_ERR_RANGE if one flagged an invalid device-resident set (and clear
+ * both flags), GPA_ERR_CUDA on an asynchronous CUDA error, else GPA_OK. */
 int32_t gpa_ctx_sync(gpa_ctx* ctx);
 /* Copy the last error message of this thread into buf (NUL-terminated). */
 int32_t gpa_last_error(char* buf, int32_t len);
@@ -312,7 +323,8 @@ typedef struct {
 
 /* a4 over a flat batch: candidate c is schedulable iff sum of its part sizes
  * <= M and every non-empty part meets the per-partition test at its size (a
- * non-empty part of size 0 fails).  verdict[c] in {0,1}; R (nullable) gets
+ * non-empty part of size 0 fails).  verdict[c] in {0,1}, or 2 when a part's
+ * test was undecided and no other part fails; R (nullable) gets
  * each task's response time at R[c * map_stride + t], -1 for a miss (under
  * EDF: 0 for the tasks of a passing part, -1 otherwise).
  * Arrays live in cands->mem (which must equal sets->mem). */
@@ -357,12 +369,19 @@ int32_t gpa_allocate(gpa_ctx* ctx, const gpa_tasksets* sets, const gpa_model* mo
  * someone else's pool or a fixed budget, or a real-time process that must not
  * allocate once it runs.  This call takes no context and allocates nothing
  * (no cudaMalloc, cudaFree or allocating library routine); its scratch -- the
- * work-queue counters, a queue of up to GPA_NOALLOC_MAX_SETS deferred sets
- * and the reciprocal table, about 2 MB -- is a static device array of the
- * library, held by every GPU that loads it until the process exits.
+ * work-queue counters, the error word, a queue of up to GPA_NOALLOC_MAX_SETS
+ * deferred sets and the reciprocal table, about 2 MB -- is a static device
+ * array of the library.  A device holds those 2 MB until the process exits
+ * from the moment the library's device code is loaded on it: at the first
+ * call of this entry point on that device under CUDA's default lazy module
+ * loading, and as soon as the process creates a CUDA context on it under
+ * eager loading (CUDA_MODULE_LOADING=EAGER), whether or not it ever calls
+ * this entry point.
  *  - Same computation and outputs as gpa_allocate with GPA_POLICY_SMS or
- *    GPA_POLICY_BF (GPA_ERR_ARG otherwise); device arrays only (both `mem`
- *    fields GPA_DEVICE); work is enqueued on `stream` (a cudaStream_t).
+ *    GPA_POLICY_BF (GPA_ERR_ARG otherwise), either per-partition policy;
+ *    device arrays only (both `mem` fields GPA_DEVICE); work is enqueued on
+ *    `stream` (a cudaStream_t), which must belong to the current device
+ *    (GPA_ERR_ARG otherwise).
  *  - More than GPA_NOALLOC_MAX_SETS sets: GPA_ERR_RANGE, nothing launched.
  *  - The first call on a device (the current device) sets that device up
  *    synchronously (uploads the reciprocal table, looks up the scratch
@@ -371,17 +390,25 @@ int32_t gpa_allocate(gpa_ctx* ctx, const gpa_tasksets* sets, const gpa_model* mo
  *    call's contents; each call clears the counters it needs zeroed.  Calls
  *    whose GPU work overlaps (other streams, other threads) race on it: the
  *    caller must serialise them.
- *  - Device-side validation marks invalid sets with GPA_REASON_INVALID as
- *    gpa_allocate does; there is no context to report it to beyond that. */
+ *  - Problems found on the device are marked per set as gpa_allocate marks
+ *    them (GPA_REASON_INVALID, GPA_REASON_UNDECIDED) and recorded in the
+ *    scratch's error word; the call itself returns before they are known.
+ *    gpa_allocate_noalloc_status reports and clears that word. */
 int32_t gpa_allocate_noalloc(void* stream, const gpa_tasksets* sets, const gpa_model* model,
                              const gpa_params* params, gpa_alloc_result* result);
+/* The error word of gpa_allocate_noalloc on the current device: waits for
+ * `stream` (which must belong to the current device), then returns
+ * GPA_ERR_TIMEOUT if a set of the calls since the last status was left
+ * undecided, else GPA_ERR_RANGE if one failed validation, else GPA_OK, and
+ * clears the word.  Allocates nothing. */
+int32_t gpa_allocate_noalloc_status(void* stream);
 
 /* ------------------------------------------------------ exhaustive optimum */
 
 typedef struct {
   int32_t mem;
   int32_t pad_;
-  uint8_t* feasible;      /* [nsets] */
+  uint8_t* feasible;      /* [nsets] 1 feasible, 0 not, 2 undecided (a test hit its step limit) */
   int64_t* W;             /* [nsets] inflated workload of the optimum */
   int32_t* sum_minm;      /* [nsets] sum over blocks of the block's minimum size */
   int32_t* n_blocks;      /* [nsets] */
@@ -460,7 +487,9 @@ typedef struct {
 
 typedef struct {
   uint64_t req_id;
-  int32_t status;                /* GPA_OK, or the request's error (GPA_ERR_RANGE / ARG / NOTFOUND) */
+  int32_t status;                /* GPA_OK, or the request's error (GPA_ERR_RANGE / ARG / NOTFOUND), or
+                                    GPA_ERR_TIMEOUT when a test of the request was undecided (the tenant's
+                                    state is still an allocation whose every partition passes) */
   uint8_t verdict;               /* ADMIT/ADD: 1 if accepted; REMOVE/EVICT: 1 */
   uint8_t reason;                /* GPA_REASON_* of the Alg. 1 run (ADMIT, ADD re-allocation) */
   uint8_t path;                  /* GPA_PATH_* (ADD) */

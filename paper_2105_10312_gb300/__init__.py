@@ -28,7 +28,7 @@ OK, ERR_ARG, ERR_RANGE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_NOTFOUND
 HOST, DEVICE = 0, 1
 POLICY = {"SMS": 0, "BF": 1, "ONE_GPU": 2}
 SCHED = {"DM": 0, "EDF": 1}
-REASON = {"OK": 0, "LEMMA1": 1, "LEMMA2": 2, "NO_MERGE": 3, "TEST": 4, "INVALID": 5}
+REASON = {"OK": 0, "LEMMA1": 1, "LEMMA2": 2, "NO_MERGE": 3, "TEST": 4, "INVALID": 5, "UNDECIDED": 6}
 OPT = {"AUTOTUNE": 1, "GRAPH": 2, "FAST_WARPS": 3, "FAST_CHUNK": 4, "FAST_BLOCKS": 5, "PER_SET_LAUNCH": 6,
        "PROFILE": 7, "FAST_STAGES": 8, "HOST_SLICES": 9,
        "HOST_COPY": 10}
@@ -121,6 +121,7 @@ def _set_signatures(L):
     L.gpa_unrank_rgs.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _vp]
     L.gpa_allocate_noalloc.argtypes = [_vp, ctypes.POINTER(Tasksets), ctypes.POINTER(Model), ctypes.POINTER(Params),
                                        ctypes.POINTER(AllocResult)]
+    L.gpa_allocate_noalloc_status.argtypes = [_vp]
 
 
 def lib():
@@ -356,14 +357,15 @@ NOALLOC_MAX_SETS = 262144
 
 
 def allocate_noalloc(sets, out, M, g=1, k_c_pm=1200, k_m_pm=2300, policy="SMS", act=False, linear=True,
-                     stream=None):
+                     stream=None, sched="DM"):
     """gpa_allocate_noalloc: the heuristic for callers that may not allocate device
     memory.  No context; the library's static device scratch is used, so calls
     must not overlap on the GPU.  ``sets`` and ``out`` are CUDA tensors the caller
-    allocated; work is enqueued on ``stream`` (default: torch's current stream)."""
+    allocated; work is enqueued on ``stream`` (default: torch's current stream).
+    Problems found on the device are reported by allocate_noalloc_status."""
     import torch
     ts, mem = make_tasksets(sets)
-    md = Model(M, g, k_c_pm, k_m_pm)
+    md = make_model(M, g, k_c_pm, k_m_pm, sched)
     pr = Params(POLICY[policy], 1 if act else 0, 1 if linear else 0, 0)
     res = AllocResult(mem, 0, _ptr(out["verdict"]), _ptr(out["reason"]), _ptr(out["n_parts"]), _ptr(out["Pi"]),
                       _ptr(out["W"]), _ptr(out.get("n_tests")), _ptr(out["part_of_task"]), _ptr(out["size_of_part"]))
@@ -372,6 +374,17 @@ def allocate_noalloc(sets, out, M, g=1, k_c_pm=1200, k_m_pm=2300, policy="SMS", 
     _check(lib().gpa_allocate_noalloc(_vp(stream.cuda_stream), ctypes.byref(ts), ctypes.byref(md), ctypes.byref(pr),
                                       ctypes.byref(res)))
     return out
+
+
+def allocate_noalloc_status(stream=None):
+    """gpa_allocate_noalloc_status: waits for ``stream`` and raises GpaError
+    (ERR_TIMEOUT: a set was left undecided; ERR_RANGE: a set failed
+    validation) if the allocation-free calls since the last status recorded a
+    problem on the current device; clears the record."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(lib().gpa_allocate_noalloc_status(_vp(stream.cuda_stream)))
 
 
 def to_device(sets, device="cuda"):

@@ -54,6 +54,22 @@ __device__ __forceinline__ void write_empty(long long s, long long o, int n, uns
 }
 
 
+// After a set's run with its own error word e: a per-partition test that hit
+// its step limit (kErrIter) leaves the set undecided (verdict 0, reason
+// GPA_REASON_UNDECIDED; its other outputs are those of the run, unspecified);
+// the bits go to the sticky error word too.
+__device__ __forceinline__ void finish_set_errors(long long s, unsigned int e, const AllocOut& out,
+                                                  unsigned int* gerr) {
+  if ((threadIdx.x & 31) == 0 && e) {
+    if (e & kErrIter) {
+      out.verdict[s] = 0;
+      out.reason[s] = GPA_REASON_UNDECIDED;
+    }
+    atomicOr(gerr, e);
+  }
+  __syncwarp();
+}
+
 // ------------------------------------------------------------ merge kernel
 
 constexpr int kLaneMax = 16;  // merged sets of up to this many tasks are tested by one lane
@@ -86,6 +102,7 @@ struct MergeSmem {
   unsigned char cand[kNmax];         // BF: eligible slots sorted by (W, position)
   unsigned char slot_of[kNmax];      // slot of each row
   unsigned char rank[kNmax];         // output numbering of each slot
+  unsigned int err;                  // error bits of the set being processed
 };
 
 

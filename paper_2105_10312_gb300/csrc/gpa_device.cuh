@@ -26,7 +26,7 @@ constexpr int kIterCap = 1 << 20;         // response-time iterations per task b
 
 // error bits of the context's sticky error word
 constexpr unsigned kErrRange = 1u;        // a set failed device-side validation
-constexpr unsigned kErrIter = 2u;         // a response-time iteration hit kIterCap
+constexpr unsigned kErrIter = 2u;         // a per-partition test hit its step limit: undecided
 constexpr unsigned kErrWait = 4u;         // a pipeline barrier wait hit its time limit
 
 // floor(x / d) for 0 <= x < 2^60 and d = 10^6 m (m <= GPA_MMAX):
@@ -379,56 +379,124 @@ static __device__ __noinline__ bool warp_rta(const SetSmem& st, const unsigned i
 //
 // Second per-partition policy (the paper leaves §5.5's policy open):
 // preemptive EDF on the partition as one processor, synchronous periodic
-// release, constrained deadlines.  Exact processor-demand test by QPA (Zhang
-// & Burns, 2009): with dbf(t) = sum_{D_i <= t} (floor((t - D_i)/T_i) + 1) C_i,
-// start from the largest absolute deadline t < L and repeat
+// release, constrained deadlines.  Exact processor-demand criterion: every
+// deadline is met iff U <= 1 and dbf(t) <= t at every absolute deadline up to
+// L, with dbf(t) = sum_{D_i <= t} (floor((t - D_i)/T_i) + 1) C_i (Baruah,
+// Rosier & Howell, 1990).  Evaluated by QPA (Zhang & Burns, 2009): start from
+// the largest absolute deadline t < L and repeat
 //     h = dbf(t);  h > t: miss;  h <= d_min: schedulable;
 //     t = h if h < t, else the largest absolute deadline below t,
 // where L = min(L_a, L_b): L_a = max(D_max, sum (T_i - D_i) U_i / (1 - U))
-// (bounded from above in integers and floating point with a margin) and L_b
+// (bounded from above in floating point with a margin, when U < 1) and L_b
 // the synchronous busy period (least fixed point of sum ceil(w/T_i) C_i).
-// Same verdict as the plain criterion over every deadline up to the busy
-// period.  Readings (shared with the CPU reference): one task passes iff
-// C <= D; with two or more tasks the test needs
-// U_hi = sum ceil(2^32 C_i / T_i) <= 2^32 - 2^22, i.e. U <= 1 - 2^-10 (a
-// miss is reported above that: conservative, and it bounds the busy period
-// by about 2^10 times the total WCET, so both iterations end quickly).  A
-// task with C > D misses at t = D.
+// U is compared with 1 exactly: a float sum first (it is within 2^-14 of U),
+// then, near 1, integer terms floor(2^64 C_i / T_i) (U 2^64 lies in
+// [sum, sum + number of inexact terms)), then, if that still straddles 1,
+// the exact fraction over the periods' least common multiple when it stays
+// below 2^62.  One task passes iff C <= D; a task with C > D misses at t = D.
+// When an analysis cannot finish -- U within n 2^-64 of 1 with periods whose
+// least common multiple exceeds 2^62, a busy period beyond 2^62, or more than
+// kIterCap busy-period or QPA steps -- the test is undecided: it sets
+// kErrIter in *err and returns false, and the caller reports the set as
+// undecided (never as a miss).
 // Values stay below 2^63: C <= D <= T bounds each demand term by t + C.
 
-constexpr unsigned long long kEdfLmax = 1ull << 62;
-constexpr unsigned long long kEdfUmax = (1ull << 32) - (1ull << 22);  // the largest accepted U_hi (x 2^32)
+constexpr unsigned long long kEdfLmax = 1ull << 62;  // also "no L_a bound"
+constexpr unsigned long long kEdfLcmMax = 1ull << 62;
 
-__device__ __forceinline__ unsigned long long edf_uterm(unsigned int C, unsigned int T) {
-  return (((unsigned long long)C << 32) + T - 1u) / T;
-}
-
-// Upper bound of L_a from the integer utilisation bound (floating point with
-// a relative margin far above its rounding error), capped at kEdfLmax.
-__device__ __forceinline__ unsigned long long edf_la_bound(double num, unsigned long long uhi, unsigned int dmax) {
-  const double den = (double)((1ull << 32) - uhi);
-  const double la = num / den * (1.0 + 0x1p-30) + 2.0;
-  const unsigned long long up = la >= (double)kEdfLmax ? kEdfLmax : (unsigned long long)la;
-  return up > dmax ? up : (unsigned long long)dmax;
-}
-
-// The band rule decided cheaply first: uf = sum of float C_i / T_i is within
-// 2^-14 of U for n <= 256 (each term within 3 ulp, the float sum within
-// n ulp: at most 258 ulp = 2^-16), and U <= U_hi / 2^32 <= U + n 2^-32.  So uf below kEdfPass means
-// U_hi <= kEdfUmax, above kEdfFail means U_hi > kEdfUmax; only in between
-// are the exact integer terms summed.  numf = sum (T_i - D_i) C_i / T_i in
-// the same precision gives L_a <= numf (1 + 2^-20) / (1 - uf - 2^-14).
-constexpr float kEdfPass = 1.0f - 0x1p-10f - 0x1p-13f;
-constexpr float kEdfFail = 1.0f - 0x1p-10f + 0x1p-13f;
+// Float screen: uf = sum of float C_i / T_i is within 2^-14 of U for n <= 256
+// (each term within 3 ulp, the sums within n ulp: at most 2^-16 of U for
+// U <= 2).  uf above kEdfFail proves U > 1, below kEdfPass proves
+// 1 - U >= 1 - uf - 2^-14.
+constexpr float kEdfPass = 1.0f - 0x1p-13f;
+constexpr float kEdfFail = 1.0f + 0x1p-13f;
 // Density: sum C_i / D_i <= 1 makes a constrained-deadline set EDF-feasible
 // (dbf(t) <= sum C_i (t / D_i) <= t); the float sum is within 2^-14 of the
 // exact one, so dens <= 1 - 2^-14 proves it.
 constexpr float kEdfDensity = 1.0f - 0x1p-14f;
 
-__device__ __forceinline__ unsigned long long edf_la_bound_f(double numf, float uf, unsigned int dmax) {
-  const double den = 1.0 - ((double)uf + 0x1p-14);
-  const double la = numf * (1.0 + 0x1p-20) / den * (1.0 + 0x1p-30) + 2.0;
-  const unsigned long long up = la >= (double)kEdfLmax ? kEdfLmax : (unsigned long long)la;
+// 128-bit unsigned (hi, lo) accumulation.
+struct U128 {
+  unsigned long long hi, lo;
+};
+__device__ __forceinline__ void add128(U128& a, unsigned long long bhi, unsigned long long blo) {
+  const unsigned long long lo = a.lo + blo;
+  a.hi += bhi + (lo < a.lo ? 1ull : 0ull);
+  a.lo = lo;
+}
+
+// Adds floor(2^64 C / T) to q and counts an inexact term in nz (C <= T < 2^31):
+// long division in base 2^32, q1 = floor(C 2^32 / T) <= 2^32, then the next
+// 32 bits from the remainder.
+__device__ __forceinline__ void edf_uterm64(unsigned int C, unsigned int T, U128& q, unsigned int& nz) {
+  const unsigned long long n1 = (unsigned long long)C << 32;
+  const unsigned long long q1 = n1 / T, r1 = n1 - q1 * T;
+  const unsigned long long n2 = r1 << 32;
+  const unsigned long long q2 = n2 / T, r2 = n2 - q2 * T;
+  add128(q, q1 >> 32, (q1 << 32) + q2);
+  nz += r2 != 0ull ? 1u : 0u;
+}
+
+// Sign of U - 1 from q = sum floor(2^64 C_i / T_i) and nz inexact terms:
+// -1, 0 or 1, or 2 when U 2^64 in [q, q + nz) straddles 2^64.  With -1,
+// *gap gets a lower bound of 1 - U (possibly 0).
+__device__ __forceinline__ int edf_classify64(const U128& q, unsigned int nz, double* gap) {
+  if (q.hi > 1ull || (q.hi == 1ull && q.lo != 0ull)) return 1;
+  if (q.hi == 1ull) return nz == 0u ? 0 : 1;
+  // q < 2^64: the gap 2^64 - q, as an integer
+  const unsigned long long g = 0ull - q.lo;  // 2^64 - lo (lo > 0 since every C >= 1)
+  if (nz == 0u) {
+    *gap = (double)g * 0x1p-64 * (1.0 - 0x1p-50);
+    return -1;
+  }
+  if (q.lo == 0ull || g >= nz) {
+    *gap = q.lo == 0ull ? 1.0 - 0x1p-50 : (double)(g - nz) * 0x1p-64 * (1.0 - 0x1p-50);
+    return -1;
+  }
+  return 2;
+}
+
+__device__ __forceinline__ unsigned long long gcd64(unsigned long long a, unsigned long long b) {
+  while (b) {
+    const unsigned long long r = a % b;
+    a = b;
+    b = r;
+  }
+  return a;
+}
+
+// Sign of U - 1 over the k tasks get(a, C, T) yields, exactly, by the
+// periods' least common multiple H: U - 1 = (sum C_i H / T_i - H) / H.
+// Returns 2 when H exceeds 2^62.
+template <class Get>
+__device__ int edf_lcm_classify(int k, Get get) {
+  unsigned long long H = 1ull;
+  for (int a = 0; a < k; a++) {
+    unsigned int C, T;
+    get(a, C, T);
+    const unsigned long long f = T / gcd64(H, T);
+    if (H > kEdfLcmMax / f) return 2;
+    H *= f;
+  }
+  U128 N{0ull, 0ull};
+  for (int a = 0; a < k; a++) {
+    unsigned int C, T;
+    get(a, C, T);
+    const unsigned long long term = (H / T) * C;  // <= H since C <= T
+    add128(N, 0ull, term);
+  }
+  if (N.hi != 0ull || N.lo > H) return 1;
+  return N.lo == H ? 0 : -1;
+}
+
+// L_a from a numerator bound num >= sum (T_i - D_i) U_i and gap <= 1 - U:
+// num / gap rounded up with margins, at least D_max; kEdfLmax when that
+// reaches 2^62 or gap is 0 (no usable bound).
+__device__ __forceinline__ unsigned long long edf_la(double num, double gap, unsigned int dmax) {
+  if (!(gap > 0.0)) return kEdfLmax;
+  const double la = num * (1.0 + 0x1p-20) / gap * (1.0 + 0x1p-30) + 2.0;
+  if (!(la < (double)kEdfLmax)) return kEdfLmax;
+  const unsigned long long up = (unsigned long long)la;
   return up > dmax ? up : (unsigned long long)dmax;
 }
 
@@ -453,6 +521,15 @@ __device__ __forceinline__ unsigned long long warp_sum_u64_edf(unsigned long lon
   return v;
 }
 
+__device__ __forceinline__ U128 warp_sum_u128(U128 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long hi = __shfl_xor_sync(kFull, v.hi, o), lo = __shfl_xor_sync(kFull, v.lo, o);
+    add128(v, hi, lo);
+  }
+  return v;
+}
+
 // floor(x / T) and ceil(x / T) for 64-bit x: the period's reciprocal while
 // x stays below 2^31 (the common case), a 64-bit division above.
 __device__ __forceinline__ unsigned long long floor_div_T64(unsigned long long x, unsigned int T, unsigned int mg,
@@ -474,8 +551,8 @@ __device__ __forceinline__ unsigned long long edf_deadline_below(unsigned long l
 }
 
 // Warp-cooperative EDF test of S at m SMs; lane l holds the compacted tasks
-// l, l + 32, ...  Returns the verdict on every lane; *err |= kErrIter if an
-// iteration cap was reached (the verdict is then 0).
+// l, l + 32, ...  Returns the verdict on every lane; an undecided test sets
+// kErrIter in *err and returns false.
 static __device__ __noinline__ bool warp_edf(const SetSmem& st, const unsigned int* S, unsigned int m, unsigned int kc,
                                       unsigned int km, const MagicDiv* __restrict__ mdiv, RtaScratch& sc,
                                       unsigned int* err) {
@@ -507,22 +584,39 @@ static __device__ __noinline__ bool warp_edf(const SetSmem& st, const unsigned i
   dmin = __reduce_min_sync(kFull, dmin);
   dmax = __reduce_max_sync(kFull, dmax);
   if (uf > kEdfFail) return false;
-  // density sum C_i / D_i <= 1 is sufficient (within the band)
-  if (uf < kEdfPass && dens <= kEdfDensity) return true;
+  if (dens <= kEdfDensity) return true;  // density <= 1 suffices
   unsigned long long La;
   if (uf < kEdfPass) {
-    La = edf_la_bound_f(warp_sum_f64(numf), uf, dmax);
+    La = edf_la(warp_sum_f64(numf), 1.0 - ((double)uf + 0x1p-14), dmax);
   } else {
-    unsigned long long uhi = 0;
+    U128 q{0ull, 0ull};
+    unsigned int nz = 0u;
     double num = 0.0;
     for (int i = lane; i < s; i += 32) {
-      const unsigned long long q = edf_uterm(sc.C[i], sc.T[i]);
-      uhi += q;
-      num += (double)(sc.T[i] - sc.D[i]) * (double)q;
+      const unsigned long long hi0 = q.hi, lo0 = q.lo;
+      edf_uterm64(sc.C[i], sc.T[i], q, nz);
+      // this term's value (q after - q before) times (T - D) / 2^64
+      const unsigned long long dlo = q.lo - lo0, dhi = q.hi - hi0 - (q.lo < lo0 ? 1ull : 0ull);
+      num += (double)(sc.T[i] - sc.D[i]) * ((double)dhi + (double)dlo * 0x1p-64);
     }
-    uhi = warp_sum_u64_edf(uhi);
-    if (uhi > kEdfUmax) return false;
-    La = edf_la_bound(warp_sum_f64(num), uhi, dmax);
+    q = warp_sum_u128(q);
+    nz = __reduce_add_sync(kFull, nz);
+    num = warp_sum_f64(num);
+    double gap = 0.0;
+    int cmp = edf_classify64(q, nz, &gap);
+    if (cmp == 2) {
+      cmp = edf_lcm_classify(s, [&](int a, unsigned int& C, unsigned int& T) {
+        C = sc.C[a];
+        T = sc.T[a];
+      });
+      gap = 0.0;  // exact sign only: no L_a bound
+    }
+    if (cmp == 2) {
+      if (lane == 0) atomicOr(err, kErrIter);
+      return false;
+    }
+    if (cmp > 0) return false;
+    La = cmp < 0 ? edf_la(num, gap, dmax) : kEdfLmax;
   }
   // synchronous busy period, stopped at La
   unsigned long long L = csum;
@@ -533,6 +627,10 @@ static __device__ __noinline__ bool warp_edf(const SetSmem& st, const unsigned i
     const unsigned long long next = warp_sum_u64_edf(part);
     if (next == L) break;
     if (next >= La) {
+      if (La == kEdfLmax) {  // no bound below 2^62: undecided
+        if (lane == 0) atomicOr(err, kErrIter);
+        return false;
+      }
       L = La;
       break;
     }
@@ -578,8 +676,8 @@ static __device__ __noinline__ bool warp_edf(const SetSmem& st, const unsigned i
 }
 
 // The same EDF test by one thread over k tasks; get(a, C, T, D, mg, sh)
-// yields the a-th with its period's reciprocal.  *errbits |= kErrIter if an
-// iteration cap was reached.
+// yields the a-th with its period's reciprocal.  An undecided test sets
+// kErrIter in *errbits and returns false.
 template <class Get>
 __device__ bool serial_edf(int k, Get get, unsigned int* errbits) {
   unsigned int C, T, D, mg, sh;
@@ -605,21 +703,36 @@ __device__ bool serial_edf(int k, Get get, unsigned int* errbits) {
     dmax = max(dmax, D);
   }
   if (uf > kEdfFail) return false;
-  if (uf < kEdfPass && dens <= kEdfDensity) return true;  // density <= 1 suffices
+  if (dens <= kEdfDensity) return true;  // density <= 1 suffices
   unsigned long long La;
   if (uf < kEdfPass) {
-    La = edf_la_bound_f(numf, uf, dmax);
+    La = edf_la(numf, 1.0 - ((double)uf + 0x1p-14), dmax);
   } else {
-    unsigned long long uhi = 0;
+    U128 q{0ull, 0ull};
+    unsigned int nz = 0u;
     double num = 0.0;
     for (int a = 0; a < k; a++) {
       get(a, C, T, D, mg, sh);
-      const unsigned long long q = edf_uterm(C, T);
-      uhi += q;
-      num += (double)(T - D) * (double)q;
+      const unsigned long long hi0 = q.hi, lo0 = q.lo;
+      edf_uterm64(C, T, q, nz);
+      const unsigned long long dlo = q.lo - lo0, dhi = q.hi - hi0 - (q.lo < lo0 ? 1ull : 0ull);
+      num += (double)(T - D) * ((double)dhi + (double)dlo * 0x1p-64);
     }
-    if (uhi > kEdfUmax) return false;
-    La = edf_la_bound(num, uhi, dmax);
+    double gap = 0.0;
+    int cmp = edf_classify64(q, nz, &gap);
+    if (cmp == 2) {
+      cmp = edf_lcm_classify(k, [&](int a, unsigned int& Ca, unsigned int& Ta) {
+        unsigned int Da, mga, sha;
+        get(a, Ca, Ta, Da, mga, sha);
+      });
+      gap = 0.0;
+    }
+    if (cmp == 2) {
+      *errbits |= kErrIter;
+      return false;
+    }
+    if (cmp > 0) return false;
+    La = cmp < 0 ? edf_la(num, gap, dmax) : kEdfLmax;
   }
   unsigned long long L = csum;
   int iter = 0;
@@ -631,6 +744,10 @@ __device__ bool serial_edf(int k, Get get, unsigned int* errbits) {
     }
     if (next == L) break;
     if (next >= La) {
+      if (La == kEdfLmax) {
+        *errbits |= kErrIter;
+        return false;
+      }
       L = La;
       break;
     }

@@ -18,6 +18,11 @@ struct MagicDivHost {
   unsigned int pad;
 };
 
+// Fills table[0 .. GPA_MMAX] (entry 0 unused): for d = 10^6 m and
+// l = ceil(log2 d), magic = ceil(2^(60+l) / d) and shift = l - 4.  Every
+// context and the allocation-free entry point build their table with it.
+void build_reciprocals(MagicDivHost* table);
+
 struct DevSets {
   long long nsets;
   int n_max;

@@ -233,16 +233,22 @@ extern "C" int32_t gpa_validate(const gpa_tasksets* sets, const gpa_model* model
 
 // ----------------------------------------------------------------- context
 
-static void build_mdiv(std::vector<MagicDivHost>& t) {
-  t.assign(GPA_MMAX + 1, MagicDivHost{0, 0, 0});
+namespace gpa {
+void build_reciprocals(MagicDivHost* t) {
+  t[0] = MagicDivHost{0, 0, 0};
   for (int m = 1; m <= GPA_MMAX; m++) {
     unsigned long long d = 1000000ull * (unsigned long long)m;
     unsigned int l = 0;
     while ((1ull << l) < d) l++;
     unsigned __int128 num = ((unsigned __int128)1 << (60 + l)) + d - 1;
-    t[m].magic = (unsigned long long)(num / d);
-    t[m].shift = l - 4;
+    t[m] = MagicDivHost{(unsigned long long)(num / d), l - 4, 0};
   }
+}
+}  // namespace gpa
+
+static void build_mdiv(std::vector<MagicDivHost>& t) {
+  t.assign(GPA_MMAX + 1, MagicDivHost{0, 0, 0});
+  build_reciprocals(t.data());
 }
 
 extern "C" int32_t gpa_ctx_create(int32_t device, void* stream, gpa_ctx** out) {
@@ -400,7 +406,8 @@ extern "C" int32_t gpa_ctx_set_option(gpa_ctx* c, int32_t opt, int64_t value) {
 static int32_t err_word_status(gpa_ctx* c, unsigned int err) {
   if (!err) return GPA_OK;
   cudaMemset(c->d_err, 0, sizeof(unsigned int));
-  if (err & 2u) return gpa_fail(GPA_ERR_TIMEOUT, "a response-time iteration exceeded its step limit");
+  if (err & 2u)
+    return gpa_fail(GPA_ERR_TIMEOUT, "a per-partition test hit its step limit: the sets concerned are undecided");
   if (err & 4u) return gpa_fail(GPA_ERR_TIMEOUT, "a pipeline barrier wait exceeded its time limit");
   return gpa_fail(GPA_ERR_RANGE, "a device-resident set failed validation");
 }

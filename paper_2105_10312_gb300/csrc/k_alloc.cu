@@ -434,8 +434,11 @@ __global__ void __launch_bounds__(128) alloc_merge(DevSets S, DevModel md, gpa_p
       write_invalid(s, o, n, out, q.err);
       continue;
     }
-    merge_set(sm, s, o, n, md, p, out, mdiv, q.err);
+    if (lane == 0) sm.err = 0u;
     __syncwarp();
+    merge_set(sm, s, o, n, md, p, out, mdiv, &sm.err);
+    __syncwarp();
+    finish_set_errors(s, sm.err, out, q.err);
   }
 }
 
@@ -444,6 +447,7 @@ __global__ void __launch_bounds__(128) alloc_merge(DevSets S, DevModel md, gpa_p
 struct OneGpuSmem {
   SetSmem st;
   RtaScratch sc;
+  unsigned int err;  // error bits of the set being tested
 };
 // the dynamic shared memory opted in by alloc_kernels_init (227 KB per CTA at most)
 static_assert(4 * sizeof(MergeSmem) <= 232448, "merge kernel: four warps must fit 227 KB");
@@ -476,8 +480,11 @@ __global__ void __launch_bounds__(256) one_gpu(DevSets S, DevModel md, AllocOut 
       int lo = w * 32;
       all[w] = n >= lo + 32 ? kFull : (n > lo ? ((1u << (n - lo)) - 1u) : 0u);
     }
+    if (lane == 0) sm.err = 0u;
+    __syncwarp();
     bool ok = n == 0 ? true
-                     : warp_test(sm.st, all, (unsigned)md.M, md.kc, md.km, md.sched, mdiv, sm.sc, nullptr, true, err);
+                     : warp_test(sm.st, all, (unsigned)md.M, md.kc, md.km, md.sched, mdiv, sm.sc, nullptr, true,
+                                 &sm.err);
     unsigned long long Uc = 0, Um = 0;
     int nm = 0;
     for (int r = lane; r < n; r += 32) {
@@ -501,6 +508,7 @@ __global__ void __launch_bounds__(256) one_gpu(DevSets S, DevModel md, AllocOut 
       if (out.n_tests) out.n_tests[s] = 1;
     }
     __syncwarp();
+    finish_set_errors((long long)s, sm.err, out, err);
   }
 }
 

@@ -16,7 +16,10 @@
 // share the arrays, which keep the last call's contents; each call clears
 // the counters that must start at zero before its kernels run.  Calls whose
 // work overlaps on the GPU (on different streams, or from different threads)
-// race on the shared arrays and must be serialised by the caller.
+// race on the shared arrays and must be serialised by the caller.  The
+// kernels record problems (an invalid set, a test that hit its step limit)
+// in the arrays' error word, which gpa_allocate_noalloc_status reads and
+// clears.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -66,15 +69,7 @@ int32_t setup_current_device(DeviceSetup** out) {
   DeviceSetup& d = g_setup[dev];
   if (!d.ready) {
     gpa::MagicDivHost table[GPA_MMAX + 1];
-    for (int m = 0; m <= GPA_MMAX; m++) table[m] = gpa::MagicDivHost{0, 0, 0};
-    for (int m = 1; m <= GPA_MMAX; m++) {
-      const unsigned long long div = 1000000ull * (unsigned long long)m;
-      unsigned int l = 0;
-      while ((1ull << l) < div) l++;
-      const unsigned __int128 num = ((unsigned __int128)1 << (60 + l)) + div - 1;
-      table[m].magic = (unsigned long long)(num / div);
-      table[m].shift = l - 4;
-    }
+    gpa::build_reciprocals(table);
     void* p = nullptr;
     if ((e = cudaGetSymbolAddress(&p, g_scratch)) != cudaSuccess)
       return gpa_cuda_fail(e, "gpa_allocate_noalloc: cudaGetSymbolAddress(scratch)");
@@ -96,7 +91,39 @@ int32_t setup_current_device(DeviceSetup** out) {
   return GPA_OK;
 }
 
+// The work goes onto the caller's stream, the scratch addresses are the
+// current device's: the two must be the same device.
+int32_t check_stream_device(cudaStream_t stream, const char* who) {
+  int cur = 0, sdev = 0;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return gpa_cuda_fail(e, who);
+  e = cudaStreamGetDevice(stream, &sdev);
+  if (e != cudaSuccess) return gpa_cuda_fail(e, who);
+  if (sdev != cur)
+    return gpa_fail(GPA_ERR_ARG, "%s: the stream belongs to device %d, the current device is %d", who, sdev, cur);
+  return GPA_OK;
+}
+
 }  // namespace
+
+extern "C" int32_t gpa_allocate_noalloc_status(void* stream) {
+  int32_t st = check_stream_device((cudaStream_t)stream, "gpa_allocate_noalloc_status");
+  if (st != GPA_OK) return st;
+  DeviceSetup* d = nullptr;
+  if ((st = setup_current_device(&d)) != GPA_OK) return st;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return gpa_cuda_fail(e, "gpa_allocate_noalloc_status: cudaStreamSynchronize");
+  unsigned int err = 0;
+  if ((e = cudaMemcpy(&err, &d->scratch->err, sizeof err, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return gpa_cuda_fail(e, "gpa_allocate_noalloc_status: reading the error word");
+  if (!err) return GPA_OK;
+  if ((e = cudaMemset(&d->scratch->err, 0, sizeof err)) != cudaSuccess)
+    return gpa_cuda_fail(e, "gpa_allocate_noalloc_status: clearing the error word");
+  if (err & 2u)
+    return gpa_fail(GPA_ERR_TIMEOUT,
+                    "gpa_allocate_noalloc: a per-partition test hit its step limit (sets with GPA_REASON_UNDECIDED)");
+  return gpa_fail(GPA_ERR_RANGE, "gpa_allocate_noalloc: a set failed validation (sets with GPA_REASON_INVALID)");
+}
 
 extern "C" int32_t gpa_allocate_noalloc(void* stream, const gpa_tasksets* sets, const gpa_model* model,
                                         const gpa_params* params, gpa_alloc_result* r) {
@@ -120,8 +147,10 @@ extern "C" int32_t gpa_allocate_noalloc(void* stream, const gpa_tasksets* sets, 
   if (!sets->T || !sets->D || !sets->A || !sets->B || !sets->u_ppm || !sets->type || !r->verdict || !r->reason ||
       !r->n_parts || !r->Pi || !r->W || !r->part_of_task || !r->size_of_part)
     return gpa_fail(GPA_ERR_ARG, "gpa_allocate_noalloc: NULL array");
+  int32_t st = check_stream_device((cudaStream_t)stream, "gpa_allocate_noalloc");
+  if (st != GPA_OK) return st;
   DeviceSetup* d = nullptr;
-  int32_t st = setup_current_device(&d);
+  st = setup_current_device(&d);
   if (st != GPA_OK) return st;
   gpa::DevSets ds{sets->nsets,
                   sets->n_max,

@@ -45,6 +45,7 @@ struct SearchHead {
   unsigned long long bestK1[kSThreads / 32];
   unsigned long long bestK2[kSThreads / 32];
   unsigned long long gbestW;   // best W found by any thread of the CTA (for cutting)
+  unsigned int err;            // error bits of the set (kErrIter: a test hit its step limit)
   int n;
   long long set;
 };
@@ -66,8 +67,11 @@ struct WcetTables {
 };
 
 // Serial per-partition test (one thread): rows of S in priority order at m.
+// A fixed point that needs more than kIterCap steps leaves the test
+// undecided: kErrIter goes to *errp and the test returns false.
 __device__ bool serial_rta(const SearchHead& h, SearchThreads& w, unsigned int S, unsigned int m, unsigned int g,
-                           unsigned int kc, unsigned int km, const MagicDiv& md, const WcetTables& tb) {
+                           unsigned int kc, unsigned int km, const MagicDiv& md, const WcetTables& tb,
+                           unsigned int* errp) {
   const int tid = threadIdx.x;
   const int nm = __popc(S & h.memmask), ns = __popc(S);
   const bool cm = nm >= 2, cc = (ns - nm) >= 2;
@@ -100,7 +104,10 @@ __device__ bool serial_rta(const SearchHead& h, SearchThreads& w, unsigned int S
       }
       if (next == R) break;
       R = next;
-      if (++iter > kIterCap) return false;
+      if (++iter > kIterCap) {
+        atomicOr(errp, kErrIter);
+        return false;
+      }
     }
     Rprev = R;
   }
@@ -110,8 +117,9 @@ __device__ bool serial_rta(const SearchHead& h, SearchThreads& w, unsigned int S
 // The model's per-partition test, serially: DM as above, or EDF (the
 // tasks' WCETs into w.C, then the processor-demand test).
 __device__ bool serial_test(const SearchHead& h, SearchThreads& w, unsigned int S, unsigned int m, unsigned int g,
-                            unsigned int kc, unsigned int km, int sched, const MagicDiv& md, const WcetTables& tb) {
-  if (sched != GPA_SCHED_EDF) return serial_rta(h, w, S, m, g, kc, km, md, tb);
+                            unsigned int kc, unsigned int km, int sched, const MagicDiv& md, const WcetTables& tb,
+                            unsigned int* errp) {
+  if (sched != GPA_SCHED_EDF) return serial_rta(h, w, S, m, g, kc, km, md, tb, errp);
   const int tid = threadIdx.x;
   const int nm = __popc(S & h.memmask), ns = __popc(S);
   const bool cm = nm >= 2, cc = (ns - nm) >= 2;
@@ -124,7 +132,7 @@ __device__ bool serial_test(const SearchHead& h, SearchThreads& w, unsigned int 
                         : wcet(h.A[i], h.B[i], mem ? kmem : kcmp, m, md);
   }
   unsigned int eb = 0u;
-  return serial_edf(
+  const bool ok = serial_edf(
       ns,
       [&](int a, unsigned int& C, unsigned int& T, unsigned int& D, unsigned int& mg, unsigned int& sh) {
         const int i = (int)__fns(S, 0u, a + 1);
@@ -135,6 +143,8 @@ __device__ bool serial_test(const SearchHead& h, SearchThreads& w, unsigned int 
         sh = h.sh[i];
       },
       &eb);
+  if (eb) atomicOr(errp, eb);
+  return ok;
 }
 
 __device__ __forceinline__ Sizes sizes_of(const DevModel& md) {
@@ -148,13 +158,13 @@ __device__ __forceinline__ Sizes sizes_of(const DevModel& md) {
 // §4.1).
 __device__ unsigned int serial_minm(const SearchHead& h, SearchThreads& w, unsigned int S, unsigned int lo,
                                     const DevModel& md, const Sizes& z, const MagicDiv* __restrict__ mdiv,
-                                    const WcetTables& tb) {
+                                    const WcetTables& tb, unsigned int* errp) {
   const int e = z.count();
   int a = z.below(lo), b = e;
   while (a < b) {
     const int mid = a + (b - a) / 2;
     const unsigned int m = z.at(mid);
-    if (serial_test(h, w, S, m, (unsigned)md.g, md.kc, md.km, md.sched, mdiv[m], tb)) b = mid;
+    if (serial_test(h, w, S, m, (unsigned)md.g, md.kc, md.km, md.sched, mdiv[m], tb, errp)) b = mid;
     else a = mid + 1;
   }
   return a < e ? z.at(a) : 0u;
@@ -238,6 +248,7 @@ __global__ void __launch_bounds__(kSThreads) search_sets(DevSets S, DevModel md,
         h.memmask = mm;
         h.n = ok ? n : -1;
         h.gbestW = kNoKey;
+        h.err = 0u;
       }
       // prefix-completion counts: cnt[i][j] = ways to label positions i..L-1
       // with j blocks already open and at most kmax blocks in total
@@ -306,7 +317,7 @@ __global__ void __launch_bounds__(kSThreads) search_sets(DevSets S, DevModel md,
         dead = dead || z == 0u;
         lo = max(lo, z);
       }
-      msub[S2] = (unsigned short)(dead ? 0u : (__popc(S2) == 1 ? lo : serial_minm(h, w, S2, lo, md, z, mdiv, tb)));
+      msub[S2] = (unsigned short)(dead ? 0u : (__popc(S2) == 1 ? lo : serial_minm(h, w, S2, lo, md, z, mdiv, tb, &h.err)));
       const int nmS = __popc(S2 & h.memmask), ncS = __popc(S2) - nmS;
       unsigned long long Uc = 0, Um = 0;
       for (unsigned int r = S2; r; r &= r - 1u) {
@@ -464,7 +475,11 @@ __global__ void __launch_bounds__(kSThreads) search_sets(DevSets S, DevModel md,
       if (lane == 0) {
         const unsigned int sm = found ? (unsigned int)(best1 & 2047ull) : 0u;
         const int empty = (found && kmin > nb) ? kmin - nb : 0;
-        out.feasible[s] = found ? 1 : 0;
+        // a minimum size computed from an undecided test may be wrong: the
+        // optimum is then undecided (feasible = 2)
+        const unsigned int e = *(volatile unsigned int*)&h.err;
+        out.feasible[s] = e & kErrIter ? 2 : found ? 1 : 0;
+        if (e) atomicOr(err, e);
         out.W[s] = found ? (long long)(best1 >> 11) : 0;
         out.sum_minm[s] = (int)sm;
         out.n_blocks[s] = found ? nb : 0;

@@ -108,17 +108,11 @@ __device__ bool run_alg1(ServeSmem& sm, TenantSlot* t, ServeResp* rs, int n, con
   return ok;
 }
 
-__global__ void __launch_bounds__(128) serve_batch(const ServeReq* __restrict__ reqs, int nreq,
-                                                   TenantSlot* const* __restrict__ chunks, ServePayload pay,
-                                                   ServeResp* __restrict__ resps, DevModel md, gpa_params prm,
-                                                   const MagicDiv* __restrict__ mdiv, unsigned int* err) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int q = blockIdx.x * (blockDim.x >> 5) + warp;
-  if (q >= nreq) return;
-  ServeSmem& sm = reinterpret_cast<ServeSmem*>(smem_raw)[warp];
-  const ServeReq rq = reqs[q];
-  ServeResp* rs = resps + q;
+// One request by one warp.  err receives the request's error bits.
+__device__ void serve_one(ServeSmem& sm, const ServeReq rq, ServeResp* rs, TenantSlot* const* __restrict__ chunks,
+                          const ServePayload& pay, const DevModel& md, const gpa_params& prm,
+                          const MagicDiv* __restrict__ mdiv, unsigned int* err) {
+  const int lane = threadIdx.x & 31;
   if (lane == 0) {
     rs->verdict = 0;
     rs->reason = GPA_REASON_OK;
@@ -395,6 +389,30 @@ __global__ void __launch_bounds__(128) serve_batch(const ServeReq* __restrict__ 
     __syncwarp();
     copy_state_to_resp(t, rs);
     return;
+  }
+}
+
+// One warp per request.  A request whose analysis hit a test's step limit
+// (kErrIter) answers status 2 (GPA_ERR_TIMEOUT): the tenant's state is still
+// an allocation whose every partition passes, but the choice among them may
+// differ from that of the exact analysis.
+__global__ void __launch_bounds__(128) serve_batch(const ServeReq* __restrict__ reqs, int nreq,
+                                                   TenantSlot* const* __restrict__ chunks, ServePayload pay,
+                                                   ServeResp* __restrict__ resps, DevModel md, gpa_params prm,
+                                                   const MagicDiv* __restrict__ mdiv, unsigned int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (q >= nreq) return;
+  ServeSmem& sm = reinterpret_cast<ServeSmem*>(smem_raw)[warp];
+  if (lane == 0) sm.m.err = 0u;
+  __syncwarp();
+  serve_one(sm, reqs[q], resps + q, chunks, pay, md, prm, mdiv, &sm.m.err);
+  __syncwarp();
+  const unsigned int e = sm.m.err;
+  if (lane == 0 && e) {
+    if ((e & kErrIter) && resps[q].status == 0) resps[q].status = 2;
+    atomicOr(err, e);
   }
 }
 

@@ -66,6 +66,7 @@ struct TestSmem {
   RtaScratch sc;
   long long R[kNmax];          // per row
   unsigned char part[kNmax];   // per row
+  unsigned int err;            // error bits of the candidate being tested
 };
 
 // One warp per candidate: stage its set, then test every non-empty part at
@@ -126,7 +127,11 @@ __global__ void __launch_bounds__(256) test_candidates(DevSets S, DevModel md, C
     }
     for (int off = 16; off > 0; off >>= 1) total += __shfl_xor_sync(kFull, total, off);
     bool ok = total <= md.M;
+    if (lane == 0) sm.err = 0u;
     __syncwarp();
+    // ok: no part fails for certain; undecided: a part's test hit its step
+    // limit (the candidate is then undecided, 2, unless another part fails)
+    bool undecided = false;
     for (int p = 0; p < C.kparts; p++) {
       unsigned int Sp[kWords];
       unsigned int any = 0u;
@@ -140,15 +145,23 @@ __global__ void __launch_bounds__(256) test_candidates(DevSets S, DevModel md, C
       const int z = size[p];
       if (z == 0) {
         ok = false;
+        if (!Rout) break;
         continue;
       }
+      const unsigned int e0 = sm.err;
       const bool pass = warp_test(sm.st, Sp, (unsigned)z, (unsigned)md.kc, (unsigned)md.km, md.sched, mdiv, sm.sc,
-                                  Rout ? sm.R : nullptr, Rout == nullptr, err);
-      ok = ok && pass;
+                                  Rout ? sm.R : nullptr, Rout == nullptr, &sm.err);
+      if (!pass) {
+        if (sm.err != e0) undecided = true;
+        else ok = false;
+      }
       if (!ok && !Rout) break;
     }
     __syncwarp();
-    if (lane == 0) verdict[c] = ok ? 1 : 0;
+    if (lane == 0) {
+      verdict[c] = ok ? (undecided ? 2 : 1) : 0;
+      if (sm.err) atomicOr(err, sm.err);
+    }
     if (Rout) {
       for (int r = lane; r < n; r += 32) Rout[c * C.map_stride + sm.st.orig[r]] = sm.R[r];
       for (int t = n + lane; t < C.map_stride; t += 32) Rout[c * C.map_stride + t] = -1;

@@ -152,7 +152,7 @@ void harvest(ServeState* S, StreamCtx& sc) {
     gpa_response r;
     std::memset(&r, 0, sizeof r);
     r.req_id = p.id;
-    r.status = d.status ? GPA_ERR_RANGE : GPA_OK;
+    r.status = d.status == 1 ? GPA_ERR_RANGE : d.status == 2 ? GPA_ERR_TIMEOUT : GPA_OK;
     r.verdict = d.verdict;
     r.reason = d.reason;
     r.path = d.path;
@@ -168,7 +168,7 @@ void harvest(ServeState* S, StreamCtx& sc) {
       TenantInfo& ti = it->second;
       ti.busy = false;
       const bool drop = (p.op == GPA_SERVE_EVICT) || (p.op == GPA_SERVE_ADMIT && !d.verdict) ||
-                        (p.op == GPA_SERVE_ADMIT && d.status);
+                        (p.op == GPA_SERVE_ADMIT && d.status == 1);
       if (drop) {
         S->free_slots.push_back(ti.slot);
         S->tenants.erase(it);

@@ -150,30 +150,54 @@ def _edf_candidate_parity(ctx, s, M=1, kc=1000, km=1000):
     return vr
 
 
-def test_edf_utilisation_band_edges(ctx):
-    """Pairs of tasks whose U straddles the accepted bound 1 - 2^-10 by a few
-    WCET units, so the float pre-check defers to the exact integer terms;
-    constrained and implicit deadlines; verdicts equal the oracle's."""
+def test_edf_utilisation_one_edges(ctx):
+    """Sets whose U equals 1 exactly or misses it by one unit of C: harmonic
+    periods, 1/3 + 2/3 (the 2^64-scaled terms straddle 1, decided by the
+    periods' least common multiple), pairs of large coprime periods (U - 1 a
+    multiple of 1 / (T1 T2)); implicit deadlines, and a first deadline
+    shortened by one and by a quarter.  Every verdict equals the oracle's
+    exact test, and none is undecided."""
+    base = [([3, 3], [1, 2]), ([1000003, 2000006], [600001, 800004]), ([7, 14, 28], [3, 4, 8]),
+            ([1000, 4000, 500], [250, 1000, 250])]
+    T1, T2 = 1329, 1048573
+    for C1 in (1, 664, 1328):
+        base.append(([T1, T2], [C1, (T2 * (T1 - C1)) // T1]))
     sets = []
-    T1 = T2 = 1000000
-    for dc in range(-40, 41, 4):
-        C1 = 499000
-        C2 = 500023 + dc        # U = (C1 + C2) / 10^6 around 1 - 2^-10 = 0.9990234375
-        sets.append([(T1, T1, C1), (T2, T2, C2)])
-        sets.append([(T1, 999999, C1), (T2, T2, C2)])
-    for dc in range(-30, 31, 3):
-        sets.append([(3 * 1000003, 3 * 1000003, 1500000 + dc), (2000000, 1999000, 998000)])
-    # floored and rounded-up band sums straddling the bound by one unit: a miss,
-    # and one unit of C less passes
-    for c2 in (523657, 523656):
-        sets.append([(1329, 1329, 664), (1048573, 1048573, c2)])
+    for T, C in base:
+        for dc in (-1, 0, 1):
+            CC = list(C[:-1]) + [C[-1] + dc]
+            if not 1 <= CC[-1] <= T[-1]:
+                continue
+            for cut in (0, 1, T[0] // 4):
+                D = [T[0] - cut] + list(T[1:])
+                if CC[0] <= D[0]:
+                    sets.append(list(zip(T, D, CC)))
+    s = _crafted_batch(sets)
+    v = _edf_candidate_parity(ctx, s)
+    assert 0 < v.sum() < len(v) and (v <= 1).all()
+
+
+def test_edf_near_one(ctx):
+    """Eight tasks on periods in [10^5, 10^6] with U = 1 - 2^-k, k = 11..17
+    (rounded to whole WCET units), constrained and implicit deadlines: the
+    L_a bound and the QPA walk grow like 2^k; verdicts equal the oracle's."""
+    rng = np.random.default_rng(11)
+    sets = []
+    for k in (11, 13, 15, 17):
+        for trial in range(4):
+            n = 8
+            T = rng.integers(100_000, 1_000_000, n)
+            w = rng.random(n)
+            C = np.floor((1 - 2.0 ** -k) * w / w.sum() * T).astype(np.int64)
+            C = np.maximum(C, 1)
+            D = T if trial % 2 == 0 else np.maximum(C, (T * 0.9).astype(np.int64))
+            sets.append(list(zip(T.tolist(), D.tolist(), C.tolist())))
     v = _edf_candidate_parity(ctx, _crafted_batch(sets))
-    assert 0 < v.sum() < len(v)
-    assert list(v[-2:]) == [0, 1]
+    assert (v <= 1).all() and v.sum() > 0
 
 
 def test_edf_busy_period_beyond_31_bits(ctx):
-    """Many large tasks at U close to the bound: the busy period and the QPA
+    """Many large tasks at U close to 1: the busy period and the QPA
     points pass 2^31, so the 64-bit division paths run; verdicts equal the
     oracle's."""
     rng = np.random.default_rng(7)
