@@ -1,10 +1,10 @@
 """Tests whose analysis cannot finish within the kernels' step limits are
-reported as undecided, never as misses: a deadline-monotonic fixed point
+reported as undecided, never as misses: a deadline-monotonic iteration
 that needs more than 2^20 steps, and an EDF set whose U lies within n 2^-64
 of 1 over periods whose least common multiple exceeds 2^62.  The first is
-schedulable by the oracle's exact iteration; the second is beyond the
-oracle too (its busy period passes 2^100), so the test checks the condition
-the header states instead."""
+decided (a miss) by the oracle's unbounded iteration; the second is beyond
+the oracle too (its busy period passes 2^100), so the test checks the
+condition the header states instead."""
 import math
 from fractions import Fraction
 
@@ -71,17 +71,17 @@ def _near_one_set():
 
 
 def test_dm_fixed_point_beyond_the_step_limit(ctx):
-    """One higher-priority task (T = 1024, C = 1023) in front of a task with
-    C = 1.5 2^20 and D = T = 2^31 - 1: the fixed point is C 2^10 = 1.5 2^30
-    <= D, reached after about 1.5 2^20 steps.  The GPU gives up after 2^20
-    (candidate verdict 2, set reason UNDECIDED, sync GPA_ERR_TIMEOUT); the
-    oracle's unbounded iteration finds R = 1.5 2^30."""
-    C2 = 3 << 19
-    tasks = [(1024, 1024, 1023), ((1 << 31) - 1, (1 << 31) - 1, C2)]
+    """A higher-priority task with T = D = C = 1 in front of a task with
+    C = 1 and D = T = 2^21: the second task's iteration R = 1 + ceil(R / 1)
+    climbs by one per step, so it passes D only after about 2^21 steps.  The
+    GPU gives up after 2^20 (candidate verdict 2, set reason UNDECIDED, sync
+    GPA_ERR_TIMEOUT); the oracle's unbounded iteration finds the miss."""
+    D2 = 1 << 21
+    tasks = [(1, 1, 1), (D2, D2, 1)]
     s = _crafted([tasks])
     vr, Rr = oracle.test_schedulable(s, 1, 1, 1000, 1000, np.zeros(1, np.int64), np.zeros(2, np.uint8), 2, 1,
                                      np.ones(1, np.int32))
-    assert vr[0] == 1 and Rr[1] == C2 << 10
+    assert vr[0] == 0 and list(Rr) == [1, -1]
     d = gpa.to_device(s)
     v, R = ctx.test_schedulable(d, 1, torch.zeros(1, dtype=torch.int64).cuda(),
                                 torch.zeros(2, dtype=torch.uint8).cuda(), torch.ones(1, dtype=torch.int32).cuda(),
