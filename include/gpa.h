@@ -166,8 +166,11 @@ int32_t gpa_ctx_launch_count(gpa_ctx* ctx, int64_t* out);
 
 /* Context options (gpa_ctx_set_option).  None changes any result. */
 enum {
-  GPA_OPT_AUTOTUNE = 1,       /* 1: time the fast allocate kernel's launch shapes on the first call of each
-                                 batch signature and keep the fastest (default 0) */
+  GPA_OPT_AUTOTUNE = 1,       /* 1: on the first gpa_allocate call of each batch signature, time the
+                                 launch shapes of the kernels the call runs (the fast kernel's loads,
+                                 warps and sets per ticket; the merge kernel's warps per CTA, warps
+                                 per set and CTAs per SM; the 1G kernel's warps per CTA) and keep the
+                                 fastest for that signature (default 0) */
   GPA_OPT_GRAPH = 2,          /* 1: capture gpa_allocate's launches in a CUDA graph per argument set and
                                  replay it (default 0); not allowed while the stream is being captured */
   GPA_OPT_FAST_WARPS = 3,     /* force warps per CTA of the fast allocate kernel: 1, 2, 4 or 8 (the staged
@@ -188,11 +191,20 @@ enum {
                                  rejected batch leaves the outputs untouched); n in 2..64 = as 0 but
                                  every batch split into n slices (fewer when it has fewer sets)
                                  (default 0) */
-  GPA_OPT_HOST_COPY = 10      /* how host buffers move: 0 = arrays that are page-locked (cudaHostAlloc,
+  GPA_OPT_HOST_COPY = 10,     /* how host buffers move: 0 = arrays that are page-locked (cudaHostAlloc,
                                  cudaHostRegister) are read and written by one staging kernel per
                                  direction and slice, over the host link, with up to 16 CTAs per array;
                                  other arrays by cudaMemcpyAsync; 1 = cudaMemcpyAsync for every array;
                                  n in 2..256 = the staging kernel with n CTAs per array (default 0) */
+  GPA_OPT_MERGE_WARPS = 11,   /* force warps per CTA of the merge kernel (Alg. 1 for the sets the fast
+                                 kernel could not decide): 1..8, a multiple of GPA_OPT_MERGE_GROUP; lowered
+                                 to the largest such multiple whose shared memory fits one SM
+                                 (0 = tuned/default) */
+  GPA_OPT_MERGE_GROUP = 12,   /* force warps per task set in the merge kernel: 1, 2, 4 or 8; a set's
+                                 candidate merges are spread over its warps (0 = tuned/default) */
+  GPA_OPT_MERGE_BLOCKS = 13,  /* force CTAs of the persistent merge grid (0 = tuned/default) */
+  GPA_OPT_TEST_WARPS = 14     /* force warps per CTA of the 1G kernel (one test of all tasks at M per
+                                 set, one warp per set): 1..8 (0 = tuned/default) */
 };
 int32_t gpa_ctx_set_option(gpa_ctx* ctx, int32_t option, int64_t value);
 
@@ -201,6 +213,14 @@ int32_t gpa_ctx_set_option(gpa_ctx* ctx, int32_t option, int64_t value);
  * every other entry point: its one kernel).  Waits for that call's work.
  * ms[0 .. *count) are written, at most n of them. */
 int32_t gpa_ctx_last_timing(gpa_ctx* ctx, float* ms, int32_t n, int32_t* count);
+
+/* Interference terms evaluated by the kernels of the context's last
+ * gpa_allocate, gpa_test_schedulable, gpa_search_best or gpa_search_explicit
+ * call on device buffers (one launch sequence; a call on host buffers may
+ * run several, and the count then covers its last slice).  A term is one
+ * ceil(R / T_j) C_j of a response-time iteration (§5.5, DM), or one task's
+ * demand in a busy-period or QPA step (EDF).  Waits for the context stream. */
+int32_t gpa_ctx_last_terms(gpa_ctx* ctx, int64_t* terms);
 
 /* --------------------------------------------------------------- task sets */
 
@@ -426,6 +446,28 @@ typedef struct {
 int32_t gpa_search_best(gpa_ctx* ctx, const gpa_tasksets* sets, const gpa_model* model,
                         int32_t kmin, int32_t kmax, gpa_best_result* result);
 
+/* a6/a8 on the explicit candidates, enumerated on the device: for each set,
+ * every composition of Mu = M / g into k in [kmin, min(kmax, Mu)] positive
+ * parts (part b gets parts[b] * g SMs) times every map of its n tasks to the
+ * k parts (problem statement of §5: an SM split and a task-to-partition
+ * allocation).  Candidate ranks run over k, then the composition in
+ * lexicographic order of its parts, then the map code c, which sends task i
+ * (in set order) to part (c / k^i) mod k.  A candidate is feasible iff
+ * every non-empty part passes the model's test at its size; the result is
+ * the optimum of gpa_search_best (the same key and fields; identical
+ * values), here found over the explicit space.
+ *  - cand_verdict (nullable; memory of sets->mem): [nsets * cand_stride]
+ *    bytes, candidate r of set s at s * cand_stride + r: 1 feasible,
+ *    0 not, 2 undecided (a test hit its step limit); entries past a set's
+ *    own count are 255.  cand_stride = the count for n_max tasks, returned
+ *    in *ncand (nullable) by every call, also when cand_verdict is NULL.
+ *  - Limits: n_max <= GPA_SEARCH_NMAX, 1 <= kmin <= kmax <= GPA_SEARCH_KMAX,
+ *    at most GPA_EXPLICIT_MAX candidates per set (GPA_ERR_RANGE);
+ *    admissible size lists are not supported (GPA_ERR_ARG). */
+#define GPA_EXPLICIT_MAX (1ll << 26)
+int32_t gpa_search_explicit(gpa_ctx* ctx, const gpa_tasksets* sets, const gpa_model* model, int32_t kmin,
+                            int32_t kmax, gpa_best_result* result, uint8_t* cand_verdict, int64_t* ncand);
+
 /* ----------------------------------------------------------------- serving */
 
 /* Admission control as a service: tenants (task sets of up to
@@ -566,6 +608,39 @@ int32_t gpa_measure_wcet(gpa_ctx* ctx, const gpa_probe_cfg* cfg, const int32_t* 
  * skipped.  Errors: GPA_ERR_ARG (NULL, fewer than two usable points or all
  * at one m). */
 int32_t gpa_fit_wcet(const int32_t* m, const double* ms, int32_t n, double* a, double* b);
+
+/* The kernel under test of gpa_measure_wcet run once, on the whole device,
+ * on the caller's data, so that what it computes can be checked: `a` (and
+ * `b` for GPA_PROBE_VADD; may be NULL otherwise) are host arrays of n
+ * floats (VADD, COMPUTE) or n x n floats, row-major (TRANSPOSE, STENCIL);
+ * `out` (host, same size) receives c = a + b (VADD), the transpose of a
+ * (TRANSPOSE), one sweep c = a + 0.1 (left + right + up + down - 4 a) with
+ * edge cells reusing their own value for a missing neighbour (STENCIL), or
+ * y_64 with y_0 = 1, y_{k+1} = y_k a + 0.5 (COMPUTE, fused multiply-adds).
+ * ctas = 0: 4 per SM.  Synchronous; allocates and frees its device buffers.
+ * Errors as gpa_measure_wcet. */
+int32_t gpa_probe_run(gpa_ctx* ctx, int32_t kernel, int64_t n, int32_t ctas, const float* a, const float* b,
+                      float* out);
+
+/* -------------------------------------- integer throughput of the device
+ *
+ * The ceiling against which the tests' throughput is reported: the rate at
+ * which every SM of the context's device evaluates interference terms
+ * ceil(R / T_j) C_j of the response-time iteration (§5.5) with the same
+ * arithmetic the test kernels use (the period's reciprocal from shared
+ * memory, a 32 x 32 -> 64-bit multiply and shift, a 64-bit product with C_j,
+ * the D + 1 cap and a 64-bit sum), four independent iterations per thread,
+ * all warps busy; and, for context, the rate of dependent-free 32-bit
+ * integer multiply-adds.  Each is the best of five timed launches (CUDA
+ * events on the context stream) of about 2-5 ms.  Synchronous; allocates
+ * and frees a small device buffer. */
+typedef struct {
+  double terms_per_s;  /* interference terms per second, whole device */
+  double imad_per_s;   /* 32-bit integer multiply-adds per second, whole device */
+  double term_ms;      /* device time of the best term launch */
+  int64_t terms;       /* terms evaluated by one term launch */
+} gpa_alu_peak;
+int32_t gpa_measure_alu_peak(gpa_ctx* ctx, gpa_alu_peak* out);
 
 #ifdef __cplusplus
 }

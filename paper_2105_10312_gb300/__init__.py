@@ -31,7 +31,8 @@ SCHED = {"DM": 0, "EDF": 1}
 REASON = {"OK": 0, "LEMMA1": 1, "LEMMA2": 2, "NO_MERGE": 3, "TEST": 4, "INVALID": 5, "UNDECIDED": 6}
 OPT = {"AUTOTUNE": 1, "GRAPH": 2, "FAST_WARPS": 3, "FAST_CHUNK": 4, "FAST_BLOCKS": 5, "PER_SET_LAUNCH": 6,
        "PROFILE": 7, "FAST_STAGES": 8, "HOST_SLICES": 9,
-       "HOST_COPY": 10}
+       "HOST_COPY": 10, "MERGE_WARPS": 11, "MERGE_GROUP": 12, "MERGE_BLOCKS": 13, "TEST_WARPS": 14}
+EXPLICIT_MAX = 1 << 26
 NMAX, SERVE_NMAX, MMAX, SEARCH_NMAX, SEARCH_KMAX = 256, 128, 1024, 14, 8
 
 _vp = ctypes.c_void_p
@@ -96,6 +97,11 @@ class BestResult(ctypes.Structure):
 _lib = None
 
 
+class AluPeak(ctypes.Structure):
+    _fields_ = [("terms_per_s", ctypes.c_double), ("imad_per_s", ctypes.c_double), ("term_ms", ctypes.c_double),
+                ("terms", ctypes.c_int64)]
+
+
 def _set_signatures(L):
     L.gpa_ctx_create.argtypes = [ctypes.c_int32, _vp, ctypes.POINTER(_vp)]
     L.gpa_ctx_destroy.argtypes = [_vp]
@@ -122,6 +128,10 @@ def _set_signatures(L):
     L.gpa_allocate_noalloc.argtypes = [_vp, ctypes.POINTER(Tasksets), ctypes.POINTER(Model), ctypes.POINTER(Params),
                                        ctypes.POINTER(AllocResult)]
     L.gpa_allocate_noalloc_status.argtypes = [_vp]
+    L.gpa_ctx_last_terms.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
+    L.gpa_search_explicit.argtypes = [_vp, ctypes.POINTER(Tasksets), ctypes.POINTER(Model), ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.POINTER(BestResult), _vp, ctypes.POINTER(ctypes.c_int64)]
+    L.gpa_measure_alu_peak.argtypes = [_vp, ctypes.POINTER(AluPeak)]
 
 
 def lib():
@@ -267,6 +277,19 @@ class Context:
         _check(lib().gpa_ctx_last_timing(self._h, ms, 4, ctypes.byref(cnt)))
         return [ms[i] for i in range(cnt.value)]
 
+    def last_terms(self):
+        """Interference terms the kernels of the last device-buffer call evaluated."""
+        out = ctypes.c_int64()
+        _check(lib().gpa_ctx_last_terms(self._h, ctypes.byref(out)))
+        return out.value
+
+    def measure_alu_peak(self):
+        """The device's rate of interference terms and of integer multiply-adds."""
+        pk = AluPeak()
+        _check(lib().gpa_measure_alu_peak(self._h, ctypes.byref(pk)))
+        return {"terms_per_s": pk.terms_per_s, "imad_per_s": pk.imad_per_s, "term_ms": pk.term_ms,
+                "terms": pk.terms}
+
     @property
     def handle(self):
         return self._h
@@ -350,6 +373,39 @@ class Context:
         res = BestResult(mem, 0, _ptr(out["feasible"]), _ptr(out["W"]), _ptr(out["sum_minm"]),
                          _ptr(out["n_blocks"]), _ptr(out["spare"]), _ptr(out["rgs"]), _ptr(out["minm_block"]))
         _check(lib().gpa_search_best(self._h, ctypes.byref(ts), ctypes.byref(md), kmin, kmax, ctypes.byref(res)))
+        return out
+
+    def explicit_count(self, sets, M, g=1, kmin=1, kmax=4, k_c_pm=1200, k_m_pm=2300, sched="DM"):
+        """Explicit candidates per set for the batch's n_max (the cand_verdict stride)."""
+        ts, _ = make_tasksets(sets)
+        md = make_model(M, g, k_c_pm, k_m_pm, sched)
+        n = ctypes.c_int64()
+        empty = Tasksets(0, ts.mem, ts.n_max, ts.set_off, None, None, None, None, None, None)
+        res = BestResult(ts.mem, 0, None, None, None, None, None, None, None)
+        _check(lib().gpa_search_explicit(self._h, ctypes.byref(empty), ctypes.byref(md), kmin, kmax,
+                                         ctypes.byref(res), None, ctypes.byref(n)))
+        return n.value
+
+    def search_explicit(self, sets, M, g=1, k_c_pm=1200, k_m_pm=2300, kmin=1, kmax=4, out=None, sched="DM",
+                        cand_verdict=False):
+        """The optimum over every explicit candidate (composition x map); with
+        cand_verdict=True also every candidate's verdict, [nsets, count]."""
+        ts, mem = make_tasksets(sets)
+        md = make_model(M, g, k_c_pm, k_m_pm, sched)
+        if out is None:
+            out = self.best_result(sets, kmax)
+        res = BestResult(mem, 0, _ptr(out["feasible"]), _ptr(out["W"]), _ptr(out["sum_minm"]),
+                         _ptr(out["n_blocks"]), _ptr(out["spare"]), _ptr(out["rgs"]), _ptr(out["minm_block"]))
+        cv = None
+        if cand_verdict:
+            stride = self.explicit_count(sets, M, g, kmin, kmax, k_c_pm, k_m_pm, sched)
+            dev = sets["T"].device if mem == DEVICE else None
+            cv = _empty_like_mem(mem, (_len(sets["set_off"]) - 1) * stride, np.uint8, dev)
+        n = ctypes.c_int64()
+        _check(lib().gpa_search_explicit(self._h, ctypes.byref(ts), ctypes.byref(md), kmin, kmax, ctypes.byref(res),
+                                         _ptr(cv), ctypes.byref(n)))
+        if cand_verdict:
+            out["cand_verdict"] = cv.reshape(-1, n.value) if n.value else cv
         return out
 
 
@@ -502,8 +558,21 @@ class ProbeCfg(ctypes.Structure):
 
 def _probe_sigs(L):
     L.gpa_measure_wcet.argtypes = [_vp, ctypes.POINTER(ProbeCfg), _vp, ctypes.c_int32, _vp, _vp]
+    L.gpa_probe_run.argtypes = [_vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _vp, _vp, _vp]
     L.gpa_fit_wcet.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_double)]
+
+
+def probe_run(ctx, kernel, n, a, b=None, ctas=0):
+    """gpa_probe_run: probe `kernel` once on the whole GPU on host float32
+    data a (and b); returns its output."""
+    _probe_sigs(lib())
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    b = None if b is None else np.ascontiguousarray(b, dtype=np.float32)
+    out = np.empty_like(a)
+    _check(lib().gpa_probe_run(ctx.handle, PROBE[kernel], int(n), int(ctas), a.ctypes.data,
+                               None if b is None else b.ctypes.data, out.ctypes.data))
+    return out
 
 
 def measure_wcet(ctx, kernel, m, n, reps=5, interfere=False, ctas=0):

@@ -20,7 +20,7 @@ LIB = os.path.join(PKG, "libgpa.so")
 GENLIB = os.path.join(PKG, "libgpa_gen.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["k_alloc.cu", "k_test.cu", "k_search.cu", "k_serve.cu", "k_noalloc.cu", "k_stage.cu",
+CU_SOURCES = ["k_alloc.cu", "k_test.cu", "k_search.cu", "k_serve.cu", "k_noalloc.cu", "k_stage.cu", "k_peak.cu",
               "k_alloc_wide.cu", "k_test_wide.cu", "k_alloc_small.cu", "k_probe.cu"]
 CPP_SOURCES = ["host.cpp", "serve.cpp", "probe.cpp"]
 C_SOURCES = ["gen.c"]

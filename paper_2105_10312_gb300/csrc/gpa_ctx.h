@@ -29,7 +29,7 @@ struct gpa_ctx {
   cudaStream_t stream = nullptr;
   int sm_count = 0;
   gpa::MagicDivHost* d_mdiv = nullptr;      // [GPA_MMAX + 1] reciprocals of 10^6 m
-  unsigned long long* d_counters = nullptr; // [8] work-queue tickets
+  unsigned long long* d_counters = nullptr; // [8] work-queue tickets, [4] interference terms of the last call
   unsigned int* d_err = nullptr;            // sticky error word
   long long* d_slow = nullptr;              // deferred-set queue of the allocate kernels
   long long slow_cap = 0;
@@ -43,6 +43,8 @@ struct gpa_ctx {
   gpa::Prof prof{};                          // timing events of direct (non-graph) calls
   const gpa::Prof* last_prof = nullptr;      // events of the last profiled call
   gpa::LaunchShape force_fast{0, 0, 0, 0};
+  gpa::LaunchShape force_merge{0, 0, 0, 0};  // GPA_OPT_MERGE_*: warps per CTA, warps per set, CTAs
+  int force_test_warps = 0;                   // GPA_OPT_TEST_WARPS
   int host_slices = 0;                       // GPA_OPT_HOST_SLICES
   int host_copy = 0;                         // GPA_OPT_HOST_COPY
   cudaStream_t copy_in = nullptr;            // sliced host path: host-to-device copies
@@ -51,7 +53,7 @@ struct gpa_ctx {
   unsigned int* h_err = nullptr;             // page-locked copy of the error word read at the end of a call
   std::vector<unsigned short> size_table;   // last admissible-size table copied to the device
   void* size_table_ptr = nullptr;
-  std::map<std::string, gpa::LaunchShape> tuned;
+  std::map<std::string, gpa::AllocShapes> tuned;  // autotuned shapes per batch signature
   std::map<std::string, CachedGraph> graphs;
   ServeState* serve = nullptr;
 };

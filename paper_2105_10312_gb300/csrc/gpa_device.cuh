@@ -168,7 +168,16 @@ struct RtaScratch {
   unsigned int D[kNmax];
   unsigned char sh[kNmax];
   unsigned char pos[kNmax];
+  // interference terms evaluated by this warp's tests: ceil(R / T_j) C_j of
+  // the response-time iteration, or one task's demand of an EDF step
+  unsigned long long terms;
 };
+
+// Adds the lanes' term counts (each below 2^32) to a per-warp counter.
+__device__ __forceinline__ void warp_add_terms(unsigned long long& total, unsigned int nt) {
+  const unsigned int lo = __reduce_add_sync(0xffffffffu, nt & 0xFFFFu), hi = __reduce_add_sync(0xffffffffu, nt >> 16);
+  if ((threadIdx.x & 31) == 0) total += ((unsigned long long)hi << 16) + lo;
+}
 
 // Stage set [o, o + n) into st (warp-cooperative).  Returns false (on all
 // lanes) if any task violates the validation bounds.
@@ -326,18 +335,28 @@ static __device__ __noinline__ bool warp_rta(const SetSmem& st, const unsigned i
   const int lane = threadIdx.x & 31;
   const int s = compact_partition(st, S, m, kc, km, mdiv[m], sc);
   bool all_ok = true;
-  unsigned int errbits = 0u;
+  unsigned int errbits = 0u, nt = 0u;
+  // Start values: the least fixed points grow along the priority order by at
+  // least each task's own WCET (R_i >= R_{i-1} + C_i), so task i starts at
+  // R_last + C_{c0} + ... + C_i, R_last being where the previous chunk's last
+  // task stopped (its fixed point, or an iterate below it); every start is
+  // at most the fixed point, so the iteration reaches the same one.
+  unsigned long long Rlast = 0ull;
   for (int c0 = 0; c0 < s; c0 += 32) {
     const int i = c0 + lane;
     const bool active = i < s;
     unsigned int Ci = 0, Di = 0;
-    unsigned long long R = 0ull;
     if (active) {
       Ci = sc.C[i];
       Di = sc.D[i];
-      R = Ci;
-      for (int j = 0; j < i; j++) R += sc.C[j];
     }
+    unsigned long long pre = Ci;  // inclusive prefix sum of the chunk's WCETs
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long v = __shfl_up_sync(kFull, pre, o);
+      if (lane >= o) pre += v;
+    }
+    unsigned long long R = active ? Rlast + pre : 0ull;
     bool done = !active, ok = true;
     int iter = 0;
     while (__any_sync(kFull, !done)) {
@@ -349,6 +368,7 @@ static __device__ __noinline__ bool warp_rta(const SetSmem& st, const unsigned i
           const unsigned int Rc = (unsigned int)R;
           const unsigned long long cap = (unsigned long long)Di + 1ull;
           unsigned long long next = Ci;
+          nt += (unsigned int)i;
           for (int j = 0; j < i; j++) {
             unsigned int q = ceil_div_T(Rc, sc.mT[j], sc.sh[j]);
             unsigned long long t = (unsigned long long)q * sc.C[j];
@@ -368,9 +388,11 @@ static __device__ __noinline__ bool warp_rta(const SetSmem& st, const unsigned i
     if (R_row && active) R_row[sc.pos[i]] = ok ? (long long)R : -1LL;
     all_ok = __all_sync(kFull, ok) && all_ok;
     if (early_exit && !all_ok) break;
+    Rlast = __shfl_sync(kFull, R, min(31, s - 1 - c0));
   }
   errbits = __reduce_or_sync(kFull, errbits);
   if (errbits && lane == 0) atomicOr(err, errbits);
+  warp_add_terms(sc.terms, nt);
   __syncwarp();
   return all_ok;
 }
@@ -623,6 +645,7 @@ static __device__ __noinline__ bool warp_edf(const SetSmem& st, const unsigned i
   int iter = 0;
   for (;;) {
     unsigned long long part = 0;
+    if (lane == 0) sc.terms += (unsigned int)s;
     for (int i = lane; i < s; i += 32) part += ceil_div_T64(L, sc.T[i], sc.mT[i], sc.sh[i]) * sc.C[i];
     const unsigned long long next = warp_sum_u64_edf(part);
     if (next == L) break;
@@ -650,6 +673,7 @@ static __device__ __noinline__ bool warp_edf(const SetSmem& st, const unsigned i
   iter = 0;
   while (t > 0ull) {
     unsigned long long part = 0;
+    if (lane == 0) sc.terms += (unsigned int)s;
     for (int i = lane; i < s; i += 32) {
       const unsigned int D = sc.D[i];
       if (D <= t) part += (floor_div_T64(t - D, sc.T[i], sc.mT[i], sc.sh[i]) + 1ull) * sc.C[i];
@@ -677,9 +701,10 @@ static __device__ __noinline__ bool warp_edf(const SetSmem& st, const unsigned i
 
 // The same EDF test by one thread over k tasks; get(a, C, T, D, mg, sh)
 // yields the a-th with its period's reciprocal.  An undecided test sets
-// kErrIter in *errbits and returns false.
+// kErrIter in *errbits and returns false.  nterms counts the demand terms
+// evaluated (k per busy-period or QPA step).
 template <class Get>
-__device__ bool serial_edf(int k, Get get, unsigned int* errbits) {
+__device__ bool serial_edf(int k, Get get, unsigned int* errbits, unsigned int& nterms) {
   unsigned int C, T, D, mg, sh;
   if (k == 0) return true;
   if (k == 1) {
@@ -738,6 +763,7 @@ __device__ bool serial_edf(int k, Get get, unsigned int* errbits) {
   int iter = 0;
   for (;;) {
     unsigned long long next = 0;
+    nterms += (unsigned int)k;
     for (int a = 0; a < k; a++) {
       get(a, C, T, D, mg, sh);
       next += ceil_div_T64(L, T, mg, sh) * C;
@@ -766,6 +792,7 @@ __device__ bool serial_edf(int k, Get get, unsigned int* errbits) {
   iter = 0;
   while (t > 0ull) {
     unsigned long long h = 0;
+    nterms += (unsigned int)k;
     for (int a = 0; a < k; a++) {
       get(a, C, T, D, mg, sh);
       if (D <= t) h += (floor_div_T64(t - D, T, mg, sh) + 1ull) * C;

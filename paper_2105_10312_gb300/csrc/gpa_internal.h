@@ -87,7 +87,8 @@ cudaError_t launch_probe_kernel(int kernel, int ctas, const ProbeBuffers& b, uns
 
 // Work-queue state of the persistent allocate kernels.
 struct AllocQueue {
-  unsigned long long* counters;  // [4]: fast ticket, slow count, slow ticket, 1G ticket
+  unsigned long long* counters;  // [5]: fast ticket, slow count, slow ticket, 1G / search ticket,
+                                 // interference terms evaluated by the call's kernels
   long long* slow_sets;          // [nsets] sets deferred to the merge kernel
   unsigned int* err;             // sticky error word
 };
@@ -103,9 +104,17 @@ void prof_mark(Prof* p, cudaStream_t st);
 
 struct LaunchShape {
   int warps_per_block;  // warps per CTA
-  int chunk;            // sets per ticket (fast kernel)
+  int chunk;            // sets per ticket (fast kernel); warps per set (merge kernel)
   int blocks;           // CTAs of the persistent grid
   int stages;           // fast kernel: 1 = direct loads, 2..5 = shared-memory stages fed by bulk copies
+};
+
+// The launch shapes of one gpa_allocate call: the fast kernel, the merge
+// kernel (chunk = warps per set) and the 1G kernel.
+struct AllocShapes {
+  LaunchShape fast;
+  LaunchShape slow;
+  LaunchShape one;
 };
 
 struct BestOut {
@@ -149,9 +158,22 @@ cudaError_t launch_test_schedulable(const DevSets& s, const DevModel& md, const 
 cudaError_t launch_search_best(const DevSets& s, const DevModel& md, int kmin, int kmax, const BestOut& out,
                                const AllocQueue& q, const MagicDivHost* mdiv, int sm_count, cudaStream_t st,
                                long long* launches, Prof* prof);
+// The explicit candidates (every composition x map) of each set; cverdict
+// (nullable) receives each candidate's verdict at cstride bytes per set.
+cudaError_t launch_search_explicit(const DevSets& s, const DevModel& md, int kmin, int kmax, const BestOut& out,
+                                   unsigned char* cverdict, long long cstride, const AllocQueue& q,
+                                   const MagicDivHost* mdiv, int sm_count, cudaStream_t st, long long* launches,
+                                   Prof* prof);
+// Measured throughput of the integer work the tests are made of (k_peak.cu).
+cudaError_t measure_alu_peak(int sm_count, cudaStream_t st, double* terms_per_s, double* imad_per_s,
+                             double* term_ms, long long* terms);
 
 // Largest dynamic shared memory (bytes) the allocate merge kernel needs per CTA.
-size_t slow_smem_bytes(int warps_per_block);
+size_t slow_smem_bytes(int warps_per_block, int warps_per_set);
+// CTAs per SM of the merge kernel (wpb warps per CTA in groups of gw) and of
+// the 1G kernel (wpb warps per CTA), by occupancy; 0 when none fits.
+int merge_ctas_per_sm(int wpb, int gw);
+int one_gpu_ctas_per_sm(int wpb);
 size_t staged_smem_bytes(int stages);
 size_t one_gpu_smem_bytes(int warps_per_block);
 
@@ -162,6 +184,8 @@ size_t one_gpu_smem_bytes(int warps_per_block);
 constexpr int kSmallNmax = 64;
 constexpr int kNarrowNmax = 128;
 namespace small {
+int merge_ctas_per_sm(int wpb, int gw);
+int one_gpu_ctas_per_sm(int wpb);
 cudaError_t launch_allocate(const DevSets& s, const DevModel& md, const gpa_params& p, const AllocOut& out,
                             const AllocQueue& q, const MagicDivHost* mdiv, const LaunchShape& fast,
                             const LaunchShape& slow, cudaStream_t st, long long* launches, Prof* prof);
@@ -171,6 +195,8 @@ cudaError_t launch_one_gpu(const DevSets& s, const DevModel& md, const AllocOut&
 cudaError_t alloc_kernels_init();
 }  // namespace small
 namespace wide {
+int merge_ctas_per_sm(int wpb, int gw);
+int one_gpu_ctas_per_sm(int wpb);
 cudaError_t launch_allocate(const DevSets& s, const DevModel& md, const gpa_params& p, const AllocOut& out,
                             const AllocQueue& q, const MagicDivHost* mdiv, const LaunchShape& fast,
                             const LaunchShape& slow, cudaStream_t st, long long* launches, Prof* prof);

@@ -330,6 +330,28 @@ extern "C" int32_t gpa_ctx_last_timing(gpa_ctx* c, float* ms, int32_t n, int32_t
   return GPA_OK;
 }
 
+extern "C" int32_t gpa_ctx_last_terms(gpa_ctx* c, int64_t* terms) {
+  if (!c || !terms) return gpa_fail(GPA_ERR_ARG, "gpa_ctx_last_terms: NULL argument");
+  DeviceGuard guard(c->device);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  unsigned long long v = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&v, c->d_counters + 4, sizeof v, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return gpa_cuda_fail(e, "gpa_ctx_last_terms");
+  *terms = (int64_t)v;
+  return GPA_OK;
+}
+
+extern "C" int32_t gpa_measure_alu_peak(gpa_ctx* c, gpa_alu_peak* out) {
+  if (!c || !out) return gpa_fail(GPA_ERR_ARG, "gpa_measure_alu_peak: NULL argument");
+  DeviceGuard guard(c->device);
+  long long terms = 0;
+  cudaError_t e = measure_alu_peak(c->sm_count, c->stream, &out->terms_per_s, &out->imad_per_s, &out->term_ms,
+                                   &terms);
+  if (e != cudaSuccess) return gpa_cuda_fail(e, "gpa_measure_alu_peak");
+  out->terms = terms;
+  return GPA_OK;
+}
+
 extern "C" int32_t gpa_ctx_destroy(gpa_ctx* c) {
   if (!c) return GPA_OK;
   DeviceGuard guard(c->device);
@@ -391,6 +413,23 @@ extern "C" int32_t gpa_ctx_set_option(gpa_ctx* c, int32_t opt, int64_t value) {
     case GPA_OPT_HOST_COPY:
       if (value < 0 || value > 256) return gpa_fail(GPA_ERR_RANGE, "host copy (0 = by kernel where page-locked, 1 = copies, <= 256)");
       c->host_copy = (int)value;
+      break;
+    case GPA_OPT_MERGE_WARPS:
+      if (value < 0 || value > 8) return gpa_fail(GPA_ERR_RANGE, "merge warps per CTA (0 = tuned, 1..8)");
+      c->force_merge.warps_per_block = (int)value;
+      break;
+    case GPA_OPT_MERGE_GROUP:
+      if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8)
+        return gpa_fail(GPA_ERR_RANGE, "merge warps per set (0 = tuned, 1, 2, 4, 8)");
+      c->force_merge.chunk = (int)value;
+      break;
+    case GPA_OPT_MERGE_BLOCKS:
+      if (value < 0 || value > (1 << 20)) return gpa_fail(GPA_ERR_RANGE, "merge blocks");
+      c->force_merge.blocks = (int)value;
+      break;
+    case GPA_OPT_TEST_WARPS:
+      if (value < 0 || value > 8) return gpa_fail(GPA_ERR_RANGE, "1G warps per CTA (0 = tuned, 1..8)");
+      c->force_test_warps = (int)value;
       break;
     case GPA_OPT_PER_SET_LAUNCH: c->per_set_launch = value != 0; break;
     case GPA_OPT_PROFILE:
@@ -716,24 +755,11 @@ static LaunchShape default_fast(const gpa_ctx* c) {
   (void)c;
   return LaunchShape{4, 2, 0, 1};
 }
-// merge kernel: 2 warps (44 KB of shared memory) per CTA, 5 CTAs per SM
-static LaunchShape default_slow(const gpa_ctx* c) { return LaunchShape{2, 1, c->sm_count * 5, 1}; }
-
-static LaunchShape fast_shape(gpa_ctx* c, const DevSets& ds, const DevModel& md, const gpa_params& p) {
-  LaunchShape sh = default_fast(c);
-  auto it = c->tuned.find(tune_key(ds, md, p));
-  if (it != c->tuned.end()) sh = it->second;
-  if (c->force_fast.warps_per_block) sh.warps_per_block = c->force_fast.warps_per_block;
-  if (c->force_fast.chunk) sh.chunk = c->force_fast.chunk;
-  if (c->force_fast.blocks) sh.blocks = c->force_fast.blocks;
-  if (c->force_fast.stages) sh.stages = c->force_fast.stages;
-  return sh;
-}
 
 std::string tune_key(const DevSets& ds, const DevModel& md, const gpa_params& p) {
   char buf[160];
-  std::snprintf(buf, sizeof buf, "alloc:%lld:%d:%d:%d:%d:%d:%d:%d", ds.nsets, ds.n_max, md.M, md.g, p.policy, p.act,
-                md.sched, md.nz);
+  std::snprintf(buf, sizeof buf, "alloc:%lld:%d:%d:%d:%d:%d:%d:%d:%d", ds.nsets, ds.n_max, md.M, md.g, p.policy,
+                p.act, md.sched, md.nz, p.linear_merge);
   return buf;
 }
 
@@ -746,61 +772,160 @@ using AllocLauncher = cudaError_t (*)(const DevSets&, const DevModel&, const gpa
 static AllocLauncher allocate_launcher(int n_max) {
   return n_max > kNarrowNmax ? wide::launch_allocate : n_max <= kSmallNmax ? small::launch_allocate : launch_allocate;
 }
-
-static cudaError_t run_allocate(gpa_ctx* c, const DevSets& ds, const DevModel& md, const gpa_params& p,
-                                const AllocOut& out, const LaunchShape& fast, Prof* prof) {
-  AllocQueue q{c->d_counters, c->d_slow, c->d_err};
-  const bool wide_sets = ds.n_max > kNarrowNmax, small_sets = ds.n_max <= kSmallNmax;
-  if (p.policy == GPA_POLICY_ONE_GPU) {
-    LaunchShape sh{8, 1, c->sm_count * 4, 1};
-    return (wide_sets ? wide::launch_one_gpu : small_sets ? small::launch_one_gpu : launch_one_gpu)(
-        ds, md, out, q, c->d_mdiv, sh, c->stream, &c->launches, prof);
-  }
-  // merge kernel: the 256-task build keeps 58 KB of shared memory per warp
-  // (one warp per CTA, three CTAs per SM); the 64-task build 10 KB and 128
-  // registers per thread (two warps per CTA, eight CTAs per SM)
-  const LaunchShape slow = wide_sets    ? LaunchShape{1, 1, c->sm_count * 3, 1}
-                           : small_sets ? LaunchShape{2, 1, c->sm_count * 8, 1}
-                                        : default_slow(c);
-  return allocate_launcher(ds.n_max)(ds, md, p, out, q, c->d_mdiv, fast, slow, c->stream, &c->launches, prof);
+static int merge_ctas(int n_max, int wpb, int gw) {
+  return n_max > kNarrowNmax ? wide::merge_ctas_per_sm(wpb, gw)
+                             : n_max <= kSmallNmax ? small::merge_ctas_per_sm(wpb, gw) : merge_ctas_per_sm(wpb, gw);
+}
+static int one_gpu_ctas(int n_max, int wpb) {
+  return n_max > kNarrowNmax ? wide::one_gpu_ctas_per_sm(wpb)
+                             : n_max <= kSmallNmax ? small::one_gpu_ctas_per_sm(wpb) : one_gpu_ctas_per_sm(wpb);
 }
 
-// Autotuner: time the candidate shapes of the fast kernel on this batch
-// (every shape computes the same result) and keep the fastest.
+// Merge kernel: wpb warps per CTA in groups of gw warps per set, as many
+// CTAs per SM as fit (at most `cap`).
+static LaunchShape merge_shape(const gpa_ctx* c, int n_max, int wpb, int gw, int cap) {
+  int per_sm = merge_ctas(n_max, wpb, gw);
+  if (cap > 0 && per_sm > cap) per_sm = cap;
+  return LaunchShape{wpb, gw, c->sm_count * (per_sm > 0 ? per_sm : 1), 1};
+}
+
+// Library defaults per capacity build: one warp per set; the 256-task build
+// keeps 58 KB of shared memory per set (one-warp CTAs, up to three per SM),
+// the 64-task build 10 KB (two-warp CTAs, up to eight per SM), the 128-task
+// build 22 KB (two-warp CTAs, up to five per SM), as many as the registers
+// and shared memory allow.  The 1G kernel: eight-warp CTAs, as many as fit.
+static AllocShapes default_shapes(const gpa_ctx* c, const DevSets& ds) {
+  AllocShapes sh;
+  sh.fast = default_fast(c);
+  const bool wide_sets = ds.n_max > kNarrowNmax, small_sets = ds.n_max <= kSmallNmax;
+  sh.slow = wide_sets ? merge_shape(c, ds.n_max, 1, 1, 3)
+                      : small_sets ? merge_shape(c, ds.n_max, 2, 1, 8) : merge_shape(c, ds.n_max, 2, 1, 5);
+  const int per_sm = one_gpu_ctas(ds.n_max, 8);
+  sh.one = LaunchShape{8, 1, c->sm_count * (per_sm > 0 ? per_sm : 1), 1};
+  return sh;
+}
+
+// The shapes of a call: tuned for its signature when the autotuner ran,
+// else the defaults; forced options override either.
+static AllocShapes call_shapes(gpa_ctx* c, const DevSets& ds, const DevModel& md, const gpa_params& p) {
+  AllocShapes sh = default_shapes(c, ds);
+  auto it = c->tuned.find(tune_key(ds, md, p));
+  if (it != c->tuned.end()) sh = it->second;
+  if (c->force_fast.warps_per_block) sh.fast.warps_per_block = c->force_fast.warps_per_block;
+  if (c->force_fast.chunk) sh.fast.chunk = c->force_fast.chunk;
+  if (c->force_fast.blocks) sh.fast.blocks = c->force_fast.blocks;
+  if (c->force_fast.stages) sh.fast.stages = c->force_fast.stages;
+  if (c->force_merge.warps_per_block || c->force_merge.chunk || c->force_merge.blocks) {
+    const int gw = c->force_merge.chunk ? c->force_merge.chunk : sh.slow.chunk;
+    int wpb = c->force_merge.warps_per_block ? c->force_merge.warps_per_block : sh.slow.warps_per_block;
+    if (wpb < gw || wpb % gw) wpb = gw;
+    // the largest multiple of the group width up to wpb whose CTA fits an SM
+    while (wpb > gw && merge_ctas(ds.n_max, wpb, gw) <= 0) wpb -= gw;
+    sh.slow = merge_shape(c, ds.n_max, wpb, gw, 0);
+    if (c->force_merge.blocks) sh.slow.blocks = c->force_merge.blocks;
+  }
+  if (c->force_test_warps) {
+    const int w = c->force_test_warps;
+    const int per_sm = one_gpu_ctas(ds.n_max, w);
+    sh.one = LaunchShape{w, 1, c->sm_count * (per_sm > 0 ? per_sm : 1), 1};
+  }
+  return sh;
+}
+
+static cudaError_t run_allocate(gpa_ctx* c, const DevSets& ds, const DevModel& md, const gpa_params& p,
+                                const AllocOut& out, const AllocShapes& sh, Prof* prof) {
+  AllocQueue q{c->d_counters, c->d_slow, c->d_err};
+  const bool wide_sets = ds.n_max > kNarrowNmax, small_sets = ds.n_max <= kSmallNmax;
+  if (p.policy == GPA_POLICY_ONE_GPU)
+    return (wide_sets ? wide::launch_one_gpu : small_sets ? small::launch_one_gpu : launch_one_gpu)(
+        ds, md, out, q, c->d_mdiv, sh.one, c->stream, &c->launches, prof);
+  return allocate_launcher(ds.n_max)(ds, md, p, out, q, c->d_mdiv, sh.fast, sh.slow, c->stream, &c->launches, prof);
+}
+
+// Mean device time (ms) of `reps` runs after one untimed run.
+static float time_allocate(gpa_ctx* c, const DevSets& ds, const DevModel& md, const gpa_params& p, const AllocOut& out,
+                           const AllocShapes& sh, int reps, cudaEvent_t e0, cudaEvent_t e1) {
+  run_allocate(c, ds, md, p, out, sh, nullptr);
+  cudaEventRecord(e0, c->stream);
+  for (int r = 0; r < reps; r++) run_allocate(c, ds, md, p, out, sh, nullptr);
+  cudaEventRecord(e1, c->stream);
+  if (cudaEventSynchronize(e1) != cudaSuccess) return 1e30f;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  return ms / (float)reps;
+}
+
+// Autotuner: on the first call of a batch signature, time the candidate
+// launch shapes of the kernels the call runs on this batch (every shape
+// computes the same result) and keep the fastest for the signature:
+//  * 1G: warps per CTA of the test kernel (1, 2, 4, 8; CTAs per SM by
+//    occupancy);
+//  * heuristic: the fast kernel (direct loads: warps {4, 8} x sets per
+//    ticket {1, 2, 3, 4, 8}; staged: compute warps {4, 8} x sets {1, 2, 4} x
+//    stages {2, 3}), then the merge kernel with the best of those: warps per
+//    set {1, 2, 4, 8} x warps per CTA (multiples of it, up to 8) x CTAs per
+//    SM (as many as fit, or half of that).
+// The merge kernel's shapes are tried while the time spent tuning stays
+// below max(50 ms, 8 x the default run): a batch whose merges take seconds
+// keeps the shapes tried by then.
 static void autotune_allocate(gpa_ctx* c, const DevSets& ds, const DevModel& md, const gpa_params& p,
                               const AllocOut& out) {
   const std::string key = tune_key(ds, md, p);
   if (c->tuned.count(key)) return;
-  static const int warps_opts[] = {4, 8};
-  static const int chunk_opts[] = {1, 2, 3, 4, 8};
-  // direct loads: warps {4, 8} x chunks {1, 2, 3, 4, 8}; staged: compute
-  // warps {4, 8} x chunks {1, 2, 4} x stages {2, 3}
-  std::vector<LaunchShape> shapes;
-  for (int w : warps_opts)
-    for (int ch : chunk_opts) shapes.push_back(LaunchShape{w, ch, 0, 1});
-  for (int w : warps_opts)
-    for (int ch : {1, 2, 4})
-      for (int stg : {2, 3}) shapes.push_back(LaunchShape{w, ch, 0, stg});
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  float best_ms = 1e30f;
-  LaunchShape best = default_fast(c);
-  for (const LaunchShape& sh : shapes) {
-    float tot = 0.f;
-    for (int rep = 0; rep < 3; rep++) {
-      cudaEventRecord(e0, c->stream);
-      run_allocate(c, ds, md, p, out, sh, nullptr);
-      cudaEventRecord(e1, c->stream);
-      cudaEventSynchronize(e1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (rep > 0) tot += ms;
+  AllocShapes best = default_shapes(c, ds);
+  float best_ms = time_allocate(c, ds, md, p, out, best, 2, e0, e1);
+  if (p.policy == GPA_POLICY_ONE_GPU) {
+    for (int w : {1, 2, 4, 8}) {
+      AllocShapes t = best;
+      const int per_sm = one_gpu_ctas(ds.n_max, w);
+      if (per_sm <= 0) continue;
+      t.one = LaunchShape{w, 1, c->sm_count * per_sm, 1};
+      const float ms = time_allocate(c, ds, md, p, out, t, 2, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = t;
+      }
     }
-    if (tot < best_ms) {
-      best_ms = tot;
-      best = sh;
+  } else {
+    std::vector<LaunchShape> shapes;
+    for (int w : {4, 8})
+      for (int ch : {1, 2, 3, 4, 8}) shapes.push_back(LaunchShape{w, ch, 0, 1});
+    for (int w : {4, 8})
+      for (int ch : {1, 2, 4})
+        for (int stg : {2, 3}) shapes.push_back(LaunchShape{w, ch, 0, stg});
+    for (const LaunchShape& f : shapes) {
+      AllocShapes t = best;
+      t.fast = f;
+      const float ms = time_allocate(c, ds, md, p, out, t, 2, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = t;
+      }
     }
+    const float budget = std::max(50.f, 8.f * best_ms);
+    float spent = 0.f;
+    for (int gw : {1, 2, 4, 8})
+      for (int wpb = gw; wpb <= 8 && spent < budget; wpb += gw) {
+        const int full = merge_ctas(ds.n_max, wpb, gw);
+        if (full <= 0) continue;
+        for (int cap : {full, full / 2}) {
+          if (cap <= 0 || spent >= budget || (cap == full / 2 && cap == full)) continue;
+          AllocShapes t = best;
+          t.slow = merge_shape(c, ds.n_max, wpb, gw, cap);
+          if (t.slow.warps_per_block == best.slow.warps_per_block && t.slow.chunk == best.slow.chunk &&
+              t.slow.blocks == best.slow.blocks)
+            continue;
+          const float ms = time_allocate(c, ds, md, p, out, t, 1, e0, e1);
+          spent += 2.f * ms;
+          if (ms < best_ms) {
+            best_ms = ms;
+            best = t;
+          }
+        }
+      }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -808,14 +933,15 @@ static void autotune_allocate(gpa_ctx* c, const DevSets& ds, const DevModel& md,
 }
 
 static std::string graph_key(const DevSets& ds, const DevModel& md, const gpa_params& p, const AllocOut& o,
-                             const LaunchShape& sh) {
-  char buf[512];
-  std::snprintf(buf, sizeof buf, "%lld|%d|%p|%p|%p|%p|%p|%p|%p|%d|%d|%d|%d|%d|%d|%p|%d|%d|%d|%p|%p|%p|%p|%p|%p|%p|%p|%d|%d|%d|%d",
+                             const AllocShapes& sh) {
+  char buf[640];
+  std::snprintf(buf, sizeof buf, "%lld|%d|%p|%p|%p|%p|%p|%p|%p|%d|%d|%d|%d|%d|%d|%p|%d|%d|%d|%p|%p|%p|%p|%p|%p|%p|%p|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d",
                 ds.nsets, ds.n_max, (const void*)ds.set_off, (const void*)ds.T, (const void*)ds.D,
                 (const void*)ds.A, (const void*)ds.B, (const void*)ds.u, (const void*)ds.type, md.M, md.g, md.kc,
                 md.km, md.sched, md.nz, (const void*)md.zlist, p.policy, p.act, p.linear_merge, (void*)o.verdict, (void*)o.reason, (void*)o.n_parts,
                 (void*)o.Pi, (void*)o.W, (void*)o.n_tests, (void*)o.part_of_task, (void*)o.size_of_part,
-                sh.warps_per_block, sh.chunk, sh.blocks, sh.stages);
+                sh.fast.warps_per_block, sh.fast.chunk, sh.fast.blocks, sh.fast.stages, sh.slow.warps_per_block,
+                sh.slow.chunk, sh.slow.blocks, sh.one.warps_per_block, sh.one.blocks, 0);
   return buf;
 }
 
@@ -845,8 +971,8 @@ static int32_t allocate_device(gpa_ctx* c, const DevSets& ds, const DevModel& md
     }
     return GPA_OK;
   }
-  if (c->autotune && p.policy != GPA_POLICY_ONE_GPU) autotune_allocate(c, ds, md, p, out);
-  const LaunchShape fast = fast_shape(c, ds, md, p);
+  if (c->autotune) autotune_allocate(c, ds, md, p, out);
+  const AllocShapes shapes = call_shapes(c, ds, md, p);
   if (c->use_graph) {
     if (c->graphs_dirty) {
       for (auto& kv : c->graphs) destroy_graph(kv.second);
@@ -854,7 +980,7 @@ static int32_t allocate_device(gpa_ctx* c, const DevSets& ds, const DevModel& md
       c->last_prof = nullptr;
       c->graphs_dirty = false;
     }
-    const std::string key = graph_key(ds, md, p, out, fast) + (c->profile ? "|prof" : "");
+    const std::string key = graph_key(ds, md, p, out, shapes) + (c->profile ? "|prof" : "");
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
       Prof gp{};
@@ -868,7 +994,7 @@ static int32_t allocate_device(gpa_ctx* c, const DevSets& ds, const DevModel& md
       cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) return gpa_cuda_fail(e, "cudaStreamBeginCapture (graphs need a non-default stream)");
       long long before = c->launches;
-      cudaError_t le = run_allocate(c, ds, md, p, out, fast, c->profile ? &gp : nullptr);
+      cudaError_t le = run_allocate(c, ds, md, p, out, shapes, c->profile ? &gp : nullptr);
       long long kernels = c->launches - before;
       c->launches = before;
       e = cudaStreamEndCapture(c->stream, &g);
@@ -889,7 +1015,7 @@ static int32_t allocate_device(gpa_ctx* c, const DevSets& ds, const DevModel& md
     c->last_prof = it->second.prof.used ? &it->second.prof : nullptr;
     return GPA_OK;
   }
-  cudaError_t e = run_allocate(c, ds, md, p, out, fast, begin_prof(c));
+  cudaError_t e = run_allocate(c, ds, md, p, out, shapes, begin_prof(c));
   return e == cudaSuccess ? GPA_OK : gpa_cuda_fail(e, "allocate launch");
 }
 
@@ -1153,6 +1279,77 @@ extern "C" int32_t gpa_search_best(gpa_ctx* c, const gpa_tasksets* sets, const g
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(r->minm_block, out.minm_block, 2 * (size_t)(ns * kmax), cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return gpa_cuda_fail(e, "search_best");
+  return finish_host_call(c);
+}
+
+extern "C" int32_t gpa_search_explicit(gpa_ctx* c, const gpa_tasksets* sets, const gpa_model* model, int32_t kmin,
+                                       int32_t kmax, gpa_best_result* r, uint8_t* cand_verdict, int64_t* ncand) {
+  int32_t st = common_checks(c, sets, model, "gpa_search_explicit");
+  if (st != GPA_OK) return st;
+  if (!r) return gpa_fail(GPA_ERR_ARG, "gpa_search_explicit: NULL result");
+  if (kmin < 1 || kmax < kmin || kmax > GPA_SEARCH_KMAX)
+    return gpa_fail(GPA_ERR_RANGE, "gpa_search_explicit: need 1 <= kmin <= kmax <= %d", GPA_SEARCH_KMAX);
+  if (sets->n_max > GPA_SEARCH_NMAX)
+    return gpa_fail(GPA_ERR_RANGE, "gpa_search_explicit: n_max %d exceeds %d", sets->n_max, GPA_SEARCH_NMAX);
+  if (model->nsizes != 0) return gpa_fail(GPA_ERR_ARG, "gpa_search_explicit: admissible size lists are not supported");
+  if (r->mem != sets->mem) return gpa_fail(GPA_ERR_ARG, "gpa_search_explicit: result and sets differ in mem");
+  // candidates of a set of n_max tasks: sum over k of C(Mu - 1, k - 1) k^n_max
+  const int Mu = model->M / model->g;
+  const int nmax = sets->n_max < 0 ? 0 : sets->n_max;
+  unsigned __int128 total = 0;
+  for (int k = kmin; k <= kmax && k <= Mu; k++) {
+    unsigned __int128 maps = 1;
+    for (int i = 0; i < nmax && maps <= (unsigned __int128)GPA_EXPLICIT_MAX; i++) maps *= (unsigned)k;
+    unsigned __int128 comps = 1;
+    for (int i = 1; i <= k - 1 && comps <= (unsigned __int128)GPA_EXPLICIT_MAX; i++)
+      comps = comps * (unsigned)(Mu - 1 - (k - 1) + i) / (unsigned)i;
+    total += comps * maps;
+    if (total > (unsigned __int128)GPA_EXPLICIT_MAX) break;
+  }
+  if (total > (unsigned __int128)GPA_EXPLICIT_MAX)
+    return gpa_fail(GPA_ERR_RANGE, "gpa_search_explicit: more than %lld candidates per set", (long long)GPA_EXPLICIT_MAX);
+  const long long stride = (long long)total;
+  if (ncand) *ncand = stride;
+  if (sets->nsets == 0) return GPA_OK;
+  if (!sets->u_ppm) return gpa_fail(GPA_ERR_ARG, "gpa_search_explicit: u_ppm is required");
+  if (!r->feasible || !r->W || !r->sum_minm || !r->n_blocks || !r->spare || !r->rgs || !r->minm_block)
+    return gpa_fail(GPA_ERR_ARG, "gpa_search_explicit: NULL result array");
+  DeviceGuard guard(c->device);
+  DevModel md;
+  if ((st = device_model(c, model, &md)) != GPA_OK) return st;
+  AllocQueue q{c->d_counters, c->d_slow, c->d_err};
+  if (sets->mem == GPA_DEVICE) {
+    BestOut out{r->feasible, (long long*)r->W, r->sum_minm, r->n_blocks, r->spare, r->rgs, r->minm_block};
+    cudaError_t e = launch_search_explicit(dev_sets(sets), md, kmin, kmax, out, cand_verdict, stride, q, c->d_mdiv,
+                                           c->sm_count, c->stream, &c->launches, begin_prof(c));
+    return e == cudaSuccess ? GPA_OK : gpa_cuda_fail(e, "search_explicit launch");
+  }
+  HostStage hs;
+  if ((st = stage_in_validated(c, sets, model, &hs)) != GPA_OK) return st;
+  const long long ns = sets->nsets, nt = hs.ntasks > 0 ? hs.ntasks : 1;
+  BestOut out{(unsigned char*)ctx_buffer(c, 22, (size_t)ns), (long long*)ctx_buffer(c, 23, 8 * (size_t)ns),
+              (int*)ctx_buffer(c, 24, 4 * (size_t)ns), (int*)ctx_buffer(c, 25, 4 * (size_t)ns),
+              (int*)ctx_buffer(c, 26, 4 * (size_t)ns), (unsigned char*)ctx_buffer(c, 27, (size_t)nt),
+              (short*)ctx_buffer(c, 28, 2 * (size_t)(ns * kmax))};
+  unsigned char* dcv = cand_verdict ? (unsigned char*)ctx_buffer(c, 29, (size_t)(ns * stride)) : nullptr;
+  if (!out.feasible || !out.W || !out.sum_minm || !out.n_blocks || !out.spare || !out.rgs || !out.minm_block ||
+      (cand_verdict && !dcv))
+    return gpa_fail(GPA_ERR_NOMEM, "result staging failed");
+  cudaStream_t s = c->stream;
+  cudaError_t e = launch_search_explicit(hs.ds, md, kmin, kmax, out, dcv, stride, q, c->d_mdiv, c->sm_count, s,
+                                         &c->launches, begin_prof(c));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(r->feasible, out.feasible, (size_t)ns, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(r->W, out.W, 8 * (size_t)ns, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(r->sum_minm, out.sum_minm, 4 * (size_t)ns, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(r->n_blocks, out.n_blocks, 4 * (size_t)ns, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(r->spare, out.spare, 4 * (size_t)ns, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && hs.ntasks > 0)
+    e = cudaMemcpyAsync(r->rgs, out.rgs, (size_t)hs.ntasks, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(r->minm_block, out.minm_block, 2 * (size_t)(ns * kmax), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && cand_verdict)
+    e = cudaMemcpyAsync(cand_verdict, dcv, (size_t)(ns * stride), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return gpa_cuda_fail(e, "search_explicit");
   return finish_host_call(c);
 }
 

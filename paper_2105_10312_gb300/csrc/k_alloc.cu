@@ -409,37 +409,68 @@ __global__ void __launch_bounds__(288, 2) alloc_fast_staged(DevSets S, DevModel 
   }
 }
 
-__global__ void __launch_bounds__(128) alloc_merge(DevSets S, DevModel md, gpa_params p, AllocOut out, AllocQueue q,
-                                                   const MagicDiv* __restrict__ mdiv) {
+// Bytes of one merge group (the set state plus the test scratch of each of
+// its warps after the first).
+__host__ __device__ constexpr size_t merge_group_bytes(int gw) {
+  return (sizeof(MergeSmem) + (size_t)(gw - 1) * sizeof(WarpScratch) + 127) / 128 * 128;
+}
+
+// The merge kernel: CTAs of warps_per_block warps in groups of gw warps;
+// each group pops deferred sets from the queue and runs Alg. 1 on them.
+__global__ void __launch_bounds__(256, 1) alloc_merge(DevSets S, DevModel md, gpa_params p, AllocOut out, AllocQueue q,
+                                                   const MagicDiv* __restrict__ mdiv, int gw) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  MergeSmem& sm = reinterpret_cast<MergeSmem*>(smem_raw)[warp];
+  const int gi = warp / gw;
+  Grp g;
+  g.nthreads = gw * 32;
+  g.nwarps = gw;
+  g.warp = warp - gi * gw;
+  g.tid = (int)threadIdx.x - gi * gw * 32;
+  g.lane = lane;
+  g.bar = 1 + gi;
+  unsigned char* base = smem_raw + (size_t)gi * merge_group_bytes(gw);
+  MergeSmem& sm = *reinterpret_cast<MergeSmem*>(base);
+  WarpScratch* extra = reinterpret_cast<WarpScratch*>(base + sizeof(MergeSmem));
+  RtaScratch& sc = grp_sc(sm, extra, g);
+  LaneScratch& ls = grp_ls(sm, extra, g);
+  ls.terms[lane] = 0ull;
+  if (lane == 0) sc.terms = 0ull;
   asm volatile("griddepcontrol.wait;" ::: "memory");  // the fast grid has finished and its writes are visible
   const unsigned long long nslow = *(volatile unsigned long long*)(q.counters + 1);
   const long long ntasks = S.set_off[S.nsets];
   for (;;) {
-    unsigned long long i = 0;
-    if (lane == 0) i = atomicAdd(q.counters + 2, 1ull);
-    i = __shfl_sync(kFull, i, 0);
+    if (g.tid == 0) sm.ticket = (long long)atomicAdd(q.counters + 2, 1ull);
+    g.sync();
+    const unsigned long long i = (unsigned long long)sm.ticket;
+    g.sync();
     if (i >= nslow) break;
     const long long s = q.slow_sets[i];
     const long long o = S.set_off[s];
     const long long nl = S.set_off[s + 1] - o;
     if (nl < 0 || nl > S.n_max || nl > kNmax || !slice_inside(o, nl, ntasks)) {
-      write_invalid(s, o, slice_inside(o, nl, ntasks) ? nl : 0, out, q.err);
+      if (g.warp == 0) write_invalid(s, o, slice_inside(o, nl, ntasks) ? nl : 0, out, q.err);
       continue;
     }
     const int n = (int)nl;
-    if (!stage_set(sm.st, o, n, S.T, S.D, S.A, S.B, S.u, S.type)) {
-      write_invalid(s, o, n, out, q.err);
+    if (g.warp == 0) {
+      const bool ok = stage_set(sm.st, o, n, S.T, S.D, S.A, S.B, S.u, S.type);
+      if (lane == 0) {
+        sm.ctl[5] = ok ? 1 : 0;
+        sm.err = 0u;
+      }
+    }
+    g.sync();
+    if (!sm.ctl[5]) {
+      if (g.warp == 0) write_invalid(s, o, n, out, q.err);
+      g.sync();
       continue;
     }
-    if (lane == 0) sm.err = 0u;
-    __syncwarp();
-    merge_set(sm, s, o, n, md, p, out, mdiv, &sm.err);
-    __syncwarp();
-    finish_set_errors(s, sm.err, out, q.err);
+    merge_set(g, sm, extra, s, o, n, md, p, out, mdiv, &sm.err);
+    if (g.warp == 0) finish_set_errors(s, sm.err, out, q.err);
+    g.sync();
   }
+  flush_terms(sc, ls, q.counters + 4);
 }
 
 // --------------------------------------------------------------- 1G kernel
@@ -450,7 +481,7 @@ struct OneGpuSmem {
   unsigned int err;  // error bits of the set being tested
 };
 // the dynamic shared memory opted in by alloc_kernels_init (227 KB per CTA at most)
-static_assert(4 * sizeof(MergeSmem) <= 232448, "merge kernel: four warps must fit 227 KB");
+static_assert(merge_group_bytes(1) <= 232448, "merge kernel: one group must fit 227 KB");
 static_assert(8 * sizeof(OneGpuSmem) <= 232448, "1G kernel: eight warps must fit 227 KB");
 
 __global__ void __launch_bounds__(256) one_gpu(DevSets S, DevModel md, AllocOut out, unsigned int* err,
@@ -458,6 +489,7 @@ __global__ void __launch_bounds__(256) one_gpu(DevSets S, DevModel md, AllocOut 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   OneGpuSmem& sm = reinterpret_cast<OneGpuSmem*>(smem_raw)[warp];
+  if (lane == 0) sm.sc.terms = 0ull;
   const long long ntasks = S.set_off[S.nsets];
   for (;;) {
     unsigned long long s = 0;
@@ -510,18 +542,40 @@ __global__ void __launch_bounds__(256) one_gpu(DevSets S, DevModel md, AllocOut 
     __syncwarp();
     finish_set_errors((long long)s, sm.err, out, err);
   }
+  __syncwarp();
+  if (lane == 0 && sm.sc.terms) atomicAdd(ticket + 1, sm.sc.terms);  // the context's term counter follows the ticket
 }
 
 }  // namespace
 
 size_t staged_smem_bytes(int stages) { return kStageHeader + sizeof(FastStage) * (size_t)stages; }
-size_t slow_smem_bytes(int warps_per_block) { return sizeof(MergeSmem) * (size_t)warps_per_block; }
+size_t slow_smem_bytes(int warps_per_block, int gw) {
+  return merge_group_bytes(gw) * (size_t)(warps_per_block / (gw > 0 ? gw : 1));
+}
 size_t one_gpu_smem_bytes(int warps_per_block) { return sizeof(OneGpuSmem) * (size_t)warps_per_block; }
+
+int merge_ctas_per_sm(int wpb, int gw) {
+  if (gw < 1 || gw > kGrpWarpsMax || wpb < gw || wpb > 8 || wpb % gw) return 0;
+  const size_t smem = slow_smem_bytes(wpb, gw);
+  if (smem > 232448) return 0;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, alloc_merge, wpb * 32, smem) != cudaSuccess) return 0;
+  return per_sm;
+}
+
+int one_gpu_ctas_per_sm(int wpb) {
+  if (wpb < 1 || wpb > 8) return 0;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, one_gpu, wpb * 32, one_gpu_smem_bytes(wpb)) != cudaSuccess)
+    return 0;
+  return per_sm;
+}
 
 cudaError_t launch_allocate(const DevSets& s, const DevModel& md, const gpa_params& p, const AllocOut& out,
                             const AllocQueue& q, const MagicDivHost* mdiv, const LaunchShape& fast,
                             const LaunchShape& slow, cudaStream_t st, long long* launches, Prof* prof) {
-  cudaError_t e = cudaMemsetAsync(q.counters, 0, 4 * sizeof(unsigned long long), st);
+  // tickets, deferred count and the interference-term counter start at zero
+  cudaError_t e = cudaMemsetAsync(q.counters, 0, 5 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
   prof_mark(prof, st);
   const int threads = min(fast.warps_per_block, 8) * 32;  // the direct kernel takes up to 8 warps
@@ -585,17 +639,22 @@ cudaError_t launch_allocate(const DevSets& s, const DevModel& md, const gpa_para
   // programmatic dependent launch: the merge grid may be scheduled while the
   // fast grid drains; it waits (griddepcontrol.wait) for the fast grid's
   // completion and memory before it reads the queue
+  // merge grid: slow.warps_per_block warps per CTA in groups of slow.chunk
+  // warps, one set per group at a time
+  const int gw = slow.chunk >= 1 && slow.chunk <= kGrpWarpsMax ? slow.chunk : 1;
+  const int wpb = max(gw, min(slow.warps_per_block, 8) / gw * gw);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)slow.blocks);
-  cfg.blockDim = dim3((unsigned)(slow.warps_per_block * 32));
-  cfg.dynamicSmemBytes = slow_smem_bytes(slow.warps_per_block);
+  cfg.blockDim = dim3((unsigned)(wpb * 32));
+  cfg.dynamicSmemBytes = slow_smem_bytes(wpb, gw);
+  if (cfg.dynamicSmemBytes > 232448) return cudaErrorInvalidConfiguration;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, alloc_merge, s, md, p, out, q, reinterpret_cast<const MagicDiv*>(mdiv));
+  e = cudaLaunchKernelEx(&cfg, alloc_merge, s, md, p, out, q, reinterpret_cast<const MagicDiv*>(mdiv), gw);
   if (e != cudaSuccess) return e;
   e = cudaGetLastError();
   prof_mark(prof, st);
@@ -606,9 +665,9 @@ cudaError_t launch_allocate(const DevSets& s, const DevModel& md, const gpa_para
 cudaError_t launch_one_gpu(const DevSets& s, const DevModel& md, const AllocOut& out, const AllocQueue& q,
                            const MagicDivHost* mdiv, const LaunchShape& shape, cudaStream_t st, long long* launches,
                            Prof* prof) {
-  unsigned long long* ticket = q.counters + 3;
+  unsigned long long* ticket = q.counters + 3;  // followed by the interference-term counter
   unsigned int* err = q.err;
-  cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), st);
+  cudaError_t e = cudaMemsetAsync(ticket, 0, 2 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
   prof_mark(prof, st);
   one_gpu<<<shape.blocks, shape.warps_per_block * 32, one_gpu_smem_bytes(shape.warps_per_block), st>>>(
@@ -628,8 +687,7 @@ void prof_mark(Prof* p, cudaStream_t st) {
 
 // Opt in to the dynamic shared memory the kernels need (once per process).
 cudaError_t alloc_kernels_init() {
-  cudaError_t e = cudaFuncSetAttribute(alloc_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)slow_smem_bytes(4));
+  cudaError_t e = cudaFuncSetAttribute(alloc_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
   if (e != cudaSuccess) return e;
   const int staged = (int)staged_smem_bytes(kStagesMax);
   if ((e = cudaFuncSetAttribute(alloc_fast_staged<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, staged)) !=

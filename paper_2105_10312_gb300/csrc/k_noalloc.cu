@@ -34,9 +34,10 @@ namespace {
 constexpr long long kNoAllocMaxSets = GPA_NOALLOC_MAX_SETS;
 constexpr int kMaxDevices = 64;
 
-// work-queue counters [0..3], error word, deferred-set queue
+// work-queue counters [0..3], interference-term counter [4], error word,
+// deferred-set queue
 struct NoAllocScratch {
-  unsigned long long counters[4];
+  unsigned long long counters[8];
   unsigned int err;
   unsigned int pad[7];
   long long slow_sets[kNoAllocMaxSets];

@@ -194,3 +194,33 @@ extern "C" int32_t gpa_measure_wcet(gpa_ctx* c, const gpa_probe_cfg* cfg, const 
   }
   return GPA_OK;
 }
+
+extern "C" int32_t gpa_probe_run(gpa_ctx* c, int32_t kernel, int64_t n, int32_t ctas, const float* a, const float* b,
+                                 float* out) {
+  if (!c || !a || !out || (kernel == GPA_PROBE_VADD && !b)) return gpa_fail(GPA_ERR_ARG, "gpa_probe_run: NULL argument");
+  if (kernel < GPA_PROBE_VADD || kernel > GPA_PROBE_COMPUTE) return gpa_fail(GPA_ERR_ARG, "gpa_probe_run: bad kernel");
+  const bool square = kernel == GPA_PROBE_TRANSPOSE || kernel == GPA_PROBE_STENCIL;
+  if (square ? (n < 32 || n > 16384) : (n < 1 || n > (1ll << 28)))
+    return gpa_fail(GPA_ERR_RANGE, "gpa_probe_run: problem size %lld out of range", (long long)n);
+  if (ctas < 0 || ctas > (1 << 20)) return gpa_fail(GPA_ERR_RANGE, "gpa_probe_run: ctas");
+  DeviceGuard guard(c->device);
+  const size_t elems = square ? (size_t)n * (size_t)n : (size_t)n;
+  const int nctas = ctas ? ctas : 4 * c->sm_count;
+  ProbeState S;
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t x) { return (e = x) == cudaSuccess; };
+  if (!ok(cudaMalloc(&S.b.a, elems * sizeof(float))) || !ok(cudaMalloc(&S.b.b, elems * sizeof(float))) ||
+      !ok(cudaMalloc(&S.b.c, elems * sizeof(float))) ||
+      !ok(cudaMalloc(&S.smid_test, sizeof(unsigned int) * (size_t)nctas)) ||
+      !ok(cudaMalloc(&S.times, 2 * sizeof(unsigned long long))))
+    return e == cudaErrorMemoryAllocation ? gpa_fail(GPA_ERR_NOMEM, "gpa_probe_run: device buffers")
+                                          : gpa_cuda_fail(e, "gpa_probe_run: device buffers");
+  if (!ok(cudaMemcpy(S.b.a, a, elems * sizeof(float), cudaMemcpyHostToDevice)) ||
+      (b && !ok(cudaMemcpy(S.b.b, b, elems * sizeof(float), cudaMemcpyHostToDevice))) ||
+      !ok(cudaMemset(S.times, 0, 2 * sizeof(unsigned long long))) ||
+      !ok(launch_probe_kernel(kernel, nctas, S.b, (unsigned long long)n, S.smid_test, S.times + 1, c->stream)) ||
+      !ok(cudaStreamSynchronize(c->stream)) ||
+      !ok(cudaMemcpy(out, S.b.c, elems * sizeof(float), cudaMemcpyDeviceToHost)))
+    return gpa_cuda_fail(e, "gpa_probe_run");
+  return GPA_OK;
+}

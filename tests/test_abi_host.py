@@ -157,6 +157,8 @@ def test_binding_constants_match_the_header():
                     "GPA_ERR_BUSY": gpa.ERR_BUSY, "GPA_ERR_NOTFOUND": gpa.ERR_NOTFOUND}
     assert (defines["GPA_NMAX"], defines["GPA_SERVE_NMAX"], defines["GPA_MMAX"], defines["GPA_SEARCH_NMAX"],
             defines["GPA_SEARCH_KMAX"]) == (gpa.NMAX, gpa.SERVE_NMAX, gpa.MMAX, gpa.SEARCH_NMAX, gpa.SEARCH_KMAX)
+    m = re.search(r"#define\s+GPA_EXPLICIT_MAX\s+\(1ll << (\d+)\)", text)
+    assert m and 1 << int(m.group(1)) == gpa.EXPLICIT_MAX
 
 
 def test_struct_layouts_match_the_header(tmp_path):
@@ -169,7 +171,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     pairs = {"gpa_tasksets": gpa.Tasksets, "gpa_model": gpa.Model, "gpa_candidates": gpa.Candidates,
              "gpa_params": gpa.Params, "gpa_alloc_result": gpa.AllocResult, "gpa_best_result": gpa.BestResult,
              "gpa_serve_cfg": gpa.ServeCfg, "gpa_request": gpa.Request, "gpa_response": gpa.Response,
-             "gpa_probe_cfg": gpa.ProbeCfg, "gpa_gen_params": G.GenParams, "gpa_gen_out": G.GenOut}
+             "gpa_probe_cfg": gpa.ProbeCfg, "gpa_gen_params": G.GenParams, "gpa_gen_out": G.GenOut,
+             "gpa_alu_peak": gpa.AluPeak}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "gpa.h"', "int main(void) {"]
     for cname, cls in pairs.items():
         lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')

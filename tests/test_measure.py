@@ -60,6 +60,35 @@ def test_placement_and_scaling_on_the_gpu(ctx):
 
 
 @pytest.mark.gpu
+def test_probe_kernels_compute_what_they_claim(ctx):
+    """Each kernel the measurement times, run on seeded data, against NumPy:
+    the vector add and the transpose exactly; the stencil sweep and the
+    64-step multiply-add chain within float32 rounding (the device fuses
+    multiply and add, NumPy does not; the chain contracts, |a| < 1)."""
+    rng = np.random.default_rng(9)
+    for n, ctas in ((1, 1), (1000003, 0), (4099, 3)):
+        a = rng.standard_normal(n).astype(np.float32)
+        b = rng.standard_normal(n).astype(np.float32)
+        assert np.array_equal(gpa.probe_run(ctx, "VADD", n, a, b, ctas=ctas), a + b)
+    for n in (32, 100, 1031):
+        a = rng.standard_normal((n, n)).astype(np.float32)
+        assert np.array_equal(gpa.probe_run(ctx, "TRANSPOSE", n, a).reshape(n, n), a.T)
+        p = np.pad(a.astype(np.float64), 1, mode="edge")
+        want = a + 0.1 * (p[1:-1, :-2] + p[1:-1, 2:] + p[:-2, 1:-1] + p[2:, 1:-1] - 4 * a.astype(np.float64))
+        got = gpa.probe_run(ctx, "STENCIL", n, a).reshape(n, n)
+        assert np.allclose(got, want, rtol=1e-5, atol=1e-5)
+    x = rng.uniform(-0.99, 0.99, 100003).astype(np.float32)
+    y = np.ones_like(x, dtype=np.float64)
+    for _ in range(64):
+        y = y * x + 0.5
+    got = gpa.probe_run(ctx, "COMPUTE", len(x), x)
+    assert np.allclose(got, y, rtol=1e-5, atol=1e-5)
+    with pytest.raises(gpa.GpaError) as ei:
+        gpa.probe_run(ctx, "TRANSPOSE", 16, np.zeros(256, np.float32))
+    assert ei.value.code == gpa.ERR_RANGE
+
+
+@pytest.mark.gpu
 def test_measure_rejects_bad_arguments(ctx):
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
