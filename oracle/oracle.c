@@ -40,6 +40,14 @@
  * read as the m-independent inflated workload W(S) = sum k_i(S) u_ppm_i;
  * ACT evaluated only when the loop of Alg. 1 will run (Pi > M after init);
  * partitions reported in order of their lowest task index.
+ *
+ * Pin status: allocate_one()'s trajectory (which merges Alg. 1-3 make, in
+ * which order) is parity unpinned against the paper, which prints no worked
+ * run: its tests check invariants every reading satisfies and a second
+ * coding of the same readings, so a reading that differs from the authors'
+ * intent would pass them.  Every other function above is pinned by values
+ * the paper or the mathematics fix (worked example, closed forms,
+ * schedule simulation, brute force, published bounds).
  */
 #include <pthread.h>
 #include <stdint.h>

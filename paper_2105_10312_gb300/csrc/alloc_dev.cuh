@@ -106,7 +106,8 @@ constexpr int kWinMax = 256;      // jobs per window of first_pass
 // merged set's tasks in priority order, [position][lane] (conflict-free
 // banks), and the thread's count of interference terms.
 struct LaneScratch {
-  unsigned int C[kLaneMax][32];
+  uint2 cm[kLaneMax][32];             // .x: WCET, .y: reciprocal of the period
+  unsigned char sh[kLaneMax][32];     // shift of that reciprocal
   unsigned char row[kLaneMax][32];
   unsigned long long terms[32];
 };
@@ -246,8 +247,8 @@ __device__ bool lane_rta(const SetSmem& st, const unsigned int* S, unsigned int 
       const int row = w * 32 + __ffs(bits) - 1;
       const bool mem = (st.memmask[w] >> (row & 31)) & 1u;
       const unsigned int Ci = wcet(st.A[row], st.B[row], mem ? kmem : kcmp, m, md);
-      ls.C[pos][lane] = Ci;
-      ls.row[pos][lane] = (unsigned char)row;
+      ls.cm[pos][lane] = make_uint2(Ci, st.mT[row]);
+      ls.sh[pos][lane] = st.shT[row];
       unsigned long long R = Rprev + Ci;
       const unsigned int Di = st.D[row];
       const unsigned long long cap = (unsigned long long)Di + 1ull;
@@ -260,9 +261,8 @@ __device__ bool lane_rta(const SetSmem& st, const unsigned int* S, unsigned int 
         unsigned long long next = Ci;
         nt += (unsigned int)pos;
         for (int q = 0; q < pos; q++) {
-          const int rq = ls.row[q][lane];
-          const unsigned long long t = (unsigned long long)ceil_div_T((unsigned int)R, st.mT[rq], st.shT[rq]) *
-                                       ls.C[q][lane];
+          const uint2 v = ls.cm[q][lane];
+          const unsigned long long t = (unsigned long long)ceil_div_T((unsigned int)R, v.y, ls.sh[q][lane]) * v.x;
           next += t < cap ? t : cap;
         }
         if (next == R) break;
@@ -296,7 +296,7 @@ __device__ bool lane_edf(const SetSmem& st, const unsigned int* S, unsigned int 
     for (unsigned int bits = S[w]; bits; bits &= bits - 1u) {
       const int row = w * 32 + __ffs(bits) - 1;
       const bool mem = (st.memmask[w] >> (row & 31)) & 1u;
-      ls.C[pos][lane] = wcet(st.A[row], st.B[row], mem ? kmem : kcmp, m, md);
+      ls.cm[pos][lane] = make_uint2(wcet(st.A[row], st.B[row], mem ? kmem : kcmp, m, md), st.mT[row]);
       ls.row[pos][lane] = (unsigned char)row;
       pos++;
     }
@@ -306,7 +306,7 @@ __device__ bool lane_edf(const SetSmem& st, const unsigned int* S, unsigned int 
       pos,
       [&](int a, unsigned int& C, unsigned int& T, unsigned int& D, unsigned int& mg, unsigned int& sh) {
         const int r = ls.row[a][lane];
-        C = ls.C[a][lane];
+        C = ls.cm[a][lane].x;
         T = st.T[r];
         D = st.D[r];
         mg = st.mT[r];
@@ -466,21 +466,26 @@ __device__ __forceinline__ bool mask_meets(const unsigned int* a, const unsigned
   return x != 0u;
 }
 
-// par_list order (decreasing utilisation, ties to the lower lowest index).
+// par_list key of slot x: larger first; utilisation, then the lower lowest
+// task index (unique among live slots, their task sets being disjoint).
+__device__ __forceinline__ unsigned long long par_key(const MergeSmem& sm, int x) {
+  return ((sm.Uc[x] + sm.Um[x]) << 8) | (unsigned long long)(255u - sm.lowest[x]);
+}
+
+// par_list order (decreasing utilisation, ties to the lower lowest index),
+// by counting larger keys.
 __device__ int sort_par_list(const Grp& g, MergeSmem& sm, int nslots) {
   int alive_count = 0;
   for (int x = g.tid; x < nslots; x += g.nthreads) alive_count += sm.alive[x];
   alive_count = grp_sum_int(g, sm, alive_count);
+  for (int x = g.tid; x < nslots; x += g.nthreads) sm.wkey[x] = sm.alive[x] ? par_key(sm, x) : 0ull;
+  g.sync();
   for (int x = g.tid; x < nslots; x += g.nthreads) {
     if (!sm.alive[x]) continue;
-    const unsigned long long ux = sm.Uc[x] + sm.Um[x];
-    const unsigned char lx = sm.lowest[x];
+    const unsigned long long kx = sm.wkey[x];
     int r = 0;
-    for (int y = 0; y < nslots; y++) {
-      if (!sm.alive[y] || y == x) continue;
-      const unsigned long long uy = sm.Uc[y] + sm.Um[y];
-      r += (uy > ux) || (uy == ux && sm.lowest[y] < lx);
-    }
+#pragma unroll 4
+    for (int y = 0; y < nslots; y++) r += sm.wkey[y] > kx;  // dead slots have key 0
     sm.order[r] = (unsigned char)x;
   }
   g.sync();
@@ -488,14 +493,14 @@ __device__ int sort_par_list(const Grp& g, MergeSmem& sm, int nslots) {
 }
 
 // Eligibility of every slot for a merge with slot c (Alg. 3: partners in a
-// forbidden pair are excluded), by one warp.
-__device__ __forceinline__ void eligible_of(const MergeSmem& sm, int c, int nslots, unsigned int* elig) {
+// forbidden pair are excluded), by one warp; act: some ACT pair is forbidden.
+__device__ __forceinline__ void eligible_of(const MergeSmem& sm, int c, int nslots, bool act, unsigned int* elig) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int w = 0; w < kWords; w++) {
     const int e = w * 32 + lane;
-    bool ok = e < nslots && sm.alive[e] && e != c && !((sm.forb[c][w] >> lane) & 1u) &&
-              !mask_meets(sm.mask[e], sm.actm[c]);
+    bool ok = e < nslots && w * 32 < nslots && sm.alive[e] && e != c && !((sm.forb[c][w] >> lane) & 1u) &&
+              !(act && mask_meets(sm.mask[e], sm.actm[c]));
     elig[w] = __ballot_sync(kFull, ok);
   }
 }
@@ -525,6 +530,35 @@ __device__ void apply_merge(const Grp& g, MergeSmem& sm, int a, int b, unsigned 
     if (sm.slot_of[x] == b) sm.slot_of[x] = (unsigned char)a;
   }
   g.sync();
+}
+
+// par_list after slot b was merged into slot a (positions pa, pb in the old
+// order): the others keep their order, b leaves and a moves to its new rank,
+// the number of the others with a larger key.  Returns the new length.
+__device__ int reorder_after_merge(const Grp& g, MergeSmem& sm, int a, int b, int nal) {
+  const unsigned long long ka = par_key(sm, a);
+  int pa = -1, pb = -1, ra = 0;
+  for (int p = g.tid; p < nal; p += g.nthreads) {
+    const int x = sm.order[p];
+    if (x == a) pa = p;
+    else if (x == b) pb = p;
+    else ra += par_key(sm, x) > ka;
+  }
+  pa = grp_max_int(g, sm, pa);
+  pb = grp_max_int(g, sm, pb);
+  ra = grp_sum_int(g, sm, ra);
+  for (int p = g.tid; p < nal; p += g.nthreads) {
+    const int x = sm.order[p];
+    if (x == a || x == b) continue;
+    int q = p - (pa < p) - (pb < p);
+    q += q >= ra;
+    sm.jk[q] = (unsigned char)x;
+  }
+  if (g.tid == 0) sm.jk[ra] = (unsigned char)a;
+  g.sync();
+  for (int p = g.tid; p < nal - 1; p += g.nthreads) sm.order[p] = sm.jk[p];
+  g.sync();
+  return nal - 1;
 }
 
 // Forbids the pairs (p1, cand[k]) for k < kend.
@@ -625,6 +659,7 @@ __device__ void merge_set(const Grp& g, MergeSmem& sm, WarpScratch* extra, long 
     return;
   }
   int tests = 0;
+  bool act_any = false;  // some ACT pair is forbidden
   // ACT: every task pair is tried as a merge of two singletons; pairs that
   // fail are forbidden for the rest of the run (§5.3).  A pair merges iff
   // it passes at the top admissible size of its range.
@@ -651,20 +686,19 @@ __device__ void merge_set(const Grp& g, MergeSmem& sm, WarpScratch* extra, long 
     }
     tests += n * (n - 1) / 2;
     g.sync();
+    int any = 0;
     for (int r = tid; r < n; r += g.nthreads)
 #pragma unroll
-      for (int w = 0; w < kWords; w++) sm.actm[r][w] = sm.act[r][w];
-    g.sync();
+      for (int w = 0; w < kWords; w++) {
+        sm.actm[r][w] = sm.act[r][w];
+        any |= sm.act[r][w] != 0u;
+      }
+    act_any = grp_sum_int(g, sm, any) != 0;
   }
 
-  bool stuck = false, need_sort = true;
-  int nal = 0, r0 = 0;
+  bool stuck = false;
+  int nal = pi > (int)M ? sort_par_list(g, sm, n) : 0, r0 = 0;
   while (pi > (int)M) {
-    if (need_sort) {
-      nal = sort_par_list(g, sm, n);
-      r0 = 0;
-      need_sort = false;
-    }
     // Alg. 3 (warp 0): the first partition in par_list order, from r0, with
     // an eligible partner; its eligible partners in par_list order
     if (g.warp == 0) {
@@ -672,7 +706,7 @@ __device__ void merge_set(const Grp& g, MergeSmem& sm, WarpScratch* extra, long 
       unsigned int elig[kWords];
       for (int r = r0; r < nal; r++) {
         const int c = sm.order[r];
-        eligible_of(sm, c, n, elig);
+        eligible_of(sm, c, n, act_any, elig);
         unsigned int any = 0u;
 #pragma unroll
         for (int w = 0; w < kWords; w++) any |= elig[w];
@@ -764,7 +798,8 @@ __device__ void merge_set(const Grp& g, MergeSmem& sm, WarpScratch* extra, long 
         const int best = sm.cand[win];
         pi -= (int)sm.m[p1] + (int)sm.m[best] - (int)wm;
         apply_merge(g, sm, p1, best, wm, n);
-        need_sort = true;
+        nal = reorder_after_merge(g, sm, p1, best, nal);
+        r0 = 0;
       } else {
         forbid_cands(g, sm, p1, ne);
         r0 = rp + 1;
@@ -825,7 +860,8 @@ __device__ void merge_set(const Grp& g, MergeSmem& sm, WarpScratch* extra, long 
         const int best = sm.cand[win];
         pi -= (int)sm.m[p1] + (int)sm.m[best] - (int)wm;
         apply_merge(g, sm, p1, best, wm, n);
-        need_sort = true;
+        nal = reorder_after_merge(g, sm, p1, best, nal);
+        r0 = 0;
       } else {
         tests += ne;
         r0 = rp + 1;

@@ -84,12 +84,12 @@ struct Sizes {
   const unsigned short* list;
   const unsigned short* rank;
   int n;
-  // number of admissible sizes below m (m <= M + 1)
+  // number of admissible sizes below m (m <= M + 1); unit 1 needs no division
   __device__ __forceinline__ int below(unsigned int m) const {
-    if (!list) return m == 0u ? 0 : (int)((m - 1u) / g);
+    if (!list) return m == 0u ? 0 : (int)(g == 1u ? m - 1u : (m - 1u) / g);
     return rank[m];
   }
-  __device__ __forceinline__ int count() const { return list ? n : (int)(M / g); }
+  __device__ __forceinline__ int count() const { return list ? n : (int)(g == 1u ? M : M / g); }
   __device__ __forceinline__ unsigned int at(int k) const { return list ? (unsigned int)list[k] : (unsigned int)(k + 1) * g; }
   // smallest admissible size >= m (1 <= m), 0 if none
   __device__ __forceinline__ unsigned int next(unsigned int m) const {
@@ -162,9 +162,8 @@ struct SetSmem {
 // Per-warp scratch of the response-time test: the partition's tasks,
 // compacted in priority order.
 struct RtaScratch {
-  unsigned int C[kNmax];
+  uint2 cm[kNmax];  // .x: the task's WCET at the tested size, .y: the reciprocal of its period
   unsigned int T[kNmax];
-  unsigned int mT[kNmax];
   unsigned int D[kNmax];
   unsigned char sh[kNmax];
   unsigned char pos[kNmax];
@@ -315,9 +314,8 @@ __device__ __forceinline__ int compact_partition(const SetSmem& st, const unsign
       if ((word >> lane) & 1u) {
         int idx = base + __popc(word & ((1u << lane) - 1u));
         bool mem = (st.memmask[w] >> lane) & 1u;
-        sc.C[idx] = wcet(st.A[row], st.B[row], mem ? kmem : kcmp, m, md);
+        sc.cm[idx] = make_uint2(wcet(st.A[row], st.B[row], mem ? kmem : kcmp, m, md), st.mT[row]);
         sc.T[idx] = st.T[row];
-        sc.mT[idx] = st.mT[row];
         sc.sh[idx] = st.shT[row];
         sc.D[idx] = st.D[row];
         sc.pos[idx] = (unsigned char)row;
@@ -347,7 +345,7 @@ static __device__ __noinline__ bool warp_rta(const SetSmem& st, const unsigned i
     const bool active = i < s;
     unsigned int Ci = 0, Di = 0;
     if (active) {
-      Ci = sc.C[i];
+      Ci = sc.cm[i].x;
       Di = sc.D[i];
     }
     unsigned long long pre = Ci;  // inclusive prefix sum of the chunk's WCETs
@@ -370,8 +368,9 @@ static __device__ __noinline__ bool warp_rta(const SetSmem& st, const unsigned i
           unsigned long long next = Ci;
           nt += (unsigned int)i;
           for (int j = 0; j < i; j++) {
-            unsigned int q = ceil_div_T(Rc, sc.mT[j], sc.sh[j]);
-            unsigned long long t = (unsigned long long)q * sc.C[j];
+            const uint2 v = sc.cm[j];  // one 8-byte broadcast load: C_j and T_j's reciprocal
+            const unsigned int q = ceil_div_T(Rc, v.y, sc.sh[j]);
+            const unsigned long long t = (unsigned long long)q * v.x;
             next += t < cap ? t : cap;
           }
           if (next == R) done = true;
@@ -581,7 +580,7 @@ static __device__ __noinline__ bool warp_edf(const SetSmem& st, const unsigned i
   const int lane = threadIdx.x & 31;
   const int s = compact_partition(st, S, m, kc, km, mdiv[m], sc);
   if (s == 0) return true;
-  if (s == 1) return sc.C[0] <= sc.D[0];
+  if (s == 1) return sc.cm[0].x <= sc.D[0];
   bool late = false;
   unsigned long long csum = 0;
   float uf = 0.0f;
@@ -589,7 +588,7 @@ static __device__ __noinline__ bool warp_edf(const SetSmem& st, const unsigned i
   unsigned int dmin = 0xffffffffu, dmax = 0u;
   float dens = 0.0f;
   for (int i = lane; i < s; i += 32) {
-    const unsigned int C = sc.C[i], T = sc.T[i], D = sc.D[i];
+    const unsigned int C = sc.cm[i].x, T = sc.T[i], D = sc.D[i];
     late = late || C > D;
     const float r = (float)C / (float)T;
     uf += r;
@@ -616,7 +615,7 @@ static __device__ __noinline__ bool warp_edf(const SetSmem& st, const unsigned i
     double num = 0.0;
     for (int i = lane; i < s; i += 32) {
       const unsigned long long hi0 = q.hi, lo0 = q.lo;
-      edf_uterm64(sc.C[i], sc.T[i], q, nz);
+      edf_uterm64(sc.cm[i].x, sc.T[i], q, nz);
       // this term's value (q after - q before) times (T - D) / 2^64
       const unsigned long long dlo = q.lo - lo0, dhi = q.hi - hi0 - (q.lo < lo0 ? 1ull : 0ull);
       num += (double)(sc.T[i] - sc.D[i]) * ((double)dhi + (double)dlo * 0x1p-64);
@@ -628,7 +627,7 @@ static __device__ __noinline__ bool warp_edf(const SetSmem& st, const unsigned i
     int cmp = edf_classify64(q, nz, &gap);
     if (cmp == 2) {
       cmp = edf_lcm_classify(s, [&](int a, unsigned int& C, unsigned int& T) {
-        C = sc.C[a];
+        C = sc.cm[a].x;
         T = sc.T[a];
       });
       gap = 0.0;  // exact sign only: no L_a bound
@@ -646,7 +645,7 @@ static __device__ __noinline__ bool warp_edf(const SetSmem& st, const unsigned i
   for (;;) {
     unsigned long long part = 0;
     if (lane == 0) sc.terms += (unsigned int)s;
-    for (int i = lane; i < s; i += 32) part += ceil_div_T64(L, sc.T[i], sc.mT[i], sc.sh[i]) * sc.C[i];
+    for (int i = lane; i < s; i += 32) part += ceil_div_T64(L, sc.T[i], sc.cm[i].y, sc.sh[i]) * sc.cm[i].x;
     const unsigned long long next = warp_sum_u64_edf(part);
     if (next == L) break;
     if (next >= La) {
@@ -666,7 +665,7 @@ static __device__ __noinline__ bool warp_edf(const SetSmem& st, const unsigned i
   // QPA
   unsigned long long t = 0;
   for (int i = lane; i < s; i += 32) {
-    const unsigned long long d = edf_deadline_below(L, sc.T[i], sc.D[i], sc.mT[i], sc.sh[i]);
+    const unsigned long long d = edf_deadline_below(L, sc.T[i], sc.D[i], sc.cm[i].y, sc.sh[i]);
     t = d > t ? d : t;
   }
   t = warp_max_u64(t);
@@ -676,7 +675,7 @@ static __device__ __noinline__ bool warp_edf(const SetSmem& st, const unsigned i
     if (lane == 0) sc.terms += (unsigned int)s;
     for (int i = lane; i < s; i += 32) {
       const unsigned int D = sc.D[i];
-      if (D <= t) part += (floor_div_T64(t - D, sc.T[i], sc.mT[i], sc.sh[i]) + 1ull) * sc.C[i];
+      if (D <= t) part += (floor_div_T64(t - D, sc.T[i], sc.cm[i].y, sc.sh[i]) + 1ull) * sc.cm[i].x;
     }
     const unsigned long long h = warp_sum_u64_edf(part);
     if (h > t) return false;
@@ -686,7 +685,7 @@ static __device__ __noinline__ bool warp_edf(const SetSmem& st, const unsigned i
     } else {
       unsigned long long d = 0;
       for (int i = lane; i < s; i += 32) {
-        const unsigned long long e = edf_deadline_below(t, sc.T[i], sc.D[i], sc.mT[i], sc.sh[i]);
+        const unsigned long long e = edf_deadline_below(t, sc.T[i], sc.D[i], sc.cm[i].y, sc.sh[i]);
         d = e > d ? e : d;
       }
       t = warp_max_u64(d);

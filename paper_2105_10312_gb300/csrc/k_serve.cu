@@ -396,7 +396,7 @@ __device__ void serve_one(ServeSmem& sm, const ServeReq rq, ServeResp* rs, Tenan
 // (kErrIter) answers status 2 (GPA_ERR_TIMEOUT): the tenant's state is still
 // an allocation whose every partition passes, but the choice among them may
 // differ from that of the exact analysis.
-__global__ void __launch_bounds__(128) serve_batch(const ServeReq* __restrict__ reqs, int nreq,
+__global__ void __launch_bounds__(128, 1) serve_batch(const ServeReq* __restrict__ reqs, int nreq,
                                                    TenantSlot* const* __restrict__ chunks, ServePayload pay,
                                                    ServeResp* __restrict__ resps, DevModel md, gpa_params prm,
                                                    const MagicDiv* __restrict__ mdiv, unsigned int* err) {
