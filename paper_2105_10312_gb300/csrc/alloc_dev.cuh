@@ -226,9 +226,12 @@ __device__ __forceinline__ unsigned long long grp_sum_u64(const Grp& g, MergeSme
 }
 
 // §5.5 per-partition test of a merged set S (at most kLaneMax tasks) by one
-// thread, serially.  Tasks are visited in priority order and each earlier
-// task met its deadline, so R_i >= R_prev + C_i starts the iteration (same
-// least fixed point as starting from the sum of the WCETs).
+// thread, serially.  First the tasks' WCETs in priority order, with a
+// float utilisation sum: a task with C > D, or a sum above 1 + 2^-13
+// (U > 1, see kUtilFail), fails the set before any iteration.  Then tasks
+// are visited in priority order and each earlier task met its deadline, so
+// R_i >= R_prev + C_i starts the iteration (same least fixed point as
+// starting from the sum of the WCETs).
 __device__ bool lane_rta(const SetSmem& st, const unsigned int* S, unsigned int m, unsigned int kc, unsigned int km,
                          const MagicDiv& md, LaneScratch& ls, int lane, unsigned int* err) {
   int nm = 0, ns = 0;
@@ -238,44 +241,53 @@ __device__ bool lane_rta(const SetSmem& st, const unsigned int* S, unsigned int 
     ns += __popc(S[w]);
   }
   const unsigned int kmem = nm >= 2 ? km : 1000u, kcmp = (ns - nm) >= 2 ? kc : 1000u;
-  unsigned long long Rprev = 0;
-  unsigned int nt = 0;
-  bool ok = true;
-  int pos = 0;
-  for (int w = 0; w < kWords && ok; w++) {
-    for (unsigned int bits = S[w]; bits && ok; bits &= bits - 1u) {
+  int n = 0;
+  float uf = 0.0f;
+  bool c_le_d = true;
+  for (int w = 0; w < kWords; w++) {
+    for (unsigned int bits = S[w]; bits; bits &= bits - 1u) {
       const int row = w * 32 + __ffs(bits) - 1;
       const bool mem = (st.memmask[w] >> (row & 31)) & 1u;
       const unsigned int Ci = wcet(st.A[row], st.B[row], mem ? kmem : kcmp, m, md);
-      ls.cm[pos][lane] = make_uint2(Ci, st.mT[row]);
-      ls.sh[pos][lane] = st.shT[row];
-      unsigned long long R = Rprev + Ci;
-      const unsigned int Di = st.D[row];
-      const unsigned long long cap = (unsigned long long)Di + 1ull;
-      int iter = 0;
-      for (;;) {
-        if (R > Di) {
-          ok = false;
-          break;
-        }
-        unsigned long long next = Ci;
-        nt += (unsigned int)pos;
-        for (int q = 0; q < pos; q++) {
-          const uint2 v = ls.cm[q][lane];
-          const unsigned long long t = (unsigned long long)ceil_div_T((unsigned int)R, v.y, ls.sh[q][lane]) * v.x;
-          next += t < cap ? t : cap;
-        }
-        if (next == R) break;
-        R = next;
-        if (++iter > kIterCap) {
-          atomicOr(err, kErrIter);
-          ok = false;
-          break;
-        }
-      }
-      Rprev = R;
-      pos++;
+      ls.cm[n][lane] = make_uint2(Ci, st.mT[row]);
+      ls.sh[n][lane] = st.shT[row];
+      ls.row[n][lane] = (unsigned char)row;
+      c_le_d = c_le_d && Ci <= st.D[row];
+      uf += (float)Ci / (float)st.T[row];
+      n++;
     }
+  }
+  if (!c_le_d || uf > kUtilFail) return false;
+  unsigned long long Rprev = 0;
+  unsigned int nt = 0;
+  bool ok = true;
+  for (int pos = 0; pos < n && ok; pos++) {
+    const uint2 self = ls.cm[pos][lane];
+    const unsigned int Ci = self.x, Di = st.D[ls.row[pos][lane]];
+    unsigned long long R = Rprev + Ci;
+    int iter = 0;
+    for (;;) {
+      if (R > Di) {
+        ok = false;
+        break;
+      }
+      // every earlier task met its deadline, so C_q <= D_q <= T_q and each
+      // term stays below R + T_q < 2^32: the sum cannot overflow
+      unsigned long long next = Ci;
+      nt += (unsigned int)pos;
+      for (int q = 0; q < pos; q++) {
+        const uint2 v = ls.cm[q][lane];
+        next += (unsigned long long)ceil_div_T((unsigned int)R, v.y, ls.sh[q][lane]) * v.x;
+      }
+      if (next == R) break;
+      R = next;
+      if (++iter > kIterCap) {
+        atomicOr(err, kErrIter);
+        ok = false;
+        break;
+      }
+    }
+    Rprev = R;
   }
   ls.terms[lane] += nt;
   return ok;
@@ -583,9 +595,8 @@ __device__ void cand_ranges(const Grp& g, MergeSmem& sm, int p1, int ne, const S
     const int a = z.below(lo), b = lo <= hi ? z.below(hi + 1u) - 1 : a - 1;
     sm.ka[k] = (unsigned short)a;
     sm.kb[k] = (unsigned short)(b < 0 ? 0 : b);
-    int cnt = 0;
-#pragma unroll
-    for (int w = 0; w < kWords; w++) cnt += __popc(sm.mask[p1][w] | sm.mask[e][w]);
+    // tasks of the merged set (the two slots' task sets are disjoint)
+    const int cnt = sm.nc[p1] + sm.nm[p1] + sm.nc[e] + sm.nm[e];
     sm.big[k] = cnt > kLaneMax ? 1 : 0;
     sm.live[k] = b >= a ? 1 : 0;
     if (b >= a) {

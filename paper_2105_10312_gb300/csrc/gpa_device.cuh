@@ -167,6 +167,7 @@ struct RtaScratch {
   unsigned int D[kNmax];
   unsigned char sh[kNmax];
   unsigned char pos[kNmax];
+  unsigned int Rcur[kNmax];  // verdict-only test: each task's latest iterate (saturated at 2^32 - 1)
   // interference terms evaluated by this warp's tests: ceil(R / T_j) C_j of
   // the response-time iteration, or one task's demand of an EDF step
   unsigned long long terms;
@@ -327,13 +328,138 @@ __device__ __forceinline__ int compact_partition(const SetSmem& st, const unsign
   return base;
 }
 
+// A float sum of the terms C_i / T_i (each at most 1) of at most 256 tasks
+// is within 2^-15 of U when U <= 1, so a sum above 1 + 2^-13 proves U > 1,
+// and with it a miss under any policy on one processor.
+constexpr float kUtilFail = 1.0f + 0x1p-13f;
+
+// One step of task i's response-time iteration: next = C_i + sum_{j<i}
+// ceil(R / T_j) C_j over the compacted tasks (uncapped when every C_j <= D_j,
+// see warp_rta).
+__device__ __forceinline__ unsigned long long rta_step(const RtaScratch& sc, int i, unsigned long long R,
+                                                      unsigned int Ci, unsigned int Di, bool c_le_d) {
+  const unsigned int Rc = (unsigned int)R;
+  unsigned long long next = Ci;
+  if (c_le_d) {
+    for (int j = 0; j < i; j++) {
+      const uint2 v = sc.cm[j];  // one 8-byte broadcast load: C_j and T_j's reciprocal
+      next += (unsigned long long)ceil_div_T(Rc, v.y, sc.sh[j]) * v.x;
+    }
+  } else {
+    // terms capped at D_i + 1: a capped term already puts the sum above D_i
+    const unsigned long long cap = (unsigned long long)Di + 1ull;
+    for (int j = 0; j < i; j++) {
+      const uint2 v = sc.cm[j];
+      const unsigned long long t = (unsigned long long)ceil_div_T(Rc, v.y, sc.sh[j]) * v.x;
+      next += t < cap ? t : cap;
+    }
+  }
+  return next;
+}
+
+// Verdict-only response-time test of the s compacted tasks, lanes taking
+// tasks in priority order as they finish: lane l starts with task l, and a
+// lane whose task reached its fixed point takes the next unassigned one, so
+// no lane idles while another iterates.  A new task i starts at the latest
+// iterate of task i - 1 plus C_i (with several tasks assigned in one step, a
+// prefix sum of their WCETs): an iterate is at most its least fixed point
+// and R_i >= R_{i-1} + C_i, so the start is at most task i's least fixed
+// point.  Returns false at the first step in which some task passed its
+// deadline (or hit the step limit: *eb |= kErrIter).
+__device__ __forceinline__ bool rta_verdict(RtaScratch& sc, int s, bool c_le_d, unsigned int* eb, unsigned int& nt) {
+  const int lane = threadIdx.x & 31;
+  const unsigned int lt = (1u << lane) - 1u;
+  int i = lane < s ? lane : -1;
+  unsigned int Ci = i >= 0 ? sc.cm[i].x : 0u, Di = i >= 0 ? sc.D[i] : 0u;
+  unsigned long long R = Ci;  // inclusive prefix sum of the first 32 WCETs
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long v = __shfl_up_sync(kFull, R, o);
+    if (lane >= o) R += v;
+  }
+  int next = s < 32 ? s : 32;  // the first task not yet assigned
+  int iter = 0;
+  for (;;) {
+    bool miss = false, conv = i < 0;
+    if (i >= 0) {
+      if (R > Di) {
+        miss = true;
+      } else {
+        const unsigned long long nx = rta_step(sc, i, R, Ci, Di, c_le_d);
+        nt += (unsigned int)i;
+        if (nx == R) {
+          conv = true;
+        } else {
+          R = nx;
+          if (++iter > kIterCap) {
+            *eb |= kErrIter;
+            miss = true;
+          }
+        }
+      }
+      sc.Rcur[i] = R > 0xffffffffull ? 0xffffffffu : (unsigned int)R;
+    }
+    if (__any_sync(kFull, miss)) return false;
+    const unsigned int freem = __ballot_sync(kFull, conv);
+    if (next >= s && freem == kFull) return true;
+    __syncwarp();
+    // free lanes take tasks next, next + 1, ... in lane order
+    const int idx = next + __popc(freem & lt);
+    const bool take = conv && idx < s;
+    const unsigned int Cn = take ? sc.cm[idx].x : 0u;
+    unsigned long long start = Cn;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long v = __shfl_up_sync(kFull, start, o);
+      if (lane >= o) start += v;
+    }
+    const unsigned long long base = next > 0 ? (unsigned long long)sc.Rcur[next - 1] : 0ull;
+    if (take) {
+      i = idx;
+      Ci = Cn;
+      Di = sc.D[idx];
+      R = base + start;
+      iter = 0;
+    } else if (conv) {
+      i = -1;
+    }
+    next = min(s, next + __popc(freem));
+    __syncwarp();
+  }
+}
+
 static __device__ __noinline__ bool warp_rta(const SetSmem& st, const unsigned int* S, unsigned int m, unsigned int kc,
                                       unsigned int km, const MagicDiv* __restrict__ mdiv, RtaScratch& sc,
                                       long long* R_row, bool early_exit, unsigned int* err) {
   const int lane = threadIdx.x & 31;
   const int s = compact_partition(st, S, m, kc, km, mdiv[m], sc);
+  // Every C_j <= D_j (<= T_j) bounds each term ceil(R / T_j) C_j by R + T_j
+  // < 2^32 while R <= D < 2^31, so the sums need no cap; a task with
+  // C > D misses.  For a verdict alone, such a task or U > 1 decides it at
+  // once.
+  bool c_le_d = true;
+  float uf = 0.0f;
+  for (int i = lane; i < s; i += 32) {
+    const unsigned int C = sc.cm[i].x;
+    c_le_d = c_le_d && C <= sc.D[i];
+    uf += (float)C / (float)sc.T[i];
+  }
+  c_le_d = __all_sync(kFull, c_le_d);
+  if (early_exit) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) uf += __shfl_xor_sync(kFull, uf, o);
+    if (!c_le_d || uf > kUtilFail) return false;
+  }
   bool all_ok = true;
   unsigned int errbits = 0u, nt = 0u;
+  if (early_exit && !R_row) {
+    all_ok = rta_verdict(sc, s, c_le_d, &errbits, nt);
+    errbits = __reduce_or_sync(kFull, errbits);
+    if (errbits && lane == 0) atomicOr(err, errbits);
+    warp_add_terms(sc.terms, nt);
+    __syncwarp();
+    return all_ok;
+  }
   // Start values: the least fixed points grow along the priority order by at
   // least each task's own WCET (R_i >= R_{i-1} + C_i), so task i starts at
   // R_last + C_{c0} + ... + C_i, R_last being where the previous chunk's last
@@ -363,16 +489,8 @@ static __device__ __noinline__ bool warp_rta(const SetSmem& st, const unsigned i
           ok = false;
           done = true;
         } else {
-          const unsigned int Rc = (unsigned int)R;
-          const unsigned long long cap = (unsigned long long)Di + 1ull;
-          unsigned long long next = Ci;
+          const unsigned long long next = rta_step(sc, i, R, Ci, Di, c_le_d);
           nt += (unsigned int)i;
-          for (int j = 0; j < i; j++) {
-            const uint2 v = sc.cm[j];  // one 8-byte broadcast load: C_j and T_j's reciprocal
-            const unsigned int q = ceil_div_T(Rc, v.y, sc.sh[j]);
-            const unsigned long long t = (unsigned long long)q * v.x;
-            next += t < cap ? t : cap;
-          }
           if (next == R) done = true;
           else R = next;
           if (++iter > kIterCap) {

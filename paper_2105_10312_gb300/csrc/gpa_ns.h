@@ -12,8 +12,13 @@
 // 256-task state.
 #pragma once
 
+// GPA_MERGE_MINB: CTAs of 256 threads the merge kernel's registers must
+// allow per SM; the 64-task build keeps its state in 128 registers (more
+// sets in flight: paper50 2.7 -> 2.2 ms), the larger builds in up to 255
+// (fewer spills: 200-task sets 126 -> 114 ms).
 #if defined(GPA_WIDE)
 #define GPA_KNMAX 256
+#define GPA_MERGE_MINB 1
 #define GPA_NS_BEGIN \
   namespace gpa {    \
   namespace wide {
@@ -22,6 +27,7 @@
   }
 #elif defined(GPA_SMALL)
 #define GPA_KNMAX 64
+#define GPA_MERGE_MINB 2
 #define GPA_NS_BEGIN \
   namespace gpa {    \
   namespace small {
@@ -30,6 +36,7 @@
   }
 #else
 #define GPA_KNMAX 128
+#define GPA_MERGE_MINB 1
 #define GPA_NS_BEGIN namespace gpa {
 #define GPA_NS_END }
 #endif

@@ -417,7 +417,7 @@ __host__ __device__ constexpr size_t merge_group_bytes(int gw) {
 
 // The merge kernel: CTAs of warps_per_block warps in groups of gw warps;
 // each group pops deferred sets from the queue and runs Alg. 1 on them.
-__global__ void __launch_bounds__(256, 1) alloc_merge(DevSets S, DevModel md, gpa_params p, AllocOut out, AllocQueue q,
+__global__ void __launch_bounds__(256, GPA_MERGE_MINB) alloc_merge(DevSets S, DevModel md, gpa_params p, AllocOut out, AllocQueue q,
                                                    const MagicDiv* __restrict__ mdiv, int gw) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -438,6 +438,7 @@ __global__ void __launch_bounds__(256, 1) alloc_merge(DevSets S, DevModel md, gp
   if (lane == 0) sc.terms = 0ull;
   asm volatile("griddepcontrol.wait;" ::: "memory");  // the fast grid has finished and its writes are visible
   const unsigned long long nslow = *(volatile unsigned long long*)(q.counters + 1);
+  if (nslow == 0ull) return;  // the fast kernel decided every set
   const long long ntasks = S.set_off[S.nsets];
   for (;;) {
     if (g.tid == 0) sm.ticket = (long long)atomicAdd(q.counters + 2, 1ull);

@@ -96,13 +96,13 @@ __device__ bool serial_rta(const SearchHead& h, SearchThreads& w, unsigned int S
     int iter = 0;
     for (;;) {
       if (R > Di) return false;
-      const unsigned long long cap = (unsigned long long)Di + 1ull;
+      // every earlier task met its deadline (C_j <= D_j <= T_j): each term
+      // stays below R + T_j < 2^32 and the sum cannot overflow
       unsigned long long next = Ci;
       nt += (unsigned int)__popc(hp);
       for (unsigned int r2 = hp; r2; r2 &= r2 - 1u) {
         const int j = __ffs(r2) - 1;
-        const unsigned long long t = (unsigned long long)ceil_div_T((unsigned int)R, h.mT[j], h.sh[j]) * w.C[j][tid];
-        next += t < cap ? t : cap;
+        next += (unsigned long long)ceil_div_T((unsigned int)R, h.mT[j], h.sh[j]) * w.C[j][tid];
       }
       if (next == R) break;
       R = next;

@@ -123,45 +123,68 @@ def test_one_gpu_warps_and_autotuner(ctx):
 
 
 def _hand_terms(s, M, g):
-    """Interference terms of the 1G test by the iteration the warp test runs:
-    tasks in deadline-monotonic order, 32 at a time (one per lane); task i
-    of a chunk starting at task c0 starts at R_{c0-1} + C_{c0} + ... + C_i
-    (R_{-1} = 0, R_{c0-1} where the previous chunk's last task stopped) and
-    each step evaluates i terms; the lanes step together, and the test stops
-    after the step in which some task passed its deadline."""
+    """Interference terms of the 1G verdict test, by the iteration the warp
+    runs: no iteration when a task has C > D or U > 1; otherwise tasks in
+    deadline-monotonic order, lane l starting with task l at C_0 + ... + C_l,
+    every lane stepping once per round (task i's step evaluates i terms); a
+    lane whose task reached its fixed point takes the next unassigned task in
+    lane order, starting at the latest iterate of the task before it plus
+    the WCETs of the tasks assigned up to it in that round; the test stops
+    after the round in which some task passed its deadline."""
     import math
+    from fractions import Fraction
     T, D, A, B, ty = (np.asarray(s[k], np.int64) for k in ("T", "D", "A", "B", "type"))
     n = len(T)
     order = sorted(range(n), key=lambda i: (D[i], T[i], i))
     nmem = int(ty.sum())
     k = [(KM if nmem >= 2 else 1000) if ty[i] else (KC if n - nmem >= 2 else 1000) for i in range(n)]
-    C = [-(-(k[i] * (int(A[i]) + int(B[i]) * M)) // (1000000 * M)) for i in range(n)]
-    terms, Rlast = 0, 0
-    for c0 in range(0, n, 32):
-        lanes = list(range(c0, min(n, c0 + 32)))
-        R = {p: Rlast + sum(C[order[j]] for j in range(c0, p + 1)) for p in lanes}
-        done = {p: False for p in lanes}
-        ok = {p: True for p in lanes}
-        while not all(done.values()):
-            for p in lanes:
-                if done[p]:
-                    continue
-                i = order[p]
-                if R[p] > D[i]:
-                    ok[p], done[p] = False, True
-                    continue
-                terms += p
-                nxt = C[i] + sum(math.ceil(R[p] / T[order[j]]) * C[order[j]] for j in range(p))
-                if nxt == R[p]:
-                    done[p] = True
+    Cr = [-(-(k[i] * (int(A[i]) + int(B[i]) * M)) // (1000000 * M)) for i in range(n)]
+    C = [Cr[order[p]] for p in range(n)]
+    Dp = [int(D[order[p]]) for p in range(n)]
+    Tp = [int(T[order[p]]) for p in range(n)]
+    U = sum(Fraction(C[p], Tp[p]) for p in range(n))
+    assert abs(U - 1) > Fraction(1, 4096), "too close to 1 for a float-order-free count"
+    if any(C[p] > Dp[p] for p in range(n)) or U > 1:
+        return 0
+    lane_task = [p if p < n else -1 for p in range(32)]
+    R = [sum(C[:p + 1]) if p < n else 0 for p in range(32)]
+    Rcur = [0] * n
+    nxt, terms = min(n, 32), 0
+    while True:
+        miss, conv = False, [False] * 32
+        for l in range(32):
+            i = lane_task[l]
+            if i < 0:
+                conv[l] = True
+                continue
+            if R[l] > Dp[i]:
+                miss = True
+            else:
+                terms += i
+                step = C[i] + sum(math.ceil(R[l] / Tp[j]) * C[j] for j in range(i))
+                if step == R[l]:
+                    conv[l] = True
                 else:
-                    R[p] = nxt
-            if not all(ok.values()):
-                break
-        if not all(ok.values()):
-            break
-        Rlast = R[lanes[-1]]
-    return terms
+                    R[l] = step
+            Rcur[i] = min(R[l], 2**32 - 1)
+        if miss:
+            return terms
+        if nxt >= n and all(conv):
+            return terms
+        base = Rcur[nxt - 1] if nxt > 0 else 0
+        rank, acc = 0, 0
+        nfree = sum(conv)
+        for l in range(32):
+            if not conv[l]:
+                continue
+            idx = nxt + rank
+            rank += 1
+            if idx < n:
+                acc += C[idx]
+                lane_task[l], R[l] = idx, base + acc
+            else:
+                lane_task[l] = -1
+        nxt = min(n, nxt + nfree)
 
 
 def test_term_counter(ctx):
