@@ -230,8 +230,8 @@ __device__ __forceinline__ unsigned long long grp_sum_u64(const Grp& g, MergeSme
 // float utilisation sum: a task with C > D, or a sum above 1 + 2^-13
 // (U > 1, see kUtilFail), fails the set before any iteration.  Then tasks
 // are visited in priority order and each earlier task met its deadline, so
-// R_i >= R_prev + C_i starts the iteration (same least fixed point as
-// starting from the sum of the WCETs).
+// the iteration starts at the larger of R_prev + C_i and the utilisation
+// bound (util_start), both at most the least fixed point.
 __device__ bool lane_rta(const SetSmem& st, const unsigned int* S, unsigned int m, unsigned int kc, unsigned int km,
                          const MagicDiv& md, LaneScratch& ls, int lane, unsigned int* err) {
   int nm = 0, ns = 0;
@@ -260,11 +260,16 @@ __device__ bool lane_rta(const SetSmem& st, const unsigned int* S, unsigned int 
   if (!c_le_d || uf > kUtilFail) return false;
   unsigned long long Rprev = 0;
   unsigned int nt = 0;
+  float ua = 0.0f;  // sum of C_q / T_q over the tasks before pos
   bool ok = true;
   for (int pos = 0; pos < n && ok; pos++) {
     const uint2 self = ls.cm[pos][lane];
-    const unsigned int Ci = self.x, Di = st.D[ls.row[pos][lane]];
+    const int row = ls.row[pos][lane];
+    const unsigned int Ci = self.x, Di = st.D[row];
     unsigned long long R = Rprev + Ci;
+    const unsigned long long lb = util_start(Ci, ua);
+    R = lb > R ? lb : R;
+    ua += (float)Ci / (float)st.T[row];
     int iter = 0;
     for (;;) {
       if (R > Di) {

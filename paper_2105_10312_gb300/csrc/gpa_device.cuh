@@ -147,6 +147,7 @@ __device__ __forceinline__ unsigned int lemma2_size_fast(unsigned long long A, u
 // One task set staged in shared memory, rows in deadline-monotonic order
 // (D ascending, then T, then original index).
 struct SetSmem {
+  unsigned long long key[kNmax];  // staging: deadline-monotonic sort key (D, T) of each original task
   unsigned int T[kNmax];
   unsigned int D[kNmax];
   unsigned int mT[kNmax];    // Granlund-Montgomery magic of T
@@ -168,6 +169,7 @@ struct RtaScratch {
   unsigned char sh[kNmax];
   unsigned char pos[kNmax];
   unsigned int Rcur[kNmax];  // verdict-only test: each task's latest iterate (saturated at 2^32 - 1)
+  float Uex[kNmax];          // float sum of C_j / T_j over the tasks before each (when every C <= D)
   // interference terms evaluated by this warp's tests: ceil(R / T_j) C_j of
   // the response-time iteration, or one task's demand of an EDF step
   unsigned long long terms;
@@ -208,24 +210,22 @@ __device__ __forceinline__ bool stage_set(SetSmem& st, long long o, int n, const
       st.A[t] = (unsigned long long)At;
       st.B[t] = (unsigned long long)Bt;
       st.u[t] = (unsigned int)ut;
-      st.T[t] = (unsigned int)Tt;
-      st.D[t] = (unsigned int)Dt;
+      st.key[t] = ((unsigned long long)Dt << 31) | (unsigned long long)Tt;
     }
   }
   ok = __all_sync(kFull, ok);
   if (!ok) return false;
   __syncwarp();
-  // DM rank of each task by counting
+  // DM rank of each task by counting: smaller (D, T), or the same and a
+  // lower index
   int rank[kWords];
   for (int c = 0; c < kWords; c++) {
     int t = c * 32 + lane;
     int r = 0;
     if (t < n) {
-      unsigned long long key = ((unsigned long long)Dv[c] << 31) | (unsigned long long)Tv[c];
-      for (int j = 0; j < n; j++) {
-        unsigned long long kj = ((unsigned long long)st.D[j] << 31) | (unsigned long long)st.T[j];
-        r += (kj < key) || (kj == key && j < t);
-      }
+      const unsigned long long key = ((unsigned long long)Dv[c] << 31) | (unsigned long long)Tv[c];
+      for (int j = 0; j < t; j++) r += st.key[j] <= key;
+      for (int j = t + 1; j < n; j++) r += st.key[j] < key;
     }
     rank[c] = r;
   }
@@ -328,6 +328,23 @@ __device__ __forceinline__ int compact_partition(const SetSmem& st, const unsign
   return base;
 }
 
+// A lower bound of task i's least fixed point from the utilisation U_hp of
+// the tasks before it (Sjodin & Hansson, 1998): R = C_i + sum ceil(R / T_j)
+// C_j >= C_i + R U_hp, so R >= C_i / (1 - U_hp), and there is no fixed
+// point when U_hp >= 1.  uhp is a float sum of the C_j / T_j (each at most
+// 1, at most 255 of them) within 2^-15 of U_hp; the bound uses uhp - 2^-14
+// and rounds down with a 2^-20 margin, so it never exceeds the fixed point.
+// Returns 2^32 (above every deadline) when U_hp >= 1 is proven.
+__device__ __forceinline__ unsigned long long util_start(unsigned int Ci, float uhp) {
+  const float u = uhp - 0x1p-14f;
+  if (u <= 0.0f) return Ci;
+  if (u >= 1.0f) return 1ull << 32;
+  const float b = (float)Ci / (1.0f - u) * (1.0f - 0x1p-20f);
+  if (!(b < 4294967296.0f)) return 1ull << 32;
+  const unsigned long long lb = (unsigned long long)b;
+  return lb > Ci ? lb : (unsigned long long)Ci;
+}
+
 // A float sum of the terms C_i / T_i (each at most 1) of at most 256 tasks
 // is within 2^-15 of U when U <= 1, so a sum above 1 + 2^-13 proves U > 1,
 // and with it a miss under any policy on one processor.
@@ -377,6 +394,10 @@ __device__ __forceinline__ bool rta_verdict(RtaScratch& sc, int s, bool c_le_d, 
     const unsigned long long v = __shfl_up_sync(kFull, R, o);
     if (lane >= o) R += v;
   }
+  if (c_le_d && i >= 0) {
+    const unsigned long long lb = util_start(Ci, sc.Uex[i]);
+    R = lb > R ? lb : R;
+  }
   int next = s < 32 ? s : 32;  // the first task not yet assigned
   int iter = 0;
   for (;;) {
@@ -401,7 +422,12 @@ __device__ __forceinline__ bool rta_verdict(RtaScratch& sc, int s, bool c_le_d, 
     }
     if (__any_sync(kFull, miss)) return false;
     const unsigned int freem = __ballot_sync(kFull, conv);
-    if (next >= s && freem == kFull) return true;
+    if (next >= s) {
+      if (freem == kFull) return true;
+      if (conv) i = -1;
+      continue;  // nothing left to assign
+    }
+    if (freem == 0u) continue;  // no lane is free
     __syncwarp();
     // free lanes take tasks next, next + 1, ... in lane order
     const int idx = next + __popc(freem & lt);
@@ -419,6 +445,10 @@ __device__ __forceinline__ bool rta_verdict(RtaScratch& sc, int s, bool c_le_d, 
       Ci = Cn;
       Di = sc.D[idx];
       R = base + start;
+      if (c_le_d) {
+        const unsigned long long lb = util_start(Ci, sc.Uex[idx]);
+        R = lb > R ? lb : R;
+      }
       iter = 0;
     } else if (conv) {
       i = -1;
@@ -452,6 +482,23 @@ static __device__ __noinline__ bool warp_rta(const SetSmem& st, const unsigned i
   }
   bool all_ok = true;
   unsigned int errbits = 0u, nt = 0u;
+  if (c_le_d) {
+    // exclusive prefix sums of C_j / T_j, chunk by chunk
+    float carry = 0.0f;
+    for (int c0 = 0; c0 < s; c0 += 32) {
+      const int i = c0 + lane;
+      float u = i < s ? (float)sc.cm[i].x / (float)sc.T[i] : 0.0f;
+      float incl = u;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+      }
+      if (i < s) sc.Uex[i] = carry + (incl - u);
+      carry += __shfl_sync(kFull, incl, 31);
+    }
+    __syncwarp();
+  }
   if (early_exit && !R_row) {
     all_ok = rta_verdict(sc, s, c_le_d, &errbits, nt);
     errbits = __reduce_or_sync(kFull, errbits);
@@ -481,6 +528,10 @@ static __device__ __noinline__ bool warp_rta(const SetSmem& st, const unsigned i
       if (lane >= o) pre += v;
     }
     unsigned long long R = active ? Rlast + pre : 0ull;
+    if (c_le_d && active) {
+      const unsigned long long lb = util_start(Ci, sc.Uex[i]);
+      R = lb > R ? lb : R;
+    }
     bool done = !active, ok = true;
     int iter = 0;
     while (__any_sync(kFull, !done)) {

@@ -791,7 +791,7 @@ static LaunchShape merge_shape(const gpa_ctx* c, int n_max, int wpb, int gw, int
 
 // Library defaults per capacity build: one warp per set; the 256-task build
 // keeps 58 KB of shared memory per set (one-warp CTAs, up to three per SM),
-// the 64-task build 10 KB (two-warp CTAs, up to eight per SM), the 128-task
+// the 64-task build 10 KB and 128 registers (four-warp CTAs), the 128-task
 // build 22 KB (two-warp CTAs, up to five per SM), as many as the registers
 // and shared memory allow.  The 1G kernel: eight-warp CTAs, as many as fit.
 static AllocShapes default_shapes(const gpa_ctx* c, const DevSets& ds) {
@@ -799,7 +799,7 @@ static AllocShapes default_shapes(const gpa_ctx* c, const DevSets& ds) {
   sh.fast = default_fast(c);
   const bool wide_sets = ds.n_max > kNarrowNmax, small_sets = ds.n_max <= kSmallNmax;
   sh.slow = wide_sets ? merge_shape(c, ds.n_max, 1, 1, 3)
-                      : small_sets ? merge_shape(c, ds.n_max, 2, 1, 8) : merge_shape(c, ds.n_max, 2, 1, 5);
+                      : small_sets ? merge_shape(c, ds.n_max, 4, 1, 0) : merge_shape(c, ds.n_max, 2, 1, 5);
   const int per_sm = one_gpu_ctas(ds.n_max, 8);
   sh.one = LaunchShape{8, 1, c->sm_count * (per_sm > 0 ? per_sm : 1), 1};
   return sh;

@@ -79,10 +79,11 @@ __device__ bool serial_rta(const SearchHead& h, SearchThreads& w, unsigned int S
   const unsigned int kmem = cm ? km : 1000u, kcmp = cc ? kc : 1000u;
   const int mi = (int)(m / g) - 1;
   // Tasks are visited in priority order, and every one before task i met its
-  // deadline (the test stops at the first miss), so R_i >= R_prev + C_i: the
-  // iteration starts there instead of at the sum of the WCETs (same least
-  // fixed point, fewer steps).
+  // deadline (the test stops at the first miss), so R_i >= R_prev + C_i and
+  // R_i >= C_i / (1 - U_hp) (util_start): the iteration starts at the larger
+  // instead of at the sum of the WCETs (same least fixed point, fewer steps).
   unsigned long long Rprev = 0;
+  float ua = 0.0f;  // sum of C_j / T_j over the tasks before i (each at most 1: they met their deadlines)
   for (unsigned int rest = S; rest; rest &= rest - 1u) {
     const int i = __ffs(rest) - 1;
     const bool mem = (h.memmask >> i) & 1u;
@@ -91,6 +92,9 @@ __device__ bool serial_rta(const SearchHead& h, SearchThreads& w, unsigned int S
     else Ci = wcet(h.A[i], h.B[i], mem ? kmem : kcmp, m, md);
     w.C[i][tid] = Ci;
     unsigned long long R = Rprev + Ci;
+    const unsigned long long lb = util_start(Ci, ua);
+    R = lb > R ? lb : R;
+    ua += (float)Ci / (float)h.T[i];
     const unsigned int Di = h.D[i];
     const unsigned int hp = S & ((1u << i) - 1u);
     int iter = 0;

@@ -129,8 +129,10 @@ def _hand_terms(s, M, g):
     every lane stepping once per round (task i's step evaluates i terms); a
     lane whose task reached its fixed point takes the next unassigned task in
     lane order, starting at the latest iterate of the task before it plus
-    the WCETs of the tasks assigned up to it in that round; the test stops
-    after the round in which some task passed its deadline."""
+    the WCETs of the tasks assigned up to it in that round; every start is
+    raised to the utilisation bound C_i / (1 - U_hp) as the kernel rounds it
+    (float32, the same operations in the same order); the test stops after
+    the round in which some task passed its deadline."""
     import math
     from fractions import Fraction
     T, D, A, B, ty = (np.asarray(s[k], np.int64) for k in ("T", "D", "A", "B", "type"))
@@ -146,8 +148,35 @@ def _hand_terms(s, M, g):
     assert abs(U - 1) > Fraction(1, 4096), "too close to 1 for a float-order-free count"
     if any(C[p] > Dp[p] for p in range(n)) or U > 1:
         return 0
+    # float sums of C_j / T_j before each task, as the warp forms them:
+    # chunks of 32, an inclusive Hillis-Steele scan per chunk plus a carry
+    f32 = np.float32
+    Uex, carry = [f32(0)] * n, f32(0)
+    for c0 in range(0, n, 32):
+        u = np.array([f32(C[p]) / f32(Tp[p]) if p < n else f32(0) for p in range(c0, c0 + 32)], np.float32)
+        incl = u.copy()
+        for o in (1, 2, 4, 8, 16):
+            nxt_incl = incl.copy()
+            nxt_incl[o:] = incl[o:] + incl[:-o]
+            incl = nxt_incl
+        for l in range(32):
+            if c0 + l < n:
+                Uex[c0 + l] = f32(carry + f32(incl[l] - u[l]))
+        carry = f32(carry + incl[31])
+
+    def util_start(Ci, uhp):
+        u = f32(uhp - f32(2.0 ** -14))
+        if u <= 0:
+            return Ci
+        if u >= 1:
+            return 2 ** 32
+        b = f32(f32(f32(Ci) / f32(f32(1) - u)) * f32(1 - 2.0 ** -20))
+        if not b < 2.0 ** 32:
+            return 2 ** 32
+        return max(int(b), Ci)
+
     lane_task = [p if p < n else -1 for p in range(32)]
-    R = [sum(C[:p + 1]) if p < n else 0 for p in range(32)]
+    R = [max(sum(C[:p + 1]), util_start(C[p], Uex[p])) if p < n else 0 for p in range(32)]
     Rcur = [0] * n
     nxt, terms = min(n, 32), 0
     while True:
@@ -181,7 +210,7 @@ def _hand_terms(s, M, g):
             rank += 1
             if idx < n:
                 acc += C[idx]
-                lane_task[l], R[l] = idx, base + acc
+                lane_task[l], R[l] = idx, max(base + acc, util_start(C[idx], Uex[idx]))
             else:
                 lane_task[l] = -1
         nxt = min(n, nxt + nfree)
