@@ -122,12 +122,30 @@ def recorded_profile(kernel, workload):
     out = {"source": "profiles/" + name}
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.]+)", text)
     out["traffic"] = float(m.group(1)) if m else None
+    m = re.search(r"captured_tasks:\s*([0-9]+)", text)
+    out["captured_tasks"] = int(m.group(1)) if m else None
     for key, metric in (("alu_pipe_pct", "sm__pipe_alu_cycles_active.avg.pct_of_peak_sustained_active"),
                         ("issue_active_pct", "smsp__issue_active.avg.pct_of_peak_sustained_active"),
                         ("warps_active_pct", "sm__warps_active.avg.pct_of_peak_sustained_active")):
         m = re.search(r"\| " + re.escape(metric) + r" \| ([0-9.]+)", text)
         out[key] = float(m.group(1)) if m else None
     return out
+
+
+def scaled_traffic(prof, ntasks):
+    """DRAM bytes per launch from a committed capture, scaled from the
+    captured case's task count to this launch's (the kernels' traffic grows
+    with the tasks they read), with its source; None without a capture on
+    the current sources."""
+    if not prof or prof.get("traffic") is None:
+        return None
+    cap = prof.get("captured_tasks")
+    if not cap:
+        return None
+    return {"bytes": prof["traffic"] * ntasks / cap, "captured_bytes": prof["traffic"], "captured_tasks": cap,
+            "launch_tasks": ntasks, "source": prof["source"],
+            "note": "dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of a smaller case of the same "
+                    "kernel, scaled by tasks"}
 
 
 def gpu_id_for_smi(local):
@@ -623,16 +641,18 @@ def measure(bench, name, rank, world, steps, warmup, with_cpu=True, e2e_steps=5,
                 alg = 44 * ntasks + 30 * nsets
                 ach = alg / (kms / 1000.0) / 1e9
                 prof = recorded_profile(kname, name)
+                tr = scaled_traffic(prof, ntasks)
                 rec.update({"bound": "hbm", "achieved": ach, "peak": bench.hbm_peak, "unit": "GB/s",
-                            "frac": ach / bench.hbm_peak, "traffic": prof["traffic"] if prof else None,
+                            "frac": ach / bench.hbm_peak, "traffic": tr["bytes"] if tr else None, "traffic_detail": tr,
                             "algorithmic_bytes": alg, "peak_source": bench.hbm_src + " hbm_gbs (MEASURED_PEAKS.json)"})
             else:
                 t = terms[j]
                 ach = t / (kms / 1000.0)
                 prof = recorded_profile(kname, name)
+                tr = scaled_traffic(prof, ntasks)
                 rec.update({"bound": "alu", "achieved": ach, "peak": bench.alu["terms_per_s"],
                             "unit": "interference terms/s", "frac": ach / bench.alu["terms_per_s"],
-                            "traffic": prof["traffic"] if prof else None, "terms_per_launch": t,
+                            "traffic": tr["bytes"] if tr else None, "traffic_detail": tr, "terms_per_launch": t,
                             "peak_source": "measured in this run by gpa_measure_alu_peak (the term's arithmetic, "
                                            "4 independent iterations per thread, every SM and warp slot)",
                             "ncu": prof})
