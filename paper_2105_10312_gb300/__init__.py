@@ -31,7 +31,8 @@ SCHED = {"DM": 0, "EDF": 1}
 REASON = {"OK": 0, "LEMMA1": 1, "LEMMA2": 2, "NO_MERGE": 3, "TEST": 4, "INVALID": 5, "UNDECIDED": 6}
 OPT = {"AUTOTUNE": 1, "GRAPH": 2, "FAST_WARPS": 3, "FAST_CHUNK": 4, "FAST_BLOCKS": 5, "PER_SET_LAUNCH": 6,
        "PROFILE": 7, "FAST_STAGES": 8, "HOST_SLICES": 9,
-       "HOST_COPY": 10, "MERGE_WARPS": 11, "MERGE_GROUP": 12, "MERGE_BLOCKS": 13, "TEST_WARPS": 14}
+       "HOST_COPY": 10, "MERGE_WARPS": 11, "MERGE_GROUP": 12, "MERGE_BLOCKS": 13, "TEST_WARPS": 14,
+       "MERGE_TOPFIRST": 15}
 EXPLICIT_MAX = 1 << 26
 NMAX, SERVE_NMAX, MMAX, SEARCH_NMAX, SEARCH_KMAX = 256, 128, 1024, 14, 8
 

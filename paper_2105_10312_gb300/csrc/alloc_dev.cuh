@@ -88,11 +88,12 @@ __device__ __forceinline__ void finish_set_errors(long long s, unsigned int e, c
 //    pairs only removes eligibility: the next Alg. 3 scan resumes after the
 //    position of the partition that just failed.
 // SMS (Def. 3: the smallest merged size, ties to the earlier par_list
-// position) is evaluated size level by size level: at level L every
-// candidate whose range holds the L-th admissible size and that failed below
-// it is tested at that size, in position order, and the first pass at the
-// lowest level is the chosen merge; no later candidate of that level, and no
-// higher level, is tested.  BF (Def. 4) tests each candidate, in its order,
+// position) is evaluated size level by size level (optionally after a round
+// that tests every thread-tested candidate with more than one size in its
+// range at its top size; a failure there rules it out): at level L every candidate whose range holds
+// the L-th admissible size and that failed below it is tested at that size,
+// in position order, and the first pass at the lowest level is the chosen
+// merge; no later candidate of that level, and no higher level, is tested.  BF (Def. 4) tests each candidate, in its order,
 // at its top size; the first that passes is merged at its smallest passing
 // size and every earlier one is forbidden.  The number of candidate merges
 // counted in n_tests is the algorithm's (every candidate of an SMS step,
@@ -614,10 +615,11 @@ __device__ void cand_ranges(const Grp& g, MergeSmem& sm, int p1, int ne, const S
 }
 
 // Alg. 1 for the set staged in sm.st (n tasks), by group g.  extra holds the
-// test scratch of the group's warps after its first.
+// test scratch of the group's warps after its first; top_first selects the
+// SMS top-size round (same results either way).
 __device__ void merge_set(const Grp& g, MergeSmem& sm, WarpScratch* extra, long long s, long long o, int n,
                           const DevModel& md, const gpa_params& p, const AllocOut& out, const MagicDiv* mdiv,
-                          unsigned int* err) {
+                          unsigned int* err, bool top_first) {
   const int tid = g.tid;
   RtaScratch& sc = grp_sc(sm, extra, g);
   LaneScratch& ls = grp_ls(sm, extra, g);
@@ -763,6 +765,37 @@ __device__ void merge_set(const Grp& g, MergeSmem& sm, WarpScratch* extra, long 
       int lmin, lmax;
       cand_ranges(g, sm, p1, ne, z, &lmin, &lmax);
       if (linear) {
+        // with top_first, a candidate tested by one thread with more than
+        // one size in its range is first tested at its top size: failing
+        // there, it fails at every size (§4.1) and leaves the scan, so a step
+        // whose merges all fail takes one round.  (A top-size test costs more
+        // than one at the range's bottom, so this pays where failing steps
+        // with short ranges dominate -- the 50-task paper setting -- and not
+        // on 200-task sets; the launch shape carries the choice, which the
+        // autotuner times.)
+        const int nt = !top_first ? 0 : compact_jobs(g, sm, ne, [&](int k) {
+          return sm.live[k] && !sm.big[k] && sm.ka[k] < sm.kb[k];
+        });
+        if (nt > 0) {
+          eval_all(
+              g, sm, sc, ls, p1, nt,
+              [&](int jj, int& k, int& Li) {
+                k = sm.jk[jj];
+                Li = sm.kb[k];
+              },
+              tc);
+          int lo_i = 1 << 30, hi_i = -1;
+          for (int jj = tid; jj < nt; jj += g.nthreads)
+            if (!sm.pass[jj]) sm.live[sm.jk[jj]] = 0;
+          g.sync();
+          for (int k = tid; k < ne; k += g.nthreads)
+            if (sm.live[k]) {
+              lo_i = min(lo_i, (int)sm.ka[k]);
+              hi_i = max(hi_i, (int)sm.kb[k]);
+            }
+          lmin = grp_min_int(g, sm, lo_i);
+          lmax = grp_max_int(g, sm, hi_i);
+        }
         for (int L = lmin; L <= lmax && win < 0; L++) {
           const int nj = compact_jobs(g, sm, ne, [&](int k) { return sm.live[k] && sm.ka[k] <= L && L <= sm.kb[k]; });
           if (nj == 0) continue;

@@ -106,7 +106,8 @@ struct LaunchShape {
   int warps_per_block;  // warps per CTA
   int chunk;            // sets per ticket (fast kernel); warps per set (merge kernel)
   int blocks;           // CTAs of the persistent grid
-  int stages;           // fast kernel: 1 = direct loads, 2..5 = shared-memory stages fed by bulk copies
+  int stages;           // fast kernel: 1 = direct loads, 2..5 = shared-memory stages fed by bulk copies;
+                        // merge kernel: 2 = SMS steps open with the top-size round, else not
 };
 
 // The launch shapes of one gpa_allocate call: the fast kernel, the merge

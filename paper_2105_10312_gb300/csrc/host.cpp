@@ -427,6 +427,10 @@ extern "C" int32_t gpa_ctx_set_option(gpa_ctx* c, int32_t opt, int64_t value) {
       if (value < 0 || value > (1 << 20)) return gpa_fail(GPA_ERR_RANGE, "merge blocks");
       c->force_merge.blocks = (int)value;
       break;
+    case GPA_OPT_MERGE_TOPFIRST:
+      if (value < 0 || value > 2) return gpa_fail(GPA_ERR_RANGE, "merge top-size round (0 = tuned, 1 = off, 2 = on)");
+      c->force_merge.stages = (int)value;
+      break;
     case GPA_OPT_TEST_WARPS:
       if (value < 0 || value > 8) return gpa_fail(GPA_ERR_RANGE, "1G warps per CTA (0 = tuned, 1..8)");
       c->force_test_warps = (int)value;
@@ -793,13 +797,15 @@ static LaunchShape merge_shape(const gpa_ctx* c, int n_max, int wpb, int gw, int
 // keeps 58 KB of shared memory per set (one-warp CTAs, up to three per SM),
 // the 64-task build 10 KB and 128 registers (four-warp CTAs), the 128-task
 // build 22 KB (two-warp CTAs, up to five per SM), as many as the registers
-// and shared memory allow.  The 1G kernel: eight-warp CTAs, as many as fit.
+// and shared memory allow; the 64-task build opens SMS steps with the
+// top-size round (merge_set).  The 1G kernel: eight-warp CTAs, as many as fit.
 static AllocShapes default_shapes(const gpa_ctx* c, const DevSets& ds) {
   AllocShapes sh;
   sh.fast = default_fast(c);
   const bool wide_sets = ds.n_max > kNarrowNmax, small_sets = ds.n_max <= kSmallNmax;
   sh.slow = wide_sets ? merge_shape(c, ds.n_max, 1, 1, 3)
                       : small_sets ? merge_shape(c, ds.n_max, 4, 1, 0) : merge_shape(c, ds.n_max, 2, 1, 5);
+  if (small_sets) sh.slow.stages = 2;  // the SMS top-size round
   const int per_sm = one_gpu_ctas(ds.n_max, 8);
   sh.one = LaunchShape{8, 1, c->sm_count * (per_sm > 0 ? per_sm : 1), 1};
   return sh;
@@ -821,9 +827,12 @@ static AllocShapes call_shapes(gpa_ctx* c, const DevSets& ds, const DevModel& md
     if (wpb < gw || wpb % gw) wpb = gw;
     // the largest multiple of the group width up to wpb whose CTA fits an SM
     while (wpb > gw && merge_ctas(ds.n_max, wpb, gw) <= 0) wpb -= gw;
+    const int stages = sh.slow.stages;
     sh.slow = merge_shape(c, ds.n_max, wpb, gw, 0);
+    sh.slow.stages = stages;
     if (c->force_merge.blocks) sh.slow.blocks = c->force_merge.blocks;
   }
+  if (c->force_merge.stages) sh.slow.stages = c->force_merge.stages;
   if (c->force_test_warps) {
     const int w = c->force_test_warps;
     const int per_sm = one_gpu_ctas(ds.n_max, w);
@@ -864,7 +873,8 @@ static float time_allocate(gpa_ctx* c, const DevSets& ds, const DevModel& md, co
 //    ticket {1, 2, 3, 4, 8}; staged: compute warps {4, 8} x sets {1, 2, 4} x
 //    stages {2, 3}), then the merge kernel with the best of those: warps per
 //    set {1, 2, 4, 8} x warps per CTA (multiples of it, up to 8) x CTAs per
-//    SM (as many as fit, or half of that).
+//    SM (as many as fit, or half of that), then the SMS top-size round on
+//    and off.
 // The merge kernel's shapes are tried while the time spent tuning stays
 // below max(50 ms, 8 x the default run): a batch whose merges take seconds
 // keeps the shapes tried by then.
@@ -926,6 +936,14 @@ static void autotune_allocate(gpa_ctx* c, const DevSets& ds, const DevModel& md,
           }
         }
       }
+    // the SMS top-size round on or off, with the best of those shapes
+    AllocShapes t = best;
+    t.slow.stages = best.slow.stages == 2 ? 1 : 2;
+    const float ms = time_allocate(c, ds, md, p, out, t, 1, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = t;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -941,7 +959,7 @@ static std::string graph_key(const DevSets& ds, const DevModel& md, const gpa_pa
                 md.km, md.sched, md.nz, (const void*)md.zlist, p.policy, p.act, p.linear_merge, (void*)o.verdict, (void*)o.reason, (void*)o.n_parts,
                 (void*)o.Pi, (void*)o.W, (void*)o.n_tests, (void*)o.part_of_task, (void*)o.size_of_part,
                 sh.fast.warps_per_block, sh.fast.chunk, sh.fast.blocks, sh.fast.stages, sh.slow.warps_per_block,
-                sh.slow.chunk, sh.slow.blocks, sh.one.warps_per_block, sh.one.blocks, 0);
+                sh.slow.chunk, sh.slow.blocks, sh.one.warps_per_block, sh.one.blocks, sh.slow.stages);
   return buf;
 }
 

@@ -416,9 +416,10 @@ __host__ __device__ constexpr size_t merge_group_bytes(int gw) {
 }
 
 // The merge kernel: CTAs of warps_per_block warps in groups of gw warps;
-// each group pops deferred sets from the queue and runs Alg. 1 on them.
+// each group pops deferred sets from the queue and runs Alg. 1 on them
+// (top_first: the SMS top-size round of merge_set).
 __global__ void __launch_bounds__(256, GPA_MERGE_MINB) alloc_merge(DevSets S, DevModel md, gpa_params p, AllocOut out, AllocQueue q,
-                                                   const MagicDiv* __restrict__ mdiv, int gw) {
+                                                   const MagicDiv* __restrict__ mdiv, int gw, int top_first) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gi = warp / gw;
@@ -467,7 +468,7 @@ __global__ void __launch_bounds__(256, GPA_MERGE_MINB) alloc_merge(DevSets S, De
       g.sync();
       continue;
     }
-    merge_set(g, sm, extra, s, o, n, md, p, out, mdiv, &sm.err);
+    merge_set(g, sm, extra, s, o, n, md, p, out, mdiv, &sm.err, top_first != 0);
     if (g.warp == 0) finish_set_errors(s, sm.err, out, q.err);
     g.sync();
   }
@@ -655,7 +656,9 @@ cudaError_t launch_allocate(const DevSets& s, const DevModel& md, const gpa_para
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, alloc_merge, s, md, p, out, q, reinterpret_cast<const MagicDiv*>(mdiv), gw);
+  // slow.stages == 2: the SMS top-size round (see merge_set)
+  e = cudaLaunchKernelEx(&cfg, alloc_merge, s, md, p, out, q, reinterpret_cast<const MagicDiv*>(mdiv), gw,
+                         slow.stages == 2 ? 1 : 0);
   if (e != cudaSuccess) return e;
   e = cudaGetLastError();
   prof_mark(prof, st);

@@ -589,20 +589,22 @@ struct ExplicitPlan {
 };
 
 // Candidate `rank` of a set of n tasks: its part count k, its parts (in
-// units of g) and its map code.
-__device__ __forceinline__ void unrank_candidate(const ExplicitPlan& pl, int n, unsigned long long rank, int* k_out,
-                                                 int* parts, unsigned long long* code) {
+// units of g) and its map code.  A set has at most GPA_EXPLICIT_MAX (2^26)
+// candidates, so ranks, codes and every k^n with compositions fit in 32 bits.
+__device__ __forceinline__ void unrank_candidate(const ExplicitPlan& pl, int n, unsigned int rank, int* k_out,
+                                                 int* parts, unsigned int* code) {
   int k = pl.kmin;
-  unsigned long long nmaps = 0;
+  unsigned int nmaps = 1u;
   for (; k <= pl.kmax; k++) {
-    nmaps = 1ull;
-    for (int i = 0; i < n; i++) nmaps *= (unsigned long long)k;
-    const unsigned long long c = pl.comps[k] * nmaps;
+    if (pl.comps[k] == 0ull) continue;
+    nmaps = 1u;
+    for (int i = 0; i < n; i++) nmaps *= (unsigned int)k;
+    const unsigned int c = (unsigned int)pl.comps[k] * nmaps;
     if (rank < c) break;
     rank -= c;
   }
   *k_out = k;
-  unsigned long long comp = rank / nmaps;
+  unsigned int comp = rank / nmaps;
   *code = rank - comp * nmaps;
   // lexicographic unrank: parts[i] = p leaves C(left - p - 1, rest - 1)
   // completions of the remaining parts
@@ -620,7 +622,7 @@ __device__ __forceinline__ void unrank_candidate(const ExplicitPlan& pl, int n, 
         left -= pv;
         break;
       }
-      comp -= c;
+      comp -= (unsigned int)c;
     }
   }
 }
@@ -678,16 +680,16 @@ __global__ void __launch_bounds__(kSThreads) search_explicit(DevSets S, DevModel
     unsigned long long best1 = kNoKey, best2 = kNoKey;
     for (unsigned long long r = tid; r < ncand; r += kSThreads) {
       int k, parts[kSK];
-      unsigned long long code;
-      unrank_candidate(pl, n, r, &k, parts, &code);
+      unsigned int code;
+      unrank_candidate(pl, n, (unsigned int)r, &k, parts, &code);
       // the parts' task masks (rows)
       unsigned int pm[kSK];
       for (int b = 0; b < kSK; b++) pm[b] = 0u;
-      unsigned long long c = code;
+      unsigned int c = code;
       for (int i = 0; i < n; i++) {
-        const int part = (int)(c % (unsigned long long)k);
-        c /= (unsigned long long)k;
-        pm[part] |= h.rowbit[i];
+        const unsigned int q = c / (unsigned int)k;
+        pm[c - q * (unsigned int)k] |= h.rowbit[i];
+        c = q;
       }
       w.terr[tid] = 0u;
       bool feasible = true;
@@ -711,8 +713,9 @@ __global__ void __launch_bounds__(kSThreads) search_explicit(DevSets S, DevModel
       unsigned int summ = 0;
       c = code;
       for (int i = 0; i < n; i++) {
-        const int part = (int)(c % (unsigned long long)k);
-        c /= (unsigned long long)k;
+        const unsigned int q = c / (unsigned int)k;
+        const int part = (int)(c - q * (unsigned int)k);
+        c = q;
         if (label[part] < 0) {
           label[part] = nb++;
           W += smm.Wsub[pm[part]];

@@ -86,7 +86,7 @@ __device__ bool run_alg1(ServeSmem& sm, TenantSlot* t, ServeResp* rs, int n, con
   const int lane = threadIdx.x & 31;
   AllocOut out{&rs->verdict, &rs->reason, &rs->n_parts, &rs->Pi, (long long*)&rs->W, &rs->n_tests, rs->part,
                rs->size};
-  merge_set(warp_group(), sm.m, nullptr, 0, 0, n, md, p, out, mdiv, err);
+  merge_set(warp_group(), sm.m, nullptr, 0, 0, n, md, p, out, mdiv, err, false);
   __syncwarp();
   const bool ok = rs->verdict != 0;
   if (ok) {

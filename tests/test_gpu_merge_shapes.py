@@ -3,9 +3,10 @@ interference-term counter.
 
 Every shape computes the same results: the merge kernel with one to eight
 warps per task set (a set's candidate merges spread over its warps) and
-several sets per CTA, for the 64-, 128- and 256-task builds, both orders
-(SMS, BF), with and without ACT, the level-by-level and the binary search
-of Alg. 2; the 1G kernel with one to eight warps per CTA.  Each is compared
+several sets per CTA, with and without the SMS top-size round, for the 64-,
+128- and 256-task builds, both orders (SMS, BF), with and without ACT, the
+level-by-level and the binary search of Alg. 2; the 1G kernel with one to
+eight warps per CTA.  Each is compared
 element by element with the oracle."""
 import numpy as np
 import pytest
@@ -58,16 +59,18 @@ def test_merge_shapes_match_the_oracle(ctx, batches, policy, act, linear):
             continue  # one set with ACT pairs takes the oracle long; the variants run on the smaller builds
         ref = oracle.allocate(s, 68, 1, KC, KM, policy=policy, act=act, linear=linear, nthreads=8)
         d = gpa.to_device(s)
-        for gw, wpb in SHAPES:
+        for idx, (gw, wpb) in enumerate(SHAPES):
+            top = 1 + (idx + len(name)) % 2  # the SMS top-size round off (1) or on (2), alternating
             ctx.set_option("MERGE_GROUP", gw)
             ctx.set_option("MERGE_WARPS", wpb)
+            ctx.set_option("MERGE_TOPFIRST", top)
             try:
                 out = ctx.allocate(d, 68, 1, KC, KM, policy=policy, act=act, linear=linear)
                 ctx.sync()
             finally:
-                ctx.set_option("MERGE_GROUP", 0)
-                ctx.set_option("MERGE_WARPS", 0)
-            _assert_equal(out, ref, f"{name} {policy} act={act} linear={linear} shape={gw}x{wpb}")
+                for k in ("MERGE_GROUP", "MERGE_WARPS", "MERGE_TOPFIRST"):
+                    ctx.set_option(k, 0)
+            _assert_equal(out, ref, f"{name} {policy} act={act} linear={linear} shape={gw}x{wpb} top={top}")
 
 
 @pytest.mark.parametrize("sched", ["DM", "EDF"])
