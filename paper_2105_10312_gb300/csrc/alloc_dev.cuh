@@ -259,7 +259,7 @@ __device__ bool lane_rta(const SetSmem& st, const unsigned int* S, unsigned int 
     }
   }
   if (!c_le_d || uf > kUtilFail) return false;
-  unsigned long long Rprev = 0;
+  unsigned long long Rprev = 0, chp = 0;
   unsigned int nt = 0;
   float ua = 0.0f;  // sum of C_q / T_q over the tasks before pos
   bool ok = true;
@@ -270,9 +270,13 @@ __device__ bool lane_rta(const SetSmem& st, const unsigned int* S, unsigned int 
     unsigned long long R = Rprev + Ci;
     const unsigned long long lb = util_start(Ci, ua);
     R = lb > R ? lb : R;
+    // a task the utilisation bound settles keeps its start value, at most
+    // its least fixed point, as the next task's lower bound
+    const bool settled = util_pass(Ci, chp, ua, Di);
     ua += (float)Ci / (float)st.T[row];
+    chp += Ci;
     int iter = 0;
-    for (;;) {
+    for (; !settled;) {
       if (R > Di) {
         ok = false;
         break;

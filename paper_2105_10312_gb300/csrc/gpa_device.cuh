@@ -170,6 +170,8 @@ struct RtaScratch {
   unsigned char pos[kNmax];
   unsigned int Rcur[kNmax];  // verdict-only test: each task's latest iterate (saturated at 2^32 - 1)
   float Uex[kNmax];          // float sum of C_j / T_j over the tasks before each (when every C <= D)
+  unsigned long long Cin[kNmax];  // sum of the WCETs up to and including each task (when every C <= D)
+  unsigned char need[kNmax];      // verdict-only test: the tasks the utilisation bound leaves undecided
   // interference terms evaluated by this warp's tests: ceil(R / T_j) C_j of
   // the response-time iteration, or one task's demand of an EDF step
   unsigned long long terms;
@@ -345,6 +347,23 @@ __device__ __forceinline__ unsigned long long util_start(unsigned int Ci, float 
   return lb > Ci ? lb : (unsigned long long)Ci;
 }
 
+// An upper bound of task i's least fixed point, the counterpart of util_start.
+// With f(t) = C_i + sum_{j<i} ceil(t / T_j) C_j and ceil(t / T_j) C_j <=
+// t U_j + C_j, the value X = (C_i + sum_{j<i} C_j) / (1 - U_hp) satisfies
+// f(X) <= X U_hp + C_i + sum_{j<i} C_j = X.  f is non-decreasing, so every
+// iterate started at or below the least fixed point stays at or below X, and
+// R_i <= X: X <= D_i proves that task i meets its deadline without iterating.
+// uhp is within 2^-15 of U_hp (see util_start) and chp is the exact sum of
+// the C_j; the float quotient is computed from U_hp + 2^-14 and raised by
+// 2^-18, which covers the four roundings (each at most 2^-24 relative) and
+// the rounding of D_i to float, so a true result is never wrong.
+__device__ __forceinline__ bool util_pass(unsigned int Ci, unsigned long long chp, float uhp, unsigned int Di) {
+  const float u = uhp + 0x1p-14f;
+  if (!(u < 1.0f)) return false;
+  const float x = (float)(chp + Ci) / (1.0f - u) * (1.0f + 0x1p-18f);
+  return x <= (float)Di;
+}
+
 // A float sum of the terms C_i / T_i (each at most 1) of at most 256 tasks
 // is within 2^-15 of U when U <= 1, so a sum above 1 + 2^-13 proves U > 1,
 // and with it a miss under any policy on one processor.
@@ -374,31 +393,29 @@ __device__ __forceinline__ unsigned long long rta_step(const RtaScratch& sc, int
   return next;
 }
 
-// Verdict-only response-time test of the s compacted tasks, lanes taking
-// tasks in priority order as they finish: lane l starts with task l, and a
-// lane whose task reached its fixed point takes the next unassigned one, so
-// no lane idles while another iterates.  A new task i starts at the latest
-// iterate of task i - 1 plus C_i (with several tasks assigned in one step, a
-// prefix sum of their WCETs): an iterate is at most its least fixed point
-// and R_i >= R_{i-1} + C_i, so the start is at most task i's least fixed
-// point.  Returns false at the first step in which some task passed its
-// deadline (or hit the step limit: *eb |= kErrIter).
-__device__ __forceinline__ bool rta_verdict(RtaScratch& sc, int s, bool c_le_d, unsigned int* eb, unsigned int& nt) {
+// Verdict-only response-time test of the q tasks listed in sc.need (indices
+// of compacted tasks in priority order: those util_pass could not settle),
+// lanes taking tasks in list order as they finish: lane l starts with the
+// l-th, and a lane whose task reached its fixed point takes the next
+// unassigned one, so no lane idles while another iterates.  Task i starts at
+// the larger of util_start and a bound from the last task q assigned before
+// it: R_i >= R_q + C_{q+1} + ... + C_i (each task's least fixed point is at
+// least the previous one's plus its own WCET), with R_q replaced by q's
+// latest iterate, which is at most R_q.  The first tasks start at
+// C_0 + ... + C_i.  Returns false at the first step in which some task
+// passed its deadline (or hit the step limit: *eb |= kErrIter).  Every
+// C_j <= D_j, so the sums need no cap (see warp_rta).
+__device__ __forceinline__ bool rta_verdict(RtaScratch& sc, int q, unsigned int* eb, unsigned int& nt) {
   const int lane = threadIdx.x & 31;
   const unsigned int lt = (1u << lane) - 1u;
-  int i = lane < s ? lane : -1;
+  int i = lane < q ? sc.need[lane] : -1;
   unsigned int Ci = i >= 0 ? sc.cm[i].x : 0u, Di = i >= 0 ? sc.D[i] : 0u;
-  unsigned long long R = Ci;  // inclusive prefix sum of the first 32 WCETs
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long v = __shfl_up_sync(kFull, R, o);
-    if (lane >= o) R += v;
-  }
-  if (c_le_d && i >= 0) {
+  unsigned long long R = 0ull;
+  if (i >= 0) {
     const unsigned long long lb = util_start(Ci, sc.Uex[i]);
-    R = lb > R ? lb : R;
+    R = lb > sc.Cin[i] ? lb : sc.Cin[i];
   }
-  int next = s < 32 ? s : 32;  // the first task not yet assigned
+  int next = q < 32 ? q : 32;  // the first list position not yet assigned
   int iter = 0;
   for (;;) {
     bool miss = false, conv = i < 0;
@@ -406,7 +423,7 @@ __device__ __forceinline__ bool rta_verdict(RtaScratch& sc, int s, bool c_le_d, 
       if (R > Di) {
         miss = true;
       } else {
-        const unsigned long long nx = rta_step(sc, i, R, Ci, Di, c_le_d);
+        const unsigned long long nx = rta_step(sc, i, R, Ci, Di, true);
         nt += (unsigned int)i;
         if (nx == R) {
           conv = true;
@@ -422,38 +439,28 @@ __device__ __forceinline__ bool rta_verdict(RtaScratch& sc, int s, bool c_le_d, 
     }
     if (__any_sync(kFull, miss)) return false;
     const unsigned int freem = __ballot_sync(kFull, conv);
-    if (next >= s) {
+    if (next >= q) {
       if (freem == kFull) return true;
       if (conv) i = -1;
       continue;  // nothing left to assign
     }
     if (freem == 0u) continue;  // no lane is free
     __syncwarp();
-    // free lanes take tasks next, next + 1, ... in lane order
+    // free lanes take list positions next, next + 1, ... in lane order
     const int idx = next + __popc(freem & lt);
-    const bool take = conv && idx < s;
-    const unsigned int Cn = take ? sc.cm[idx].x : 0u;
-    unsigned long long start = Cn;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long v = __shfl_up_sync(kFull, start, o);
-      if (lane >= o) start += v;
-    }
-    const unsigned long long base = next > 0 ? (unsigned long long)sc.Rcur[next - 1] : 0ull;
-    if (take) {
-      i = idx;
-      Ci = Cn;
-      Di = sc.D[idx];
-      R = base + start;
-      if (c_le_d) {
-        const unsigned long long lb = util_start(Ci, sc.Uex[idx]);
-        R = lb > R ? lb : R;
-      }
+    const int prev = sc.need[next - 1];  // the last task assigned so far
+    if (conv && idx < q) {
+      i = sc.need[idx];
+      Ci = sc.cm[i].x;
+      Di = sc.D[i];
+      R = (unsigned long long)sc.Rcur[prev] + (sc.Cin[i] - sc.Cin[prev]);
+      const unsigned long long lb = util_start(Ci, sc.Uex[i]);
+      R = lb > R ? lb : R;
       iter = 0;
     } else if (conv) {
       i = -1;
     }
-    next = min(s, next + __popc(freem));
+    next = min(q, next + __popc(freem));
     __syncwarp();
   }
 }
@@ -482,25 +489,48 @@ static __device__ __noinline__ bool warp_rta(const SetSmem& st, const unsigned i
   }
   bool all_ok = true;
   unsigned int errbits = 0u, nt = 0u;
+  const bool verdict_only = early_exit && !R_row;
+  int q = 0;  // verdict only: tasks util_pass leaves undecided
   if (c_le_d) {
-    // exclusive prefix sums of C_j / T_j, chunk by chunk
+    // exclusive prefix sums of C_j / T_j and inclusive ones of C_j, chunk by
+    // chunk; for a verdict, the list of tasks util_pass does not settle
     float carry = 0.0f;
+    unsigned long long ccarry = 0ull;
+    const unsigned int lt = (1u << lane) - 1u;
     for (int c0 = 0; c0 < s; c0 += 32) {
       const int i = c0 + lane;
-      float u = i < s ? (float)sc.cm[i].x / (float)sc.T[i] : 0.0f;
+      const unsigned int C = i < s ? sc.cm[i].x : 0u;
+      float u = i < s ? (float)C / (float)sc.T[i] : 0.0f;
       float incl = u;
+      unsigned long long cin = C;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const float v = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += v;
+        const unsigned long long w = __shfl_up_sync(kFull, cin, o);
+        if (lane >= o) {
+          incl += v;
+          cin += w;
+        }
       }
-      if (i < s) sc.Uex[i] = carry + (incl - u);
+      const float uex = carry + (incl - u);
+      cin += ccarry;
+      if (i < s) {
+        sc.Uex[i] = uex;
+        sc.Cin[i] = cin;
+      }
+      if (verdict_only) {
+        const bool nd = i < s && !util_pass(C, cin - C, uex, sc.D[i]);
+        const unsigned int b = __ballot_sync(kFull, nd);
+        if (nd) sc.need[q + __popc(b & lt)] = (unsigned char)i;
+        q += __popc(b);
+      }
       carry += __shfl_sync(kFull, incl, 31);
+      ccarry = __shfl_sync(kFull, cin, 31);
     }
     __syncwarp();
   }
-  if (early_exit && !R_row) {
-    all_ok = rta_verdict(sc, s, c_le_d, &errbits, nt);
+  if (verdict_only) {
+    all_ok = q == 0 || rta_verdict(sc, q, &errbits, nt);
     errbits = __reduce_or_sync(kFull, errbits);
     if (errbits && lane == 0) atomicOr(err, errbits);
     warp_add_terms(sc.terms, nt);

@@ -82,7 +82,7 @@ __device__ bool serial_rta(const SearchHead& h, SearchThreads& w, unsigned int S
   // deadline (the test stops at the first miss), so R_i >= R_prev + C_i and
   // R_i >= C_i / (1 - U_hp) (util_start): the iteration starts at the larger
   // instead of at the sum of the WCETs (same least fixed point, fewer steps).
-  unsigned long long Rprev = 0;
+  unsigned long long Rprev = 0, chp = 0;
   float ua = 0.0f;  // sum of C_j / T_j over the tasks before i (each at most 1: they met their deadlines)
   for (unsigned int rest = S; rest; rest &= rest - 1u) {
     const int i = __ffs(rest) - 1;
@@ -94,11 +94,15 @@ __device__ bool serial_rta(const SearchHead& h, SearchThreads& w, unsigned int S
     unsigned long long R = Rprev + Ci;
     const unsigned long long lb = util_start(Ci, ua);
     R = lb > R ? lb : R;
-    ua += (float)Ci / (float)h.T[i];
     const unsigned int Di = h.D[i];
+    // a task the utilisation bound settles keeps its start value, at most
+    // its least fixed point, as the next task's lower bound
+    const bool settled = util_pass(Ci, chp, ua, Di);
+    ua += (float)Ci / (float)h.T[i];
+    chp += Ci;
     const unsigned int hp = S & ((1u << i) - 1u);
     int iter = 0;
-    for (;;) {
+    for (; !settled;) {
       if (R > Di) return false;
       // every earlier task met its deadline (C_j <= D_j <= T_j): each term
       // stays below R + T_j < 2^32 and the sum cannot overflow

@@ -128,14 +128,17 @@ def test_one_gpu_warps_and_autotuner(ctx):
 def _hand_terms(s, M, g):
     """Interference terms of the 1G verdict test, by the iteration the warp
     runs: no iteration when a task has C > D or U > 1; otherwise tasks in
-    deadline-monotonic order, lane l starting with task l at C_0 + ... + C_l,
-    every lane stepping once per round (task i's step evaluates i terms); a
-    lane whose task reached its fixed point takes the next unassigned task in
-    lane order, starting at the latest iterate of the task before it plus
-    the WCETs of the tasks assigned up to it in that round; every start is
-    raised to the utilisation bound C_i / (1 - U_hp) as the kernel rounds it
-    (float32, the same operations in the same order); the test stops after
-    the round in which some task passed its deadline."""
+    deadline-monotonic order, and of those only the ones whose response-time
+    upper bound (C_i + sum_{j<i} C_j) / (1 - U_hp) exceeds D_i, as the kernel
+    rounds it (float32, the same operations in the same order).  Lane l
+    starts with the l-th such task i at C_0 + ... + C_i, every lane stepping
+    once per round (task i's step evaluates i terms); a lane whose task
+    reached its fixed point takes the next unassigned one in lane order,
+    starting at the latest iterate of the last task assigned before that
+    round plus the WCETs between the two; every start is raised to the
+    utilisation bound C_i / (1 - U_hp) (float32 as well); the test stops
+    after the round in which some task passed its deadline."""
+    import itertools
     import math
     from fractions import Fraction
     T, D, A, B, ty = (np.asarray(s[k], np.int64) for k in ("T", "D", "A", "B", "type"))
@@ -178,10 +181,24 @@ def _hand_terms(s, M, g):
             return 2 ** 32
         return max(int(b), Ci)
 
-    lane_task = [p if p < n else -1 for p in range(32)]
-    R = [max(sum(C[:p + 1]), util_start(C[p], Uex[p])) if p < n else 0 for p in range(32)]
+    def util_pass(Ci, chp, uhp, Di):
+        u = f32(uhp + f32(2.0 ** -14))
+        if not u < 1:
+            return False
+        x = f32(f32(f32(chp + Ci) / f32(f32(1) - u)) * f32(1 + 2.0 ** -18))
+        return bool(x <= f32(Di))
+
+    # tasks the utilisation bound settles are never iterated; the others are
+    # taken by the lanes in priority order
+    Cin = list(itertools.accumulate(C))
+    need = [p for p in range(n) if not util_pass(C[p], Cin[p] - C[p], Uex[p], Dp[p])]
+    q = len(need)
+    if q == 0:
+        return 0
+    lane_task = [need[l] if l < q else -1 for l in range(32)]
+    R = [max(Cin[i], util_start(C[i], Uex[i])) if i >= 0 else 0 for i in lane_task]
     Rcur = [0] * n
-    nxt, terms = min(n, 32), 0
+    nxt, terms = min(q, 32), 0
     while True:
         miss, conv = False, [False] * 32
         for l in range(32):
@@ -201,34 +218,36 @@ def _hand_terms(s, M, g):
             Rcur[i] = min(R[l], 2**32 - 1)
         if miss:
             return terms
-        if nxt >= n and all(conv):
+        if nxt >= q and all(conv):
             return terms
-        base = Rcur[nxt - 1] if nxt > 0 else 0
-        rank, acc = 0, 0
-        nfree = sum(conv)
+        prev = need[nxt - 1]
+        rank, nfree = 0, sum(conv)
         for l in range(32):
             if not conv[l]:
                 continue
             idx = nxt + rank
             rank += 1
-            if idx < n:
-                acc += C[idx]
-                lane_task[l], R[l] = idx, max(base + acc, util_start(C[idx], Uex[idx]))
+            if idx < q:
+                i = need[idx]
+                lane_task[l], R[l] = i, max(Rcur[prev] + Cin[i] - Cin[prev], util_start(C[i], Uex[i]))
             else:
                 lane_task[l] = -1
-        nxt = min(n, nxt + nfree)
+        nxt = min(q, nxt + nfree)
 
 
 def test_term_counter(ctx):
     """The counter of the 1G kernel equals a hand count of the iteration on
     single sets; it is zero when every set is decided by the fast kernel,
     and the same on a repeated call."""
-    s = gpa.gen_tasksets(**W.gen_params("sweep", nsets=40))
-    for i in (0, 7, 19, 33):
+    s = gpa.gen_tasksets(**W.gen_params("sweep", nsets=120))
+    counts = []
+    for i in (0, 19, 26, 33, 37, 99):
         sub = G.subset(s, np.array([i]))
         ctx.allocate(gpa.to_device(sub), 148, 1, KC, KM, policy="ONE_GPU")
         got = ctx.last_terms()
-        assert got == _hand_terms({k: sub[k] for k in ("T", "D", "A", "B", "type")}, 148, 1), i
+        counts.append(_hand_terms({k: sub[k] for k in ("T", "D", "A", "B", "type")}, 148, 1))
+        assert got == counts[-1], i
+    assert min(counts) == 0 and sum(c > 0 for c in counts) >= 4, counts  # settled and iterated sets both covered
     b = gpa.gen_tasksets(**W.gen_params("batch", nsets=2000))
     ref = oracle.allocate(b, 80, 1, KC, KM, nthreads=8)
     assert (ref["n_tests"] == 0).all()
