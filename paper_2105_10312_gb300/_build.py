@@ -47,6 +47,17 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
+def _included_sources(src):
+    """The .cu files `src` includes (the capacity builds re-include a kernel source)."""
+    out = []
+    with open(src) as fh:
+        for line in fh:
+            line = line.strip()
+            if line.startswith("#include") and line.endswith('.cu"'):
+                out.append(os.path.join(CSRC, line.split('"')[1]))
+    return out
+
+
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
     os.makedirs(OBJ, exist_ok=True)
     nvcc = _nvcc()
@@ -60,7 +71,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             continue
         obj = os.path.join(OBJ, f + ".o")
         objs.append(obj)
-        if force or _stale(obj, [src] + headers):
+        if force or _stale(obj, [src] + _included_sources(src) + headers):
             cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INC, "-I", CSRC,
                    "-c", src, "-o", obj]
             if ptxas_info:

@@ -465,6 +465,55 @@ __device__ __forceinline__ bool rta_verdict(RtaScratch& sc, int q, unsigned int*
   }
 }
 
+// Lists of at most this many undecided tasks are tested one task at a time
+// by the whole warp (rta_verdict_seq), longer ones a task per lane.
+constexpr int kSeqTasksMax = 16;
+
+// Verdict-only response-time test of the q tasks listed in sc.need, one task
+// at a time by the whole warp: in a step of task i, lane l evaluates the
+// terms of tasks l, l + 32, ... below i, and the warp adds them.  Task i
+// starts at the larger of util_start and R_p + C_{p+1} + ... + C_i, p being
+// the listed task before it and R_p its least fixed point (the first at
+// C_0 + ... + C_i).  Returns false as soon as a task passes its deadline (or
+// hits the step limit: *eb |= kErrIter).  Every C_j <= D_j, so the sums need
+// no cap (see warp_rta); a lane's terms each stay below 2^32, at most
+// kNmax / 32 of them, so the halves of its sum below 2^16 and above add up
+// without overflow in 32-bit warp reductions.
+__device__ __forceinline__ bool rta_verdict_seq(const RtaScratch& sc, int q, unsigned int* eb, unsigned int& nt) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long Rp = 0ull, Cp = 0ull;
+  for (int k = 0; k < q; k++) {
+    const int i = sc.need[k];
+    const unsigned int Ci = sc.cm[i].x, Di = sc.D[i];
+    unsigned long long R = Rp + (sc.Cin[i] - Cp);
+    const unsigned long long lb = util_start(Ci, sc.Uex[i]);
+    R = lb > R ? lb : R;
+    int iter = 0;
+    for (;;) {
+      if (R > Di) return false;
+      const unsigned int Rc = (unsigned int)R;
+      unsigned long long part = 0ull;
+      for (int j = lane; j < i; j += 32) {
+        const uint2 v = sc.cm[j];
+        part += (unsigned long long)ceil_div_T(Rc, v.y, sc.sh[j]) * v.x;
+      }
+      const unsigned int lo = __reduce_add_sync(kFull, (unsigned int)(part & 0xFFFFull));
+      const unsigned int hi = __reduce_add_sync(kFull, (unsigned int)(part >> 16));
+      const unsigned long long next = Ci + ((unsigned long long)hi << 16) + lo;
+      if (lane == 0) nt += (unsigned int)i;
+      if (next == R) break;
+      R = next;
+      if (++iter > kIterCap) {
+        *eb |= kErrIter;
+        return false;
+      }
+    }
+    Rp = R;
+    Cp = sc.Cin[i];
+  }
+  return true;
+}
+
 static __device__ __noinline__ bool warp_rta(const SetSmem& st, const unsigned int* S, unsigned int m, unsigned int kc,
                                       unsigned int km, const MagicDiv* __restrict__ mdiv, RtaScratch& sc,
                                       long long* R_row, bool early_exit, unsigned int* err) {
@@ -530,7 +579,7 @@ static __device__ __noinline__ bool warp_rta(const SetSmem& st, const unsigned i
     __syncwarp();
   }
   if (verdict_only) {
-    all_ok = q == 0 || rta_verdict(sc, q, &errbits, nt);
+    all_ok = q == 0 || (q <= kSeqTasksMax ? rta_verdict_seq(sc, q, &errbits, nt) : rta_verdict(sc, q, &errbits, nt));
     errbits = __reduce_or_sync(kFull, errbits);
     if (errbits && lane == 0) atomicOr(err, errbits);
     warp_add_terms(sc.terms, nt);

@@ -15,10 +15,13 @@
 // GPA_MERGE_MINB: CTAs of 256 threads the merge kernel's registers must
 // allow per SM; the 64-task build keeps its state in 128 registers (more
 // sets in flight: paper50 2.7 -> 2.2 ms), the larger builds in up to 255
-// (fewer spills: 200-task sets 126 -> 114 ms).
+// (fewer spills: 200-task sets 126 -> 114 ms).  GPA_ONEGPU_MINB: the same
+// for the 1G kernel (64-task build: 64 registers, 1 000 000 sets 2.43 ->
+// 1.96 ms against no limit).
 #if defined(GPA_WIDE)
 #define GPA_KNMAX 256
 #define GPA_MERGE_MINB 1
+#define GPA_ONEGPU_MINB 1
 #define GPA_NS_BEGIN \
   namespace gpa {    \
   namespace wide {
@@ -28,6 +31,7 @@
 #elif defined(GPA_SMALL)
 #define GPA_KNMAX 64
 #define GPA_MERGE_MINB 2
+#define GPA_ONEGPU_MINB 4
 #define GPA_NS_BEGIN \
   namespace gpa {    \
   namespace small {
@@ -37,6 +41,7 @@
 #else
 #define GPA_KNMAX 128
 #define GPA_MERGE_MINB 1
+#define GPA_ONEGPU_MINB 1
 #define GPA_NS_BEGIN namespace gpa {
 #define GPA_NS_END }
 #endif

@@ -480,13 +480,120 @@ __global__ void __launch_bounds__(256, GPA_MERGE_MINB) alloc_merge(DevSets S, De
 struct OneGpuSmem {
   SetSmem st;
   RtaScratch sc;
+  uint4 rec[kNmax];  // pre-pass: per task D, C and C / T (as float bits)
   unsigned int err;  // error bits of the set being tested
 };
 // the dynamic shared memory opted in by alloc_kernels_init (227 KB per CTA at most)
 static_assert(merge_group_bytes(1) <= 232448, "merge kernel: one group must fit 227 KB");
 static_assert(8 * sizeof(OneGpuSmem) <= 232448, "1G kernel: eight warps must fit 227 KB");
 
-__global__ void __launch_bounds__(256) one_gpu(DevSets S, DevModel md, AllocOut out, unsigned int* err,
+// Outcomes of the 1G pre-pass.
+enum { kPreOpen = 0, kPrePass = 1, kPreMiss = 2, kPreInvalid = 3 };
+
+// 1G pre-pass over set [o, o + n) (warp-cooperative, original task order):
+// decides most sets without the deadline-monotonic staging of stage_set.
+// It validates the tasks (kPreInvalid), computes every WCET at m = M with
+// the conflict factors of the whole set, and returns kPreMiss when a task has
+// C > D or U > 1 (either rules out every policy on one processor), kPrePass
+// when every task's response-time upper bound (see util_pass) is within its
+// deadline, else kPreOpen.  The bound takes as higher-priority tasks every
+// other task whose deadline is at most its own: a superset of its
+// deadline-monotonic predecessors, which only raises the bound.  A set that
+// passes under DM passes under EDF too (EDF meets every deadline that any
+// policy meets on one processor).  Uc, Um: the per-type sums of u; nm: the
+// memory-intensive tasks (every lane).
+//
+// The sums are float: for task t, a = sum of C_j and b = sum of C_j / T_j
+// over the tasks with D_j <= D_t, t included; b then drops t's own term.
+// Each of at most 256 non-negative terms is rounded once (2^-24 relative)
+// and each partial sum once, so a (the bound's numerator C_t + sum C_hp) is
+// within 2^-16 of its true value (relative), and b within 2^-15 of U_hp
+// (b and t's term add up to at most U <= 1 + 2^-13).
+// The bound's quotient uses U_hp + 2^-14 and is raised by 2^-13, which also
+// covers its remaining roundings and that of D_t, so a pass is never wrong.
+__device__ __forceinline__ int one_gpu_prepass(SetSmem& st, uint4* __restrict__ rec, long long o, int n,
+                                               const DevSets& S, const DevModel& md, const MagicDiv& mdM,
+                                               unsigned long long& Uc, unsigned long long& Um, int& nm) {
+  const int lane = threadIdx.x & 31;
+  const int nch = (n + 31) >> 5;  // chunks of 32 tasks
+  bool ok = true;
+  unsigned int mm[kWords];
+  unsigned long long uc = 0ull, um = 0ull;
+#pragma unroll
+  for (int c = 0; c < kWords; c++) {
+    mm[c] = 0u;
+    if (c >= nch) continue;
+    const int t = c * 32 + lane;
+    bool mem = false;
+    if (t < n) {
+      const long long T = __ldg(S.T + o + t), D = __ldg(S.D + o + t), A = __ldg(S.A + o + t),
+                      B = __ldg(S.B + o + t);
+      const long long u = S.u ? __ldg(S.u + o + t) : 0;
+      const unsigned int y = __ldg(S.type + o + t);
+      ok = ok && task_valid(T, D, A, B, u, y);
+      st.T[t] = (unsigned int)T;
+      st.D[t] = (unsigned int)D;
+      st.A[t] = (unsigned long long)A;
+      st.B[t] = (unsigned long long)B;
+      mem = y == 1u;
+      (mem ? um : uc) += (unsigned long long)(unsigned int)u;
+    }
+    mm[c] = __ballot_sync(kFull, mem);
+  }
+  if (!__all_sync(kFull, ok)) return kPreInvalid;
+  // a lane's sum of at most kNmax / 32 values below 2^32: its halves below
+  // and above 2^16 add up in 32-bit warp reductions
+  Uc = ((unsigned long long)__reduce_add_sync(kFull, (unsigned int)(uc >> 16)) << 16) +
+       __reduce_add_sync(kFull, (unsigned int)(uc & 0xFFFFull));
+  Um = ((unsigned long long)__reduce_add_sync(kFull, (unsigned int)(um >> 16)) << 16) +
+       __reduce_add_sync(kFull, (unsigned int)(um & 0xFFFFull));
+  nm = 0;
+#pragma unroll
+  for (int c = 0; c < kWords; c++) nm += __popc(mm[c]);
+  const unsigned int kmem = nm >= 2 ? (unsigned int)md.km : 1000u;
+  const unsigned int kcmp = (n - nm) >= 2 ? (unsigned int)md.kc : 1000u;
+  bool c_le_d = true;
+  float uf = 0.0f;
+#pragma unroll
+  for (int c = 0; c < kWords; c++) {
+    const int t = c * 32 + lane;
+    if (c < nch && t < n) {
+      const unsigned int T = st.T[t], D = st.D[t];
+      const unsigned int C = wcet(st.A[t], st.B[t], ((mm[c] >> lane) & 1u) ? kmem : kcmp, (unsigned int)md.M, mdM);
+      const float f = (float)C / (float)T;
+      c_le_d = c_le_d && C <= D;
+      uf += f;
+      rec[t] = make_uint4(D, __float_as_uint((float)C), __float_as_uint(f), 0u);
+    }
+  }
+  if (!__all_sync(kFull, c_le_d)) return kPreMiss;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) uf += __shfl_xor_sync(kFull, uf, d);
+  if (uf > kUtilFail) return kPreMiss;
+  __syncwarp();
+  bool pass = true;
+  for (int c = 0; c < nch; c++) {
+    const int t = c * 32 + lane;
+    const uint4 own = t < n ? rec[t] : make_uint4(0u, 0u, 0u, 0u);
+    float a = 0.0f, b = 0.0f;
+#pragma unroll 4
+    for (int j = 0; j < n; j++) {
+      const uint4 r = rec[j];
+      if (r.x <= own.x) {
+        a += __uint_as_float(r.y);
+        b += __uint_as_float(r.z);
+      }
+    }
+    if (t < n) {
+      // a already holds C_t + sum C_j, the bound's numerator
+      const float u = (b - __uint_as_float(own.z)) + 0x1p-14f;
+      pass = pass && u < 1.0f && a / (1.0f - u) * (1.0f + 0x1p-13f) <= (float)own.x;
+    }
+  }
+  return __all_sync(kFull, pass) ? kPrePass : kPreOpen;
+}
+
+__global__ void __launch_bounds__(256, GPA_ONEGPU_MINB) one_gpu(DevSets S, DevModel md, AllocOut out, unsigned int* err,
                                                const MagicDiv* __restrict__ mdiv, unsigned long long* ticket) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -504,31 +611,31 @@ __global__ void __launch_bounds__(256) one_gpu(DevSets S, DevModel md, AllocOut 
       write_invalid((long long)s, o, slice_inside(o, n, ntasks) ? n : 0, out, err);
       continue;
     }
-    if (!stage_set(sm.st, o, (int)n, S.T, S.D, S.A, S.B, S.u, S.type)) {
+    unsigned long long Uc = 0, Um = 0;
+    int nm = 0;
+    const int pre = one_gpu_prepass(sm.st, sm.rec, o, (int)n, S, md, mdiv[md.M], Uc, Um, nm);
+    if (pre == kPreInvalid) {
       write_invalid((long long)s, o, n, out, err);
       continue;
     }
-    unsigned int all[kWords];
-#pragma unroll
-    for (int w = 0; w < kWords; w++) {
-      int lo = w * 32;
-      all[w] = n >= lo + 32 ? kFull : (n > lo ? ((1u << (n - lo)) - 1u) : 0u);
-    }
     if (lane == 0) sm.err = 0u;
-    __syncwarp();
-    bool ok = n == 0 ? true
-                     : warp_test(sm.st, all, (unsigned)md.M, md.kc, md.km, md.sched, mdiv, sm.sc, nullptr, true,
-                                 &sm.err);
-    unsigned long long Uc = 0, Um = 0;
-    int nm = 0;
-    for (int r = lane; r < n; r += 32) {
-      const bool mem = (sm.st.memmask[r >> 5] >> (r & 31)) & 1u;
-      (mem ? Um : Uc) += sm.st.u[r];
-      nm += mem;
+    bool ok = pre == kPrePass;
+    if (pre == kPreOpen) {
+      // the full test: deadline-monotonic staging and the iteration
+      __syncwarp();
+      if (!stage_set(sm.st, o, (int)n, S.T, S.D, S.A, S.B, S.u, S.type)) {
+        write_invalid((long long)s, o, n, out, err);
+        continue;
+      }
+      unsigned int all[kWords];
+#pragma unroll
+      for (int w = 0; w < kWords; w++) {
+        int lo = w * 32;
+        all[w] = n >= lo + 32 ? kFull : (n > lo ? ((1u << (n - lo)) - 1u) : 0u);
+      }
+      __syncwarp();
+      ok = warp_test(sm.st, all, (unsigned)md.M, md.kc, md.km, md.sched, mdiv, sm.sc, nullptr, true, &sm.err);
     }
-    Uc = warp_sum_u64(Uc);
-    Um = warp_sum_u64(Um);
-    nm = warp_sum_i32(nm);
     for (long long t = lane; t < n; t += 32) {
       out.part_of_task[o + t] = 0;
       out.size_of_part[o + t] = (t == 0) ? (short)md.M : (short)0;

@@ -127,10 +127,14 @@ def test_one_gpu_warps_and_autotuner(ctx):
 
 def _hand_terms(s, M, g):
     """Interference terms of the 1G verdict test, by the iteration the warp
-    runs: no iteration when a task has C > D or U > 1; otherwise tasks in
-    deadline-monotonic order, and of those only the ones whose response-time
-    upper bound (C_i + sum_{j<i} C_j) / (1 - U_hp) exceeds D_i, as the kernel
-    rounds it (float32, the same operations in the same order).  Lane l
+    runs: no iteration when a task has C > D or U > 1, or when the kernel's
+    pre-pass settles every task by its response-time upper bound (below);
+    otherwise tasks in deadline-monotonic order, and of those only the ones
+    whose response-time upper bound (C_i + sum_{j<i} C_j) / (1 - U_hp)
+    exceeds D_i, as the kernel rounds it (float32, the same operations in
+    the same order).  Up to 16 such tasks are iterated one after another,
+    each from the previous one's fixed point plus the WCETs between them
+    (task i's step evaluates i terms).  For longer lists, lane l
     starts with the l-th such task i at C_0 + ... + C_i, every lane stepping
     once per round (task i's step evaluates i terms); a lane whose task
     reached its fixed point takes the next unassigned one in lane order,
@@ -154,9 +158,34 @@ def _hand_terms(s, M, g):
     assert abs(U - 1) > Fraction(1, 4096), "too close to 1 for a float-order-free count"
     if any(C[p] > Dp[p] for p in range(n)) or U > 1:
         return 0
+    f32 = np.float32
+
+    def util_pass(Ci, chp, uhp, Di):
+        u = f32(uhp + f32(2.0 ** -14))
+        if not u < 1:
+            return False
+        x = f32(f32(f32(chp + Ci) / f32(f32(1) - u)) * f32(1 + 2.0 ** -18))
+        return bool(x <= f32(Di))
+
+    # the kernel's pre-pass: in the original task order, each task's bound
+    # with every task whose deadline is at most its own (itself included) as
+    # higher priority, float32 sums in index order (its own C / T taken out
+    # of the utilisation); all within their deadlines: no iteration
+    Tr, Dr = [int(x) for x in T], [int(x) for x in D]
+    fr = [f32(f32(Cr[i]) / f32(Tr[i])) for i in range(n)]
+    settled = True
+    for i in range(n):
+        a, b = f32(0), f32(0)
+        for j in range(n):
+            if Dr[j] <= Dr[i]:
+                a = f32(a + f32(Cr[j]))
+                b = f32(b + fr[j])
+        u = f32(f32(b - fr[i]) + f32(2.0 ** -14))
+        settled = settled and bool(u < 1) and bool(f32(f32(a / f32(f32(1) - u)) * f32(1 + 2.0 ** -13)) <= f32(Dr[i]))
+    if settled:
+        return 0
     # float sums of C_j / T_j before each task, as the warp forms them:
     # chunks of 32, an inclusive Hillis-Steele scan per chunk plus a carry
-    f32 = np.float32
     Uex, carry = [f32(0)] * n, f32(0)
     for c0 in range(0, n, 32):
         u = np.array([f32(C[p]) / f32(Tp[p]) if p < n else f32(0) for p in range(c0, c0 + 32)], np.float32)
@@ -181,13 +210,6 @@ def _hand_terms(s, M, g):
             return 2 ** 32
         return max(int(b), Ci)
 
-    def util_pass(Ci, chp, uhp, Di):
-        u = f32(uhp + f32(2.0 ** -14))
-        if not u < 1:
-            return False
-        x = f32(f32(f32(chp + Ci) / f32(f32(1) - u)) * f32(1 + 2.0 ** -18))
-        return bool(x <= f32(Di))
-
     # tasks the utilisation bound settles are never iterated; the others are
     # taken by the lanes in priority order
     Cin = list(itertools.accumulate(C))
@@ -195,6 +217,22 @@ def _hand_terms(s, M, g):
     q = len(need)
     if q == 0:
         return 0
+    if q <= 16:
+        # short lists: one task at a time by the whole warp, each starting at
+        # the previous listed task's fixed point plus the WCETs between them
+        Rp, Cp, terms = 0, 0, 0
+        for i in need:
+            R = max(Rp + Cin[i] - Cp, util_start(C[i], Uex[i]))
+            while True:
+                if R > Dp[i]:
+                    return terms
+                terms += i
+                step = C[i] + sum(math.ceil(R / Tp[j]) * C[j] for j in range(i))
+                if step == R:
+                    break
+                R = step
+            Rp, Cp = R, Cin[i]
+        return terms
     lane_task = [need[l] if l < q else -1 for l in range(32)]
     R = [max(Cin[i], util_start(C[i], Uex[i])) if i >= 0 else 0 for i in lane_task]
     Rcur = [0] * n
