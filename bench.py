@@ -103,7 +103,8 @@ def kernel_source_hash(kernel="alloc_fast"):
 
 # the committed ncu summary of each workload's kernels
 PROFILES = {("alloc_fast", "batch"): "alloc_fast_batch.md", ("alloc_merge", "paper50"): "alloc_merge_paper50.md",
-            ("one_gpu", "sweep"): "one_gpu_sweep.md", ("search_sets", "exhaustive"): "search_sets_exhaustive.md",
+            ("one_gpu", "sweep"): "one_gpu_sweep.md", ("one_gpu_fast", "sweep"): "one_gpu_fast_sweep.md",
+            ("search_sets", "exhaustive"): "search_sets_exhaustive.md",
             ("alloc_fast", "sweep"): "alloc_fast_sweep.md"}
 
 
@@ -624,7 +625,7 @@ def measure(bench, name, rank, world, steps, warmup, with_cpu=True, e2e_steps=5,
     cand_total = shard.sum_over_ranks(cand)
 
     # per-kernel times and rooflines
-    names = {"SMS": ("alloc_fast", "alloc_merge"), "ONE_GPU": ("one_gpu",), "SEARCH": ("search_sets",),
+    names = {"SMS": ("alloc_fast", "alloc_merge"), "ONE_GPU": ("one_gpu_fast", "one_gpu"), "SEARCH": ("search_sets",),
              "EXPLICIT": ("search_explicit",)}
     kernels = []
     for j, call in enumerate(calls):
@@ -635,7 +636,8 @@ def measure(bench, name, rank, world, steps, warmup, with_cpu=True, e2e_steps=5,
                 continue
             kms = float(np.mean(ts))
             rec = {"kernel": kname, "kernel_ms": kms}
-            if kname == "alloc_fast":
+            if kname in ("alloc_fast", "one_gpu_fast"):
+                # both stream every set once (the heuristic's Lemma 2 pass, the 1G pre-pass)
                 # per task: T, D, A, B, u (5 x 8 B) + type (1 B) read; part (1 B) + size (2 B) written;
                 # per set: offset (8 B) read; verdict, reason, n_parts, Pi, W, n_tests (22 B) written
                 alg = 44 * ntasks + 30 * nsets
@@ -662,7 +664,7 @@ def measure(bench, name, rank, world, steps, warmup, with_cpu=True, e2e_steps=5,
     if roof:
         roof["kernel_timing"] = ("CUDA events recorded by the library around each kernel (inside its graphs), "
                                  "a second pass of the same K flushed steps")
-        if roof["kernel"] == "alloc_fast":
+        if roof["kernel"] in ("alloc_fast", "one_gpu_fast"):
             roof["size_floor"] = bench.read_floor(44 * ntasks + 8 * nsets, roof["kernel_ms"])
 
     # outcome summaries the configurations ask for (untimed)

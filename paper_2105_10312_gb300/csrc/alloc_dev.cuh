@@ -283,11 +283,14 @@ __device__ bool lane_rta(const SetSmem& st, const unsigned int* S, unsigned int 
       }
       // every earlier task met its deadline, so C_q <= D_q <= T_q and each
       // term stays below R + T_q < 2^32: the sum cannot overflow
-      unsigned long long next = Ci;
+      // ceil(R / T_q) = floor((R - 1) / T_q) + 1: C_i and the +1 terms add up to
+      // chp, which already holds C_i here
+      unsigned long long next = chp;
       nt += (unsigned int)pos;
+      const unsigned int R2 = 2u * ((unsigned int)R - 1u);
       for (int q = 0; q < pos; q++) {
         const uint2 v = ls.cm[q][lane];
-        next += (unsigned long long)ceil_div_T((unsigned int)R, v.y, ls.sh[q][lane]) * v.x;
+        next += (unsigned long long)floor_div_T2(R2, v.y, ls.sh[q][lane]) * v.x;
       }
       if (next == R) break;
       R = next;

@@ -43,18 +43,24 @@ __device__ __forceinline__ unsigned long long div_by_1e6m(unsigned long long x, 
 }
 
 // 32-bit divisor T (1 <= T < 2^31), dividend n < 2^31:
-// magic = ceil(2^(31+l) / T) < 2^32 with l = ceil(log2 T);
-// floor(n / T) = (n * magic) >> (31 + l).
+// magic = ceil(2^(31+l) / T) < 2^32 with l = ceil(log2 T), shift = l;
+// floor(n / T) = floor(n magic / 2^(31+l)) = floor(2n magic / 2^(32+l)): the
+// high word of the 32 x 32-bit product (2n) magic, shifted right by l.
 __device__ __forceinline__ void magic_for_period(unsigned int T, unsigned int* magic, unsigned int* shift) {
   unsigned int l = (T <= 1u) ? 0u : 32u - __clz(T - 1u);
   unsigned long long num = (1ull << (31 + l)) + T - 1;
   *magic = (unsigned int)(num / T);
-  *shift = 31u + l;
+  *shift = l;
 }
 
-// ceil(R / T) for 1 <= R < 2^31 as floor((R - 1) / T) + 1.
+// floor(n / T) from n2 = 2n (n < 2^31) and T's reciprocal.
+__device__ __forceinline__ unsigned int floor_div_T2(unsigned int n2, unsigned int magic, unsigned int shift) {
+  return __umulhi(n2, magic) >> shift;
+}
+
+// ceil(R / T) for 1 <= R <= 2^31 as floor((R - 1) / T) + 1.
 __device__ __forceinline__ unsigned int ceil_div_T(unsigned int R, unsigned int magic, unsigned int shift) {
-  return (unsigned int)(((unsigned long long)(R - 1u) * magic) >> shift) + 1u;
+  return floor_div_T2(2u * (R - 1u), magic, shift) + 1u;
 }
 
 // WCET at m SMs with factor k per mille: ceil(k (A + B m) / (10^6 m)).
@@ -371,17 +377,21 @@ constexpr float kUtilFail = 1.0f + 0x1p-13f;
 
 // One step of task i's response-time iteration: next = C_i + sum_{j<i}
 // ceil(R / T_j) C_j over the compacted tasks (uncapped when every C_j <= D_j,
-// see warp_rta).
+// see warp_rta).  Uncapped, ceil(R / T_j) = floor((R - 1) / T_j) + 1 and the
+// +1 terms add up to C_0 + ... + C_{i-1}: next = Cin[i] + sum floor(...) C_j.
 __device__ __forceinline__ unsigned long long rta_step(const RtaScratch& sc, int i, unsigned long long R,
                                                       unsigned int Ci, unsigned int Di, bool c_le_d) {
   const unsigned int Rc = (unsigned int)R;
-  unsigned long long next = Ci;
+  unsigned long long next;
   if (c_le_d) {
+    next = sc.Cin[i];
+    const unsigned int R2 = 2u * (Rc - 1u);
     for (int j = 0; j < i; j++) {
       const uint2 v = sc.cm[j];  // one 8-byte broadcast load: C_j and T_j's reciprocal
-      next += (unsigned long long)ceil_div_T(Rc, v.y, sc.sh[j]) * v.x;
+      next += (unsigned long long)floor_div_T2(R2, v.y, sc.sh[j]) * v.x;
     }
   } else {
+    next = Ci;
     // terms capped at D_i + 1: a capped term already puts the sum above D_i
     const unsigned long long cap = (unsigned long long)Di + 1ull;
     for (int j = 0; j < i; j++) {
@@ -489,17 +499,19 @@ __device__ __forceinline__ bool rta_verdict_seq(const RtaScratch& sc, int q, uns
     const unsigned long long lb = util_start(Ci, sc.Uex[i]);
     R = lb > R ? lb : R;
     int iter = 0;
+    const unsigned long long Cin = sc.Cin[i];
     for (;;) {
       if (R > Di) return false;
-      const unsigned int Rc = (unsigned int)R;
+      // next = C_0 + ... + C_i + sum_{j<i} floor((R - 1) / T_j) C_j (see rta_step)
+      const unsigned int R2 = 2u * ((unsigned int)R - 1u);
       unsigned long long part = 0ull;
       for (int j = lane; j < i; j += 32) {
         const uint2 v = sc.cm[j];
-        part += (unsigned long long)ceil_div_T(Rc, v.y, sc.sh[j]) * v.x;
+        part += (unsigned long long)floor_div_T2(R2, v.y, sc.sh[j]) * v.x;
       }
       const unsigned int lo = __reduce_add_sync(kFull, (unsigned int)(part & 0xFFFFull));
       const unsigned int hi = __reduce_add_sync(kFull, (unsigned int)(part >> 16));
-      const unsigned long long next = Ci + ((unsigned long long)hi << 16) + lo;
+      const unsigned long long next = Cin + ((unsigned long long)hi << 16) + lo;
       if (lane == 0) nt += (unsigned int)i;
       if (next == R) break;
       R = next;

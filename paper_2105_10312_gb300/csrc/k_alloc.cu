@@ -480,12 +480,20 @@ __global__ void __launch_bounds__(256, GPA_MERGE_MINB) alloc_merge(DevSets S, De
 struct OneGpuSmem {
   SetSmem st;
   RtaScratch sc;
-  uint4 rec[kNmax];  // pre-pass: per task D, C and C / T (as float bits)
   unsigned int err;  // error bits of the set being tested
+};
+
+// Per-warp scratch of the 1G pre-pass: the set's columns in original order
+// and, per task, D, C and C / T (as float bits).
+struct PreSmem {
+  unsigned long long A[kNmax], B[kNmax];
+  unsigned int T[kNmax], D[kNmax];
+  uint4 rec[kNmax];
 };
 // the dynamic shared memory opted in by alloc_kernels_init (227 KB per CTA at most)
 static_assert(merge_group_bytes(1) <= 232448, "merge kernel: one group must fit 227 KB");
 static_assert(8 * sizeof(OneGpuSmem) <= 232448, "1G kernel: eight warps must fit 227 KB");
+static_assert(8 * sizeof(PreSmem) <= 232448, "1G pre-pass kernel: eight warps must fit 227 KB");
 
 // Outcomes of the 1G pre-pass.
 enum { kPreOpen = 0, kPrePass = 1, kPreMiss = 2, kPreInvalid = 3 };
@@ -495,8 +503,8 @@ enum { kPreOpen = 0, kPrePass = 1, kPreMiss = 2, kPreInvalid = 3 };
 // It validates the tasks (kPreInvalid), computes every WCET at m = M with
 // the conflict factors of the whole set, and returns kPreMiss when a task has
 // C > D or U > 1 (either rules out every policy on one processor), kPrePass
-// when every task's response-time upper bound (see util_pass) is within its
-// deadline, else kPreOpen.  The bound takes as higher-priority tasks every
+// when the hyperbolic bound holds or every task's response-time upper bound
+// (see util_pass) is within its deadline, else kPreOpen.  The bound takes as higher-priority tasks every
 // other task whose deadline is at most its own: a superset of its
 // deadline-monotonic predecessors, which only raises the bound.  A set that
 // passes under DM passes under EDF too (EDF meets every deadline that any
@@ -505,15 +513,18 @@ enum { kPreOpen = 0, kPrePass = 1, kPreMiss = 2, kPreInvalid = 3 };
 //
 // The sums are float: for task t, a = sum of C_j and b = sum of C_j / T_j
 // over the tasks with D_j <= D_t, t included; b then drops t's own term.
-// Each of at most 256 non-negative terms is rounded once (2^-24 relative)
-// and each partial sum once, so a (the bound's numerator C_t + sum C_hp) is
-// within 2^-16 of its true value (relative), and b within 2^-15 of U_hp
-// (b and t's term add up to at most U <= 1 + 2^-13).
+// Each of at most 256 non-negative terms is within 2^-22 of its value
+// (relative: the conversion of C_j rounds once, the quotients C_j / T_j come
+// from __fdividef, at most 2 ulp) and each partial sum is rounded once
+// (2^-24), so a (the bound's numerator C_t + sum C_hp) is within 2^-16 of its
+// true value (relative), and b within 2^-15 of U_hp (b and t's term add up
+// to at most U <= 1 + 2^-13).
 // The bound's quotient uses U_hp + 2^-14 and is raised by 2^-13, which also
 // covers its remaining roundings and that of D_t, so a pass is never wrong.
-__device__ __forceinline__ int one_gpu_prepass(SetSmem& st, uint4* __restrict__ rec, long long o, int n,
-                                               const DevSets& S, const DevModel& md, const MagicDiv& mdM,
-                                               unsigned long long& Uc, unsigned long long& Um, int& nm) {
+__device__ __forceinline__ int one_gpu_prepass(PreSmem& st, long long o, int n, const DevSets& S,
+                                               const DevModel& md, const MagicDiv& mdM, unsigned long long& Uc,
+                                               unsigned long long& Um, int& nm) {
+  uint4* __restrict__ rec = st.rec;
   const int lane = threadIdx.x & 31;
   const int nch = (n + 31) >> 5;  // chunks of 32 tasks
   bool ok = true;
@@ -553,23 +564,39 @@ __device__ __forceinline__ int one_gpu_prepass(SetSmem& st, uint4* __restrict__ 
   const unsigned int kmem = nm >= 2 ? (unsigned int)md.km : 1000u;
   const unsigned int kcmp = (n - nm) >= 2 ? (unsigned int)md.kc : 1000u;
   bool c_le_d = true;
-  float uf = 0.0f;
+  float uf = 0.0f, hyp = 1.0f;
 #pragma unroll
   for (int c = 0; c < kWords; c++) {
     const int t = c * 32 + lane;
     if (c < nch && t < n) {
       const unsigned int T = st.T[t], D = st.D[t];
       const unsigned int C = wcet(st.A[t], st.B[t], ((mm[c] >> lane) & 1u) ? kmem : kcmp, (unsigned int)md.M, mdM);
-      const float f = (float)C / (float)T;
+      const float f = __fdividef((float)C, (float)T);
       c_le_d = c_le_d && C <= D;
       uf += f;
+      hyp *= 1.0f + __fdividef((float)C, (float)D);
       rec[t] = make_uint4(D, __float_as_uint((float)C), __float_as_uint(f), 0u);
     }
   }
   if (!__all_sync(kFull, c_le_d)) return kPreMiss;
 #pragma unroll
-  for (int d = 16; d > 0; d >>= 1) uf += __shfl_xor_sync(kFull, uf, d);
+  for (int d = 16; d > 0; d >>= 1) {
+    uf += __shfl_xor_sync(kFull, uf, d);
+    hyp *= __shfl_xor_sync(kFull, hyp, d);
+  }
   if (uf > kUtilFail) return kPreMiss;
+  // The hyperbolic bound (Bini, Buttazzo & Buttazzo, 2003): implicit-deadline
+  // tasks with prod (1 + C_i / T_i) <= 2 meet every deadline under
+  // rate-monotonic priorities.  Here the periods are taken as D_i: each term
+  // ceil(t / T_j) C_j of the response-time iteration is at most
+  // ceil(t / D_j) C_j, so every response time is at most that of the set
+  // with periods D_i, where deadline-monotonic order is rate-monotonic order.
+  // Each of the at most 256 factors 1 + C_i / D_i is within 2^-22 of its
+  // value (the quotient from __fdividef, at most 2 ulp, and one rounding)
+  // and each product is rounded once (2^-24), so the float product is
+  // within 2^-14 of the true one (relative): at most 2 (1 - 2^-13) proves
+  // the true one <= 2.
+  if (hyp <= 2.0f * (1.0f - 0x1p-13f)) return kPrePass;
   __syncwarp();
   bool pass = true;
   for (int c = 0; c < nch; c++) {
@@ -593,49 +620,35 @@ __device__ __forceinline__ int one_gpu_prepass(SetSmem& st, uint4* __restrict__ 
   return __all_sync(kFull, pass) ? kPrePass : kPreOpen;
 }
 
-__global__ void __launch_bounds__(256, GPA_ONEGPU_MINB) one_gpu(DevSets S, DevModel md, AllocOut out, unsigned int* err,
-                                               const MagicDiv* __restrict__ mdiv, unsigned long long* ticket) {
+// 1G, first kernel: one warp per set, grid-stride.  The pre-pass decides a
+// set (outputs written here), or the set goes to the deferred queue: the
+// ones it leaves open, and the malformed ones, which the second kernel
+// validates.  The second kernel may be scheduled as this grid drains.
+__global__ void __launch_bounds__(256) one_gpu_fast(DevSets S, DevModel md, AllocOut out, AllocQueue q,
+                                                    const MagicDiv* __restrict__ mdiv) {
+  asm volatile("griddepcontrol.launch_dependents;");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  OneGpuSmem& sm = reinterpret_cast<OneGpuSmem*>(smem_raw)[warp];
-  if (lane == 0) sm.sc.terms = 0ull;
-  const long long ntasks = S.set_off[S.nsets];
-  for (;;) {
-    unsigned long long s = 0;
-    if (lane == 0) s = atomicAdd(ticket, 1ull);
-    s = __shfl_sync(kFull, s, 0);
-    if ((long long)s >= S.nsets) break;
-    const long long o = S.set_off[s];
-    const long long n = S.set_off[s + 1] - o;
-    if (n < 0 || n > S.n_max || n > kNmax || !slice_inside(o, n, ntasks)) {
-      write_invalid((long long)s, o, slice_inside(o, n, ntasks) ? n : 0, out, err);
-      continue;
-    }
+  PreSmem& ps = reinterpret_cast<PreSmem*>(smem_raw)[warp];
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long ntasks = __ldg(S.set_off + S.nsets);
+  const MagicDiv mdM = mdiv[md.M];
+  long long s = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  // lanes 0 and 1 hold the offsets of the warp's next set
+  long long offv = (s < S.nsets && lane < 2) ? __ldg(S.set_off + s + lane) : 0;
+  for (; s < S.nsets; s += nw) {
+    const long long o = __shfl_sync(kFull, offv, 0), n = __shfl_sync(kFull, offv, 1) - o;
+    if (s + nw < S.nsets && lane < 2) offv = __ldg(S.set_off + s + nw + lane);
+    int pre = kPreInvalid, nm = 0;
     unsigned long long Uc = 0, Um = 0;
-    int nm = 0;
-    const int pre = one_gpu_prepass(sm.st, sm.rec, o, (int)n, S, md, mdiv[md.M], Uc, Um, nm);
-    if (pre == kPreInvalid) {
-      write_invalid((long long)s, o, n, out, err);
+    if (n >= 0 && n <= S.n_max && n <= kNmax && slice_inside(o, n, ntasks))
+      pre = one_gpu_prepass(ps, o, (int)n, S, md, mdM, Uc, Um, nm);
+    if (pre == kPreOpen || pre == kPreInvalid) {
+      if (lane == 0) q.slow_sets[atomicAdd(q.counters + 1, 1ull)] = s;
+      __syncwarp();
       continue;
     }
-    if (lane == 0) sm.err = 0u;
-    bool ok = pre == kPrePass;
-    if (pre == kPreOpen) {
-      // the full test: deadline-monotonic staging and the iteration
-      __syncwarp();
-      if (!stage_set(sm.st, o, (int)n, S.T, S.D, S.A, S.B, S.u, S.type)) {
-        write_invalid((long long)s, o, n, out, err);
-        continue;
-      }
-      unsigned int all[kWords];
-#pragma unroll
-      for (int w = 0; w < kWords; w++) {
-        int lo = w * 32;
-        all[w] = n >= lo + 32 ? kFull : (n > lo ? ((1u << (n - lo)) - 1u) : 0u);
-      }
-      __syncwarp();
-      ok = warp_test(sm.st, all, (unsigned)md.M, md.kc, md.km, md.sched, mdiv, sm.sc, nullptr, true, &sm.err);
-    }
+    const bool ok = pre == kPrePass;
     for (long long t = lane; t < n; t += 32) {
       out.part_of_task[o + t] = 0;
       out.size_of_part[o + t] = (t == 0) ? (short)md.M : (short)0;
@@ -649,10 +662,75 @@ __global__ void __launch_bounds__(256, GPA_ONEGPU_MINB) one_gpu(DevSets S, DevMo
       if (out.n_tests) out.n_tests[s] = 1;
     }
     __syncwarp();
-    finish_set_errors((long long)s, sm.err, out, err);
+  }
+}
+
+// 1G, second kernel: the deferred sets, one warp per set from a ticket
+// queue: validation, deadline-monotonic staging and the per-partition test
+// of all tasks at m = M.
+__global__ void __launch_bounds__(256, GPA_ONEGPU_MINB) one_gpu(DevSets S, DevModel md, AllocOut out, AllocQueue q,
+                                                                const MagicDiv* __restrict__ mdiv) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  OneGpuSmem& sm = reinterpret_cast<OneGpuSmem*>(smem_raw)[warp];
+  if (lane == 0) sm.sc.terms = 0ull;
+  asm volatile("griddepcontrol.wait;" ::: "memory");  // the first grid has finished and its writes are visible
+  const unsigned long long nslow = *(volatile unsigned long long*)(q.counters + 1);
+  const long long ntasks = S.set_off[S.nsets];
+  for (;;) {
+    unsigned long long i = 0;
+    if (lane == 0) i = atomicAdd(q.counters + 2, 1ull);
+    i = __shfl_sync(kFull, i, 0);
+    if (i >= nslow) break;
+    const long long s = q.slow_sets[i];
+    const long long o = S.set_off[s];
+    const long long n = S.set_off[s + 1] - o;
+    if (n < 0 || n > S.n_max || n > kNmax || !slice_inside(o, n, ntasks)) {
+      write_invalid(s, o, slice_inside(o, n, ntasks) ? n : 0, out, q.err);
+      continue;
+    }
+    if (!stage_set(sm.st, o, (int)n, S.T, S.D, S.A, S.B, S.u, S.type)) {
+      write_invalid(s, o, n, out, q.err);
+      continue;
+    }
+    unsigned int all[kWords];
+#pragma unroll
+    for (int w = 0; w < kWords; w++) {
+      int lo = w * 32;
+      all[w] = n >= lo + 32 ? kFull : (n > lo ? ((1u << (n - lo)) - 1u) : 0u);
+    }
+    if (lane == 0) sm.err = 0u;
+    __syncwarp();
+    const bool ok = n == 0 ? true
+                           : warp_test(sm.st, all, (unsigned)md.M, md.kc, md.km, md.sched, mdiv, sm.sc, nullptr,
+                                       true, &sm.err);
+    unsigned long long Uc = 0, Um = 0;
+    int nm = 0;
+    for (int r = lane; r < n; r += 32) {
+      const bool mem = (sm.st.memmask[r >> 5] >> (r & 31)) & 1u;
+      (mem ? Um : Uc) += sm.st.u[r];
+      nm += mem;
+    }
+    Uc = warp_sum_u64(Uc);
+    Um = warp_sum_u64(Um);
+    nm = warp_sum_i32(nm);
+    for (long long t = lane; t < n; t += 32) {
+      out.part_of_task[o + t] = 0;
+      out.size_of_part[o + t] = (t == 0) ? (short)md.M : (short)0;
+    }
+    if (lane == 0) {
+      out.verdict[s] = ok ? 1 : 0;
+      out.reason[s] = ok ? GPA_REASON_OK : GPA_REASON_TEST;
+      out.n_parts[s] = n > 0 ? 1 : 0;
+      out.Pi[s] = n > 0 ? md.M : 0;
+      out.W[s] = (long long)workload_from_sums(Uc, Um, (int)n - nm, nm, md.kc, md.km);
+      if (out.n_tests) out.n_tests[s] = 1;
+    }
+    __syncwarp();
+    finish_set_errors(s, sm.err, out, q.err);
   }
   __syncwarp();
-  if (lane == 0 && sm.sc.terms) atomicAdd(ticket + 1, sm.sc.terms);  // the context's term counter follows the ticket
+  if (lane == 0 && sm.sc.terms) atomicAdd(q.counters + 4, sm.sc.terms);
 }
 
 }  // namespace
@@ -776,16 +854,39 @@ cudaError_t launch_allocate(const DevSets& s, const DevModel& md, const gpa_para
 cudaError_t launch_one_gpu(const DevSets& s, const DevModel& md, const AllocOut& out, const AllocQueue& q,
                            const MagicDivHost* mdiv, const LaunchShape& shape, cudaStream_t st, long long* launches,
                            Prof* prof) {
-  unsigned long long* ticket = q.counters + 3;  // followed by the interference-term counter
-  unsigned int* err = q.err;
-  cudaError_t e = cudaMemsetAsync(ticket, 0, 2 * sizeof(unsigned long long), st);
+  // tickets, deferred count and the interference-term counter start at zero
+  cudaError_t e = cudaMemsetAsync(q.counters, 0, 5 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
   prof_mark(prof, st);
-  one_gpu<<<shape.blocks, shape.warps_per_block * 32, one_gpu_smem_bytes(shape.warps_per_block), st>>>(
-      s, md, out, err, reinterpret_cast<const MagicDiv*>(mdiv), ticket);
+  // first kernel: as many eight-warp CTAs as fit on every SM at once
+  const size_t fsmem = sizeof(PreSmem) * 8;
+  int per_sm = 0, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, one_gpu_fast, 256, fsmem);
+  const long long want = (long long)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1) * 8;  // warps
+  const long long fblocks = (std::min(want, s.nsets > 0 ? s.nsets : 1) + 7) / 8;
+  one_gpu_fast<<<(unsigned)fblocks, 256, fsmem, st>>>(s, md, out, q, reinterpret_cast<const MagicDiv*>(mdiv));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  prof_mark(prof, st);
+  // second kernel: programmatic dependent launch (it waits for the first
+  // grid's completion and memory before it reads the queue)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)shape.blocks);
+  cfg.blockDim = dim3((unsigned)(shape.warps_per_block * 32));
+  cfg.dynamicSmemBytes = one_gpu_smem_bytes(shape.warps_per_block);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, one_gpu, s, md, out, q, reinterpret_cast<const MagicDiv*>(mdiv));
+  if (e != cudaSuccess) return e;
   e = cudaGetLastError();
   prof_mark(prof, st);
-  *launches += 1;
+  *launches += 2;
   return e;
 }
 
@@ -807,6 +908,9 @@ cudaError_t alloc_kernels_init() {
           cudaSuccess ||
       (e = cudaFuncSetAttribute(alloc_fast_staged<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, staged)) !=
           cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(one_gpu_fast, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(PreSmem) * 8))) != cudaSuccess)
     return e;
   return cudaFuncSetAttribute(one_gpu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)one_gpu_smem_bytes(8));
 }

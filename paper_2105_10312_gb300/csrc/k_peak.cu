@@ -4,9 +4,10 @@
 // The unit of work of the per-partition test (§5.5) is one interference
 // term ceil(R / T_j) C_j of the response-time iteration.  The test kernels
 // evaluate it as: the period's reciprocal and shift and C_j read from shared
-// memory (the same address for every lane of a warp), a 32 x 32 -> 64-bit
-// multiply and shift (ceil_div_T), a 64-bit product with C_j, the D + 1 cap
-// and a 64-bit sum.  term_peak runs exactly that sequence with four
+// memory (the same address for every lane of a warp), the high word of a
+// 32 x 32-bit product and a shift (floor_div_T2), and a 32 x 32 -> 64-bit
+// multiply-add into the sum (the +1 of the ceiling is added once per step,
+// as a sum of WCETs).  term_peak runs exactly that sequence with four
 // independent iterations per thread over a 64-entry table, on every SM with
 // every warp slot it can fill, so its rate is what the device can sustain on
 // this arithmetic when nothing (dependences, divergence, idle warps) holds
@@ -29,7 +30,7 @@ constexpr int kPeakChains = 4;
 constexpr int kImadChains = 8;
 constexpr int kImadUnroll = 16;
 
-__global__ void __launch_bounds__(kPeakThreads) term_peak(int reps, unsigned long long cap, unsigned int seed,
+__global__ void __launch_bounds__(kPeakThreads) term_peak(int reps, unsigned long long base, unsigned int seed,
                                                           unsigned long long* sink) {
   __shared__ unsigned int sC[kPeakTab], sM[kPeakTab];
   __shared__ unsigned char sS[kPeakTab];
@@ -49,16 +50,17 @@ __global__ void __launch_bounds__(kPeakThreads) term_peak(int reps, unsigned lon
   unsigned long long chk = 0ull;
   for (int rep = 0; rep < reps; rep++) {
     unsigned long long nx[kPeakChains];
+    unsigned int R2[kPeakChains];
 #pragma unroll
-    for (int c = 0; c < kPeakChains; c++) nx[c] = 0ull;
+    for (int c = 0; c < kPeakChains; c++) {
+      nx[c] = base;  // stands for the step's sum of WCETs
+      R2[c] = 2u * (R[c] - 1u);
+    }
 #pragma unroll 4
     for (int j = 0; j < kPeakTab; j++) {
       const unsigned int mg = sM[j], sh = sS[j], C = sC[j];
 #pragma unroll
-      for (int c = 0; c < kPeakChains; c++) {
-        const unsigned long long tt = (unsigned long long)ceil_div_T(R[c], mg, sh) * C;
-        nx[c] += tt < cap ? tt : cap;
-      }
+      for (int c = 0; c < kPeakChains; c++) nx[c] += (unsigned long long)floor_div_T2(R2[c], mg, sh) * C;
     }
 #pragma unroll
     for (int c = 0; c < kPeakChains; c++) {
@@ -133,11 +135,11 @@ cudaError_t measure_alu_peak(int sm_count, cudaStream_t st, double* terms_per_s,
   int reps = 8;
   float ms = 0.f;
   for (int round = 0; round < 2 && e == cudaSuccess; round++) {
-    e = best_ms([&] { term_peak<<<blocks_t, kPeakThreads, 0, st>>>(reps, 1ull << 40, 3u, sink); }, st, 1, &ms);
+    e = best_ms([&] { term_peak<<<blocks_t, kPeakThreads, 0, st>>>(reps, 4321ull, 3u, sink); }, st, 1, &ms);
     if (e == cudaSuccess && ms > 0.f) reps = std::max(1, (int)std::min(1048576.0f, reps * 3.0f / ms));
   }
   if (e == cudaSuccess)
-    e = best_ms([&] { term_peak<<<blocks_t, kPeakThreads, 0, st>>>(reps, 1ull << 40, 3u, sink); }, st, 5, &ms);
+    e = best_ms([&] { term_peak<<<blocks_t, kPeakThreads, 0, st>>>(reps, 4321ull, 3u, sink); }, st, 5, &ms);
   if (e == cudaSuccess) {
     const double n = (double)blocks_t * kPeakThreads * kPeakChains * kPeakTab * (double)reps;
     *terms_per_s = n / (ms * 1e-3);

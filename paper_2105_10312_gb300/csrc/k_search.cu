@@ -106,11 +106,14 @@ __device__ bool serial_rta(const SearchHead& h, SearchThreads& w, unsigned int S
       if (R > Di) return false;
       // every earlier task met its deadline (C_j <= D_j <= T_j): each term
       // stays below R + T_j < 2^32 and the sum cannot overflow
-      unsigned long long next = Ci;
+      // ceil(R / T_j) = floor((R - 1) / T_j) + 1: C_i and the +1 terms add up to
+      // chp, which already holds C_i here
+      unsigned long long next = chp;
       nt += (unsigned int)__popc(hp);
+      const unsigned int R2 = 2u * ((unsigned int)R - 1u);
       for (unsigned int r2 = hp; r2; r2 &= r2 - 1u) {
         const int j = __ffs(r2) - 1;
-        next += (unsigned long long)ceil_div_T((unsigned int)R, h.mT[j], h.sh[j]) * w.C[j][tid];
+        next += (unsigned long long)floor_div_T2(R2, h.mT[j], h.sh[j]) * w.C[j][tid];
       }
       if (next == R) break;
       R = next;

@@ -127,8 +127,9 @@ def test_one_gpu_warps_and_autotuner(ctx):
 
 def _hand_terms(s, M, g):
     """Interference terms of the 1G verdict test, by the iteration the warp
-    runs: no iteration when a task has C > D or U > 1, or when the kernel's
-    pre-pass settles every task by its response-time upper bound (below);
+    runs: no iteration when a task has C > D or U > 1, when the hyperbolic
+    bound prod (1 + C_i / D_i) <= 2 holds, or when the kernel's pre-pass
+    settles every task by its response-time upper bound (below);
     otherwise tasks in deadline-monotonic order, and of those only the ones
     whose response-time upper bound (C_i + sum_{j<i} C_j) / (1 - U_hp)
     exceeds D_i, as the kernel rounds it (float32, the same operations in
@@ -167,6 +168,12 @@ def _hand_terms(s, M, g):
         x = f32(f32(f32(chp + Ci) / f32(f32(1) - u)) * f32(1 + 2.0 ** -18))
         return bool(x <= f32(Di))
 
+    # the kernel's hyperbolic test: prod (1 + C_i / D_i) <= 2 (with a 2^-13
+    # margin) settles the set
+    hyp = float(np.prod([1 + Fraction(Cr[i], int(D[i])) for i in range(n)]))
+    assert abs(hyp - 2 * (1 - 2.0 ** -13)) > 2.0 ** -10, "too close to the hyperbolic threshold"
+    if hyp <= 2 * (1 - 2.0 ** -13):
+        return 0
     # the kernel's pre-pass: in the original task order, each task's bound
     # with every task whose deadline is at most its own (itself included) as
     # higher priority, float32 sums in index order (its own C / T taken out
