@@ -427,11 +427,16 @@ __device__ __forceinline__ bool rta_verdict(RtaScratch& sc, int q, unsigned int*
   }
   int next = q < 32 ? q : 32;  // the first list position not yet assigned
   int iter = 0;
+  bool probe = true;  // the task's first step evaluates f(D_i) (see rta_verdict_seq)
   for (;;) {
     bool miss = false, conv = i < 0;
     if (i >= 0) {
       if (R > Di) {
         miss = true;
+      } else if (probe) {
+        probe = false;
+        conv = rta_step(sc, i, Di, Ci, Di, true) <= Di;
+        nt += (unsigned int)i;
       } else {
         const unsigned long long nx = rta_step(sc, i, R, Ci, Di, true);
         nt += (unsigned int)i;
@@ -467,6 +472,7 @@ __device__ __forceinline__ bool rta_verdict(RtaScratch& sc, int q, unsigned int*
       const unsigned long long lb = util_start(Ci, sc.Uex[i]);
       R = lb > R ? lb : R;
       iter = 0;
+      probe = true;
     } else if (conv) {
       i = -1;
     }
@@ -500,10 +506,16 @@ __device__ __forceinline__ bool rta_verdict_seq(const RtaScratch& sc, int q, uns
     R = lb > R ? lb : R;
     int iter = 0;
     const unsigned long long Cin = sc.Cin[i];
+    if (R > Di) return false;
+    // R_i is the least t with f(t) <= t (f: the step's function, which is
+    // non-decreasing), so f(D_i) <= D_i proves R_i <= D_i: one evaluation at
+    // D_i first; R (at most R_i) then serves the next listed task's start
+    bool probe = true;
     for (;;) {
       if (R > Di) return false;
-      // next = C_0 + ... + C_i + sum_{j<i} floor((R - 1) / T_j) C_j (see rta_step)
-      const unsigned int R2 = 2u * ((unsigned int)R - 1u);
+      // next = C_0 + ... + C_i + sum_{j<i} floor((t - 1) / T_j) C_j (see
+      // rta_step) at t = D_i for the probe, else at t = R
+      const unsigned int R2 = 2u * ((probe ? Di : (unsigned int)R) - 1u);
       unsigned long long part = 0ull;
       for (int j = lane; j < i; j += 32) {
         const uint2 v = sc.cm[j];
@@ -513,6 +525,11 @@ __device__ __forceinline__ bool rta_verdict_seq(const RtaScratch& sc, int q, uns
       const unsigned int hi = __reduce_add_sync(kFull, (unsigned int)(part >> 16));
       const unsigned long long next = Cin + ((unsigned long long)hi << 16) + lo;
       if (lane == 0) nt += (unsigned int)i;
+      if (probe) {
+        probe = false;
+        if (next <= Di) break;
+        continue;
+      }
       if (next == R) break;
       R = next;
       if (++iter > kIterCap) {

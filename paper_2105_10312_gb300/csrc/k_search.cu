@@ -97,10 +97,22 @@ __device__ bool serial_rta(const SearchHead& h, SearchThreads& w, unsigned int S
     const unsigned int Di = h.D[i];
     // a task the utilisation bound settles keeps its start value, at most
     // its least fixed point, as the next task's lower bound
-    const bool settled = util_pass(Ci, chp, ua, Di);
+    bool settled = util_pass(Ci, chp, ua, Di);
     ua += (float)Ci / (float)h.T[i];
     chp += Ci;
     const unsigned int hp = S & ((1u << i) - 1u);
+    if (!settled && R <= Di) {
+      // R_i is the least t with f(t) <= t (f: the iteration's non-decreasing
+      // function), so f(D_i) <= D_i settles the task too
+      unsigned long long fd = chp;
+      nt += (unsigned int)__popc(hp);
+      const unsigned int D2 = 2u * (Di - 1u);
+      for (unsigned int r2 = hp; r2; r2 &= r2 - 1u) {
+        const int j = __ffs(r2) - 1;
+        fd += (unsigned long long)floor_div_T2(D2, h.mT[j], h.sh[j]) * w.C[j][tid];
+      }
+      settled = fd <= Di;
+    }
     int iter = 0;
     for (; !settled;) {
       if (R > Di) return false;

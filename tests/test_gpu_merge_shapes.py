@@ -135,7 +135,9 @@ def _hand_terms(s, M, g):
     exceeds D_i, as the kernel rounds it (float32, the same operations in
     the same order).  Up to 16 such tasks are iterated one after another,
     each from the previous one's fixed point plus the WCETs between them
-    (task i's step evaluates i terms).  For longer lists, lane l
+    (task i's step evaluates i terms); each first evaluates f(D_i) and is
+    settled if that is at most D_i.  For longer lists (each task's first
+    step the same evaluation at D_i), lane l
     starts with the l-th such task i at C_0 + ... + C_i, every lane stepping
     once per round (task i's step evaluates i terms); a lane whose task
     reached its fixed point takes the next unassigned one in lane order,
@@ -230,6 +232,13 @@ def _hand_terms(s, M, g):
         Rp, Cp, terms = 0, 0, 0
         for i in need:
             R = max(Rp + Cin[i] - Cp, util_start(C[i], Uex[i]))
+            if R > Dp[i]:
+                return terms
+            # one evaluation at D_i first: f(D_i) <= D_i settles the task
+            terms += i
+            if C[i] + sum(math.ceil(Dp[i] / Tp[j]) * C[j] for j in range(i)) <= Dp[i]:
+                Rp, Cp = R, Cin[i]
+                continue
             while True:
                 if R > Dp[i]:
                     return terms
@@ -241,6 +250,7 @@ def _hand_terms(s, M, g):
             Rp, Cp = R, Cin[i]
         return terms
     lane_task = [need[l] if l < q else -1 for l in range(32)]
+    probe = [True] * 32  # a task's first step evaluates f(D_i)
     R = [max(Cin[i], util_start(C[i], Uex[i])) if i >= 0 else 0 for i in lane_task]
     Rcur = [0] * n
     nxt, terms = min(q, 32), 0
@@ -253,6 +263,10 @@ def _hand_terms(s, M, g):
                 continue
             if R[l] > Dp[i]:
                 miss = True
+            elif probe[l]:
+                probe[l] = False
+                terms += i
+                conv[l] = C[i] + sum(math.ceil(Dp[i] / Tp[j]) * C[j] for j in range(i)) <= Dp[i]
             else:
                 terms += i
                 step = C[i] + sum(math.ceil(R[l] / Tp[j]) * C[j] for j in range(i))
@@ -275,6 +289,7 @@ def _hand_terms(s, M, g):
             if idx < q:
                 i = need[idx]
                 lane_task[l], R[l] = i, max(Rcur[prev] + Cin[i] - Cin[prev], util_start(C[i], Uex[i]))
+                probe[l] = True
             else:
                 lane_task[l] = -1
         nxt = min(q, nxt + nfree)
