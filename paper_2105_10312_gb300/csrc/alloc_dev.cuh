@@ -272,21 +272,11 @@ __device__ bool lane_rta(const SetSmem& st, const unsigned int* S, unsigned int 
     R = lb > R ? lb : R;
     // a task the utilisation bound settles keeps its start value, at most
     // its least fixed point, as the next task's lower bound
-    bool settled = util_pass(Ci, chp, ua, Di);
+    // (unlike the warp and serial tests, no evaluation of f(D_i) first:
+    // merge candidates fail often, and on the paper setting it cost 6 %)
+    const bool settled = util_pass(Ci, chp, ua, Di);
     ua += (float)Ci / (float)st.T[row];
     chp += Ci;
-    if (!settled && R <= Di) {
-      // R_i is the least t with f(t) <= t (f: the iteration's non-decreasing
-      // function), so f(D_i) <= D_i settles the task too
-      unsigned long long fd = chp;
-      nt += (unsigned int)pos;
-      const unsigned int D2 = 2u * (Di - 1u);
-      for (int q = 0; q < pos; q++) {
-        const uint2 v = ls.cm[q][lane];
-        fd += (unsigned long long)floor_div_T2(D2, v.y, ls.sh[q][lane]) * v.x;
-      }
-      settled = fd <= Di;
-    }
     int iter = 0;
     for (; !settled;) {
       if (R > Di) {
