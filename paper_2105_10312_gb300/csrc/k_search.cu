@@ -15,10 +15,11 @@
 //            lexicographic order, spread over the threads); a thread extends
 //            it label by label with the block masks, sum minm and W updated
 //            in place.  A branch is cut when a block becomes infeasible, sum
-//            minm exceeds M, or W exceeds the CTA's best W so far: all three
-//            only grow as tasks are added, so no cut branch holds the
-//            optimum.  Leaves are compared by the key (W, sum minm, RGS) and a
-//            CTA-wide shuffle argmin finishes.
+//            minm exceeds M, or W plus the singleton W of the tasks still to
+//            place exceeds the CTA's best W so far: all three only grow as
+//            tasks are added (a task adds at least its singleton W), so no
+//            cut branch holds the optimum.  Leaves are compared by the key
+//            (W, sum minm, RGS) and a CTA-wide shuffle argmin finishes.
 #include <cuda_runtime.h>
 
 #include "gpa_device.cuh"
@@ -45,6 +46,7 @@ struct SearchHead {
   unsigned long long bestK1[kSThreads / 32];
   unsigned long long bestK2[kSThreads / 32];
   unsigned long long gbestW;   // best W found by any thread of the CTA (for cutting)
+  unsigned long long restW[kSN + 1];  // sum of the singleton W of tasks i..n-1 (phase B's bound)
   unsigned int err;            // error bits of the set (kErrIter: a test hit its step limit)
   int n;
   long long set;
@@ -484,6 +486,15 @@ __global__ void __launch_bounds__(kSThreads) search_sets(DevSets S, DevModel md,
     unsigned int nt = 0;
     subset_table(h, w, smm, n, tab_cap, md, z, mdiv, nt);
     terms += nt;
+    // Adding a task to a block adds at least its own W alone (1000 u, its
+    // factor at least 1000 per mille) and never lowers the others' factors,
+    // so a prefix's W plus the singleton W of the tasks still to place is a
+    // lower bound of every completion's W.
+    if (tid == 0) {
+      h.restW[n] = 0ull;
+      for (int i = n - 1; i >= 0; i--) h.restW[i] = h.restW[i + 1] + Wsub[h.rowbit[i]];
+    }
+    __syncthreads();
     // ---- phase B: depth-first over RGS, jobs = prefixes of length L
     const unsigned long long njobs = h.cnt[1][1];
     const unsigned int M = (unsigned)md.M;
@@ -518,7 +529,7 @@ __global__ void __launch_bounds__(kSThreads) search_sets(DevSets S, DevModel md,
         dead = dead || msub[nw] == 0;
       }
       w.used[L][tid] = (unsigned char)used;
-      if (dead || Sp > M || Wp > *(volatile unsigned long long*)&h.gbestW) continue;
+      if (dead || Sp > M || Wp + h.restW[L] > *(volatile unsigned long long*)&h.gbestW) continue;
       // depth-first over positions L..n-1; lab = 255 means "not placed yet"
       int i = L;
       if (i == n) {
@@ -560,7 +571,7 @@ __global__ void __launch_bounds__(kSThreads) search_sets(DevSets S, DevModel md,
         w.msk[lb][tid] = (unsigned short)nw;
         Wp += Wsub[nw] - Wsub[old];
         Sp += (unsigned)msub[nw] - (unsigned)msub[old];
-        if (msub[nw] == 0 || Sp > M || Wp > *(volatile unsigned long long*)&h.gbestW) continue;
+        if (msub[nw] == 0 || Sp > M || Wp + h.restW[i + 1] > *(volatile unsigned long long*)&h.gbestW) continue;
         const unsigned int u_next = lb + 1u > u_i ? lb + 1u : u_i;
         if (i + 1 == n) {
           const int empty = kmin > (int)u_next ? kmin - (int)u_next : 0;
