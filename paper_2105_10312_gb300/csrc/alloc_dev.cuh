@@ -254,7 +254,7 @@ __device__ bool lane_rta(const SetSmem& st, const unsigned int* S, unsigned int 
       ls.sh[n][lane] = st.shT[row];
       ls.row[n][lane] = (unsigned char)row;
       c_le_d = c_le_d && Ci <= st.D[row];
-      uf += (float)Ci / (float)st.T[row];
+      uf += __fdividef((float)Ci, (float)st.T[row]);
       n++;
     }
   }
@@ -275,7 +275,7 @@ __device__ bool lane_rta(const SetSmem& st, const unsigned int* S, unsigned int 
     // (unlike the warp and serial tests, no evaluation of f(D_i) first:
     // merge candidates fail often, and on the paper setting it cost 6 %)
     const bool settled = util_pass(Ci, chp, ua, Di);
-    ua += (float)Ci / (float)st.T[row];
+    ua += __fdividef((float)Ci, (float)st.T[row]);
     chp += Ci;
     int iter = 0;
     for (; !settled;) {

@@ -340,14 +340,16 @@ __device__ __forceinline__ int compact_partition(const SetSmem& st, const unsign
 // the tasks before it (Sjodin & Hansson, 1998): R = C_i + sum ceil(R / T_j)
 // C_j >= C_i + R U_hp, so R >= C_i / (1 - U_hp), and there is no fixed
 // point when U_hp >= 1.  uhp is a float sum of the C_j / T_j (each at most
-// 1, at most 255 of them) within 2^-15 of U_hp; the bound uses uhp - 2^-14
-// and rounds down with a 2^-20 margin, so it never exceeds the fixed point.
+// 1, at most 255 of them, each quotient from __fdividef: within 2 ulp) within
+// 2^-15 of U_hp; the bound uses uhp - 2^-14 and rounds down with a 2^-20
+// margin (its own quotient within 2 ulp too), so it never exceeds the fixed
+// point.
 // Returns 2^32 (above every deadline) when U_hp >= 1 is proven.
 __device__ __forceinline__ unsigned long long util_start(unsigned int Ci, float uhp) {
   const float u = uhp - 0x1p-14f;
   if (u <= 0.0f) return Ci;
   if (u >= 1.0f) return 1ull << 32;
-  const float b = (float)Ci / (1.0f - u) * (1.0f - 0x1p-20f);
+  const float b = __fdividef((float)Ci, 1.0f - u) * (1.0f - 0x1p-20f);
   if (!(b < 4294967296.0f)) return 1ull << 32;
   const unsigned long long lb = (unsigned long long)b;
   return lb > Ci ? lb : (unsigned long long)Ci;
@@ -361,17 +363,18 @@ __device__ __forceinline__ unsigned long long util_start(unsigned int Ci, float 
 // R_i <= X: X <= D_i proves that task i meets its deadline without iterating.
 // uhp is within 2^-15 of U_hp (see util_start) and chp is the exact sum of
 // the C_j; the float quotient is computed from U_hp + 2^-14 and raised by
-// 2^-18, which covers the four roundings (each at most 2^-24 relative) and
-// the rounding of D_i to float, so a true result is never wrong.
+// 2^-18, which covers the quotient's error (__fdividef: at most 2 ulp), the
+// other roundings (each at most 2^-24 relative) and the rounding of D_i to
+// float, so a true result is never wrong.
 __device__ __forceinline__ bool util_pass(unsigned int Ci, unsigned long long chp, float uhp, unsigned int Di) {
   const float u = uhp + 0x1p-14f;
   if (!(u < 1.0f)) return false;
-  const float x = (float)(chp + Ci) / (1.0f - u) * (1.0f + 0x1p-18f);
+  const float x = __fdividef((float)(chp + Ci), 1.0f - u) * (1.0f + 0x1p-18f);
   return x <= (float)Di;
 }
 
-// A float sum of the terms C_i / T_i (each at most 1) of at most 256 tasks
-// is within 2^-15 of U when U <= 1, so a sum above 1 + 2^-13 proves U > 1,
+// A float sum of the terms C_i / T_i (each at most 1, each within 2 ulp) of
+// at most 256 tasks is within 2^-15 of U when U <= 1, so a sum above 1 + 2^-13 proves U > 1,
 // and with it a miss under any policy on one processor.
 constexpr float kUtilFail = 1.0f + 0x1p-13f;
 
@@ -557,7 +560,7 @@ static __device__ __noinline__ bool warp_rta(const SetSmem& st, const unsigned i
   for (int i = lane; i < s; i += 32) {
     const unsigned int C = sc.cm[i].x;
     c_le_d = c_le_d && C <= sc.D[i];
-    uf += (float)C / (float)sc.T[i];
+    uf += __fdividef((float)C, (float)sc.T[i]);
   }
   c_le_d = __all_sync(kFull, c_le_d);
   if (early_exit) {
@@ -578,7 +581,7 @@ static __device__ __noinline__ bool warp_rta(const SetSmem& st, const unsigned i
     for (int c0 = 0; c0 < s; c0 += 32) {
       const int i = c0 + lane;
       const unsigned int C = i < s ? sc.cm[i].x : 0u;
-      float u = i < s ? (float)C / (float)sc.T[i] : 0.0f;
+      float u = i < s ? __fdividef((float)C, (float)sc.T[i]) : 0.0f;
       float incl = u;
       unsigned long long cin = C;
 #pragma unroll

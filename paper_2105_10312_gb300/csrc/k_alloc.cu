@@ -614,7 +614,7 @@ __device__ __forceinline__ int one_gpu_prepass(PreSmem& st, long long o, int n, 
     if (t < n) {
       // a already holds C_t + sum C_j, the bound's numerator
       const float u = (b - __uint_as_float(own.z)) + 0x1p-14f;
-      pass = pass && u < 1.0f && a / (1.0f - u) * (1.0f + 0x1p-13f) <= (float)own.x;
+      pass = pass && u < 1.0f && __fdividef(a, 1.0f - u) * (1.0f + 0x1p-13f) <= (float)own.x;
     }
   }
   return __all_sync(kFull, pass) ? kPrePass : kPreOpen;

@@ -100,7 +100,7 @@ __device__ bool serial_rta(const SearchHead& h, SearchThreads& w, unsigned int S
     // a task the utilisation bound settles keeps its start value, at most
     // its least fixed point, as the next task's lower bound
     bool settled = util_pass(Ci, chp, ua, Di);
-    ua += (float)Ci / (float)h.T[i];
+    ua += __fdividef((float)Ci, (float)h.T[i]);
     chp += Ci;
     const unsigned int hp = S & ((1u << i) - 1u);
     if (!settled && R <= Di) {

@@ -125,7 +125,7 @@ def test_one_gpu_warps_and_autotuner(ctx):
         c2.close()
 
 
-def _hand_terms(s, M, g):
+def _hand_terms(s, M, g, eps=0.0):
     """Interference terms of the 1G verdict test, by the iteration the warp
     runs: no iteration when a task has C > D or U > 1, when the hyperbolic
     bound prod (1 + C_i / D_i) <= 2 holds, or when the kernel's pre-pass
@@ -163,11 +163,16 @@ def _hand_terms(s, M, g):
         return 0
     f32 = np.float32
 
+    def quo(x, y):
+        # a float quotient as the kernel forms it (within 2 ulp); eps scales
+        # it to check that no decision sits at a rounding boundary
+        return f32(f32(f32(x) / f32(y)) * f32(1 + eps))
+
     def util_pass(Ci, chp, uhp, Di):
         u = f32(uhp + f32(2.0 ** -14))
         if not u < 1:
             return False
-        x = f32(f32(f32(chp + Ci) / f32(f32(1) - u)) * f32(1 + 2.0 ** -18))
+        x = f32(quo(chp + Ci, f32(f32(1) - u)) * f32(1 + 2.0 ** -18))
         return bool(x <= f32(Di))
 
     # the kernel's hyperbolic test: prod (1 + C_i / D_i) <= 2 (with a 2^-13
@@ -181,7 +186,7 @@ def _hand_terms(s, M, g):
     # higher priority, float32 sums in index order (its own C / T taken out
     # of the utilisation); all within their deadlines: no iteration
     Tr, Dr = [int(x) for x in T], [int(x) for x in D]
-    fr = [f32(f32(Cr[i]) / f32(Tr[i])) for i in range(n)]
+    fr = [quo(Cr[i], Tr[i]) for i in range(n)]
     settled = True
     for i in range(n):
         a, b = f32(0), f32(0)
@@ -190,14 +195,14 @@ def _hand_terms(s, M, g):
                 a = f32(a + f32(Cr[j]))
                 b = f32(b + fr[j])
         u = f32(f32(b - fr[i]) + f32(2.0 ** -14))
-        settled = settled and bool(u < 1) and bool(f32(f32(a / f32(f32(1) - u)) * f32(1 + 2.0 ** -13)) <= f32(Dr[i]))
+        settled = settled and bool(u < 1) and bool(f32(quo(a, f32(f32(1) - u)) * f32(1 + 2.0 ** -13)) <= f32(Dr[i]))
     if settled:
         return 0
     # float sums of C_j / T_j before each task, as the warp forms them:
     # chunks of 32, an inclusive Hillis-Steele scan per chunk plus a carry
     Uex, carry = [f32(0)] * n, f32(0)
     for c0 in range(0, n, 32):
-        u = np.array([f32(C[p]) / f32(Tp[p]) if p < n else f32(0) for p in range(c0, c0 + 32)], np.float32)
+        u = np.array([quo(C[p], Tp[p]) if p < n else f32(0) for p in range(c0, c0 + 32)], np.float32)
         incl = u.copy()
         for o in (1, 2, 4, 8, 16):
             nxt_incl = incl.copy()
@@ -214,7 +219,7 @@ def _hand_terms(s, M, g):
             return Ci
         if u >= 1:
             return 2 ** 32
-        b = f32(f32(f32(Ci) / f32(f32(1) - u)) * f32(1 - 2.0 ** -20))
+        b = f32(quo(Ci, f32(f32(1) - u)) * f32(1 - 2.0 ** -20))
         if not b < 2.0 ** 32:
             return 2 ** 32
         return max(int(b), Ci)
@@ -305,7 +310,11 @@ def test_term_counter(ctx):
         sub = G.subset(s, np.array([i]))
         ctx.allocate(gpa.to_device(sub), 148, 1, KC, KM, policy="ONE_GPU")
         got = ctx.last_terms()
-        counts.append(_hand_terms({k: sub[k] for k in ("T", "D", "A", "B", "type")}, 148, 1))
+        cols = {k: sub[k] for k in ("T", "D", "A", "B", "type")}
+        counts.append(_hand_terms(cols, 148, 1))
+        # the same count with every float quotient 2^-21 off either way: no
+        # decision of the set sits at a rounding boundary
+        assert _hand_terms(cols, 148, 1, 2.0 ** -21) == counts[-1] == _hand_terms(cols, 148, 1, -(2.0 ** -21)), i
         assert got == counts[-1], i
     assert min(counts) == 0 and sum(c > 0 for c in counts) >= 4, counts  # settled and iterated sets both covered
     b = gpa.gen_tasksets(**W.gen_params("batch", nsets=2000))
