@@ -677,20 +677,26 @@ __global__ void __launch_bounds__(256, GPA_ONEGPU_MINB) one_gpu(DevSets S, DevMo
   asm volatile("griddepcontrol.wait;" ::: "memory");  // the first grid has finished and its writes are visible
   const unsigned long long nslow = *(volatile unsigned long long*)(q.counters + 1);
   const long long ntasks = S.set_off[S.nsets];
+  // lane 0 fetches the next ticket when a set starts and its queue entry once
+  // the set is staged, so neither round trip delays the next set
+  unsigned long long tnext = 0ull;
+  long long snext = 0;
+  if (lane == 0) {
+    tnext = atomicAdd(q.counters + 2, 1ull);
+    if (tnext < nslow) snext = q.slow_sets[tnext];
+  }
   for (;;) {
-    unsigned long long i = 0;
-    if (lane == 0) i = atomicAdd(q.counters + 2, 1ull);
-    i = __shfl_sync(kFull, i, 0);
+    const unsigned long long i = __shfl_sync(kFull, tnext, 0);
     if (i >= nslow) break;
-    const long long s = q.slow_sets[i];
+    const long long s = __shfl_sync(kFull, snext, 0);
+    if (lane == 0) tnext = atomicAdd(q.counters + 2, 1ull);
     const long long o = S.set_off[s];
     const long long n = S.set_off[s + 1] - o;
-    if (n < 0 || n > S.n_max || n > kNmax || !slice_inside(o, n, ntasks)) {
+    const bool inside = n >= 0 && n <= S.n_max && n <= kNmax && slice_inside(o, n, ntasks);
+    const bool staged = inside && stage_set(sm.st, o, (int)n, S.T, S.D, S.A, S.B, S.u, S.type);
+    if (lane == 0 && tnext < nslow) snext = q.slow_sets[tnext];
+    if (!staged) {
       write_invalid(s, o, slice_inside(o, n, ntasks) ? n : 0, out, q.err);
-      continue;
-    }
-    if (!stage_set(sm.st, o, (int)n, S.T, S.D, S.A, S.B, S.u, S.type)) {
-      write_invalid(s, o, n, out, q.err);
       continue;
     }
     unsigned int all[kWords];
