@@ -14,7 +14,8 @@ iterates from the plain start value and knows none of them:
 * hyperbolic bound with deadlines as periods: prod (1 + C_i / D_i) <= 2
   means every task meets its deadline under DM;
 * one evaluation at the deadline: f(D_i) <= D_i (f the iteration's
-  function) means task i meets D_i;
+  function) means task i meets D_i, also with the higher-priority set
+  widened to every task with D_j <= D_i;
 * lower bounds: R_i >= C_i / (1 - U_hp), R_i >= R_{i-1} + C_i and
   R_i >= C_0 + ... + C_i for tasks whose fixed point is within D_i;
 * the exhaustive search's cut: adding a task to a block adds at least the
@@ -53,7 +54,7 @@ def _dm_order(T, D):
 
 def test_closed_form_shortcuts_agree_with_the_exact_analysis():
     rng = np.random.default_rng(2024)
-    checked = dict(upper=0, upper_wide=0, hyperbolic=0, at_deadline=0, lower=0)
+    checked = dict(upper=0, upper_wide=0, hyperbolic=0, at_deadline=0, at_deadline_wide=0, lower=0)
     for _ in range(3000):
         T, D, C = _random_set(rng)
         n = len(T)
@@ -87,6 +88,11 @@ def test_closed_form_shortcuts_agree_with_the_exact_analysis():
             if fD <= D[i]:
                 assert meets[i]
                 checked["at_deadline"] += 1
+            # the same over every task with D_j <= D_i, task i included
+            fw = sum(-(-int(D[i]) // int(T[j])) * int(C[j]) for j in range(n) if D[j] <= D[i])
+            if fw <= D[i]:
+                assert meets[i]
+                checked["at_deadline_wide"] += 1
             if meets[i]:
                 if Uhp < 1:
                     assert R[i] >= Fraction(int(C[i]), 1) / (1 - Uhp)
