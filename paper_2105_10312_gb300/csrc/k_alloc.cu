@@ -503,9 +503,9 @@ enum { kPreOpen = 0, kPrePass = 1, kPreMiss = 2, kPreInvalid = 3 };
 // It validates the tasks (kPreInvalid), computes every WCET at m = M with
 // the conflict factors of the whole set, and returns kPreMiss when a task has
 // C > D or U > 1 (either rules out every policy on one processor), kPrePass
-// when the hyperbolic bound holds or every task passes its response-time
-// upper bound (see util_pass) or one evaluation of the iteration at its
-// deadline, else kPreOpen.  The bound takes as higher-priority tasks every
+// when the hyperbolic bound holds or every task passes one evaluation of the
+// iteration at its deadline or its response-time upper bound (see
+// util_pass), else kPreOpen.  The bound takes as higher-priority tasks every
 // other task whose deadline is at most its own: a superset of its
 // deadline-monotonic predecessors, which only raises the bound.  A set that
 // passes under DM passes under EDF too (EDF meets every deadline that any
@@ -605,39 +605,40 @@ __device__ __forceinline__ int one_gpu_prepass(PreSmem& st, long long o, int n, 
   for (int c = 0; c < nch; c++) {
     const int t = c * 32 + lane;
     const uint4 own = t < n ? rec[t] : make_uint4(0u, 0u, 0u, 0u);
-    float a = 0.0f, b = 0.0f;
+    // One evaluation at the deadline.  The response time is the least t with
+    // f(t) <= t, f(t) = C_t + sum_{hp} ceil(t / T_j) C_j, so f(D_t) <= D_t
+    // proves D_t met.  The sum runs over every task with D_j <= D_t (a
+    // superset of t's deadline-monotonic predecessors; t itself, with a
+    // ceiling of at least 1, stands for C_t), and each ceiling comes from
+    // D_t times 1 / T_j raised by 2^-19, which is above D_t / T_j: every term
+    // is at least the exact one.  The float sum of at most 256 terms is
+    // within 2^-16 of its value (relative), and the test's 2^-13 margin
+    // covers that and the rounding of D_t.
+    const float Dt = (float)own.x;
+    float cs = 0.0f;
 #pragma unroll 4
     for (int j = 0; j < n; j++) {
       const uint4 r = rec[j];
-      if (r.x <= own.x) {
-        a += __uint_as_float(r.y);
-        b += __uint_as_float(r.z);
-      }
+      if (r.x <= own.x) cs = fmaf(ceilf(Dt * __uint_as_float(r.w)), __uint_as_float(r.y), cs);
     }
-    bool ok = true;
-    if (t < n) {
-      // a already holds C_t + sum C_j, the bound's numerator
-      const float u = (b - __uint_as_float(own.z)) + 0x1p-14f;
-      ok = u < 1.0f && __fdividef(a, 1.0f - u) * (1.0f + 0x1p-13f) <= (float)own.x;
-    }
-    // Tasks the bound leaves open: one evaluation at the deadline.  The
-    // response time is the least t with f(t) <= t, f(t) = C_t + sum_{hp}
-    // ceil(t / T_j) C_j, so f(D_t) <= D_t proves D_t met.  The sum runs over
-    // the same widened set (every task with D_j <= D_t, t itself with a
-    // ceiling of at least 1 standing for C_t), and each ceiling comes from
-    // D_t times 1 / T_j raised by 2^-19, which is above D_t / T_j: every
-    // term is at least the exact one.  The float sum of at most 256 terms is
-    // within 2^-16 of its value (relative), and the test's 2^-13 margin
-    // covers that and the rounding of D_t.
+    bool ok = t >= n || cs * (1.0f + 0x1p-13f) <= Dt;
+    // Tasks it leaves open: the response-time upper bound over the same
+    // tasks (see util_pass and the error analysis above).
     if (__any_sync(kFull, !ok)) {
-      const float Dt = (float)own.x;
-      float cs = 0.0f;
+      float a = 0.0f, b = 0.0f;
 #pragma unroll 4
       for (int j = 0; j < n; j++) {
         const uint4 r = rec[j];
-        if (r.x <= own.x) cs = fmaf(ceilf(Dt * __uint_as_float(r.w)), __uint_as_float(r.y), cs);
+        if (r.x <= own.x) {
+          a += __uint_as_float(r.y);
+          b += __uint_as_float(r.z);
+        }
       }
-      ok = ok || cs * (1.0f + 0x1p-13f) <= Dt;
+      if (!ok) {
+        // a already holds C_t + sum C_j, the bound's numerator
+        const float u = (b - __uint_as_float(own.z)) + 0x1p-14f;
+        ok = u < 1.0f && __fdividef(a, 1.0f - u) * (1.0f + 0x1p-13f) <= Dt;
+      }
     }
     pass = pass && ok;
   }
