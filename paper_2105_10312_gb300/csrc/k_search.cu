@@ -322,10 +322,12 @@ __device__ void write_search_empty(long long s, int kmin, int kmax, const DevMod
 
 // Phase A: minm(S) and W(S) of every non-empty subset S of the n rows (one
 // thread per subset); the WCET tables first when they fit.  Counts the
-// interference terms of its tests into nt.
+// interference terms of its tests into nt.  With flag_undecided, a subset
+// whose size search hit a test's step limit gets kMsubUndecided in msub.
+constexpr unsigned short kMsubUndecided = 0x8000;
 __device__ WcetTables subset_table(SearchHead& h, SearchThreads& w, const SearchSmem& sm, int n, int tab_cap,
                                    const DevModel& md, const Sizes& z, const MagicDiv* __restrict__ mdiv,
-                                   unsigned int& nt) {
+                                   unsigned int& nt, bool flag_undecided = false) {
   const int tid = threadIdx.x;
   const unsigned int nsub = 1u << n;
   const int Mu = md.M / md.g;
@@ -355,9 +357,18 @@ __device__ WcetTables subset_table(SearchHead& h, SearchThreads& w, const Search
       dead = dead || zs == 0u;
       lo = max(lo, zs);
     }
-    sm.msub[S2] = (unsigned short)(dead ? 0u
-                                        : (__popc(S2) == 1 ? lo
-                                                           : serial_minm(h, w, S2, lo, md, z, mdiv, tb, &h.err, nt)));
+    if (!flag_undecided) {
+      sm.msub[S2] = (unsigned short)(dead ? 0u
+                                          : (__popc(S2) == 1 ? lo
+                                                             : serial_minm(h, w, S2, lo, md, z, mdiv, tb, &h.err, nt)));
+    } else {
+      w.terr[tid] = 0u;
+      const unsigned int mm =
+          dead ? 0u : (__popc(S2) == 1 ? lo : serial_minm(h, w, S2, lo, md, z, mdiv, tb, &w.terr[tid], nt));
+      const unsigned int te = w.terr[tid];
+      if (te) atomicOr(&h.err, te);
+      sm.msub[S2] = (unsigned short)(mm | ((te & kErrIter) ? kMsubUndecided : 0u));
+    }
     const int nmS = __popc(S2 & h.memmask), ncS = __popc(S2) - nmS;
     unsigned long long Uc = 0, Um = 0;
     for (unsigned int r = S2; r; r &= r - 1u) {
@@ -697,7 +708,7 @@ __global__ void __launch_bounds__(kSThreads) search_explicit(DevSets S, DevModel
       continue;
     }
     unsigned int nt = 0;
-    const WcetTables tb = n > 0 ? subset_table(h, w, smm, n, tab_cap, md, z, mdiv, nt) : WcetTables{nullptr, nullptr};
+    if (n > 0) subset_table(h, w, smm, n, tab_cap, md, z, mdiv, nt, true);
     terms += nt;
     nt = 0;
     // this set's candidate count
@@ -721,20 +732,20 @@ __global__ void __launch_bounds__(kSThreads) search_explicit(DevSets S, DevModel
         pm[c - q * (unsigned int)k] |= h.rowbit[i];
         c = q;
       }
-      w.terr[tid] = 0u;
-      bool feasible = true;
-      for (int b = 0; b < k && feasible; b++) {
+      // A part passes at its size m iff its task set's minimum passing size
+      // is at most m: the test is monotone in m (§4.1), and every size is
+      // admissible here (no size lists).  A part whose size search hit a
+      // test's step limit leaves the candidate (and the optimum) undecided.
+      bool feasible = true, undecided = false;
+      for (int b = 0; b < k; b++) {
         if (!pm[b]) continue;
         const unsigned int m = (unsigned)parts[b] * (unsigned)md.g;
-        feasible = serial_test(h, w, pm[b], m, (unsigned)md.g, md.kc, md.km, md.sched, mdiv[m], tb, &w.terr[tid], nt);
+        const unsigned int ms = smm.msub[pm[b]];
+        if (ms & kMsubUndecided) undecided = true;
+        else feasible = feasible && ms != 0u && ms <= m;
       }
-      terms += nt;
-      nt = 0;
-      // a test that hit its step limit leaves the candidate (and the optimum) undecided
-      const unsigned int terr = w.terr[tid];
-      if (terr) atomicOr(&h.err, terr);
-      if (cverdict) cverdict[s * cstride + (long long)r] = (terr & kErrIter) ? 2 : feasible ? 1 : 0;
-      if (!feasible) continue;
+      if (cverdict) cverdict[s * cstride + (long long)r] = undecided ? 2 : feasible ? 1 : 0;
+      if (undecided || !feasible) continue;
       // induced set partition: blocks relabelled by first occurrence (task order)
       int label[kSK];
       for (int b = 0; b < kSK; b++) label[b] = -1;
