@@ -254,7 +254,7 @@ __device__ bool lane_rta(const SetSmem& st, const unsigned int* S, unsigned int 
       ls.sh[n][lane] = st.shT[row];
       ls.row[n][lane] = (unsigned char)row;
       c_le_d = c_le_d && Ci <= st.D[row];
-      uf += __fdividef((float)Ci, (float)st.T[row]);
+      uf += (float)Ci * st.rT[row];
       n++;
     }
   }
@@ -267,15 +267,17 @@ __device__ bool lane_rta(const SetSmem& st, const unsigned int* S, unsigned int 
     const uint2 self = ls.cm[pos][lane];
     const int row = ls.row[pos][lane];
     const unsigned int Ci = self.x, Di = st.D[row];
-    unsigned long long R = Rprev + Ci;
-    const unsigned long long lb = util_start(Ci, ua);
-    R = lb > R ? lb : R;
     // a task the utilisation bound settles keeps its start value, at most
     // its least fixed point, as the next task's lower bound
     // (unlike the warp and serial tests, no evaluation of f(D_i) first:
     // merge candidates fail often, and on the paper setting it cost 6 %)
     const bool settled = util_pass(Ci, chp, ua, Di);
-    ua += __fdividef((float)Ci, (float)st.T[row]);
+    unsigned long long R = Rprev + Ci;
+    if (!settled) {
+      const unsigned long long lb = util_start(Ci, ua);
+      R = lb > R ? lb : R;
+    }
+    ua += (float)Ci * st.rT[row];  // C_i / T_i within 2^-22 (two roundings)
     chp += Ci;
     int iter = 0;
     for (; !settled;) {

@@ -162,6 +162,7 @@ struct SetSmem {
   unsigned long long A[kNmax];
   unsigned long long B[kNmax];
   unsigned int u[kNmax];
+  float rT[kNmax];               // 1 / T (float, correctly rounded)
   unsigned int memmask[kWords];  // rows holding memory-intensive tasks
   int n;
 };
@@ -256,6 +257,7 @@ __device__ __forceinline__ bool stage_set(SetSmem& st, long long o, int n, const
     if (t < n) {
       int r = rank[c];
       st.T[r] = (unsigned int)Tv[c];
+      st.rT[r] = __frcp_rn((float)Tv[c]);
       st.D[r] = (unsigned int)Dv[c];
       unsigned int mg, sh;
       magic_for_period((unsigned int)Tv[c], &mg, &sh);
@@ -362,15 +364,13 @@ __device__ __forceinline__ unsigned long long util_start(unsigned int Ci, float 
 // iterate started at or below the least fixed point stays at or below X, and
 // R_i <= X: X <= D_i proves that task i meets its deadline without iterating.
 // uhp is within 2^-15 of U_hp (see util_start) and chp is the exact sum of
-// the C_j; the float quotient is computed from U_hp + 2^-14 and raised by
-// 2^-18, which covers the quotient's error (__fdividef: at most 2 ulp), the
-// other roundings (each at most 2^-24 relative) and the rounding of D_i to
-// float, so a true result is never wrong.
+// the C_j.  X <= D_i is tested as (C_i + sum C_j) <= D_i (1 - U_hp), with
+// U_hp + 2^-14 for U_hp and the left side raised by 2^-17, which covers the
+// five roundings of the two sides (conversions, 1 - u, products; each at most
+// 2^-24 relative), so a true result is never wrong.
 __device__ __forceinline__ bool util_pass(unsigned int Ci, unsigned long long chp, float uhp, unsigned int Di) {
   const float u = uhp + 0x1p-14f;
-  if (!(u < 1.0f)) return false;
-  const float x = __fdividef((float)(chp + Ci), 1.0f - u) * (1.0f + 0x1p-18f);
-  return x <= (float)Di;
+  return u < 1.0f && (float)(chp + Ci) * (1.0f + 0x1p-17f) <= (float)Di * (1.0f - u);
 }
 
 // A float sum of the terms C_i / T_i (each at most 1, each within 2 ulp) of

@@ -172,8 +172,7 @@ def _hand_terms(s, M, g, eps=0.0):
         u = f32(uhp + f32(2.0 ** -14))
         if not u < 1:
             return False
-        x = f32(quo(chp + Ci, f32(f32(1) - u)) * f32(1 + 2.0 ** -18))
-        return bool(x <= f32(Di))
+        return bool(f32(f32(chp + Ci) * f32(1 + 2.0 ** -17)) <= f32(f32(Di) * f32(f32(1) - u)))
 
     # the kernel's hyperbolic test: prod (1 + C_i / D_i) <= 2 (with a 2^-13
     # margin) settles the set
