@@ -646,7 +646,8 @@ def measure(bench, name, rank, world, steps, warmup, with_cpu=True, e2e_steps=5,
                 tr = scaled_traffic(prof, ntasks)
                 rec.update({"bound": "hbm", "achieved": ach, "peak": bench.hbm_peak, "unit": "GB/s",
                             "frac": ach / bench.hbm_peak, "traffic": tr["bytes"] if tr else None, "traffic_detail": tr,
-                            "algorithmic_bytes": alg, "peak_source": bench.hbm_src + " hbm_gbs (MEASURED_PEAKS.json)"})
+                            "algorithmic_bytes": alg, "peak_source": bench.hbm_src + " hbm_gbs (MEASURED_PEAKS.json)",
+                            "ncu": prof})
             else:
                 t = terms[j]
                 ach = t / (kms / 1000.0)
