@@ -169,8 +169,9 @@ enum {
   GPA_OPT_AUTOTUNE = 1,       /* 1: on the first gpa_allocate call of each batch signature, time the
                                  launch shapes of the kernels the call runs (the fast kernel's loads,
                                  warps and sets per ticket; the merge kernel's warps per CTA, warps
-                                 per set, CTAs per SM and top-size round; the 1G kernel's warps per
-                                 CTA) and keep the fastest for that signature (default 0) */
+                                 per set, CTAs per SM and top-size round; the 1G deferred-set
+                                 kernel's warps per CTA) and keep the fastest for that signature
+                                 (default 0) */
   GPA_OPT_GRAPH = 2,          /* 1: capture gpa_allocate's launches in a CUDA graph per argument set and
                                  replay it (default 0); not allowed while the stream is being captured */
   GPA_OPT_FAST_WARPS = 3,     /* force warps per CTA of the fast allocate kernel: 1, 2, 4 or 8 (the staged
@@ -203,8 +204,9 @@ enum {
   GPA_OPT_MERGE_GROUP = 12,   /* force warps per task set in the merge kernel: 1, 2, 4 or 8; a set's
                                  candidate merges are spread over its warps (0 = tuned/default) */
   GPA_OPT_MERGE_BLOCKS = 13,  /* force CTAs of the persistent merge grid (0 = tuned/default) */
-  GPA_OPT_TEST_WARPS = 14,    /* force warps per CTA of the 1G kernel (one test of all tasks at M per
-                                 set, one warp per set): 1..8 (0 = tuned/default) */
+  GPA_OPT_TEST_WARPS = 14,    /* force warps per CTA of the 1G deferred-set kernel (the sets the 1G
+                                 pre-pass does not decide in closed form: one test of all tasks at M
+                                 per set, one warp per set): 1..8 (0 = tuned/default) */
   GPA_OPT_MERGE_TOPFIRST = 15 /* force whether the merge kernel's SMS steps first test every candidate
                                  merge with several sizes in its range at its top size (a failure there
                                  rules it out at every size): 1 = off, 2 = on (0 = tuned/default) */
