@@ -520,8 +520,9 @@ enum { kPreOpen = 0, kPrePass = 1, kPreMiss = 2, kPreInvalid = 3 };
 // (2^-24), so a (the bound's numerator C_t + sum C_hp) is within 2^-16 of its
 // true value (relative), and b within 2^-15 of U_hp (b and t's term add up
 // to at most U <= 1 + 2^-13).
-// The bound's quotient uses U_hp + 2^-14 and is raised by 2^-13, which also
-// covers its remaining roundings and that of D_t, so a pass is never wrong.
+// The bound is tested as a <= D_t (1 - U_hp), with U_hp + 2^-14 for U_hp
+// and a raised by 2^-13, which also covers the test's roundings and that of
+// D_t, so a pass is never wrong.
 __device__ __forceinline__ int one_gpu_prepass(PreSmem& st, long long o, int n, const DevSets& S,
                                                const DevModel& md, const MagicDiv& mdM, unsigned long long& Uc,
                                                unsigned long long& Um, int& nm) {
@@ -637,7 +638,7 @@ __device__ __forceinline__ int one_gpu_prepass(PreSmem& st, long long o, int n, 
       if (!ok) {
         // a already holds C_t + sum C_j, the bound's numerator
         const float u = (b - __uint_as_float(own.z)) + 0x1p-14f;
-        ok = u < 1.0f && __fdividef(a, 1.0f - u) * (1.0f + 0x1p-13f) <= Dt;
+        ok = u < 1.0f && a * (1.0f + 0x1p-13f) <= Dt * (1.0f - u);
       }
     }
     pass = pass && ok;

@@ -195,7 +195,7 @@ def _hand_terms(s, M, g, eps=0.0):
                 a = f32(a + f32(Cr[j]))
                 b = f32(b + fr[j])
         u = f32(f32(b - fr[i]) + f32(2.0 ** -14))
-        ok = bool(u < 1) and bool(f32(quo(a, f32(f32(1) - u)) * f32(1 + 2.0 ** -13)) <= f32(Dr[i]))
+        ok = bool(u < 1) and bool(f32(a * f32(1 + 2.0 ** -13)) <= f32(f32(Dr[i]) * f32(f32(1) - u)))
         if not ok:
             # one evaluation at D_i over the same tasks, ceilings from 1 / T_j
             # raised by 2^-19, a fused multiply-add per term
