@@ -603,24 +603,28 @@ __device__ void forbid_cands(const Grp& g, MergeSmem& sm, int p1, int kend) {
 // Size ranges of the candidates (indices of admissible sizes in
 // [max(m1, m2), min(m1 + m2 - g, M)], ka > kb when there is none) and which
 // are tested by a warp.  Returns the lowest and highest live index.
+// Candidate k (slot e): its range, whether a warp tests it, whether it is
+// live; lo_i / hi_i take in its range.
+__device__ __forceinline__ void cand_range_of(MergeSmem& sm, int p1, int k, int e, const Sizes& z, int& lo_i,
+                                              int& hi_i) {
+  const unsigned int lo = max(sm.m[p1], sm.m[e]);
+  const unsigned int hi = min((unsigned int)sm.m[p1] + sm.m[e] - 1u, z.M);
+  const int a = z.below(lo), b = lo <= hi ? z.below(hi + 1u) - 1 : a - 1;
+  sm.ka[k] = (unsigned short)a;
+  sm.kb[k] = (unsigned short)(b < 0 ? 0 : b);
+  // tasks of the merged set (the two slots' task sets are disjoint)
+  const int cnt = sm.nc[p1] + sm.nm[p1] + sm.nc[e] + sm.nm[e];
+  sm.big[k] = cnt > kLaneMax ? 1 : 0;
+  sm.live[k] = b >= a ? 1 : 0;
+  if (b >= a) {
+    lo_i = min(lo_i, a);
+    hi_i = max(hi_i, b);
+  }
+}
+
 __device__ void cand_ranges(const Grp& g, MergeSmem& sm, int p1, int ne, const Sizes& z, int* lmin, int* lmax) {
   int lo_i = 1 << 30, hi_i = -1;
-  for (int k = g.tid; k < ne; k += g.nthreads) {
-    const int e = sm.cand[k];
-    const unsigned int lo = max(sm.m[p1], sm.m[e]);
-    const unsigned int hi = min((unsigned int)sm.m[p1] + sm.m[e] - 1u, z.M);
-    const int a = z.below(lo), b = lo <= hi ? z.below(hi + 1u) - 1 : a - 1;
-    sm.ka[k] = (unsigned short)a;
-    sm.kb[k] = (unsigned short)(b < 0 ? 0 : b);
-    // tasks of the merged set (the two slots' task sets are disjoint)
-    const int cnt = sm.nc[p1] + sm.nm[p1] + sm.nc[e] + sm.nm[e];
-    sm.big[k] = cnt > kLaneMax ? 1 : 0;
-    sm.live[k] = b >= a ? 1 : 0;
-    if (b >= a) {
-      lo_i = min(lo_i, a);
-      hi_i = max(hi_i, b);
-    }
-  }
+  for (int k = g.tid; k < ne; k += g.nthreads) cand_range_of(sm, p1, k, sm.cand[k], z, lo_i, hi_i);
   *lmin = grp_min_int(g, sm, lo_i);
   *lmax = grp_max_int(g, sm, hi_i);
 }
@@ -745,24 +749,36 @@ __device__ void merge_set(const Grp& g, MergeSmem& sm, WarpScratch* extra, long 
           break;
         }
       }
+      // SMS keeps the candidates in par_list order, so their size ranges are
+      // set here as they are listed (BF sorts them first: cand_ranges)
+      const bool sms = p.policy == GPA_POLICY_SMS;
+      int lo_i = 1 << 30, hi_i = -1;
       if (p1 >= 0) {
         for (int b0 = 0; b0 < nal; b0 += 32) {
           const int r = b0 + g.lane;
           const int e = r < nal ? sm.order[r] : 0;
           const bool in = r < nal && ((elig[e >> 5] >> (e & 31)) & 1u);
           const unsigned int bm = __ballot_sync(kFull, in);
-          if (in) sm.cand[ne + __popc(bm & ((1u << g.lane) - 1u))] = (unsigned char)e;
+          if (in) {
+            const int k = ne + __popc(bm & ((1u << g.lane) - 1u));
+            sm.cand[k] = (unsigned char)e;
+            if (sms) cand_range_of(sm, p1, k, e, z, lo_i, hi_i);
+          }
           ne += __popc(bm);
         }
       }
+      lo_i = __reduce_min_sync(kFull, lo_i);
+      hi_i = __reduce_max_sync(kFull, hi_i);
       if (g.lane == 0) {
         sm.ctl[0] = p1;
         sm.ctl[1] = rp;
         sm.ctl[2] = ne;
+        sm.ctl[3] = lo_i;
+        sm.ctl[4] = hi_i;
       }
     }
     g.sync();
-    const int p1 = sm.ctl[0], rp = sm.ctl[1], ne = sm.ctl[2];
+    const int p1 = sm.ctl[0], rp = sm.ctl[1], ne = sm.ctl[2], lmin_sel = sm.ctl[3], lmax_sel = sm.ctl[4];
     g.sync();
     if (p1 < 0) {
       stuck = true;
@@ -772,9 +788,8 @@ __device__ void merge_set(const Grp& g, MergeSmem& sm, WarpScratch* extra, long 
     unsigned int wm = 0u;    // its merged size
     if (p.policy == GPA_POLICY_SMS) {
       // Def. 3: compute every candidate merge; smallest size wins, ties to
-      // the earlier par_list position
-      int lmin, lmax;
-      cand_ranges(g, sm, p1, ne, z, &lmin, &lmax);
+      // the earlier par_list position (ranges set by the selection above)
+      int lmin = lmin_sel, lmax = lmax_sel;
       if (linear) {
         // with top_first, a candidate tested by one thread with more than
         // one size in its range is first tested at its top size: failing
