@@ -463,7 +463,8 @@ int32_t gpa_search_best(gpa_ctx* ctx, const gpa_tasksets* sets, const gpa_model*
  * values), here found over the explicit space.
  *  - cand_verdict (nullable; memory of sets->mem): [nsets * cand_stride]
  *    bytes, candidate r of set s at s * cand_stride + r: 1 feasible,
- *    0 not, 2 undecided (a test hit its step limit); entries past a set's
+ *    0 not, 2 undecided (a test of one of its parts' task sets hit its step
+ *    limit); entries past a set's
  *    own count are 255.  cand_stride = the count for n_max tasks, returned
  *    in *ncand (nullable) by every call, also when cand_verdict is NULL.
  *  - Limits: n_max <= GPA_SEARCH_NMAX, 1 <= kmin <= kmax <= GPA_SEARCH_KMAX,

@@ -230,9 +230,10 @@ __device__ __forceinline__ unsigned long long grp_sum_u64(const Grp& g, MergeSme
 // thread, serially.  First the tasks' WCETs in priority order, with a
 // float utilisation sum: a task with C > D, or a sum above 1 + 2^-13
 // (U > 1, see kUtilFail), fails the set before any iteration.  Then tasks
-// are visited in priority order and each earlier task met its deadline, so
-// the iteration starts at the larger of R_prev + C_i and the utilisation
-// bound (util_start), both at most the least fixed point.
+// are visited in priority order and each earlier task met its deadline: a
+// task the response-time upper bound settles (util_pass) needs no
+// iteration; the others start at the larger of R_prev + C_i and the
+// utilisation bound (util_start), both at most the least fixed point.
 __device__ bool lane_rta(const SetSmem& st, const unsigned int* S, unsigned int m, unsigned int kc, unsigned int km,
                          const MagicDiv& md, LaneScratch& ls, int lane, unsigned int* err) {
   int nm = 0, ns = 0;

@@ -484,7 +484,8 @@ struct OneGpuSmem {
 };
 
 // Per-warp scratch of the 1G pre-pass: the set's columns in original order
-// and, per task, D, C and C / T (as float bits).
+// and, per task, D, C, C / T and a raised 1 / T (the last three as float
+// bits).
 struct PreSmem {
   unsigned long long A[kNmax], B[kNmax];
   unsigned int T[kNmax], D[kNmax];
