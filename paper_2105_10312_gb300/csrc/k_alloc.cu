@@ -603,7 +603,8 @@ __device__ __forceinline__ int one_gpu_prepass(PreSmem& st, long long o, int n, 
   // the true one <= 2.
   if (hyp <= 2.0f * (1.0f - 0x1p-13f)) return kPrePass;
   __syncwarp();
-  bool pass = true;
+  // chunk by chunk; the first chunk with a task that neither test passes
+  // leaves the set open, and the later chunks are not examined
   for (int c = 0; c < nch; c++) {
     const int t = c * 32 + lane;
     const uint4 own = t < n ? rec[t] : make_uint4(0u, 0u, 0u, 0u);
@@ -642,9 +643,9 @@ __device__ __forceinline__ int one_gpu_prepass(PreSmem& st, long long o, int n, 
         ok = u < 1.0f && a * (1.0f + 0x1p-13f) <= Dt * (1.0f - u);
       }
     }
-    pass = pass && ok;
+    if (!__all_sync(kFull, ok)) return kPreOpen;
   }
-  return __all_sync(kFull, pass) ? kPrePass : kPreOpen;
+  return kPrePass;
 }
 
 // 1G, first kernel: one warp per set, grid-stride.  The pre-pass decides a
