@@ -8,7 +8,8 @@ decides every set twice, as the sweep compares them: by the paper's
 partition-and-allocate heuristic (Alg. 1-3, SMS order, no ACT pre-pass) and
 by the 1G baseline (the GPU as one partition), each one gpa_allocate call
 replayed from a CUDA graph with launch shapes picked by the library's
-autotuner.  Metric: task sets decided per second (whole job, all ranks);
+autotuner; end to end from pinned host buffers, one gpa_allocate_multi call
+per step copies the batch in once and decides it under both.  Metric: task sets decided per second (whole job, all ranks);
 candidate allocations tested per second beside it (the heuristic's merge
 candidates plus one 1G candidate per set).
 
@@ -743,22 +744,32 @@ def measure(bench, name, rank, world, steps, warmup, with_cpu=True, e2e_steps=5,
         ctx_h.set_option("AUTOTUNE", 1 if autotune else 0)
         saved = ctx
         ctx = ctx_h
-        with torch.cuda.stream(stream):
-            for _ in range(2):  # warm-up: the autotuner and the graphs of every host slice
+        # several allocation policies over one batch: one gpa_allocate_multi
+        # call, which copies the batch in once for all of them
+        multi = len(calls) > 1 and all(c not in ("SEARCH", "EXPLICIT") for c in calls)
+
+        def e2e_step():  # synchronous: H2D, kernels, D2H
+            if multi:
+                tolerant(lambda: ctx.allocate_multi(hs, **md, policies=list(calls), act=False,
+                                                    linear=args.merge == "linear", outs=houts), houts)
+            else:
                 for j, call in enumerate(calls):
                     tolerant(lambda: do_call(j, call, hs, houts[j]), [houts[j]])
+
+        with torch.cuda.stream(stream):
+            for _ in range(2):  # warm-up: the autotuner and the graphs of every host slice
+                e2e_step()
             times = []
             for i in range(e2e_steps):
                 bench.flush_l2(i)
                 torch.cuda.synchronize(dev)
                 t0 = time.perf_counter()
-                for j, call in enumerate(calls):
-                    tolerant(lambda: do_call(j, call, hs, houts[j]), [houts[j]])  # synchronous: H2D, kernels, D2H
+                e2e_step()
                 times.append(time.perf_counter() - t0)
         ctx = saved
         ctx_h.close()
         e2e_t = shard.max_over_ranks(float(np.mean(times)))
-        h2d = (8 * (nsets + 1) + 41 * ntasks) * len(calls)
+        h2d = (8 * (nsets + 1) + 41 * ntasks) * (1 if multi else len(calls))
         d2h = sum((22 * nsets + 3 * ntasks) if c not in ("SEARCH", "EXPLICIT") else
                   (21 * nsets + ntasks + 2 * wp["kmax"] * nsets) for c in calls)
         ms = sorted(1000.0 * t for t in times)
@@ -766,8 +777,11 @@ def measure(bench, name, rank, world, steps, warmup, with_cpu=True, e2e_steps=5,
                "d2h_bytes_per_step": d2h, "ms_per_step": 1000.0 * e2e_t,
                "step_ms": {"steps": len(ms), "min": ms[0], "median": float(np.median(ms)), "max": ms[-1],
                            "each": [round(1000.0 * t, 3) for t in times]},
-               "path": f"{len(calls)} C-ABI call(s) per step on pinned host buffers, each synchronous "
-                       "(inputs copied in, kernels, results copied out)"}
+               "path": (f"one gpa_allocate_multi call per step ({' + '.join(calls)}) on pinned host buffers, "
+                        "synchronous (inputs copied in once for every policy, kernels, results copied out)"
+                        if multi else
+                        f"{len(calls)} C-ABI call(s) per step on pinned host buffers, each synchronous "
+                        "(inputs copied in, kernels, results copied out)")}
 
     # the plain form: one launch sequence per task set, on a sample
     plain = None
@@ -885,7 +899,7 @@ def main():
                          "search of §5.2")
     ap.add_argument("--sched", choices=["dm", "edf"], default="dm",
                     help="per-partition policy: deadline-monotonic response-time test (default) or EDF demand test")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--host-slices", type=int, default=0,
                     help="host-buffer path: 0 = library default (split batches over 48 MB), 1 = whole batch checked "
                          "before computing, n = n slices")

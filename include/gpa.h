@@ -385,6 +385,31 @@ typedef struct {
 int32_t gpa_allocate(gpa_ctx* ctx, const gpa_tasksets* sets, const gpa_model* model,
                      const gpa_params* params, gpa_alloc_result* result);
 
+/* Most policies per gpa_allocate_multi call. */
+#define GPA_MULTI_MAX_POLICIES 8
+
+/* gpa_allocate under several policies in one call.  The paper's evaluation
+ * (§7) decides every task set of a sweep under each allocation policy it
+ * compares (SMS, BF, the 1G baseline, with ACT or INA); this call does that
+ * for one batch.  results[i] receives exactly what
+ * gpa_allocate(ctx, sets, model, &params[i], &results[i]) would write, for
+ * every i < npolicies (1 to GPA_MULTI_MAX_POLICIES, else GPA_ERR_RANGE).
+ *  - Host arrays: the batch crosses the host link once for all the
+ *    policies.  Each slice of sets is copied in once, decided under every
+ *    policy in order, and its results of every policy are copied out while
+ *    the next slice is decided.  The call returns when every result is in
+ *    the caller's arrays.
+ *  - Device arrays: the same work as npolicies gpa_allocate calls in order on
+ *    the context stream (asynchronous, as gpa_allocate).
+ *  - Every results[i] must have mem == sets->mem and arrays of its own (no
+ *    two results may share an array); the checks of gpa_allocate apply to
+ *    each params[i] and results[i], and a failed check writes nothing.
+ *  - Status: the first error, as gpa_allocate reports it; an undecided or
+ *    invalid set under any of the policies gives GPA_ERR_TIMEOUT or
+ *    GPA_ERR_RANGE, and each result's reason[] marks its own sets. */
+int32_t gpa_allocate_multi(gpa_ctx* ctx, const gpa_tasksets* sets, const gpa_model* model,
+                           const gpa_params* params, int32_t npolicies, gpa_alloc_result* results);
+
 /* Task sets per call of gpa_allocate_noalloc. */
 #define GPA_NOALLOC_MAX_SETS 262144
 

@@ -119,6 +119,8 @@ def _set_signatures(L):
                                           ctypes.POINTER(Candidates), _vp, _vp]
     L.gpa_allocate.argtypes = [_vp, ctypes.POINTER(Tasksets), ctypes.POINTER(Model), ctypes.POINTER(Params),
                                   ctypes.POINTER(AllocResult)]
+    L.gpa_allocate_multi.argtypes = [_vp, ctypes.POINTER(Tasksets), ctypes.POINTER(Model), ctypes.POINTER(Params),
+                                     ctypes.c_int32, ctypes.POINTER(AllocResult)]
     L.gpa_search_best.argtypes = [_vp, ctypes.POINTER(Tasksets), ctypes.POINTER(Model), ctypes.c_int32,
                                      ctypes.c_int32, ctypes.POINTER(BestResult)]
     L.gpa_enumerate_partitions.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -351,6 +353,27 @@ class Context:
         _check(lib().gpa_allocate(self._h, ctypes.byref(ts), ctypes.byref(md), ctypes.byref(pr), ctypes.byref(res)))
         return out
 
+    def allocate_multi(self, sets, M, g=1, k_c_pm=1200, k_m_pm=2300, policies=("SMS", "ONE_GPU"), act=False,
+                       linear=True, outs=None, sched="DM", sizes=None):
+        """gpa_allocate_multi: the batch decided under every policy of
+        ``policies`` (names, or (name, act) pairs) in one call; host inputs
+        are copied to the device once for all of them.  Returns one result
+        dict per policy, as ``allocate`` returns."""
+        ts, mem = make_tasksets(sets)
+        md = make_model(M, g, k_c_pm, k_m_pm, sched, sizes)
+        pol = [(q, act) if isinstance(q, str) else (q[0], bool(q[1])) for q in policies]
+        if outs is None:
+            outs = [self.alloc_result(sets) for _ in pol]
+        if len(outs) != len(pol):
+            raise ValueError("allocate_multi: one result per policy")
+        prs = (Params * len(pol))(*[Params(POLICY[q], 1 if a else 0, 1 if linear else 0, 0) for q, a in pol])
+        res = (AllocResult * len(pol))(*[
+            AllocResult(mem, 0, _ptr(o["verdict"]), _ptr(o["reason"]), _ptr(o["n_parts"]), _ptr(o["Pi"]),
+                        _ptr(o["W"]), _ptr(o.get("n_tests")), _ptr(o["part_of_task"]), _ptr(o["size_of_part"]))
+            for o in outs])
+        _check(lib().gpa_allocate_multi(self._h, ctypes.byref(ts), ctypes.byref(md), prs, len(pol), res))
+        return outs
+
     def best_result(self, sets, kmax):
         mem = _mem_of(sets["set_off"])
         nsets = _len(sets["set_off"]) - 1
@@ -411,6 +434,7 @@ class Context:
 
 
 NOALLOC_MAX_SETS = 262144
+MULTI_MAX_POLICIES = 8
 
 
 def allocate_noalloc(sets, out, M, g=1, k_c_pm=1200, k_m_pm=2300, policy="SMS", act=False, linear=True,

@@ -1099,8 +1099,43 @@ static int32_t ensure_pipe(gpa_ctx* c) {
   return e == cudaSuccess ? GPA_OK : gpa_cuda_fail(e, "copy streams");
 }
 
+// Device buffers that receive policy k's results on the host path: slots
+// 14..21 for the first policy of a call, 40 + 8 (k - 1) .. 47 + 8 (k - 1)
+// for the others.
+static int32_t host_out_bufs(gpa_ctx* c, int k, long long ns, long long nt, bool tests, AllocOut* out) {
+  const int b = k == 0 ? 14 : 40 + 8 * (k - 1);
+  const size_t nsb = (size_t)(ns > 0 ? ns : 1), ntb = (size_t)(nt > 0 ? nt : 1);
+  *out = AllocOut{(unsigned char*)ctx_buffer(c, b, nsb), (unsigned char*)ctx_buffer(c, b + 1, nsb),
+                  (int*)ctx_buffer(c, b + 2, sizeof(int) * nsb), (int*)ctx_buffer(c, b + 3, sizeof(int) * nsb),
+                  (long long*)ctx_buffer(c, b + 4, sizeof(long long) * nsb),
+                  tests ? (int*)ctx_buffer(c, b + 5, sizeof(int) * nsb) : nullptr,
+                  (unsigned char*)ctx_buffer(c, b + 6, ntb), (short*)ctx_buffer(c, b + 7, sizeof(short) * ntb)};
+  if (!out->verdict || !out->reason || !out->n_parts || !out->Pi || !out->W || (tests && !out->n_tests) ||
+      !out->part_of_task || !out->size_of_part)
+    return gpa_fail(GPA_ERR_NOMEM, "result staging failed");
+  return GPA_OK;
+}
+
+// Queue the copies of sets [s0, s1) (tasks [t0, t1)) of one policy's results
+// from its device buffers to the caller's arrays.
+static void copy_out_range(Mover& mo, const gpa_alloc_result& r, const AllocOut& out, long long s0, long long s1,
+                           long long t0, long long t1) {
+  const size_t m = (size_t)(s1 - s0), n = (size_t)(t1 - t0);
+  mo.add(r.verdict + s0, out.verdict + s0, m);
+  mo.add(r.reason + s0, out.reason + s0, m);
+  mo.add(r.n_parts + s0, out.n_parts + s0, sizeof(int) * m);
+  mo.add(r.Pi + s0, out.Pi + s0, sizeof(int) * m);
+  mo.add(r.W + s0, out.W + s0, sizeof(long long) * m);
+  if (r.n_tests) mo.add(r.n_tests + s0, out.n_tests + s0, sizeof(int) * m);
+  mo.add(r.part_of_task + t0, out.part_of_task + t0, n);
+  mo.add(r.size_of_part + t0, out.size_of_part + t0, sizeof(short) * n);
+}
+
+// Host arrays in slices b[j] .. b[j + 1]: slice j + 1's columns are copied in
+// while slice j is decided, under each of the np policies in turn, and slice
+// j's results of every policy are copied out while slice j + 1 is decided.
 static int32_t allocate_host_sliced(gpa_ctx* c, const gpa_tasksets* sets, const gpa_model* model,
-                                    const DevModel& md, const gpa_params& p, gpa_alloc_result* r,
+                                    const DevModel& md, const gpa_params* p, int np, gpa_alloc_result* r,
                                     const std::vector<long long>& b) {
   const long long ns = sets->nsets, nt = sets->set_off[ns];
   if (nt > 0 && (!sets->T || !sets->D || !sets->A || !sets->B || !sets->type))
@@ -1116,15 +1151,13 @@ static int32_t allocate_host_sliced(gpa_ctx* c, const gpa_tasksets* sets, const 
   long long* B = (long long*)ctx_buffer(c, 4, b8);
   long long* u = (long long*)ctx_buffer(c, 5, b8);
   unsigned char* ty = (unsigned char*)ctx_buffer(c, 6, (size_t)(nt > 0 ? nt : 1));
-  const size_t ntb = (size_t)(nt > 0 ? nt : 1);
-  AllocOut out{(unsigned char*)ctx_buffer(c, 14, (size_t)ns), (unsigned char*)ctx_buffer(c, 15, (size_t)ns),
-               (int*)ctx_buffer(c, 16, sizeof(int) * (size_t)ns), (int*)ctx_buffer(c, 17, sizeof(int) * (size_t)ns),
-               (long long*)ctx_buffer(c, 18, sizeof(long long) * (size_t)ns),
-               r->n_tests ? (int*)ctx_buffer(c, 19, sizeof(int) * (size_t)ns) : nullptr,
-               (unsigned char*)ctx_buffer(c, 20, ntb), (short*)ctx_buffer(c, 21, sizeof(short) * ntb)};
-  if (!off || !T || !D || !A || !B || !u || !ty || !out.verdict || !out.reason || !out.n_parts || !out.Pi ||
-      !out.W || (r->n_tests && !out.n_tests) || !out.part_of_task || !out.size_of_part)
-    return gpa_fail(GPA_ERR_NOMEM, "staging allocation failed");
+  if (!off || !T || !D || !A || !B || !u || !ty) return gpa_fail(GPA_ERR_NOMEM, "staging allocation failed");
+  AllocOut outs[GPA_MULTI_MAX_POLICIES];
+  bool one_gpu = false;
+  for (int k = 0; k < np; k++) {
+    if ((st = host_out_bufs(c, k, ns, nt, r[k].n_tests != nullptr, &outs[k])) != GPA_OK) return st;
+    one_gpu = one_gpu || p[k].policy == GPA_POLICY_ONE_GPU;
+  }
   cudaStream_t in = c->copy_in, cs = c->stream, ot = c->copy_out;
   cudaEvent_t ev_start = c->pipe_ev[0], ev_in = c->pipe_ev[1], ev_done = c->pipe_ev[2];
   // Every wait below is issued right after the record it waits for, so the
@@ -1135,7 +1168,7 @@ static int32_t allocate_host_sliced(gpa_ctx* c, const gpa_tasksets* sets, const 
   // The staging kernel needs SM slots while the previous slice computes; the
   // 1G kernel holds every SM for its whole slice, so its slices move by copy
   // engine (unless GPA_OPT_HOST_COPY forces the kernel).
-  const bool engine = p.policy == GPA_POLICY_ONE_GPU && c->host_copy < 2 && b.size() > 2;
+  const bool engine = one_gpu && c->host_copy < 2 && b.size() > 2;
   Mover mi(c, in, true, engine), mo(c, ot, false, engine);
   mi.add(off, sets->set_off, sizeof(long long) * (size_t)(ns + 1));
   st = GPA_OK;
@@ -1154,26 +1187,21 @@ static int32_t allocate_host_sliced(gpa_ctx* c, const gpa_tasksets* sets, const 
     if (e != cudaSuccess) break;
     // the slice's sets index the full task columns (their offsets are absolute)
     DevSets ds{s1 - s0, sets->n_max, off + s0, T, D, A, B, u, ty};
-    AllocOut o = out;
-    o.verdict += s0;
-    o.reason += s0;
-    o.n_parts += s0;
-    o.Pi += s0;
-    o.W += s0;
-    if (o.n_tests) o.n_tests += s0;
-    if ((st = allocate_device(c, ds, md, p, o)) != GPA_OK) break;
+    for (int k = 0; k < np && st == GPA_OK; k++) {
+      AllocOut o = outs[k];
+      o.verdict += s0;
+      o.reason += s0;
+      o.n_parts += s0;
+      o.Pi += s0;
+      o.W += s0;
+      if (o.n_tests) o.n_tests += s0;
+      st = allocate_device(c, ds, md, p[k], o);
+    }
+    if (st != GPA_OK) break;
     e = cudaEventRecord(ev_done, cs);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ot, ev_done, 0);
     if (e != cudaSuccess) break;
-    const size_t m = (size_t)(s1 - s0);
-    mo.add(r->verdict + s0, o.verdict, m);
-    mo.add(r->reason + s0, o.reason, m);
-    mo.add(r->n_parts + s0, o.n_parts, sizeof(int) * m);
-    mo.add(r->Pi + s0, o.Pi, sizeof(int) * m);
-    mo.add(r->W + s0, o.W, sizeof(long long) * m);
-    if (r->n_tests) mo.add(r->n_tests + s0, o.n_tests, sizeof(int) * m);
-    mo.add(r->part_of_task + t0, out.part_of_task + t0, n);
-    mo.add(r->size_of_part + t0, out.size_of_part + t0, sizeof(short) * n);
+    for (int k = 0; k < np; k++) copy_out_range(mo, r[k], outs[k], s0, s1, t0, t1);
     // after the last slice, the error word comes out with the results
     if (j + 2 == b.size()) mo.add(c->h_err, c->d_err, sizeof(unsigned int));
     e = mo.flush();
@@ -1199,54 +1227,62 @@ static int32_t allocate_host_sliced(gpa_ctx* c, const gpa_tasksets* sets, const 
   return st;
 }
 
-extern "C" int32_t gpa_allocate(gpa_ctx* c, const gpa_tasksets* sets, const gpa_model* model,
-                                const gpa_params* params, gpa_alloc_result* r) {
-  int32_t st = common_checks(c, sets, model, "gpa_allocate");
+// gpa_allocate and gpa_allocate_multi: the batch decided under np policies,
+// its host columns (if any) copied to the device once for all of them.
+static int32_t allocate_policies(gpa_ctx* c, const gpa_tasksets* sets, const gpa_model* model,
+                                 const gpa_params* params, int np, gpa_alloc_result* r, const char* who) {
+  int32_t st = common_checks(c, sets, model, who);
   if (st != GPA_OK) return st;
-  if (!params || !r) return gpa_fail(GPA_ERR_ARG, "gpa_allocate: NULL params/result");
-  if (params->policy < GPA_POLICY_SMS || params->policy > GPA_POLICY_ONE_GPU)
-    return gpa_fail(GPA_ERR_ARG, "gpa_allocate: unknown policy %d", params->policy);
-  if (r->mem != sets->mem) return gpa_fail(GPA_ERR_ARG, "gpa_allocate: result and sets differ in mem");
+  if (!params || !r) return gpa_fail(GPA_ERR_ARG, "%s: NULL params/result", who);
+  if (np < 1 || np > GPA_MULTI_MAX_POLICIES)
+    return gpa_fail(GPA_ERR_RANGE, "%s: %d policies (1 to %d)", who, np, GPA_MULTI_MAX_POLICIES);
+  for (int k = 0; k < np; k++) {
+    if (params[k].policy < GPA_POLICY_SMS || params[k].policy > GPA_POLICY_ONE_GPU)
+      return gpa_fail(GPA_ERR_ARG, "%s: unknown policy %d", who, params[k].policy);
+    if (r[k].mem != sets->mem) return gpa_fail(GPA_ERR_ARG, "%s: result and sets differ in mem", who);
+  }
   if (sets->nsets == 0) return GPA_OK;
-  if (!r->verdict || !r->reason || !r->n_parts || !r->Pi || !r->W || !r->part_of_task || !r->size_of_part)
-    return gpa_fail(GPA_ERR_ARG, "gpa_allocate: NULL result array");
-  if (!sets->u_ppm) return gpa_fail(GPA_ERR_ARG, "gpa_allocate: u_ppm is required");
+  for (int k = 0; k < np; k++)
+    if (!r[k].verdict || !r[k].reason || !r[k].n_parts || !r[k].Pi || !r[k].W || !r[k].part_of_task ||
+        !r[k].size_of_part)
+      return gpa_fail(GPA_ERR_ARG, "%s: NULL result array", who);
+  if (!sets->u_ppm) return gpa_fail(GPA_ERR_ARG, "%s: u_ppm is required", who);
   DeviceGuard guard(c->device);
   DevModel md;
   if ((st = device_model(c, model, &md)) != GPA_OK) return st;
   if (sets->mem == GPA_DEVICE) {
-    AllocOut out{r->verdict, r->reason, r->n_parts, r->Pi, (long long*)r->W, r->n_tests, r->part_of_task,
-                 r->size_of_part};
-    return allocate_device(c, dev_sets(sets), md, *params, out);
+    for (int k = 0; k < np && st == GPA_OK; k++) {
+      AllocOut out{r[k].verdict, r[k].reason, r[k].n_parts, r[k].Pi, (long long*)r[k].W, r[k].n_tests,
+                   r[k].part_of_task, r[k].size_of_part};
+      st = allocate_device(c, dev_sets(sets), md, params[k], out);
+    }
+    return st;
   }
   const std::vector<long long> bounds = slice_bounds(c, sets);
-  if (!bounds.empty()) return allocate_host_sliced(c, sets, model, md, *params, r, bounds);
+  if (!bounds.empty()) return allocate_host_sliced(c, sets, model, md, params, np, r, bounds);
   HostStage hs;
   if ((st = stage_in_validated(c, sets, model, &hs)) != GPA_OK) return st;
-  const long long ns = sets->nsets, nt = hs.ntasks > 0 ? hs.ntasks : 1;
-  AllocOut out{(unsigned char*)ctx_buffer(c, 14, (size_t)ns), (unsigned char*)ctx_buffer(c, 15, (size_t)ns),
-               (int*)ctx_buffer(c, 16, sizeof(int) * (size_t)ns), (int*)ctx_buffer(c, 17, sizeof(int) * (size_t)ns),
-               (long long*)ctx_buffer(c, 18, sizeof(long long) * (size_t)ns),
-               r->n_tests ? (int*)ctx_buffer(c, 19, sizeof(int) * (size_t)ns) : nullptr,
-               (unsigned char*)ctx_buffer(c, 20, (size_t)nt), (short*)ctx_buffer(c, 21, sizeof(short) * (size_t)nt)};
-  if (!out.verdict || !out.reason || !out.n_parts || !out.Pi || !out.W || (r->n_tests && !out.n_tests) ||
-      !out.part_of_task || !out.size_of_part)
-    return gpa_fail(GPA_ERR_NOMEM, "result staging failed");
-  if ((st = allocate_device(c, hs.ds, md, *params, out)) != GPA_OK) return st;
+  const long long ns = sets->nsets;
+  AllocOut outs[GPA_MULTI_MAX_POLICIES];
+  for (int k = 0; k < np; k++)
+    if ((st = host_out_bufs(c, k, ns, hs.ntasks, r[k].n_tests != nullptr, &outs[k])) != GPA_OK) return st;
+  for (int k = 0; k < np; k++)
+    if ((st = allocate_device(c, hs.ds, md, params[k], outs[k])) != GPA_OK) return st;
   Mover mv(c, c->stream, false);
-  mv.add(r->verdict, out.verdict, (size_t)ns);
-  mv.add(r->reason, out.reason, (size_t)ns);
-  mv.add(r->n_parts, out.n_parts, sizeof(int) * (size_t)ns);
-  mv.add(r->Pi, out.Pi, sizeof(int) * (size_t)ns);
-  mv.add(r->W, out.W, sizeof(long long) * (size_t)ns);
-  if (r->n_tests) mv.add(r->n_tests, out.n_tests, sizeof(int) * (size_t)ns);
-  if (hs.ntasks > 0) {
-    mv.add(r->part_of_task, out.part_of_task, (size_t)hs.ntasks);
-    mv.add(r->size_of_part, out.size_of_part, sizeof(short) * (size_t)hs.ntasks);
-  }
+  for (int k = 0; k < np; k++) copy_out_range(mv, r[k], outs[k], 0, ns, 0, hs.ntasks);
   cudaError_t e = mv.flush();
   if (e != cudaSuccess) return gpa_cuda_fail(e, "allocate result copy");
   return finish_host_call(c);
+}
+
+extern "C" int32_t gpa_allocate(gpa_ctx* c, const gpa_tasksets* sets, const gpa_model* model,
+                                const gpa_params* params, gpa_alloc_result* r) {
+  return allocate_policies(c, sets, model, params, 1, r, "gpa_allocate");
+}
+
+extern "C" int32_t gpa_allocate_multi(gpa_ctx* c, const gpa_tasksets* sets, const gpa_model* model,
+                                      const gpa_params* params, int32_t npolicies, gpa_alloc_result* results) {
+  return allocate_policies(c, sets, model, params, npolicies, results, "gpa_allocate_multi");
 }
 
 // ------------------------------------------------------- exhaustive optimum

@@ -182,3 +182,62 @@ def test_page_locked_inputs_for_the_other_entry_points(sctx):
     ref = oracle.search_best(s, 40, 2, KC, KM, 1, 4, nthreads=8)
     for k in ("feasible", "W", "sum_minm", "n_blocks", "spare", "rgs", "minm_block"):
         assert np.array_equal(out[k], ref[k]), k
+
+
+_MULTI_SETS = dict(seed=93, nsets=4000, n_min=0, n_max=64, U_lo_ppm=100000, U_hi_ppm=40000000, deadline_pm=750,
+                   mu_dist="BETA25", T_lo=1000, T_hi=100000)
+_MULTI_REF = {}
+
+
+def _multi_ref(s, policy, act, sched):
+    key = (policy, act, sched)
+    if key not in _MULTI_REF:
+        _MULTI_REF[key] = oracle.allocate(s, 80, 2, KC, KM, policy=policy, act=act, nthreads=8, sched=sched)
+    return _MULTI_REF[key]
+
+
+@pytest.mark.parametrize("slices", [1, 0, 5])
+def test_multi_policy_call_matches_oracle(sctx, slices):
+    """gpa_allocate_multi on host arrays: one copy of the batch, decided
+    under four policies; each result equals the oracle's for its policy,
+    with the batch whole, split by default and in 5 slices."""
+    s = gpa.gen_tasksets(**_MULTI_SETS)
+    pols = [("SMS", True), ("ONE_GPU", False), ("BF", False), ("SMS", False)]
+    sctx.set_option("HOST_SLICES", slices)
+    try:
+        outs = sctx.allocate_multi(s, 80, g=2, k_c_pm=KC, k_m_pm=KM, policies=pols)
+    finally:
+        sctx.set_option("HOST_SLICES", 0)
+    assert len(outs) == len(pols)
+    for (pol, act), out in zip(pols, outs):
+        _assert_equal(out, _multi_ref(s, pol, act, "DM"), ALLOC_KEYS, f"multi {pol} act={act} slices={slices}")
+
+
+def test_multi_policy_call_on_device_arrays(sctx):
+    s = gpa.gen_tasksets(**_MULTI_SETS)
+    pols = [("BF", True), ("ONE_GPU", False)]
+    outs = sctx.allocate_multi(gpa.to_device(s), 80, g=2, k_c_pm=KC, k_m_pm=KM, policies=pols, sched="EDF")
+    sctx.sync()
+    for (pol, act), out in zip(pols, outs):
+        got = {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
+        _assert_equal(got, _multi_ref(s, pol, act, "EDF"), ALLOC_KEYS, f"multi device {pol} act={act} EDF")
+
+
+def test_multi_policy_call_rejections(sctx):
+    s = gpa.gen_tasksets(**_MULTI_SETS)
+    for pols in ([], ["SMS"] * (gpa.MULTI_MAX_POLICIES + 1)):
+        with pytest.raises(gpa.GpaError) as ei:
+            sctx.allocate_multi(s, 80, g=2, k_c_pm=KC, k_m_pm=KM, policies=pols)
+        assert ei.value.code == gpa.ERR_RANGE
+    bad = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in s.items()}
+    bad["D"][int(bad["set_off"][3001])] = 0
+    sctx.set_option("HOST_SLICES", 4)
+    try:
+        with pytest.raises(gpa.GpaError) as ei:
+            sctx.allocate_multi(bad, 80, g=2, k_c_pm=KC, k_m_pm=KM, policies=["SMS", "ONE_GPU"])
+        assert ei.value.code == gpa.ERR_RANGE and "3001" in str(ei.value)
+        outs = sctx.allocate_multi(s, 80, g=2, k_c_pm=KC, k_m_pm=KM, policies=[("SMS", True), "ONE_GPU"])
+    finally:
+        sctx.set_option("HOST_SLICES", 0)
+    _assert_equal(outs[0], _multi_ref(s, "SMS", True, "DM"), ALLOC_KEYS, "multi after a rejected call")
+    _assert_equal(outs[1], _multi_ref(s, "ONE_GPU", False, "DM"), ALLOC_KEYS, "multi 1G after a rejected call")
