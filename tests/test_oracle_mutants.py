@@ -2,14 +2,15 @@
 
 Each case plants one mistake in a copy of oracle.c (a dropped term, a
 flipped comparison, a swapped operand, an off-by-one), builds it into a
-temporary library, points the oracle module at it and runs every pin of
-tests/test_oracle_pins.py: at least one pin must fail.  The real oracle is
-untouched; all of this runs on the CPU."""
+temporary library, points the oracle module at it and runs the pins of
+tests/test_oracle_pins.py, quickest first, until one fails: at least one
+must.  The real oracle is untouched; all of this runs on the CPU."""
 import ctypes
 import inspect
 import itertools
 import os
 import subprocess
+import time
 
 import pytest
 
@@ -62,6 +63,22 @@ MUTANTS = [
      "if (sm != b->sum_minm) return sm > b->sum_minm;"),
     ("optimum ties to the later RGS", "if (rgs[i] != b->rgs[i]) return rgs[i] < b->rgs[i];",
      "if (rgs[i] != b->rgs[i]) return rgs[i] > b->rgs[i];"),
+    ("response time equal to D misses", "      if (r > s->D[i]) { ok = 0; break; }",
+     "      if (r >= s->D[i]) { ok = 0; break; }"),
+    ("interference from lower-priority tasks", "if (in[j] && j != i && higher_prio(s, j, i)) next +=",
+     "if (in[j] && j != i) next +="),
+    ("start value counts lower-priority tasks", "if (in[j] && j != i && higher_prio(s, j, i)) r += C[j];",
+     "if (in[j] && j != i) r += C[j];"),
+    ("binary size search skips its top check", "if (nc == 0 || !test(s, md, in, cand[nc - 1])) return 0;",
+     "if (nc == 0) return 0;"),
+    ("Lemma 1 at M SMs", "wcet(s->A[i], s->B[i], 1000, 1) * 1000000", "wcet(s->A[i], s->B[i], 1000, md->M) * 1000000"),
+    ("Alg. 1 merges until the sum is below M", "  while (Pi > md->M) {", "  while (Pi >= md->M) {"),
+    ("success needs a sum below M", "  if (Pi <= md->M) { r->verdict = 1;", "  if (Pi < md->M) { r->verdict = 1;"),
+    ("ACT runs when no merge is needed", "if (act && Pi > md->M) {", "if (act) {"),
+    ("forbidden pair matched one way only",
+     "    if (same_tasks(pl->v[k].a, Q->in, s->n) && same_tasks(pl->v[k].b, P->in, s->n)) return 1;\n", ""),
+    ("1G tests at one SM", "  int ok = test(s, md, in, md->M);", "  int ok = test(s, md, in, 1);"),
+    ("1G workload left out", "  r->W = workload(s, md, in);\n  size_of_part[0]", "  r->W = 0;\n  size_of_part[0]"),
 ]
 
 
@@ -88,8 +105,14 @@ def _pin_calls():
     return calls
 
 
-def _failing_pins(source, tmp_path):
-    """Names of the pins that fail with the oracle built from `source`."""
+# seconds each pin took in the last full run (the control below), so that
+# a run that stops at its first failing pin tries the quick pins first
+_PIN_SECONDS = {}
+
+
+def _failing_pins(source, tmp_path, first_only=False):
+    """Names of the pins that fail with the oracle built from `source` (only
+    the first one with first_only)."""
     c_path = tmp_path / "mutant.c"
     so_path = tmp_path / "libmutant.so"
     c_path.write_text(source)
@@ -99,12 +122,18 @@ def _failing_pins(source, tmp_path):
     saved = oracle._lib
     oracle._lib = ctypes.CDLL(str(so_path))
     failed = []
+    calls = sorted(_pin_calls(), key=lambda c: _PIN_SECONDS.get(c[0] + repr(c[2]), 0.0))
     try:
-        for name, f, kw in _pin_calls():
+        for name, f, kw in calls:
+            t0 = time.perf_counter()
             try:
                 f(**kw)
             except Exception:  # an AssertionError, or a status the mutant made the oracle return
                 failed.append(name)
+                if first_only:
+                    break
+            if not first_only:
+                _PIN_SECONDS[name + repr(kw)] = time.perf_counter() - t0
     finally:
         oracle._lib = saved
     return failed
@@ -119,4 +148,5 @@ def test_unmutated_copy_passes_every_pin(tmp_path):
 def test_pins_catch_planted_mistake(label, old, new, tmp_path):
     src = open(oracle._SRC).read()
     assert old in src, label
-    assert _failing_pins(src.replace(old, new), tmp_path), f"no pin caught the planted mistake: {label}"
+    assert _failing_pins(src.replace(old, new), tmp_path, first_only=True), \
+        f"no pin caught the planted mistake: {label}"

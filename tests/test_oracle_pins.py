@@ -532,15 +532,36 @@ def test_heuristic_invariants_paper_workload():
 
 
 def test_one_gpu_is_the_whole_set_at_M():
-    s = gen_tasksets(seed=13, nsets=40, n_min=1, n_max=20, U_lo_ppm=100000, U_hi_ppm=6000000, deadline_pm=750,
+    """§7.2's baseline: the whole set as one partition of all M SMs.  The
+    verdict is the (separately pinned) test at M; the workload is Def. 4's
+    sum of k_i u_i written out from the §4.2 conflict rule (k_i is the
+    type's factor when the set holds at least two tasks of that type, else
+    1000); every task sits in part 0 of size M; one test per set; an empty
+    set is decided schedulable with no partition."""
+    s = gen_tasksets(seed=13, nsets=60, n_min=0, n_max=20, U_lo_ppm=100000, U_hi_ppm=6000000, deadline_pm=750,
                      mu_dist="BETA25")
     M = 148
     r = oracle.allocate(s, M, 1, KC, KM, policy="ONE_GPU")
-    for si in range(40):
+    empty = nonempty = 0
+    for si in range(60):
         v, o, n = _set_view(s, si)
+        assert r["n_tests"][si] == 1
+        if n == 0:
+            empty += 1
+            assert r["verdict"][si] == 1 and r["reason"][si] == 0
+            assert r["n_parts"][si] == 0 and r["Pi"][si] == 0 and r["W"][si] == 0
+            continue
+        nonempty += 1
         ok, _ = oracle.rta(v["T"], v["D"], v["A"], v["B"], v["type"], np.ones(n, np.uint8), M, KC, KM)
         assert r["verdict"][si] == ok
+        assert r["reason"][si] == (0 if ok else 4)  # GPA_REASON_OK / GPA_REASON_TEST
         assert r["n_parts"][si] == 1 and r["Pi"][si] == M
+        typ = [int(t) for t in v["type"]]
+        factor = {0: KC if typ.count(0) >= 2 else 1000, 1: KM if typ.count(1) >= 2 else 1000}
+        assert r["W"][si] == sum(factor[t] * int(u) for t, u in zip(typ, v["u_ppm"]))
+        assert (r["part_of_task"][o:o + n] == 0).all()
+        assert r["size_of_part"][o] == M and (r["size_of_part"][o + 1:o + n] == 0).all()
+    assert empty > 0 and nonempty > 40
 
 
 # ------------------------------------------------------- exhaustive optimum
