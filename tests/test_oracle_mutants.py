@@ -79,6 +79,15 @@ MUTANTS = [
      "    if (same_tasks(pl->v[k].a, Q->in, s->n) && same_tasks(pl->v[k].b, P->in, s->n)) return 1;\n", ""),
     ("1G tests at one SM", "  int ok = test(s, md, in, md->M);", "  int ok = test(s, md, in, 1);"),
     ("1G workload left out", "  r->W = workload(s, md, in);\n  size_of_part[0]", "  r->W = 0;\n  size_of_part[0]"),
+    ("EDF skips each task's first deadline", "for (i128 t = s->D[i]; t <= L; t += s->T[i]) {",
+     "for (i128 t = s->D[i] + s->T[i]; t <= L; t += s->T[i]) {"),
+    ("EDF ignores conflicts", "      C[i] = wcet(s->A[i], s->B[i], kfactor(s, md, in, i), m);\n      idx[k++] = i;",
+     "      C[i] = wcet(s->A[i], s->B[i], 1000, m);\n      idx[k++] = i;"),
+    ("DM ignores conflicts", "    if (in[i]) C[i] = wcet(s->A[i], s->B[i], kfactor(s, md, in, i), m);",
+     "    if (in[i]) C[i] = wcet(s->A[i], s->B[i], 1000, m);"),
+    ("EDF busy period from zero", "  for (int a = 0; a < k; a++) L += C[idx[a]];\n", ""),
+    ("EDF demand rounds its job count up", "dbf += ((t - s->D[j]) / s->T[j] + 1) * (i128)C[j];",
+     "dbf += ((t - s->D[j] + s->T[j] - 1) / s->T[j] + 1) * (i128)C[j];"),
 ]
 
 

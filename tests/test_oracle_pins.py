@@ -266,6 +266,44 @@ def test_edf_matches_edf_simulation():
     assert ok > 150 and miss > 150 and at_one > 40
 
 
+def test_both_tests_inflate_by_the_conflict_factors():
+    """§4.2 inside the per-partition tests: with both task types present and
+    factors above 1000, at several partition sizes m, the DM response times
+    equal the first jobs' completions in a fixed-priority schedule, and the
+    EDF verdict an EDF schedule, of the WCETs C_i(m) inflated by the
+    conflict rule (restated in refs.conflict_k)."""
+    rng = random.Random(57)
+    periods = [4, 5, 6, 8, 10, 12, 15, 20]
+    kc, km = 1500, 2500
+    cnt = dict(dm_ok=0, dm_miss=0, edf_ok=0, edf_miss=0, inflated=0)
+    for trial in range(500):
+        n = rng.randrange(2, 6)
+        m = rng.randrange(1, 5)
+        T = [rng.choice(periods) for _ in range(n)]
+        D = [rng.randrange(max(1, t // 2), t + 1) for t in T]
+        typ = [rng.randrange(2) for _ in range(n)]
+        A = [rng.randrange(1000, 3000 * m) for _ in range(n)]
+        B = [rng.randrange(0, 1000) for _ in range(n)]
+        C = [oracle.wcet(A[i], B[i], refs.conflict_k(typ, range(n), i, kc, km), m) for i in range(n)]
+        cnt["inflated"] += C != [oracle.wcet(A[i], B[i], 1000, m) for i in range(n)]
+        args = (np.array(T, np.int64), np.array(D, np.int64), np.array(A, np.int64), np.array(B, np.int64),
+                np.array(typ, np.uint8), np.ones(n, np.uint8), m, kc, km)
+        horizon = _hyperperiod(T) + max(D) + 1
+        v, R = oracle.rta(*args)
+        order = refs.dm_order(T, D, range(n))
+        first, _ = refs.simulate_fp([(T[i], D[i], C[i]) for i in order], horizon)
+        for rank, i in enumerate(order):
+            if R[i] >= 0:
+                assert first[rank] == R[i], (trial, T, D, C, i)
+            else:
+                assert first[rank] is None or first[rank] > D[i], (trial, T, D, C, i)
+        cnt["dm_ok" if v else "dm_miss"] += 1
+        ve = oracle.edf(*args)
+        assert ve == int(refs.simulate_edf(list(zip(T, D, C)), 2 * _hyperperiod(T) + max(D) + 1)), (trial, T, D, C)
+        cnt["edf_ok" if ve else "edf_miss"] += 1
+    assert min(cnt.values()) > 50, cnt
+
+
 def test_edf_exact_at_utilisation_one():
     """U is compared with 1 exactly: with D = T a set passes iff U <= 1, at
     U = 1 exactly and one unit of C either side of it, for harmonic pairs,
