@@ -88,6 +88,21 @@ MUTANTS = [
     ("EDF busy period from zero", "  for (int a = 0; a < k; a++) L += C[idx[a]];\n", ""),
     ("EDF demand rounds its job count up", "dbf += ((t - s->D[j]) / s->T[j] + 1) * (i128)C[j];",
      "dbf += ((t - s->D[j] + s->T[j] - 1) / s->T[j] + 1) * (i128)C[j];"),
+    ("RGS allows kmax + 1 blocks", "int top = used < w->kmax ? used : w->kmax - 1;",
+     "int top = used <= w->kmax ? used : w->kmax;"),
+    ("search counts an unschedulable block as size 0", "    if (w->minm_sub[mask[b]] == 0) return;\n", ""),
+    ("search rejects a size sum equal to M", "if (sm + empty * smallest_size(w->md) > w->md->M) return;",
+     "if (sm + empty * smallest_size(w->md) >= w->md->M) return;"),
+    ("compositions skip the largest first part", "for (int64_t v = 1; v <= left - (w->k - 1 - part); v++) {",
+     "for (int64_t v = 1; v < left - (w->k - 1 - part); v++) {"),
+    ("optimum keyed by size sum before W",
+     "  if (W != b->W) return W < b->W;\n  if (sm != b->sum_minm) return sm < b->sum_minm;",
+     "  if (sm != b->sum_minm) return sm < b->sum_minm;\n  if (W != b->W) return W < b->W;"),
+    ("optimum's block sizes left out",
+     "for (int b = 0; b < 8; b++) w->best->minm_block[b] = b < nb ? w->minm_sub[mask[b]] : 0;",
+     "for (int b = 0; b < 8; b++) w->best->minm_block[b] = 0;"),
+    ("spare SMs ignore empty parts", "(j->md.M - best.sum_minm - empty * smallest_size(&j->md))",
+     "(j->md.M - best.sum_minm)"),
 ]
 
 

@@ -640,6 +640,12 @@ def test_exhaustive_explicit_equals_subset_form_and_bruteforce(sched):
         assert bool(a["feasible"][0]) == (best is not None)
         if best is not None:
             assert (a["W"][0], a["sum_minm"][0], tuple(a["rgs"][:n])) == best
+            # the outputs derived from the optimum, as the header defines them
+            nb = int(max(a["rgs"][:n])) + 1
+            assert a["n_blocks"][0] == nb
+            sizes = [minsize([i for i in range(n) if a["rgs"][i] == b]) for b in range(nb)]
+            assert list(a["minm_block"][:kmax]) == sizes + [0] * (kmax - nb)
+            assert a["spare"][0] == M - sum(sizes) - max(0, kmin - nb) * g
 
 
 def test_explicit_candidate_count_single_workload():
