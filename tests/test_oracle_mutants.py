@@ -103,6 +103,11 @@ MUTANTS = [
      "for (int b = 0; b < 8; b++) w->best->minm_block[b] = 0;"),
     ("spare SMs ignore empty parts", "(j->md.M - best.sum_minm - empty * smallest_size(&j->md))",
      "(j->md.M - best.sum_minm)"),
+    ("serving NEW rejects a partition equal to the spare SMs", "if (z && z <= spare) {", "if (z && z < spare) {"),
+    ("serving REMOVE leaves a gap in the numbering", "      if (part_out[i] > pr) part_out[i]--;\n", ""),
+    ("serving summary misses the last partition", "  for (int p = 0; p < np; p++) {\n    pi += size[p];",
+     "  for (int p = 0; p + 1 < np; p++) {\n    pi += size[p];"),
+    ("serving REMOVE skips the renumbering", "  canonical(n2, part_out, size_out, np);\n", ""),
 ]
 
 

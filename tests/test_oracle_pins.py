@@ -919,6 +919,25 @@ def test_serving_paths_match_a_restatement():
     assert {1, 3} <= paths
 
 
+def test_serving_new_partition_may_take_every_spare_sm():
+    """8 SMs, one compute task X held at its Lemma 2 size (A = 1000 * 100,
+    B = 1000 * 60, T = D = 100: C = ceil(100 / m + 60) is 94 at 3 SMs, 110
+    at 2): five SMs spare.  A compute task Y with A = 1000 * 500 needs
+    exactly 5 SMs alone (C = 100).  Beside Y, X takes the compute conflict
+    factor 1.2, at least ceil(1.2 * 72.5) = 87 even at 8 SMs, and Y at least
+    75, so Y neither fits nor grows X's partition; a new partition of 5 SMs
+    fits the 5 spare ones exactly, and the GPU is then full."""
+    def task(a, b):
+        return {"T": 100, "D": 100, "A": 1000 * a, "B": 1000 * b, "u_ppm": a * 10000, "type": 0}
+    t = oracle.Tenant(8, 1, KC, KM)
+    cols = {k: np.array([task(100, 60)[k]], np.uint8 if k == "type" else np.int64) for k in oracle.Tenant.COLS}
+    assert t.admit(cols)["verdict"] == 1
+    assert list(t.size[:t.n_parts]) == [3]
+    r = t.add(task(500, 0))
+    assert r["verdict"] == 1 and r["path"] == 3  # a new partition
+    assert list(t.size[:t.n_parts]) == [3, 5] and r["Pi"] == 8
+
+
 def test_serving_new_partition_must_fit_the_spare_sms():
     """8 SMs held as 3 + 4 (a compute task of C1 = 250 and a memory task of
     C1 = 350, both T = D = 100): one SM spare.  A compute task of C1 = 190
