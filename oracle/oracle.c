@@ -848,7 +848,7 @@ static int valid_set(const oset* s) {
   for (int i = 0; i < s->n; i++) {
     if (s->D[i] < 1 || s->D[i] > s->T[i] || s->T[i] > 2147483647LL) return 0;
     if (s->A[i] < 0 || s->B[i] < 0 || s->A[i] + s->B[i] < 1 || s->A[i] + s->B[i] > ((int64_t)1 << 36)) return 0;
-    if (s->u && (s->u[i] < 0 || s->u[i] > ((int64_t)1 << 32))) return 0;
+    if (s->u && (s->u[i] < 0 || s->u[i] >= ((int64_t)1 << 32))) return 0;
     if (s->type[i] > 1) return 0;
   }
   return 1;

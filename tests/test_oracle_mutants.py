@@ -108,6 +108,15 @@ MUTANTS = [
     ("serving summary misses the last partition", "  for (int p = 0; p < np; p++) {\n    pi += size[p];",
      "  for (int p = 0; p + 1 < np; p++) {\n    pi += size[p];"),
     ("serving REMOVE skips the renumbering", "  canonical(n2, part_out, size_out, np);\n", ""),
+    ("validation admits D > T", "if (s->D[i] < 1 || s->D[i] > s->T[i] || s->T[i] > 2147483647LL) return 0;",
+     "if (s->D[i] < 1 || s->T[i] > 2147483647LL) return 0;"),
+    ("validation refuses A + B = 2^36", "s->A[i] + s->B[i] > ((int64_t)1 << 36)) return 0;",
+     "s->A[i] + s->B[i] >= ((int64_t)1 << 36)) return 0;"),
+    ("validation admits u = 2^32", "s->u[i] >= ((int64_t)1 << 32))) return 0;", "s->u[i] > ((int64_t)1 << 32))) return 0;"),
+    ("WCET tables at sizes in units of one SM", "        int64_t m = g * (mi + 1);\n", "        int64_t m = mi + 1;\n"),
+    ("WCET tables swap the factors by type", "int64_t kx = type[o + t] == 1 ? km : kc;",
+     "int64_t kx = type[o + t] == 1 ? kc : km;"),
+    ("WCET tables transposed", "Cc[o * Mu + mi * n + t] = wcet(", "Cc[o * Mu + t * Mu + mi] = wcet("),
 ]
 
 

@@ -64,6 +64,25 @@ def test_conflict_needs_same_type_partner():
 
 # ---------------------------------------------------------------- WCET model
 
+def test_oracle_refuses_exactly_the_tasks_outside_the_input_bounds():
+    """The library's documented input bounds (1 <= D <= T <= 2^31 - 1,
+    A, B >= 0, 1 <= A + B <= 2^36, 0 <= u_ppm < 2^32, type in {0, 1}): a
+    one-task set at each bound is decided, and one a unit beyond it is
+    marked invalid (reason 5), as the kernels mark it."""
+    base = dict(T=1000, D=1000, A=1000, B=0, u_ppm=1000, type=0)
+    inside = [dict(D=1), dict(T=2**31 - 1, D=2**31 - 1), dict(A=2**36), dict(A=0, B=2**36), dict(A=1),
+              dict(A=0, B=1), dict(A=2**35, B=2**35), dict(u_ppm=2**32 - 1), dict(u_ppm=0), dict(type=1)]
+    outside = [dict(D=0), dict(D=1001), dict(T=2**31, D=2**31), dict(A=0, B=0), dict(A=2**36, B=1),
+               dict(A=-1, B=5), dict(B=-1), dict(u_ppm=2**32), dict(u_ppm=-1), dict(type=2)]
+    cases = [dict(base, **c) for c in inside + outside]
+    s = {k: np.array([c[k] for c in cases], np.uint8 if k == "type" else np.int64)
+         for k in ("T", "D", "A", "B", "u_ppm", "type")}
+    s["set_off"] = np.arange(len(cases) + 1, dtype=np.int64)
+    s["n_max"] = 1
+    r = oracle.allocate(s, 8, 1, KC, KM, policy="ONE_GPU")
+    assert [int(x) != 5 for x in r["reason"]] == [True] * len(inside) + [False] * len(outside), r["reason"]
+
+
 def test_model_constants_golden():
     g = golden("model_constants.json")
     p = workloads.gen_params("paper50")
