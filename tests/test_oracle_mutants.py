@@ -117,6 +117,9 @@ MUTANTS = [
     ("WCET tables swap the factors by type", "int64_t kx = type[o + t] == 1 ? km : kc;",
      "int64_t kx = type[o + t] == 1 ? kc : km;"),
     ("WCET tables transposed", "Cc[o * Mu + mi * n + t] = wcet(", "Cc[o * Mu + t * Mu + mi] = wcet("),
+    ("model admits M = 1025", "md->M > 1024 ||", "md->M > 1025 ||"),
+    ("model admits g not dividing M", " || md->M % md->g != 0) return 0;", ") return 0;"),
+    ("model admits a compute factor below 1000", "if (md->kc < 1000 ||", "if (md->kc < 999 ||"),
 ]
 
 
@@ -166,7 +169,9 @@ def _failing_pins(source, tmp_path, first_only=False):
             t0 = time.perf_counter()
             try:
                 f(**kw)
-            except Exception:  # an AssertionError, or a status the mutant made the oracle return
+            # an AssertionError, a status the mutant made the oracle return, or
+            # pytest.raises finding no error (pytest's Failed is no Exception)
+            except (Exception, pytest.fail.Exception):
                 failed.append(name)
                 if first_only:
                     break

@@ -83,6 +83,18 @@ def test_oracle_refuses_exactly_the_tasks_outside_the_input_bounds():
     assert [int(x) != 5 for x in r["reason"]] == [True] * len(inside) + [False] * len(outside), r["reason"]
 
 
+def test_oracle_refuses_exactly_the_models_outside_the_bounds():
+    """The documented model bounds (1 <= g, g | M, 1 <= M <= 1024, 1000 <=
+    k_c, k_m <= 16000): accepted at each bound, refused one step beyond."""
+    s = gen_tasksets(seed=3, nsets=4, n_min=1, n_max=4, U_lo_ppm=100000, U_hi_ppm=900000, deadline_pm=750)
+    for M, g, kc, km in ((1, 1, 1000, 1000), (1024, 1, 16000, 16000), (1024, 1024, 1000, 16000), (12, 4, 1200, 2300)):
+        oracle.allocate(s, M, g, kc, km)
+    for M, g, kc, km in ((0, 1, 1200, 2300), (1025, 1, 1200, 2300), (12, 5, 1200, 2300), (12, 0, 1200, 2300),
+                         (12, 1, 999, 2300), (12, 1, 1200, 999), (12, 1, 16001, 2300), (12, 1, 1200, 16001)):
+        with pytest.raises(RuntimeError):
+            oracle.allocate(s, M, g, kc, km)
+
+
 def test_model_constants_golden():
     g = golden("model_constants.json")
     p = workloads.gen_params("paper50")
