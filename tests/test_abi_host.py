@@ -40,6 +40,44 @@ def test_header_documents_every_entry_point():
         assert "/*" in before or "*/" in before, n
 
 
+def _ctx_entry_points():
+    """(name, ctypes argument types) of every declared entry point whose first
+    parameter is the context, from the header's declarations."""
+    text = open(os.path.join(ROOT, "include", "gpa.h")).read()
+    out = []
+    for name, params in re.findall(r"^\s*int32_t\s+(gpa_\w+)\s*\(([^)]*)\)\s*;", text, flags=re.M):
+        ps = [q.strip() for q in params.split(",")]
+        if not ps or not ps[0].startswith("gpa_ctx*"):
+            continue
+        types = []
+        for q in ps:
+            if "*" in q:
+                types.append(ctypes.c_void_p)
+            elif q.startswith("uint64_t"):
+                types.append(ctypes.c_uint64)
+            elif q.startswith("int64_t"):
+                types.append(ctypes.c_int64)
+            else:
+                assert q.startswith("int32_t"), (name, q)
+                types.append(ctypes.c_int32)
+        out.append((name, types))
+    return out
+
+
+def test_every_context_entry_point_rejects_a_null_context():
+    """No entry point dereferences a NULL context: each returns GPA_ERR_ARG
+    (gpa_ctx_destroy: GPA_OK, nothing to free) before any CUDA call, so this
+    runs without a GPU."""
+    fns = _ctx_entry_points()
+    assert len(fns) >= 15 and "gpa_allocate_multi" in [n for n, _ in fns]
+    lib = ctypes.CDLL(gpa.LIB_PATH)
+    for name, types in fns:
+        f = getattr(lib, name)
+        f.argtypes, f.restype = types, ctypes.c_int32
+        code = f(*[None if t is ctypes.c_void_p else 0 for t in types])
+        assert code == (gpa.OK if name == "gpa_ctx_destroy" else gpa.ERR_ARG), (name, code)
+
+
 def test_ctx_create_without_gpu_fails_cleanly():
     import torch
     if torch.cuda.is_available():
