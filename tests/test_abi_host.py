@@ -40,14 +40,14 @@ def test_header_documents_every_entry_point():
         assert "/*" in before or "*/" in before, n
 
 
-def _ctx_entry_points():
+def _entry_points(with_ctx):
     """(name, ctypes argument types) of every declared entry point whose first
-    parameter is the context, from the header's declarations."""
+    parameter is (with_ctx) or is not the context, from the header."""
     text = open(os.path.join(ROOT, "include", "gpa.h")).read()
     out = []
     for name, params in re.findall(r"^\s*int32_t\s+(gpa_\w+)\s*\(([^)]*)\)\s*;", text, flags=re.M):
-        ps = [q.strip() for q in params.split(",")]
-        if not ps or not ps[0].startswith("gpa_ctx*"):
+        ps = [q.strip() for q in params.split(",") if q.strip()]
+        if bool(ps) and ps[0].startswith("gpa_ctx*") != with_ctx:
             continue
         types = []
         for q in ps:
@@ -68,7 +68,7 @@ def test_every_context_entry_point_rejects_a_null_context():
     """No entry point dereferences a NULL context: each returns GPA_ERR_ARG
     (gpa_ctx_destroy: GPA_OK, nothing to free) before any CUDA call, so this
     runs without a GPU."""
-    fns = _ctx_entry_points()
+    fns = _entry_points(True)
     assert len(fns) >= 15 and "gpa_allocate_multi" in [n for n, _ in fns]
     lib = ctypes.CDLL(gpa.LIB_PATH)
     for name, types in fns:
@@ -76,6 +76,21 @@ def test_every_context_entry_point_rejects_a_null_context():
         f.argtypes, f.restype = types, ctypes.c_int32
         code = f(*[None if t is ctypes.c_void_p else 0 for t in types])
         assert code == (gpa.OK if name == "gpa_ctx_destroy" else gpa.ERR_ARG), (name, code)
+
+
+def test_every_other_entry_point_rejects_null_arguments():
+    """The entry points without a context, given NULL pointers and zero
+    sizes, return an error status instead of dereferencing them (the
+    allocation-free call's status read is left out: a NULL stream is the
+    default stream, valid wherever a GPU is)."""
+    fns = [(n, t) for n, t in _entry_points(False) if n != "gpa_allocate_noalloc_status"]
+    assert {"gpa_validate", "gpa_gen_tasksets", "gpa_allocate_noalloc", "gpa_fit_wcet"} <= {n for n, _ in fns}
+    lib = ctypes.CDLL(gpa.LIB_PATH)
+    for name, types in fns:
+        f = getattr(lib, name)
+        f.argtypes, f.restype = types, ctypes.c_int32
+        code = f(*[None if t is ctypes.c_void_p else 0 for t in types])
+        assert code < 0, (name, code)
 
 
 def test_ctx_create_without_gpu_fails_cleanly():
