@@ -402,11 +402,15 @@ int32_t gpa_allocate(gpa_ctx* ctx, const gpa_tasksets* sets, const gpa_model* mo
  *  - Device arrays: the same work as npolicies gpa_allocate calls in order on
  *    the context stream (asynchronous, as gpa_allocate).
  *  - Every results[i] must have mem == sets->mem and arrays of its own (no
- *    two results may share an array); the checks of gpa_allocate apply to
- *    each params[i] and results[i], and a failed check writes nothing.
+ *    two results may share an array); the argument checks of gpa_allocate
+ *    apply to each params[i] and results[i], and an argument that fails
+ *    them is reported before any copy or launch.
  *  - Status: the first error, as gpa_allocate reports it; an undecided or
  *    invalid set under any of the policies gives GPA_ERR_TIMEOUT or
- *    GPA_ERR_RANGE, and each result's reason[] marks its own sets. */
+ *    GPA_ERR_RANGE, and each result's reason[] marks its own sets.  Host
+ *    sets out of bounds are handled as by gpa_allocate (GPA_ERR_RANGE naming
+ *    the first; the outputs unspecified when the batch was split into
+ *    slices, untouched otherwise). */
 int32_t gpa_allocate_multi(gpa_ctx* ctx, const gpa_tasksets* sets, const gpa_model* model,
                            const gpa_params* params, int32_t npolicies, gpa_alloc_result* results);
 
