@@ -150,6 +150,21 @@ def scaled_traffic(prof, ntasks):
                     "kernel, scaled by tasks"}
 
 
+def e2e_bytes(calls, nsets, ntasks, kmax, multi):
+    """Bytes one end-to-end step copies in and out.  In: the task columns
+    (set_off as int64 per set and one more; T, D, A, B, u_ppm as int64 and
+    type as a byte per task), once per call, or once for every policy of a
+    multi-policy call.  Out, per call: an allocation's verdict and reason
+    (bytes), n_parts, Pi and n_tests (int32) and W (int64) per set, and
+    part_of_task (byte) and size_of_part (int16) per task; a search's
+    feasible (byte), W (int64), sum_minm, n_blocks and spare (int32) per
+    set, rgs (byte) per task and minm_block (int16) per set and block."""
+    h2d = (8 * (nsets + 1) + 41 * ntasks) * (1 if multi else len(calls))
+    d2h = sum((22 * nsets + 3 * ntasks) if c not in ("SEARCH", "EXPLICIT") else
+              (21 * nsets + ntasks + 2 * kmax * nsets) for c in calls)
+    return h2d, d2h
+
+
 def gpu_id_for_smi(local):
     """nvidia-smi id of the CUDA device `local` (UUID when torch exposes it)."""
     try:
@@ -769,9 +784,7 @@ def measure(bench, name, rank, world, steps, warmup, with_cpu=True, e2e_steps=5,
         ctx = saved
         ctx_h.close()
         e2e_t = shard.max_over_ranks(float(np.mean(times)))
-        h2d = (8 * (nsets + 1) + 41 * ntasks) * (1 if multi else len(calls))
-        d2h = sum((22 * nsets + 3 * ntasks) if c not in ("SEARCH", "EXPLICIT") else
-                  (21 * nsets + ntasks + 2 * wp["kmax"] * nsets) for c in calls)
+        h2d, d2h = e2e_bytes(calls, nsets, ntasks, wp["kmax"], multi)
         ms = sorted(1000.0 * t for t in times)
         e2e = {"value": total_sets / e2e_t, "unit": "tasksets/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": 1000.0 * e2e_t,

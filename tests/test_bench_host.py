@@ -42,3 +42,22 @@ def test_reference_arm_other_ranks_print_nothing():
     lines = _run(["--impl", "reference", "--nsets", "200", "--steps", "1", "--warmup", "1", "--gpus", "2"],
                  env={"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert lines == []
+
+
+@pytest.mark.parametrize("calls,multi", [(("SMS", "ONE_GPU"), True), (("SMS", "ONE_GPU"), False), (("SMS",), False),
+                                         (("SEARCH",), False), (("EXPLICIT",), False)])
+def test_e2e_byte_counts_are_the_copied_arrays(calls, multi):
+    """The end-to-end line's bytes per step equal the sizes of the arrays the
+    calls copy: the input columns (once for a multi-policy call) and every
+    call's result arrays, as the binding allocates them."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import paper_2105_10312_gb300 as gpa
+    s = gpa.gen_tasksets(seed=5, nsets=300, n_min=0, n_max=12, U_lo_ppm=100000, U_hi_ppm=2000000, deadline_pm=750)
+    nsets, ntasks, kmax = 300, int(s["set_off"][-1]), 4
+    cols = sum(s[k].nbytes for k in ("set_off", "T", "D", "A", "B", "u_ppm", "type"))
+    outs = 0
+    for c in calls:
+        o = gpa.Context.best_result(None, s, kmax) if c in ("SEARCH", "EXPLICIT") else gpa.Context.alloc_result(None, s)
+        outs += sum(v.nbytes for v in o.values() if v is not None)
+    assert bench.e2e_bytes(calls, nsets, ntasks, kmax, multi) == (cols * (1 if multi else len(calls)), outs)
