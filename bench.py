@@ -784,7 +784,7 @@ def measure(bench, name, rank, world, steps, warmup, with_cpu=True, e2e_steps=5,
         ctx = saved
         ctx_h.close()
         e2e_t = shard.max_over_ranks(float(np.mean(times)))
-        h2d, d2h = e2e_bytes(calls, nsets, ntasks, wp["kmax"], multi)
+        h2d, d2h = e2e_bytes(calls, nsets, ntasks, wp.get("kmax", 0), multi)  # kmax: searches only
         ms = sorted(1000.0 * t for t in times)
         e2e = {"value": total_sets / e2e_t, "unit": "tasksets/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": 1000.0 * e2e_t,

@@ -61,3 +61,15 @@ def test_e2e_byte_counts_are_the_copied_arrays(calls, multi):
         o = gpa.Context.best_result(None, s, kmax) if c in ("SEARCH", "EXPLICIT") else gpa.Context.alloc_result(None, s)
         outs += sum(v.nbytes for v in o.values() if v is not None)
     assert bench.e2e_bytes(calls, nsets, ntasks, kmax, multi) == (cols * (1 if multi else len(calls)), outs)
+
+
+def test_every_workload_with_a_search_call_has_its_block_limit():
+    """Each bench workload whose step makes a search call names kmax (the
+    end-to-end byte count and the search calls read it); the others need none."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2105_10312_gb300 import workloads as W
+    for name, calls in bench.CALLS.items():
+        wp = W.WORKLOADS.get(name, W.WORKLOADS["batch"])
+        if any(c in ("SEARCH", "EXPLICIT") for c in calls):
+            assert "kmax" in wp and "kmin" in wp, name
