@@ -120,6 +120,15 @@ MUTANTS = [
     ("model admits M = 1025", "md->M > 1024 ||", "md->M > 1025 ||"),
     ("model admits g not dividing M", " || md->M % md->g != 0) return 0;", ") return 0;"),
     ("model admits a compute factor below 1000", "if (md->kc < 1000 ||", "if (md->kc < 999 ||"),
+    ("ACT counts each pair twice",
+     "        tests++;\n        if (minm(s, md, in, lo, hi, linear) == 0) act_pair",
+     "        tests += 2;\n        if (minm(s, md, in, lo, hi, linear) == 0) act_pair"),
+    ("SMS counts only passing candidates",
+     "        int64_t m3 = minm(s, md, in, lo, hi, linear);\n        tests++;\n        if (m3 > 0 && (best < 0",
+     "        int64_t m3 = minm(s, md, in, lo, hi, linear);\n        if (m3 > 0) tests++;\n        if (m3 > 0 && (best < 0"),
+    ("par_list never re-sorted", "  while (Pi > md->M) {\n    sort_par_list(s, list, np);", "  while (Pi > md->M) {"),
+    ("BF tries its candidates unsorted",
+     "        while (j >= 0 && w[j] > xw) { elig[j + 1] = elig[j]; w[j + 1] = w[j]; j--; }", "        while (0) { }"),
 ]
 
 
