@@ -831,6 +831,11 @@ static int64_t search_explicit(const oset* s, const omodel* md, int kmin, int km
 
 /* ------------------------------------------------------------ validation */
 
+/* The library's input bounds.  Model: 1 <= g, g | M, 1 <= M <= 1024, an
+ * increasing size list of multiples of g in [g, M], DM or EDF, factors in
+ * [1000, 16000] per mille.  Task: 1 <= D <= T <= 2^31 - 1, A, B >= 0,
+ * 1 <= A + B <= 2^36, 0 <= u_ppm < 2^32, type 0 or 1.  A set with a task
+ * outside them is marked invalid; a model outside them fails the call. */
 static int valid_model(const omodel* md) {
   if (md->g < 1 || md->M < 1 || md->M > 1024 || md->M % md->g != 0) return 0;
   if (md->sched != S_DM && md->sched != S_EDF) return 0;
