@@ -178,6 +178,35 @@ def test_generator_is_deterministic_and_shaped():
         assert abs(U - 0.1 * (s % 60 + 1)) < 0.02 * (e - o) / 10 + 0.01
 
 
+def test_generator_follows_the_stated_input_recipe():
+    """The recipe the workloads are described by: the paper's setting takes
+    its periods from the divisors of 4000 in [50, 4000], D = 0.75 T, 50
+    tasks, U = 2, 4, .. 68 by set index and memory intensity uniform (half
+    the tasks memory-bound); the sweep's periods are log-uniform on
+    [10^4, 10^6]; utilisations are uniform on the simplex sum u = U, whose
+    marginal u_i / U is Beta(1, n - 1): variance (n - 1) / (n^2 (n + 1)) and
+    P(u_i / U > 2 / n) = (1 - 2 / n)^(n - 1)."""
+    from paper_2105_10312_gb300 import workloads as W
+    p = gpa.gen_tasksets(**W.gen_params("paper50", nsets=680))
+    div = [d for d in range(50, 4001) if 4000 % d == 0]
+    assert set(p["T"].tolist()) <= set(div) and len(set(p["T"].tolist())) > 10
+    assert (p["D"] == p["T"] * 750 // 1000).all() and (np.diff(p["set_off"]) == 50).all()
+    assert 0.45 < p["type"].mean() < 0.55
+    for k in range(0, 680, 23):
+        o, e = p["set_off"][k], p["set_off"][k + 1]
+        assert abs((p["C1"][o:e] / p["T"][o:e]).sum() - 2 * (k % 34 + 1)) < 0.1
+    w = gpa.gen_tasksets(**W.gen_params("sweep", nsets=3000))
+    lt = np.log10(w["T"])
+    assert lt.min() >= 4 and lt.max() <= 6 and abs(lt.mean() - 5) < 0.02 and abs((lt < 5).mean() - 0.5) < 0.02
+    n = 8
+    u = gpa.gen_tasksets(seed=11, nsets=3000, n_min=n, n_max=n, U_lo_ppm=2000000, U_hi_ppm=2000000,
+                         deadline_pm=750, T_lo=1000000, T_hi=10000000)
+    share = (u["C1"] / u["T"]).reshape(-1, n)
+    share = share / share.sum(axis=1, keepdims=True)
+    assert abs(share.var() / ((n - 1) / (n * n * (n + 1))) - 1) < 0.05
+    assert abs((share > 2 / n).mean() - (1 - 2 / n) ** (n - 1)) < 0.015
+
+
 def test_task_limits():
     """Sets of up to 256 tasks pass the host check and the generator; 257
     do not (the serving tenants' 128-task limit is checked on the GPU)."""
