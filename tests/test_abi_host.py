@@ -183,7 +183,7 @@ def test_generator_follows_the_stated_input_recipe():
     its periods from the divisors of 4000 in [50, 4000], D = 0.75 T, 50
     tasks, U = 2, 4, .. 68 by set index and memory intensity uniform (half
     the tasks memory-bound); the sweep's periods are log-uniform on
-    [10^4, 10^6]; utilisations are uniform on the simplex sum u = U, whose
+    [10^4, 10^6] and its intensity Beta(2, 5); utilisations are uniform on the simplex sum u = U, whose
     marginal u_i / U is Beta(1, n - 1): variance (n - 1) / (n^2 (n + 1)) and
     P(u_i / U > 2 / n) = (1 - 2 / n)^(n - 1)."""
     from paper_2105_10312_gb300 import workloads as W
@@ -198,6 +198,9 @@ def test_generator_follows_the_stated_input_recipe():
     w = gpa.gen_tasksets(**W.gen_params("sweep", nsets=3000))
     lt = np.log10(w["T"])
     assert lt.min() >= 4 and lt.max() <= 6 and abs(lt.mean() - 5) < 0.02 and abs((lt < 5).mean() - 0.5) < 0.02
+    # Beta(2, 5) intensity (second order statistic of six uniforms) >= 0.5
+    # when at most one of the six is below 0.5: probability 7 / 64
+    assert abs(w["type"].mean() - 7 / 64) < 0.005
     n = 8
     u = gpa.gen_tasksets(seed=11, nsets=3000, n_min=n, n_max=n, U_lo_ppm=2000000, U_hi_ppm=2000000,
                          deadline_pm=750, T_lo=1000000, T_hi=10000000)
